@@ -1,0 +1,310 @@
+"""Pins for the FP64 oracle: closed forms, library routines and invariants.
+
+Each test ties the oracle to something other than itself, so that a dropped
+term, a wrong sign or a transposed message index fails at least one of them:
+
+* the 2-node graph worked by hand (tests/golden/n2_closed_form.json),
+* trees, where GaBP is exact in means and precisions after diameter rounds,
+* dense diagonally dominant matrices, where the converged means solve Q mu = b
+  (numpy's LAPACK solve),
+* equality of the information form, the printed form of Algorithm 2 and
+  Algorithm 1 round by round,
+* invariants (precisions independent of b, linearity in b, permutation
+  equivariance, message fixed-point equations),
+* the RBF matrix against scipy's pairwise distances and hand values,
+* the decision function against the SVM matrix, the dual objective at the
+  optimum, matrix-free CG against a dense solve, the box-QP brute force
+  against scipy's bounded minimiser and its KKT conditions.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0810_1648_gb300 import workloads
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _dd_matrix(n, seed, delta=0.2, density=1.0):
+    """Random symmetric matrix with a dominant diagonal, mixed signs."""
+    rng = np.random.default_rng(seed)
+    A = rng.uniform(-1, 1, (n, n))
+    if density < 1.0:
+        A *= rng.uniform(0, 1, (n, n)) < density
+    A = np.triu(A, 1)
+    A = A + A.T
+    d = (1 + delta) * np.abs(A).sum(1) + rng.uniform(0.1, 1.0, n)
+    A[np.diag_indices(n)] = d
+    return A
+
+
+# ---------------------------------------------------------------- 2-node graph
+def test_two_node_closed_form():
+    g = json.load(open(os.path.join(GOLD, "n2_closed_form.json")))
+    Q, b = np.array(g["Q"]), np.array(g["b"])
+    r0 = oracle.gabp(Q, b, iters=0)
+    np.testing.assert_allclose(r0.Pt, g["t0"]["Ptilde"], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(r0.mu, g["t0"]["mutilde"], rtol=0, atol=1e-15)
+    for t in range(1, 6):
+        r = oracle.gabp(Q, b, iters=t, keep_messages=True)
+        np.testing.assert_allclose(r.Pt, g["t_ge_1"]["Ptilde"], rtol=1e-15)
+        np.testing.assert_allclose(r.mu, g["t_ge_1"]["mutilde"], rtol=1e-15)
+        assert r.rinf <= 1e-15
+        m = g["messages_t_ge_1"]
+        # Pin[i, k] = P_ki: message node1 -> node2 sits in row 1 (0-based).
+        assert r.Pin[1, 0] == pytest.approx(m["P_12"], rel=1e-15)
+        assert r.Pin[0, 1] == pytest.approx(m["P_21"], rel=1e-15)
+        assert r.Hin[1, 0] == pytest.approx(m["H_12"], rel=1e-15)
+        assert r.Hin[0, 1] == pytest.approx(m["H_21"], rel=1e-15)
+    # with a tolerance, the first converged round is t = 1
+    r = oracle.gabp(Q, b, iters=50, tol=1e-12)
+    assert r.kstar == 1
+
+
+# ----------------------------------------------------------------------- trees
+def _chain(n, seed):
+    rng = np.random.default_rng(seed)
+    A = np.zeros((n, n))
+    off = rng.uniform(-1, 1, n - 1)
+    A[np.arange(n - 1), np.arange(1, n)] = off
+    A[np.arange(1, n), np.arange(n - 1)] = off
+    A[np.diag_indices(n)] = np.abs(A).sum(1) * rng.uniform(0.8, 1.5, n) + 0.2
+    return A
+
+
+def _star(n, seed):
+    rng = np.random.default_rng(seed)
+    A = np.zeros((n, n))
+    off = rng.uniform(-1, 1, n - 1)
+    A[0, 1:] = off
+    A[1:, 0] = off
+    A[np.diag_indices(n)] = np.abs(A).sum(1) * 1.3 + 0.1
+    return A
+
+
+@pytest.mark.parametrize("make,n,diam", [(_chain, 9, 8), (_star, 12, 2)])
+def test_tree_exact_means_and_precisions(make, n, diam):
+    Q = make(n, 3)
+    assert np.all(np.linalg.eigvalsh(Q) > 0)
+    b = np.random.default_rng(4).standard_normal(n)
+    inv = np.linalg.inv(Q)
+    r = oracle.gabp(Q, b, iters=diam)
+    np.testing.assert_allclose(r.mu, inv @ b, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(r.Pt, 1.0 / np.diag(inv), rtol=1e-12)
+    # before `diam` rounds the far ends have not heard from each other yet
+    r_early = oracle.gabp(Q, b, iters=diam - 1)
+    assert np.max(np.abs(r_early.mu - inv @ b)) > 1e-9
+
+
+# ------------------------------------------------------- dense DD fixed point
+@pytest.mark.parametrize("n,seed", [(5, 1), (17, 2), (64, 3)])
+def test_dense_fixed_point_is_linear_solve(n, seed):
+    Q = _dd_matrix(n, seed)
+    b = np.ones(n)
+    ref = np.linalg.solve(Q, b)
+    r = oracle.gabp(Q, b, iters=2000, tol=1e-13)
+    assert r.kstar < 2000
+    np.testing.assert_allclose(r.mu, ref, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(oracle.cholesky_solve(Q, b), ref, rtol=1e-12, atol=1e-14)
+    # residual history is what it claims: ||b - Q mu||_inf at kstar
+    assert r.rinf == pytest.approx(np.max(np.abs(b - Q @ r.mu)), rel=1e-6, abs=1e-13)
+
+
+def test_loopy_precisions_are_not_exact():
+    """On a loopy graph only the means are exact (Section 2 convergence)."""
+    Q = _dd_matrix(10, 5)
+    r = oracle.gabp(Q, np.ones(10), iters=3000, tol=1e-14)
+    inv = np.linalg.inv(Q)
+    np.testing.assert_allclose(r.mu, inv @ np.ones(10), rtol=1e-10)
+    assert np.max(np.abs(r.Pt - 1.0 / np.diag(inv)) / r.Pt) > 1e-6
+
+
+# ------------------------------------------------------------ form equivalence
+@pytest.mark.parametrize("n,seed,density", [(6, 7, 1.0), (12, 8, 1.0), (15, 9, 0.5)])
+@pytest.mark.parametrize("iters", [1, 2, 3, 7])
+def test_three_forms_agree_round_by_round(n, seed, density, iters):
+    Q = _dd_matrix(n, seed, density=density)
+    b = np.random.default_rng(seed).standard_normal(n)
+    r = oracle.gabp(Q, b, iters=iters)
+    mu_l, Pt_l = oracle.gabp_literal(Q, b, iters=iters)
+    mu_1, Pt_1 = oracle.gabp_alg1(Q, b, iters=iters)
+    np.testing.assert_allclose(r.mu, mu_l, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(r.Pt, Pt_l, rtol=1e-12)
+    np.testing.assert_allclose(r.mu, mu_1, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(r.Pt, Pt_1, rtol=1e-12)
+
+
+# ------------------------------------------------------------------ invariants
+def test_precisions_do_not_depend_on_b_and_means_are_linear_in_b():
+    Q = _dd_matrix(20, 11)
+    rng = np.random.default_rng(12)
+    b1, b2 = rng.standard_normal(20), rng.standard_normal(20)
+    for it in (1, 4, 9):
+        r1 = oracle.gabp(Q, b1, iters=it)
+        r2 = oracle.gabp(Q, b2, iters=it)
+        r3 = oracle.gabp(Q, 2.0 * b1 - 3.0 * b2, iters=it)
+        np.testing.assert_array_equal(r1.Pt, r2.Pt)
+        np.testing.assert_allclose(r3.mu, 2.0 * r1.mu - 3.0 * r2.mu, rtol=1e-11, atol=1e-13)
+
+
+def test_permutation_equivariance():
+    Q = _dd_matrix(14, 13)
+    b = np.random.default_rng(14).standard_normal(14)
+    perm = np.random.default_rng(15).permutation(14)
+    r = oracle.gabp(Q, b, iters=6)
+    rp = oracle.gabp(Q[np.ix_(perm, perm)], b[perm], iters=6)
+    np.testing.assert_allclose(rp.mu, r.mu[perm], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(rp.Pt, r.Pt[perm], rtol=1e-12)
+
+
+def test_message_fixed_point_equations_hold_at_convergence():
+    n = 16
+    Q = _dd_matrix(n, 21)
+    b = np.ones(n)
+    r = oracle.gabp(Q, b, iters=3000, tol=1e-14, keep_messages=True)
+    Pin, Hin = r.Pin, r.Hin
+    ht = b + (Hin.sum(1) - np.diag(Hin))
+    for i in range(n):
+        for j in range(n):
+            if i == j:
+                continue
+            cav = r.Pt[i] - Pin[i, j]            # P_{i\j} = Ptilde_i - P_ji
+            assert cav > 0
+            # message i->j is stored at Pin[j, i]
+            assert Pin[j, i] == pytest.approx(-Q[i, j] ** 2 / cav, rel=1e-9)
+            assert Hin[j, i] == pytest.approx(-Q[i, j] * (ht[i] - Hin[i, j]) / cav,
+                                              rel=1e-8, abs=1e-14)
+
+
+def test_pair_update_matches_one_round():
+    n = 9
+    Q = _dd_matrix(n, 31)
+    b = np.ones(n)
+    r1 = oracle.gabp(Q, b, iters=3, keep_messages=True)
+    r2 = oracle.gabp(Q, b, iters=4, keep_messages=True)
+    ht = b + (r1.Hin.sum(1) - np.diag(r1.Hin))
+    for (i, j) in [(0, 1), (2, 7), (5, 8)]:
+        msg = [r1.Pin[j, i], r1.Pin[i, j], r1.Hin[j, i], r1.Hin[i, j]]
+        out = oracle.pair_update(Q[i, j], r1.Pt[i], ht[i], r1.Pt[j], ht[j], msg)
+        np.testing.assert_allclose(out, [r2.Pin[j, i], r2.Pin[i, j], r2.Hin[j, i], r2.Hin[i, j]],
+                                   rtol=1e-14)
+
+
+def test_non_dominant_matrix_reports_numeric_failure():
+    # Strongly coupled 3-cycle with a tiny diagonal: the cavity precision
+    # P_ii + sum P_ki goes nonpositive in the first rounds.
+    Q = np.array([[0.1, 1.0, 1.0], [1.0, 0.1, 1.0], [1.0, 1.0, 0.1]])
+    with pytest.raises(oracle.OracleError):
+        oracle.gabp(Q, np.ones(3), iters=20)
+
+
+# ------------------------------------------------------------------ SVM matrix
+def test_q_matches_scipy_rbf_and_hand_values():
+    from scipy.spatial.distance import cdist
+
+    p = workloads.two_gaussians(40, 5, seed=3)
+    lam = 1.0 / p.n
+    Q = oracle.build_q(p.X, p.y, p.gamma, p.C)
+    K = np.exp(-p.gamma * cdist(p.X, p.X, "sqeuclidean"))
+    Dm = np.outer(p.y, p.y) * (K + lam * lam)
+    off = ~np.eye(p.n, dtype=bool)
+    np.testing.assert_allclose(Q[off], Dm[off], rtol=1e-13)
+    np.testing.assert_array_equal(Q, Q.T)
+    # dominant rule: Q_ii = max(1 + lam^2 + 1/C, (1 + delta) sum_{j != i} |Q_ij|)
+    R = np.abs(Q).sum(1) - np.diag(Q)
+    floor = 1.0 + lam * lam + 1.0 / p.C
+    np.testing.assert_allclose(np.diag(Q), np.maximum(1.1 * R, floor), rtol=1e-14)
+    assert np.any(1.1 * R < floor) and np.any(1.1 * R > floor)   # both branches seen
+    # soft2 rule: D_ii + 1/C
+    Q2 = oracle.build_q(p.X, p.y, p.gamma, p.C, diag_rule=oracle.DIAG_SOFT2)
+    np.testing.assert_allclose(np.diag(Q2), 1.0 + lam * lam + 1.0 / p.C, rtol=1e-15)
+    # hand value: x=(0,0), x'=(1,0), gamma=1/2, y=(+1,-1), lambda=0.5
+    q = oracle.q_offdiag([0.0, 0.0], [1.0, 0.0], 1.0, -1.0, 0.5, 0.5)
+    assert q == pytest.approx(-(np.exp(-0.5) + 0.25), rel=1e-15)
+    # translation invariance of the RBF kernel
+    Qs = oracle.build_q(p.X + 3.25, p.y, p.gamma, p.C)
+    np.testing.assert_allclose(Qs, Q, rtol=1e-12)
+    # small-C floor of the diagonal rule
+    assert oracle.q_diag(0.5, 0.1, 0.25) == pytest.approx(1.0 + 0.01 + 4.0)
+
+
+def test_workload_solve_reaches_the_linear_solve():
+    p = workloads.two_gaussians(300, 10, seed=5)
+    Q, r = oracle.solve_svm(p.X, p.y, p.gamma, p.C, iters=400, tol=1e-10)
+    assert r.kstar < 400
+    ref = np.linalg.solve(Q, np.ones(p.n))
+    np.testing.assert_allclose(r.mu, ref, rtol=1e-8, atol=1e-12)
+    # residual decreases over the run (dominant diagonal: contraction)
+    assert r.rhist[-1] < 1e-3 * r.rhist[0]
+
+
+# ------------------------------------------------------------ decision / dual
+def test_decision_matches_svm_matrix_on_training_points():
+    p = workloads.two_gaussians(60, 4, seed=6)
+    lam = 1.0 / p.n
+    Q = oracle.build_q(p.X, p.y, p.gamma, p.C)
+    alpha = np.random.default_rng(7).uniform(0, 1, p.n)
+    f = oracle.decision(p.X, p.y, alpha, p.X, p.gamma)
+    # f(x_k) = y_k (D alpha)_k with D = Q except D_kk = 1 + lambda^2
+    D = Q.copy()
+    D[np.diag_indices(p.n)] = 1.0 + lam * lam
+    np.testing.assert_allclose(f, p.y * (D @ alpha), rtol=1e-12, atol=1e-13)
+    from scipy.spatial.distance import cdist
+    Xt = workloads.test_points(p, 7, seed=8)
+    K = np.exp(-p.gamma * cdist(Xt, p.X, "sqeuclidean"))
+    np.testing.assert_allclose(oracle.decision(p.X, p.y, alpha, Xt, p.gamma),
+                               (K + lam * lam) @ (alpha * p.y), rtol=1e-12)
+
+
+def test_dual_objective():
+    Q = _dd_matrix(12, 41)
+    h = np.random.default_rng(42).uniform(0, 1, 12)
+    assert oracle.dual_objective(Q, h) == pytest.approx(h.sum() - 0.5 * h @ Q @ h, rel=1e-13)
+    # at the unconstrained optimum a* = Q^-1 1 the value is 1/2 sum a*
+    a = np.linalg.solve(Q, np.ones(12))
+    assert oracle.dual_objective(Q, a) == pytest.approx(0.5 * a.sum(), rel=1e-12)
+
+
+def test_matrix_free_cg_matches_dense_solve():
+    p = workloads.mixture(150, 8, seed=9, C=2.0)
+    Q = oracle.build_q(p.X, p.y, p.gamma, p.C)
+    x, its = oracle.cg_rbf(p.X, p.y, p.gamma, p.C, rtol=1e-13)
+    np.testing.assert_allclose(x, np.linalg.solve(Q, np.ones(p.n)), rtol=1e-9, atol=1e-13)
+    row = oracle.q_row(p.X, p.y, 17, p.gamma, p.C)
+    np.testing.assert_allclose(row, Q[17], rtol=1e-14)
+
+
+# ------------------------------------------------------------------ box QP
+@pytest.mark.parametrize("n,seed,C", [(6, 51, 0.05), (9, 52, 0.3), (11, 53, 10.0)])
+def test_boxqp_bruteforce_against_scipy_and_kkt(n, seed, C):
+    from scipy.optimize import minimize
+
+    p = workloads.two_gaussians(n, 3, seed=seed)
+    Q = oracle.build_q(p.X, p.y, p.gamma, p.C, diag_rule=oracle.DIAG_SOFT2)
+    a, nk = oracle.boxqp_bruteforce(Q, C)
+    assert nk == 1          # strictly convex: exactly one KKT point
+    g = Q @ a - 1.0
+    assert np.all(a >= -1e-12) and np.all(a <= C + 1e-12)
+    free = (a > 1e-9) & (a < C - 1e-9)
+    assert np.all(np.abs(g[free]) < 1e-9)
+    assert np.all(g[a <= 1e-9] >= -1e-9) and np.all(g[a >= C - 1e-9] <= 1e-9)
+    res = minimize(lambda v: 0.5 * v @ Q @ v - v.sum(), np.full(n, C / 2),
+                   jac=lambda v: Q @ v - 1.0, bounds=[(0, C)] * n, method="L-BFGS-B",
+                   options={"ftol": 1e-15, "gtol": 1e-12, "maxiter": 10000})
+    np.testing.assert_allclose(a, res.x, atol=1e-6)
+
+
+def test_boxqp_equals_clipped_gabp_when_inside_box():
+    """When Q^-1 1 lies inside [0, C]^n, the box constraints are inactive and
+    the paper's relaxation (Section 3) loses nothing: alpha_box = mu*."""
+    p = workloads.two_gaussians(10, 4, seed=61)
+    C = 10.0
+    Q = oracle.build_q(p.X, p.y, p.gamma, C)
+    r = oracle.gabp(Q, np.ones(p.n), iters=5000, tol=1e-14)
+    if not np.all((r.mu > 0) & (r.mu < C)):
+        pytest.skip("optimum not inside the box for this draw")
+    a, _ = oracle.boxqp_bruteforce(Q, C)
+    np.testing.assert_allclose(a, r.alpha(C), rtol=1e-9, atol=1e-12)
