@@ -1,0 +1,350 @@
+#!/usr/bin/env python3
+"""Throughput of the GaBP SVM solver on one GB300 (or N independent replicas).
+
+A step is one complete solve of the n=20000, m=128 FP32 mixture workload
+(gamma = 1/128, C = 10, Q stored FP32, 100 synchronous rounds): input
+staging, Q formation with the weighted diagonal, 100 broadcast-GaBP rounds
+(pair sweep + per-node finalize each), and the final FP64 residual, dual
+objective and alpha.  `value` is synchronous rounds ("sweeps") per second over
+all ranks, with the inputs resident on the device; `e2e` is the same through
+the C ABI with pinned host buffers (H2D of X and y, D2H of alpha inside the
+timed region).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun every rank solves its own instance (no collective): weak
+scaling, `value` = all ranks' sweeps / max elapsed over ranks.
+`--impl reference` times the FP64 CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_0810_1648_gb300 import workloads  # noqa: E402
+
+METRIC = "GaBP sweeps/sec (n² edge updates/s, % HBM roofline); solves/s + p50/p99 vs plain"
+UNIT = "sweeps/s"
+ROUNDS = 100
+WORKLOAD = {
+    "workload": "plain GaBP SVM, n=20000, m=128 FP32 two-class 3-component Gaussian mixture "
+                "(means N(0,1), sigma 0.7), RBF gamma=1/128, C=10, Q stored FP32 upper triangle, "
+                "100 synchronous sweeps per solve, seed 1",
+    "n": 20000, "m": 128, "sweeps_per_step": ROUNDS, "q_mode": "f32",
+    "l2": "no flush: every sweep streams 3.3 GB of messages + 0.8 GB of Q, far above the 129 MB L2",
+}
+# Algorithmic bytes per unordered pair of one pair-sweep launch (FP32 Q):
+# read 16 B of messages + 4 B of Q, write 16 B; the first round reads no messages.
+BYTES_PER_PAIR = 36
+BYTES_PER_PAIR_ROUND0 = 20
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _traffic_from_profile(kernel_src: str):
+    """DRAM bytes per launch of the pair sweep from the committed ncu summary,
+    or None when the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "k_sweep_plain_large.txt")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m_sha = re.search(r"^source_sha256:\s*([0-9a-f]+)", txt, re.M)
+    m_b = re.search(r"^traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt, re.M)
+    if not (m_sha and m_b):
+        return None
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    return float(m_b.group(1)) if sha == m_sha.group(1) else None
+
+
+def _oracle_sample(p, sweeps: int):
+    """Times the FP64 oracle: Q formation for the whole set + `sweeps` rounds.
+    Returns (t_q, t_per_sweep, threads)."""
+    import oracle
+    X = p.X.astype(np.float64)
+    y = p.y.astype(np.float64)
+    t0 = time.perf_counter()
+    Q = oracle.build_q(X, y, p.gamma, p.C)
+    t1 = time.perf_counter()
+    oracle.gabp(Q, np.ones(p.n), iters=sweeps, tol=0.0)
+    t2 = time.perf_counter()
+    del Q
+    return t1 - t0, (t2 - t1) / max(sweeps, 1), oracle.threads()
+
+
+def _host_mem_gb():
+    try:
+        for ln in open("/proc/meminfo"):
+            if ln.startswith("MemAvailable:"):
+                return int(ln.split()[1]) / 1e6
+    except OSError:
+        pass
+    return 0.0
+
+
+def _cpu_baseline(p, sweeps: int):
+    need_gb = 3 * 8 * p.n * p.n / 1e9 + 1
+    if _host_mem_gb() < need_gb * 1.3:
+        return {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
+                "sample": f"skipped: the FP64 oracle needs {need_gb:.0f} GB of host memory"}
+    tq, ts, th = _oracle_sample(p, sweeps)
+    v = ROUNDS / (tq + ROUNDS * ts)
+    return {"value": v, "unit": UNIT, "cores": th, "kind": "oracle",
+            "sample": f"FP64 oracle on the same workload: Q formation for all n=20000 points "
+                      f"({tq:.1f} s) + {sweeps} synchronous rounds ({ts:.2f} s each), "
+                      f"scaled to one {ROUNDS}-round solve"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    p = workloads.plain_large()
+    sweeps = args.ref_sweeps
+    for _ in range(args.warmup):
+        _oracle_sample(p, sweeps)
+    vals, secs = [], []
+    th = 1
+    for _ in range(args.steps):
+        tq, ts, th = _oracle_sample(p, sweeps)
+        secs.append(tq + ROUNDS * ts)
+        vals.append(ROUNDS / (tq + ROUNDS * ts))
+    v = float(np.mean(vals))
+    sample = (f"FP64 oracle ({th} threads) per step: Q formation for all n=20000 points + {sweeps} "
+              f"rounds, scaled to one {ROUNDS}-round solve")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(WORKLOAD),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": th, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_0810_1648_gb300 import build as gbuild
+    from paper_0810_1648_gb300 import gabp
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if not os.path.exists(gabp.LIB_PATH):
+        gbuild.build()
+    gabp.load()
+
+    p = workloads.mixture(20000, 128, seed=1 + rank, gamma=1.0 / 128, C=10.0)
+    n = p.n
+    stream = torch.cuda.Stream(device=dev)
+    Xd = torch.from_numpy(p.X).to(dev)
+    yd = torch.from_numpy(p.y).to(dev)
+    alpha_d = torch.empty(n, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    opts = gabp.opts_default(stream=stream.cuda_stream, chunk=ROUNDS)
+    h = gabp.svm_create(Xd, yd, p.gamma, p.C, opts)
+    gabp.svm_set_profiling(h, True)
+
+    def step():
+        gabp.svm_refit(h, Xd, yd, p.gamma, p.C)
+        gabp.svm_solve(h, ROUNDS, 0.0, alpha_d)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    gabp.svm_get_profile(h, reset=True)
+    launches0 = gabp.svm_get_profile(h)["kernel_launches"]
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    prof = gabp.svm_get_profile(h)
+    launches = prof["kernel_launches"] - launches0
+    st = gabp.svm_get_stats(h)
+    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t_max.item())
+    value = ws * ROUNDS * args.steps / (ms_max / 1e3)
+
+    # roofline of the dominant kernel (the pair sweep), timed live by events
+    pairs = n * (n - 1) // 2
+    nz = prof["sweep_launches_zero_state"]
+    nl = prof["sweep_launches"]
+    alg_bytes = pairs * (BYTES_PER_PAIR * (nl - nz) + BYTES_PER_PAIR_ROUND0 * nz)
+    sweep_s = prof["sweep_ms"] / 1e3
+    achieved = alg_bytes / sweep_s / 1e9 if sweep_s > 0 else None
+    peaks = _peaks()
+    if peaks and "hbm_gbs" in peaks:
+        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    else:
+        peak, peak_src = 6800.0, "fallback"
+    traffic = _traffic_from_profile(os.path.join(ROOT, "paper_0810_1648_gb300", "csrc", "sweep.cu"))
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "kernel": "k_sweep<float> (pair sweep)", "peak_source": peak_src,
+            "algorithmic_bytes_per_launch": alg_bytes / max(nl, 1),
+            "avg_launch_ms": prof["sweep_ms"] / max(nl, 1), "launches_timed": nl,
+            "share_of_step": (prof["sweep_ms"] / ms) if ms > 0 else None}
+
+    # end to end through the C ABI with pinned host buffers
+    Xh = torch.from_numpy(p.X).pin_memory()
+    yh = torch.from_numpy(p.y).pin_memory()
+    ah = torch.empty(n, dtype=torch.float32).pin_memory()
+    opts2 = gabp.opts_default(stream=stream.cuda_stream, chunk=ROUNDS)
+    h2 = gabp.svm_create(Xh, yh, p.gamma, p.C, opts2)
+
+    def step_e2e():
+        gabp.svm_refit(h2, Xh, yh, p.gamma, p.C)
+        gabp.svm_solve(h2, ROUNDS, 0.0, ah)
+
+    for _ in range(max(1, args.warmup)):
+        step_e2e()
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step_e2e()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms2 = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(ms2, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = ws * ROUNDS * args.steps / (float(ms2.item()) / 1e3)
+    gabp.svm_destroy(h2)
+    gabp.svm_destroy(h)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = _cpu_baseline(p, args.cpu_sweeps)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(WORKLOAD, parallelism=f"replicas{ws}"),
+                "edge_updates_per_s": value * n * (n - 1),
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT,
+                        "h2d_bytes_per_step": int(p.X.nbytes + p.y.nbytes),
+                        "d2h_bytes_per_step": int(4 * n)},
+                "gpu_launches": int(launches), "clocks": clk,
+                "result": {"residual_inf": st["residual_inf"], "dual_objective": st["dual_objective"],
+                           "n_support": st["n_support"]}}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-sweeps", type=int, default=2)
+    ap.add_argument("--ref-sweeps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

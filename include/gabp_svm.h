@@ -1,0 +1,212 @@
+/*
+ * gabp_svm.h -- C ABI of the GB300 GaBP SVM solver.
+ *
+ * The solver follows Bickson, Yom-Tov and Dolev, "A Gaussian Belief
+ * Propagation Solver for Large Scale Support Vector Machines":
+ *
+ *   - the SVM dual (Section 1.1) with D_ij = y_i y_j K(x_i, x_j) and the RBF
+ *     kernel K(a, b) = exp(-gamma ||a - b||^2);
+ *   - the bias as an extra constant feature lambda (Section 3), which for the
+ *     RBF kernel adds lambda^2 to every kernel value; default lambda = 1/n;
+ *   - a weighted main diagonal that makes the matrix diagonally dominant
+ *     (Section 3.1), giving the matrix Q that the solver works on;
+ *   - the unconstrained Gaussian p(h) ~ exp(-h'Qh/2 + h'1) (Section 3), whose
+ *     mean Q^-1 1 is found by the broadcast form of Gaussian belief
+ *     propagation (Algorithm 2, Section 4) in synchronous rounds (Section 5);
+ *   - the weights alpha = clip(mean, 0, C) and the decision function
+ *     f(x) = sum_i alpha_i y_i K'(x_i, x) (Section 1.1).
+ *
+ * Everything after create() runs on one CUDA device in hand-written kernels.
+ * There is no CPU fallback: every call that needs the GPU fails with
+ * GABP_ECUDA when there is none.
+ *
+ * Conventions
+ *   - Every call returns a gabp_status; no exception or signal crosses the ABI.
+ *     On failure gabp_last_error() returns a message (thread-local).
+ *   - Inputs are read-only and stay owned by the caller; outputs are
+ *     caller-allocated.  In device-pointer mode (opts.ptr_mode = 1) the library
+ *     reads and writes the caller's device buffers during the call only and
+ *     never frees them.
+ *   - A handle owns every device buffer it allocates and frees them in
+ *     gabp_svm_destroy().  A handle is not thread-safe: one thread at a time.
+ *   - All work is issued on the handle's stream (opts.stream, or a stream the
+ *     handle creates).  Every call returns after its work has completed.
+ *   - Non-convergence is not an error: gabp_svm_solve() returns GABP_OK with
+ *     *iters_done == iters and the residual of the last round.
+ */
+#ifndef GABP_SVM_H
+#define GABP_SVM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GABP_SVM_VERSION 1
+
+#if defined(__GNUC__)
+#define GABP_API __attribute__((visibility("default")))
+#else
+#define GABP_API
+#endif
+
+typedef enum {
+    GABP_OK = 0,
+    GABP_EINVAL = 1,    /* bad argument (size, pointer, label not +-1, non-finite input ...) */
+    GABP_ENOMEM = 2,    /* device memory for the handle does not fit; nothing was launched */
+    GABP_ECUDA = 3,     /* a CUDA runtime call failed (no device, launch error ...) */
+    GABP_ENUMERIC = 4,  /* a cavity precision Ptilde_i - P_ji went nonpositive or non-finite */
+    GABP_ETIMEOUT = 5,  /* a bounded device-side wait ran out (batched/serving forms) */
+    GABP_ESTATE = 6     /* call not valid in the handle's current state */
+} gabp_status;
+
+/* How Q is held during the sweeps. */
+typedef enum {
+    GABP_Q_F32 = 0,        /* upper triangle stored in FP32, formed by an FP32 Gram kernel */
+    GABP_Q_BF16 = 1,       /* upper triangle stored in BF16, formed by the tensor-core Gram kernel */
+    GABP_Q_RECOMPUTE = 2   /* not stored: every sweep recomputes Q tiles on the tensor cores (BF16 Gram, FP32 accumulate) */
+} gabp_q_mode;
+
+typedef enum {
+    GABP_DIAG_DOMINANT = 0, /* Q_ii = max(1 + lambda^2 + 1/C, (1 + delta) sum_{j!=i} |Q_ij|) */
+    GABP_DIAG_SOFT2 = 1     /* Q_ii = 1 + lambda^2 + 1/C (2-norm soft margin only) */
+} gabp_diag_rule;
+
+/* Options.  gabp_svm_opts_default() fills the defaults; a zero-initialised
+ * struct also means the defaults except where noted. */
+typedef struct {
+    int32_t x_dtype;       /* layout of X and Xtest: 0 = float32 (default), 1 = float64 (converted to FP32 on the device) */
+    int32_t ptr_mode;      /* 0 = host pointers (copied in/out, default), 1 = device pointers */
+    void*   stream;        /* cudaStream_t to run on; NULL = the handle creates its own */
+    int32_t diag_rule;     /* gabp_diag_rule, default GABP_DIAG_DOMINANT */
+    double  diag_delta;    /* delta of the dominant rule; 0 selects the default 0.1 */
+    int32_t bias_mode;     /* 0 = lambda = 1/n (default), 1 = lambda = bias_lambda (may be 0) */
+    double  bias_lambda;
+    int32_t q_mode;        /* gabp_q_mode, default GABP_Q_F32 */
+    int32_t refine;        /* reserved for the precision form; 0 */
+    double  sv_threshold;  /* support vectors are the i with alpha_i > sv_threshold (default 0) */
+    int32_t chunk;         /* sweeps per captured CUDA graph replay between convergence checks; 0 = 16 */
+    int32_t reserved[7];
+} gabp_svm_opts;
+
+typedef struct gabp_svm_s* gabp_svm_t;
+
+/* Per-handle results of the last solve. */
+typedef struct {
+    int64_t n, m;
+    int64_t sweeps_total;      /* message updates applied to the state since the last create/refit */
+    int32_t kstar;             /* round whose means were returned (counted since create/refit) */
+    int32_t converged;         /* 1 if ||r(kstar)||_inf < tol stopped the last solve */
+    double  residual_inf;      /* ||1 - Q mu(kstar)||_inf, FP64 sums */
+    double  dual_objective;    /* sum_i alpha_i - 1/2 alpha' Q alpha for alpha = clip(mu(kstar), 0, C), FP64 */
+    int64_t n_support;         /* #{i : alpha_i > sv_threshold} */
+    double  lambda, gamma, C, diag_delta;
+    int64_t device_bytes;      /* device memory held by the handle */
+    int32_t q_mode, diag_rule;
+} gabp_svm_stats;
+
+/* Default options. */
+GABP_API void gabp_svm_opts_default(gabp_svm_opts* opts);
+
+/*
+ * Create a solver for the n x m training set X (row-major) with labels y
+ * (n floats, each +1 or -1), RBF width gamma > 0 and box constant C > 0.
+ * Forms Q on the device (Gram kernel fused with exp, bias and labels), weights
+ * its diagonal (Section 3.1) and sets the GaBP state to Algorithm 2's Step 1
+ * (all messages 0).  Requires n >= 2, m >= 1.
+ * Device memory: about 8 n^2 bytes of message state plus the stored Q
+ * (2 n^2 bytes for FP32, n^2 for BF16, 0 for recompute); GABP_ENOMEM if that
+ * does not fit in free device memory, before anything is allocated.
+ * X may be host or device memory per opts->ptr_mode and is not retained.
+ */
+GABP_API gabp_status gabp_svm_create(const void* X, const float* y, int64_t n, int64_t m,
+                            double gamma, double C, gabp_svm_t* out);
+GABP_API gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t m,
+                               double gamma, double C, const gabp_svm_opts* opts,
+                               gabp_svm_t* out);
+
+/*
+ * Replace the training set of an existing handle with a new one of the same
+ * n and m (new X, y, gamma, C), reusing its device memory: forms Q and resets
+ * the state as create() does.
+ */
+GABP_API gabp_status gabp_svm_refit(gabp_svm_t h, const void* X, const float* y, double gamma,
+                           double C);
+
+/*
+ * Run synchronous broadcast-GaBP rounds (Algorithm 2, Steps 2-3) from the
+ * handle's current state.  Round t forms the aggregates Ptilde_i, mutilde_i of
+ * the current messages and the residual r(t) = 1 - Q mutilde(t); it stops at
+ * the first t with ||r(t)||_inf < tol (tol <= 0: never), or after `iters`
+ * message updates.  Writes alpha = clip(mutilde(kstar), 0, C) (n floats) and,
+ * when non-NULL, ||r(kstar)||_inf (FP64) and the number of updates done in
+ * this call.  Calling again continues from the current messages.
+ * GABP_ENUMERIC if a cavity precision went nonpositive (the matrix is then
+ * outside GaBP's convergence conditions); the state is then undefined until
+ * the next refit.
+ */
+GABP_API gabp_status gabp_svm_solve(gabp_svm_t h, int32_t iters, double tol, float* alpha,
+                           double* residual_inf, int32_t* iters_done);
+
+/* Unclipped means mutilde(kstar) of the last solve (n floats; before any solve,
+ * the Step-1 means b_i / Q_ii). */
+GABP_API gabp_status gabp_svm_get_mean(gabp_svm_t h, float* mu);
+
+/* Decision values f(x) = sum_i alpha_i y_i (K(x_i, x) + lambda^2) for t test
+ * rows Xtest (t x m, same dtype and pointer mode as X) with the alpha of the
+ * last solve; the predicted label is sign(f).  out: t floats. */
+GABP_API gabp_status gabp_svm_decision(gabp_svm_t h, const void* Xtest, int64_t t, float* out);
+
+/* Indices i with alpha_i > sv_threshold, ascending (host memory). Writes up to
+ * cap indices and the total count. */
+GABP_API gabp_status gabp_svm_support(gabp_svm_t h, int32_t* idx, int64_t cap, int64_t* count);
+
+GABP_API gabp_status gabp_svm_get_stats(gabp_svm_t h, gabp_svm_stats* stats);
+
+/*
+ * Inspection, for tests and diagnostics (host memory, small sizes):
+ *   get_q:     the dense n x n matrix Q as the sweeps see it (FP32; BF16 values
+ *              widened), mirrored from the stored upper triangle.  Not
+ *              available in recompute mode (GABP_ESTATE).
+ *   get_pairs: for cnt index pairs (i[k] < j[k]) the current messages
+ *              {P_ij, P_ji, H_ij, H_ji} with H = P mu (information form);
+ *              out: 4*cnt floats.
+ *   get_aggregates: Ptilde, htilde = Ptilde*mutilde and mutilde of the
+ *              current message state (n floats each; any may be NULL).
+ */
+GABP_API gabp_status gabp_svm_get_q(gabp_svm_t h, float* Q);
+GABP_API gabp_status gabp_svm_get_pairs(gabp_svm_t h, const int64_t* i, const int64_t* j, int64_t cnt,
+                               float* out);
+GABP_API gabp_status gabp_svm_get_aggregates(gabp_svm_t h, float* Pt, float* ht, float* mu);
+
+/*
+ * Instrumentation.  With profiling on, every pair-sweep kernel of a solve is
+ * bracketed by CUDA events recorded on the handle's stream (inside the
+ * captured graphs) and its device time is summed here.  kernel_launches counts
+ * every kernel the handle has launched since create (always on).
+ */
+typedef struct {
+    int64_t sweep_launches;            /* pair sweeps timed */
+    int64_t sweep_launches_zero_state; /* of which the first round (messages all 0, not read) */
+    double  sweep_ms;                  /* their summed device time */
+    int64_t kernel_launches;           /* all kernels launched by this handle */
+} gabp_svm_profile;
+
+GABP_API gabp_status gabp_svm_set_profiling(gabp_svm_t h, int32_t on);
+/* Copies the counters; reset != 0 zeroes the timing counters afterwards. */
+GABP_API gabp_status gabp_svm_get_profile(gabp_svm_t h, gabp_svm_profile* out, int32_t reset);
+
+/* Frees everything the handle owns. NULL is accepted. */
+GABP_API gabp_status gabp_svm_destroy(gabp_svm_t h);
+
+/* Message of the last failing call on this thread ("" if none). */
+GABP_API const char* gabp_last_error(void);
+
+/* GABP_SVM_VERSION of the loaded library. */
+GABP_API int32_t gabp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GABP_SVM_H */

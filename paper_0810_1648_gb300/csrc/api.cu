@@ -1,0 +1,650 @@
+// C ABI of the GaBP SVM solver (declared in include/gabp_svm.h): handle
+// lifetime, argument checks, the device memory plan, the solve loop with its
+// captured CUDA graphs, and the host-side views of the results.  All
+// arithmetic of the method runs in the kernels of gram.cu and sweep.cu.
+#include "common.cuh"
+#include "gabp_svm.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace gabp;
+
+namespace {
+
+thread_local std::string g_err;
+
+gabp_status fail(gabp_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+gabp_status fail(gabp_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CK(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(GABP_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                               \
+    } while (0)
+
+constexpr int kRhistCap = 1 << 16;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct gabp_svm_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    gabp_svm_opts opts{};
+    int64_t n = 0, m = 0;
+    int Nt = 0, npad = 0;
+    long long ntiles = 0;
+    double gamma = 0, C = 0, lambda = 0, delta = 0;
+    void* pool = nullptr;
+    size_t pool_bytes = 0;
+    Inst inst{};
+    int2* work = nullptr;
+    float* alpha = nullptr;
+    double* final3 = nullptr;
+    double* blockbuf = nullptr;
+    Ctrl* hctrl = nullptr;          // pinned mirror of the control block
+    double* hfinal = nullptr;       // pinned {rinf, objective, nsv}
+    struct Graph {
+        cudaGraphExec_t exec = nullptr;
+        std::vector<cudaEvent_t> ev;   // 2 per round when captured with profiling on
+    };
+    std::map<std::pair<int, bool>, Graph> graphs;
+    bool profiling = false;
+    gabp_svm_profile prof{};
+    bool solved = false;
+    int kstar = 0;
+    gabp_svm_stats stats{};
+};
+
+namespace {
+
+gabp_status check_handle(gabp_svm_t h)
+{
+    if (!h) return fail(GABP_EINVAL, "null handle");
+    return GABP_OK;
+}
+
+// Device memory plan of one handle (bytes, 256-aligned sub-buffers).
+struct Plan {
+    size_t X, vec, agg, part, state, q, work, ctrl, rhist, final3, blockbuf, total;
+};
+
+Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_mode)
+{
+    Plan p{};
+    p.X = align_up((size_t)n * m * sizeof(float), 256);
+    p.vec = align_up((size_t)npad * sizeof(float), 256);
+    p.agg = align_up((size_t)6 * npad * sizeof(float), 256);
+    p.part = align_up((size_t)4 * Nt * n * sizeof(float), 256);
+    p.state = align_up((size_t)ntiles * TT * sizeof(float4), 256);
+    p.q = q_mode == GABP_Q_F32 ? align_up((size_t)ntiles * TT * sizeof(float), 256)
+        : q_mode == GABP_Q_BF16 ? align_up((size_t)ntiles * TT * sizeof(__nv_bfloat16), 256)
+        : 0;
+    p.work = align_up((size_t)ntiles * sizeof(int2), 256);
+    p.ctrl = align_up(sizeof(Ctrl), 256);
+    p.rhist = align_up((size_t)kRhistCap * sizeof(double), 256);
+    p.final3 = 256;
+    p.blockbuf = align_up((size_t)3 * ((n + 31) / 32) * sizeof(double), 256);
+    p.total = p.X + 6 * p.vec + p.agg + p.part + p.state + p.q + p.work + p.ctrl + p.rhist +
+              p.final3 + p.blockbuf;
+    return p;
+}
+
+void clear_graphs(gabp_svm_t h)
+{
+    for (auto& kv : h->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        for (auto e : kv.second.ev) cudaEventDestroy(e);
+    }
+    h->graphs.clear();
+}
+
+gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
+{
+    cudaStream_t s = h->stream;
+    const int64_t n = h->n, m = h->m;
+    const bool dev = h->opts.ptr_mode == 1;
+    const bool f64 = h->opts.x_dtype == 1;
+    Inst& p = h->inst;
+    p.gamma = (float)h->gamma;
+    p.lam2 = (float)(h->lambda * h->lambda);
+    p.C = (float)h->C;
+    clear_graphs(h);
+    h->solved = false;
+    h->kstar = 0;
+
+    CK(cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), s));
+    // labels -> device copy (validated by the staging kernel, which also sets b = 1)
+    CK(cudaMemcpyAsync((void*)p.y, y, (size_t)n * sizeof(float),
+                       dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    void* tmp = nullptr;
+    const void* src = X;
+    if (!dev) {
+        if (f64) {
+            CK(cudaMallocAsync(&tmp, (size_t)n * m * sizeof(double), s));
+            CK(cudaMemcpyAsync(tmp, X, (size_t)n * m * sizeof(double), cudaMemcpyHostToDevice, s));
+            src = tmp;
+        } else {
+            CK(cudaMemcpyAsync((void*)p.X, X, (size_t)n * m * sizeof(float), cudaMemcpyHostToDevice, s));
+            src = p.X;
+        }
+    }
+    launch_stage(src, f64 ? 1 : 0, (int)n, (int)m, p.y, (float*)p.X, (float*)p.sq, (float*)p.b, p.ctrl, s);
+    h->prof.kernel_launches += 1;
+    CK(cudaGetLastError());
+    if (tmp) CK(cudaFreeAsync(tmp, s));
+    CK(cudaMemcpyAsync(h->hctrl, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h->hctrl->status != 0)
+        return fail(GABP_EINVAL, "row %lld: non-finite feature or label not +-1",
+                    (long long)h->hctrl->bad_index);
+    launch_form_q(p, h->work, h->ntiles, h->opts.q_mode == GABP_Q_BF16, s);
+    CK(cudaGetLastError());
+    launch_init(p, h->opts.diag_rule, (float)h->delta, s);
+    h->prof.kernel_launches += 2;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    return GABP_OK;
+}
+
+void destroy_all(gabp_svm_t h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    clear_graphs(h);
+    if (h->pool) cudaFree(h->pool);
+    if (h->hctrl) cudaFreeHost(h->hctrl);
+    if (h->hfinal) cudaFreeHost(h->hfinal);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+// A captured chunk of `rounds` synchronous rounds; with profiling on, every
+// pair sweep in it is bracketed by two event-record nodes.
+gabp_status get_graph(gabp_svm_t h, int rounds, gabp_svm_s::Graph** out)
+{
+    const auto key = std::make_pair(rounds, h->profiling);
+    auto it = h->graphs.find(key);
+    if (it != h->graphs.end()) { *out = &it->second; return GABP_OK; }
+    gabp_svm_s::Graph G;
+    if (h->profiling) {
+        G.ev.resize((size_t)2 * rounds);
+        for (auto& e : G.ev) CK(cudaEventCreate(&e));
+    }
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < rounds; ++k)
+        launch_round(h->inst, h->work, h->ntiles, h->opts.q_mode, h->stream,
+                     h->profiling ? &G.ev[(size_t)2 * k] : nullptr);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (e != cudaSuccess) return fail(GABP_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&G.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(GABP_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    auto res = h->graphs.emplace(key, std::move(G));
+    *out = &res.first->second;
+    return GABP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gabp_svm_opts_default(gabp_svm_opts* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->diag_rule = GABP_DIAG_DOMINANT;
+    o->diag_delta = 0.1;
+    o->q_mode = GABP_Q_F32;
+    o->chunk = 16;
+}
+
+const char* gabp_last_error(void) { return g_err.c_str(); }
+
+int32_t gabp_version(void) { return GABP_SVM_VERSION; }
+
+gabp_status gabp_svm_create(const void* X, const float* y, int64_t n, int64_t m, double gamma,
+                            double C, gabp_svm_t* out)
+{
+    gabp_svm_opts o;
+    gabp_svm_opts_default(&o);
+    return gabp_svm_create_ex(X, y, n, m, gamma, C, &o, out);
+}
+
+gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t m, double gamma,
+                               double C, const gabp_svm_opts* opts, gabp_svm_t* out)
+{
+    g_err.clear();
+    if (!out) return fail(GABP_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!X || !y) return fail(GABP_EINVAL, "X or y is NULL");
+    if (n < 2 || m < 1) return fail(GABP_EINVAL, "need n >= 2 and m >= 1 (got n=%lld m=%lld)",
+                                    (long long)n, (long long)m);
+    if (n > (int64_t)1 << 30 || m > (int64_t)1 << 20 || n * m > ((int64_t)1 << 40))
+        return fail(GABP_EINVAL, "n or m too large");
+    if (!(gamma > 0) || !std::isfinite(gamma)) return fail(GABP_EINVAL, "gamma must be finite and > 0");
+    if (!(C > 0) || !std::isfinite(C)) return fail(GABP_EINVAL, "C must be finite and > 0");
+    gabp_svm_opts o;
+    gabp_svm_opts_default(&o);
+    if (opts) {
+        o = *opts;
+        if (o.diag_delta == 0) o.diag_delta = 0.1;
+        if (o.chunk <= 0) o.chunk = 16;
+    }
+    if (o.x_dtype != 0 && o.x_dtype != 1) return fail(GABP_EINVAL, "x_dtype must be 0 (f32) or 1 (f64)");
+    if (o.ptr_mode != 0 && o.ptr_mode != 1) return fail(GABP_EINVAL, "ptr_mode must be 0 or 1");
+    if (o.diag_rule != GABP_DIAG_DOMINANT && o.diag_rule != GABP_DIAG_SOFT2)
+        return fail(GABP_EINVAL, "unknown diag_rule");
+    if (!(o.diag_delta > 0) || !std::isfinite(o.diag_delta)) return fail(GABP_EINVAL, "diag_delta must be > 0");
+    if (o.bias_mode == 1 && (!(o.bias_lambda >= 0) || !std::isfinite(o.bias_lambda)))
+        return fail(GABP_EINVAL, "bias_lambda must be finite and >= 0");
+    if (o.q_mode != GABP_Q_F32)
+        return fail(GABP_EINVAL, "q_mode %d is not available in this build", o.q_mode);
+
+    int dev = 0, ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) return fail(GABP_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    CK(cudaGetDevice(&dev));
+
+    gabp_svm_t h = new (std::nothrow) gabp_svm_s();
+    if (!h) return fail(GABP_ENOMEM, "host allocation failed");
+    h->device = dev;
+    h->opts = o;
+    h->n = n;
+    h->m = m;
+    h->Nt = (int)((n + T - 1) / T);
+    h->npad = (int)align_up((size_t)n, 64);
+    h->ntiles = tri_tiles(h->Nt);
+    h->gamma = gamma;
+    h->C = C;
+    h->lambda = o.bias_mode == 1 ? o.bias_lambda : 1.0 / (double)n;
+    h->delta = o.diag_delta;
+
+    const Plan pl = make_plan(n, m, h->Nt, h->ntiles, h->npad, o.q_mode);
+    size_t free_b = 0, total_b = 0;
+    e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) { destroy_all(h); return fail(GABP_ECUDA, "cudaMemGetInfo: %s", cudaGetErrorString(e)); }
+    const size_t margin = (size_t)256 << 20;
+    if (pl.total + margin > free_b) {
+        destroy_all(h);
+        return fail(GABP_ENOMEM, "needs %.2f GB of device memory, %.2f GB free", pl.total / 1e9, free_b / 1e9);
+    }
+    if (o.stream) {
+        h->stream = (cudaStream_t)o.stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { destroy_all(h); return fail(GABP_ECUDA, "stream: %s", cudaGetErrorString(e)); }
+        h->own_stream = true;
+    }
+    e = cudaMalloc(&h->pool, pl.total);
+    if (e != cudaSuccess) { destroy_all(h); return fail(GABP_ENOMEM, "cudaMalloc(%zu): %s", pl.total, cudaGetErrorString(e)); }
+    h->pool_bytes = pl.total;
+    if (cudaMallocHost(&h->hctrl, sizeof(Ctrl)) != cudaSuccess ||
+        cudaMallocHost(&h->hfinal, 4 * sizeof(double)) != cudaSuccess) {
+        destroy_all(h);
+        return fail(GABP_ENOMEM, "pinned host allocation failed");
+    }
+    char* base = static_cast<char*>(h->pool);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { void* r = base + off; off += bytes; return r; };
+    Inst& p = h->inst;
+    p.n = (int)n;
+    p.Nt = h->Nt;
+    p.m = (int)m;
+    p.npad = h->npad;
+    p.X = (const float*)take(pl.X);
+    p.sq = (const float*)take(pl.vec);
+    p.y = (const float*)take(pl.vec);
+    p.b = (const float*)take(pl.vec);
+    p.qdiag = (float*)take(pl.vec);
+    h->alpha = (float*)take(pl.vec);
+    take(pl.vec);
+    p.agg = (float*)take(pl.agg);
+    p.part = (float*)take(pl.part);
+    p.state = (float4*)take(pl.state);
+    p.qstore = pl.q ? take(pl.q) : nullptr;
+    h->work = (int2*)take(pl.work);
+    p.ctrl = (Ctrl*)take(pl.ctrl);
+    p.rhist = (double*)take(pl.rhist);
+    p.rhist_cap = kRhistCap;
+    h->final3 = (double*)take(pl.final3);
+    h->blockbuf = (double*)take(pl.blockbuf);
+
+    // Tile work list: the upper triangle, row by row; L(I,J) = I*Nt - I(I-1)/2 + (J-I).
+    std::vector<int2> wl((size_t)h->ntiles);
+    size_t k = 0;
+    for (int I = 0; I < h->Nt; ++I)
+        for (int J = I; J < h->Nt; ++J) wl[k++] = make_int2(I, J);
+    e = cudaMemcpyAsync(h->work, wl.data(), wl.size() * sizeof(int2), cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) { destroy_all(h); return fail(GABP_ECUDA, "work list copy: %s", cudaGetErrorString(e)); }
+
+    gabp_status st = stage_and_form(h, X, y);
+    if (st != GABP_OK) { std::string msg = g_err; destroy_all(h); g_err = msg; return st; }
+    *out = h;
+    return GABP_OK;
+}
+
+gabp_status gabp_svm_refit(gabp_svm_t h, const void* X, const float* y, double gamma, double C)
+{
+    g_err.clear();
+    if (gabp_status s = check_handle(h)) return s;
+    if (!X || !y) return fail(GABP_EINVAL, "X or y is NULL");
+    if (!(gamma > 0) || !std::isfinite(gamma)) return fail(GABP_EINVAL, "gamma must be finite and > 0");
+    if (!(C > 0) || !std::isfinite(C)) return fail(GABP_EINVAL, "C must be finite and > 0");
+    h->gamma = gamma;
+    h->C = C;
+    return stage_and_form(h, X, y);
+}
+
+gabp_status gabp_svm_solve(gabp_svm_t h, int32_t iters, double tol, float* alpha, double* residual_inf,
+                           int32_t* iters_done)
+{
+    g_err.clear();
+    if (gabp_status s = check_handle(h)) return s;
+    if (iters < 0) return fail(GABP_EINVAL, "iters must be >= 0");
+    if (std::isnan(tol)) return fail(GABP_EINVAL, "tol is NaN");
+    cudaStream_t s = h->stream;
+    Inst& p = h->inst;
+    CK(cudaMemcpyAsync(h->hctrl, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h->hctrl->status != 0) return fail(GABP_ESTATE, "state is invalid after an earlier failure; refit first");
+    const int t0 = h->hctrl->t;
+    if ((long long)t0 + iters >= (long long)INT_MAX) return fail(GABP_EINVAL, "too many rounds");
+    launch_begin(p, iters, tol, s);
+    h->prof.kernel_launches += 1;
+    CK(cudaGetLastError());
+    if (iters > 0) {
+        const int len = tol > 0 ? std::min<int>(h->opts.chunk, iters) : iters;
+        gabp_svm_s::Graph* g = nullptr;
+        if (gabp_status st = get_graph(h, len, &g)) return st;
+        const int max_chunks = (iters + len - 1) / len + 1;
+        int t_before = t0;
+        for (int c = 0; c < max_chunks; ++c) {
+            CK(cudaGraphLaunch(g->exec, s));
+            h->prof.kernel_launches += 2 * len;
+            CK(cudaMemcpyAsync(h->hctrl, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            const int ran = h->hctrl->t - t_before;
+            if (!g->ev.empty()) {
+                for (int k = 0; k < ran && k < len; ++k) {
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, g->ev[(size_t)2 * k], g->ev[(size_t)2 * k + 1]));
+                    h->prof.sweep_ms += ms;
+                    h->prof.sweep_launches += 1;
+                    if (t_before + k == 0) h->prof.sweep_launches_zero_state += 1;
+                }
+            }
+            t_before = h->hctrl->t;
+            if (h->hctrl->done) break;
+        }
+    } else {
+        CK(cudaMemcpyAsync(h->hctrl, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    const Ctrl c = *h->hctrl;
+    if (!c.done) return fail(GABP_ECUDA, "solve loop did not reach its stop condition");
+    h->kstar = c.kstar;
+    if (c.status == ST_ENUMERIC)
+        return fail(GABP_ENUMERIC, "nonpositive or non-finite cavity precision near node %lld in round %d",
+                    c.bad_index, c.kstar);
+    launch_final(p, h->work, h->ntiles, c.kstar & 1, h->alpha, h->final3, h->blockbuf, 0,
+                 (float)h->opts.sv_threshold, s);
+    h->prof.kernel_launches += 3;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->hfinal, h->final3, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (alpha)
+        CK(cudaMemcpyAsync(alpha, h->alpha, (size_t)h->n * sizeof(float),
+                           h->opts.ptr_mode == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    h->solved = true;
+    gabp_svm_stats& S = h->stats;
+    S.n = h->n;
+    S.m = h->m;
+    S.sweeps_total = c.t;
+    S.kstar = c.kstar;
+    S.converged = c.converged;
+    S.residual_inf = h->hfinal[0];
+    S.dual_objective = h->hfinal[1];
+    S.n_support = (int64_t)std::llround(h->hfinal[2]);
+    if (residual_inf) *residual_inf = h->hfinal[0];
+    if (iters_done) *iters_done = c.kstar - t0;
+    return GABP_OK;
+}
+
+gabp_status gabp_svm_get_mean(gabp_svm_t h, float* mu)
+{
+    g_err.clear();
+    if (gabp_status s = check_handle(h)) return s;
+    if (!mu) return fail(GABP_EINVAL, "mu is NULL");
+    const Inst& p = h->inst;
+    const float* src = p.agg + (size_t)(h->kstar & 1) * 3 * p.npad + 2 * (size_t)p.npad;
+    CK(cudaMemcpyAsync(mu, src, (size_t)h->n * sizeof(float),
+                       h->opts.ptr_mode == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return GABP_OK;
+}
+
+gabp_status gabp_svm_get_aggregates(gabp_svm_t h, float* Pt, float* ht, float* mu)
+{
+    g_err.clear();
+    if (gabp_status s = check_handle(h)) return s;
+    const Inst& p = h->inst;
+    CK(cudaMemcpyAsync(h->hctrl, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const float* base = p.agg + (size_t)(h->hctrl->t & 1) * 3 * p.npad;
+    const cudaMemcpyKind kind = h->opts.ptr_mode == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    float* dst[3] = {Pt, ht, mu};
+    for (int a = 0; a < 3; ++a)
+        if (dst[a]) CK(cudaMemcpyAsync(dst[a], base + (size_t)a * p.npad, (size_t)h->n * sizeof(float), kind, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return GABP_OK;
+}
+
+gabp_status gabp_svm_decision(gabp_svm_t h, const void* Xtest, int64_t t, float* out)
+{
+    g_err.clear();
+    if (gabp_status s = check_handle(h)) return s;
+    if (!h->solved) return fail(GABP_ESTATE, "no solve yet");
+    if (t < 0 || (t > 0 && (!Xtest || !out))) return fail(GABP_EINVAL, "bad test set");
+    if (t == 0) return GABP_OK;
+    if (t > ((int64_t)1 << 30)) return fail(GABP_EINVAL, "t too large");
+    cudaStream_t s = h->stream;
+    const bool dev = h->opts.ptr_mode == 1, f64 = h->opts.x_dtype == 1;
+    const int64_t m = h->m;
+    const int Ntt = (int)((t + T - 1) / T);
+    const long long ntl = (long long)Ntt * h->Nt;
+    const size_t bx = align_up((size_t)t * m * sizeof(float), 256), bsq = align_up((size_t)t * 4, 256);
+    const size_t bin = (!dev && f64) ? align_up((size_t)t * m * sizeof(double), 256) : 0;
+    const size_t bpart = align_up((size_t)h->Nt * t * sizeof(float), 256);
+    const size_t bw = align_up((size_t)ntl * sizeof(int2), 256), bout = align_up((size_t)t * 4, 256);
+    char* tmp = nullptr;
+    CK(cudaMallocAsync((void**)&tmp, bx + bsq + bin + bpart + bw + bout, s));
+    float* Xt = (float*)tmp;
+    float* sqt = (float*)(tmp + bx);
+    void* in = tmp + bx + bsq;
+    float* part = (float*)(tmp + bx + bsq + bin);
+    int2* w = (int2*)(tmp + bx + bsq + bin + bpart);
+    float* dout = (float*)(tmp + bx + bsq + bin + bpart + bw);
+    std::vector<int2> wl((size_t)ntl);
+    size_t k = 0;
+    for (int I = 0; I < Ntt; ++I)
+        for (int J = 0; J < h->Nt; ++J) wl[k++] = make_int2(I, J);
+    gabp_status st = GABP_OK;
+    auto run = [&]() -> gabp_status {
+        CK(cudaMemcpyAsync(w, wl.data(), wl.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+        const void* src = Xtest;
+        if (!dev) {
+            if (f64) {
+                CK(cudaMemcpyAsync(in, Xtest, (size_t)t * m * sizeof(double), cudaMemcpyHostToDevice, s));
+                src = in;
+            } else {
+                CK(cudaMemcpyAsync(Xt, Xtest, (size_t)t * m * sizeof(float), cudaMemcpyHostToDevice, s));
+                src = Xt;
+            }
+        }
+        CK(cudaMemcpyAsync(h->hctrl, h->inst.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const int saved_status = h->hctrl->status;
+        launch_stage(src, f64 ? 1 : 0, (int)t, (int)m, nullptr, Xt, sqt, nullptr, h->inst.ctrl, s);
+        h->prof.kernel_launches += 1;
+        CK(cudaMemcpyAsync(h->hctrl, h->inst.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (h->hctrl->status != saved_status) {
+            CK(cudaMemsetAsync(&h->inst.ctrl->status, 0, sizeof(int), s));
+            CK(cudaStreamSynchronize(s));
+            return fail(GABP_EINVAL, "test row %lld: non-finite feature", h->hctrl->bad_index);
+        }
+        launch_decision(h->inst, Xt, sqt, (int)t, h->alpha, w, ntl, part, dev ? out : dout, s);
+        h->prof.kernel_launches += 2;
+        CK(cudaGetLastError());
+        if (!dev) CK(cudaMemcpyAsync(out, dout, (size_t)t * sizeof(float), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        return GABP_OK;
+    };
+    st = run();
+    cudaFreeAsync(tmp, s);
+    cudaStreamSynchronize(s);
+    return st;
+}
+
+gabp_status gabp_svm_support(gabp_svm_t h, int32_t* idx, int64_t cap, int64_t* count)
+{
+    g_err.clear();
+    if (gabp_status s = check_handle(h)) return s;
+    if (!h->solved) return fail(GABP_ESTATE, "no solve yet");
+    if (!count || (cap > 0 && !idx)) return fail(GABP_EINVAL, "bad output");
+    std::vector<float> a((size_t)h->n);
+    CK(cudaMemcpyAsync(a.data(), h->alpha, a.size() * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    int64_t c = 0;
+    const float th = (float)h->opts.sv_threshold;
+    for (int64_t i = 0; i < h->n; ++i)
+        if (a[(size_t)i] > th) {
+            if (c < cap) idx[c] = (int32_t)i;
+            ++c;
+        }
+    *count = c;
+    return GABP_OK;
+}
+
+gabp_status gabp_svm_get_stats(gabp_svm_t h, gabp_svm_stats* st)
+{
+    g_err.clear();
+    if (gabp_status s = check_handle(h)) return s;
+    if (!st) return fail(GABP_EINVAL, "stats is NULL");
+    h->stats.n = h->n;
+    h->stats.m = h->m;
+    h->stats.lambda = h->lambda;
+    h->stats.gamma = h->gamma;
+    h->stats.C = h->C;
+    h->stats.diag_delta = h->delta;
+    h->stats.device_bytes = (int64_t)h->pool_bytes;
+    h->stats.q_mode = h->opts.q_mode;
+    h->stats.diag_rule = h->opts.diag_rule;
+    *st = h->stats;
+    return GABP_OK;
+}
+
+gabp_status gabp_svm_get_q(gabp_svm_t h, float* Q)
+{
+    g_err.clear();
+    if (gabp_status s = check_handle(h)) return s;
+    if (!Q) return fail(GABP_EINVAL, "Q is NULL");
+    if (h->opts.q_mode == GABP_Q_RECOMPUTE) return fail(GABP_ESTATE, "Q is not stored in recompute mode");
+    if (h->n > 46340) return fail(GABP_EINVAL, "n too large for a dense copy");
+    const size_t bytes = (size_t)h->n * h->n * sizeof(float);
+    float* d = nullptr;
+    CK(cudaMallocAsync((void**)&d, bytes, h->stream));
+    CK(cudaMemsetAsync(d, 0, bytes, h->stream));
+    launch_get_q(h->inst, h->work, h->ntiles, h->opts.q_mode == GABP_Q_BF16, d, h->stream);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(Q, d, bytes, h->opts.ptr_mode == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            h->stream);
+    cudaFreeAsync(d, h->stream);
+    cudaError_t e2 = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return fail(GABP_ECUDA, "get_q: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    return GABP_OK;
+}
+
+gabp_status gabp_svm_get_pairs(gabp_svm_t h, const int64_t* i, const int64_t* j, int64_t cnt, float* out)
+{
+    g_err.clear();
+    if (gabp_status s = check_handle(h)) return s;
+    if (cnt < 0 || (cnt > 0 && (!i || !j || !out))) return fail(GABP_EINVAL, "bad pair list");
+    if (cnt == 0) return GABP_OK;
+    std::vector<long long> ij((size_t)cnt * 2);
+    for (int64_t k = 0; k < cnt; ++k) {
+        if (i[k] < 0 || j[k] >= h->n || i[k] >= j[k])
+            return fail(GABP_EINVAL, "pair %lld: need 0 <= i < j < n", (long long)k);
+        ij[2 * k] = i[k];
+        ij[2 * k + 1] = j[k];
+    }
+    long long* dij = nullptr;
+    float4* dout = nullptr;
+    CK(cudaMallocAsync((void**)&dij, ij.size() * sizeof(long long), h->stream));
+    CK(cudaMallocAsync((void**)&dout, (size_t)cnt * sizeof(float4), h->stream));
+    CK(cudaMemcpyAsync(dij, ij.data(), ij.size() * sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+    launch_get_pairs(h->inst, dij, cnt, dout, h->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, dout, (size_t)cnt * sizeof(float4), cudaMemcpyDeviceToHost, h->stream));
+    cudaFreeAsync(dij, h->stream);
+    cudaFreeAsync(dout, h->stream);
+    CK(cudaStreamSynchronize(h->stream));
+    return GABP_OK;
+}
+
+gabp_status gabp_svm_set_profiling(gabp_svm_t h, int32_t on)
+{
+    g_err.clear();
+    if (gabp_status s = check_handle(h)) return s;
+    h->profiling = on != 0;
+    return GABP_OK;
+}
+
+gabp_status gabp_svm_get_profile(gabp_svm_t h, gabp_svm_profile* out, int32_t reset)
+{
+    g_err.clear();
+    if (gabp_status s = check_handle(h)) return s;
+    if (!out) return fail(GABP_EINVAL, "out is NULL");
+    *out = h->prof;
+    if (reset) {
+        const int64_t kl = h->prof.kernel_launches;
+        h->prof = gabp_svm_profile{};
+        h->prof.kernel_launches = kl;
+    }
+    return GABP_OK;
+}
+
+gabp_status gabp_svm_destroy(gabp_svm_t h)
+{
+    g_err.clear();
+    destroy_all(h);
+    return GABP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// Internal declarations shared by the CUDA sources of the GaBP SVM library.
+//
+// Geometry.  Q and the message state are kept for the upper triangle only,
+// cut into T x T pair tiles (I, J) with I <= J, tile I holding nodes
+// [I*T, I*T + T).  Tile L of the work list owns the contiguous slab
+// [L*T*T, (L+1)*T*T) of every per-pair array, row-major inside the tile:
+// pair (r, c) of the tile is node pair (I*T + r, J*T + c).  On diagonal
+// tiles only c > r is used; on edge tiles only nodes < n.
+//
+// Per-pair message state (information form of Algorithm 2): one float4
+//   {P_ij, P_ji, H_ij, H_ji},  i = I*T + r < j = J*T + c,
+// where P_ij is the precision of the message i -> j and H_ij = P_ij mu_ij.
+//
+// Per-node partial sums: every kernel that reduces over pairs writes, for
+// node x and tile index k along the other axis, one value into
+// part[a][k][x] (a = which sum).  For node x in tile row X = x / T the slot
+// k > X comes from tile (X, k) (x as a row), k < X from tile (k, X) (x as a
+// column) and k = X from the diagonal tile (both roles added).  Every slot is
+// written exactly once per pass, so the reduction order is fixed.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace gabp {
+
+constexpr int T = 128;                 // pair tile edge
+constexpr int TT = T * T;
+constexpr int NTHREADS = 256;          // threads per tile CTA
+constexpr int NWARPS = NTHREADS / 32;
+
+enum Status : int {
+    ST_OK = 0, ST_EINVAL = 1, ST_ENOMEM = 2, ST_ECUDA = 3, ST_ENUMERIC = 4,
+    ST_ETIMEOUT = 5, ST_ESTATE = 6
+};
+
+// Device-resident control block of one solver instance.  Kernels of a sweep
+// read `t` and `done` from here, so a captured chunk of sweeps can be
+// replayed from any starting round.
+struct Ctrl {
+    int t;                    // message updates applied since create/refit
+    int done;                 // set once the solve must stop
+    int limit;                // stop when t reaches this
+    int kstar;                // round whose aggregates are the answer
+    int converged;            // 1 if the residual test stopped the solve
+    int status;               // first error (Status), 0 if none
+    long long bad_index;      // offending node (or pair row) of the first error
+    unsigned int blocks_done; // last-block-done counter of the finalize kernel
+    int pad0;
+    unsigned long long rmax_bits;  // running max |r_i| of the round (bits of a nonnegative double)
+    double tol;
+    double rinf;              // ||r(kstar)||_inf as seen by the convergence test
+};
+
+// One solver instance as the kernels see it.
+struct Inst {
+    int n;            // nodes (training points)
+    int Nt;           // tiles per axis = ceil(n / T)
+    int m;            // features
+    int npad;         // stride of the per-node arrays inside agg
+    const float* X;   // n x m FP32, row-major
+    const float* sq;  // ||x_i||^2 of the FP32 rows
+    const float* y;   // labels +-1
+    const float* b;   // right-hand side (ones for the SVM)
+    float* qdiag;     // Q_ii
+    float4* state;    // ntiles * TT messages
+    void* qstore;     // ntiles * TT values of Q (float or bf16), or nullptr
+    float* agg;       // [2][3][npad]: double-buffered {Ptilde, htilde, mutilde}
+    float* part;      // [4][Nt][n] partial sums
+    Ctrl* ctrl;
+    double* rhist;    // ||r(t)||_inf per round (rhist_cap entries)
+    int rhist_cap;
+    float gamma;      // RBF width
+    float lam2;       // lambda^2
+    float C;          // box constant
+};
+
+// Gram operands: rows [0, n) of an n x m FP32 matrix with row norms sq.
+struct GramSide {
+    const float* X;
+    const float* sq;
+    int n;
+};
+
+// ---- launchers (defined in the .cu files) --------------------------------
+// Inputs: convert/validate X and y, row norms.  Returns nothing; errors go to ctrl->status.
+void launch_stage(const void* X, int x_f64, int n, int m, const float* y, float* Xf, float* sq,
+                  float* b, Ctrl* ctrl, cudaStream_t s);
+// Q formation (FP32 SIMT Gram fused with exp, labels and bias) + |Q| row-sum partials.
+void launch_form_q(const Inst& p, const int2* work, long long ntiles, int q_bf16, cudaStream_t s);
+// Diagonal rule, Step-1 aggregates and control reset.
+void launch_init(const Inst& p, int diag_rule, float delta, cudaStream_t s);
+// Solve control: arm the control block for `iters` more rounds with tolerance `tol`.
+void launch_begin(const Inst& p, int iters, double tol, cudaStream_t s);
+// One synchronous round: pair sweep then per-node finalize.  When ev is not
+// null, ev[0] is recorded before and ev[1] after the pair sweep.
+void launch_round(const Inst& p, const int2* work, long long ntiles, int q_mode, cudaStream_t s,
+                  cudaEvent_t* ev = nullptr);
+// Final residual / dual objective / alpha for the aggregates in buffer `buf`.
+void launch_final(const Inst& p, const int2* work, long long ntiles, int buf, float* alpha,
+                  double* out3 /* rinf, objective, nsv */, double* blockbuf, int nblockbuf,
+                  float sv_threshold, cudaStream_t s);
+// Decision values for t test rows (Xt FP32, sqt norms) using alpha.
+void launch_decision(const Inst& p, const float* Xt, const float* sqt, int t, const float* alpha,
+                     const int2* work, long long ntiles, float* part, float* out, cudaStream_t s);
+// Gather helpers for inspection.
+void launch_get_q(const Inst& p, const int2* work, long long ntiles, int q_bf16, float* Qdense,
+                  cudaStream_t s);
+void launch_get_pairs(const Inst& p, const long long* ij, long long cnt, float4* out,
+                      cudaStream_t s);
+
+// ---- small device helpers --------------------------------------------------
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// Tile index along the triangle -> slot k for node x (see the header comment).
+__host__ __device__ __forceinline__ long long tri_tiles(long long Nt) { return Nt * (Nt + 1) / 2; }
+
+}  // namespace gabp

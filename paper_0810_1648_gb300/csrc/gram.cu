@@ -1,0 +1,457 @@
+// FP32 Gram tiles fused with the RBF kernel, and everything built on them:
+//   - input staging (FP64 -> FP32, row norms, label/finiteness checks),
+//   - formation of the stored Q tiles with |Q| row-sum partials (Section 5:
+//     every node computes its rows of D; Section 3.1: those sums set the
+//     weighted diagonal),
+//   - the final residual r = 1 - Q mu and Q alpha for the dual objective,
+//   - the decision values f(x) = sum_i alpha_i y_i (K(x_i, x) + lambda^2)
+//     (Section 1.1).
+//
+// One CTA computes one 128 x 128 Gram tile G = X_I X_J^T by SIMT FP32 FMAs
+// (8 x 8 outputs per thread, K-chunks of 16 staged in shared memory), then
+// runs an epilogue on the 64 values it holds: d^2 = max(0, s_i + s_j - 2 G),
+// K = expf(-gamma d^2), Q_ij = y_i y_j (K + lambda^2).  The distances use the
+// norm expansion with norms of the same FP32 rows, so d^2_ii is 0 up to
+// rounding and is clamped at 0.
+#include "common.cuh"
+
+#include <float.h>
+
+namespace gabp {
+
+namespace {
+
+constexpr int KC = 16;
+
+struct GramSmem {
+    float A[KC][T + 4];
+    float B[KC][T + 4];
+};
+
+struct EpiSmem {
+    float rowv[2][T];
+    float colw[NWARPS][2][T];
+    float colv[2][T];
+};
+
+union TileSmem {
+    GramSmem g;
+    EpiSmem e;
+};
+
+// acc[a][b] = <x_{I*T + ty*8 + a}, x_{J*T + tx*8 + b}>
+__device__ __forceinline__ void gram_tile(const GramSide& A, const GramSide& B, int m, int I, int J,
+                                          GramSmem& sm, float (&acc)[8][8])
+{
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+
+    for (int k0 = 0; k0 < m; k0 += KC) {
+#pragma unroll
+        for (int u = 0; u < (T * KC) / NTHREADS; ++u) {
+            const int e = tid + NTHREADS * u;
+            const int row = e / KC, kk = e % KC, k = k0 + kk;
+            const int ga = I * T + row, gb = J * T + row;
+            sm.A[kk][row] = (ga < A.n && k < m) ? A.X[(size_t)ga * m + k] : 0.f;
+            sm.B[kk][row] = (gb < B.n && k < m) ? B.X[(size_t)gb * m + k] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < KC; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&sm.A[kk][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&sm.A[kk][ty * 8 + 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&sm.B[kk][tx * 8]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&sm.B[kk][tx * 8 + 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+        }
+        __syncthreads();
+    }
+}
+
+// RBF entry from a Gram value (norm expansion, clamped distance).
+__device__ __forceinline__ float rbf_from_gram(float g, float si, float sj, float gamma)
+{
+    const float d2 = fmaxf(0.f, si + sj - 2.f * g);
+    return expf(-gamma * d2);
+}
+
+// Sums over the 16 tx-lanes that share a row (lanes differ in bits 0..3).
+__device__ __forceinline__ float sum16(float v)
+{
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Row sums (rs, per thread's 8 rows) and column sums (cs, per thread's 8
+// columns) of up to two quantities -> per-node slot partials part_q[k][x].
+template <int NQ>
+__device__ __forceinline__ void reduce_and_write(EpiSmem& es, float (&rs)[NQ][8], float (&cs)[NQ][8],
+                                                 float* const (&part)[NQ], int n, int I, int J)
+{
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15, warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const float v = sum16(rs[q][a]);
+            if (tx == 0) es.rowv[q][ty * 8 + a] = v;
+        }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const float v = cs[q][b] + __shfl_xor_sync(0xffffffffu, cs[q][b], 16);
+            if (lane < 16) es.colw[warp][q][tx * 8 + b] = v;
+        }
+    __syncthreads();
+    if (tid < T) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            float s = 0.f;
+#pragma unroll
+            for (int w = 0; w < NWARPS; ++w) s += es.colw[w][q][tid];
+            es.colv[q][tid] = s;
+        }
+    }
+    __syncthreads();
+    if (I == J) {
+        if (tid < T) {
+            const int x = I * T + tid;
+            if (x < n)
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) part[q][(size_t)I * n + x] = es.rowv[q][tid] + es.colv[q][tid];
+        }
+    } else {
+        if (tid < T) {
+            const int x = I * T + tid;
+            if (x < n)
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) part[q][(size_t)J * n + x] = es.rowv[q][tid];
+        } else {
+            const int c = tid - T, x = J * T + c;
+            if (x < n)
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) part[q][(size_t)I * n + x] = es.colv[q][c];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- staging
+__global__ void k_stage(const void* __restrict__ X, int x_f64, int n, int m, const float* __restrict__ y,
+                        float* __restrict__ Xf, float* __restrict__ sq, float* __restrict__ b, Ctrl* ctrl)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (b) b[i] = 1.f;   // SVM right-hand side: the linear term 1'h of the dual
+    float s = 0.f;
+    bool ok = true;
+    for (int k = 0; k < m; ++k) {
+        const size_t e = (size_t)i * m + k;
+        const float v = x_f64 ? (float)static_cast<const double*>(X)[e] : static_cast<const float*>(X)[e];
+        ok &= isfinite(v);
+        if (Xf != X) Xf[e] = v;
+        s = fmaf(v, v, s);
+    }
+    sq[i] = s;
+    if (y) {
+        const float yi = y[i];
+        ok &= (yi == 1.f || yi == -1.f);
+    }
+    if (!ok && atomicCAS(&ctrl->status, 0, (int)ST_EINVAL) == 0) ctrl->bad_index = i;
+}
+
+// ------------------------------------------------------- Q tile formation
+__global__ void __launch_bounds__(NTHREADS) k_form_q(Inst p, const int2* __restrict__ work)
+{
+    __shared__ __align__(16) TileSmem sm;
+    const long long L = blockIdx.x;
+    const int I = work[L].x, J = work[L].y, n = p.n;
+    const GramSide S{p.X, p.sq, n};
+    float acc[8][8];
+    gram_tile(S, S, p.m, I, J, sm.g, acc);
+
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    float yj[8], sj[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const int j = J * T + tx * 8 + b;
+        yj[b] = j < n ? p.y[j] : 0.f;
+        sj[b] = j < n ? p.sq[j] : 0.f;
+    }
+    float rs[1][8], cs[1][8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) cs[0][b] = 0.f;
+    float* qt = static_cast<float*>(p.qstore) + (size_t)L * TT;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const int r = ty * 8 + a, i = I * T + r;
+        const float yi = i < n ? p.y[i] : 0.f, si = i < n ? p.sq[i] : 0.f;
+        float out[8];
+        float racc = 0.f;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const int c = tx * 8 + b, j = J * T + c;
+            const bool v = i < n && j < n && (I != J || c > r);
+            const float q = yi * yj[b] * (rbf_from_gram(acc[a][b], si, sj[b], p.gamma) + p.lam2);
+            out[b] = v ? q : 0.f;
+            racc += fabsf(out[b]);
+            cs[0][b] += fabsf(out[b]);
+        }
+        rs[0][a] = racc;
+        float4* dst = reinterpret_cast<float4*>(qt + r * T + tx * 8);
+        dst[0] = make_float4(out[0], out[1], out[2], out[3]);
+        dst[1] = make_float4(out[4], out[5], out[6], out[7]);
+    }
+    float* const parts[1] = {p.part};
+    __syncthreads();   // Gram smem is reused by the epilogue
+    reduce_and_write<1>(sm.e, rs, cs, parts, n, I, J);
+}
+
+// ------------------------------------------- final residual and Q alpha
+// Off-diagonal sums sum_{j != i} Q_ij mu_j (-> part[0]) and
+// sum_{j != i} Q_ij alpha_j (-> part[1]) with alpha = clip(mu, 0, C), Q
+// recomputed in FP32 (bitwise equal to the stored FP32 tiles).
+__global__ void __launch_bounds__(NTHREADS) k_final_tiles(Inst p, const int2* __restrict__ work,
+                                                          const float* __restrict__ mu)
+{
+    __shared__ __align__(16) TileSmem sm;
+    const long long L = blockIdx.x;
+    const int I = work[L].x, J = work[L].y, n = p.n;
+    const GramSide S{p.X, p.sq, n};
+    float acc[8][8];
+    gram_tile(S, S, p.m, I, J, sm.g, acc);
+
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    float yj[8], sj[8], mj[8], aj[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const int j = J * T + tx * 8 + b;
+        yj[b] = j < n ? p.y[j] : 0.f;
+        sj[b] = j < n ? p.sq[j] : 0.f;
+        mj[b] = j < n ? mu[j] : 0.f;
+        aj[b] = fminf(fmaxf(mj[b], 0.f), p.C);
+    }
+    float rs[2][8], cs[2][8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) cs[0][b] = cs[1][b] = 0.f;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const int r = ty * 8 + a, i = I * T + r;
+        const float yi = i < n ? p.y[i] : 0.f, si = i < n ? p.sq[i] : 0.f;
+        const float mi = i < n ? mu[i] : 0.f, ai = fminf(fmaxf(mi, 0.f), p.C);
+        float rm = 0.f, ra = 0.f;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const int c = tx * 8 + b, j = J * T + c;
+            const bool v = i < n && j < n && (I != J || c > r);
+            const float q0 = yi * yj[b] * (rbf_from_gram(acc[a][b], si, sj[b], p.gamma) + p.lam2);
+            const float q = v ? q0 : 0.f;
+            rm = fmaf(q, mj[b], rm);
+            ra = fmaf(q, aj[b], ra);
+            cs[0][b] = fmaf(q, mi, cs[0][b]);
+            cs[1][b] = fmaf(q, ai, cs[1][b]);
+        }
+        rs[0][a] = rm;
+        rs[1][a] = ra;
+    }
+    float* const parts[2] = {p.part, p.part + (size_t)p.Nt * n};
+    __syncthreads();
+    reduce_and_write<2>(sm.e, rs, cs, parts, n, I, J);
+}
+
+// Per node: r_i = b_i - Q_ii mu_i - sum part0, (Q alpha)_i = Q_ii alpha_i + sum part1;
+// writes alpha; block partials {max |r_i|, sum alpha_i - 1/2 alpha_i (Q alpha)_i, #SV}.
+__global__ void __launch_bounds__(256) k_final_nodes(Inst p, const float* __restrict__ mu,
+                                                     float* __restrict__ alpha, double* __restrict__ blockbuf,
+                                                     float sv_threshold)
+{
+    const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
+    const int x = blockIdx.x * 32 + lane, n = p.n, Nt = p.Nt;
+    const float* p0 = p.part;
+    const float* p1 = p.part + (size_t)Nt * n;
+    double s0 = 0.0, s1 = 0.0;
+    if (x < n)
+        for (int k = g; k < Nt; k += 8) {
+            s0 += (double)p0[(size_t)k * n + x];
+            s1 += (double)p1[(size_t)k * n + x];
+        }
+    __shared__ double red[2][8][32];
+    red[0][g][lane] = s0;
+    red[1][g][lane] = s1;
+    __syncthreads();
+    if (g == 0) {
+        double absr = 0.0, obj = 0.0, nsv = 0.0;
+        if (x < n) {
+            double a0 = 0.0, a1 = 0.0;
+            for (int w = 0; w < 8; ++w) { a0 += red[0][w][lane]; a1 += red[1][w][lane]; }
+            const double qd = p.qdiag[x], m = mu[x];
+            const float af = fminf(fmaxf(mu[x], 0.f), p.C);
+            const double al = af;
+            alpha[x] = af;
+            const double r = (double)p.b[x] - qd * m - a0;
+            absr = fabs(r);
+            if (!(absr <= DBL_MAX)) absr = INFINITY;
+            const double qa = qd * al + a1;
+            obj = al - 0.5 * al * qa;
+            nsv = af > sv_threshold ? 1.0 : 0.0;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            absr = fmax(absr, __shfl_xor_sync(0xffffffffu, absr, o));
+            obj += __shfl_xor_sync(0xffffffffu, obj, o);
+            nsv += __shfl_xor_sync(0xffffffffu, nsv, o);
+        }
+        if (lane == 0) {
+            blockbuf[3 * blockIdx.x + 0] = absr;
+            blockbuf[3 * blockIdx.x + 1] = obj;
+            blockbuf[3 * blockIdx.x + 2] = nsv;
+        }
+    }
+}
+
+// Fixed-order reduction of the block partials -> out3 = {rinf, objective, nsv}.
+__global__ void k_final_reduce(const double* __restrict__ blockbuf, int nb, double* __restrict__ out3)
+{
+    __shared__ double s[3][256];
+    const int tid = threadIdx.x;
+    double m = 0.0, o = 0.0, c = 0.0;
+    for (int k = tid; k < nb; k += 256) {
+        m = fmax(m, blockbuf[3 * k]);
+        o += blockbuf[3 * k + 1];
+        c += blockbuf[3 * k + 2];
+    }
+    s[0][tid] = m; s[1][tid] = o; s[2][tid] = c;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (tid < w) {
+            s[0][tid] = fmax(s[0][tid], s[0][tid + w]);
+            s[1][tid] += s[1][tid + w];
+            s[2][tid] += s[2][tid + w];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) { out3[0] = s[0][0]; out3[1] = s[1][0]; out3[2] = s[2][0]; }
+}
+
+// ----------------------------------------------------------------- decision
+// Rectangle of tiles (test tile I, training tile J): part[J][s] =
+// sum_{j in J} alpha_j y_j (K(x_j, xt_s) + lambda^2).
+__global__ void __launch_bounds__(NTHREADS) k_decision_tiles(Inst p, const float* __restrict__ Xt,
+                                                             const float* __restrict__ sqt, int t,
+                                                             const float* __restrict__ alpha,
+                                                             const int2* __restrict__ work,
+                                                             float* __restrict__ part)
+{
+    __shared__ __align__(16) TileSmem sm;
+    const long long L = blockIdx.x;
+    const int I = work[L].x, J = work[L].y, n = p.n;
+    const GramSide A{Xt, sqt, t}, B{p.X, p.sq, n};
+    float acc[8][8];
+    gram_tile(A, B, p.m, I, J, sm.g, acc);
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    float wj[8], sj[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const int j = J * T + tx * 8 + b;
+        wj[b] = j < n ? alpha[j] * p.y[j] : 0.f;
+        sj[b] = j < n ? p.sq[j] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const int r = ty * 8 + a, s = I * T + r;
+        const float si = s < t ? sqt[s] : 0.f;
+        float f = 0.f;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const float kv = rbf_from_gram(acc[a][b], si, sj[b], p.gamma) + p.lam2;
+            f = fmaf(wj[b], kv, f);
+        }
+        f = sum16(f);
+        if (tx == 0) sm.e.rowv[0][r] = f;
+    }
+    __syncthreads();
+    if (tid < T) {
+        const int s = I * T + tid;
+        if (s < t) part[(size_t)J * t + s] = sm.e.rowv[0][tid];
+    }
+}
+
+__global__ void k_decision_sum(const float* __restrict__ part, int t, int Ntrain_tiles, float* __restrict__ out)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= t) return;
+    double f = 0.0;
+    for (int k = 0; k < Ntrain_tiles; ++k) f += (double)part[(size_t)k * t + s];
+    out[s] = (float)f;
+}
+
+// ---------------------------------------------------------------- inspection
+__global__ void k_get_q(Inst p, const int2* __restrict__ work, int q_bf16, float* __restrict__ Qd)
+{
+    const long long L = blockIdx.x;
+    const int I = work[L].x, J = work[L].y, n = p.n;
+    for (int e = threadIdx.x; e < TT; e += blockDim.x) {
+        const int r = e / T, c = e % T, i = I * T + r, j = J * T + c;
+        if (i >= n || j >= n || (I == J && c <= r)) continue;
+        const size_t o = (size_t)L * TT + e;
+        const float q = q_bf16 ? __bfloat162float(static_cast<const __nv_bfloat16*>(p.qstore)[o])
+                               : static_cast<const float*>(p.qstore)[o];
+        Qd[(size_t)i * n + j] = q;
+        Qd[(size_t)j * n + i] = q;
+    }
+    if (I == J)
+        for (int r = threadIdx.x; r < T; r += blockDim.x) {
+            const int i = I * T + r;
+            if (i < n) Qd[(size_t)i * n + i] = p.qdiag[i];
+        }
+}
+
+}  // namespace
+
+void launch_stage(const void* X, int x_f64, int n, int m, const float* y, float* Xf, float* sq,
+                  float* b, Ctrl* ctrl, cudaStream_t s)
+{
+    k_stage<<<(n + 255) / 256, 256, 0, s>>>(X, x_f64, n, m, y, Xf, sq, b, ctrl);
+}
+
+void launch_form_q(const Inst& p, const int2* work, long long ntiles, int q_bf16, cudaStream_t s)
+{
+    (void)q_bf16;
+    k_form_q<<<(unsigned)ntiles, NTHREADS, 0, s>>>(p, work);
+}
+
+void launch_final(const Inst& p, const int2* work, long long ntiles, int buf, float* alpha,
+                  double* out3, double* blockbuf, int nblockbuf, float sv_threshold, cudaStream_t s)
+{
+    const float* mu = p.agg + (size_t)(buf & 1) * 3 * p.npad + 2 * (size_t)p.npad;
+    k_final_tiles<<<(unsigned)ntiles, NTHREADS, 0, s>>>(p, work, mu);
+    const int nb = (p.n + 31) / 32;
+    (void)nblockbuf;
+    k_final_nodes<<<nb, 256, 0, s>>>(p, mu, alpha, blockbuf, sv_threshold);
+    k_final_reduce<<<1, 256, 0, s>>>(blockbuf, nb, out3);
+}
+
+void launch_decision(const Inst& p, const float* Xt, const float* sqt, int t, const float* alpha,
+                     const int2* work, long long ntiles, float* part, float* out, cudaStream_t s)
+{
+    k_decision_tiles<<<(unsigned)ntiles, NTHREADS, 0, s>>>(p, Xt, sqt, t, alpha, work, part);
+    k_decision_sum<<<(t + 255) / 256, 256, 0, s>>>(part, t, p.Nt, out);
+}
+
+void launch_get_q(const Inst& p, const int2* work, long long ntiles, int q_bf16, float* Qdense,
+                  cudaStream_t s)
+{
+    k_get_q<<<(unsigned)ntiles, 256, 0, s>>>(p, work, q_bf16, Qdense);
+}
+
+}  // namespace gabp

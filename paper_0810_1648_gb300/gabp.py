@@ -1,0 +1,331 @@
+"""Python binding of libgabp_svm.so (the C ABI in include/gabp_svm.h).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  Host inputs are numpy arrays (copied by the library); device
+inputs are torch CUDA tensors (``ptr_mode=1``), for which torch supplies the
+memory and the library reads it in place.  There is no CPU fallback: without
+the built library or a GPU every call raises.
+
+Function names follow the C ABI (``svm_create`` wraps ``gabp_svm_create_ex``
+and so on); ``GabpSVM`` bundles them for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgabp_svm.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "gabp_svm.h")
+
+OK, EINVAL, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, ESTATE = range(7)
+STATUS_NAMES = {0: "GABP_OK", 1: "GABP_EINVAL", 2: "GABP_ENOMEM", 3: "GABP_ECUDA",
+                4: "GABP_ENUMERIC", 5: "GABP_ETIMEOUT", 6: "GABP_ESTATE"}
+Q_F32, Q_BF16, Q_RECOMPUTE = 0, 1, 2
+DIAG_DOMINANT, DIAG_SOFT2 = 0, 1
+
+
+class GabpError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("x_dtype", ctypes.c_int32), ("ptr_mode", ctypes.c_int32),
+                ("stream", ctypes.c_void_p), ("diag_rule", ctypes.c_int32),
+                ("diag_delta", ctypes.c_double), ("bias_mode", ctypes.c_int32),
+                ("bias_lambda", ctypes.c_double), ("q_mode", ctypes.c_int32),
+                ("refine", ctypes.c_int32), ("sv_threshold", ctypes.c_double),
+                ("chunk", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("sweep_launches", ctypes.c_int64), ("sweep_launches_zero_state", ctypes.c_int64),
+                ("sweep_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("sweeps_total", ctypes.c_int64),
+                ("kstar", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("residual_inf", ctypes.c_double), ("dual_objective", ctypes.c_double),
+                ("n_support", ctypes.c_int64), ("lambda_", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("C", ctypes.c_double), ("diag_delta", ctypes.c_double),
+                ("device_bytes", ctypes.c_int64), ("q_mode", ctypes.c_int32),
+                ("diag_rule", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def declared_functions() -> list[str]:
+    """Names of every function include/gabp_svm.h exports."""
+    text = open(HEADER).read()
+    return re.findall(r"GABP_API\s+[\w\s\*]+?\b(gabp_\w+)\s*\(", text)
+
+
+def load():
+    """Load the in-tree library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_0810_1648_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    V, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    P = ctypes.POINTER
+    st = ctypes.c_int
+    sigs = {
+        "gabp_svm_opts_default": (None, [P(Opts)]),
+        "gabp_svm_create": (st, [V, V, I64, I64, D, D, P(V)]),
+        "gabp_svm_create_ex": (st, [V, V, I64, I64, D, D, P(Opts), P(V)]),
+        "gabp_svm_refit": (st, [V, V, V, D, D]),
+        "gabp_svm_solve": (st, [V, I32, D, V, P(D), P(I32)]),
+        "gabp_svm_get_mean": (st, [V, V]),
+        "gabp_svm_decision": (st, [V, V, I64, V]),
+        "gabp_svm_support": (st, [V, V, I64, P(I64)]),
+        "gabp_svm_get_stats": (st, [V, P(Stats)]),
+        "gabp_svm_get_q": (st, [V, V]),
+        "gabp_svm_get_pairs": (st, [V, V, V, I64, V]),
+        "gabp_svm_get_aggregates": (st, [V, V, V, V]),
+        "gabp_svm_set_profiling": (st, [V, I32]),
+        "gabp_svm_get_profile": (st, [V, P(Profile), I32]),
+        "gabp_svm_destroy": (st, [V]),
+        "gabp_last_error": (ctypes.c_char_p, []),
+        "gabp_version": (I32, []),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise GabpError(rc, load().gabp_last_error().decode(errors="replace"))
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a):
+    """Raw address of a numpy array or torch tensor (which must be contiguous)."""
+    if a is None:
+        return None
+    if _is_torch(a):
+        assert a.is_contiguous()
+        return ctypes.c_void_p(a.data_ptr())
+    assert a.flags["C_CONTIGUOUS"]
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _is_cuda(a) -> bool:
+    return _is_torch(a) and a.is_cuda
+
+
+def _sync_torch(*arrays):
+    """Device inputs written on torch's stream must be complete before the
+    library's stream reads them."""
+    for a in arrays:
+        if a is not None and _is_torch(a) and a.is_cuda:
+            import torch
+            torch.cuda.current_stream(a.device).synchronize()
+            return
+
+
+def opts_default(**kw) -> Opts:
+    o = Opts()
+    load().gabp_svm_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _prep_x(X, device_mode):
+    if device_mode:
+        import torch
+        if X.dtype not in (torch.float32, torch.float64):
+            raise TypeError("X must be float32 or float64")
+        return X.contiguous(), (1 if X.dtype == torch.float64 else 0)
+    X = np.asarray(X)
+    if X.dtype not in (np.float32, np.float64):
+        X = X.astype(np.float32)
+    return np.ascontiguousarray(X), (1 if X.dtype == np.float64 else 0)
+
+
+def svm_create(X, y, gamma: float, C: float, opts: Opts | None = None):
+    """gabp_svm_create_ex: returns an opaque handle (int).  X as a torch CUDA
+    tensor selects device-pointer mode; numpy arrays or (pinned) torch CPU
+    tensors select host-pointer mode."""
+    device_mode = _is_cuda(X)
+    if _is_torch(X) and not device_mode:
+        import torch
+        if X.dtype not in (torch.float32, torch.float64):
+            raise TypeError("X must be float32 or float64")
+        o = opts if opts is not None else opts_default()
+        o.x_dtype = 1 if X.dtype == torch.float64 else 0
+        o.ptr_mode = 0
+        y = y.to(dtype=torch.float32).contiguous()
+        h = ctypes.c_void_p()
+        _check(load().gabp_svm_create_ex(_ptr(X.contiguous()), _ptr(y), X.shape[0], X.shape[1],
+                                         float(gamma), float(C), ctypes.byref(o), ctypes.byref(h)))
+        return h.value
+    X, x_dtype = _prep_x(X, device_mode)
+    o = opts if opts is not None else opts_default()
+    o.x_dtype = x_dtype
+    o.ptr_mode = 1 if device_mode else 0
+    if device_mode:
+        import torch
+        y = y.to(device=X.device, dtype=torch.float32).contiguous()
+        _sync_torch(X, y)
+    else:
+        y = np.ascontiguousarray(y, dtype=np.float32)
+    h = ctypes.c_void_p()
+    n, m = X.shape
+    _check(load().gabp_svm_create_ex(_ptr(X), _ptr(y), n, m, float(gamma), float(C),
+                                     ctypes.byref(o), ctypes.byref(h)))
+    return h.value
+
+
+def svm_refit(h, X, y, gamma: float, C: float):
+    _sync_torch(X, y)
+    _check(load().gabp_svm_refit(ctypes.c_void_p(h), _ptr(X), _ptr(y), float(gamma), float(C)))
+
+
+def svm_solve(h, iters: int, tol: float, alpha_out):
+    """gabp_svm_solve into alpha_out (numpy float32 or torch CUDA float32).
+    Returns (residual_inf, iters_done)."""
+    r = ctypes.c_double(0)
+    k = ctypes.c_int32(0)
+    _check(load().gabp_svm_solve(ctypes.c_void_p(h), int(iters), float(tol), _ptr(alpha_out),
+                                 ctypes.byref(r), ctypes.byref(k)))
+    return r.value, k.value
+
+
+def svm_get_mean(h, out):
+    _check(load().gabp_svm_get_mean(ctypes.c_void_p(h), _ptr(out)))
+
+
+def svm_decision(h, Xt, out):
+    _sync_torch(Xt)
+    _check(load().gabp_svm_decision(ctypes.c_void_p(h), _ptr(Xt), int(Xt.shape[0]), _ptr(out)))
+
+
+def svm_support(h, n: int) -> np.ndarray:
+    idx = np.empty(n, dtype=np.int32)
+    cnt = ctypes.c_int64(0)
+    _check(load().gabp_svm_support(ctypes.c_void_p(h), _ptr(idx), n, ctypes.byref(cnt)))
+    return idx[: cnt.value].copy()
+
+
+def svm_get_stats(h) -> dict:
+    s = Stats()
+    _check(load().gabp_svm_get_stats(ctypes.c_void_p(h), ctypes.byref(s)))
+    return s.as_dict()
+
+
+def svm_get_q(h, n: int) -> np.ndarray:
+    Q = np.empty((n, n), dtype=np.float32)
+    _check(load().gabp_svm_get_q(ctypes.c_void_p(h), _ptr(Q)))
+    return Q
+
+
+def svm_get_pairs(h, i, j) -> np.ndarray:
+    i = np.ascontiguousarray(i, dtype=np.int64)
+    j = np.ascontiguousarray(j, dtype=np.int64)
+    out = np.empty((len(i), 4), dtype=np.float32)
+    _check(load().gabp_svm_get_pairs(ctypes.c_void_p(h), _ptr(i), _ptr(j), len(i), _ptr(out)))
+    return out
+
+
+def svm_get_aggregates(h, n: int):
+    Pt, ht, mu = (np.empty(n, dtype=np.float32) for _ in range(3))
+    _check(load().gabp_svm_get_aggregates(ctypes.c_void_p(h), _ptr(Pt), _ptr(ht), _ptr(mu)))
+    return Pt, ht, mu
+
+
+def svm_set_profiling(h, on: bool):
+    _check(load().gabp_svm_set_profiling(ctypes.c_void_p(h), 1 if on else 0))
+
+
+def svm_get_profile(h, reset: bool = False) -> dict:
+    p = Profile()
+    _check(load().gabp_svm_get_profile(ctypes.c_void_p(h), ctypes.byref(p), 1 if reset else 0))
+    return p.as_dict()
+
+
+def svm_destroy(h):
+    if h:
+        _check(load().gabp_svm_destroy(ctypes.c_void_p(h)))
+
+
+class GabpSVM:
+    """Owning wrapper around one handle (host numpy inputs unless X is a torch
+    CUDA tensor)."""
+
+    def __init__(self, X, y, gamma: float, C: float, **opts):
+        self.n, self.m = int(X.shape[0]), int(X.shape[1])
+        self.device_mode = _is_cuda(X)
+        self.C = float(C)
+        self.h = svm_create(X, y, gamma, C, opts_default(**opts))
+
+    def solve(self, iters: int = 200, tol: float = 1e-6):
+        if self.device_mode:
+            import torch
+            alpha = torch.empty(self.n, dtype=torch.float32, device="cuda")
+        else:
+            alpha = np.empty(self.n, dtype=np.float32)
+        rinf, k = svm_solve(self.h, iters, tol, alpha)
+        return alpha, rinf, k
+
+    def mean(self):
+        out = np.empty(self.n, dtype=np.float32)
+        if self.device_mode:
+            import torch
+            out = torch.empty(self.n, dtype=torch.float32, device="cuda")
+        svm_get_mean(self.h, out)
+        return out
+
+    def decision(self, Xt):
+        if self.device_mode:
+            import torch
+            out = torch.empty(Xt.shape[0], dtype=torch.float32, device="cuda")
+        else:
+            Xt = np.ascontiguousarray(Xt)
+            out = np.empty(Xt.shape[0], dtype=np.float32)
+        svm_decision(self.h, Xt, out)
+        return out
+
+    def support(self):
+        return svm_support(self.h, self.n)
+
+    def stats(self):
+        return svm_get_stats(self.h)
+
+    def refit(self, X, y, gamma, C):
+        self.C = float(C)
+        svm_refit(self.h, X, y, gamma, C)
+
+    def close(self):
+        if self.h:
+            svm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,60 @@
+"""CPU-side checks of the C ABI: the library builds, loads and exports every
+function the header declares; argument checks fail before any device work;
+without a GPU every call that needs one fails loudly (no CPU fallback)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_0810_1648_gb300 import build as gbuild
+from paper_0810_1648_gb300 import gabp
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gbuild.build()
+    return gabp.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = gabp.declared_functions()
+    assert len(names) >= 15
+    for nm in names:
+        assert hasattr(lib, nm), nm
+    assert lib.gabp_version() == 1
+
+
+def test_opts_default(lib):
+    o = gabp.opts_default()
+    assert o.q_mode == gabp.Q_F32 and o.diag_rule == gabp.DIAG_DOMINANT
+    assert o.diag_delta == pytest.approx(0.1) and o.chunk == 16 and o.ptr_mode == 0
+
+
+def test_argument_errors_before_device_work(lib):
+    X = np.zeros((4, 3), np.float32)
+    y = np.array([1, -1, 1, -1], np.float32)
+    h = ctypes.c_void_p()
+    V = ctypes.c_void_p
+    assert lib.gabp_svm_create(V(X.ctypes.data), V(y.ctypes.data), 4, 3, 1.0, 1.0, None) == gabp.EINVAL
+    assert lib.gabp_svm_create(V(X.ctypes.data), V(y.ctypes.data), 1, 3, 1.0, 1.0, ctypes.byref(h)) == gabp.EINVAL
+    assert b"n >= 2" in lib.gabp_last_error()
+    assert lib.gabp_svm_create(V(X.ctypes.data), V(y.ctypes.data), 4, 3, -1.0, 1.0, ctypes.byref(h)) == gabp.EINVAL
+    assert lib.gabp_svm_create(V(X.ctypes.data), V(y.ctypes.data), 4, 3, 1.0, 0.0, ctypes.byref(h)) == gabp.EINVAL
+    assert lib.gabp_svm_create(None, V(y.ctypes.data), 4, 3, 1.0, 1.0, ctypes.byref(h)) == gabp.EINVAL
+    o = gabp.opts_default(q_mode=7)
+    assert lib.gabp_svm_create_ex(V(X.ctypes.data), V(y.ctypes.data), 4, 3, 1.0, 1.0,
+                                  ctypes.byref(o), ctypes.byref(h)) == gabp.EINVAL
+    # null handles
+    assert lib.gabp_svm_solve(None, 1, 0.0, None, None, None) == gabp.EINVAL
+    assert lib.gabp_svm_destroy(None) == gabp.OK
+
+
+def test_no_gpu_fails_loudly(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    X = np.random.default_rng(0).standard_normal((8, 3)).astype(np.float32)
+    y = np.array([1, -1] * 4, np.float32)
+    with pytest.raises(gabp.GabpError) as ei:
+        gabp.svm_create(X, y, 0.5, 1.0)
+    assert ei.value.status == gabp.ECUDA
