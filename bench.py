@@ -200,6 +200,26 @@ def run_reference(args):
     return 0
 
 
+def run_profile_small(args):
+    """One short solve on a smaller set (n=6144, 3 rounds) for ncu captures:
+    the message state (0.3 GB) is still above L2, the device footprint small."""
+    import torch
+
+    from paper_0810_1648_gb300 import build as gbuild
+    from paper_0810_1648_gb300 import gabp
+    if not os.path.exists(gabp.LIB_PATH):
+        gbuild.build()
+    p = workloads.mixture(6144, 128, seed=1, gamma=1.0 / 128, C=10.0)
+    h = gabp.svm_create(p.X, p.y, p.gamma, p.C, gabp.opts_default(chunk=3))
+    alpha = np.empty(p.n, dtype=np.float32)
+    rinf, k = gabp.svm_solve(h, 3, 0.0, alpha)
+    gabp.svm_destroy(h)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "n=6144 m=128 mixture, 3 rounds", "rounds": k,
+                      "residual_inf": rinf}), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -340,7 +360,11 @@ def main():
     ap.add_argument("--cpu-sweeps", type=int, default=2)
     ap.add_argument("--ref-sweeps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-small", action="store_true",
+                    help="one 3-round solve at n=6144 (for ncu captures), no JSON bench line")
     args = ap.parse_args()
+    if args.profile_small:
+        return run_profile_small(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -332,12 +332,12 @@ void launch_begin(const Inst& p, int iters, double tol, cudaStream_t s)
 void launch_round(const Inst& p, const int2* work, long long ntiles, int q_mode, cudaStream_t s,
                   cudaEvent_t* ev)
 {
-    if (ev) cudaEventRecord(ev[0], s);
+    if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
     if (q_mode == 1)
         k_sweep<__nv_bfloat16><<<(unsigned)ntiles, NTHREADS, 0, s>>>(p, work);
     else
         k_sweep<float><<<(unsigned)ntiles, NTHREADS, 0, s>>>(p, work);
-    if (ev) cudaEventRecord(ev[1], s);
+    if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
     k_finalize<<<(p.n + 31) / 32, 256, 0, s>>>(p);
 }
 
