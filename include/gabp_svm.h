@@ -197,6 +197,33 @@ GABP_API gabp_status gabp_svm_set_profiling(gabp_svm_t h, int32_t on);
 /* Copies the counters; reset != 0 zeroes the timing counters afterwards. */
 GABP_API gabp_status gabp_svm_get_profile(gabp_svm_t h, gabp_svm_profile* out, int32_t reset);
 
+/*
+ * Decision values with no device allocation (the paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory,
+ * e.g. code running during CUDA graph capture, plugins whose host framework
+ * owns all device memory, or loops that cannot afford cudaMalloc's implicit
+ * synchronisation).
+ *
+ * Computes out[s] = sum_i alpha_i y_i (exp(-gamma ||x_i - xt_s||^2) + lambda^2)
+ * for s < t, like gabp_svm_decision, but without a handle.  All pointers are
+ * DEVICE memory owned by the caller: X (n x m FP32, row-major), y and alpha
+ * (n FP32), Xtest (t x m FP32), out (t FP32).  stream is a cudaStream_t (NULL =
+ * legacy default stream); the call returns after its work has completed.
+ *
+ * Temporaries live in one fixed 4 MiB array in device memory that every GPU
+ * which loads this library holds until the process exits; the call calls no
+ * cudaMalloc, cudaFree or allocating library routine.  Sizes must satisfy
+ * n + t + ceil(n/128) * t <= 1048576 floats, else GABP_EINVAL (split the test
+ * rows into smaller calls).  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Every call shares the array and keeps
+ * the last call's contents: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ */
+GABP_API gabp_status gabp_decision_noalloc(const float* X, const float* y, const float* alpha,
+                                           int64_t n, int64_t m, const float* Xtest, int64_t t,
+                                           double gamma, double lambda, float* out, void* stream);
+
 /* Frees everything the handle owns. NULL is accepted. */
 GABP_API gabp_status gabp_svm_destroy(gabp_svm_t h);
 

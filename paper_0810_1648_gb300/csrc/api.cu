@@ -48,6 +48,8 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 }  // namespace
 
+void gabp::set_last_error(const char* msg) { g_err = msg; }
+
 struct gabp_svm_s {
     int device = 0;
     cudaStream_t stream = nullptr;

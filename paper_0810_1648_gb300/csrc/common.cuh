@@ -110,6 +110,9 @@ void launch_get_q(const Inst& p, const int2* work, long long ntiles, int q_bf16,
 void launch_get_pairs(const Inst& p, const long long* ij, long long cnt, float4* out,
                       cudaStream_t s);
 
+// Sets the thread-local message returned by gabp_last_error().
+void set_last_error(const char* msg);
+
 // ---- small device helpers --------------------------------------------------
 __device__ __forceinline__ float warp_sum(float v)
 {

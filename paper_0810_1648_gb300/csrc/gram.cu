@@ -14,8 +14,11 @@
 // norm expansion with norms of the same FP32 rows, so d^2_ii is 0 up to
 // rounding and is clamped at 0.
 #include "common.cuh"
+#include "gabp_svm.h"
 
 #include <float.h>
+#include <mutex>
+#include <string>
 
 namespace gabp {
 
@@ -455,3 +458,136 @@ void launch_get_q(const Inst& p, const int2* work, long long ntiles, int q_bf16,
 }
 
 }  // namespace gabp
+
+// ---------------------------------------------------------------------------
+// Decision values with no device allocation.
+//
+// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
+// being captured (allocation calls are not allowed there), plugins inside a
+// host framework that owns all device memory through its own allocator, and
+// latency-critical loops that cannot afford the implicit device-wide
+// synchronisation of cudaMalloc/cudaFree.  gabp_decision_noalloc serves them:
+// the caller passes every input and output as device memory, and the
+// temporaries (row norms and per-tile partial sums) live in the file-scope
+// array below, which every GPU that loads this library holds until the
+// process exits.
+namespace gabp {
+namespace {
+
+constexpr long long kNoAllocScratchFloats = 1LL << 20;   // 4 MiB
+
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchFloats];
+
+__global__ void k_rownorms(const float* __restrict__ X, int n, int m, float* __restrict__ sq)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.f;
+    for (int k = 0; k < m; ++k) {
+        const float v = X[(size_t)i * m + k];
+        s = fmaf(v, v, s);
+    }
+    sq[i] = s;
+}
+
+// Same tile computation as k_decision_tiles, on a rectangle enumerated by the
+// block index (I = test tile, J = training tile) instead of a work list.
+__global__ void __launch_bounds__(NTHREADS) k_decision_tiles_noalloc(
+    const float* __restrict__ X, const float* __restrict__ y, const float* __restrict__ alpha,
+    const float* __restrict__ sq, int n, int m, const float* __restrict__ Xt,
+    const float* __restrict__ sqt, int t, float gamma, float lam2, int Nt, float* __restrict__ part)
+{
+    __shared__ __align__(16) TileSmem sm;
+    const long long L = blockIdx.x;
+    const int I = (int)(L / Nt), J = (int)(L % Nt);
+    const GramSide A{Xt, sqt, t}, B{X, sq, n};
+    float acc[8][8];
+    gram_tile(A, B, m, I, J, sm.g, acc);
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    float wj[8], sj[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const int j = J * T + tx * 8 + b;
+        wj[b] = j < n ? alpha[j] * y[j] : 0.f;
+        sj[b] = j < n ? sq[j] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const int r = ty * 8 + a, s = I * T + r;
+        const float si = s < t ? sqt[s] : 0.f;
+        float f = 0.f;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const float kv = rbf_from_gram(acc[a][b], si, sj[b], gamma) + lam2;
+            f = fmaf(wj[b], kv, f);
+        }
+        f = sum16(f);
+        if (tx == 0) sm.e.rowv[0][r] = f;
+    }
+    __syncthreads();
+    if (tid < T) {
+        const int s = I * T + tid;
+        if (s < t) part[(size_t)J * t + s] = sm.e.rowv[0][tid];
+    }
+}
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float* g_noalloc_dev_ptr[kMaxDevices] = {};
+
+}  // namespace
+}  // namespace gabp
+
+extern "C" GABP_API gabp_status gabp_decision_noalloc(const float* X, const float* y, const float* alpha,
+                                                      int64_t n, int64_t m, const float* Xtest, int64_t t,
+                                                      double gamma, double lambda, float* out, void* stream)
+{
+    using namespace gabp;
+    set_last_error("");
+    auto fail = [](gabp_status st, const std::string& msg) { set_last_error(msg.c_str()); return st; };
+    if (!X || !y || !alpha || (t > 0 && (!Xtest || !out)))
+        return fail(GABP_EINVAL, "gabp_decision_noalloc: null pointer");
+    if (n < 1 || m < 1 || t < 0 || n > (1LL << 30) || m > (1LL << 20) || t > (1LL << 30))
+        return fail(GABP_EINVAL, "gabp_decision_noalloc: bad sizes");
+    if (!(gamma > 0) || !(lambda >= 0)) return fail(GABP_EINVAL, "gabp_decision_noalloc: need gamma > 0, lambda >= 0");
+    if (t == 0) return GABP_OK;
+    const long long Nt = (n + T - 1) / T, Ntt = (t + T - 1) / T;
+    const long long need = n + t + Nt * t;
+    if (need > kNoAllocScratchFloats)
+        return fail(GABP_EINVAL, "gabp_decision_noalloc: n + t + ceil(n/128)*t = " + std::to_string(need) +
+                                     " floats of scratch exceeds the fixed maximum of " +
+                                     std::to_string(kNoAllocScratchFloats) + "; split the test rows");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(GABP_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fail(GABP_ECUDA, "gabp_decision_noalloc: device index out of range");
+    float* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_dev_ptr[dev]) {
+            // Once per device, with that device current: the device address of the
+            // array (its name in host code is only a host-side stand-in).
+            void* ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess)
+                return fail(GABP_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            g_noalloc_dev_ptr[dev] = static_cast<float*>(ptr);
+        }
+        scratch = g_noalloc_dev_ptr[dev];
+    }
+    // Every scratch element read below is written earlier in the same call.
+    float* sq = scratch;
+    float* sqt = scratch + n;
+    float* part = scratch + n + t;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    k_rownorms<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(X, (int)n, (int)m, sq);
+    k_rownorms<<<(unsigned)((t + 255) / 256), 256, 0, s>>>(Xtest, (int)t, (int)m, sqt);
+    k_decision_tiles_noalloc<<<(unsigned)(Ntt * Nt), NTHREADS, 0, s>>>(
+        X, y, alpha, sq, (int)n, (int)m, Xtest, sqt, (int)t, (float)gamma, (float)(lambda * lambda), (int)Nt, part);
+    k_decision_sum<<<(unsigned)((t + 255) / 256), 256, 0, s>>>(part, (int)t, (int)Nt, out);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(GABP_ECUDA, std::string("gabp_decision_noalloc: ") + cudaGetErrorString(e));
+    return GABP_OK;
+}

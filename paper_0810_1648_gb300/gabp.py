@@ -101,6 +101,7 @@ def load():
         "gabp_svm_set_profiling": (st, [V, I32]),
         "gabp_svm_get_profile": (st, [V, P(Profile), I32]),
         "gabp_svm_destroy": (st, [V]),
+        "gabp_decision_noalloc": (st, [V, V, V, I64, I64, V, I64, D, D, V, V]),
         "gabp_last_error": (ctypes.c_char_p, []),
         "gabp_version": (I32, []),
     }
@@ -265,6 +266,14 @@ def svm_get_profile(h, reset: bool = False) -> dict:
     p = Profile()
     _check(load().gabp_svm_get_profile(ctypes.c_void_p(h), ctypes.byref(p), 1 if reset else 0))
     return p.as_dict()
+
+
+def decision_noalloc(X, y, alpha, Xt, gamma: float, lam: float, out, stream=None):
+    """gabp_decision_noalloc: torch CUDA float32 tensors, no allocation in the library."""
+    _sync_torch(X, y, alpha, Xt)
+    _check(load().gabp_decision_noalloc(_ptr(X), _ptr(y), _ptr(alpha), int(X.shape[0]), int(X.shape[1]),
+                                        _ptr(Xt), int(Xt.shape[0]), float(gamma), float(lam), _ptr(out),
+                                        ctypes.c_void_p(stream) if stream else None))
 
 
 def svm_destroy(h):
