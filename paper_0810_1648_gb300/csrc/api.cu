@@ -301,6 +301,8 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
         if (e != cudaSuccess) { destroy_all(h); return fail(GABP_ECUDA, "stream: %s", cudaGetErrorString(e)); }
         h->own_stream = true;
     }
+    e = prepare_sweep();
+    if (e != cudaSuccess) { destroy_all(h); return fail(GABP_ECUDA, "sweep kernel setup: %s", cudaGetErrorString(e)); }
     e = cudaMalloc(&h->pool, pl.total);
     if (e != cudaSuccess) { destroy_all(h); return fail(GABP_ENOMEM, "cudaMalloc(%zu): %s", pl.total, cudaGetErrorString(e)); }
     h->pool_bytes = pl.total;

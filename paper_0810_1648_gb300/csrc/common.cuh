@@ -93,6 +93,8 @@ void launch_form_q(const Inst& p, const int2* work, long long ntiles, int q_bf16
 void launch_init(const Inst& p, int diag_rule, float delta, cudaStream_t s);
 // Solve control: arm the control block for `iters` more rounds with tolerance `tol`.
 void launch_begin(const Inst& p, int iters, double tol, cudaStream_t s);
+// Raises the dynamic shared-memory limit of the pair-sweep kernels (once per device).
+cudaError_t prepare_sweep();
 // One synchronous round: pair sweep then per-node finalize.  When ev is not
 // null, ev[0] is recorded before and ev[1] after the pair sweep.
 void launch_round(const Inst& p, const int2* work, long long ntiles, int q_mode, cudaStream_t s,

@@ -16,13 +16,13 @@
 //            Step-3 test ||r(t)||_inf < tol in the last CTA to finish.
 //
 // The sweep is bound by HBM bandwidth: per pair it reads 16 B of messages and
-// 4 B of Q and writes 16 B.  Each CTA owns one 128 x 128 tile; warp w takes
-// rows w, w+8, ...; lane l takes columns l, l+32, l+64, l+96, so every warp
-// load or store of messages covers 512 contiguous bytes.  The next row's loads
-// are issued before the current row's arithmetic and stores.  Row sums go
-// through warp shuffles, column sums stay in registers and meet in shared
-// memory, and each node's per-tile sums go to its own slot (common.cuh), so
-// the reduction order is fixed and the result reproducible.
+// 4 B of Q (2 B in BF16) and writes 16 B.  Messages and Q arrive in shared
+// memory through bulk copies issued by a producer warp well ahead of use;
+// consumer warp w takes one row of each 8-row chunk, lane l the columns l,
+// l+32, l+64, l+96, so every message store of a warp covers 512 contiguous
+// bytes.  Row sums go through warp shuffles, column sums stay in registers
+// and meet in shared memory, and each node's per-tile sums go to its own slot
+// (common.cuh), so the reduction order is fixed and the result reproducible.
 #include "common.cuh"
 
 #include <float.h>
@@ -31,152 +31,324 @@ namespace gabp {
 
 namespace {
 
+// ---- mbarrier / bulk-copy helpers (inline PTX, sm_90+ forms) ---------------
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // bounded waits: 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr)
+{
+    return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase of `parity` to complete; false after kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    return true;
+}
+
+__device__ __forceinline__ uint64_t l2_evict_first_policy()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// Bulk copy global -> shared (16-byte aligned addresses, size a multiple of
+// 16) completing on `bar` with a transaction count of `bytes`.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, unsigned long long* bar,
+                                          uint64_t pol)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+
+__device__ __forceinline__ void consumer_bar() { asm volatile("bar.sync 1, %0;" ::"n"(NTHREADS) : "memory"); }
+
+__device__ __forceinline__ void record_error(Ctrl* c, int code, long long where)
+{
+    if (atomicCAS(&c->status, 0, code) == 0) c->bad_index = where;
+}
+
+// ---- pair sweep -----------------------------------------------------------
+// Persistent CTAs (two per SM) walk the tile list with stride gridDim.x.  A
+// producer warp streams every tile as chunks of RC rows (messages and Q) into
+// a STAGES-deep shared-memory ring with bulk copies, running ahead across
+// tile boundaries; eight consumer warps take one row of each chunk, update
+// its pairs from shared memory and store the new messages straight to
+// global memory with 128-bit streaming stores.  Only the pairs the tile owns
+// are copied: whole chunks for interior tiles, the c > r part of each row on
+// diagonal tiles, the first `cols` columns on the last tile column.
+constexpr int RC = NWARPS;                    // rows per chunk, one per consumer warp
+constexpr int STAGES = 4;
+constexpr int SWEEP_THREADS = NTHREADS + 32;  // + one producer warp
+constexpr int SWEEP_CTAS_PER_SM = 2;
+
 template <typename QT>
-struct RowData {
-    float q[4];
-    float4 s[4];
+struct SweepStage {
+    float4 s[RC][T];
+    QT q[RC][T];
+};
+
+struct SweepTail {
+    unsigned long long full[STAGES], empty[STAGES];
+    float row[3][T], col[3][T];
+    float cp[NWARPS][T], ch[NWARPS][T], cr[NWARPS][T];
+    float rp[T], rh[T], rr[T];
 };
 
 template <typename QT>
-__device__ __forceinline__ void load_row(RowData<QT>& d, const QT* __restrict__ qt, const float4* st,
-                                         int r, int lane, int cols, bool diag, bool zero)
+constexpr size_t sweep_smem_bytes()
 {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int c = lane + 32 * k;
-        const bool v = c < cols && (!diag || c > r);
-        d.q[k] = v ? to_f(qt[r * T + c]) : 0.f;
-        d.s[k] = (v && !zero) ? __ldcs(&st[r * T + c]) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    return 128 + STAGES * sizeof(SweepStage<QT>) + sizeof(SweepTail);
 }
 
 template <typename QT>
-__global__ void __launch_bounds__(NTHREADS, 2) k_sweep(Inst p, const int2* __restrict__ work)
+__global__ void __launch_bounds__(SWEEP_THREADS, SWEEP_CTAS_PER_SM)
+    k_sweep(Inst p, const int2* __restrict__ work, long long ntiles)
 {
-    const Ctrl* ctrl = p.ctrl;
+    Ctrl* ctrl = p.ctrl;
     if (*(volatile const int*)&ctrl->done) return;
     const int t = *(volatile const int*)&ctrl->t;
-    const long long L = blockIdx.x;
-    const int2 tile = work[L];
-    const int I = tile.x, J = tile.y, n = p.n;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool zero = (t == 0);   // Step 1: all messages 0, nothing to read
 
-    __shared__ float sRow[3][T], sCol[3][T];
-    __shared__ float sCp[NWARPS][T], sCh[NWARPS][T], sCr[NWARPS][T];
-    __shared__ float sRp[T], sRh[T], sRr[T];
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+    SweepStage<QT>* stages = reinterpret_cast<SweepStage<QT>*>(base);
+    SweepTail& sm = *reinterpret_cast<SweepTail*>(base + STAGES * sizeof(SweepStage<QT>));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, n = p.n;
 
-    const float* agg = p.agg + (size_t)(t & 1) * 3 * p.npad;
-    {
-        const int rc = tid < T ? tid : tid - T;
-        const int x = (tid < T ? I : J) * T + rc;
-        const bool v = x < n;
-        float* dst0 = tid < T ? sRow[0] : sCol[0];
-        float* dst1 = tid < T ? sRow[1] : sCol[1];
-        float* dst2 = tid < T ? sRow[2] : sCol[2];
-        dst0[rc] = v ? agg[x] : 1.f;
-        dst1[rc] = v ? agg[p.npad + x] : 0.f;
-        dst2[rc] = v ? agg[2 * p.npad + x] : 0.f;
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&sm.full[s], 1);
+            mbar_init(&sm.empty[s], NWARPS);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
-    const int rows = min(T, n - I * T), cols = min(T, n - J * T);
-    const bool diag = (I == J);
-    const bool zero = (t == 0);   // Step 1: all messages 0, nothing to read
-    float cP[4], cH[4], cM[4], aP[4], aH[4], aR[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int c = lane + 32 * k;
-        cP[k] = sCol[0][c];
-        cH[k] = sCol[1][c];
-        cM[k] = sCol[2][c];
-        aP[k] = aH[k] = aR[k] = 0.f;
-    }
-    float4* st = p.state + (size_t)L * TT;
-    const QT* qt = static_cast<const QT*>(p.qstore) + (size_t)L * TT;
-    bool bad = false;
-
-    RowData<QT> cur, nxt;
-    int r = warp;
-    if (r < rows) load_row(cur, qt, st, r, lane, cols, diag, zero);
-    for (; r < rows; r += NWARPS) {
-        const int rn = r + NWARPS;
-        if (rn < rows) load_row(nxt, qt, st, rn, lane, cols, diag, zero);
-        const float rP = sRow[0][r], rH = sRow[1][r], rM = sRow[2][r];
-        float sp = 0.f, sh = 0.f, sr = 0.f;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int c = lane + 32 * k;
-            const bool v = c < cols && (!diag || c > r);
-            if (v) {
-                const float q = cur.q[k];
-                const float4 s = cur.s[k];       // {P_ij, P_ji, H_ij, H_ji}
-                const float di = rP - s.y;       // Ptilde_i - P_ji
-                const float dj = cP[k] - s.x;    // Ptilde_j - P_ij
-                bad |= !(di > 0.f && di <= FLT_MAX && dj > 0.f && dj <= FLT_MAX);
-                const float ii = __frcp_rn(di), ij = __frcp_rn(dj);
-                const float q2 = q * q;
-                const float nPij = -q2 * ii;
-                const float nPji = -q2 * ij;
-                const float nHij = -q * (rH - s.w) * ii;
-                const float nHji = -q * (cH[k] - s.z) * ij;
-                __stcs(&st[r * T + c], make_float4(nPij, nPji, nHij, nHji));
-                sp += nPji;
-                sh += nHji;
-                sr = fmaf(q, cM[k], sr);
-                aP[k] += nPij;
-                aH[k] += nHij;
-                aR[k] = fmaf(q, rM, aR[k]);
+    if (warp == NWARPS) {
+        // ------------------------------------------------------ producer
+        if (lane != 0) return;
+        const uint64_t pol = l2_evict_first_policy();
+        int stage = 0;
+        uint32_t phase = 0;
+        for (long long L = blockIdx.x; L < ntiles; L += gridDim.x) {
+            const int2 tile = work[L];
+            const int I = tile.x, J = tile.y;
+            const int rows = min(T, n - I * T), cols = min(T, n - J * T);
+            const bool diag = (I == J);
+            const float4* st = p.state + (size_t)L * TT;
+            const QT* qt = static_cast<const QT*>(p.qstore) + (size_t)L * TT;
+            const int nch = (rows + RC - 1) / RC;
+            for (int c = 0; c < nch; ++c) {
+                if (!mbar_wait(&sm.empty[stage], phase ^ 1u)) {
+                    record_error(ctrl, ST_ETIMEOUT, L);
+                    return;
+                }
+                SweepStage<QT>& S = stages[stage];
+                unsigned long long* bar = &sm.full[stage];
+                const int r0 = c * RC, nr = min(RC, rows - r0);
+                if (!diag && cols == T) {
+                    const uint32_t bq = (uint32_t)(nr * T * sizeof(QT));
+                    const uint32_t bs = zero ? 0u : (uint32_t)(nr * T * sizeof(float4));
+                    mbar_arrive_expect_tx(bar, bq + bs);
+                    bulk_load(&S.q[0][0], qt + (size_t)r0 * T, bq, bar, pol);
+                    if (!zero) bulk_load(&S.s[0][0], st + (size_t)r0 * T, bs, bar, pol);
+                } else {
+                    // per row: columns [c0, c1) with c0, c1 multiples of 8 (16-byte
+                    // granules of both arrays) covering the pairs the row owns
+                    const int c1 = min(T, (cols + 7) & ~7);
+                    uint32_t bytes = 0;
+                    for (int k = 0; k < nr; ++k) {
+                        const int r = r0 + k, c0 = diag ? ((r + 1) & ~7) : 0;
+                        if (c0 < c1 && (!diag || r + 1 < cols))
+                            bytes += (uint32_t)((c1 - c0) * (sizeof(QT) + (zero ? 0 : sizeof(float4))));
+                    }
+                    mbar_arrive_expect_tx(bar, bytes);
+                    for (int k = 0; k < nr; ++k) {
+                        const int r = r0 + k, c0 = diag ? ((r + 1) & ~7) : 0;
+                        if (!(c0 < c1 && (!diag || r + 1 < cols))) continue;
+                        bulk_load(&S.q[k][c0], qt + (size_t)r * T + c0, (uint32_t)((c1 - c0) * sizeof(QT)), bar, pol);
+                        if (!zero)
+                            bulk_load(&S.s[k][c0], st + (size_t)r * T + c0, (uint32_t)((c1 - c0) * sizeof(float4)),
+                                      bar, pol);
+                    }
+                }
+                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
             }
         }
-        sp = warp_sum(sp);
-        sh = warp_sum(sh);
-        sr = warp_sum(sr);
-        if (lane == 0) { sRp[r] = sp; sRh[r] = sh; sRr[r] = sr; }
-        if (rn < rows) cur = nxt;
+        return;
     }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int c = lane + 32 * k;
-        sCp[warp][c] = aP[k];
-        sCh[warp][c] = aH[k];
-        sCr[warp][c] = aR[k];
-    }
-    if (bad) {
-        Ctrl* cw = p.ctrl;
-        if (atomicCAS(&cw->status, 0, (int)ST_ENUMERIC) == 0) cw->bad_index = (long long)I * T;
-    }
-    __syncthreads();
 
+    // ---------------------------------------------------------- consumers
+    const float* agg = p.agg + (size_t)(t & 1) * 3 * p.npad;
     float* partP = p.part;
     float* partH = partP + (size_t)p.Nt * n;
     float* partR = partH + (size_t)p.Nt * n;
-    if (diag) {
-        if (tid < rows) {
-            float P = sRp[tid], H = sRh[tid], R = sRr[tid];
-#pragma unroll
-            for (int w = 0; w < NWARPS; ++w) { P += sCp[w][tid]; H += sCh[w][tid]; R += sCr[w][tid]; }
-            const size_t o = (size_t)I * n + I * T + tid;
-            partP[o] = P; partH[o] = H; partR[o] = R;
+    int stage = 0;
+    uint32_t phase = 0;
+    bool bad = false, abort = false;
+    for (long long L = blockIdx.x; L < ntiles; L += gridDim.x) {
+        const int2 tile = work[L];
+        const int I = tile.x, J = tile.y;
+        const int rows = min(T, n - I * T), cols = min(T, n - J * T);
+        const bool diag = (I == J);
+        {
+            const int rc = tid < T ? tid : tid - T;
+            const int x = (tid < T ? I : J) * T + rc;
+            const bool v = x < n;
+            float(*dst)[T] = tid < T ? sm.row : sm.col;
+            dst[0][rc] = v ? agg[x] : 1.f;
+            dst[1][rc] = v ? agg[p.npad + x] : 0.f;
+            dst[2][rc] = v ? agg[2 * p.npad + x] : 0.f;
         }
-    } else if (tid < T) {
-        if (tid < rows) {
-            const size_t o = (size_t)J * n + I * T + tid;
-            partP[o] = sRp[tid]; partH[o] = sRh[tid]; partR[o] = sRr[tid];
-        }
-    } else {
-        const int c = tid - T;
-        if (c < cols) {
-            float P = 0.f, H = 0.f, R = 0.f;
+        consumer_bar();
+        float cP[4], cH[4], cM[4], aP[4], aH[4], aR[4];
 #pragma unroll
-            for (int w = 0; w < NWARPS; ++w) { P += sCp[w][c]; H += sCh[w][c]; R += sCr[w][c]; }
-            const size_t o = (size_t)I * n + J * T + c;
-            partP[o] = P; partH[o] = H; partR[o] = R;
+        for (int k = 0; k < 4; ++k) {
+            const int c = lane + 32 * k;
+            cP[k] = sm.col[0][c];
+            cH[k] = sm.col[1][c];
+            cM[k] = sm.col[2][c];
+            aP[k] = aH[k] = aR[k] = 0.f;
+        }
+        float4* st = p.state + (size_t)L * TT;
+        const int nch = (rows + RC - 1) / RC;
+        for (int ch = 0; ch < nch; ++ch) {
+            if (!abort && !mbar_wait(&sm.full[stage], phase)) {
+                abort = true;
+                record_error(ctrl, ST_ETIMEOUT, L);
+            }
+            const int r = ch * RC + warp;
+            if (!abort && r < rows) {
+                const SweepStage<QT>& S = stages[stage];
+                const float rP = sm.row[0][r], rH = sm.row[1][r], rM = sm.row[2][r];
+                float sp = 0.f, sh = 0.f, sr = 0.f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int c = lane + 32 * k;
+                    if (c < cols && (!diag || c > r)) {
+                        const float q = to_f(S.q[warp][c]);
+                        const float4 s = zero ? make_float4(0.f, 0.f, 0.f, 0.f) : S.s[warp][c];  // {P_ij, P_ji, H_ij, H_ji}
+                        const float di = rP - s.y;      // Ptilde_i - P_ji
+                        const float dj = cP[k] - s.x;   // Ptilde_j - P_ij
+                        bad |= !(di > 0.f && di <= FLT_MAX && dj > 0.f && dj <= FLT_MAX);
+                        const float ii = __frcp_rn(di), ij = __frcp_rn(dj);
+                        const float q2 = q * q;
+                        const float nPij = -q2 * ii;
+                        const float nPji = -q2 * ij;
+                        const float nHij = -q * (rH - s.w) * ii;
+                        const float nHji = -q * (cH[k] - s.z) * ij;
+                        __stcs(&st[r * T + c], make_float4(nPij, nPji, nHij, nHji));
+                        sp += nPji;
+                        sh += nHji;
+                        sr = fmaf(q, cM[k], sr);
+                        aP[k] += nPij;
+                        aH[k] += nHij;
+                        aR[k] = fmaf(q, rM, aR[k]);
+                    }
+                }
+                sp = warp_sum(sp);
+                sh = warp_sum(sh);
+                sr = warp_sum(sr);
+                if (lane == 0) { sm.rp[r] = sp; sm.rh[r] = sh; sm.rr[r] = sr; }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.empty[stage]);
+            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = lane + 32 * k;
+            sm.cp[warp][c] = aP[k];
+            sm.ch[warp][c] = aH[k];
+            sm.cr[warp][c] = aR[k];
+        }
+        consumer_bar();
+        if (diag) {
+            if (tid < rows) {
+                float P = sm.rp[tid], H = sm.rh[tid], R = sm.rr[tid];
+#pragma unroll
+                for (int w = 0; w < NWARPS; ++w) { P += sm.cp[w][tid]; H += sm.ch[w][tid]; R += sm.cr[w][tid]; }
+                const size_t o = (size_t)I * n + I * T + tid;
+                partP[o] = P; partH[o] = H; partR[o] = R;
+            }
+        } else if (tid < T) {
+            if (tid < rows) {
+                const size_t o = (size_t)J * n + I * T + tid;
+                partP[o] = sm.rp[tid]; partH[o] = sm.rh[tid]; partR[o] = sm.rr[tid];
+            }
+        } else {
+            const int c = tid - T;
+            if (c < cols) {
+                float P = 0.f, H = 0.f, R = 0.f;
+#pragma unroll
+                for (int w = 0; w < NWARPS; ++w) { P += sm.cp[w][c]; H += sm.ch[w][c]; R += sm.cr[w][c]; }
+                const size_t o = (size_t)I * n + J * T + c;
+                partP[o] = P; partH[o] = H; partR[o] = R;
+            }
         }
     }
+    if (bad) record_error(ctrl, ST_ENUMERIC, -1);
 }
 
-// Per node x: FP64 sums of its Nt slots (32 nodes x 8 slot groups per CTA),
-// next aggregates, residual r_x(t), CTA max |r| -> ctrl, last CTA decides.
+// Compensated FP32 accumulation (Knuth's TwoSum): s + c carries the running
+// sum with an error term, so sums of a few hundred FP32 partials keep close to
+// 48 bits without using the (slow) FP64 pipe.
+__device__ __forceinline__ void acc2(float& s, float& c, float x)
+{
+    const float t = s + x;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+}
+
+// Per node x: compensated sums of its Nt slots (32 nodes x 8 slot groups per
+// CTA, four slots in flight per thread), next aggregates, residual r_x(t) in
+// FP64, CTA max |r| -> ctrl, the last CTA to finish decides.
 __global__ void __launch_bounds__(256) k_finalize(Inst p)
 {
     Ctrl* ctrl = p.ctrl;
@@ -187,26 +359,47 @@ __global__ void __launch_bounds__(256) k_finalize(Inst p)
     const float* partP = p.part;
     const float* partH = partP + (size_t)Nt * n;
     const float* partR = partH + (size_t)Nt * n;
-    double sP = 0.0, sH = 0.0, sR = 0.0;
-    if (x < n)
-        for (int k = g; k < Nt; k += 8) {
-            const size_t o = (size_t)k * n + x;
-            sP += (double)partP[o];
-            sH += (double)partH[o];
-            sR += (double)partR[o];
+    float sP = 0.f, cPs = 0.f, sH = 0.f, cHs = 0.f, sR = 0.f, cRs = 0.f;
+    if (x < n) {
+        int k = g;
+        for (; k + 24 < Nt; k += 32) {
+            float vp[4], vh[4], vr[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const size_t o = (size_t)(k + 8 * u) * n + x;
+                vp[u] = partP[o];
+                vh[u] = partH[o];
+                vr[u] = partR[o];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { acc2(sP, cPs, vp[u]); acc2(sH, cHs, vh[u]); acc2(sR, cRs, vr[u]); }
         }
-    __shared__ double red[3][8][32];
+        for (; k < Nt; k += 8) {
+            const size_t o = (size_t)k * n + x;
+            acc2(sP, cPs, partP[o]);
+            acc2(sH, cHs, partH[o]);
+            acc2(sR, cRs, partR[o]);
+        }
+    }
+    __shared__ float red[6][8][32];
     __shared__ int s_last;
-    red[0][g][lane] = sP;
-    red[1][g][lane] = sH;
-    red[2][g][lane] = sR;
+    red[0][g][lane] = sP; red[1][g][lane] = cPs;
+    red[2][g][lane] = sH; red[3][g][lane] = cHs;
+    red[4][g][lane] = sR; red[5][g][lane] = cRs;
     __syncthreads();
     if (g == 0) {
         double absr = 0.0;
         if (x < n) {
-            double P = 0.0, H = 0.0, R = 0.0;
+            float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int w = 0; w < 8; ++w) { P += red[0][w][lane]; H += red[1][w][lane]; R += red[2][w][lane]; }
+            for (int w = 0; w < 8; ++w) {
+                acc2(a[0], a[1], red[0][w][lane]); a[1] += red[1][w][lane];
+                acc2(a[2], a[3], red[2][w][lane]); a[3] += red[3][w][lane];
+                acc2(a[4], a[5], red[4][w][lane]); a[5] += red[5][w][lane];
+            }
+            const double P = (double)a[0] + (double)a[1];
+            const double H = (double)a[2] + (double)a[3];
+            const double R = (double)a[4] + (double)a[5];
             const float* cur = p.agg + (size_t)(t & 1) * 3 * p.npad;
             float* nxt = p.agg + (size_t)((t + 1) & 1) * 3 * p.npad;
             const double qd = p.qdiag[x], bx = p.b[x];
@@ -219,9 +412,7 @@ __global__ void __launch_bounds__(256) k_finalize(Inst p)
             const double r = bx - qd * (double)cur[2 * p.npad + x] - R;
             absr = fabs(r);
             if (!(absr <= DBL_MAX)) absr = INFINITY;
-            if (!(Pn > 0.f) || !isfinite(mn)) {
-                if (atomicCAS(&ctrl->status, 0, (int)ST_ENUMERIC) == 0) ctrl->bad_index = x;
-            }
+            if (!(Pn > 0.f) || !isfinite(mn)) record_error(ctrl, ST_ENUMERIC, x);
         }
         absr = warp_max_d(absr);
         if (lane == 0)
@@ -329,14 +520,37 @@ void launch_begin(const Inst& p, int iters, double tol, cudaStream_t s)
     k_begin<<<1, 1, 0, s>>>(p.ctrl, iters, tol);
 }
 
+int sweep_grid(long long ntiles)
+{
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    const long long g = (long long)sms * SWEEP_CTAS_PER_SM;
+    return (int)(ntiles < g ? ntiles : g);
+}
+
+cudaError_t prepare_sweep()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_sweep<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sweep_smem_bytes<float>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_sweep<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sweep_smem_bytes<__nv_bfloat16>());
+}
+
 void launch_round(const Inst& p, const int2* work, long long ntiles, int q_mode, cudaStream_t s,
                   cudaEvent_t* ev)
 {
+    const int grid = sweep_grid(ntiles);
     if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
     if (q_mode == 1)
-        k_sweep<__nv_bfloat16><<<(unsigned)ntiles, NTHREADS, 0, s>>>(p, work);
+        k_sweep<__nv_bfloat16><<<grid, SWEEP_THREADS, sweep_smem_bytes<__nv_bfloat16>(), s>>>(p, work, ntiles);
     else
-        k_sweep<float><<<(unsigned)ntiles, NTHREADS, 0, s>>>(p, work);
+        k_sweep<float><<<grid, SWEEP_THREADS, sweep_smem_bytes<float>(), s>>>(p, work, ntiles);
     if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
     k_finalize<<<(p.n + 31) / 32, 256, 0, s>>>(p);
 }
