@@ -224,6 +224,16 @@ GABP_API gabp_status gabp_decision_noalloc(const float* X, const float* y, const
                                            int64_t n, int64_t m, const float* Xtest, int64_t t,
                                            double gamma, double lambda, float* out, void* stream);
 
+/*
+ * Failure-detection self test (no counterpart in the paper): launches one
+ * kernel whose thread waits, with the bounded wait that the pair sweep uses
+ * for its shared-memory pipeline, on a barrier that nothing ever completes.
+ * Returns GABP_ETIMEOUT after about limit_ns nanoseconds (0 < limit_ns <= 1e10)
+ * with the CUDA context still usable; any other result means the bounded
+ * wait is broken.
+ */
+GABP_API gabp_status gabp_selftest_bounded_wait(int64_t limit_ns);
+
 /* Frees everything the handle owns. NULL is accepted. */
 GABP_API gabp_status gabp_svm_destroy(gabp_svm_t h);
 

@@ -644,6 +644,21 @@ gabp_status gabp_svm_get_profile(gabp_svm_t h, gabp_svm_profile* out, int32_t re
     return GABP_OK;
 }
 
+gabp_status gabp_selftest_bounded_wait(int64_t limit_ns)
+{
+    g_err.clear();
+    if (limit_ns <= 0 || limit_ns > 10000000000LL) return fail(GABP_EINVAL, "limit_ns must be in (0, 1e10]");
+    int* d = nullptr;
+    int hst = -1;
+    CK(cudaMalloc(&d, sizeof(int)));
+    cudaError_t e = launch_selftest_wait((unsigned long long)limit_ns, d, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(&hst, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(GABP_ECUDA, "selftest: %s", cudaGetErrorString(e));
+    if (hst == ST_ETIMEOUT) return fail(GABP_ETIMEOUT, "bounded device wait ran out after %lld ns", (long long)limit_ns);
+    return hst == ST_OK ? GABP_OK : fail(GABP_ECUDA, "selftest returned %d", hst);
+}
+
 gabp_status gabp_svm_destroy(gabp_svm_t h)
 {
     g_err.clear();

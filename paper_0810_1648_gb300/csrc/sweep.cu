@@ -75,13 +75,14 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t 
     return ok != 0;
 }
 
-// Waits for the phase of `parity` to complete; false after kWaitLimitNs.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity)
+// Waits for the phase of `parity` to complete; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity,
+                                          unsigned long long limit_ns = kWaitLimitNs)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > kWaitLimitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     return true;
 }
 
@@ -450,6 +451,19 @@ __global__ void __launch_bounds__(256) k_finalize(Inst p)
     }
 }
 
+// Failure-detection self test: one thread waits, with the same bounded wait
+// the sweep uses, on an mbarrier that nothing ever arrives on, and reports
+// ST_ETIMEOUT when the limit runs out (the kernel then returns normally).
+__global__ void k_selftest_wait(unsigned long long limit_ns, int* status)
+{
+    __shared__ unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *status = mbar_wait(&bar, 0u, limit_ns) ? (int)ST_OK : (int)ST_ETIMEOUT;
+    }
+}
+
 // Diagonal rule (Section 3.1) from the |Q| row-sum partials of the Q
 // formation, then Algorithm 2 Step 1: messages 0, so Ptilde = Q_ii,
 // htilde = b_i, mutilde = b_i / Q_ii.  CTA 0 resets the control block.
@@ -560,4 +574,12 @@ void launch_get_pairs(const Inst& p, const long long* ij, long long cnt, float4*
     if (cnt > 0) k_get_pairs<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(p, ij, cnt, out);
 }
 
+}  // namespace gabp
+
+namespace gabp {
+cudaError_t launch_selftest_wait(unsigned long long limit_ns, int* status_dev, cudaStream_t s)
+{
+    k_selftest_wait<<<1, 32, 0, s>>>(limit_ns, status_dev);
+    return cudaGetLastError();
+}
 }  // namespace gabp

@@ -102,6 +102,7 @@ def load():
         "gabp_svm_get_profile": (st, [V, P(Profile), I32]),
         "gabp_svm_destroy": (st, [V]),
         "gabp_decision_noalloc": (st, [V, V, V, I64, I64, V, I64, D, D, V, V]),
+        "gabp_selftest_bounded_wait": (st, [I64]),
         "gabp_last_error": (ctypes.c_char_p, []),
         "gabp_version": (I32, []),
     }
@@ -274,6 +275,12 @@ def decision_noalloc(X, y, alpha, Xt, gamma: float, lam: float, out, stream=None
     _check(load().gabp_decision_noalloc(_ptr(X), _ptr(y), _ptr(alpha), int(X.shape[0]), int(X.shape[1]),
                                         _ptr(Xt), int(Xt.shape[0]), float(gamma), float(lam), _ptr(out),
                                         ctypes.c_void_p(stream) if stream else None))
+
+
+def selftest_bounded_wait(limit_ns: int) -> int:
+    """Status of gabp_selftest_bounded_wait (GABP_ETIMEOUT when the wait works)."""
+    rc = load().gabp_selftest_bounded_wait(int(limit_ns))
+    return rc
 
 
 def svm_destroy(h):
