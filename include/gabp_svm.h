@@ -84,7 +84,8 @@ typedef struct {
     int32_t bias_mode;     /* 0 = lambda = 1/n (default), 1 = lambda = bias_lambda (may be 0) */
     double  bias_lambda;
     int32_t q_mode;        /* gabp_q_mode, default GABP_Q_F32 */
-    int32_t refine;        /* reserved for the precision form; 0 */
+    int32_t refine;        /* precision form only: up to this many defect-correction passes with the
+                              FP32-Gram residual (FP64 sums); 0 = plain BF16 solve */
     double  sv_threshold;  /* support vectors are the i with alpha_i > sv_threshold (default 0) */
     int32_t chunk;         /* sweeps per captured CUDA graph replay between convergence checks; 0 = 16 */
     int32_t reserved[7];
@@ -104,6 +105,7 @@ typedef struct {
     double  lambda, gamma, C, diag_delta;
     int64_t device_bytes;      /* device memory held by the handle */
     int32_t q_mode, diag_rule;
+    int32_t refine_passes;     /* defect-correction passes done by the last solve */
 } gabp_svm_stats;
 
 /* Default options. */

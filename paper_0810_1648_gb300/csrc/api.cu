@@ -77,6 +77,9 @@ struct gabp_svm_s {
     gabp_svm_profile prof{};
     bool solved = false;
     int kstar = 0;
+    float* mu_acc = nullptr;        // refined means (precision form)
+    float* r32 = nullptr;           // FP32 residual of the accurate matrix (refinement)
+    const float* mean_src = nullptr;  // device array holding the means of the last solve
     gabp_svm_stats stats{};
 };
 
@@ -90,12 +93,13 @@ gabp_status check_handle(gabp_svm_t h)
 
 // Device memory plan of one handle (bytes, 256-aligned sub-buffers).
 struct Plan {
-    size_t X, vec, agg, part, state, q, work, ctrl, rhist, final3, blockbuf, total;
+    size_t X, vec, agg, part, state, q, work, ctrl, rhist, final3, blockbuf, xp, total;
 };
 
 Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_mode)
 {
     Plan p{};
+    p.xp = q_mode != GABP_Q_F32 ? align_up(bf16_pack_bytes(Nt, (int)m), 1024) : 0;
     p.X = align_up((size_t)n * m * sizeof(float), 256);
     p.vec = align_up((size_t)npad * sizeof(float), 256);
     p.agg = align_up((size_t)6 * npad * sizeof(float), 256);
@@ -109,8 +113,8 @@ Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_m
     p.rhist = align_up((size_t)kRhistCap * sizeof(double), 256);
     p.final3 = 256;
     p.blockbuf = align_up((size_t)3 * ((n + 31) / 32) * sizeof(double), 256);
-    p.total = p.X + 6 * p.vec + p.agg + p.part + p.state + p.q + p.work + p.ctrl + p.rhist +
-              p.final3 + p.blockbuf;
+    p.total = p.X + 9 * p.vec + p.agg + p.part + p.state + p.q + p.work + p.ctrl + p.rhist +
+              p.final3 + p.blockbuf + p.xp + 1024;
     return p;
 }
 
@@ -136,6 +140,7 @@ gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
     clear_graphs(h);
     h->solved = false;
     h->kstar = 0;
+    h->mean_src = nullptr;
 
     CK(cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), s));
     // labels -> device copy (validated by the staging kernel, which also sets b = 1)
@@ -162,11 +167,27 @@ gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
     if (h->hctrl->status != 0)
         return fail(GABP_EINVAL, "row %lld: non-finite feature or label not +-1",
                     (long long)h->hctrl->bad_index);
-    launch_form_q(p, h->work, h->ntiles, h->opts.q_mode == GABP_Q_BF16, s);
-    CK(cudaGetLastError());
-    launch_init(p, h->opts.diag_rule, (float)h->delta, s);
-    h->prof.kernel_launches += 2;
-    CK(cudaGetLastError());
+    if (h->opts.q_mode == GABP_Q_F32) {
+        launch_form_q(p, h->work, h->ntiles, 1, s);
+        CK(cudaGetLastError());
+        launch_init(p, h->opts.diag_rule, (float)h->delta, s);
+        h->prof.kernel_launches += 2;
+        CK(cudaGetLastError());
+    } else {
+        // Precision form: the diagonal weighting uses the FP32 Gram's row sums
+        // (the accurate matrix); the off-diagonal entries come from the BF16
+        // tensor-core Gram.
+        CK(launch_pack_bf16(p.X, (int)n, (int)m, p.nkc, h->Nt, (void*)p.Xp, (float*)p.sqb, s));
+        launch_form_q(p, h->work, h->ntiles, 0, s);
+        CK(cudaGetLastError());
+        launch_init(p, h->opts.diag_rule, (float)h->delta, s);
+        CK(cudaGetLastError());
+        h->prof.kernel_launches += 4;
+        if (h->opts.q_mode == GABP_Q_BF16) {
+            CK(launch_form_q_tc(p, h->work, h->ntiles, p.Xp, p.nkc, p.sqb, s));
+            h->prof.kernel_launches += 1;
+        }
+    }
     CK(cudaStreamSynchronize(s));
     return GABP_OK;
 }
@@ -207,6 +228,55 @@ gabp_status get_graph(gabp_svm_t h, int rounds, gabp_svm_s::Graph** out)
     if (e != cudaSuccess) return fail(GABP_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
     auto res = h->graphs.emplace(key, std::move(G));
     *out = &res.first->second;
+    return GABP_OK;
+}
+
+// Runs up to `iters` synchronous rounds from the current state with the
+// residual test `tol`, as captured graphs of `chunk` rounds, reading the
+// control block after each replay.  *out = the final control block.
+gabp_status run_rounds(gabp_svm_t h, int iters, double tol, Ctrl* out)
+{
+    cudaStream_t s = h->stream;
+    Inst& p = h->inst;
+    launch_begin(p, iters, tol, s);
+    h->prof.kernel_launches += 1;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->hctrl, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (iters > 0) {
+        const int len = tol > 0 ? std::min<int>(h->opts.chunk, iters) : iters;
+        gabp_svm_s::Graph* g = nullptr;
+        if (gabp_status st = get_graph(h, len, &g)) return st;
+        const int max_chunks = (iters + len - 1) / len + 1;
+        int t_before = h->hctrl->t;
+        for (int c = 0; c < max_chunks; ++c) {
+            CK(cudaGraphLaunch(g->exec, s));
+            h->prof.kernel_launches += 2 * len;
+            CK(cudaMemcpyAsync(h->hctrl, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            const int ran = h->hctrl->t - t_before;
+            if (!g->ev.empty()) {
+                for (int k = 0; k < ran && k < len; ++k) {
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, g->ev[(size_t)2 * k], g->ev[(size_t)2 * k + 1]));
+                    h->prof.sweep_ms += ms;
+                    h->prof.sweep_launches += 1;
+                    if (t_before + k == 0) h->prof.sweep_launches_zero_state += 1;
+                }
+            }
+            t_before = h->hctrl->t;
+            if (h->hctrl->done) break;
+        }
+    }
+    const Ctrl c = *h->hctrl;
+    *out = c;
+    if (!c.done) return fail(GABP_ECUDA, "solve loop did not reach its stop condition");
+    if (c.status == ST_ENUMERIC)
+        return fail(GABP_ENUMERIC, "nonpositive or non-finite cavity precision near node %lld in round %d",
+                    c.bad_index, c.kstar);
+    if (c.status == ST_ETIMEOUT)
+        return fail(GABP_ETIMEOUT, "a bounded device wait ran out in round %d (tile %lld)", c.kstar, c.bad_index);
+    if (c.status != 0) return fail(GABP_ECUDA, "device status %d", c.status);
     return GABP_OK;
 }
 
@@ -263,8 +333,9 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     if (!(o.diag_delta > 0) || !std::isfinite(o.diag_delta)) return fail(GABP_EINVAL, "diag_delta must be > 0");
     if (o.bias_mode == 1 && (!(o.bias_lambda >= 0) || !std::isfinite(o.bias_lambda)))
         return fail(GABP_EINVAL, "bias_lambda must be finite and >= 0");
-    if (o.q_mode != GABP_Q_F32)
+    if (o.q_mode != GABP_Q_F32 && o.q_mode != GABP_Q_BF16)
         return fail(GABP_EINVAL, "q_mode %d is not available in this build", o.q_mode);
+    if (o.refine < 0 || o.refine > 64) return fail(GABP_EINVAL, "refine must be in [0, 64]");
 
     int dev = 0, ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -326,6 +397,9 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     p.qdiag = (float*)take(pl.vec);
     h->alpha = (float*)take(pl.vec);
     take(pl.vec);
+    p.sqb = (const float*)take(pl.vec);
+    h->mu_acc = (float*)take(pl.vec);
+    h->r32 = (float*)take(pl.vec);
     p.agg = (float*)take(pl.agg);
     p.part = (float*)take(pl.part);
     p.state = (float4*)take(pl.state);
@@ -336,6 +410,11 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     p.rhist_cap = kRhistCap;
     h->final3 = (double*)take(pl.final3);
     h->blockbuf = (double*)take(pl.blockbuf);
+    if (pl.xp) {
+        off = align_up(off, 1024);
+        p.Xp = take(pl.xp);
+        p.nkc = bf16_chunks((int)m);
+    }
 
     // Tile work list: the upper triangle, row by row; L(I,J) = I*Nt - I(I-1)/2 + (J-I).
     std::vector<int2> wl((size_t)h->ntiles);
@@ -375,66 +454,71 @@ gabp_status gabp_svm_solve(gabp_svm_t h, int32_t iters, double tol, float* alpha
     CK(cudaMemcpyAsync(h->hctrl, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (h->hctrl->status != 0) return fail(GABP_ESTATE, "state is invalid after an earlier failure; refit first");
-    const int t0 = h->hctrl->t;
-    if ((long long)t0 + iters >= (long long)INT_MAX) return fail(GABP_EINVAL, "too many rounds");
-    launch_begin(p, iters, tol, s);
-    h->prof.kernel_launches += 1;
-    CK(cudaGetLastError());
-    if (iters > 0) {
-        const int len = tol > 0 ? std::min<int>(h->opts.chunk, iters) : iters;
-        gabp_svm_s::Graph* g = nullptr;
-        if (gabp_status st = get_graph(h, len, &g)) return st;
-        const int max_chunks = (iters + len - 1) / len + 1;
-        int t_before = t0;
-        for (int c = 0; c < max_chunks; ++c) {
-            CK(cudaGraphLaunch(g->exec, s));
-            h->prof.kernel_launches += 2 * len;
-            CK(cudaMemcpyAsync(h->hctrl, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            const int ran = h->hctrl->t - t_before;
-            if (!g->ev.empty()) {
-                for (int k = 0; k < ran && k < len; ++k) {
-                    float ms = 0.f;
-                    CK(cudaEventElapsedTime(&ms, g->ev[(size_t)2 * k], g->ev[(size_t)2 * k + 1]));
-                    h->prof.sweep_ms += ms;
-                    h->prof.sweep_launches += 1;
-                    if (t_before + k == 0) h->prof.sweep_launches_zero_state += 1;
-                }
-            }
-            t_before = h->hctrl->t;
-            if (h->hctrl->done) break;
-        }
-    } else {
-        CK(cudaMemcpyAsync(h->hctrl, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
+    const bool refine = h->opts.q_mode != GABP_Q_F32 && h->opts.refine > 0;
+    if (refine) {
+        // The refined solve always starts from Step 1 (b = 1, messages 0).
+        launch_reset(p, s);
+        h->prof.kernel_launches += 1;
     }
-    const Ctrl c = *h->hctrl;
-    if (!c.done) return fail(GABP_ECUDA, "solve loop did not reach its stop condition");
+    CK(cudaMemcpyAsync(h->hctrl, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int t0 = h->hctrl->t;
+    if ((long long)t0 + (long long)iters * (1 + h->opts.refine) >= (long long)INT_MAX)
+        return fail(GABP_EINVAL, "too many rounds");
+    Ctrl c{};
+    if (gabp_status st = run_rounds(h, iters, tol, &c)) return st;
     h->kstar = c.kstar;
-    if (c.status == ST_ENUMERIC)
-        return fail(GABP_ENUMERIC, "nonpositive or non-finite cavity precision near node %lld in round %d",
-                    c.bad_index, c.kstar);
-    launch_final(p, h->work, h->ntiles, c.kstar & 1, h->alpha, h->final3, h->blockbuf, 0,
-                 (float)h->opts.sv_threshold, s);
+    const float* mu = p.agg + (size_t)(c.kstar & 1) * 3 * p.npad + 2 * (size_t)p.npad;
+    int refine_done = 0;
+    if (refine) {
+        // Defect correction: mu_acc solves the BF16 system; r = 1 - Q32 mu_acc
+        // with the FP32-Gram matrix and FP64 sums; GaBP on the BF16 system with
+        // right-hand side r (P messages kept, H restarted) gives the
+        // correction d; mu_acc += d; repeat until ||r||_inf < tol.
+        launch_axpy_mu(p, c.kstar, h->mu_acc, 1, s);
+        for (int it = 0; it < h->opts.refine; ++it) {
+            launch_final(p, h->work, h->ntiles, h->mu_acc, h->alpha, h->final3, h->blockbuf,
+                         (float)h->opts.sv_threshold, h->r32, s);
+            CK(cudaMemcpyAsync(h->hfinal, h->final3, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            h->prof.kernel_launches += 4;
+            const double rn = h->hfinal[0];
+            if (!(rn >= tol)) break;
+            launch_refine_rhs(p, h->r32, s);
+            h->prof.kernel_launches += 1;
+            const double inner = std::max(tol * 0.5, 1e-2 * rn);
+            Ctrl ci{};
+            if (gabp_status st = run_rounds(h, iters, inner, &ci)) return st;
+            launch_axpy_mu(p, ci.kstar, h->mu_acc, 0, s);
+            h->prof.kernel_launches += 1;
+            ++refine_done;
+        }
+        mu = h->mu_acc;
+    }
+    launch_final(p, h->work, h->ntiles, mu, h->alpha, h->final3, h->blockbuf, (float)h->opts.sv_threshold,
+                 nullptr, s);
     h->prof.kernel_launches += 3;
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->hfinal, h->final3, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (alpha)
         CK(cudaMemcpyAsync(alpha, h->alpha, (size_t)h->n * sizeof(float),
                            h->opts.ptr_mode == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->hctrl, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     h->solved = true;
+    h->mean_src = mu;
     gabp_svm_stats& S = h->stats;
     S.n = h->n;
     S.m = h->m;
-    S.sweeps_total = c.t;
+    S.sweeps_total = h->hctrl->t;
     S.kstar = c.kstar;
-    S.converged = c.converged;
+    S.converged = refine ? (h->hfinal[0] < tol ? 1 : 0) : c.converged;
     S.residual_inf = h->hfinal[0];
     S.dual_objective = h->hfinal[1];
     S.n_support = (int64_t)std::llround(h->hfinal[2]);
+    S.refine_passes = refine_done;
     if (residual_inf) *residual_inf = h->hfinal[0];
-    if (iters_done) *iters_done = c.kstar - t0;
+    if (iters_done) *iters_done = refine ? (h->hctrl->t - t0) : (c.kstar - t0);
     return GABP_OK;
 }
 
@@ -444,7 +528,7 @@ gabp_status gabp_svm_get_mean(gabp_svm_t h, float* mu)
     if (gabp_status s = check_handle(h)) return s;
     if (!mu) return fail(GABP_EINVAL, "mu is NULL");
     const Inst& p = h->inst;
-    const float* src = p.agg + (size_t)(h->kstar & 1) * 3 * p.npad + 2 * (size_t)p.npad;
+    const float* src = h->mean_src ? h->mean_src : p.agg + 2 * (size_t)p.npad;
     CK(cudaMemcpyAsync(mu, src, (size_t)h->n * sizeof(float),
                        h->opts.ptr_mode == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));

@@ -45,9 +45,9 @@ struct Ctrl {
     int kstar;                // round whose aggregates are the answer
     int converged;            // 1 if the residual test stopped the solve
     int status;               // first error (Status), 0 if none
+    int zero_h;               // next sweep treats the H messages as 0 (restart of the b-dependent part)
     long long bad_index;      // offending node (or pair row) of the first error
     unsigned int blocks_done; // last-block-done counter of the finalize kernel
-    int pad0;
     unsigned long long rmax_bits;  // running max |r_i| of the round (bits of a nonnegative double)
     double tol;
     double rinf;              // ||r(kstar)||_inf as seen by the convergence test
@@ -74,6 +74,9 @@ struct Inst {
     float gamma;      // RBF width
     float lam2;       // lambda^2
     float C;          // box constant
+    const void* Xp;   // BF16 features packed in tensor-core operand blocks (precision form)
+    const float* sqb; // ||bf16(x_i)||^2
+    int nkc;          // 64-feature chunks of Xp
 };
 
 // Gram operands: rows [0, n) of an n x m FP32 matrix with row norms sq.
@@ -87,8 +90,22 @@ struct GramSide {
 // Inputs: convert/validate X and y, row norms.  Returns nothing; errors go to ctrl->status.
 void launch_stage(const void* X, int x_f64, int n, int m, const float* y, float* Xf, float* sq,
                   float* b, Ctrl* ctrl, cudaStream_t s);
-// Q formation (FP32 SIMT Gram fused with exp, labels and bias) + |Q| row-sum partials.
-void launch_form_q(const Inst& p, const int2* work, long long ntiles, int q_bf16, cudaStream_t s);
+// Q formation (FP32 SIMT Gram fused with exp, labels and bias) + |Q| row-sum partials;
+// store_f32 = 0 computes only the row sums.
+void launch_form_q(const Inst& p, const int2* work, long long ntiles, int store_f32, cudaStream_t s);
+// Precision form: BF16 operand packing + norms, and the tensor-core Q formation (BF16 store).
+cudaError_t launch_pack_bf16(const float* Xf, int n, int m, int nkc, int Nt, void* Xp, float* sqb, cudaStream_t s);
+cudaError_t launch_form_q_tc(const Inst& p, const int2* work, long long ntiles, const void* Xp, int nkc,
+                             const float* sqb, cudaStream_t s);
+int bf16_chunks(int m);
+size_t bf16_pack_bytes(int Nt, int m);
+// Restart: Step-1 aggregates from the stored diagonal and b, t = 0.
+void launch_reset(const Inst& p, cudaStream_t s);
+// Refinement: b := r (FP32 residual of the accurate Q), htilde := b, next sweep
+// restarts the H messages (the P messages, independent of b, are kept).
+void launch_refine_rhs(const Inst& p, const float* r, cudaStream_t s);
+// acc += mutilde of buffer buf (n entries).
+void launch_axpy_mu(const Inst& p, int buf, float* acc, int first, cudaStream_t s);
 // Diagonal rule, Step-1 aggregates and control reset.
 void launch_init(const Inst& p, int diag_rule, float delta, cudaStream_t s);
 // Solve control: arm the control block for `iters` more rounds with tolerance `tol`.
@@ -99,10 +116,11 @@ cudaError_t prepare_sweep();
 // null, ev[0] is recorded before and ev[1] after the pair sweep.
 void launch_round(const Inst& p, const int2* work, long long ntiles, int q_mode, cudaStream_t s,
                   cudaEvent_t* ev = nullptr);
-// Final residual / dual objective / alpha for the aggregates in buffer `buf`.
-void launch_final(const Inst& p, const int2* work, long long ntiles, int buf, float* alpha,
-                  double* out3 /* rinf, objective, nsv */, double* blockbuf, int nblockbuf,
-                  float sv_threshold, cudaStream_t s);
+// Final FP32-Gram residual r = 1 - Q mu (FP64 sums), dual objective and
+// alpha = clip(mu, 0, C) for the means mu; out3 = {||r||_inf, objective, #SV};
+// r_out (optional) receives r in FP32.
+void launch_final(const Inst& p, const int2* work, long long ntiles, const float* mu, float* alpha,
+                  double* out3, double* blockbuf, float sv_threshold, float* r_out, cudaStream_t s);
 // Decision values for t test rows (Xt FP32, sqt norms) using alpha.
 void launch_decision(const Inst& p, const float* Xt, const float* sqt, int t, const float* alpha,
                      const int2* work, long long ntiles, float* part, float* out, cudaStream_t s);

@@ -173,7 +173,7 @@ __global__ void k_stage(const void* __restrict__ X, int x_f64, int n, int m, con
 }
 
 // ------------------------------------------------------- Q tile formation
-__global__ void __launch_bounds__(NTHREADS) k_form_q(Inst p, const int2* __restrict__ work)
+__global__ void __launch_bounds__(NTHREADS) k_form_q(Inst p, const int2* __restrict__ work, int store)
 {
     __shared__ __align__(16) TileSmem sm;
     const long long L = blockIdx.x;
@@ -210,9 +210,11 @@ __global__ void __launch_bounds__(NTHREADS) k_form_q(Inst p, const int2* __restr
             cs[0][b] += fabsf(out[b]);
         }
         rs[0][a] = racc;
-        float4* dst = reinterpret_cast<float4*>(qt + r * T + tx * 8);
-        dst[0] = make_float4(out[0], out[1], out[2], out[3]);
-        dst[1] = make_float4(out[4], out[5], out[6], out[7]);
+        if (store) {
+            float4* dst = reinterpret_cast<float4*>(qt + r * T + tx * 8);
+            dst[0] = make_float4(out[0], out[1], out[2], out[3]);
+            dst[1] = make_float4(out[4], out[5], out[6], out[7]);
+        }
     }
     float* const parts[1] = {p.part};
     __syncthreads();   // Gram smem is reused by the epilogue
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(NTHREADS) k_final_tiles(Inst p, const int2* __
 // writes alpha; block partials {max |r_i|, sum alpha_i - 1/2 alpha_i (Q alpha)_i, #SV}.
 __global__ void __launch_bounds__(256) k_final_nodes(Inst p, const float* __restrict__ mu,
                                                      float* __restrict__ alpha, double* __restrict__ blockbuf,
-                                                     float sv_threshold)
+                                                     float sv_threshold, float* __restrict__ r_out)
 {
     const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
     const int x = blockIdx.x * 32 + lane, n = p.n, Nt = p.Nt;
@@ -300,7 +302,8 @@ __global__ void __launch_bounds__(256) k_final_nodes(Inst p, const float* __rest
             const float af = fminf(fmaxf(mu[x], 0.f), p.C);
             const double al = af;
             alpha[x] = af;
-            const double r = (double)p.b[x] - qd * m - a0;
+            const double r = 1.0 - qd * m - a0;   // residual of the SVM system Q mu = 1
+            if (r_out) r_out[x] = (float)r;
             absr = fabs(r);
             if (!(absr <= DBL_MAX)) absr = INFINITY;
             const double qa = qd * al + a1;
@@ -427,20 +430,17 @@ void launch_stage(const void* X, int x_f64, int n, int m, const float* y, float*
     k_stage<<<(n + 255) / 256, 256, 0, s>>>(X, x_f64, n, m, y, Xf, sq, b, ctrl);
 }
 
-void launch_form_q(const Inst& p, const int2* work, long long ntiles, int q_bf16, cudaStream_t s)
+void launch_form_q(const Inst& p, const int2* work, long long ntiles, int store_f32, cudaStream_t s)
 {
-    (void)q_bf16;
-    k_form_q<<<(unsigned)ntiles, NTHREADS, 0, s>>>(p, work);
+    k_form_q<<<(unsigned)ntiles, NTHREADS, 0, s>>>(p, work, store_f32);
 }
 
-void launch_final(const Inst& p, const int2* work, long long ntiles, int buf, float* alpha,
-                  double* out3, double* blockbuf, int nblockbuf, float sv_threshold, cudaStream_t s)
+void launch_final(const Inst& p, const int2* work, long long ntiles, const float* mu, float* alpha,
+                  double* out3, double* blockbuf, float sv_threshold, float* r_out, cudaStream_t s)
 {
-    const float* mu = p.agg + (size_t)(buf & 1) * 3 * p.npad + 2 * (size_t)p.npad;
     k_final_tiles<<<(unsigned)ntiles, NTHREADS, 0, s>>>(p, work, mu);
     const int nb = (p.n + 31) / 32;
-    (void)nblockbuf;
-    k_final_nodes<<<nb, 256, 0, s>>>(p, mu, alpha, blockbuf, sv_threshold);
+    k_final_nodes<<<nb, 256, 0, s>>>(p, mu, alpha, blockbuf, sv_threshold, r_out);
     k_final_reduce<<<1, 256, 0, s>>>(blockbuf, nb, out3);
 }
 

@@ -24,6 +24,7 @@
 // and meet in shared memory, and each node's per-tile sums go to its own slot
 // (common.cuh), so the reduction order is fixed and the result reproducible.
 #include "common.cuh"
+#include "ptx.cuh"
 
 #include <float.h>
 
@@ -31,86 +32,8 @@ namespace gabp {
 
 namespace {
 
-// ---- mbarrier / bulk-copy helpers (inline PTX, sm_90+ forms) ---------------
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // bounded waits: 2 s
-
-__device__ __forceinline__ uint32_t smem_u32(const void* ptr)
-{
-    return (uint32_t)__cvta_generic_to_shared(ptr);
-}
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(unsigned long long* bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Waits for the phase of `parity` to complete; false after limit_ns.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity,
-                                          unsigned long long limit_ns = kWaitLimitNs)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > limit_ns) return false;
-    return true;
-}
-
-__device__ __forceinline__ uint64_t l2_evict_first_policy()
-{
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-
-// Bulk copy global -> shared (16-byte aligned addresses, size a multiple of
-// 16) completing on `bar` with a transaction count of `bytes`.
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, unsigned long long* bar,
-                                          uint64_t pol)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
-            "r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
-        : "memory");
-}
-
 __device__ __forceinline__ void consumer_bar() { asm volatile("bar.sync 1, %0;" ::"n"(NTHREADS) : "memory"); }
 
-__device__ __forceinline__ void record_error(Ctrl* c, int code, long long where)
-{
-    if (atomicCAS(&c->status, 0, code) == 0) c->bad_index = where;
-}
 
 // ---- pair sweep -----------------------------------------------------------
 // Persistent CTAs (two per SM) walk the tile list with stride gridDim.x.  A
@@ -153,6 +76,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, SWEEP_CTAS_PER_SM)
     if (*(volatile const int*)&ctrl->done) return;
     const int t = *(volatile const int*)&ctrl->t;
     const bool zero = (t == 0);   // Step 1: all messages 0, nothing to read
+    const bool zero_h = *(volatile const int*)&ctrl->zero_h != 0;
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -259,9 +183,9 @@ __global__ void __launch_bounds__(SWEEP_THREADS, SWEEP_CTAS_PER_SM)
         float4* st = p.state + (size_t)L * TT;
         const int nch = (rows + RC - 1) / RC;
         for (int ch = 0; ch < nch; ++ch) {
-            if (!abort && !mbar_wait(&sm.full[stage], phase)) {
+            if (!abort && !mbar_wait_warp(&sm.full[stage], phase)) {
                 abort = true;
-                record_error(ctrl, ST_ETIMEOUT, L);
+                if (lane == 0) record_error(ctrl, ST_ETIMEOUT, L);
             }
             const int r = ch * RC + warp;
             if (!abort && r < rows) {
@@ -273,7 +197,8 @@ __global__ void __launch_bounds__(SWEEP_THREADS, SWEEP_CTAS_PER_SM)
                     const int c = lane + 32 * k;
                     if (c < cols && (!diag || c > r)) {
                         const float q = to_f(S.q[warp][c]);
-                        const float4 s = zero ? make_float4(0.f, 0.f, 0.f, 0.f) : S.s[warp][c];  // {P_ij, P_ji, H_ij, H_ji}
+                        float4 s = zero ? make_float4(0.f, 0.f, 0.f, 0.f) : S.s[warp][c];  // {P_ij, P_ji, H_ij, H_ji}
+                        if (zero_h) { s.z = 0.f; s.w = 0.f; }
                         const float di = rP - s.y;      // Ptilde_i - P_ji
                         const float dj = cP[k] - s.x;   // Ptilde_j - P_ij
                         bad |= !(di > 0.f && di <= FLT_MAX && dj > 0.f && dj <= FLT_MAX);
@@ -445,10 +370,56 @@ __global__ void __launch_bounds__(256) k_finalize(Inst p)
             ctrl->kstar = t + 1;
         }
         ctrl->t = t + 1;
+        ctrl->zero_h = 0;
         ctrl->rmax_bits = 0ull;
         ctrl->blocks_done = 0u;
         __threadfence();
     }
+}
+
+__global__ void k_reset(Inst p)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        Ctrl* c = p.ctrl;
+        c->t = 0;
+        c->zero_h = 0;
+        c->done = 1;
+        c->kstar = 0;
+        c->converged = 0;
+        c->rmax_bits = 0ull;
+        c->blocks_done = 0u;
+    }
+    if (x >= p.n) return;
+    const float qd = p.qdiag[x];
+    const_cast<float*>(p.b)[x] = 1.f;
+    p.agg[x] = qd;
+    p.agg[p.npad + x] = 1.f;
+    p.agg[2 * p.npad + x] = 1.f / qd;
+}
+
+// Correction system Q d = r with the current P messages: b := r, the H
+// messages restart from 0, so htilde = b and mutilde = b / Ptilde.
+__global__ void k_refine_rhs(Inst p, const float* __restrict__ r)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    Ctrl* c = p.ctrl;
+    const int t = *(volatile int*)&c->t;
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->zero_h = 1;
+    if (x >= p.n) return;
+    float* cur = p.agg + (size_t)(t & 1) * 3 * p.npad;
+    const float bx = r[x];
+    const_cast<float*>(p.b)[x] = bx;
+    cur[p.npad + x] = bx;
+    cur[2 * p.npad + x] = bx / cur[x];
+}
+
+__global__ void k_axpy_mu(Inst p, int buf, float* __restrict__ acc, int first)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= p.n) return;
+    const float m = p.agg[(size_t)(buf & 1) * 3 * p.npad + 2 * (size_t)p.npad + x];
+    acc[x] = first ? m : acc[x] + m;
 }
 
 // Failure-detection self test: one thread waits, with the same bounded wait
@@ -527,6 +498,18 @@ __global__ void k_get_pairs(Inst p, const long long* __restrict__ ij, long long 
 void launch_init(const Inst& p, int diag_rule, float delta, cudaStream_t s)
 {
     k_init<<<(p.n + 255) / 256, 256, 0, s>>>(p, diag_rule, delta);
+}
+
+void launch_reset(const Inst& p, cudaStream_t s) { k_reset<<<(p.n + 255) / 256, 256, 0, s>>>(p); }
+
+void launch_refine_rhs(const Inst& p, const float* r, cudaStream_t s)
+{
+    k_refine_rhs<<<(p.n + 255) / 256, 256, 0, s>>>(p, r);
+}
+
+void launch_axpy_mu(const Inst& p, int buf, float* acc, int first, cudaStream_t s)
+{
+    k_axpy_mu<<<(p.n + 255) / 256, 256, 0, s>>>(p, buf, acc, first);
 }
 
 void launch_begin(const Inst& p, int iters, double tol, cudaStream_t s)

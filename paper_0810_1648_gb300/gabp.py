@@ -59,7 +59,7 @@ class Stats(ctypes.Structure):
                 ("n_support", ctypes.c_int64), ("lambda_", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("C", ctypes.c_double), ("diag_delta", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("q_mode", ctypes.c_int32),
-                ("diag_rule", ctypes.c_int32)]
+                ("diag_rule", ctypes.c_int32), ("refine_passes", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -1,0 +1,93 @@
+"""Precision form: BF16 tensor-core Gram (tcgen05) and Q stored in BF16, with
+defect-correction refinement on the FP32 Gram residual.
+
+* Q entries against the oracle fed the same BF16-rounded features: the GPU's
+  FP32-accumulated BF16 Gram, rounded to BF16 for storage, is within one BF16
+  rounding (2^-8 relative) of the exact entry; the weighted diagonal comes
+  from the accurate (unrounded) matrix.
+* an unrefined BF16 solve against the oracle run on the same BF16 matrix.
+* a refined solve against the oracle's fixed point of the exact FP64 matrix
+  (FP64 Cholesky), at the FP32 bars: |dalpha|_inf <= 1e-4 C, relative mean
+  error <= 2e-5, identical support vectors.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0810_1648_gb300 import gabp, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16(a):
+    """Round to the nearest BF16 (ties to even), returned as float64."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u >> 16) & 1) + 0x7FFF
+    return ((u + r) & 0xFFFF0000).astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_0810_1648_gb300 import build as gbuild
+    gbuild.build()
+
+
+def _bf16_matrix(p):
+    """The matrix the BF16 sweeps see: off-diagonal from BF16 features, rounded
+    to BF16; diagonal from the exact matrix of the FP32 features."""
+    X = p.X.astype(np.float64)
+    y = p.y.astype(np.float64)
+    Qx = oracle.build_q(X, y, p.gamma, p.C)
+    Qb = bf16(oracle.build_q(bf16(p.X), y, p.gamma, p.C))
+    Qb[np.diag_indices(p.n)] = np.diag(Qx)
+    return Qx, Qb
+
+
+@pytest.mark.parametrize("n,m", [(129, 7), (300, 64), (520, 100)])
+def test_bf16_q_formation(n, m):
+    p = workloads.mixture(n, m, seed=40 + n, C=1.0)
+    s = gabp.GabpSVM(p.X, p.y, p.gamma, p.C, q_mode=gabp.Q_BF16)
+    Qg = gabp.svm_get_q(s.h, n).astype(np.float64)
+    Qx, Qb = _bf16_matrix(p)
+    off = ~np.eye(n, dtype=bool)
+    exact_bf = oracle.build_q(bf16(p.X), p.y.astype(np.float64), p.gamma, p.C)
+    err = np.abs(Qg - exact_bf)[off]
+    assert np.all(err <= 2.0 ** -8 * np.abs(exact_bf[off]) + 1e-6 * np.max(np.abs(exact_bf))), err.max()
+    np.testing.assert_allclose(np.diag(Qg), np.diag(Qx), rtol=1e-5)
+    # most entries round identically
+    assert np.mean(Qg[off] == Qb[off]) > 0.95
+
+
+@pytest.mark.parametrize("n,m", [(300, 64), (1000, 10)])
+def test_bf16_solve_matches_oracle_on_bf16_matrix(n, m):
+    p = workloads.mixture(n, m, seed=50 + n, C=1.0)
+    s = gabp.GabpSVM(p.X, p.y, p.gamma, p.C, q_mode=gabp.Q_BF16)
+    alpha, rinf, k = s.solve(12, 0.0)
+    mu = s.mean().astype(np.float64)
+    _, Qb = _bf16_matrix(p)
+    Qg = gabp.svm_get_q(s.h, n).astype(np.float64)
+    r = oracle.gabp(Qg, np.ones(n), iters=12)      # oracle on the GPU's stored BF16 matrix
+    rel = np.max(np.abs(mu - r.mu)) / np.max(np.abs(r.mu))
+    assert rel <= 2e-5, rel
+    r2 = oracle.gabp(Qb, np.ones(n), iters=12)     # and on the independently rounded matrix
+    assert np.max(np.abs(mu - r2.mu)) / np.max(np.abs(r2.mu)) <= 2e-3
+
+
+@pytest.mark.parametrize("n,m,C", [(300, 64, 1.0), (1000, 10, 1.0), (777, 33, 10.0)])
+def test_refined_solve_reaches_fp64_fixed_point(n, m, C):
+    p = workloads.mixture(n, m, seed=60 + n, C=C)
+    s = gabp.GabpSVM(p.X, p.y, p.gamma, p.C, q_mode=gabp.Q_BF16, refine=8)
+    alpha, rinf, k = s.solve(200, 1e-6)
+    st = s.stats()
+    mu = s.mean().astype(np.float64)
+    Qx = oracle.build_q(p.X.astype(np.float64), p.y.astype(np.float64), p.gamma, p.C)
+    ref = np.linalg.solve(Qx, np.ones(n))
+    rel = np.max(np.abs(mu - ref)) / np.max(np.abs(ref))
+    assert rel <= 2e-5, (rel, st)
+    a_ref = np.clip(ref, 0, p.C)
+    assert np.max(np.abs(alpha.astype(np.float64) - a_ref)) <= 1e-4 * p.C
+    clear = np.abs(ref) > 1e-5 * np.max(np.abs(ref))
+    assert np.array_equal((alpha > 0)[clear], (a_ref > 0)[clear])
+    assert st["refine_passes"] >= 1 and rinf < 1e-6
+    # the FP64 residual of the GPU answer, by the oracle, agrees
+    assert np.max(np.abs(1.0 - Qx @ mu)) < 2e-6
