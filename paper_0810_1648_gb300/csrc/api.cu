@@ -333,8 +333,8 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     if (!(o.diag_delta > 0) || !std::isfinite(o.diag_delta)) return fail(GABP_EINVAL, "diag_delta must be > 0");
     if (o.bias_mode == 1 && (!(o.bias_lambda >= 0) || !std::isfinite(o.bias_lambda)))
         return fail(GABP_EINVAL, "bias_lambda must be finite and >= 0");
-    if (o.q_mode != GABP_Q_F32 && o.q_mode != GABP_Q_BF16)
-        return fail(GABP_EINVAL, "q_mode %d is not available in this build", o.q_mode);
+    if (o.q_mode != GABP_Q_F32 && o.q_mode != GABP_Q_BF16 && o.q_mode != GABP_Q_RECOMPUTE)
+        return fail(GABP_EINVAL, "unknown q_mode %d", o.q_mode);
     if (o.refine < 0 || o.refine > 64) return fail(GABP_EINVAL, "refine must be in [0, 64]");
 
     int dev = 0, ndev = 0;
@@ -373,6 +373,7 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
         h->own_stream = true;
     }
     e = prepare_sweep();
+    if (e == cudaSuccess && o.q_mode == GABP_Q_RECOMPUTE) e = prepare_sweep_rc();
     if (e != cudaSuccess) { destroy_all(h); return fail(GABP_ECUDA, "sweep kernel setup: %s", cudaGetErrorString(e)); }
     e = cudaMalloc(&h->pool, pl.total);
     if (e != cudaSuccess) { destroy_all(h); return fail(GABP_ENOMEM, "cudaMalloc(%zu): %s", pl.total, cudaGetErrorString(e)); }

@@ -29,6 +29,8 @@ constexpr int T = 128;                 // pair tile edge
 constexpr int TT = T * T;
 constexpr int NTHREADS = 256;          // threads per tile CTA
 constexpr int NWARPS = NTHREADS / 32;
+constexpr int KCH = 64;                   // features per BF16 operand block
+constexpr int BLK_BYTES = T * KCH * 2;    // one 128 x 64 BF16 operand block (16 KB)
 
 enum Status : int {
     ST_OK = 0, ST_EINVAL = 1, ST_ENOMEM = 2, ST_ECUDA = 3, ST_ENUMERIC = 4,
@@ -112,6 +114,8 @@ void launch_init(const Inst& p, int diag_rule, float delta, cudaStream_t s);
 void launch_begin(const Inst& p, int iters, double tol, cudaStream_t s);
 // Raises the dynamic shared-memory limit of the pair-sweep kernels (once per device).
 cudaError_t prepare_sweep();
+// Fused-recompute form: also raises the shared-memory limit of its sweep kernel.
+cudaError_t prepare_sweep_rc();
 // One synchronous round: pair sweep then per-node finalize.  When ev is not
 // null, ev[0] is recorded before and ev[1] after the pair sweep.
 void launch_round(const Inst& p, const int2* work, long long ntiles, int q_mode, cudaStream_t s,

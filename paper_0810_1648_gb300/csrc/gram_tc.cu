@@ -28,8 +28,6 @@ namespace gabp {
 
 namespace {
 
-constexpr int KCH = 64;                       // features per operand chunk
-constexpr int BLK_BYTES = T * KCH * 2;        // 16 KB per 128 x 64 BF16 block
 constexpr int XSTAGES = 4;
 constexpr int TC_THREADS = 6 * 32;
 constexpr uint32_t TMEM_COLS = 256;

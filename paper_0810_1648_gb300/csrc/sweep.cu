@@ -27,6 +27,7 @@
 #include "ptx.cuh"
 
 #include <float.h>
+#include <type_traits>
 
 namespace gabp {
 
@@ -36,24 +37,28 @@ __device__ __forceinline__ void consumer_bar() { asm volatile("bar.sync 1, %0;" 
 
 
 // ---- pair sweep -----------------------------------------------------------
-// Persistent CTAs (two per SM) walk the tile list with stride gridDim.x.  A
-// producer warp streams every tile as chunks of RC rows (messages and Q) into
-// a STAGES-deep shared-memory ring with bulk copies, running ahead across
-// tile boundaries; eight consumer warps take one row of each chunk, update
-// its pairs from shared memory and store the new messages straight to
+// Persistent CTAs walk the tile list with stride gridDim.x.  A producer warp
+// streams every tile as chunks of RC rows of messages (and, when Q is stored,
+// of Q) into a STAGES-deep shared-memory ring with bulk copies, running ahead
+// across tile boundaries; eight consumer warps take one row of each chunk,
+// update its pairs from shared memory and store the new messages straight to
 // global memory with 128-bit streaming stores.  Only the pairs the tile owns
 // are copied: whole chunks for interior tiles, the c > r part of each row on
 // diagonal tiles, the first `cols` columns on the last tile column.
+//
+// Two kernels share the producer and consumer code:
+//   k_sweep<QT>   Q stored (FP32 or BF16) and streamed with the messages;
+//   k_sweep_rc    Q recomputed in every sweep: a second producer streams the
+//                 BF16 feature blocks of the tile, one thread issues tcgen05
+//                 MMAs into a double-buffered TMEM accumulator, four warps
+//                 turn the Gram rows into BF16 Q values in a double-buffered
+//                 shared-memory Q tile, which the consumers read in place of
+//                 a stored tile (bitwise the same values as the BF16 store).
 constexpr int RC = NWARPS;                    // rows per chunk, one per consumer warp
 constexpr int STAGES = 4;
 constexpr int SWEEP_THREADS = NTHREADS + 32;  // + one producer warp
 constexpr int SWEEP_CTAS_PER_SM = 2;
-
-template <typename QT>
-struct SweepStage {
-    float4 s[RC][T];
-    QT q[RC][T];
-};
+constexpr size_t STATE_CHUNK = (size_t)RC * T * sizeof(float4);   // 16 KB
 
 struct SweepTail {
     unsigned long long full[STAGES], empty[STAGES];
@@ -62,93 +67,88 @@ struct SweepTail {
     float rp[T], rh[T], rr[T];
 };
 
+// Ring stage = messages of RC rows, then (stored Q) the Q values of those rows.
 template <typename QT>
-constexpr size_t sweep_smem_bytes()
+struct QBytes { static constexpr size_t v = sizeof(QT); };
+template <>
+struct QBytes<void> { static constexpr size_t v = 0; };
+
+template <typename QT>
+__host__ __device__ constexpr size_t stage_bytes() { return STATE_CHUNK + (size_t)RC * T * QBytes<QT>::v; }
+
+template <typename QT>
+__host__ __device__ constexpr size_t sweep_smem_bytes() { return 128 + STAGES * stage_bytes<QT>() + sizeof(SweepTail); }
+
+// Producer (one thread).  QT = void: messages only.
+template <typename QT, size_t SB>
+__device__ __forceinline__ void sweep_producer(const Inst& p, const int2* __restrict__ work, long long ntiles,
+                                               SweepTail& sm, unsigned char* ring, bool zero,
+                                               volatile int* abort_flag)
 {
-    return 128 + STAGES * sizeof(SweepStage<QT>) + sizeof(SweepTail);
+    constexpr size_t QB = QBytes<QT>::v;
+    const uint64_t pol = l2_evict_first_policy();
+    const int n = p.n;
+    int stage = 0;
+    uint32_t phase = 0;
+    for (long long L = blockIdx.x; L < ntiles; L += gridDim.x) {
+        const int2 tile = work[L];
+        const int I = tile.x, J = tile.y;
+        const int rows = min(T, n - I * T), cols = min(T, n - J * T);
+        const bool diag = (I == J);
+        const float4* st = p.state + (size_t)L * TT;
+        const unsigned char* qt = QB ? static_cast<const unsigned char*>(p.qstore) + (size_t)L * TT * QB : nullptr;
+        const int nch = (rows + RC - 1) / RC;
+        for (int c = 0; c < nch; ++c) {
+            if ((abort_flag && *abort_flag) || !mbar_wait(&sm.empty[stage], phase ^ 1u)) {
+                record_error(p.ctrl, ST_ETIMEOUT, L);
+                if (abort_flag) *abort_flag = 1;
+                return;
+            }
+            unsigned char* S = ring + (size_t)stage * SB;
+            unsigned long long* bar = &sm.full[stage];
+            const int r0 = c * RC, nr = min(RC, rows - r0);
+            if (!diag && cols == T) {
+                const uint32_t bq = (uint32_t)(nr * T * QB);
+                const uint32_t bs = zero ? 0u : (uint32_t)(nr * T * sizeof(float4));
+                mbar_arrive_expect_tx(bar, bq + bs);
+                if (QB) bulk_load(S + STATE_CHUNK, qt + (size_t)r0 * T * QB, bq, bar, pol);
+                if (!zero) bulk_load(S, st + (size_t)r0 * T, bs, bar, pol);
+            } else {
+                // per row: columns [c0, c1) with c0, c1 multiples of 8 (16-byte
+                // granules of both arrays) covering the pairs the row owns
+                const int c1 = min(T, (cols + 7) & ~7);
+                uint32_t bytes = 0;
+                for (int k = 0; k < nr; ++k) {
+                    const int r = r0 + k, c0 = diag ? ((r + 1) & ~7) : 0;
+                    if (c0 < c1 && (!diag || r + 1 < cols))
+                        bytes += (uint32_t)((c1 - c0) * (QB + (zero ? 0 : sizeof(float4))));
+                }
+                mbar_arrive_expect_tx(bar, bytes);
+                for (int k = 0; k < nr; ++k) {
+                    const int r = r0 + k, c0 = diag ? ((r + 1) & ~7) : 0;
+                    if (!(c0 < c1 && (!diag || r + 1 < cols))) continue;
+                    if (QB)
+                        bulk_load(S + STATE_CHUNK + ((size_t)k * T + c0) * QB, qt + ((size_t)r * T + c0) * QB,
+                                  (uint32_t)((c1 - c0) * QB), bar, pol);
+                    if (!zero)
+                        bulk_load(S + ((size_t)k * T + c0) * sizeof(float4), st + (size_t)r * T + c0,
+                                  (uint32_t)((c1 - c0) * sizeof(float4)), bar, pol);
+                }
+            }
+            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        }
+    }
 }
 
-template <typename QT>
-__global__ void __launch_bounds__(SWEEP_THREADS, SWEEP_CTAS_PER_SM)
-    k_sweep(Inst p, const int2* __restrict__ work, long long ntiles)
+// Consumers (256 threads, ctid = 0..255, consumer warp cw = ctid / 32).
+// QSrc supplies q for a pair and the per-tile hand-shake of a recomputed Q tile.
+template <size_t SB, class QSrc>
+__device__ __forceinline__ void sweep_consumers(const Inst& p, const int2* __restrict__ work, long long ntiles,
+                                                SweepTail& sm, const unsigned char* ring, int ctid, int t,
+                                                bool zero, bool zero_h, QSrc& qsrc)
 {
+    const int cw = ctid >> 5, lane = ctid & 31, n = p.n;
     Ctrl* ctrl = p.ctrl;
-    if (*(volatile const int*)&ctrl->done) return;
-    const int t = *(volatile const int*)&ctrl->t;
-    const bool zero = (t == 0);   // Step 1: all messages 0, nothing to read
-    const bool zero_h = *(volatile const int*)&ctrl->zero_h != 0;
-
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* base = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
-    SweepStage<QT>* stages = reinterpret_cast<SweepStage<QT>*>(base);
-    SweepTail& sm = *reinterpret_cast<SweepTail*>(base + STAGES * sizeof(SweepStage<QT>));
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, n = p.n;
-
-    if (tid == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&sm.full[s], 1);
-            mbar_init(&sm.empty[s], NWARPS);
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-
-    if (warp == NWARPS) {
-        // ------------------------------------------------------ producer
-        if (lane != 0) return;
-        const uint64_t pol = l2_evict_first_policy();
-        int stage = 0;
-        uint32_t phase = 0;
-        for (long long L = blockIdx.x; L < ntiles; L += gridDim.x) {
-            const int2 tile = work[L];
-            const int I = tile.x, J = tile.y;
-            const int rows = min(T, n - I * T), cols = min(T, n - J * T);
-            const bool diag = (I == J);
-            const float4* st = p.state + (size_t)L * TT;
-            const QT* qt = static_cast<const QT*>(p.qstore) + (size_t)L * TT;
-            const int nch = (rows + RC - 1) / RC;
-            for (int c = 0; c < nch; ++c) {
-                if (!mbar_wait(&sm.empty[stage], phase ^ 1u)) {
-                    record_error(ctrl, ST_ETIMEOUT, L);
-                    return;
-                }
-                SweepStage<QT>& S = stages[stage];
-                unsigned long long* bar = &sm.full[stage];
-                const int r0 = c * RC, nr = min(RC, rows - r0);
-                if (!diag && cols == T) {
-                    const uint32_t bq = (uint32_t)(nr * T * sizeof(QT));
-                    const uint32_t bs = zero ? 0u : (uint32_t)(nr * T * sizeof(float4));
-                    mbar_arrive_expect_tx(bar, bq + bs);
-                    bulk_load(&S.q[0][0], qt + (size_t)r0 * T, bq, bar, pol);
-                    if (!zero) bulk_load(&S.s[0][0], st + (size_t)r0 * T, bs, bar, pol);
-                } else {
-                    // per row: columns [c0, c1) with c0, c1 multiples of 8 (16-byte
-                    // granules of both arrays) covering the pairs the row owns
-                    const int c1 = min(T, (cols + 7) & ~7);
-                    uint32_t bytes = 0;
-                    for (int k = 0; k < nr; ++k) {
-                        const int r = r0 + k, c0 = diag ? ((r + 1) & ~7) : 0;
-                        if (c0 < c1 && (!diag || r + 1 < cols))
-                            bytes += (uint32_t)((c1 - c0) * (sizeof(QT) + (zero ? 0 : sizeof(float4))));
-                    }
-                    mbar_arrive_expect_tx(bar, bytes);
-                    for (int k = 0; k < nr; ++k) {
-                        const int r = r0 + k, c0 = diag ? ((r + 1) & ~7) : 0;
-                        if (!(c0 < c1 && (!diag || r + 1 < cols))) continue;
-                        bulk_load(&S.q[k][c0], qt + (size_t)r * T + c0, (uint32_t)((c1 - c0) * sizeof(QT)), bar, pol);
-                        if (!zero)
-                            bulk_load(&S.s[k][c0], st + (size_t)r * T + c0, (uint32_t)((c1 - c0) * sizeof(float4)),
-                                      bar, pol);
-                    }
-                }
-                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
-            }
-        }
-        return;
-    }
-
-    // ---------------------------------------------------------- consumers
     const float* agg = p.agg + (size_t)(t & 1) * 3 * p.npad;
     float* partP = p.part;
     float* partH = partP + (size_t)p.Nt * n;
@@ -156,21 +156,26 @@ __global__ void __launch_bounds__(SWEEP_THREADS, SWEEP_CTAS_PER_SM)
     int stage = 0;
     uint32_t phase = 0;
     bool bad = false, abort = false;
-    for (long long L = blockIdx.x; L < ntiles; L += gridDim.x) {
+    int it = 0;
+    for (long long L = blockIdx.x; L < ntiles; L += gridDim.x, ++it) {
         const int2 tile = work[L];
         const int I = tile.x, J = tile.y;
         const int rows = min(T, n - I * T), cols = min(T, n - J * T);
         const bool diag = (I == J);
         {
-            const int rc = tid < T ? tid : tid - T;
-            const int x = (tid < T ? I : J) * T + rc;
+            const int rc = ctid < T ? ctid : ctid - T;
+            const int x = (ctid < T ? I : J) * T + rc;
             const bool v = x < n;
-            float(*dst)[T] = tid < T ? sm.row : sm.col;
+            float(*dst)[T] = ctid < T ? sm.row : sm.col;
             dst[0][rc] = v ? agg[x] : 1.f;
             dst[1][rc] = v ? agg[p.npad + x] : 0.f;
             dst[2][rc] = v ? agg[2 * p.npad + x] : 0.f;
         }
         consumer_bar();
+        if (!abort && !qsrc.tile_begin(it, lane)) {
+            abort = true;
+            if (lane == 0) record_error(ctrl, ST_ETIMEOUT, L);
+        }
         float cP[4], cH[4], cM[4], aP[4], aH[4], aR[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -187,17 +192,18 @@ __global__ void __launch_bounds__(SWEEP_THREADS, SWEEP_CTAS_PER_SM)
                 abort = true;
                 if (lane == 0) record_error(ctrl, ST_ETIMEOUT, L);
             }
-            const int r = ch * RC + warp;
+            const int r = ch * RC + cw;
             if (!abort && r < rows) {
-                const SweepStage<QT>& S = stages[stage];
+                const unsigned char* S = ring + (size_t)stage * SB;
+                const float4* Ss = reinterpret_cast<const float4*>(S) + (size_t)cw * T;
                 const float rP = sm.row[0][r], rH = sm.row[1][r], rM = sm.row[2][r];
                 float sp = 0.f, sh = 0.f, sr = 0.f;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int c = lane + 32 * k;
                     if (c < cols && (!diag || c > r)) {
-                        const float q = to_f(S.q[warp][c]);
-                        float4 s = zero ? make_float4(0.f, 0.f, 0.f, 0.f) : S.s[warp][c];  // {P_ij, P_ji, H_ij, H_ji}
+                        const float q = qsrc.q(S, cw, r, c, it);
+                        float4 s = zero ? make_float4(0.f, 0.f, 0.f, 0.f) : Ss[c];  // {P_ij, P_ji, H_ij, H_ji}
                         if (zero_h) { s.z = 0.f; s.w = 0.f; }
                         const float di = rP - s.y;      // Ptilde_i - P_ji
                         const float dj = cP[k] - s.x;   // Ptilde_j - P_ij
@@ -229,26 +235,28 @@ __global__ void __launch_bounds__(SWEEP_THREADS, SWEEP_CTAS_PER_SM)
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int c = lane + 32 * k;
-            sm.cp[warp][c] = aP[k];
-            sm.ch[warp][c] = aH[k];
-            sm.cr[warp][c] = aR[k];
+            sm.cp[cw][c] = aP[k];
+            sm.ch[cw][c] = aH[k];
+            sm.cr[cw][c] = aR[k];
         }
+        __syncwarp();
+        qsrc.tile_end(it, lane);
         consumer_bar();
         if (diag) {
-            if (tid < rows) {
-                float P = sm.rp[tid], H = sm.rh[tid], R = sm.rr[tid];
+            if (ctid < rows) {
+                float P = sm.rp[ctid], H = sm.rh[ctid], R = sm.rr[ctid];
 #pragma unroll
-                for (int w = 0; w < NWARPS; ++w) { P += sm.cp[w][tid]; H += sm.ch[w][tid]; R += sm.cr[w][tid]; }
-                const size_t o = (size_t)I * n + I * T + tid;
+                for (int w = 0; w < NWARPS; ++w) { P += sm.cp[w][ctid]; H += sm.ch[w][ctid]; R += sm.cr[w][ctid]; }
+                const size_t o = (size_t)I * n + I * T + ctid;
                 partP[o] = P; partH[o] = H; partR[o] = R;
             }
-        } else if (tid < T) {
-            if (tid < rows) {
-                const size_t o = (size_t)J * n + I * T + tid;
-                partP[o] = sm.rp[tid]; partH[o] = sm.rh[tid]; partR[o] = sm.rr[tid];
+        } else if (ctid < T) {
+            if (ctid < rows) {
+                const size_t o = (size_t)J * n + I * T + ctid;
+                partP[o] = sm.rp[ctid]; partH[o] = sm.rh[ctid]; partR[o] = sm.rr[ctid];
             }
         } else {
-            const int c = tid - T;
+            const int c = ctid - T;
             if (c < cols) {
                 float P = 0.f, H = 0.f, R = 0.f;
 #pragma unroll
@@ -259,6 +267,256 @@ __global__ void __launch_bounds__(SWEEP_THREADS, SWEEP_CTAS_PER_SM)
         }
     }
     if (bad) record_error(ctrl, ST_ENUMERIC, -1);
+}
+
+// Q streamed with the messages: it sits after the messages in each ring stage.
+template <typename QT>
+struct StoredQ {
+    __device__ __forceinline__ bool tile_begin(int, int) { return true; }
+    __device__ __forceinline__ void tile_end(int, int) {}
+    __device__ __forceinline__ float q(const unsigned char* S, int cw, int, int c, int) const
+    {
+        return to_f(reinterpret_cast<const QT*>(S + STATE_CHUNK)[(size_t)cw * T + c]);
+    }
+};
+
+__device__ __forceinline__ unsigned char* align_smem(unsigned char* raw, uintptr_t a)
+{
+    return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + a - 1) & ~(a - 1));
+}
+
+template <typename QT>
+__global__ void __launch_bounds__(SWEEP_THREADS, SWEEP_CTAS_PER_SM)
+    k_sweep(Inst p, const int2* __restrict__ work, long long ntiles)
+{
+    Ctrl* ctrl = p.ctrl;
+    if (*(volatile const int*)&ctrl->done) return;
+    const int t = *(volatile const int*)&ctrl->t;
+    const bool zero = (t == 0);   // Step 1: all messages 0, nothing to read
+    const bool zero_h = *(volatile const int*)&ctrl->zero_h != 0;
+    constexpr size_t SB = stage_bytes<QT>();
+
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* ring = align_smem(smem_raw, 128);
+    SweepTail& sm = *reinterpret_cast<SweepTail*>(ring + STAGES * SB);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&sm.full[s], 1);
+            mbar_init(&sm.empty[s], NWARPS);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == NWARPS) {
+        if (lane == 0) sweep_producer<QT, SB>(p, work, ntiles, sm, ring, zero, nullptr);
+        return;
+    }
+    StoredQ<QT> qsrc;
+    sweep_consumers<SB>(p, work, ntiles, sm, ring, tid, t, zero, zero_h, qsrc);
+}
+
+// ---- fused recompute ------------------------------------------------------
+constexpr int RC_XSTAGES = 2;
+constexpr int RC_THREADS = 15 * 32;     // 3 role warps + 4 epilogue + 8 consumers
+constexpr uint32_t RC_TMEM_COLS = 256;
+constexpr size_t RC_QTILE = (size_t)TT * sizeof(__nv_bfloat16);   // 32 KB
+
+struct RcExtra {
+    unsigned long long xfull[RC_XSTAGES], xempty[RC_XSTAGES];
+    unsigned long long accfull[2], accempty[2];
+    unsigned long long qfull[2], qempty[2];
+    unsigned long long drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
+__host__ __device__ constexpr size_t rc_smem_bytes()
+{
+    return 1024 + STAGES * STATE_CHUNK + RC_XSTAGES * 2 * BLK_BYTES + 2 * RC_QTILE + sizeof(SweepTail) +
+           sizeof(RcExtra);
+}
+
+// Q from the shared-memory tile written by the epilogue warps.
+struct RecomputedQ {
+    const __nv_bfloat16* qtile;   // [2][T][T]
+    RcExtra* ex;
+    __device__ __forceinline__ bool tile_begin(int it, int)
+    {
+        return mbar_wait_warp(&ex->qfull[it & 1], (uint32_t)((it >> 1) & 1));
+    }
+    __device__ __forceinline__ void tile_end(int it, int lane)
+    {
+        if (lane == 0) mbar_arrive(&ex->qempty[it & 1]);
+    }
+    __device__ __forceinline__ float q(const unsigned char*, int, int r, int c, int it) const
+    {
+        return __bfloat162float(qtile[(size_t)(it & 1) * TT + (size_t)r * T + c]);
+    }
+};
+
+__global__ void __launch_bounds__(RC_THREADS, 1) k_sweep_rc(Inst p, const int2* __restrict__ work, long long ntiles)
+{
+    Ctrl* ctrl = p.ctrl;
+    if (*(volatile const int*)&ctrl->done) return;
+    const int t = *(volatile const int*)&ctrl->t;
+    const bool zero = (t == 0);
+    const bool zero_h = *(volatile const int*)&ctrl->zero_h != 0;
+
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* ring = align_smem(smem_raw, 1024);
+    unsigned char* xops = ring + STAGES * STATE_CHUNK;                       // [2][A, B]
+    __nv_bfloat16* qtile = reinterpret_cast<__nv_bfloat16*>(xops + RC_XSTAGES * 2 * BLK_BYTES);
+    SweepTail& sm = *reinterpret_cast<SweepTail*>(reinterpret_cast<unsigned char*>(qtile) + 2 * RC_QTILE);
+    RcExtra& ex = *reinterpret_cast<RcExtra*>(reinterpret_cast<unsigned char*>(&sm) + sizeof(SweepTail));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, n = p.n;
+    const int nkc = p.nkc;
+
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&sm.full[s], 1);
+            mbar_init(&sm.empty[s], NWARPS);
+        }
+        for (int s = 0; s < RC_XSTAGES; ++s) { mbar_init(&ex.xfull[s], 1); mbar_init(&ex.xempty[s], 1); }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&ex.accfull[b], 1);
+            mbar_init(&ex.accempty[b], 4);
+            mbar_init(&ex.qfull[b], 4);
+            mbar_init(&ex.qempty[b], NWARPS);
+        }
+        mbar_init(&ex.drain, 1);
+        ex.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) tmem_alloc(&ex.tmem_base, RC_TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = ex.tmem_base;
+    volatile int* abort_flag = &ex.abort;
+
+    if (warp == 0) {
+        if (lane == 0) sweep_producer<void, STATE_CHUNK>(p, work, ntiles, sm, ring, zero, abort_flag);
+    } else if (warp == 1) {
+        // feature blocks of each tile
+        if (lane == 0) {
+            const uint64_t pol = l2_evict_first_policy();
+            const unsigned char* Xp = static_cast<const unsigned char*>(p.Xp);
+            int xs = 0;
+            uint32_t ph = 0;
+            bool run = true;
+            for (long long L = blockIdx.x; L < ntiles && run; L += gridDim.x) {
+                const int I = work[L].x, J = work[L].y;
+                for (int kc = 0; kc < nkc; ++kc) {
+                    if (*abort_flag || !mbar_wait(&ex.xempty[xs], ph ^ 1u)) {
+                        *abort_flag = 1;
+                        record_error(ctrl, ST_ETIMEOUT, L);
+                        run = false;
+                        break;
+                    }
+                    unsigned char* A = xops + (size_t)xs * 2 * BLK_BYTES;
+                    mbar_arrive_expect_tx(&ex.xfull[xs], 2 * BLK_BYTES);
+                    bulk_load(A, Xp + ((size_t)I * nkc + kc) * BLK_BYTES, BLK_BYTES, &ex.xfull[xs], pol);
+                    bulk_load(A + BLK_BYTES, Xp + ((size_t)J * nkc + kc) * BLK_BYTES, BLK_BYTES, &ex.xfull[xs], pol);
+                    if (++xs == RC_XSTAGES) { xs = 0; ph ^= 1u; }
+                }
+            }
+        }
+    } else if (warp == 2) {
+        // MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t IDESC = idesc_bf16_f32(T, T);
+            int xs = 0, acc = 0;
+            uint32_t ph = 0, aph = 0;
+            for (long long L = blockIdx.x; L < ntiles; L += gridDim.x) {
+                if (*abort_flag || !mbar_wait(&ex.accempty[acc], aph ^ 1u)) {
+                    *abort_flag = 1;
+                    record_error(ctrl, ST_ETIMEOUT, L);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tbase + (uint32_t)acc * T;
+                bool ok = true;
+                for (int kc = 0; kc < nkc; ++kc) {
+                    if (*abort_flag || !mbar_wait(&ex.xfull[xs], ph)) {
+                        *abort_flag = 1;
+                        record_error(ctrl, ST_ETIMEOUT, L);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const unsigned char* A = xops + (size_t)xs * 2 * BLK_BYTES;
+#pragma unroll
+                    for (int s = 0; s < KCH / 16; ++s) {
+                        const uint64_t ad = smem_desc(A + s * 256, 128, 1024);
+                        const uint64_t bd = smem_desc(A + BLK_BYTES + s * 256, 128, 1024);
+                        tc_mma_bf16(d, ad, bd, IDESC, (kc | s) != 0);
+                    }
+                    tc_commit(&ex.xempty[xs]);
+                    if (++xs == RC_XSTAGES) { xs = 0; ph ^= 1u; }
+                }
+                if (!ok) break;
+                tc_commit(&ex.accfull[acc]);
+                if (++acc == 2) { acc = 0; aph ^= 1u; }
+            }
+            tc_commit(&ex.drain);
+            if (!mbar_wait(&ex.drain, 0u)) record_error(ctrl, ST_ETIMEOUT, -2);
+        }
+    } else if (warp < 7) {
+        // epilogue: TMEM rows -> BF16 Q tile in shared memory
+        const int g = warp & 3, r = 32 * g + lane;
+        int it = 0;
+        for (long long L = blockIdx.x; L < ntiles; L += gridDim.x, ++it) {
+            const int acc = it & 1;
+            const uint32_t par = (uint32_t)((it >> 1) & 1);
+            const bool stop = __shfl_sync(0xffffffffu, *abort_flag, 0) != 0;
+            if (stop || !mbar_wait_warp(&ex.accfull[acc], par) || !mbar_wait_warp(&ex.qempty[acc], par ^ 1u)) {
+                if (lane == 0) {
+                    *abort_flag = 1;
+                    record_error(ctrl, ST_ETIMEOUT, L);
+                }
+                break;
+            }
+            tc_fence_after();
+            const int I = work[L].x, J = work[L].y, i = I * T + r;
+            const float yi = i < n ? p.y[i] : 0.f, si = i < n ? p.sqb[i] : 0.f;
+            __nv_bfloat16* qrow = qtile + (size_t)acc * TT + (size_t)r * T;
+#pragma unroll 1
+            for (int cc = 0; cc < T / 32; ++cc) {
+                float v[32];
+                tmem_ld32(tbase + (uint32_t)acc * T + ((uint32_t)(32 * g) << 16) + (uint32_t)(32 * cc), v);
+                __align__(16) __nv_bfloat16 out[32];
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const int col = 32 * cc + c, j = J * T + col;
+                    const bool valid = i < n && j < n && (I != J || col > r);
+                    const float yj = j < n ? p.y[j] : 0.f, sj = j < n ? p.sqb[j] : 0.f;
+                    const float d2 = fmaxf(0.f, si + sj - 2.f * v[c]);
+                    const float q = yi * yj * (expf(-p.gamma * d2) + p.lam2);
+                    out[c] = __float2bfloat16_rn(valid ? q : 0.f);
+                }
+                uint4* dst = reinterpret_cast<uint4*>(qrow + 32 * cc);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) dst[u] = reinterpret_cast<const uint4*>(out)[u];
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&ex.accempty[acc]);
+                mbar_arrive(&ex.qfull[acc]);
+            }
+        }
+    } else {
+        RecomputedQ qsrc{qtile, &ex};
+        sweep_consumers<STATE_CHUNK>(p, work, ntiles, sm, ring, tid - 7 * 32, t, zero, zero_h, qsrc);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 2) {
+        tc_fence_after();
+        tmem_dealloc(tbase, RC_TMEM_COLS);
+    }
 }
 
 // Compensated FP32 accumulation (Knuth's TwoSum): s + c carries the running
@@ -530,6 +788,11 @@ int sweep_grid(long long ntiles)
     return (int)(ntiles < g ? ntiles : g);
 }
 
+cudaError_t prepare_sweep_rc()
+{
+    return cudaFuncSetAttribute(k_sweep_rc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rc_smem_bytes());
+}
+
 cudaError_t prepare_sweep()
 {
     cudaError_t e = cudaFuncSetAttribute(k_sweep<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -544,7 +807,11 @@ void launch_round(const Inst& p, const int2* work, long long ntiles, int q_mode,
 {
     const int grid = sweep_grid(ntiles);
     if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
-    if (q_mode == 1)
+    if (q_mode == 2) {
+        const int grid_rc = (grid + SWEEP_CTAS_PER_SM - 1) / SWEEP_CTAS_PER_SM;   // one CTA per SM
+        k_sweep_rc<<<grid_rc, RC_THREADS, rc_smem_bytes(), s>>>(p, work, ntiles);
+    }
+    else if (q_mode == 1)
         k_sweep<__nv_bfloat16><<<grid, SWEEP_THREADS, sweep_smem_bytes<__nv_bfloat16>(), s>>>(p, work, ntiles);
     else
         k_sweep<float><<<grid, SWEEP_THREADS, sweep_smem_bytes<float>(), s>>>(p, work, ntiles);

@@ -91,3 +91,29 @@ def test_refined_solve_reaches_fp64_fixed_point(n, m, C):
     assert st["refine_passes"] >= 1 and rinf < 1e-6
     # the FP64 residual of the GPU answer, by the oracle, agrees
     assert np.max(np.abs(1.0 - Qx @ mu)) < 2e-6
+
+
+@pytest.mark.parametrize("n,m", [(129, 7), (300, 64), (700, 100)])
+def test_recompute_equals_bf16_store(n, m):
+    """Recomputing the BF16 Q tiles inside every sweep gives exactly the
+    values the BF16 store holds, so both forms agree bitwise."""
+    p = workloads.mixture(n, m, seed=70 + n, C=1.0)
+    a_store, _, _ = gabp.GabpSVM(p.X, p.y, p.gamma, p.C, q_mode=gabp.Q_BF16).solve(9, 0.0)
+    s_rc = gabp.GabpSVM(p.X, p.y, p.gamma, p.C, q_mode=gabp.Q_RECOMPUTE)
+    a_rc, _, k = s_rc.solve(9, 0.0)
+    assert k == 9
+    np.testing.assert_array_equal(a_store, a_rc)
+    with pytest.raises(gabp.GabpError):
+        gabp.svm_get_q(s_rc.h, n)
+
+
+def test_refined_recompute_reaches_fp64_fixed_point():
+    p = workloads.mixture(900, 64, seed=81, C=1.0)
+    s = gabp.GabpSVM(p.X, p.y, p.gamma, p.C, q_mode=gabp.Q_RECOMPUTE, refine=8)
+    alpha, rinf, k = s.solve(200, 1e-6)
+    mu = s.mean().astype(np.float64)
+    Qx = oracle.build_q(p.X.astype(np.float64), p.y.astype(np.float64), p.gamma, p.C)
+    ref = np.linalg.solve(Qx, np.ones(p.n))
+    assert np.max(np.abs(mu - ref)) / np.max(np.abs(ref)) <= 2e-5
+    assert np.max(np.abs(alpha.astype(np.float64) - np.clip(ref, 0, p.C))) <= 1e-4 * p.C
+    assert rinf < 1e-6
