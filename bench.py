@@ -44,10 +44,16 @@ WORKLOAD = {
     "n": 20000, "m": 128, "sweeps_per_step": ROUNDS, "q_mode": "f32",
     "l2": "no flush: every sweep streams 3.3 GB of messages + 0.8 GB of Q, far above the 129 MB L2",
 }
-# Algorithmic bytes per unordered pair of one pair-sweep launch (FP32 Q):
-# read 16 B of messages + 4 B of Q, write 16 B; the first round reads no messages.
-BYTES_PER_PAIR = 36
-BYTES_PER_PAIR_ROUND0 = 20
+PRECISION_WORKLOAD = {
+    "workload": "precision form, n=100000, m=64 FP32 3-component mixture (seed 2), RBF gamma=0.5/64, C=1, "
+                "100 synchronous sweeps per solve, Q as selected by q_mode",
+    "n": 100000, "m": 64, "sweeps_per_step": ROUNDS,
+    "l2": "no flush: every sweep streams 80 GB of messages, far above the 129 MB L2",
+}
+# Algorithmic bytes per unordered pair of one pair-sweep launch: read 16 B of
+# messages + the stored Q entry, write 16 B; the first round reads no messages.
+Q_BYTES = {"f32": 4, "bf16": 2, "recompute": 0}
+Q_MODES = {"f32": 0, "bf16": 1, "recompute": 2}
 
 
 def _dist():
@@ -236,14 +242,20 @@ def run_ours(args):
         gbuild.build()
     gabp.load()
 
-    p = workloads.mixture(20000, 128, seed=1 + rank, gamma=1.0 / 128, C=10.0)
+    if args.workload == "precision_large":
+        p = workloads.mixture(100000, 64, seed=2 + rank, gamma=0.5 / 64, C=1.0)
+        wl = dict(PRECISION_WORKLOAD, q_mode=args.q_mode)
+    else:
+        p = workloads.mixture(20000, 128, seed=1 + rank, gamma=1.0 / 128, C=10.0)
+        wl = dict(WORKLOAD, q_mode=args.q_mode)
+    qb = Q_BYTES[args.q_mode]
     n = p.n
     stream = torch.cuda.Stream(device=dev)
     Xd = torch.from_numpy(p.X).to(dev)
     yd = torch.from_numpy(p.y).to(dev)
     alpha_d = torch.empty(n, dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
-    opts = gabp.opts_default(stream=stream.cuda_stream, chunk=ROUNDS)
+    opts = gabp.opts_default(stream=stream.cuda_stream, chunk=ROUNDS, q_mode=Q_MODES[args.q_mode])
     h = gabp.svm_create(Xd, yd, p.gamma, p.C, opts)
     gabp.svm_set_profiling(h, True)
 
@@ -285,7 +297,7 @@ def run_ours(args):
     pairs = n * (n - 1) // 2
     nz = prof["sweep_launches_zero_state"]
     nl = prof["sweep_launches"]
-    alg_bytes = pairs * (BYTES_PER_PAIR * (nl - nz) + BYTES_PER_PAIR_ROUND0 * nz)
+    alg_bytes = pairs * ((32 + qb) * (nl - nz) + (16 + qb) * nz)
     sweep_s = prof["sweep_ms"] / 1e3
     achieved = alg_bytes / sweep_s / 1e9 if sweep_s > 0 else None
     peaks = _peaks()
@@ -296,17 +308,52 @@ def run_ours(args):
     traffic = _traffic_from_profile(os.path.join(ROOT, "paper_0810_1648_gb300", "csrc", "sweep.cu"))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-            "kernel": "k_sweep<float> (pair sweep)", "peak_source": peak_src,
+            "kernel": {"f32": "k_sweep<float>", "bf16": "k_sweep<bf16>", "recompute": "k_sweep_rc"}[args.q_mode]
+                      + " (pair sweep)", "peak_source": peak_src,
+            "bytes_per_pair": 32 + qb,
             "algorithmic_bytes_per_launch": alg_bytes / max(nl, 1),
             "avg_launch_ms": prof["sweep_ms"] / max(nl, 1), "launches_timed": nl,
             "share_of_step": (prof["sweep_ms"] / ms) if ms > 0 else None}
 
-    # end to end through the C ABI with pinned host buffers
+    gabp.svm_destroy(h)
+    e2e = None
+    if not args.no_e2e:
+        e2e = _e2e(args, p, stream, dev, ws, gabp, torch)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = (_cpu_baseline(p, args.cpu_sweeps) if args.workload == "plain_large" else
+               {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
+                "sample": "skipped: the FP64 oracle of n=100000 needs 240 GB of host memory"})
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.q_mode == "f32" else "bf16+f32",
+                "data": "synthetic", "config": dict(wl, parallelism=f"replicas{ws}"),
+                "edge_updates_per_s": value * n * (n - 1),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clk,
+                "result": {"residual_inf": st["residual_inf"], "dual_objective": st["dual_objective"],
+                           "n_support": st["n_support"]}}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _e2e(args, p, stream, dev, ws, gabp, torch):
+    """Same solve through the C ABI from pinned host buffers: H2D of X and y and
+    D2H of alpha inside the timed region."""
+    n = p.n
     Xh = torch.from_numpy(p.X).pin_memory()
     yh = torch.from_numpy(p.y).pin_memory()
     ah = torch.empty(n, dtype=torch.float32).pin_memory()
-    opts2 = gabp.opts_default(stream=stream.cuda_stream, chunk=ROUNDS)
+    opts2 = gabp.opts_default(stream=stream.cuda_stream, chunk=ROUNDS, q_mode=Q_MODES[args.q_mode])
     h2 = gabp.svm_create(Xh, yh, p.gamma, p.C, opts2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
 
     def step_e2e():
         gabp.svm_refit(h2, Xh, yh, p.gamma, p.C)
@@ -327,28 +374,8 @@ def run_ours(args):
         torch.distributed.all_reduce(ms2, op=torch.distributed.ReduceOp.MAX)
     e2e_value = ws * ROUNDS * args.steps / (float(ms2.item()) / 1e3)
     gabp.svm_destroy(h2)
-    gabp.svm_destroy(h)
-
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = _cpu_baseline(p, args.cpu_sweeps)
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": dict(WORKLOAD, parallelism=f"replicas{ws}"),
-                "edge_updates_per_s": value * n * (n - 1),
-                "roofline": roof, "cpu_baseline": cpu,
-                "e2e": {"value": e2e_value, "unit": UNIT,
-                        "h2d_bytes_per_step": int(p.X.nbytes + p.y.nbytes),
-                        "d2h_bytes_per_step": int(4 * n)},
-                "gpu_launches": int(launches), "clocks": clk,
-                "result": {"residual_inf": st["residual_inf"], "dual_objective": st["dual_objective"],
-                           "n_support": st["n_support"]}}
-        print(json.dumps(line), flush=True)
-    if ws > 1:
-        torch.distributed.destroy_process_group()
-    return 0
+    return {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(p.X.nbytes + p.y.nbytes),
+            "d2h_bytes_per_step": int(4 * n)}
 
 
 def main():
@@ -360,9 +387,14 @@ def main():
     ap.add_argument("--cpu-sweeps", type=int, default=2)
     ap.add_argument("--ref-sweeps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="plain_large", choices=["plain_large", "precision_large"])
+    ap.add_argument("--q-mode", default=None, choices=list(Q_MODES))
     ap.add_argument("--profile-small", action="store_true",
                     help="one 3-round solve at n=6144 (for ncu captures), no JSON bench line")
     args = ap.parse_args()
+    if args.q_mode is None:
+        args.q_mode = "f32" if args.workload == "plain_large" else "bf16"
     if args.profile_small:
         return run_profile_small(args)
     if args.impl == "reference":
