@@ -182,6 +182,69 @@ GABP_API gabp_status gabp_svm_get_pairs(gabp_svm_t h, const int64_t* i, const in
                                float* out);
 GABP_API gabp_status gabp_svm_get_aggregates(gabp_svm_t h, float* Pt, float* ht, float* mu);
 
+/* ------------------------------------------------------------------------
+ * Batched and served forms.  Many instances of uneven size are swept
+ * together: every synchronous round is one persistent launch over the tiles
+ * of all live instances, and each instance keeps its own round count,
+ * limit, tolerance and stop test (Algorithm 2, Step 3, per instance).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    const void* X;        /* n x m features (dtype and pointer mode from the options) */
+    const float* y;       /* n labels +-1 */
+    int64_t n, m;
+    double gamma, C;
+} gabp_problem;
+
+typedef struct {
+    float*  alpha;          /* caller buffer for n weights (host or device per ptr_mode), may be NULL */
+    double  residual_inf;   /* ||1 - Q mu||_inf of the answer, FP32-Gram Q, FP64 sums */
+    double  dual_objective;
+    int64_t n_support;
+    int32_t iters_done;     /* synchronous rounds run (refinement passes included) */
+    int32_t converged;      /* residual_inf < tol */
+    int32_t status;         /* gabp_status of this problem */
+    int32_t refine_passes;
+} gabp_result;
+
+/*
+ * Solves `count` independent problems together.  opts (may be NULL) applies
+ * to all: q_mode (BF16 store / recompute run the tensor-core Gram), refine
+ * (precision forms: defect-correction passes until residual_inf < tol),
+ * ptr_mode / x_dtype / stream.  opts->chunk = 0 lets the solver choose the
+ * schedule (persistent sweep CTAs per SM, rounds per convergence check) by
+ * timing candidates on this set; results are cached per shape signature.
+ * results[k].alpha must point to the caller's buffer (or NULL).  Returns
+ * GABP_OK, or the status of the first problem that failed (each result
+ * carries its own status).
+ */
+GABP_API gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gabp_svm_opts* opts,
+                                      int32_t iters, double tol, gabp_result* results);
+
+/*
+ * Continuous-batching server.  Requests queue in arrival order; each
+ * gabp_server_step() admits queued requests while free slots and the device
+ * memory budget allow (their Q is formed on a side stream while the other
+ * instances keep sweeping), runs one chunk of rounds over every live
+ * instance, and retires the instances that stopped (their alpha is copied to
+ * the caller's buffer).  The problem's X and y must stay valid until its
+ * ticket completes.
+ */
+typedef struct gabp_server_s* gabp_server_t;
+typedef struct {
+    int64_t hbm_budget_bytes;  /* device memory for instances; 0 = 80% of free memory */
+    int32_t max_members;       /* concurrent instances; 0 = 64 */
+    int32_t iters;             /* round limit per request */
+    double  tol;               /* residual tolerance per request */
+    gabp_svm_opts opts;        /* q_mode, refine, diag rule, pointer mode, stream, chunk (0 = 8) */
+} gabp_server_cfg;
+
+GABP_API gabp_status gabp_server_create(const gabp_server_cfg* cfg, gabp_server_t* out);
+GABP_API gabp_status gabp_server_submit(gabp_server_t s, const gabp_problem* p, float* alpha_out, int64_t* ticket);
+GABP_API gabp_status gabp_server_step(gabp_server_t s, int32_t* active, int32_t* queued, int32_t* completed);
+/* done = 1 once the ticket finished; then *res holds its result. */
+GABP_API gabp_status gabp_server_poll(gabp_server_t s, int64_t ticket, gabp_result* res, int32_t* done);
+GABP_API gabp_status gabp_server_destroy(gabp_server_t s);
+
 /*
  * Instrumentation.  With profiling on, every pair-sweep kernel of a solve is
  * bracketed by CUDA events recorded on the handle's stream (inside the

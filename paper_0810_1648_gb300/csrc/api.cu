@@ -62,7 +62,11 @@ struct gabp_svm_s {
     void* pool = nullptr;
     size_t pool_bytes = 0;
     Inst inst{};
-    int2* work = nullptr;
+    Inst* d_tab = nullptr;          // device copy of inst (a one-instance batch)
+    int4* work = nullptr;           // tile list {0, I, J, L}
+    int2* nbl = nullptr;            // node blocks {0, b}
+    Sched* sched = nullptr;
+    RoundGrid grid{};
     float* alpha = nullptr;
     double* final3 = nullptr;
     double* blockbuf = nullptr;
@@ -93,7 +97,7 @@ gabp_status check_handle(gabp_svm_t h)
 
 // Device memory plan of one handle (bytes, 256-aligned sub-buffers).
 struct Plan {
-    size_t X, vec, agg, part, state, q, work, ctrl, rhist, final3, blockbuf, xp, total;
+    size_t X, vec, agg, part, state, q, work, ctrl, rhist, final3, blockbuf, xp, tab, nbl, total;
 };
 
 Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_mode)
@@ -108,13 +112,15 @@ Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_m
     p.q = q_mode == GABP_Q_F32 ? align_up((size_t)ntiles * TT * sizeof(float), 256)
         : q_mode == GABP_Q_BF16 ? align_up((size_t)ntiles * TT * sizeof(__nv_bfloat16), 256)
         : 0;
-    p.work = align_up((size_t)ntiles * sizeof(int2), 256);
+    p.work = align_up((size_t)ntiles * sizeof(int4), 256);
+    p.tab = align_up(sizeof(Inst) + sizeof(Sched), 256);
+    p.nbl = align_up((size_t)((n + 31) / 32) * sizeof(int2), 256);
     p.ctrl = align_up(sizeof(Ctrl), 256);
     p.rhist = align_up((size_t)kRhistCap * sizeof(double), 256);
     p.final3 = 256;
     p.blockbuf = align_up((size_t)3 * ((n + 31) / 32) * sizeof(double), 256);
     p.total = p.X + 9 * p.vec + p.agg + p.part + p.state + p.q + p.work + p.ctrl + p.rhist +
-              p.final3 + p.blockbuf + p.xp + 1024;
+              p.final3 + p.blockbuf + p.xp + p.tab + p.nbl + 1024;
     return p;
 }
 
@@ -143,6 +149,7 @@ gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
     h->mean_src = nullptr;
 
     CK(cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), s));
+    CK(cudaMemcpyAsync(h->d_tab, &p, sizeof(Inst), cudaMemcpyHostToDevice, s));
     // labels -> device copy (validated by the staging kernel, which also sets b = 1)
     CK(cudaMemcpyAsync((void*)p.y, y, (size_t)n * sizeof(float),
                        dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
@@ -168,7 +175,7 @@ gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
         return fail(GABP_EINVAL, "row %lld: non-finite feature or label not +-1",
                     (long long)h->hctrl->bad_index);
     if (h->opts.q_mode == GABP_Q_F32) {
-        launch_form_q(p, h->work, h->ntiles, 1, s);
+        launch_form_q(h->d_tab, h->work, h->ntiles, 1, s);
         CK(cudaGetLastError());
         launch_init(p, h->opts.diag_rule, (float)h->delta, s);
         h->prof.kernel_launches += 2;
@@ -178,13 +185,13 @@ gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
         // (the accurate matrix); the off-diagonal entries come from the BF16
         // tensor-core Gram.
         CK(launch_pack_bf16(p.X, (int)n, (int)m, p.nkc, h->Nt, (void*)p.Xp, (float*)p.sqb, s));
-        launch_form_q(p, h->work, h->ntiles, 0, s);
+        launch_form_q(h->d_tab, h->work, h->ntiles, 0, s);
         CK(cudaGetLastError());
         launch_init(p, h->opts.diag_rule, (float)h->delta, s);
         CK(cudaGetLastError());
         h->prof.kernel_launches += 4;
         if (h->opts.q_mode == GABP_Q_BF16) {
-            CK(launch_form_q_tc(p, h->work, h->ntiles, p.Xp, p.nkc, p.sqb, s));
+            CK(launch_form_q_tc(h->d_tab, h->work, h->ntiles, s));
             h->prof.kernel_launches += 1;
         }
     }
@@ -219,7 +226,7 @@ gabp_status get_graph(gabp_svm_t h, int rounds, gabp_svm_s::Graph** out)
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < rounds; ++k)
-        launch_round(h->inst, h->work, h->ntiles, h->opts.q_mode, h->stream,
+        launch_round(h->d_tab, h->work, h->nbl, h->sched, h->grid, h->opts.q_mode, h->stream,
                      h->profiling ? &G.ev[(size_t)2 * k] : nullptr);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (e != cudaSuccess) return fail(GABP_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
@@ -238,7 +245,7 @@ gabp_status run_rounds(gabp_svm_t h, int iters, double tol, Ctrl* out)
 {
     cudaStream_t s = h->stream;
     Inst& p = h->inst;
-    launch_begin(p, iters, tol, s);
+    launch_begin(h->d_tab, 1, iters, tol, s);
     h->prof.kernel_launches += 1;
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->hctrl, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
@@ -405,7 +412,13 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     p.part = (float*)take(pl.part);
     p.state = (float4*)take(pl.state);
     p.qstore = pl.q ? take(pl.q) : nullptr;
-    h->work = (int2*)take(pl.work);
+    h->work = (int4*)take(pl.work);
+    {
+        char* tb = (char*)take(pl.tab);
+        h->d_tab = (Inst*)tb;
+        h->sched = (Sched*)(tb + align_up(sizeof(Inst), 16));
+    }
+    h->nbl = (int2*)take(pl.nbl);
     p.ctrl = (Ctrl*)take(pl.ctrl);
     p.rhist = (double*)take(pl.rhist);
     p.rhist_cap = kRhistCap;
@@ -418,11 +431,19 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     }
 
     // Tile work list: the upper triangle, row by row; L(I,J) = I*Nt - I(I-1)/2 + (J-I).
-    std::vector<int2> wl((size_t)h->ntiles);
+    std::vector<int4> wl((size_t)h->ntiles);
     size_t k = 0;
     for (int I = 0; I < h->Nt; ++I)
-        for (int J = I; J < h->Nt; ++J) wl[k++] = make_int2(I, J);
-    e = cudaMemcpyAsync(h->work, wl.data(), wl.size() * sizeof(int2), cudaMemcpyHostToDevice, h->stream);
+        for (int J = I; J < h->Nt; ++J, ++k) wl[k] = make_int4(0, I, J, (int)k);
+    const int nblk = (int)((n + 31) / 32);
+    std::vector<int2> nb((size_t)nblk);
+    for (int b = 0; b < nblk; ++b) nb[(size_t)b] = make_int2(0, b);
+    Sched sc{h->ntiles, nblk, 1};
+    h->grid = round_grid(h->ntiles, nblk, o.q_mode, 0);
+    e = cudaMemcpyAsync(h->work, wl.data(), wl.size() * sizeof(int4), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->nbl, nb.data(), nb.size() * sizeof(int2), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->sched, &sc, sizeof sc, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) { destroy_all(h); return fail(GABP_ECUDA, "work list copy: %s", cudaGetErrorString(e)); }
 
     gabp_status st = stage_and_form(h, X, y);

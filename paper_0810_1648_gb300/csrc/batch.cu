@@ -1,0 +1,776 @@
+// Batched and served forms: many GaBP SVM instances of uneven size swept
+// together, one persistent launch per synchronous round for all of them.
+//
+// An Engine owns a device table of instances (Inst), their control blocks in
+// one contiguous array (one copy reads every instance's progress), and the
+// combined tile list and node-block list of the live instances.  A round is
+// the same pair-sweep + finalize pair the single-instance solver uses; the
+// kernels look each tile's instance up in the table and skip instances that
+// have stopped, so a captured chunk of rounds stays valid while instances
+// finish, leave and join.  Each instance keeps its own round counter,
+// iteration limit, tolerance and stop decision (Algorithm 2, Step 3, per
+// instance).
+//
+// gabp_batch_solve runs a fixed set to completion; gabp_server_* admits
+// instances as they arrive, by device-memory budget, forms their Q on a side
+// stream while the others keep sweeping, and retires them as they converge
+// (continuous batching).  The schedule knobs (persistent sweep CTAs per SM,
+// rounds per convergence check) are chosen by measuring candidates on the
+// actual set; results are cached per shape signature.
+#include "common.cuh"
+#include "gabp_svm.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+namespace gabp {
+
+namespace {
+
+size_t aup(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Device memory of one instance (one allocation), carved like the handle's.
+struct MemberPlan {
+    size_t X, vec, agg, part, state, q, work, rhist, final3, blockbuf, xp, total;
+};
+
+MemberPlan member_plan(int64_t n, int64_t m, int q_mode)
+{
+    const int Nt = (int)((n + T - 1) / T);
+    const long long nt = tri_tiles(Nt);
+    const size_t npad = aup((size_t)n, 128);
+    MemberPlan p{};
+    p.X = aup((size_t)n * m * 4, 256);
+    p.vec = aup(npad * 4, 256);
+    p.agg = aup(6 * npad * 4, 256);
+    p.part = aup((size_t)4 * Nt * n * 4, 256);
+    p.state = aup((size_t)nt * TT * 16, 256);
+    p.q = q_mode == 0 ? aup((size_t)nt * TT * 4, 256) : q_mode == 1 ? aup((size_t)nt * TT * 2, 256) : 0;
+    p.work = aup((size_t)nt * sizeof(int4), 256);
+    p.rhist = 0;
+    p.final3 = 256;
+    p.blockbuf = aup((size_t)3 * ((n + 31) / 32) * 8, 256);
+    p.xp = q_mode != 0 ? aup(bf16_pack_bytes(Nt, (int)m), 1024) : 0;
+    p.total = p.X + 9 * p.vec + p.agg + p.part + p.state + p.q + p.work + p.final3 + p.blockbuf + p.xp + 2048;
+    return p;
+}
+
+struct Member {
+    bool used = false;
+    bool formed = false;     // Q formation finished (event)
+    bool active = false;     // in the round lists
+    bool finished = false;   // results available
+    Inst inst{};
+    void* mem = nullptr;
+    size_t bytes = 0;
+    int4* work = nullptr;    // own tile list {slot, I, J, L}
+    long long ntiles = 0;
+    int nblk = 0;
+    float* alpha = nullptr;
+    float* mu_acc = nullptr;
+    float* r32 = nullptr;
+    double* final3 = nullptr;
+    double* blockbuf = nullptr;
+    cudaEvent_t ready = nullptr;
+    // request bookkeeping
+    int iters = 0;
+    double tol = 0;
+    int refine_left = 0;
+    int refine_done = 0;
+    bool refining = false;
+    int t_first_stop = 0;
+    gabp_result res{};
+    float* out_alpha = nullptr;  // caller buffer
+    int out_dev = 0;
+    int64_t ticket = -1;
+};
+
+struct TuneKey {
+    int q_mode;
+    long long tiles_bucket;
+    int members_bucket;
+    bool operator<(const TuneKey& o) const
+    {
+        return std::tie(q_mode, tiles_bucket, members_bucket) < std::tie(o.q_mode, o.tiles_bucket, o.members_bucket);
+    }
+};
+struct TuneVal {
+    int ctas_per_sm;
+    int chunk;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
+
+}  // namespace
+
+// ---------------------------------------------------------------- Engine
+class Engine {
+  public:
+    std::string err;
+    gabp_status fail(gabp_status st, const std::string& m)
+    {
+        err = m;
+        set_last_error(m.c_str());
+        return st;
+    }
+#define EK(call)                                                                                    \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) return fail(GABP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+    int q_mode = 0, diag_rule = 0, x_f64 = 0, ptr_mode = 0;
+    double delta = 0.1, sv_threshold = 0.0;
+    int cap_members = 0;
+    long long cap_tiles = 0;
+    int cap_nblk = 0;
+    cudaStream_t stream = nullptr, side = nullptr;
+    bool own_stream = false;
+    Inst* d_tab = nullptr;
+    Ctrl* d_ctrl = nullptr;
+    int4* d_work = nullptr;
+    int2* d_nbl = nullptr;
+    Sched* d_sched = nullptr;
+    Ctrl* h_ctrl = nullptr;       // pinned mirror
+    std::vector<Member> mem;
+    RoundGrid grid{};
+    int ctas_per_sm = 0;
+    int chunk = 16;
+    std::map<int, cudaGraphExec_t> graphs;
+    long long live_tiles = 0;     // tiles in the current lists
+    bool lists_dirty = true;
+    size_t bytes_in_use = 0;
+    int64_t launches = 0;
+
+    ~Engine()
+    {
+        if (stream) cudaStreamSynchronize(stream);
+        if (side) cudaStreamSynchronize(side);
+        for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+        for (auto& m : mem) release(m);
+        if (stream) cudaStreamSynchronize(stream);
+        if (d_tab) cudaFree(d_tab);
+        if (h_ctrl) cudaFreeHost(h_ctrl);
+        if (side) cudaStreamDestroy(side);
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+
+    gabp_status init(int members, long long tiles, int nblk, const gabp_svm_opts& o)
+    {
+        q_mode = o.q_mode;
+        diag_rule = o.diag_rule;
+        delta = o.diag_delta > 0 ? o.diag_delta : 0.1;
+        x_f64 = o.x_dtype;
+        ptr_mode = o.ptr_mode;
+        sv_threshold = o.sv_threshold;
+        cap_members = members;
+        cap_tiles = std::max<long long>(tiles, 1);
+        cap_nblk = std::max(nblk, 1);
+        if (o.stream) {
+            stream = (cudaStream_t)o.stream;
+        } else {
+            EK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+            own_stream = true;
+        }
+        EK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+        {
+            // keep freed instance memory in the stream-ordered pool for reuse
+            int dev = 0;
+            cudaMemPool_t pool;
+            EK(cudaGetDevice(&dev));
+            EK(cudaDeviceGetDefaultMemPool(&pool, dev));
+            uint64_t keep = UINT64_MAX;
+            EK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        }
+        EK(prepare_sweep());
+        if (q_mode == 2) EK(prepare_sweep_rc());
+        const size_t b_tab = aup((size_t)cap_members * sizeof(Inst), 256);
+        const size_t b_ctrl = aup((size_t)cap_members * sizeof(Ctrl), 256);
+        const size_t b_work = aup((size_t)cap_tiles * sizeof(int4), 256);
+        const size_t b_nbl = aup((size_t)cap_nblk * sizeof(int2), 256);
+        char* base = nullptr;
+        EK(cudaMalloc((void**)&base, b_tab + b_ctrl + b_work + b_nbl + 256));
+        d_tab = (Inst*)base;
+        d_ctrl = (Ctrl*)(base + b_tab);
+        d_work = (int4*)(base + b_tab + b_ctrl);
+        d_nbl = (int2*)(base + b_tab + b_ctrl + b_work);
+        d_sched = (Sched*)(base + b_tab + b_ctrl + b_work + b_nbl);
+        EK(cudaMemsetAsync(d_ctrl, 0, b_ctrl, stream));
+        EK(cudaMemsetAsync(d_sched, 0, sizeof(Sched), stream));
+        EK(cudaMallocHost((void**)&h_ctrl, (size_t)cap_members * sizeof(Ctrl)));
+        mem.resize((size_t)cap_members);
+        set_grid(0);
+        EK(cudaStreamSynchronize(stream));
+        return GABP_OK;
+    }
+
+    void set_grid(int cps)
+    {
+        ctas_per_sm = cps;
+        grid = round_grid(cap_tiles, cap_nblk, q_mode, cps);
+    }
+
+    void release(Member& m)
+    {
+        if (m.mem) cudaFreeAsync(m.mem, stream);
+        if (m.ready) cudaEventDestroy(m.ready);
+        if (m.used) bytes_in_use -= m.bytes;
+        m = Member{};
+    }
+
+    int free_slot() const
+    {
+        for (int k = 0; k < cap_members; ++k)
+            if (!mem[(size_t)k].used) return k;
+        return -1;
+    }
+
+    // Allocates and forms one instance in `slot` on the side stream.
+    gabp_status add(int slot, const gabp_problem& pr, float* out_alpha, int out_dev)
+    {
+        Member& M = mem[(size_t)slot];
+        const int64_t n = pr.n, m = pr.m;
+        if (n < 2 || m < 1 || !pr.X || !pr.y) return fail(GABP_EINVAL, "problem needs n >= 2, m >= 1, X and y");
+        if (!(pr.gamma > 0) || !(pr.C > 0)) return fail(GABP_EINVAL, "problem needs gamma > 0 and C > 0");
+        const MemberPlan pl = member_plan(n, m, q_mode);
+        M = Member{};
+        M.used = true;
+        M.bytes = pl.total;
+        bytes_in_use += pl.total;
+        cudaStream_t s = side;
+        EK(cudaMallocAsync(&M.mem, pl.total, s));
+        char* b = static_cast<char*>(M.mem);
+        size_t off = 0;
+        auto take = [&](size_t bytes) { void* r = b + off; off += bytes; return r; };
+        Inst& p = M.inst;
+        p.n = (int)n;
+        p.Nt = (int)((n + T - 1) / T);
+        p.m = (int)m;
+        p.npad = (int)aup((size_t)n, 128);
+        p.X = (const float*)take(pl.X);
+        p.sq = (const float*)take(pl.vec);
+        p.y = (const float*)take(pl.vec);
+        p.b = (const float*)take(pl.vec);
+        p.qdiag = (float*)take(pl.vec);
+        M.alpha = (float*)take(pl.vec);
+        p.sqb = (const float*)take(pl.vec);
+        M.mu_acc = (float*)take(pl.vec);
+        M.r32 = (float*)take(pl.vec);
+        take(pl.vec);
+        p.agg = (float*)take(pl.agg);
+        p.part = (float*)take(pl.part);
+        p.state = (float4*)take(pl.state);
+        p.qstore = pl.q ? take(pl.q) : nullptr;
+        M.work = (int4*)take(pl.work);
+        M.final3 = (double*)take(pl.final3);
+        M.blockbuf = (double*)take(pl.blockbuf);
+        if (pl.xp) {
+            off = aup(off, 1024);
+            p.Xp = take(pl.xp);
+            p.nkc = bf16_chunks((int)m);
+        }
+        p.ctrl = d_ctrl + slot;
+        p.rhist = nullptr;
+        p.rhist_cap = 0;
+        const double lam = 1.0 / (double)n;
+        p.gamma = (float)pr.gamma;
+        p.lam2 = (float)(lam * lam);
+        p.C = (float)pr.C;
+        M.ntiles = tri_tiles(p.Nt);
+        M.nblk = (int)((n + 31) / 32);
+        M.out_alpha = out_alpha;
+        M.out_dev = out_dev;
+        M.res.status = GABP_OK;
+        M.res.alpha = out_alpha;
+        // tile list of the instance (inst field = its slot in the table)
+        std::vector<int4> wl((size_t)M.ntiles);
+        size_t k = 0;
+        for (int I = 0; I < p.Nt; ++I)
+            for (int J = I; J < p.Nt; ++J, ++k) wl[k] = make_int4(slot, I, J, (int)k);
+        EK(cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), s));
+        EK(cudaMemcpyAsync(d_tab + slot, &p, sizeof(Inst), cudaMemcpyHostToDevice, s));
+        EK(cudaMemcpyAsync(M.work, wl.data(), wl.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+        EK(cudaMemcpyAsync((void*)p.y, pr.y, (size_t)n * 4, ptr_mode ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        const void* src = pr.X;
+        void* tmp = nullptr;
+        if (!ptr_mode) {
+            if (x_f64) {
+                EK(cudaMallocAsync(&tmp, (size_t)n * m * 8, s));
+                EK(cudaMemcpyAsync(tmp, pr.X, (size_t)n * m * 8, cudaMemcpyHostToDevice, s));
+                src = tmp;
+            } else {
+                EK(cudaMemcpyAsync((void*)p.X, pr.X, (size_t)n * m * 4, cudaMemcpyHostToDevice, s));
+                src = p.X;
+            }
+        }
+        launch_stage(src, x_f64, (int)n, (int)m, p.y, (float*)p.X, (float*)p.sq, (float*)p.b, p.ctrl, s);
+        if (tmp) EK(cudaFreeAsync(tmp, s));
+        if (q_mode != 0) EK(launch_pack_bf16(p.X, (int)n, (int)m, p.nkc, p.Nt, (void*)p.Xp, (float*)p.sqb, s));
+        launch_form_q(d_tab, M.work, M.ntiles, q_mode == 0 ? 1 : 0, s);
+        launch_init(p, diag_rule, (float)delta, s);
+        if (q_mode == 1) EK(launch_form_q_tc(d_tab, M.work, M.ntiles, s));
+        launches += q_mode == 0 ? 3 : (q_mode == 1 ? 6 : 5);
+        EK(cudaGetLastError());
+        EK(cudaEventCreateWithFlags(&M.ready, cudaEventDisableTiming));
+        EK(cudaEventRecord(M.ready, s));
+        return GABP_OK;
+    }
+
+    // Arms a formed instance for `iters` rounds and puts it in the lists.
+    gabp_status activate(int slot, int iters, double tol)
+    {
+        Member& M = mem[(size_t)slot];
+        EK(cudaStreamWaitEvent(stream, M.ready, 0));
+        launch_begin(d_tab + slot, 1, iters, tol, stream);
+        ++launches;
+        M.formed = true;
+        M.active = true;
+        lists_dirty = true;
+        return GABP_OK;
+    }
+
+    gabp_status rebuild()
+    {
+        if (!lists_dirty) return GABP_OK;
+        std::vector<int4> wl;
+        std::vector<int2> nb;
+        for (int k = 0; k < cap_members; ++k) {
+            const Member& M = mem[(size_t)k];
+            if (!M.used || !M.active) continue;
+            const int Nt = M.inst.Nt;
+            long long L = 0;
+            for (int I = 0; I < Nt; ++I)
+                for (int J = I; J < Nt; ++J, ++L) wl.push_back(make_int4(k, I, J, (int)L));
+            for (int b = 0; b < M.nblk; ++b) nb.push_back(make_int2(k, b));
+        }
+        if ((long long)wl.size() > cap_tiles || (int)nb.size() > cap_nblk)
+            return fail(GABP_ENOMEM, "batch lists exceed their capacity");
+        Sched sc{(long long)wl.size(), (int)nb.size(), cap_members};
+        if (!wl.empty()) EK(cudaMemcpyAsync(d_work, wl.data(), wl.size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
+        if (!nb.empty()) EK(cudaMemcpyAsync(d_nbl, nb.data(), nb.size() * sizeof(int2), cudaMemcpyHostToDevice, stream));
+        EK(cudaMemcpyAsync(d_sched, &sc, sizeof sc, cudaMemcpyHostToDevice, stream));
+        EK(cudaStreamSynchronize(stream));   // host vectors go out of scope
+        live_tiles = (long long)wl.size();
+        lists_dirty = false;
+        return GABP_OK;
+    }
+
+    gabp_status graph_for(int rounds, cudaGraphExec_t* out)
+    {
+        const int key = rounds * 16 + ctas_per_sm;
+        auto it = graphs.find(key);
+        if (it != graphs.end()) { *out = it->second; return GABP_OK; }
+        cudaGraph_t g = nullptr;
+        EK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        for (int k = 0; k < rounds; ++k) launch_round(d_tab, d_work, d_nbl, d_sched, grid, q_mode, stream);
+        EK(cudaStreamEndCapture(stream, &g));
+        cudaGraphExec_t ex = nullptr;
+        cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        EK(e);
+        graphs[key] = ex;
+        *out = ex;
+        return GABP_OK;
+    }
+
+    // One captured chunk of rounds over the live lists, then reads every control block.
+    gabp_status run_chunk(int rounds)
+    {
+        if (gabp_status st = rebuild()) return st;
+        if (live_tiles > 0) {
+            cudaGraphExec_t g = nullptr;
+            if (gabp_status st = graph_for(rounds, &g)) return st;
+            EK(cudaGraphLaunch(g, stream));
+            launches += 2LL * rounds;
+        }
+        EK(cudaMemcpyAsync(h_ctrl, d_ctrl, (size_t)cap_members * sizeof(Ctrl), cudaMemcpyDeviceToHost, stream));
+        EK(cudaStreamSynchronize(stream));
+        return GABP_OK;
+    }
+
+    // Final residual / objective / alpha of a stopped instance; copies alpha out.
+    gabp_status finish(int slot)
+    {
+        Member& M = mem[(size_t)slot];
+        const Ctrl& c = h_ctrl[slot];
+        const float* mu = M.refining
+                              ? M.mu_acc
+                              : M.inst.agg + (size_t)(c.kstar & 1) * 3 * M.inst.npad + 2 * (size_t)M.inst.npad;
+        launch_final(M.inst, M.work, M.ntiles, mu, M.alpha, M.final3, M.blockbuf, (float)sv_threshold, nullptr,
+                     stream);
+        launches += 3;
+        double f3[3];
+        EK(cudaMemcpyAsync(f3, M.final3, sizeof f3, cudaMemcpyDeviceToHost, stream));
+        if (M.out_alpha)
+            EK(cudaMemcpyAsync(M.out_alpha, M.alpha, (size_t)M.inst.n * 4,
+                               M.out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream));
+        EK(cudaStreamSynchronize(stream));
+        M.res.residual_inf = f3[0];
+        M.res.dual_objective = f3[1];
+        M.res.n_support = (int64_t)std::llround(f3[2]);
+        M.res.iters_done = c.t;
+        M.res.converged = f3[0] < M.tol ? 1 : 0;
+        M.res.refine_passes = M.refine_done;
+        if (c.status == ST_ENUMERIC) M.res.status = GABP_ENUMERIC;
+        else if (c.status == ST_EINVAL) M.res.status = GABP_EINVAL;
+        else if (c.status == ST_ETIMEOUT) M.res.status = GABP_ETIMEOUT;
+        else if (c.status != 0) M.res.status = GABP_ECUDA;
+        M.finished = true;
+        M.active = false;
+        lists_dirty = true;
+        return GABP_OK;
+    }
+
+    // After a chunk: instances that stopped either start a refinement pass
+    // (precision form) or finish.  Returns the number still running.
+    gabp_status advance(int* running, std::vector<int>* finished = nullptr)
+    {
+        int run = 0;
+        for (int k = 0; k < cap_members; ++k) {
+            Member& M = mem[(size_t)k];
+            if (!M.used || !M.active) continue;
+            const Ctrl& c = h_ctrl[k];
+            if (!c.done) { ++run; continue; }
+            if (c.status == 0 && q_mode != 0 && (M.refining || M.refine_left > 0)) {
+                // Defect correction on the FP32-Gram residual (as in the handle's
+                // solve): accumulate the means (or the correction), form
+                // r = 1 - Q32 mu_acc and, while it is above tol, solve for the
+                // next correction with the P messages kept.
+                launch_axpy_mu(M.inst, c.kstar, M.mu_acc, M.refining ? 0 : 1, stream);
+                if (M.refining) ++M.refine_done;
+                M.refining = true;
+                launch_final(M.inst, M.work, M.ntiles, M.mu_acc, M.alpha, M.final3, M.blockbuf,
+                             (float)sv_threshold, M.r32, stream);
+                double f3[3];
+                EK(cudaMemcpyAsync(f3, M.final3, sizeof f3, cudaMemcpyDeviceToHost, stream));
+                EK(cudaStreamSynchronize(stream));
+                launches += 4;
+                if (f3[0] >= M.tol && M.refine_left > 0) {
+                    --M.refine_left;
+                    launch_refine_rhs(M.inst, M.r32, stream);
+                    launch_begin(d_tab + k, 1, M.iters, std::max(M.tol * 0.5, 1e-2 * f3[0]), stream);
+                    launches += 2;
+                    ++run;
+                    continue;
+                }
+            }
+            if (gabp_status st = finish(k)) return st;
+            if (finished) finished->push_back(k);
+        }
+        *running = run;
+        return GABP_OK;
+    }
+
+    // Restart every active instance from Step 1 (used after tuning runs).
+    gabp_status reset_all()
+    {
+        for (int k = 0; k < cap_members; ++k) {
+            Member& M = mem[(size_t)k];
+            if (!M.used || !M.active) continue;
+            launch_reset(M.inst, stream);
+            ++launches;
+        }
+        EK(cudaStreamSynchronize(stream));
+        return GABP_OK;
+    }
+
+    // Picks sweep CTAs per SM and the chunk length by timing candidate
+    // schedules for a few rounds of the real set (then restarts it).
+    gabp_status autotune(int iters)
+    {
+        long long tiles = 0;
+        int members = 0;
+        for (auto& M : mem)
+            if (M.used && M.active) { tiles += M.ntiles; ++members; }
+        TuneKey key{q_mode, tiles >> 8, members >> 3};
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) {
+                set_grid(it->second.ctas_per_sm);
+                chunk = it->second.chunk;
+                return GABP_OK;
+            }
+        }
+        const int probe = std::max(1, std::min(4, iters));
+        std::vector<int> cands = q_mode == 2 ? std::vector<int>{1} : std::vector<int>{1, 2};
+        float best = 1e30f;
+        int best_c = cands[0];
+        cudaEvent_t e0, e1;
+        EK(cudaEventCreate(&e0));
+        EK(cudaEventCreate(&e1));
+        double round_ms = 1.0;
+        for (int c : cands) {
+            set_grid(c);
+            for (int k = 0; k < cap_members; ++k)
+                if (mem[(size_t)k].used && mem[(size_t)k].active) launch_begin(d_tab + k, 1, probe, 0.0, stream);
+            if (gabp_status st = rebuild()) return st;
+            cudaGraphExec_t g = nullptr;
+            if (gabp_status st = graph_for(probe, &g)) return st;
+            EK(cudaEventRecord(e0, stream));
+            EK(cudaGraphLaunch(g, stream));
+            EK(cudaEventRecord(e1, stream));
+            EK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            EK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) { best = ms; best_c = c; round_ms = ms / probe; }
+            if (gabp_status st = reset_all()) return st;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        set_grid(best_c);
+        // rounds per convergence check: keep the host check (~0.05 ms) under
+        // about 2% of the rounds it covers, within [4, 64]
+        int ch = 4;
+        while (ch < 64 && 0.05 / (ch * round_ms) > 0.02) ch *= 2;
+        chunk = ch;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = TuneVal{best_c, chunk};
+        return GABP_OK;
+    }
+};
+
+}  // namespace gabp
+
+using gabp::Engine;
+
+extern "C" {
+
+gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gabp_svm_opts* opts, int32_t iters,
+                             double tol, gabp_result* results)
+{
+    using namespace gabp;
+    set_last_error("");
+    if (!probs || !results || count < 1 || count > (1 << 20)) {
+        set_last_error("gabp_batch_solve: need problems, results and 1 <= count <= 2^20");
+        return GABP_EINVAL;
+    }
+    if (iters < 0 || std::isnan(tol)) {
+        set_last_error("gabp_batch_solve: bad iters or tol");
+        return GABP_EINVAL;
+    }
+    gabp_svm_opts o;
+    gabp_svm_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.diag_delta == 0) o.diag_delta = 0.1;
+    if (o.q_mode < 0 || o.q_mode > 2 || o.refine < 0 || o.refine > 64) {
+        set_last_error("gabp_batch_solve: bad q_mode or refine");
+        return GABP_EINVAL;
+    }
+    long long tiles = 0, nblk = 0;
+    size_t bytes = 0;
+    for (int64_t k = 0; k < count; ++k) {
+        const gabp_problem& p = probs[k];
+        if (p.n < 2 || p.m < 1 || p.n > (1 << 30) || !p.X || !p.y || !(p.gamma > 0) || !(p.C > 0)) {
+            set_last_error(("gabp_batch_solve: problem " + std::to_string(k) + " is invalid").c_str());
+            return GABP_EINVAL;
+        }
+        const long long Nt = (p.n + T - 1) / T;
+        tiles += tri_tiles(Nt);
+        nblk += (p.n + 31) / 32;
+        bytes += member_plan(p.n, p.m, o.q_mode).total;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        set_last_error("no CUDA device");
+        return GABP_ECUDA;
+    }
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    if (bytes + ((size_t)512 << 20) > free_b) {
+        set_last_error(("gabp_batch_solve: needs " + std::to_string(bytes / 1e9) + " GB of device memory").c_str());
+        return GABP_ENOMEM;
+    }
+    Engine E;
+    if (gabp_status st = E.init((int)count, tiles, (int)nblk, o)) return st;
+    for (int64_t k = 0; k < count; ++k) {
+        if (gabp_status st = E.add((int)k, probs[k], results[k].alpha, o.ptr_mode)) return st;
+        E.mem[(size_t)k].iters = iters;
+        E.mem[(size_t)k].tol = tol;
+        E.mem[(size_t)k].refine_left = o.q_mode != 0 ? o.refine : 0;
+        E.mem[(size_t)k].ticket = k;
+    }
+    if (cudaStreamSynchronize(E.side) != cudaSuccess) return E.fail(GABP_ECUDA, "formation failed");
+    // labels / features validated by the staging kernels
+    if (cudaMemcpy(E.h_ctrl, E.d_ctrl, (size_t)count * sizeof(Ctrl), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return E.fail(GABP_ECUDA, "control read failed");
+    for (int64_t k = 0; k < count; ++k)
+        if (E.h_ctrl[k].status != 0)
+            return E.fail(GABP_EINVAL, "problem " + std::to_string(k) + ": non-finite feature or label not +-1");
+    for (int64_t k = 0; k < count; ++k)
+        if (gabp_status st = E.activate((int)k, iters, tol)) return st;
+    if (o.chunk <= 0) {
+        if (gabp_status st = E.autotune(iters)) return st;
+        for (int64_t k = 0; k < count; ++k) gabp::launch_begin(E.d_tab + k, 1, iters, tol, E.stream);
+    } else {
+        E.chunk = o.chunk;
+    }
+    const int max_loops = (int)(((long long)iters * (1 + o.refine)) / std::max(1, E.chunk) + 4 * (2 + o.refine) + 8);
+    int running = (int)count;
+    for (int loop = 0; loop < max_loops && running > 0; ++loop) {
+        if (gabp_status st = E.run_chunk(E.chunk)) return st;
+        if (gabp_status st = E.advance(&running)) return st;
+    }
+    if (running > 0) return E.fail(GABP_ECUDA, "batch did not reach its stop condition");
+    gabp_status worst = GABP_OK;
+    for (int64_t k = 0; k < count; ++k) {
+        gabp_result r = E.mem[(size_t)k].res;
+        r.alpha = results[k].alpha;
+        results[k] = r;
+        if (r.status != GABP_OK && worst == GABP_OK) worst = (gabp_status)r.status;
+    }
+    if (worst != GABP_OK) set_last_error("one or more problems failed; see their result status");
+    return worst;
+}
+
+// ------------------------------------------------------------------ server
+struct gabp_server_s {
+    Engine E;
+    gabp_server_cfg cfg{};
+    size_t budget = 0;
+    std::deque<std::pair<int64_t, gabp_problem>> queue;
+    std::map<int64_t, float*> outs;
+    std::map<int64_t, gabp_result> done;
+    std::vector<int> forming;   // slots whose Q formation runs on the side stream
+    int64_t next_ticket = 0;
+};
+
+gabp_status gabp_server_create(const gabp_server_cfg* cfg, gabp_server_t* out)
+{
+    using namespace gabp;
+    set_last_error("");
+    if (!cfg || !out) { set_last_error("gabp_server_create: null argument"); return GABP_EINVAL; }
+    *out = nullptr;
+    gabp_server_cfg c = *cfg;
+    if (c.max_members <= 0) c.max_members = 64;
+    if (c.max_members > 4096 || c.iters < 0 || std::isnan(c.tol) || c.opts.q_mode < 0 || c.opts.q_mode > 2) {
+        set_last_error("gabp_server_create: bad configuration");
+        return GABP_EINVAL;
+    }
+    if (c.opts.diag_delta == 0) c.opts.diag_delta = 0.1;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) { set_last_error("no CUDA device"); return GABP_ECUDA; }
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    size_t budget = c.hbm_budget_bytes > 0 ? (size_t)c.hbm_budget_bytes : (size_t)(0.8 * (double)free_b);
+    if (budget + ((size_t)1 << 30) > free_b) budget = free_b > ((size_t)2 << 30) ? free_b - ((size_t)2 << 30) : 0;
+    // list capacities: every tile of state costs TT * 16 bytes, so the budget bounds them
+    const long long cap_tiles = (long long)(budget / ((size_t)TT * 16)) + 1;
+    const int cap_nblk = (int)std::min<long long>(cap_tiles * 4 + 1024, 1LL << 28);
+    gabp_server_t s = new gabp_server_s();
+    if (gabp_status st = s->E.init(c.max_members, cap_tiles, cap_nblk, c.opts)) { delete s; return st; }
+    s->E.chunk = c.opts.chunk > 0 ? c.opts.chunk : 8;
+    s->cfg = c;
+    s->budget = budget;
+    *out = s;
+    return GABP_OK;
+}
+
+gabp_status gabp_server_submit(gabp_server_t s, const gabp_problem* p, float* alpha_out, int64_t* ticket)
+{
+    gabp::set_last_error("");
+    if (!s || !p || !ticket) { gabp::set_last_error("gabp_server_submit: null argument"); return GABP_EINVAL; }
+    if (p->n < 2 || p->m < 1 || !p->X || !p->y || !(p->gamma > 0) || !(p->C > 0)) {
+        gabp::set_last_error("gabp_server_submit: invalid problem");
+        return GABP_EINVAL;
+    }
+    const int64_t t = s->next_ticket++;
+    s->queue.emplace_back(t, *p);
+    s->outs[t] = alpha_out;
+    *ticket = t;
+    return GABP_OK;
+}
+
+gabp_status gabp_server_step(gabp_server_t s, int32_t* active, int32_t* queued, int32_t* completed)
+{
+    using namespace gabp;
+    set_last_error("");
+    if (!s) { set_last_error("gabp_server_step: null server"); return GABP_EINVAL; }
+    Engine& E = s->E;
+    // 1. admission, first come first served, by device-memory budget and free slots
+    while (!s->queue.empty()) {
+        const auto& front = s->queue.front();
+        const size_t need = member_plan(front.second.n, front.second.m, s->cfg.opts.q_mode).total;
+        if (need > s->budget) {
+            gabp_result r{};
+            r.status = GABP_ENOMEM;
+            r.alpha = s->outs[front.first];
+            s->done[front.first] = r;
+            s->queue.pop_front();
+            continue;
+        }
+        const int slot = E.free_slot();
+        if (slot < 0 || E.bytes_in_use + need > s->budget) break;
+        const int64_t t = front.first;
+        if (gabp_status st = E.add(slot, front.second, s->outs[t], s->cfg.opts.ptr_mode)) return st;
+        Member& M = E.mem[(size_t)slot];
+        M.ticket = t;
+        M.iters = s->cfg.iters;
+        M.tol = s->cfg.tol;
+        M.refine_left = s->cfg.opts.q_mode != 0 ? s->cfg.opts.refine : 0;
+        s->forming.push_back(slot);
+        s->queue.pop_front();
+    }
+    // 2. instances whose Q is ready join the sweeps
+    for (size_t k = 0; k < s->forming.size();) {
+        const int slot = s->forming[k];
+        cudaError_t q = cudaEventQuery(E.mem[(size_t)slot].ready);
+        if (q == cudaSuccess) {
+            if (gabp_status st = E.activate(slot, s->cfg.iters, s->cfg.tol)) return st;
+            s->forming.erase(s->forming.begin() + (long)k);
+        } else if (q == cudaErrorNotReady) {
+            ++k;
+        } else {
+            return E.fail(GABP_ECUDA, std::string("formation: ") + cudaGetErrorString(q));
+        }
+    }
+    // 3. one chunk of rounds over every live instance, then retire the finished
+    int running = 0;
+    bool any = false;
+    for (auto& M : E.mem) any |= (M.used && M.active);
+    if (any) {
+        if (gabp_status st = E.run_chunk(E.chunk)) return st;
+        std::vector<int> fin;
+        if (gabp_status st = E.advance(&running, &fin)) return st;
+        for (int slot : fin) {
+            Member& M = E.mem[(size_t)slot];
+            gabp_result r = M.res;
+            r.alpha = M.out_alpha;
+            s->done[M.ticket] = r;
+            E.release(M);
+        }
+    }
+    int act = 0;
+    for (auto& M : E.mem) act += M.used ? 1 : 0;
+    if (active) *active = act;
+    if (queued) *queued = (int32_t)s->queue.size();
+    if (completed) *completed = (int32_t)s->done.size();
+    return GABP_OK;
+}
+
+gabp_status gabp_server_poll(gabp_server_t s, int64_t ticket, gabp_result* res, int32_t* done)
+{
+    gabp::set_last_error("");
+    if (!s || !done) { gabp::set_last_error("gabp_server_poll: null argument"); return GABP_EINVAL; }
+    auto it = s->done.find(ticket);
+    *done = it != s->done.end() ? 1 : 0;
+    if (*done && res) *res = it->second;
+    return GABP_OK;
+}
+
+gabp_status gabp_server_destroy(gabp_server_t s)
+{
+    gabp::set_last_error("");
+    delete s;
+    return GABP_OK;
+}
+
+}  // extern "C"

@@ -81,6 +81,22 @@ struct Inst {
     int nkc;          // 64-feature chunks of Xp
 };
 
+// Work of one round over a set of instances (device resident, so that a
+// captured round stays valid while the set changes).  Tile list entries are
+// int4 {instance, I, J, tile index within the instance}; node-block list
+// entries are int2 {instance, block of 32 nodes}.
+struct Sched {
+    long long ntiles;
+    int nblocks;
+    int ninst;
+};
+
+// Launch shapes of one round (persistent sweep CTAs, finalize CTAs).
+struct RoundGrid {
+    int sweep = 1;
+    int finalize = 1;
+};
+
 // Gram operands: rows [0, n) of an n x m FP32 matrix with row norms sq.
 struct GramSide {
     const float* X;
@@ -94,11 +110,10 @@ void launch_stage(const void* X, int x_f64, int n, int m, const float* y, float*
                   float* b, Ctrl* ctrl, cudaStream_t s);
 // Q formation (FP32 SIMT Gram fused with exp, labels and bias) + |Q| row-sum partials;
 // store_f32 = 0 computes only the row sums.
-void launch_form_q(const Inst& p, const int2* work, long long ntiles, int store_f32, cudaStream_t s);
+void launch_form_q(const Inst* tab, const int4* work, long long ntiles, int store_f32, cudaStream_t s);
 // Precision form: BF16 operand packing + norms, and the tensor-core Q formation (BF16 store).
 cudaError_t launch_pack_bf16(const float* Xf, int n, int m, int nkc, int Nt, void* Xp, float* sqb, cudaStream_t s);
-cudaError_t launch_form_q_tc(const Inst& p, const int2* work, long long ntiles, const void* Xp, int nkc,
-                             const float* sqb, cudaStream_t s);
+cudaError_t launch_form_q_tc(const Inst* tab, const int4* work, long long ntiles, cudaStream_t s);
 int bf16_chunks(int m);
 size_t bf16_pack_bytes(int Nt, int m);
 // Restart: Step-1 aggregates from the stored diagonal and b, t = 0.
@@ -110,26 +125,31 @@ void launch_refine_rhs(const Inst& p, const float* r, cudaStream_t s);
 void launch_axpy_mu(const Inst& p, int buf, float* acc, int first, cudaStream_t s);
 // Diagonal rule, Step-1 aggregates and control reset.
 void launch_init(const Inst& p, int diag_rule, float delta, cudaStream_t s);
-// Solve control: arm the control block for `iters` more rounds with tolerance `tol`.
-void launch_begin(const Inst& p, int iters, double tol, cudaStream_t s);
+// Solve control: arm the control blocks of tab[0..ninst) for `iters` more rounds with tolerance `tol`.
+void launch_begin(Inst* tab, int ninst, int iters, double tol, cudaStream_t s);
+int num_sms();
+// Grid of a round for up to max_tiles tiles and max_nblocks node blocks
+// (ctas_per_sm: sweep CTAs per SM for the stored-Q kernels, 0 = default).
+RoundGrid round_grid(long long max_tiles, int max_nblocks, int q_mode, int ctas_per_sm);
 // Raises the dynamic shared-memory limit of the pair-sweep kernels (once per device).
 cudaError_t prepare_sweep();
 // Fused-recompute form: also raises the shared-memory limit of its sweep kernel.
 cudaError_t prepare_sweep_rc();
-// One synchronous round: pair sweep then per-node finalize.  When ev is not
-// null, ev[0] is recorded before and ev[1] after the pair sweep.
-void launch_round(const Inst& p, const int2* work, long long ntiles, int q_mode, cudaStream_t s,
-                  cudaEvent_t* ev = nullptr);
+// One synchronous round over every live instance of tab: pair sweep then
+// per-node finalize.  When ev is not null, ev[0] is recorded before and
+// ev[1] after the pair sweep.
+void launch_round(const Inst* tab, const int4* work, const int2* nbl, const Sched* sched, const RoundGrid& g,
+                  int q_mode, cudaStream_t s, cudaEvent_t* ev = nullptr);
 // Final FP32-Gram residual r = 1 - Q mu (FP64 sums), dual objective and
 // alpha = clip(mu, 0, C) for the means mu; out3 = {||r||_inf, objective, #SV};
 // r_out (optional) receives r in FP32.
-void launch_final(const Inst& p, const int2* work, long long ntiles, const float* mu, float* alpha,
+void launch_final(const Inst& p, const int4* work, long long ntiles, const float* mu, float* alpha,
                   double* out3, double* blockbuf, float sv_threshold, float* r_out, cudaStream_t s);
 // Decision values for t test rows (Xt FP32, sqt norms) using alpha.
 void launch_decision(const Inst& p, const float* Xt, const float* sqt, int t, const float* alpha,
                      const int2* work, long long ntiles, float* part, float* out, cudaStream_t s);
 // Gather helpers for inspection.
-void launch_get_q(const Inst& p, const int2* work, long long ntiles, int q_bf16, float* Qdense,
+void launch_get_q(const Inst& p, const int4* work, long long ntiles, int q_bf16, float* Qdense,
                   cudaStream_t s);
 void launch_get_pairs(const Inst& p, const long long* ij, long long cnt, float4* out,
                       cudaStream_t s);

@@ -173,11 +173,14 @@ __global__ void k_stage(const void* __restrict__ X, int x_f64, int n, int m, con
 }
 
 // ------------------------------------------------------- Q tile formation
-__global__ void __launch_bounds__(NTHREADS) k_form_q(Inst p, const int2* __restrict__ work, int store)
+__global__ void __launch_bounds__(NTHREADS) k_form_q(const Inst* __restrict__ tab, const int4* __restrict__ work,
+                                                     int store)
 {
     __shared__ __align__(16) TileSmem sm;
-    const long long L = blockIdx.x;
-    const int I = work[L].x, J = work[L].y, n = p.n;
+    const int4 w = work[blockIdx.x];
+    const Inst& p = tab[w.x];
+    const long long L = w.w;
+    const int I = w.y, J = w.z, n = p.n;
     const GramSide S{p.X, p.sq, n};
     float acc[8][8];
     gram_tile(S, S, p.m, I, J, sm.g, acc);
@@ -225,12 +228,11 @@ __global__ void __launch_bounds__(NTHREADS) k_form_q(Inst p, const int2* __restr
 // Off-diagonal sums sum_{j != i} Q_ij mu_j (-> part[0]) and
 // sum_{j != i} Q_ij alpha_j (-> part[1]) with alpha = clip(mu, 0, C), Q
 // recomputed in FP32 (bitwise equal to the stored FP32 tiles).
-__global__ void __launch_bounds__(NTHREADS) k_final_tiles(Inst p, const int2* __restrict__ work,
+__global__ void __launch_bounds__(NTHREADS) k_final_tiles(Inst p, const int4* __restrict__ work,
                                                           const float* __restrict__ mu)
 {
     __shared__ __align__(16) TileSmem sm;
-    const long long L = blockIdx.x;
-    const int I = work[L].x, J = work[L].y, n = p.n;
+    const int I = work[blockIdx.x].y, J = work[blockIdx.x].z, n = p.n;
     const GramSide S{p.X, p.sq, n};
     float acc[8][8];
     gram_tile(S, S, p.m, I, J, sm.g, acc);
@@ -402,10 +404,10 @@ __global__ void k_decision_sum(const float* __restrict__ part, int t, int Ntrain
 }
 
 // ---------------------------------------------------------------- inspection
-__global__ void k_get_q(Inst p, const int2* __restrict__ work, int q_bf16, float* __restrict__ Qd)
+__global__ void k_get_q(Inst p, const int4* __restrict__ work, int q_bf16, float* __restrict__ Qd)
 {
-    const long long L = blockIdx.x;
-    const int I = work[L].x, J = work[L].y, n = p.n;
+    const long long L = work[blockIdx.x].w;
+    const int I = work[blockIdx.x].y, J = work[blockIdx.x].z, n = p.n;
     for (int e = threadIdx.x; e < TT; e += blockDim.x) {
         const int r = e / T, c = e % T, i = I * T + r, j = J * T + c;
         if (i >= n || j >= n || (I == J && c <= r)) continue;
@@ -430,12 +432,12 @@ void launch_stage(const void* X, int x_f64, int n, int m, const float* y, float*
     k_stage<<<(n + 255) / 256, 256, 0, s>>>(X, x_f64, n, m, y, Xf, sq, b, ctrl);
 }
 
-void launch_form_q(const Inst& p, const int2* work, long long ntiles, int store_f32, cudaStream_t s)
+void launch_form_q(const Inst* tab, const int4* work, long long ntiles, int store_f32, cudaStream_t s)
 {
-    k_form_q<<<(unsigned)ntiles, NTHREADS, 0, s>>>(p, work, store_f32);
+    if (ntiles > 0) k_form_q<<<(unsigned)ntiles, NTHREADS, 0, s>>>(tab, work, store_f32);
 }
 
-void launch_final(const Inst& p, const int2* work, long long ntiles, const float* mu, float* alpha,
+void launch_final(const Inst& p, const int4* work, long long ntiles, const float* mu, float* alpha,
                   double* out3, double* blockbuf, float sv_threshold, float* r_out, cudaStream_t s)
 {
     k_final_tiles<<<(unsigned)ntiles, NTHREADS, 0, s>>>(p, work, mu);
@@ -451,7 +453,7 @@ void launch_decision(const Inst& p, const float* Xt, const float* sqt, int t, co
     k_decision_sum<<<(t + 255) / 256, 256, 0, s>>>(part, t, p.Nt, out);
 }
 
-void launch_get_q(const Inst& p, const int2* work, long long ntiles, int q_bf16, float* Qdense,
+void launch_get_q(const Inst& p, const int4* work, long long ntiles, int q_bf16, float* Qdense,
                   cudaStream_t s)
 {
     k_get_q<<<(unsigned)ntiles, 256, 0, s>>>(p, work, q_bf16, Qdense);

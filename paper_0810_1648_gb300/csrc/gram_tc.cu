@@ -77,16 +77,14 @@ struct TcSmem {
 };
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_form_q_tc(Inst p, const int2* __restrict__ work, long long ntiles, const unsigned char* __restrict__ Xp,
-                int nkc, const float* __restrict__ sqb)
+    k_form_q_tc(const Inst* __restrict__ tab, const int4* __restrict__ work, long long ntiles)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     unsigned char* ops = base;                                   // XSTAGES x (A block, B block)
     TcSmem& sm = *reinterpret_cast<TcSmem*>(base + XSTAGES * 2 * BLK_BYTES);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, n = p.n;
-    Ctrl* ctrl = p.ctrl;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
         for (int s = 0; s < XSTAGES; ++s) { mbar_init(&sm.xfull[s], 1); mbar_init(&sm.xempty[s], 1); }
@@ -109,11 +107,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             uint32_t ph = 0;
             bool run = true;
             for (long long L = blockIdx.x; L < ntiles && run; L += gridDim.x) {
-                const int I = work[L].x, J = work[L].y;
+                const int4 w = work[L];
+                const Inst& p = tab[w.x];
+                const unsigned char* Xp = static_cast<const unsigned char*>(p.Xp);
+                const int I = w.y, J = w.z, nkc = p.nkc;
                 for (int kc = 0; kc < nkc; ++kc) {
                     if (*(volatile int*)&sm.abort || !mbar_wait(&sm.xempty[stage], ph ^ 1u)) {
                         sm.abort = 1;
-                        record_error(ctrl, ST_ETIMEOUT, L);
+                        record_error(p.ctrl, ST_ETIMEOUT, L);
                         run = false;
                         break;
                     }
@@ -132,6 +133,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int stage = 0, acc = 0;
             uint32_t ph = 0, aph = 0;
             for (long long L = blockIdx.x; L < ntiles; L += gridDim.x) {
+                const Inst& p = tab[work[L].x];
+                Ctrl* ctrl = p.ctrl;
+                const int nkc = p.nkc;
                 if (*(volatile int*)&sm.abort || !mbar_wait(&sm.accempty[acc], aph ^ 1u)) {
                     sm.abort = 1;
                     record_error(ctrl, ST_ETIMEOUT, L);
@@ -164,7 +168,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             // every MMA issued above must finish before the columns are freed
             tc_commit(&sm.drain);
-            if (!mbar_wait(&sm.drain, 0u)) record_error(ctrl, ST_ETIMEOUT, -2);
+            if (!mbar_wait(&sm.drain, 0u)) sm.abort = 1;
         }
     } else {
         // --------------------------------------------------------- epilogue
@@ -172,8 +176,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int r = 32 * g + lane;
         int acc = 0;
         uint32_t aph = 0;
-        __nv_bfloat16* qs = static_cast<__nv_bfloat16*>(p.qstore);
         for (long long L = blockIdx.x; L < ntiles; L += gridDim.x) {
+            const int4 w = work[L];
+            const Inst& p = tab[w.x];
+            Ctrl* ctrl = p.ctrl;
+            const int n = p.n;
+            const float* sqb = p.sqb;
+            __nv_bfloat16* qs = static_cast<__nv_bfloat16*>(p.qstore);
             const bool stop = __shfl_sync(0xffffffffu, *(volatile int*)&sm.abort, 0) != 0;
             if (stop || !mbar_wait_warp(&sm.accfull[acc], aph)) {
                 if (lane == 0) {
@@ -183,10 +192,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 break;
             }
             tc_fence_after();
-            const int I = work[L].x, J = work[L].y;
+            const int I = w.y, J = w.z;
             const int i = I * T + r;
             const float yi = i < n ? p.y[i] : 0.f, si = i < n ? sqb[i] : 0.f;
-            __nv_bfloat16* qrow = qs + (size_t)L * TT + (size_t)r * T;
+            __nv_bfloat16* qrow = qs + (size_t)w.w * TT + (size_t)r * T;
 #pragma unroll 1
             for (int cc = 0; cc < T / 32; ++cc) {
                 float v[32];
@@ -231,9 +240,9 @@ cudaError_t launch_pack_bf16(const float* Xf, int n, int m, int nkc, int Nt, voi
     return cudaGetLastError();
 }
 
-cudaError_t launch_form_q_tc(const Inst& p, const int2* work, long long ntiles, const void* Xp, int nkc,
-                             const float* sqb, cudaStream_t s)
+cudaError_t launch_form_q_tc(const Inst* tab, const int4* work, long long ntiles, cudaStream_t s)
 {
+    if (ntiles <= 0) return cudaSuccess;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_form_q_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -245,8 +254,7 @@ cudaError_t launch_form_q_tc(const Inst& p, const int2* work, long long ntiles, 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = (int)(ntiles < sms ? ntiles : sms);
-    k_form_q_tc<<<grid, TC_THREADS, tc_smem_bytes(), s>>>(p, work, ntiles, static_cast<const unsigned char*>(Xp),
-                                                          nkc, sqb);
+    k_form_q_tc<<<grid, TC_THREADS, tc_smem_bytes(), s>>>(tab, work, ntiles);
     return cudaGetLastError();
 }
 

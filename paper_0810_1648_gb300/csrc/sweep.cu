@@ -81,22 +81,24 @@ __host__ __device__ constexpr size_t sweep_smem_bytes() { return 128 + STAGES * 
 
 // Producer (one thread).  QT = void: messages only.
 template <typename QT, size_t SB>
-__device__ __forceinline__ void sweep_producer(const Inst& p, const int2* __restrict__ work, long long ntiles,
-                                               SweepTail& sm, unsigned char* ring, bool zero,
+__device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, const int4* __restrict__ work,
+                                               long long ntiles, SweepTail& sm, unsigned char* ring,
                                                volatile int* abort_flag)
 {
     constexpr size_t QB = QBytes<QT>::v;
     const uint64_t pol = l2_evict_first_policy();
-    const int n = p.n;
     int stage = 0;
     uint32_t phase = 0;
     for (long long L = blockIdx.x; L < ntiles; L += gridDim.x) {
-        const int2 tile = work[L];
-        const int I = tile.x, J = tile.y;
+        const int4 w = work[L];
+        const Inst& p = tab[w.x];
+        if (*(volatile const int*)&p.ctrl->done) continue;      // instance finished: tile skipped
+        const bool zero = *(volatile const int*)&p.ctrl->t == 0;
+        const int n = p.n, I = w.y, J = w.z;
         const int rows = min(T, n - I * T), cols = min(T, n - J * T);
         const bool diag = (I == J);
-        const float4* st = p.state + (size_t)L * TT;
-        const unsigned char* qt = QB ? static_cast<const unsigned char*>(p.qstore) + (size_t)L * TT * QB : nullptr;
+        const float4* st = p.state + (size_t)w.w * TT;
+        const unsigned char* qt = QB ? static_cast<const unsigned char*>(p.qstore) + (size_t)w.w * TT * QB : nullptr;
         const int nch = (rows + RC - 1) / RC;
         for (int c = 0; c < nch; ++c) {
             if ((abort_flag && *abort_flag) || !mbar_wait(&sm.empty[stage], phase ^ 1u)) {
@@ -143,23 +145,30 @@ __device__ __forceinline__ void sweep_producer(const Inst& p, const int2* __rest
 // Consumers (256 threads, ctid = 0..255, consumer warp cw = ctid / 32).
 // QSrc supplies q for a pair and the per-tile hand-shake of a recomputed Q tile.
 template <size_t SB, class QSrc>
-__device__ __forceinline__ void sweep_consumers(const Inst& p, const int2* __restrict__ work, long long ntiles,
-                                                SweepTail& sm, const unsigned char* ring, int ctid, int t,
-                                                bool zero, bool zero_h, QSrc& qsrc)
+__device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, const int4* __restrict__ work,
+                                                long long ntiles, SweepTail& sm, const unsigned char* ring,
+                                                int ctid, QSrc& qsrc)
 {
-    const int cw = ctid >> 5, lane = ctid & 31, n = p.n;
-    Ctrl* ctrl = p.ctrl;
-    const float* agg = p.agg + (size_t)(t & 1) * 3 * p.npad;
-    float* partP = p.part;
-    float* partH = partP + (size_t)p.Nt * n;
-    float* partR = partH + (size_t)p.Nt * n;
+    const int cw = ctid >> 5, lane = ctid & 31;
     int stage = 0;
     uint32_t phase = 0;
-    bool bad = false, abort = false;
+    bool abort = false;
     int it = 0;
-    for (long long L = blockIdx.x; L < ntiles; L += gridDim.x, ++it) {
-        const int2 tile = work[L];
-        const int I = tile.x, J = tile.y;
+    for (long long L = blockIdx.x; L < ntiles; L += gridDim.x) {
+        const int4 w = work[L];
+        const Inst& p = tab[w.x];
+        Ctrl* ctrl = p.ctrl;
+        if (*(volatile const int*)&ctrl->done) continue;
+        const int t = *(volatile const int*)&ctrl->t;
+        const bool zero = (t == 0);   // Step 1: all messages 0, nothing to read
+        const bool zero_h = *(volatile const int*)&ctrl->zero_h != 0;
+        const float* agg = p.agg + (size_t)(t & 1) * 3 * p.npad;
+        const int n = p.n;
+        float* partP = p.part;
+        float* partH = partP + (size_t)p.Nt * n;
+        float* partR = partH + (size_t)p.Nt * n;
+        bool bad = false;
+        const int I = w.y, J = w.z;
         const int rows = min(T, n - I * T), cols = min(T, n - J * T);
         const bool diag = (I == J);
         {
@@ -185,7 +194,7 @@ __device__ __forceinline__ void sweep_consumers(const Inst& p, const int2* __res
             cM[k] = sm.col[2][c];
             aP[k] = aH[k] = aR[k] = 0.f;
         }
-        float4* st = p.state + (size_t)L * TT;
+        float4* st = p.state + (size_t)w.w * TT;
         const int nch = (rows + RC - 1) / RC;
         for (int ch = 0; ch < nch; ++ch) {
             if (!abort && !mbar_wait_warp(&sm.full[stage], phase)) {
@@ -265,8 +274,9 @@ __device__ __forceinline__ void sweep_consumers(const Inst& p, const int2* __res
                 partP[o] = P; partH[o] = H; partR[o] = R;
             }
         }
+        if (bad) record_error(ctrl, ST_ENUMERIC, (long long)I * T);
+        ++it;
     }
-    if (bad) record_error(ctrl, ST_ENUMERIC, -1);
 }
 
 // Q streamed with the messages: it sits after the messages in each ring stage.
@@ -287,13 +297,9 @@ __device__ __forceinline__ unsigned char* align_smem(unsigned char* raw, uintptr
 
 template <typename QT>
 __global__ void __launch_bounds__(SWEEP_THREADS, SWEEP_CTAS_PER_SM)
-    k_sweep(Inst p, const int2* __restrict__ work, long long ntiles)
+    k_sweep(const Inst* __restrict__ tab, const int4* __restrict__ work, const Sched* __restrict__ sched)
 {
-    Ctrl* ctrl = p.ctrl;
-    if (*(volatile const int*)&ctrl->done) return;
-    const int t = *(volatile const int*)&ctrl->t;
-    const bool zero = (t == 0);   // Step 1: all messages 0, nothing to read
-    const bool zero_h = *(volatile const int*)&ctrl->zero_h != 0;
+    const long long ntiles = sched->ntiles;
     constexpr size_t SB = stage_bytes<QT>();
 
     extern __shared__ unsigned char smem_raw[];
@@ -310,11 +316,11 @@ __global__ void __launch_bounds__(SWEEP_THREADS, SWEEP_CTAS_PER_SM)
     }
     __syncthreads();
     if (warp == NWARPS) {
-        if (lane == 0) sweep_producer<QT, SB>(p, work, ntiles, sm, ring, zero, nullptr);
+        if (lane == 0) sweep_producer<QT, SB>(tab, work, ntiles, sm, ring, nullptr);
         return;
     }
     StoredQ<QT> qsrc;
-    sweep_consumers<SB>(p, work, ntiles, sm, ring, tid, t, zero, zero_h, qsrc);
+    sweep_consumers<SB>(tab, work, ntiles, sm, ring, tid, qsrc);
 }
 
 // ---- fused recompute ------------------------------------------------------
@@ -356,13 +362,10 @@ struct RecomputedQ {
     }
 };
 
-__global__ void __launch_bounds__(RC_THREADS, 1) k_sweep_rc(Inst p, const int2* __restrict__ work, long long ntiles)
+__global__ void __launch_bounds__(RC_THREADS, 1)
+    k_sweep_rc(const Inst* __restrict__ tab, const int4* __restrict__ work, const Sched* __restrict__ sched)
 {
-    Ctrl* ctrl = p.ctrl;
-    if (*(volatile const int*)&ctrl->done) return;
-    const int t = *(volatile const int*)&ctrl->t;
-    const bool zero = (t == 0);
-    const bool zero_h = *(volatile const int*)&ctrl->zero_h != 0;
+    const long long ntiles = sched->ntiles;
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* ring = align_smem(smem_raw, 1024);
@@ -370,8 +373,7 @@ __global__ void __launch_bounds__(RC_THREADS, 1) k_sweep_rc(Inst p, const int2* 
     __nv_bfloat16* qtile = reinterpret_cast<__nv_bfloat16*>(xops + RC_XSTAGES * 2 * BLK_BYTES);
     SweepTail& sm = *reinterpret_cast<SweepTail*>(reinterpret_cast<unsigned char*>(qtile) + 2 * RC_QTILE);
     RcExtra& ex = *reinterpret_cast<RcExtra*>(reinterpret_cast<unsigned char*>(&sm) + sizeof(SweepTail));
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, n = p.n;
-    const int nkc = p.nkc;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -397,17 +399,21 @@ __global__ void __launch_bounds__(RC_THREADS, 1) k_sweep_rc(Inst p, const int2* 
     volatile int* abort_flag = &ex.abort;
 
     if (warp == 0) {
-        if (lane == 0) sweep_producer<void, STATE_CHUNK>(p, work, ntiles, sm, ring, zero, abort_flag);
+        if (lane == 0) sweep_producer<void, STATE_CHUNK>(tab, work, ntiles, sm, ring, abort_flag);
     } else if (warp == 1) {
         // feature blocks of each tile
         if (lane == 0) {
             const uint64_t pol = l2_evict_first_policy();
-            const unsigned char* Xp = static_cast<const unsigned char*>(p.Xp);
             int xs = 0;
             uint32_t ph = 0;
             bool run = true;
             for (long long L = blockIdx.x; L < ntiles && run; L += gridDim.x) {
-                const int I = work[L].x, J = work[L].y;
+                const int4 w = work[L];
+                const Inst& p = tab[w.x];
+                Ctrl* ctrl = p.ctrl;
+                if (*(volatile const int*)&ctrl->done) continue;
+                const unsigned char* Xp = static_cast<const unsigned char*>(p.Xp);
+                const int I = w.y, J = w.z, nkc = p.nkc;
                 for (int kc = 0; kc < nkc; ++kc) {
                     if (*abort_flag || !mbar_wait(&ex.xempty[xs], ph ^ 1u)) {
                         *abort_flag = 1;
@@ -430,6 +436,10 @@ __global__ void __launch_bounds__(RC_THREADS, 1) k_sweep_rc(Inst p, const int2* 
             int xs = 0, acc = 0;
             uint32_t ph = 0, aph = 0;
             for (long long L = blockIdx.x; L < ntiles; L += gridDim.x) {
+                const Inst& p = tab[work[L].x];
+                Ctrl* ctrl = p.ctrl;
+                if (*(volatile const int*)&ctrl->done) continue;
+                const int nkc = p.nkc;
                 if (*abort_flag || !mbar_wait(&ex.accempty[acc], aph ^ 1u)) {
                     *abort_flag = 1;
                     record_error(ctrl, ST_ETIMEOUT, L);
@@ -461,13 +471,18 @@ __global__ void __launch_bounds__(RC_THREADS, 1) k_sweep_rc(Inst p, const int2* 
                 if (++acc == 2) { acc = 0; aph ^= 1u; }
             }
             tc_commit(&ex.drain);
-            if (!mbar_wait(&ex.drain, 0u)) record_error(ctrl, ST_ETIMEOUT, -2);
+            if (!mbar_wait(&ex.drain, 0u)) *abort_flag = 1;
         }
     } else if (warp < 7) {
         // epilogue: TMEM rows -> BF16 Q tile in shared memory
         const int g = warp & 3, r = 32 * g + lane;
         int it = 0;
-        for (long long L = blockIdx.x; L < ntiles; L += gridDim.x, ++it) {
+        for (long long L = blockIdx.x; L < ntiles; L += gridDim.x) {
+            const int4 w = work[L];
+            const Inst& p = tab[w.x];
+            Ctrl* ctrl = p.ctrl;
+            if (*(volatile const int*)&ctrl->done) continue;
+            const int n = p.n;
             const int acc = it & 1;
             const uint32_t par = (uint32_t)((it >> 1) & 1);
             const bool stop = __shfl_sync(0xffffffffu, *abort_flag, 0) != 0;
@@ -479,7 +494,7 @@ __global__ void __launch_bounds__(RC_THREADS, 1) k_sweep_rc(Inst p, const int2* 
                 break;
             }
             tc_fence_after();
-            const int I = work[L].x, J = work[L].y, i = I * T + r;
+            const int I = w.y, J = w.z, i = I * T + r;
             const float yi = i < n ? p.y[i] : 0.f, si = i < n ? p.sqb[i] : 0.f;
             __nv_bfloat16* qrow = qtile + (size_t)acc * TT + (size_t)r * T;
 #pragma unroll 1
@@ -506,10 +521,11 @@ __global__ void __launch_bounds__(RC_THREADS, 1) k_sweep_rc(Inst p, const int2* 
                 mbar_arrive(&ex.accempty[acc]);
                 mbar_arrive(&ex.qfull[acc]);
             }
+            ++it;
         }
     } else {
         RecomputedQ qsrc{qtile, &ex};
-        sweep_consumers<STATE_CHUNK>(p, work, ntiles, sm, ring, tid - 7 * 32, t, zero, zero_h, qsrc);
+        sweep_consumers<STATE_CHUNK>(tab, work, ntiles, sm, ring, tid - 7 * 32, qsrc);
     }
     tc_fence_before();
     __syncthreads();
@@ -533,13 +549,20 @@ __device__ __forceinline__ void acc2(float& s, float& c, float x)
 // Per node x: compensated sums of its Nt slots (32 nodes x 8 slot groups per
 // CTA, four slots in flight per thread), next aggregates, residual r_x(t) in
 // FP64, CTA max |r| -> ctrl, the last CTA to finish decides.
-__global__ void __launch_bounds__(256) k_finalize(Inst p)
+__global__ void __launch_bounds__(256)
+    k_finalize(const Inst* __restrict__ tab, const int2* __restrict__ nbl, const Sched* __restrict__ sched)
 {
+    const int nblocks = sched->nblocks;
+    __shared__ float red[6][8][32];
+    __shared__ int s_last;
+    for (int bi = blockIdx.x; bi < nblocks; bi += gridDim.x) {
+    const int2 nb = nbl[bi];
+    const Inst& p = tab[nb.x];
     Ctrl* ctrl = p.ctrl;
-    if (*(volatile int*)&ctrl->done) return;
+    if (*(volatile int*)&ctrl->done) continue;
     const int t = *(volatile int*)&ctrl->t;
     const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
-    const int x = blockIdx.x * 32 + lane, n = p.n, Nt = p.Nt;
+    const int x = nb.y * 32 + lane, n = p.n, Nt = p.Nt;
     const float* partP = p.part;
     const float* partH = partP + (size_t)Nt * n;
     const float* partR = partH + (size_t)Nt * n;
@@ -565,8 +588,7 @@ __global__ void __launch_bounds__(256) k_finalize(Inst p)
             acc2(sR, cRs, partR[o]);
         }
     }
-    __shared__ float red[6][8][32];
-    __shared__ int s_last;
+    __syncthreads();   // red[] of the previous node block is consumed
     red[0][g][lane] = sP; red[1][g][lane] = cPs;
     red[2][g][lane] = sH; red[3][g][lane] = cHs;
     red[4][g][lane] = sR; red[5][g][lane] = cRs;
@@ -606,7 +628,7 @@ __global__ void __launch_bounds__(256) k_finalize(Inst p)
     __syncthreads();
     if (tid == 0) {
         const unsigned prev = atomicAdd(&ctrl->blocks_done, 1u);
-        s_last = (prev == gridDim.x - 1);
+        s_last = (prev == (unsigned)((n + 31) / 32 - 1));
     }
     __syncthreads();
     if (s_last && tid == 0) {
@@ -632,6 +654,7 @@ __global__ void __launch_bounds__(256) k_finalize(Inst p)
         ctrl->rmax_bits = 0ull;
         ctrl->blocks_done = 0u;
         __threadfence();
+    }
     }
 }
 
@@ -728,8 +751,11 @@ __global__ void k_init(Inst p, int diag_rule, float delta)
     p.agg[2 * p.npad + x] = bx / qf;
 }
 
-__global__ void k_begin(Ctrl* c, int iters, double tol)
+__global__ void k_begin(Inst* tab, int ninst, int iters, double tol)
 {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ninst) return;
+    Ctrl* c = tab[k].ctrl;
     c->limit = c->t + iters;
     c->tol = tol;
     c->converged = 0;
@@ -770,12 +796,12 @@ void launch_axpy_mu(const Inst& p, int buf, float* acc, int first, cudaStream_t 
     k_axpy_mu<<<(p.n + 255) / 256, 256, 0, s>>>(p, buf, acc, first);
 }
 
-void launch_begin(const Inst& p, int iters, double tol, cudaStream_t s)
+void launch_begin(Inst* tab, int ninst, int iters, double tol, cudaStream_t s)
 {
-    k_begin<<<1, 1, 0, s>>>(p.ctrl, iters, tol);
+    k_begin<<<(ninst + 127) / 128, 128, 0, s>>>(tab, ninst, iters, tol);
 }
 
-int sweep_grid(long long ntiles)
+int num_sms()
 {
     static int sms = 0;
     if (sms == 0) {
@@ -784,8 +810,19 @@ int sweep_grid(long long ntiles)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 1;
     }
-    const long long g = (long long)sms * SWEEP_CTAS_PER_SM;
-    return (int)(ntiles < g ? ntiles : g);
+    return sms;
+}
+
+RoundGrid round_grid(long long max_tiles, int max_nblocks, int q_mode, int ctas_per_sm)
+{
+    const int sms = num_sms();
+    RoundGrid g;
+    const long long per_sm = q_mode == 2 ? 1 : (ctas_per_sm > 0 ? ctas_per_sm : SWEEP_CTAS_PER_SM);
+    const long long gs = (long long)sms * per_sm;
+    g.sweep = (int)(max_tiles < gs ? (max_tiles > 0 ? max_tiles : 1) : gs);
+    const int gf = sms * 8;
+    g.finalize = max_nblocks < gf ? (max_nblocks > 0 ? max_nblocks : 1) : gf;
+    return g;
 }
 
 cudaError_t prepare_sweep_rc()
@@ -802,21 +839,18 @@ cudaError_t prepare_sweep()
                                 (int)sweep_smem_bytes<__nv_bfloat16>());
 }
 
-void launch_round(const Inst& p, const int2* work, long long ntiles, int q_mode, cudaStream_t s,
-                  cudaEvent_t* ev)
+void launch_round(const Inst* tab, const int4* work, const int2* nbl, const Sched* sched, const RoundGrid& g,
+                  int q_mode, cudaStream_t s, cudaEvent_t* ev)
 {
-    const int grid = sweep_grid(ntiles);
     if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
-    if (q_mode == 2) {
-        const int grid_rc = (grid + SWEEP_CTAS_PER_SM - 1) / SWEEP_CTAS_PER_SM;   // one CTA per SM
-        k_sweep_rc<<<grid_rc, RC_THREADS, rc_smem_bytes(), s>>>(p, work, ntiles);
-    }
+    if (q_mode == 2)
+        k_sweep_rc<<<g.sweep, RC_THREADS, rc_smem_bytes(), s>>>(tab, work, sched);
     else if (q_mode == 1)
-        k_sweep<__nv_bfloat16><<<grid, SWEEP_THREADS, sweep_smem_bytes<__nv_bfloat16>(), s>>>(p, work, ntiles);
+        k_sweep<__nv_bfloat16><<<g.sweep, SWEEP_THREADS, sweep_smem_bytes<__nv_bfloat16>(), s>>>(tab, work, sched);
     else
-        k_sweep<float><<<grid, SWEEP_THREADS, sweep_smem_bytes<float>(), s>>>(p, work, ntiles);
+        k_sweep<float><<<g.sweep, SWEEP_THREADS, sweep_smem_bytes<float>(), s>>>(tab, work, sched);
     if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
-    k_finalize<<<(p.n + 31) / 32, 256, 0, s>>>(p);
+    k_finalize<<<g.finalize, 256, 0, s>>>(tab, nbl, sched);
 }
 
 void launch_get_pairs(const Inst& p, const long long* ij, long long cnt, float4* out, cudaStream_t s)

@@ -65,6 +65,26 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("y", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("m", ctypes.c_int64), ("gamma", ctypes.c_double), ("C", ctypes.c_double)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_void_p), ("residual_inf", ctypes.c_double),
+                ("dual_objective", ctypes.c_double), ("n_support", ctypes.c_int64),
+                ("iters_done", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("refine_passes", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "alpha"}
+
+
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_members", ctypes.c_int32),
+                ("iters", ctypes.c_int32), ("tol", ctypes.c_double), ("opts", Opts)]
+
+
 _lib = None
 
 
@@ -103,6 +123,12 @@ def load():
         "gabp_svm_destroy": (st, [V]),
         "gabp_decision_noalloc": (st, [V, V, V, I64, I64, V, I64, D, D, V, V]),
         "gabp_selftest_bounded_wait": (st, [I64]),
+        "gabp_batch_solve": (st, [P(Problem), I64, P(Opts), I32, D, P(Result)]),
+        "gabp_server_create": (st, [P(ServerCfg), P(V)]),
+        "gabp_server_submit": (st, [V, P(Problem), V, P(I64)]),
+        "gabp_server_step": (st, [V, P(I32), P(I32), P(I32)]),
+        "gabp_server_poll": (st, [V, I64, P(Result), P(I32)]),
+        "gabp_server_destroy": (st, [V]),
         "gabp_last_error": (ctypes.c_char_p, []),
         "gabp_version": (I32, []),
     }
@@ -281,6 +307,84 @@ def selftest_bounded_wait(limit_ns: int) -> int:
     """Status of gabp_selftest_bounded_wait (GABP_ETIMEOUT when the wait works)."""
     rc = load().gabp_selftest_bounded_wait(int(limit_ns))
     return rc
+
+
+def batch_solve(problems, iters: int, tol: float, **opts):
+    """gabp_batch_solve over a list of workloads.Problem-like objects (numpy
+    X float32/float64, y).  Returns (list of alpha arrays, list of result dicts,
+    overall status)."""
+    probs = (Problem * len(problems))()
+    keep, alphas = [], []
+    f64 = None
+    for k, p in enumerate(problems):
+        X = np.ascontiguousarray(p.X)
+        if f64 is None:
+            f64 = X.dtype == np.float64
+        X = X.astype(np.float64 if f64 else np.float32, copy=False)
+        y = np.ascontiguousarray(p.y, dtype=np.float32)
+        keep += [X, y]
+        probs[k] = Problem(X.ctypes.data, y.ctypes.data, X.shape[0], X.shape[1], float(p.gamma), float(p.C))
+        alphas.append(np.empty(X.shape[0], dtype=np.float32))
+    res = (Result * len(problems))()
+    for k in range(len(problems)):
+        res[k].alpha = alphas[k].ctypes.data
+    o = opts_default(**opts)
+    o.x_dtype = 1 if f64 else 0
+    rc = load().gabp_batch_solve(probs, len(problems), ctypes.byref(o), int(iters), float(tol), res)
+    if rc not in (OK, ENUMERIC):
+        _check(rc)
+    return alphas, [res[k].as_dict() for k in range(len(problems))], rc
+
+
+class Server:
+    """Continuous-batching server (gabp_server_*), host-pointer mode."""
+
+    def __init__(self, iters=200, tol=1e-6, budget_bytes=0, max_members=64, **opts):
+        cfg = ServerCfg()
+        cfg.hbm_budget_bytes = int(budget_bytes)
+        cfg.max_members = int(max_members)
+        cfg.iters = int(iters)
+        cfg.tol = float(tol)
+        cfg.opts = opts_default(**opts)
+        self.h = ctypes.c_void_p()
+        _check(load().gabp_server_create(ctypes.byref(cfg), ctypes.byref(self.h)))
+        self._keep = {}
+
+    def submit(self, X, y, gamma, C):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        alpha = np.empty(X.shape[0], dtype=np.float32)
+        pr = Problem(X.ctypes.data, y.ctypes.data, X.shape[0], X.shape[1], float(gamma), float(C))
+        t = ctypes.c_int64()
+        _check(load().gabp_server_submit(self.h, ctypes.byref(pr), ctypes.c_void_p(alpha.ctypes.data),
+                                         ctypes.byref(t)))
+        self._keep[t.value] = (X, y, alpha)
+        return t.value
+
+    def step(self):
+        a, q, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load().gabp_server_step(self.h, ctypes.byref(a), ctypes.byref(q), ctypes.byref(c)))
+        return a.value, q.value, c.value
+
+    def poll(self, ticket):
+        r = Result()
+        d = ctypes.c_int32()
+        _check(load().gabp_server_poll(self.h, int(ticket), ctypes.byref(r), ctypes.byref(d)))
+        if not d.value:
+            return None
+        X, y, alpha = self._keep.pop(ticket)
+        return alpha, r.as_dict()
+
+    def close(self):
+        if self.h:
+            load().gabp_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def svm_destroy(h):

@@ -1,0 +1,109 @@
+"""Batched and served forms against the single-instance solver and the oracle.
+
+* every instance of a batch (uneven n, m, C, gamma; one persistent launch per
+  round for all of them) gives the same alpha as solving it alone, and
+  matches the FP64 oracle at the FP32 bars;
+* per-instance stop tests: instances converge after different numbers of
+  rounds, each at its own first round with ||r||_inf < tol;
+* the precision form (BF16 tensor-core Q + refinement) reaches the FP64
+  fixed point in the batch;
+* the server: requests admitted over several steps (continuous batching)
+  give the same results as alone.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0810_1648_gb300 import gabp, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_0810_1648_gb300 import build as gbuild
+    gbuild.build()
+
+
+def _mix(count, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n = int(rng.integers(130, 700))
+        m = int(rng.choice([8, 32, 128]))
+        C = float(rng.choice([0.1, 1.0, 10.0]))
+        g = float(rng.choice([0.5, 1.0, 2.0])) / m
+        p = workloads.mixture(n, m, seed=seed * 100 + k, gamma=g, C=C)
+        out.append(p)
+    return out
+
+
+def test_batch_equals_single_and_oracle():
+    probs = _mix(10, 1)
+    alphas, res, rc = gabp.batch_solve(probs, 25, 0.0, chunk=8)
+    assert rc == gabp.OK
+    for p, a, r in zip(probs, alphas, res):
+        assert r["status"] == 0 and r["iters_done"] == 25
+        single, _, _ = gabp.GabpSVM(p.X, p.y, p.gamma, p.C).solve(25, 0.0)
+        np.testing.assert_array_equal(a, single)
+        _, ro = oracle.solve_svm(p.X.astype(np.float64), p.y.astype(np.float64), p.gamma, p.C, iters=25)
+        assert np.max(np.abs(a - ro.alpha(p.C))) <= 1e-4 * p.C
+        assert np.max(np.abs(ro.mu)) > 0
+
+
+def test_batch_per_instance_convergence_and_autotune():
+    probs = _mix(8, 2)
+    alphas, res, rc = gabp.batch_solve(probs, 300, 1e-6, chunk=0)
+    assert rc == gabp.OK
+    ks = []
+    for p, a, r in zip(probs, alphas, res):
+        assert r["converged"] == 1 and r["residual_inf"] < 1e-6
+        _, ro = oracle.solve_svm(p.X.astype(np.float64), p.y.astype(np.float64), p.gamma, p.C,
+                                 iters=300, tol=1e-6)
+        ks.append(ro.kstar)
+        assert abs(r["iters_done"] - (ro.kstar + 1)) <= 1, (r["iters_done"], ro.kstar)
+        assert np.max(np.abs(a - ro.alpha(p.C))) <= 1e-4 * p.C
+    assert len(set(ks)) > 1      # the instances did stop at different rounds
+
+
+def test_batch_precision_form_refined():
+    probs = _mix(6, 3)
+    alphas, res, rc = gabp.batch_solve(probs, 300, 1e-6, chunk=8, q_mode=gabp.Q_BF16, refine=8)
+    assert rc == gabp.OK
+    for p, a, r in zip(probs, alphas, res):
+        Qx = oracle.build_q(p.X.astype(np.float64), p.y.astype(np.float64), p.gamma, p.C)
+        ref = np.linalg.solve(Qx, np.ones(p.n))
+        assert r["residual_inf"] < 1e-6 and r["refine_passes"] >= 1
+        assert np.max(np.abs(a - np.clip(ref, 0, p.C))) <= 1e-4 * p.C
+
+
+def test_server_results_equal_alone():
+    probs = _mix(9, 4)
+    srv = gabp.Server(iters=300, tol=1e-6, max_members=4, chunk=4)
+    tickets = []
+    # arrivals spread over steps: 3 now, then 2 per step
+    for p in probs[:3]:
+        tickets.append(srv.submit(p.X, p.y, p.gamma, p.C))
+    pending = list(probs[3:])
+    out = {}
+    for _ in range(2000):
+        if pending:
+            for p in pending[:2]:
+                tickets.append(srv.submit(p.X, p.y, p.gamma, p.C))
+            pending = pending[2:]
+        active, queued, done = srv.step()
+        assert active <= 4
+        for t in tickets:
+            if t not in out:
+                r = srv.poll(t)
+                if r is not None:
+                    out[t] = r
+        if len(out) == len(probs) and not pending:
+            break
+    assert len(out) == len(probs)
+    for t, p in zip(tickets, probs):
+        a, r = out[t]
+        assert r["status"] == 0 and r["converged"] == 1
+        single, _, _ = gabp.GabpSVM(p.X, p.y, p.gamma, p.C, chunk=4).solve(300, 1e-6)
+        np.testing.assert_array_equal(a, single)
+    srv.close()
