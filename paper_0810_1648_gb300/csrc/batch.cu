@@ -417,7 +417,8 @@ class Engine {
         M.res.dual_objective = f3[1];
         M.res.n_support = (int64_t)std::llround(f3[2]);
         M.res.iters_done = c.t;
-        M.res.converged = f3[0] < M.tol ? 1 : 0;
+        // the stop test's own decision (Step 3), or the accurate residual after refinement
+        M.res.converged = M.refining ? (f3[0] < M.tol ? 1 : 0) : c.converged;
         M.res.refine_passes = M.refine_done;
         if (c.status == ST_ENUMERIC) M.res.status = GABP_ENUMERIC;
         else if (c.status == ST_EINVAL) M.res.status = GABP_EINVAL;
