@@ -226,6 +226,101 @@ def run_profile_small(args):
     return 0
 
 
+def run_batch(args):
+    """512 uneven instances (32 data sets x C in {0.1,1,10,100} x gamma in
+    {0.1,0.5,1,2}/m, n log-uniform in [200, 4000], m in {8,32,128,256}) solved
+    together to ||r||_inf < 1e-6 or 200 rounds: plain FP32 vs the BF16
+    tensor-core form with refinement to the same tolerance.  Metric: solves/s."""
+    import torch
+
+    from paper_0810_1648_gb300 import build as gbuild
+    from paper_0810_1648_gb300 import gabp
+    if not os.path.exists(gabp.LIB_PATH):
+        gbuild.build()
+    probs = workloads.batch_grid()
+    stream = torch.cuda.Stream()
+    out = {}
+    for mode, kw in (("f32", dict(q_mode=0)), ("bf16_refined", dict(q_mode=1, refine=8))):
+        for _ in range(args.warmup):
+            gabp.batch_solve(probs, 200, 1e-6, chunk=0, stream=stream.cuda_stream, **kw)
+        times, last = [], None
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            alphas, res, rc = gabp.batch_solve(probs, 200, 1e-6, chunk=0, stream=stream.cuda_stream, **kw)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            last = res
+        conv = sum(r["converged"] for r in last)
+        out[mode] = {"solves_per_s": len(probs) / float(np.median(times)), "ms_per_batch": 1e3 * float(np.median(times)),
+                     "converged": conv, "max_residual": max(r["residual_inf"] for r in last),
+                     "mean_rounds": float(np.mean([r["iters_done"] for r in last]))}
+    n2 = sum(p.n * p.n for p in probs)
+    line = {"metric": METRIC, "value": out["bf16_refined"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
+            "config": {"workload": "batched form: 512 instances, 32 mixture data sets x C {0.1,1,10,100} x "
+                                   "gamma {0.1,0.5,1,2}/m, n log-uniform [200,4000], m in {8,32,128,256}, "
+                                   "tol 1e-6 or 200 rounds, one persistent launch per round, autotuned schedule",
+                       "instances": len(probs), "sum_n2": n2},
+            "modes": out, "bf16_over_f32": out["bf16_refined"]["solves_per_s"] / out["f32"]["solves_per_s"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Poisson stream of SVM-training requests replayed in real time through
+    the continuous-batching server; reports p50/p99 latency and solves/s."""
+    from paper_0810_1648_gb300 import build as gbuild
+    from paper_0810_1648_gb300 import gabp
+    if not os.path.exists(gabp.LIB_PATH):
+        gbuild.build()
+    reqs = workloads.poisson_requests(rate=args.rate, duration=args.duration, seed=7)
+    # request data: row/column slices of one seeded mixture pool (labels from it)
+    pool = workloads.mixture(50000, 512, seed=7)
+    rng = np.random.default_rng(8)
+    starts = [int(rng.integers(0, 50000 - r.n + 1)) for r in reqs]
+    srv = gabp.Server(iters=200, tol=1e-6, max_members=args.max_members, q_mode=Q_MODES[args.q_mode],
+                      refine=8 if args.q_mode != "f32" else 0, chunk=4)
+    t0 = time.perf_counter()
+    sub, lat, nxt = {}, [], 0
+    done_n = 0
+    while done_n < len(reqs):
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and reqs[nxt].t_arrive <= now:
+            r = reqs[nxt]
+            X = np.ascontiguousarray(pool.X[starts[nxt]:starts[nxt] + r.n, :r.m])
+            y = pool.y[starts[nxt]:starts[nxt] + r.n]
+            if abs(float(y.sum())) == r.n:          # need both classes
+                y = y.copy(); y[0] = -y[0]
+            t = srv.submit(X, y, 1.0 / r.m, r.C)
+            sub[t] = r.t_arrive
+            nxt += 1
+        active, queued, completed = srv.step()
+        for t in list(sub):
+            res = srv.poll(t)
+            if res is not None:
+                lat.append(time.perf_counter() - t0 - sub.pop(t))
+                done_n += 1
+        if active == 0 and queued == 0 and nxt < len(reqs):
+            time.sleep(max(0.0, min(0.01, reqs[nxt].t_arrive - (time.perf_counter() - t0))))
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat = np.array(lat)
+    line = {"metric": METRIC, "value": len(reqs) / wall, "unit": "solves/s", "n_gpus": 1, "steps": 1,
+            "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.q_mode == "f32" else "bf16+f32", "data": "synthetic",
+            "config": {"workload": f"serving form: Poisson arrivals rate {args.rate}/s for {args.duration} s, "
+                                   "n log-uniform [500,50000], m log-uniform [16,512], C log-uniform [0.1,100], "
+                                   "gamma 1/m, tol 1e-6 or 200 rounds, admission by device memory",
+                       "requests": len(reqs), "q_mode": args.q_mode, "max_members": args.max_members},
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "max": float(lat.max())},
+            "wall_s": wall, "offered_per_s": args.rate}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -388,7 +483,11 @@ def main():
     ap.add_argument("--ref-sweeps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="plain_large", choices=["plain_large", "precision_large"])
+    ap.add_argument("--workload", default="plain_large",
+                    choices=["plain_large", "precision_large", "batch_grid", "serve"])
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--duration", type=float, default=60.0)
+    ap.add_argument("--max-members", type=int, default=64)
     ap.add_argument("--q-mode", default=None, choices=list(Q_MODES))
     ap.add_argument("--profile-small", action="store_true",
                     help="one 3-round solve at n=6144 (for ncu captures), no JSON bench line")
@@ -397,6 +496,10 @@ def main():
         args.q_mode = "f32" if args.workload == "plain_large" else "bf16"
     if args.profile_small:
         return run_profile_small(args)
+    if args.workload == "batch_grid":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
