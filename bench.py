@@ -50,8 +50,7 @@ PRECISION_WORKLOAD = {
     "n": 100000, "m": 64, "sweeps_per_step": ROUNDS,
     "l2": "no flush: every sweep streams 80 GB of messages, far above the 129 MB L2",
 }
-# Algorithmic bytes per unordered pair of one pair-sweep launch: read 16 B of
-# messages + the stored Q entry, write 16 B; the first round reads no messages.
+# Stored bytes of one Q entry per unordered pair, by Q mode.
 Q_BYTES = {"f32": 4, "bf16": 2, "recompute": 0}
 Q_MODES = {"f32": 0, "bf16": 1, "recompute": 2}
 
@@ -391,8 +390,12 @@ def run_ours(args):
     # roofline of the dominant kernel (the pair sweep), timed live by events
     pairs = n * (n - 1) // 2
     nz = prof["sweep_launches_zero_state"]
+    nf = prof["sweep_launches_p_frozen"]
     nl = prof["sweep_launches"]
-    alg_bytes = pairs * ((32 + qb) * (nl - nz) + (16 + qb) * nz)
+    # per pair: round 0 writes P and H (16 B); later rounds read and write
+    # both (32 B) until the P messages reach their fixed point, then read P and
+    # H and write H (24 B); every round reads the stored Q entry (qb B)
+    alg_bytes = pairs * ((32 + qb) * (nl - nz - nf) + (24 + qb) * nf + (16 + qb) * nz)
     sweep_s = prof["sweep_ms"] / 1e3
     achieved = alg_bytes / sweep_s / 1e9 if sweep_s > 0 else None
     peaks = _peaks()
@@ -405,7 +408,8 @@ def run_ours(args):
             "frac": (achieved / peak) if achieved else None, "traffic": traffic,
             "kernel": {"f32": "k_sweep<float>", "bf16": "k_sweep<bf16>", "recompute": "k_sweep_rc"}[args.q_mode]
                       + " (pair sweep)", "peak_source": peak_src,
-            "bytes_per_pair": 32 + qb,
+            "bytes_per_pair": {"round0": 16 + qb, "p_live": 32 + qb, "p_frozen": 24 + qb},
+            "launches_p_frozen": nf,
             "algorithmic_bytes_per_launch": alg_bytes / max(nl, 1),
             "avg_launch_ms": prof["sweep_ms"] / max(nl, 1), "launches_timed": nl,
             "share_of_step": (prof["sweep_ms"] / ms) if ms > 0 else None}

@@ -254,6 +254,8 @@ GABP_API gabp_status gabp_server_destroy(gabp_server_t s);
 typedef struct {
     int64_t sweep_launches;            /* pair sweeps timed */
     int64_t sweep_launches_zero_state; /* of which the first round (messages all 0, not read) */
+    int64_t sweep_launches_p_frozen;   /* of which rounds after the P messages reached their fixed
+                                          point (P read, not written) */
     double  sweep_ms;                  /* their summed device time */
     int64_t kernel_launches;           /* all kernels launched by this handle */
 } gabp_svm_profile;

@@ -108,7 +108,7 @@ Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_m
     p.vec = align_up((size_t)npad * sizeof(float), 256);
     p.agg = align_up((size_t)6 * npad * sizeof(float), 256);
     p.part = align_up((size_t)4 * Nt * n * sizeof(float), 256);
-    p.state = align_up((size_t)ntiles * TT * sizeof(float4), 256);
+    p.state = 2 * align_up((size_t)ntiles * TT * sizeof(float2), 256);
     p.q = q_mode == GABP_Q_F32 ? align_up((size_t)ntiles * TT * sizeof(float), 256)
         : q_mode == GABP_Q_BF16 ? align_up((size_t)ntiles * TT * sizeof(__nv_bfloat16), 256)
         : 0;
@@ -269,6 +269,7 @@ gabp_status run_rounds(gabp_svm_t h, int iters, double tol, Ctrl* out)
                     h->prof.sweep_ms += ms;
                     h->prof.sweep_launches += 1;
                     if (t_before + k == 0) h->prof.sweep_launches_zero_state += 1;
+                    if (h->hctrl->p_frozen && t_before + k >= h->hctrl->t_frozen) h->prof.sweep_launches_p_frozen += 1;
                 }
             }
             t_before = h->hctrl->t;
@@ -410,7 +411,8 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     h->r32 = (float*)take(pl.vec);
     p.agg = (float*)take(pl.agg);
     p.part = (float*)take(pl.part);
-    p.state = (float4*)take(pl.state);
+    p.Pst = (float2*)take(pl.state / 2);
+    p.Hst = (float2*)take(pl.state / 2);
     p.qstore = pl.q ? take(pl.q) : nullptr;
     h->work = (int4*)take(pl.work);
     {
@@ -488,7 +490,9 @@ gabp_status gabp_svm_solve(gabp_svm_t h, int32_t iters, double tol, float* alpha
     if ((long long)t0 + (long long)iters * (1 + h->opts.refine) >= (long long)INT_MAX)
         return fail(GABP_EINVAL, "too many rounds");
     Ctrl c{};
-    if (gabp_status st = run_rounds(h, iters, tol, &c)) return st;
+    // With refinement ahead, the BF16 solve only needs to reach about the BF16
+    // error level of its matrix (1e-4) before the first correction.
+    if (gabp_status st = run_rounds(h, iters, refine ? std::max(tol, 1e-4) : tol, &c)) return st;
     h->kstar = c.kstar;
     const float* mu = p.agg + (size_t)(c.kstar & 1) * 3 * p.npad + 2 * (size_t)p.npad;
     int refine_done = 0;

@@ -37,6 +37,9 @@ namespace {
 
 size_t aup(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Residual at which a refined BF16 solve hands over to defect correction.
+constexpr double kRefineStart = 1e-4;
+
 // Device memory of one instance (one allocation), carved like the handle's.
 struct MemberPlan {
     size_t X, vec, agg, part, state, q, work, rhist, final3, blockbuf, xp, total;
@@ -52,7 +55,7 @@ MemberPlan member_plan(int64_t n, int64_t m, int q_mode)
     p.vec = aup(npad * 4, 256);
     p.agg = aup(6 * npad * 4, 256);
     p.part = aup((size_t)4 * Nt * n * 4, 256);
-    p.state = aup((size_t)nt * TT * 16, 256);
+    p.state = 2 * aup((size_t)nt * TT * 8, 256);
     p.q = q_mode == 0 ? aup((size_t)nt * TT * 4, 256) : q_mode == 1 ? aup((size_t)nt * TT * 2, 256) : 0;
     p.work = aup((size_t)nt * sizeof(int4), 256);
     p.rhist = 0;
@@ -140,6 +143,7 @@ class Engine {
     int2* d_nbl = nullptr;
     Sched* d_sched = nullptr;
     Ctrl* h_ctrl = nullptr;       // pinned mirror
+    double* h_f3 = nullptr;       // pinned {residual, objective, #SV} per slot
     std::vector<Member> mem;
     RoundGrid grid{};
     int ctas_per_sm = 0;
@@ -159,6 +163,7 @@ class Engine {
         if (stream) cudaStreamSynchronize(stream);
         if (d_tab) cudaFree(d_tab);
         if (h_ctrl) cudaFreeHost(h_ctrl);
+        if (h_f3) cudaFreeHost(h_f3);
         if (side) cudaStreamDestroy(side);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
@@ -206,6 +211,7 @@ class Engine {
         EK(cudaMemsetAsync(d_ctrl, 0, b_ctrl, stream));
         EK(cudaMemsetAsync(d_sched, 0, sizeof(Sched), stream));
         EK(cudaMallocHost((void**)&h_ctrl, (size_t)cap_members * sizeof(Ctrl)));
+        EK(cudaMallocHost((void**)&h_f3, (size_t)cap_members * 3 * sizeof(double)));
         mem.resize((size_t)cap_members);
         set_grid(0);
         EK(cudaStreamSynchronize(stream));
@@ -267,7 +273,8 @@ class Engine {
         take(pl.vec);
         p.agg = (float*)take(pl.agg);
         p.part = (float*)take(pl.part);
-        p.state = (float4*)take(pl.state);
+        p.Pst = (float2*)take(pl.state / 2);
+        p.Hst = (float2*)take(pl.state / 2);
         p.qstore = pl.q ? take(pl.q) : nullptr;
         M.work = (int4*)take(pl.work);
         M.final3 = (double*)take(pl.final3);
@@ -329,7 +336,10 @@ class Engine {
     {
         Member& M = mem[(size_t)slot];
         EK(cudaStreamWaitEvent(stream, M.ready, 0));
-        launch_begin(d_tab + slot, 1, iters, tol, stream);
+        // With refinement ahead, the BF16 solve only needs to reach about the
+        // BF16 error level of its matrix before the first correction.
+        const double t0 = (q_mode != 0 && M.refine_left > 0) ? std::max(tol, kRefineStart) : tol;
+        launch_begin(d_tab + slot, 1, iters, t0, stream);
         ++launches;
         M.formed = true;
         M.active = true;
@@ -396,23 +406,16 @@ class Engine {
         return GABP_OK;
     }
 
-    // Final residual / objective / alpha of a stopped instance; copies alpha out.
+    // Records the results of a stopped instance from its final residual /
+    // objective / #SV (in h_f3) and queues the copy of alpha to the caller.
     gabp_status finish(int slot)
     {
         Member& M = mem[(size_t)slot];
         const Ctrl& c = h_ctrl[slot];
-        const float* mu = M.refining
-                              ? M.mu_acc
-                              : M.inst.agg + (size_t)(c.kstar & 1) * 3 * M.inst.npad + 2 * (size_t)M.inst.npad;
-        launch_final(M.inst, M.work, M.ntiles, mu, M.alpha, M.final3, M.blockbuf, (float)sv_threshold, nullptr,
-                     stream);
-        launches += 3;
-        double f3[3];
-        EK(cudaMemcpyAsync(f3, M.final3, sizeof f3, cudaMemcpyDeviceToHost, stream));
+        const double* f3 = h_f3 + 3 * (size_t)slot;
         if (M.out_alpha)
             EK(cudaMemcpyAsync(M.out_alpha, M.alpha, (size_t)M.inst.n * 4,
                                M.out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream));
-        EK(cudaStreamSynchronize(stream));
         M.res.residual_inf = f3[0];
         M.res.dual_objective = f3[1];
         M.res.n_support = (int64_t)std::llround(f3[2]);
@@ -431,41 +434,62 @@ class Engine {
     }
 
     // After a chunk: instances that stopped either start a refinement pass
-    // (precision form) or finish.  Returns the number still running.
+    // (precision form) or finish.  All their device work is queued first and
+    // waited for once.  Returns the number still running.
     gabp_status advance(int* running, std::vector<int>* finished = nullptr)
     {
         int run = 0;
+        std::vector<int> stopped;
         for (int k = 0; k < cap_members; ++k) {
             Member& M = mem[(size_t)k];
             if (!M.used || !M.active) continue;
+            if (!h_ctrl[k].done) { ++run; continue; }
+            stopped.push_back(k);
+        }
+        if (stopped.empty()) { *running = run; return GABP_OK; }
+        // 1. final residual (and, in the precision form, the refined means)
+        for (int k : stopped) {
+            Member& M = mem[(size_t)k];
             const Ctrl& c = h_ctrl[k];
-            if (!c.done) { ++run; continue; }
-            if (c.status == 0 && q_mode != 0 && (M.refining || M.refine_left > 0)) {
-                // Defect correction on the FP32-Gram residual (as in the handle's
-                // solve): accumulate the means (or the correction), form
-                // r = 1 - Q32 mu_acc and, while it is above tol, solve for the
-                // next correction with the P messages kept.
+            const bool ref = c.status == 0 && q_mode != 0 && (M.refining || M.refine_left > 0);
+            const float* mu = M.inst.agg + (size_t)(c.kstar & 1) * 3 * M.inst.npad + 2 * (size_t)M.inst.npad;
+            if (ref) {
+                // Defect correction on the FP32-Gram residual: accumulate the
+                // means (or the correction) and form r = 1 - Q32 mu_acc.
                 launch_axpy_mu(M.inst, c.kstar, M.mu_acc, M.refining ? 0 : 1, stream);
                 if (M.refining) ++M.refine_done;
                 M.refining = true;
-                launch_final(M.inst, M.work, M.ntiles, M.mu_acc, M.alpha, M.final3, M.blockbuf,
-                             (float)sv_threshold, M.r32, stream);
-                double f3[3];
-                EK(cudaMemcpyAsync(f3, M.final3, sizeof f3, cudaMemcpyDeviceToHost, stream));
-                EK(cudaStreamSynchronize(stream));
-                launches += 4;
-                if (f3[0] >= M.tol && M.refine_left > 0) {
-                    --M.refine_left;
-                    launch_refine_rhs(M.inst, M.r32, stream);
-                    launch_begin(d_tab + k, 1, M.iters, std::max(M.tol * 0.5, 1e-2 * f3[0]), stream);
-                    launches += 2;
-                    ++run;
-                    continue;
-                }
+                mu = M.mu_acc;
+                ++launches;
+            } else if (M.refining) {
+                mu = M.mu_acc;
+            }
+            launch_final(M.inst, M.work, M.ntiles, mu, M.alpha, M.final3, M.blockbuf, (float)sv_threshold,
+                         ref ? M.r32 : nullptr, stream);
+            launches += 3;
+            EK(cudaMemcpyAsync(h_f3 + 3 * (size_t)k, M.final3, 3 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+        }
+        EK(cudaStreamSynchronize(stream));
+        // 2. next correction pass, or done
+        bool copies = false;
+        for (int k : stopped) {
+            Member& M = mem[(size_t)k];
+            const Ctrl& c = h_ctrl[k];
+            const double rn = h_f3[3 * (size_t)k];
+            if (c.status == 0 && M.refining && rn >= M.tol && M.refine_left > 0) {
+                // solve Q_bf d = r with the P messages kept (H restarted)
+                --M.refine_left;
+                launch_refine_rhs(M.inst, M.r32, stream);
+                launch_begin(d_tab + k, 1, M.iters, std::max(M.tol * 0.5, 1e-2 * rn), stream);
+                launches += 2;
+                ++run;
+                continue;
             }
             if (gabp_status st = finish(k)) return st;
+            copies = true;
             if (finished) finished->push_back(k);
         }
+        if (copies) EK(cudaStreamSynchronize(stream));
         *running = run;
         return GABP_OK;
     }
@@ -610,7 +634,8 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
         if (gabp_status st = E.activate((int)k, iters, tol)) return st;
     if (o.chunk <= 0) {
         if (gabp_status st = E.autotune(iters)) return st;
-        for (int64_t k = 0; k < count; ++k) gabp::launch_begin(E.d_tab + k, 1, iters, tol, E.stream);
+        const double t0 = (o.q_mode != 0 && o.refine > 0) ? std::max(tol, 1e-4) : tol;
+        for (int64_t k = 0; k < count; ++k) gabp::launch_begin(E.d_tab + k, 1, iters, t0, E.stream);
     } else {
         E.chunk = o.chunk;
     }

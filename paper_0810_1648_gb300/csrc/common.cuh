@@ -7,9 +7,12 @@
 // pair (r, c) of the tile is node pair (I*T + r, J*T + c).  On diagonal
 // tiles only c > r is used; on edge tiles only nodes < n.
 //
-// Per-pair message state (information form of Algorithm 2): one float4
-//   {P_ij, P_ji, H_ij, H_ji},  i = I*T + r < j = J*T + c,
-// where P_ij is the precision of the message i -> j and H_ij = P_ij mu_ij.
+// Per-pair message state (information form of Algorithm 2), two arrays in
+// the tile layout: Pst = float2 {P_ij, P_ji} and Hst = float2 {H_ij, H_ji},
+// i = I*T + r < j = J*T + c, where P_ij is the precision of the message
+// i -> j and H_ij = P_ij mu_ij.  They are separate so that, once the P
+// recursion (which does not depend on b) sits at its floating-point fixed
+// point, a round reads P and streams only H.
 //
 // Per-node partial sums: every kernel that reduces over pairs writes, for
 // node x and tile index k along the other axis, one value into
@@ -48,6 +51,9 @@ struct Ctrl {
     int converged;            // 1 if the residual test stopped the solve
     int status;               // first error (Status), 0 if none
     int zero_h;               // next sweep treats the H messages as 0 (restart of the b-dependent part)
+    int p_frozen;             // P messages at their fixed point: sweeps no longer write them
+    int p_changed;            // some P message changed in the current round
+    int t_frozen;             // first round run with frozen P (valid when p_frozen)
     long long bad_index;      // offending node (or pair row) of the first error
     unsigned int blocks_done; // last-block-done counter of the finalize kernel
     unsigned long long rmax_bits;  // running max |r_i| of the round (bits of a nonnegative double)
@@ -66,7 +72,8 @@ struct Inst {
     const float* y;   // labels +-1
     const float* b;   // right-hand side (ones for the SVM)
     float* qdiag;     // Q_ii
-    float4* state;    // ntiles * TT messages
+    float2* Pst;      // ntiles * TT precision messages {P_ij, P_ji}
+    float2* Hst;      // ntiles * TT information messages {H_ij, H_ji}
     void* qstore;     // ntiles * TT values of Q (float or bf16), or nullptr
     float* agg;       // [2][3][npad]: double-buffered {Ptilde, htilde, mutilde}
     float* part;      // [4][Nt][n] partial sums

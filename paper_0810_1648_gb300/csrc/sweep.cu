@@ -16,7 +16,8 @@
 //            Step-3 test ||r(t)||_inf < tol in the last CTA to finish.
 //
 // The sweep is bound by HBM bandwidth: per pair it reads 16 B of messages and
-// 4 B of Q (2 B in BF16) and writes 16 B.  Messages and Q arrive in shared
+// 4 B of Q (2 B in BF16) and writes 16 B; once the P messages sit at their
+// fixed point it writes only the 8 B of H.  Messages and Q arrive in shared
 // memory through bulk copies issued by a producer warp well ahead of use;
 // consumer warp w takes one row of each 8-row chunk, lane l the columns l,
 // l+32, l+64, l+96, so every message store of a warp covers 512 contiguous
@@ -58,7 +59,8 @@ constexpr int RC = NWARPS;                    // rows per chunk, one per consume
 constexpr int STAGES = 4;
 constexpr int SWEEP_THREADS = NTHREADS + 32;  // + one producer warp
 constexpr int SWEEP_CTAS_PER_SM = 2;
-constexpr size_t STATE_CHUNK = (size_t)RC * T * sizeof(float4);   // 16 KB
+constexpr size_t PCHUNK = (size_t)RC * T * sizeof(float2);        // 8 KB of P messages
+constexpr size_t STATE_CHUNK = 2 * PCHUNK;                          // + 8 KB of H messages
 
 struct SweepTail {
     unsigned long long full[STAGES], empty[STAGES];
@@ -67,7 +69,7 @@ struct SweepTail {
     float rp[T], rh[T], rr[T];
 };
 
-// Ring stage = messages of RC rows, then (stored Q) the Q values of those rows.
+// Ring stage = P messages of RC rows, their H messages, then (stored Q) their Q values.
 template <typename QT>
 struct QBytes { static constexpr size_t v = sizeof(QT); };
 template <>
@@ -97,7 +99,8 @@ __device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, con
         const int n = p.n, I = w.y, J = w.z;
         const int rows = min(T, n - I * T), cols = min(T, n - J * T);
         const bool diag = (I == J);
-        const float4* st = p.state + (size_t)w.w * TT;
+        const float2* sp = p.Pst + (size_t)w.w * TT;
+        const float2* sh = p.Hst + (size_t)w.w * TT;
         const unsigned char* qt = QB ? static_cast<const unsigned char*>(p.qstore) + (size_t)w.w * TT * QB : nullptr;
         const int nch = (rows + RC - 1) / RC;
         for (int c = 0; c < nch; ++c) {
@@ -111,10 +114,13 @@ __device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, con
             const int r0 = c * RC, nr = min(RC, rows - r0);
             if (!diag && cols == T) {
                 const uint32_t bq = (uint32_t)(nr * T * QB);
-                const uint32_t bs = zero ? 0u : (uint32_t)(nr * T * sizeof(float4));
-                mbar_arrive_expect_tx(bar, bq + bs);
+                const uint32_t bs = zero ? 0u : (uint32_t)(nr * T * sizeof(float2));
+                mbar_arrive_expect_tx(bar, bq + 2 * bs);
                 if (QB) bulk_load(S + STATE_CHUNK, qt + (size_t)r0 * T * QB, bq, bar, pol);
-                if (!zero) bulk_load(S, st + (size_t)r0 * T, bs, bar, pol);
+                if (!zero) {
+                    bulk_load(S, sp + (size_t)r0 * T, bs, bar, pol);
+                    bulk_load(S + PCHUNK, sh + (size_t)r0 * T, bs, bar, pol);
+                }
             } else {
                 // per row: columns [c0, c1) with c0, c1 multiples of 8 (16-byte
                 // granules of both arrays) covering the pairs the row owns
@@ -123,7 +129,7 @@ __device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, con
                 for (int k = 0; k < nr; ++k) {
                     const int r = r0 + k, c0 = diag ? ((r + 1) & ~7) : 0;
                     if (c0 < c1 && (!diag || r + 1 < cols))
-                        bytes += (uint32_t)((c1 - c0) * (QB + (zero ? 0 : sizeof(float4))));
+                        bytes += (uint32_t)((c1 - c0) * (QB + (zero ? 0 : 2 * sizeof(float2))));
                 }
                 mbar_arrive_expect_tx(bar, bytes);
                 for (int k = 0; k < nr; ++k) {
@@ -132,9 +138,12 @@ __device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, con
                     if (QB)
                         bulk_load(S + STATE_CHUNK + ((size_t)k * T + c0) * QB, qt + ((size_t)r * T + c0) * QB,
                                   (uint32_t)((c1 - c0) * QB), bar, pol);
-                    if (!zero)
-                        bulk_load(S + ((size_t)k * T + c0) * sizeof(float4), st + (size_t)r * T + c0,
-                                  (uint32_t)((c1 - c0) * sizeof(float4)), bar, pol);
+                    if (!zero) {
+                        const size_t o = ((size_t)k * T + c0) * sizeof(float2);
+                        const uint32_t b2 = (uint32_t)((c1 - c0) * sizeof(float2));
+                        bulk_load(S + o, sp + (size_t)r * T + c0, b2, bar, pol);
+                        bulk_load(S + PCHUNK + o, sh + (size_t)r * T + c0, b2, bar, pol);
+                    }
                 }
             }
             if (++stage == STAGES) { stage = 0; phase ^= 1u; }
@@ -162,6 +171,8 @@ __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, co
         const int t = *(volatile const int*)&ctrl->t;
         const bool zero = (t == 0);   // Step 1: all messages 0, nothing to read
         const bool zero_h = *(volatile const int*)&ctrl->zero_h != 0;
+        const bool frozen = *(volatile const int*)&ctrl->p_frozen != 0;
+        bool changed = false;
         const float* agg = p.agg + (size_t)(t & 1) * 3 * p.npad;
         const int n = p.n;
         float* partP = p.part;
@@ -194,7 +205,8 @@ __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, co
             cM[k] = sm.col[2][c];
             aP[k] = aH[k] = aR[k] = 0.f;
         }
-        float4* st = p.state + (size_t)w.w * TT;
+        float2* gp = p.Pst + (size_t)w.w * TT;
+        float2* gh = p.Hst + (size_t)w.w * TT;
         const int nch = (rows + RC - 1) / RC;
         for (int ch = 0; ch < nch; ++ch) {
             if (!abort && !mbar_wait_warp(&sm.full[stage], phase)) {
@@ -204,7 +216,8 @@ __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, co
             const int r = ch * RC + cw;
             if (!abort && r < rows) {
                 const unsigned char* S = ring + (size_t)stage * SB;
-                const float4* Ss = reinterpret_cast<const float4*>(S) + (size_t)cw * T;
+                const float2* Sp = reinterpret_cast<const float2*>(S) + (size_t)cw * T;
+                const float2* Sh = reinterpret_cast<const float2*>(S + PCHUNK) + (size_t)cw * T;
                 const float rP = sm.row[0][r], rH = sm.row[1][r], rM = sm.row[2][r];
                 float sp = 0.f, sh = 0.f, sr = 0.f;
 #pragma unroll
@@ -212,8 +225,9 @@ __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, co
                     const int c = lane + 32 * k;
                     if (c < cols && (!diag || c > r)) {
                         const float q = qsrc.q(S, cw, r, c, it);
-                        float4 s = zero ? make_float4(0.f, 0.f, 0.f, 0.f) : Ss[c];  // {P_ij, P_ji, H_ij, H_ji}
-                        if (zero_h) { s.z = 0.f; s.w = 0.f; }
+                        const float2 pv = zero ? make_float2(0.f, 0.f) : Sp[c];   // {P_ij, P_ji}
+                        const float2 hv = (zero || zero_h) ? make_float2(0.f, 0.f) : Sh[c];   // {H_ij, H_ji}
+                        const float4 s = make_float4(pv.x, pv.y, hv.x, hv.y);
                         const float di = rP - s.y;      // Ptilde_i - P_ji
                         const float dj = cP[k] - s.x;   // Ptilde_j - P_ij
                         bad |= !(di > 0.f && di <= FLT_MAX && dj > 0.f && dj <= FLT_MAX);
@@ -223,7 +237,11 @@ __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, co
                         const float nPji = -q2 * ij;
                         const float nHij = -q * (rH - s.w) * ii;
                         const float nHji = -q * (cH[k] - s.z) * ij;
-                        __stcs(&st[r * T + c], make_float4(nPij, nPji, nHij, nHji));
+                        if (!frozen) {
+                            __stcs(&gp[r * T + c], make_float2(nPij, nPji));
+                            changed |= (nPij != pv.x) | (nPji != pv.y);
+                        }
+                        __stcs(&gh[r * T + c], make_float2(nHij, nHji));
                         sp += nPji;
                         sh += nHji;
                         sr = fmaf(q, cM[k], sr);
@@ -275,6 +293,9 @@ __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, co
             }
         }
         if (bad) record_error(ctrl, ST_ENUMERIC, (long long)I * T);
+        // P fixed-point detection: one flag per instance and round
+        if (__any_sync(0xffffffffu, changed) && lane == 0 && !*(volatile int*)&ctrl->p_changed)
+            atomicExch(&ctrl->p_changed, 1);
         ++it;
     }
 }
@@ -649,6 +670,14 @@ __global__ void __launch_bounds__(256)
             ctrl->done = 1;
             ctrl->kstar = t + 1;
         }
+        // No P message changed in this round: P is at its floating-point fixed
+        // point (its recursion does not involve b or H), so later rounds would
+        // rewrite the same values; they stop writing them.
+        if (!ctrl->p_frozen && t > 0 && atomicAdd(&ctrl->p_changed, 0) == 0) {
+            ctrl->p_frozen = 1;
+            ctrl->t_frozen = t + 1;
+        }
+        ctrl->p_changed = 0;
         ctrl->t = t + 1;
         ctrl->zero_h = 0;
         ctrl->rmax_bits = 0ull;
@@ -665,6 +694,8 @@ __global__ void k_reset(Inst p)
         Ctrl* c = p.ctrl;
         c->t = 0;
         c->zero_h = 0;
+        c->p_frozen = 0;
+        c->p_changed = 0;
         c->done = 1;
         c->kstar = 0;
         c->converged = 0;
@@ -774,7 +805,12 @@ __global__ void k_get_pairs(Inst p, const long long* __restrict__ ij, long long 
     const long long I = i / T, J = j / T, Nt = p.Nt;
     const long long L = I * Nt - I * (I - 1) / 2 + (J - I);
     const int r = (int)(i - I * T), c = (int)(j - J * T);
-    out[e] = (p.ctrl->t == 0) ? make_float4(0.f, 0.f, 0.f, 0.f) : p.state[L * TT + r * T + c];
+    if (p.ctrl->t == 0) {
+        out[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        const float2 a = p.Pst[L * TT + r * T + c], b = p.Hst[L * TT + r * T + c];
+        out[e] = make_float4(a.x, a.y, b.x, b.y);
+    }
 }
 
 }  // namespace

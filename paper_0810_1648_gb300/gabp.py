@@ -46,6 +46,7 @@ class Opts(ctypes.Structure):
 
 class Profile(ctypes.Structure):
     _fields_ = [("sweep_launches", ctypes.c_int64), ("sweep_launches_zero_state", ctypes.c_int64),
+                ("sweep_launches_p_frozen", ctypes.c_int64),
                 ("sweep_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
 
     def as_dict(self):
