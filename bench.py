@@ -206,8 +206,9 @@ def run_reference(args):
 
 
 def run_profile_small(args):
-    """One short solve on a smaller set (n=6144, 3 rounds) for ncu captures:
-    the message state (0.3 GB) is still above L2, the device footprint small."""
+    """One short solve on a smaller set (n=6144, 8 rounds, so that the last
+    rounds run with frozen P messages) for ncu captures: the message state
+    (0.3 GB) is still above L2, the device footprint small."""
     import torch
 
     from paper_0810_1648_gb300 import build as gbuild
@@ -215,12 +216,12 @@ def run_profile_small(args):
     if not os.path.exists(gabp.LIB_PATH):
         gbuild.build()
     p = workloads.mixture(6144, 128, seed=1, gamma=1.0 / 128, C=10.0)
-    h = gabp.svm_create(p.X, p.y, p.gamma, p.C, gabp.opts_default(chunk=3))
+    h = gabp.svm_create(p.X, p.y, p.gamma, p.C, gabp.opts_default(chunk=8, q_mode=Q_MODES[args.q_mode]))
     alpha = np.empty(p.n, dtype=np.float32)
-    rinf, k = gabp.svm_solve(h, 3, 0.0, alpha)
+    rinf, k = gabp.svm_solve(h, 8, 0.0, alpha)
     gabp.svm_destroy(h)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": "n=6144 m=128 mixture, 3 rounds", "rounds": k,
+    print(json.dumps({"profile_case": f"n=6144 m=128 mixture, 8 rounds, q_mode {args.q_mode}", "rounds": k,
                       "residual_inf": rinf}), flush=True)
     return 0
 

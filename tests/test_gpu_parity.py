@@ -191,3 +191,29 @@ def test_rhs_scaling_and_determinism():
     p = workloads.mixture(260, 12, seed=19)
     a = [gabp.GabpSVM(p.X, p.y, p.gamma, p.C).solve(15, 0.0)[0] for _ in range(2)]
     np.testing.assert_array_equal(a[0], a[1])
+
+
+def test_p_messages_freeze_at_their_fixed_point():
+    """The P recursion does not depend on b: once a round leaves every P
+    message unchanged, later rounds stop writing P.  Afterwards one more round
+    keeps P bitwise and updates H exactly as the oracle's single-pair update
+    says."""
+    p = workloads.mixture(700, 12, seed=21, C=1.0)
+    s = gabp.GabpSVM(p.X, p.y, p.gamma, p.C)
+    gabp.svm_set_profiling(s.h, True)
+    s.solve(120, 0.0)
+    prof = gabp.svm_get_profile(s.h)
+    assert prof["sweep_launches_p_frozen"] > 0, prof
+    Pt0, ht0, _ = gabp.svm_get_aggregates(s.h, p.n)
+    rng = np.random.default_rng(22)
+    i = rng.integers(0, p.n - 1, 300)
+    j = rng.integers(i + 1, p.n)
+    m0 = gabp.svm_get_pairs(s.h, i, j)
+    s.solve(1, 0.0)
+    m1 = gabp.svm_get_pairs(s.h, i, j)
+    np.testing.assert_array_equal(m1[:, :2], m0[:, :2])          # P unchanged
+    X, y = p.X.astype(np.float64), p.y.astype(np.float64)
+    for k in range(len(i)):
+        q = oracle.q_offdiag(X[i[k]], X[j[k]], y[i[k]], y[j[k]], p.gamma, 1.0 / p.n)
+        want = oracle.pair_update(q, Pt0[i[k]], ht0[i[k]], Pt0[j[k]], ht0[j[k]], m0[k].astype(np.float64))
+        np.testing.assert_allclose(m1[k], want, rtol=2e-5, atol=1e-9 * np.max(np.abs(want)))
