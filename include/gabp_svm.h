@@ -301,6 +301,14 @@ GABP_API gabp_status gabp_decision_noalloc(const float* X, const float* y, const
  */
 GABP_API gabp_status gabp_selftest_bounded_wait(int64_t limit_ns);
 
+/*
+ * Numerics self test (no counterpart in the paper): out[i] = the reciprocal
+ * the pair sweep uses for the cavity precisions (hardware approximation
+ * refined by one Newton-Raphson step), for cnt positive FP32 inputs (host
+ * arrays).  Tests compare it with IEEE division.
+ */
+GABP_API gabp_status gabp_selftest_reciprocal(const float* d, float* out, int64_t cnt);
+
 /* Frees everything the handle owns. NULL is accepted. */
 GABP_API gabp_status gabp_svm_destroy(gabp_svm_t h);
 

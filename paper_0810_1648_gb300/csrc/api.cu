@@ -769,6 +769,22 @@ gabp_status gabp_selftest_bounded_wait(int64_t limit_ns)
     return hst == ST_OK ? GABP_OK : fail(GABP_ECUDA, "selftest returned %d", hst);
 }
 
+gabp_status gabp_selftest_reciprocal(const float* d, float* out, int64_t cnt)
+{
+    g_err.clear();
+    if (cnt < 0 || cnt > (1LL << 30) || (cnt > 0 && (!d || !out))) return fail(GABP_EINVAL, "bad arguments");
+    float *dd = nullptr, *dout = nullptr;
+    CK(cudaMalloc(&dd, (size_t)cnt * 4 + 4));
+    CK(cudaMalloc(&dout, (size_t)cnt * 4 + 4));
+    cudaError_t e = cudaMemcpy(dd, d, (size_t)cnt * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_selftest_rcp(dd, dout, (int)cnt, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, (size_t)cnt * 4, cudaMemcpyDeviceToHost);
+    cudaFree(dd);
+    cudaFree(dout);
+    if (e != cudaSuccess) return fail(GABP_ECUDA, "selftest_reciprocal: %s", cudaGetErrorString(e));
+    return GABP_OK;
+}
+
 gabp_status gabp_svm_destroy(gabp_svm_t h)
 {
     g_err.clear();

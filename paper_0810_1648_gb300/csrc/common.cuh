@@ -161,6 +161,8 @@ void launch_get_q(const Inst& p, const int4* work, long long ntiles, int q_bf16,
 void launch_get_pairs(const Inst& p, const long long* ij, long long cnt, float4* out,
                       cudaStream_t s);
 
+// Reciprocal used by the pair sweep, evaluated on d[0..cnt) (device arrays).
+cudaError_t launch_selftest_rcp(const float* d, float* out, int cnt, cudaStream_t s);
 // Bounded-wait self test: writes ST_ETIMEOUT to *status_dev once limit_ns ran out.
 cudaError_t launch_selftest_wait(unsigned long long limit_ns, int* status_dev, cudaStream_t s);
 // Sets the thread-local message returned by gabp_last_error().

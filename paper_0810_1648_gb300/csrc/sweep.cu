@@ -151,6 +151,97 @@ __device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, con
     }
 }
 
+// 1/d for the cavity precisions: the hardware approximate reciprocal
+// refined by one Newton-Raphson step r <- r (2 - d r) (error within about one
+// unit in the last place for normal positive d; checked against IEEE division
+// by gabp_selftest_reciprocal).
+__device__ __forceinline__ float rcp_nr(float d)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+    return fmaf(r, fmaf(-d, r, 1.0f), r);
+}
+
+// Sums 16 values over the 32 lanes of a warp with the same pairing as a
+// butterfly all-reduce (xor 16, 8, 4, 2, 1), but halving the set at every
+// step: afterwards lanes 2v and 2v+1 hold the total of value v.
+__device__ __forceinline__ float reduce_scatter16(float (&a)[16], int lane)
+{
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const bool up = lane & 16;
+        const float send = up ? a[i] : a[i + 8], keep = up ? a[i + 8] : a[i];
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool up = lane & 8;
+        const float send = up ? a[i] : a[i + 4], keep = up ? a[i + 4] : a[i];
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool up = lane & 4;
+        const float send = up ? a[i] : a[i + 2], keep = up ? a[i + 2] : a[i];
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {
+        const bool up = lane & 2;
+        const float send = up ? a[0] : a[1], keep = up ? a[1] : a[0];
+        a[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    return a[0] + __shfl_xor_sync(0xffffffffu, a[0], 1);
+}
+
+// Per-tile values a consumer needs for its row updates.
+struct ColVals {
+    float P[4], H[4], M[4];      // aggregates of the lane's four columns
+    float aP[4], aH[4], aR[4];   // column partial sums
+};
+
+// Updates the pairs of row r (one chunk row) held in shared memory.  FULL:
+// interior tile, every column valid (no predicates); FROZEN: the P messages
+// are at their fixed point (no P stores, no P sums).  Adds the lane's share
+// of the row sums to rs[0..2] (P, H, residual).
+template <bool FULL, bool FROZEN, class QSrc>
+__device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char* S, int cw, int lane, int r,
+                                           int cols, bool diag, int it, bool zero, bool zero_h, float rP,
+                                           float rH, float rM, ColVals& cv, float2* __restrict__ gp,
+                                           float2* __restrict__ gh, float (&rs)[3], bool& bad, bool& changed)
+{
+    const float2* Sp = reinterpret_cast<const float2*>(S) + (size_t)cw * T;
+    const float2* Sh = reinterpret_cast<const float2*>(S + PCHUNK) + (size_t)cw * T;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int c = lane + 32 * k;
+        if (FULL || (c < cols && (!diag || c > r))) {
+            const float q = qsrc.q(S, cw, r, c, it);
+            const float2 pv = zero ? make_float2(0.f, 0.f) : Sp[c];                 // {P_ij, P_ji}
+            const float2 hv = (zero || zero_h) ? make_float2(0.f, 0.f) : Sh[c];     // {H_ij, H_ji}
+            const float di = rP - pv.y;        // cavity Ptilde_i - P_ji
+            const float dj = cv.P[k] - pv.x;   // cavity Ptilde_j - P_ij
+            bad |= !((di > 0.f) & (dj > 0.f));
+            const float ii = rcp_nr(di), ij = rcp_nr(dj);
+            const float nHij = -q * (rH - hv.y) * ii;
+            const float nHji = -q * (cv.H[k] - hv.x) * ij;
+            __stcs(&gh[r * T + c], make_float2(nHij, nHji));
+            if (!FROZEN) {
+                const float q2 = q * q;
+                const float nPij = -q2 * ii;
+                const float nPji = -q2 * ij;
+                __stcs(&gp[r * T + c], make_float2(nPij, nPji));
+                changed |= (nPij != pv.x) | (nPji != pv.y);
+                rs[0] += nPji;
+                cv.aP[k] += nPij;
+            }
+            rs[1] += nHji;
+            rs[2] = fmaf(q, cv.M[k], rs[2]);
+            cv.aH[k] += nHij;
+            cv.aR[k] = fmaf(q, rM, cv.aR[k]);
+        }
+    }
+}
+
 // Consumers (256 threads, ctid = 0..255, consumer warp cw = ctid / 32).
 // QSrc supplies q for a pair and the per-tile hand-shake of a recomputed Q tile.
 template <size_t SB, class QSrc>
@@ -182,6 +273,7 @@ __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, co
         const int I = w.y, J = w.z;
         const int rows = min(T, n - I * T), cols = min(T, n - J * T);
         const bool diag = (I == J);
+        const bool full = !diag && cols == T;
         {
             const int rc = ctid < T ? ctid : ctid - T;
             const int x = (ctid < T ? I : J) * T + rc;
@@ -196,91 +288,93 @@ __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, co
             abort = true;
             if (lane == 0) record_error(ctrl, ST_ETIMEOUT, L);
         }
-        float cP[4], cH[4], cM[4], aP[4], aH[4], aR[4];
+        ColVals cv;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int c = lane + 32 * k;
-            cP[k] = sm.col[0][c];
-            cH[k] = sm.col[1][c];
-            cM[k] = sm.col[2][c];
-            aP[k] = aH[k] = aR[k] = 0.f;
+            cv.P[k] = sm.col[0][c];
+            cv.H[k] = sm.col[1][c];
+            cv.M[k] = sm.col[2][c];
+            cv.aP[k] = cv.aH[k] = cv.aR[k] = 0.f;
         }
         float2* gp = p.Pst + (size_t)w.w * TT;
         float2* gh = p.Hst + (size_t)w.w * TT;
         const int nch = (rows + RC - 1) / RC;
+        float rowacc[16];   // row sums of 4 consecutive chunks: [g*4 + {P, H, R, -}]
         for (int ch = 0; ch < nch; ++ch) {
             if (!abort && !mbar_wait_warp(&sm.full[stage], phase)) {
                 abort = true;
                 if (lane == 0) record_error(ctrl, ST_ETIMEOUT, L);
             }
+            const int g = ch & 3;
+            if (g == 0) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) rowacc[i] = 0.f;
+            }
             const int r = ch * RC + cw;
+            float rs[3] = {0.f, 0.f, 0.f};
             if (!abort && r < rows) {
                 const unsigned char* S = ring + (size_t)stage * SB;
-                const float2* Sp = reinterpret_cast<const float2*>(S) + (size_t)cw * T;
-                const float2* Sh = reinterpret_cast<const float2*>(S + PCHUNK) + (size_t)cw * T;
                 const float rP = sm.row[0][r], rH = sm.row[1][r], rM = sm.row[2][r];
-                float sp = 0.f, sh = 0.f, sr = 0.f;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int c = lane + 32 * k;
-                    if (c < cols && (!diag || c > r)) {
-                        const float q = qsrc.q(S, cw, r, c, it);
-                        const float2 pv = zero ? make_float2(0.f, 0.f) : Sp[c];   // {P_ij, P_ji}
-                        const float2 hv = (zero || zero_h) ? make_float2(0.f, 0.f) : Sh[c];   // {H_ij, H_ji}
-                        const float4 s = make_float4(pv.x, pv.y, hv.x, hv.y);
-                        const float di = rP - s.y;      // Ptilde_i - P_ji
-                        const float dj = cP[k] - s.x;   // Ptilde_j - P_ij
-                        bad |= !(di > 0.f && di <= FLT_MAX && dj > 0.f && dj <= FLT_MAX);
-                        const float ii = __frcp_rn(di), ij = __frcp_rn(dj);
-                        const float q2 = q * q;
-                        const float nPij = -q2 * ii;
-                        const float nPji = -q2 * ij;
-                        const float nHij = -q * (rH - s.w) * ii;
-                        const float nHji = -q * (cH[k] - s.z) * ij;
-                        if (!frozen) {
-                            __stcs(&gp[r * T + c], make_float2(nPij, nPji));
-                            changed |= (nPij != pv.x) | (nPji != pv.y);
-                        }
-                        __stcs(&gh[r * T + c], make_float2(nHij, nHji));
-                        sp += nPji;
-                        sh += nHji;
-                        sr = fmaf(q, cM[k], sr);
-                        aP[k] += nPij;
-                        aH[k] += nHij;
-                        aR[k] = fmaf(q, rM, aR[k]);
-                    }
+                if (full) {
+                    if (frozen)
+                        update_row<true, true>(qsrc, S, cw, lane, r, cols, diag, it, zero, zero_h, rP, rH, rM, cv,
+                                               gp, gh, rs, bad, changed);
+                    else
+                        update_row<true, false>(qsrc, S, cw, lane, r, cols, diag, it, zero, zero_h, rP, rH, rM, cv,
+                                                gp, gh, rs, bad, changed);
+                } else {
+                    if (frozen)
+                        update_row<false, true>(qsrc, S, cw, lane, r, cols, diag, it, zero, zero_h, rP, rH, rM, cv,
+                                                gp, gh, rs, bad, changed);
+                    else
+                        update_row<false, false>(qsrc, S, cw, lane, r, cols, diag, it, zero, zero_h, rP, rH, rM,
+                                                 cv, gp, gh, rs, bad, changed);
                 }
-                sp = warp_sum(sp);
-                sh = warp_sum(sh);
-                sr = warp_sum(sr);
-                if (lane == 0) { sm.rp[r] = sp; sm.rh[r] = sh; sm.rr[r] = sr; }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm.empty[stage]);
             if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+#pragma unroll
+            for (int gg = 0; gg < 4; ++gg)
+                if (gg == g) { rowacc[4 * gg] = rs[0]; rowacc[4 * gg + 1] = rs[1]; rowacc[4 * gg + 2] = rs[2]; }
+            if (g == 3 || ch == nch - 1) {
+                // row sums of this warp's last (up to) four rows
+                const float v = reduce_scatter16(rowacc, lane);
+                const int gv = lane >> 3, qv = (lane >> 1) & 3;
+                const int rr = (ch - g + gv) * RC + cw;
+                if ((lane & 1) == 0 && qv < 3 && gv <= g && rr < rows) {
+                    float* dst = qv == 0 ? sm.rp : (qv == 1 ? sm.rh : sm.rr);
+                    dst[rr] = v;
+                }
+            }
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int c = lane + 32 * k;
-            sm.cp[cw][c] = aP[k];
-            sm.ch[cw][c] = aH[k];
-            sm.cr[cw][c] = aR[k];
+            sm.cp[cw][c] = cv.aP[k];
+            sm.ch[cw][c] = cv.aH[k];
+            sm.cr[cw][c] = cv.aR[k];
         }
         __syncwarp();
         qsrc.tile_end(it, lane);
         consumer_bar();
+        // With frozen P the P sums are unchanged from the previous round and
+        // the finalize keeps Ptilde; the P slots are not written.
         if (diag) {
             if (ctid < rows) {
                 float P = sm.rp[ctid], H = sm.rh[ctid], R = sm.rr[ctid];
 #pragma unroll
                 for (int w = 0; w < NWARPS; ++w) { P += sm.cp[w][ctid]; H += sm.ch[w][ctid]; R += sm.cr[w][ctid]; }
                 const size_t o = (size_t)I * n + I * T + ctid;
-                partP[o] = P; partH[o] = H; partR[o] = R;
+                if (!frozen) partP[o] = P;
+                partH[o] = H; partR[o] = R;
             }
         } else if (ctid < T) {
             if (ctid < rows) {
                 const size_t o = (size_t)J * n + I * T + ctid;
-                partP[o] = sm.rp[ctid]; partH[o] = sm.rh[ctid]; partR[o] = sm.rr[ctid];
+                if (!frozen) partP[o] = sm.rp[ctid];
+                partH[o] = sm.rh[ctid]; partR[o] = sm.rr[ctid];
             }
         } else {
             const int c = ctid - T;
@@ -289,7 +383,8 @@ __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, co
 #pragma unroll
                 for (int w = 0; w < NWARPS; ++w) { P += sm.cp[w][c]; H += sm.ch[w][c]; R += sm.cr[w][c]; }
                 const size_t o = (size_t)I * n + J * T + c;
-                partP[o] = P; partH[o] = H; partR[o] = R;
+                if (!frozen) partP[o] = P;
+                partH[o] = H; partR[o] = R;
             }
         }
         if (bad) record_error(ctrl, ST_ENUMERIC, (long long)I * T);
@@ -582,6 +677,7 @@ __global__ void __launch_bounds__(256)
     Ctrl* ctrl = p.ctrl;
     if (*(volatile int*)&ctrl->done) continue;
     const int t = *(volatile int*)&ctrl->t;
+    const bool frozen = *(volatile int*)&ctrl->p_frozen != 0;   // P sums unchanged: Ptilde kept
     const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
     const int x = nb.y * 32 + lane, n = p.n, Nt = p.Nt;
     const float* partP = p.part;
@@ -595,7 +691,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const size_t o = (size_t)(k + 8 * u) * n + x;
-                vp[u] = partP[o];
+                vp[u] = frozen ? 0.f : partP[o];
                 vh[u] = partH[o];
                 vr[u] = partR[o];
             }
@@ -604,7 +700,7 @@ __global__ void __launch_bounds__(256)
         }
         for (; k < Nt; k += 8) {
             const size_t o = (size_t)k * n + x;
-            acc2(sP, cPs, partP[o]);
+            acc2(sP, cPs, frozen ? 0.f : partP[o]);
             acc2(sH, cHs, partH[o]);
             acc2(sR, cRs, partR[o]);
         }
@@ -630,7 +726,7 @@ __global__ void __launch_bounds__(256)
             const float* cur = p.agg + (size_t)(t & 1) * 3 * p.npad;
             float* nxt = p.agg + (size_t)((t + 1) & 1) * 3 * p.npad;
             const double qd = p.qdiag[x], bx = p.b[x];
-            const float Pn = (float)(qd + P);
+            const float Pn = frozen ? cur[x] : (float)(qd + P);
             const float hn = (float)(bx + H);
             const float mn = hn / Pn;
             nxt[x] = Pn;
@@ -639,7 +735,7 @@ __global__ void __launch_bounds__(256)
             const double r = bx - qd * (double)cur[2 * p.npad + x] - R;
             absr = fabs(r);
             if (!(absr <= DBL_MAX)) absr = INFINITY;
-            if (!(Pn > 0.f) || !isfinite(mn)) record_error(ctrl, ST_ENUMERIC, x);
+            if (!(Pn > 0.f) || !isfinite(Pn) || !isfinite(mn)) record_error(ctrl, ST_ENUMERIC, x);
         }
         absr = warp_max_d(absr);
         if (lane == 0)
@@ -745,6 +841,13 @@ __global__ void k_selftest_wait(unsigned long long limit_ns, int* status)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *status = mbar_wait(&bar, 0u, limit_ns) ? (int)ST_OK : (int)ST_ETIMEOUT;
     }
+}
+
+// Reciprocal self test: out[i] = rcp_nr(d[i]).
+__global__ void k_selftest_rcp(const float* __restrict__ d, float* __restrict__ out, int cnt)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cnt) out[i] = rcp_nr(d[i]);
 }
 
 // Diagonal rule (Section 3.1) from the |Q| row-sum partials of the Q
@@ -897,6 +1000,12 @@ void launch_get_pairs(const Inst& p, const long long* ij, long long cnt, float4*
 }  // namespace gabp
 
 namespace gabp {
+cudaError_t launch_selftest_rcp(const float* d, float* out, int cnt, cudaStream_t s)
+{
+    if (cnt > 0) k_selftest_rcp<<<(cnt + 255) / 256, 256, 0, s>>>(d, out, cnt);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_selftest_wait(unsigned long long limit_ns, int* status_dev, cudaStream_t s)
 {
     k_selftest_wait<<<1, 32, 0, s>>>(limit_ns, status_dev);

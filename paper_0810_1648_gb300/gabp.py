@@ -124,6 +124,7 @@ def load():
         "gabp_svm_destroy": (st, [V]),
         "gabp_decision_noalloc": (st, [V, V, V, I64, I64, V, I64, D, D, V, V]),
         "gabp_selftest_bounded_wait": (st, [I64]),
+        "gabp_selftest_reciprocal": (st, [V, V, I64]),
         "gabp_batch_solve": (st, [P(Problem), I64, P(Opts), I32, D, P(Result)]),
         "gabp_server_create": (st, [P(ServerCfg), P(V)]),
         "gabp_server_submit": (st, [V, P(Problem), V, P(I64)]),
@@ -386,6 +387,14 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def selftest_reciprocal(d):
+    """The sweep's reciprocal evaluated on the GPU for float32 inputs d."""
+    d = np.ascontiguousarray(d, dtype=np.float32)
+    out = np.empty_like(d)
+    _check(load().gabp_selftest_reciprocal(_ptr(d), _ptr(out), d.size))
+    return out
 
 
 def svm_destroy(h):
