@@ -240,7 +240,8 @@ def run_batch(args):
     probs = workloads.batch_grid()
     stream = torch.cuda.Stream()
     out = {}
-    for mode, kw in (("f32", dict(q_mode=0)), ("bf16_refined", dict(q_mode=1, refine=8))):
+    for mode, kw in (("f32", dict(q_mode=0)), ("bf16q_refined", dict(q_mode=1, refine=8)),
+                     ("bf16_refined", dict(q_mode=1, refine=8, msg_bf16=1))):
         for _ in range(args.warmup):
             gabp.batch_solve(probs, 200, 1e-6, chunk=0, stream=stream.cuda_stream, **kw)
         times, last = [], None
@@ -261,7 +262,9 @@ def run_batch(args):
             "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
             "config": {"workload": "batched form: 512 instances, 32 mixture data sets x C {0.1,1,10,100} x "
                                    "gamma {0.1,0.5,1,2}/m, n log-uniform [200,4000], m in {8,32,128,256}, "
-                                   "tol 1e-6 or 200 rounds, one persistent launch per round, autotuned schedule",
+                                   "tol 1e-6 or 200 rounds, one persistent launch per round, autotuned schedule; "
+                                   "modes: plain FP32; BF16 Q + refinement; BF16 Q and BF16 messages + refinement "
+                                   "(all to ||1 - Q mu||_inf < 1e-6 with the FP32-Gram Q)",
                        "instances": len(probs), "sum_n2": n2},
             "modes": out, "bf16_over_f32": out["bf16_refined"]["solves_per_s"] / out["f32"]["solves_per_s"]}
     print(json.dumps(line), flush=True)
@@ -281,7 +284,7 @@ def run_serve(args):
     rng = np.random.default_rng(8)
     starts = [int(rng.integers(0, 50000 - r.n + 1)) for r in reqs]
     srv = gabp.Server(iters=200, tol=1e-6, max_members=args.max_members, q_mode=Q_MODES[args.q_mode],
-                      refine=8 if args.q_mode != "f32" else 0, chunk=4)
+                      refine=8 if args.q_mode != "f32" else 0, msg_bf16=1 if args.msg_bf16 else 0, chunk=4)
     t0 = time.perf_counter()
     sub, lat, nxt = {}, [], 0
     done_n = 0
@@ -344,13 +347,15 @@ def run_ours(args):
         p = workloads.mixture(20000, 128, seed=1 + rank, gamma=1.0 / 128, C=10.0)
         wl = dict(WORKLOAD, q_mode=args.q_mode)
     qb = Q_BYTES[args.q_mode]
+    mb = 4 if args.msg_bf16 else 8     # bytes of one stored message pair
     n = p.n
     stream = torch.cuda.Stream(device=dev)
     Xd = torch.from_numpy(p.X).to(dev)
     yd = torch.from_numpy(p.y).to(dev)
     alpha_d = torch.empty(n, dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
-    opts = gabp.opts_default(stream=stream.cuda_stream, chunk=ROUNDS, q_mode=Q_MODES[args.q_mode])
+    opts = gabp.opts_default(stream=stream.cuda_stream, chunk=ROUNDS, q_mode=Q_MODES[args.q_mode],
+                             msg_bf16=1 if args.msg_bf16 else 0)
     h = gabp.svm_create(Xd, yd, p.gamma, p.C, opts)
     gabp.svm_set_profiling(h, True)
 
@@ -396,7 +401,7 @@ def run_ours(args):
     # per pair: round 0 writes P and H (16 B); later rounds read and write
     # both (32 B) until the P messages reach their fixed point, then read P and
     # H and write H (24 B); every round reads the stored Q entry (qb B)
-    alg_bytes = pairs * ((32 + qb) * (nl - nz - nf) + (24 + qb) * nf + (16 + qb) * nz)
+    alg_bytes = pairs * ((4 * mb + qb) * (nl - nz - nf) + (3 * mb + qb) * nf + (2 * mb + qb) * nz)
     sweep_s = prof["sweep_ms"] / 1e3
     achieved = alg_bytes / sweep_s / 1e9 if sweep_s > 0 else None
     peaks = _peaks()
@@ -409,7 +414,7 @@ def run_ours(args):
             "frac": (achieved / peak) if achieved else None, "traffic": traffic,
             "kernel": {"f32": "k_sweep<float>", "bf16": "k_sweep<bf16>", "recompute": "k_sweep_rc"}[args.q_mode]
                       + " (pair sweep)", "peak_source": peak_src,
-            "bytes_per_pair": {"round0": 16 + qb, "p_live": 32 + qb, "p_frozen": 24 + qb},
+            "bytes_per_pair": {"round0": 2 * mb + qb, "p_live": 4 * mb + qb, "p_frozen": 3 * mb + qb},
             "launches_p_frozen": nf,
             "algorithmic_bytes_per_launch": alg_bytes / max(nl, 1),
             "avg_launch_ms": prof["sweep_ms"] / max(nl, 1), "launches_timed": nl,
@@ -447,7 +452,8 @@ def _e2e(args, p, stream, dev, ws, gabp, torch):
     Xh = torch.from_numpy(p.X).pin_memory()
     yh = torch.from_numpy(p.y).pin_memory()
     ah = torch.empty(n, dtype=torch.float32).pin_memory()
-    opts2 = gabp.opts_default(stream=stream.cuda_stream, chunk=ROUNDS, q_mode=Q_MODES[args.q_mode])
+    opts2 = gabp.opts_default(stream=stream.cuda_stream, chunk=ROUNDS, q_mode=Q_MODES[args.q_mode],
+                              msg_bf16=1 if args.msg_bf16 else 0)
     h2 = gabp.svm_create(Xh, yh, p.gamma, p.C, opts2)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
@@ -493,6 +499,7 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--duration", type=float, default=60.0)
     ap.add_argument("--max-members", type=int, default=64)
+    ap.add_argument("--msg-bf16", action="store_true", help="precision forms: BF16 message storage")
     ap.add_argument("--q-mode", default=None, choices=list(Q_MODES))
     ap.add_argument("--profile-small", action="store_true",
                     help="one 3-round solve at n=6144 (for ncu captures), no JSON bench line")

@@ -88,7 +88,9 @@ typedef struct {
                               FP32-Gram residual (FP64 sums); 0 = plain BF16 solve */
     double  sv_threshold;  /* support vectors are the i with alpha_i > sv_threshold (default 0) */
     int32_t chunk;         /* sweeps per captured CUDA graph replay between convergence checks; 0 = 16 */
-    int32_t reserved[7];
+    int32_t msg_bf16;      /* precision forms only: store the messages in BF16 (arithmetic stays FP32);
+                              use with refine > 0, which removes the rounding error */
+    int32_t reserved[6];
 } gabp_svm_opts;
 
 typedef struct gabp_svm_s* gabp_svm_t;

@@ -100,7 +100,7 @@ struct Plan {
     size_t X, vec, agg, part, state, q, work, ctrl, rhist, final3, blockbuf, xp, tab, nbl, total;
 };
 
-Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_mode)
+Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_mode, int msg_bf16)
 {
     Plan p{};
     p.xp = q_mode != GABP_Q_F32 ? align_up(bf16_pack_bytes(Nt, (int)m), 1024) : 0;
@@ -108,7 +108,7 @@ Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_m
     p.vec = align_up((size_t)npad * sizeof(float), 256);
     p.agg = align_up((size_t)6 * npad * sizeof(float), 256);
     p.part = align_up((size_t)4 * Nt * n * sizeof(float), 256);
-    p.state = 2 * align_up((size_t)ntiles * TT * sizeof(float2), 256);
+    p.state = 2 * align_up((size_t)ntiles * TT * (msg_bf16 ? 4 : 8), 256);
     p.q = q_mode == GABP_Q_F32 ? align_up((size_t)ntiles * TT * sizeof(float), 256)
         : q_mode == GABP_Q_BF16 ? align_up((size_t)ntiles * TT * sizeof(__nv_bfloat16), 256)
         : 0;
@@ -226,7 +226,7 @@ gabp_status get_graph(gabp_svm_t h, int rounds, gabp_svm_s::Graph** out)
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < rounds; ++k)
-        launch_round(h->d_tab, h->work, h->nbl, h->sched, h->grid, h->opts.q_mode, h->stream,
+        launch_round(h->d_tab, h->work, h->nbl, h->sched, h->grid, h->opts.q_mode, h->opts.msg_bf16, h->stream,
                      h->profiling ? &G.ev[(size_t)2 * k] : nullptr);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (e != cudaSuccess) return fail(GABP_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
@@ -344,6 +344,8 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     if (o.q_mode != GABP_Q_F32 && o.q_mode != GABP_Q_BF16 && o.q_mode != GABP_Q_RECOMPUTE)
         return fail(GABP_EINVAL, "unknown q_mode %d", o.q_mode);
     if (o.refine < 0 || o.refine > 64) return fail(GABP_EINVAL, "refine must be in [0, 64]");
+    if (o.msg_bf16 != 0 && (o.msg_bf16 != 1 || o.q_mode == GABP_Q_F32))
+        return fail(GABP_EINVAL, "msg_bf16 = 1 needs a precision form (q_mode BF16 or recompute)");
 
     int dev = 0, ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -364,7 +366,7 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     h->lambda = o.bias_mode == 1 ? o.bias_lambda : 1.0 / (double)n;
     h->delta = o.diag_delta;
 
-    const Plan pl = make_plan(n, m, h->Nt, h->ntiles, h->npad, o.q_mode);
+    const Plan pl = make_plan(n, m, h->Nt, h->ntiles, h->npad, o.q_mode, o.msg_bf16);
     size_t free_b = 0, total_b = 0;
     e = cudaMemGetInfo(&free_b, &total_b);
     if (e != cudaSuccess) { destroy_all(h); return fail(GABP_ECUDA, "cudaMemGetInfo: %s", cudaGetErrorString(e)); }
@@ -411,8 +413,9 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     h->r32 = (float*)take(pl.vec);
     p.agg = (float*)take(pl.agg);
     p.part = (float*)take(pl.part);
-    p.Pst = (float2*)take(pl.state / 2);
-    p.Hst = (float2*)take(pl.state / 2);
+    p.Pst = take(pl.state / 2);
+    p.Hst = take(pl.state / 2);
+    p.msg_bf16 = o.msg_bf16;
     p.qstore = pl.q ? take(pl.q) : nullptr;
     h->work = (int4*)take(pl.work);
     {
@@ -492,7 +495,8 @@ gabp_status gabp_svm_solve(gabp_svm_t h, int32_t iters, double tol, float* alpha
     Ctrl c{};
     // With refinement ahead, the BF16 solve only needs to reach about the BF16
     // error level of its matrix (1e-4) before the first correction.
-    if (gabp_status st = run_rounds(h, iters, refine ? std::max(tol, 1e-4) : tol, &c)) return st;
+    const double handover = h->opts.msg_bf16 ? 1e-3 : 1e-4;
+    if (gabp_status st = run_rounds(h, iters, refine ? std::max(tol, handover) : tol, &c)) return st;
     h->kstar = c.kstar;
     const float* mu = p.agg + (size_t)(c.kstar & 1) * 3 * p.npad + 2 * (size_t)p.npad;
     int refine_done = 0;
@@ -512,7 +516,7 @@ gabp_status gabp_svm_solve(gabp_svm_t h, int32_t iters, double tol, float* alpha
             if (!(rn >= tol)) break;
             launch_refine_rhs(p, h->r32, s);
             h->prof.kernel_launches += 1;
-            const double inner = std::max(tol * 0.5, 1e-2 * rn);
+            const double inner = std::max(tol * 0.5, (h->opts.msg_bf16 ? 3e-2 : 1e-2) * rn);
             Ctrl ci{};
             if (gabp_status st = run_rounds(h, iters, inner, &ci)) return st;
             launch_axpy_mu(p, ci.kstar, h->mu_acc, 0, s);

@@ -45,7 +45,7 @@ struct MemberPlan {
     size_t X, vec, agg, part, state, q, work, rhist, final3, blockbuf, xp, total;
 };
 
-MemberPlan member_plan(int64_t n, int64_t m, int q_mode)
+MemberPlan member_plan(int64_t n, int64_t m, int q_mode, int msg_bf16)
 {
     const int Nt = (int)((n + T - 1) / T);
     const long long nt = tri_tiles(Nt);
@@ -55,7 +55,7 @@ MemberPlan member_plan(int64_t n, int64_t m, int q_mode)
     p.vec = aup(npad * 4, 256);
     p.agg = aup(6 * npad * 4, 256);
     p.part = aup((size_t)4 * Nt * n * 4, 256);
-    p.state = 2 * aup((size_t)nt * TT * 8, 256);
+    p.state = 2 * aup((size_t)nt * TT * (msg_bf16 ? 4 : 8), 256);
     p.q = q_mode == 0 ? aup((size_t)nt * TT * 4, 256) : q_mode == 1 ? aup((size_t)nt * TT * 2, 256) : 0;
     p.work = aup((size_t)nt * sizeof(int4), 256);
     p.rhist = 0;
@@ -130,7 +130,7 @@ class Engine {
         if (e_ != cudaSuccess) return fail(GABP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-    int q_mode = 0, diag_rule = 0, x_f64 = 0, ptr_mode = 0;
+    int q_mode = 0, diag_rule = 0, x_f64 = 0, ptr_mode = 0, msg_bf16 = 0;
     double delta = 0.1, sv_threshold = 0.0;
     int cap_members = 0;
     long long cap_tiles = 0;
@@ -171,6 +171,7 @@ class Engine {
     gabp_status init(int members, long long tiles, int nblk, const gabp_svm_opts& o)
     {
         q_mode = o.q_mode;
+        msg_bf16 = o.msg_bf16;
         diag_rule = o.diag_rule;
         delta = o.diag_delta > 0 ? o.diag_delta : 0.1;
         x_f64 = o.x_dtype;
@@ -246,7 +247,7 @@ class Engine {
         const int64_t n = pr.n, m = pr.m;
         if (n < 2 || m < 1 || !pr.X || !pr.y) return fail(GABP_EINVAL, "problem needs n >= 2, m >= 1, X and y");
         if (!(pr.gamma > 0) || !(pr.C > 0)) return fail(GABP_EINVAL, "problem needs gamma > 0 and C > 0");
-        const MemberPlan pl = member_plan(n, m, q_mode);
+        const MemberPlan pl = member_plan(n, m, q_mode, msg_bf16);
         M = Member{};
         M.used = true;
         M.bytes = pl.total;
@@ -273,8 +274,9 @@ class Engine {
         take(pl.vec);
         p.agg = (float*)take(pl.agg);
         p.part = (float*)take(pl.part);
-        p.Pst = (float2*)take(pl.state / 2);
-        p.Hst = (float2*)take(pl.state / 2);
+        p.Pst = take(pl.state / 2);
+        p.Hst = take(pl.state / 2);
+        p.msg_bf16 = msg_bf16;
         p.qstore = pl.q ? take(pl.q) : nullptr;
         M.work = (int4*)take(pl.work);
         M.final3 = (double*)take(pl.final3);
@@ -338,7 +340,7 @@ class Engine {
         EK(cudaStreamWaitEvent(stream, M.ready, 0));
         // With refinement ahead, the BF16 solve only needs to reach about the
         // BF16 error level of its matrix before the first correction.
-        const double t0 = (q_mode != 0 && M.refine_left > 0) ? std::max(tol, kRefineStart) : tol;
+        const double t0 = (q_mode != 0 && M.refine_left > 0) ? std::max(tol, msg_bf16 ? 1e-3 : kRefineStart) : tol;
         launch_begin(d_tab + slot, 1, iters, t0, stream);
         ++launches;
         M.formed = true;
@@ -380,7 +382,7 @@ class Engine {
         if (it != graphs.end()) { *out = it->second; return GABP_OK; }
         cudaGraph_t g = nullptr;
         EK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
-        for (int k = 0; k < rounds; ++k) launch_round(d_tab, d_work, d_nbl, d_sched, grid, q_mode, stream);
+        for (int k = 0; k < rounds; ++k) launch_round(d_tab, d_work, d_nbl, d_sched, grid, q_mode, msg_bf16, stream);
         EK(cudaStreamEndCapture(stream, &g));
         cudaGraphExec_t ex = nullptr;
         cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
@@ -480,7 +482,7 @@ class Engine {
                 // solve Q_bf d = r with the P messages kept (H restarted)
                 --M.refine_left;
                 launch_refine_rhs(M.inst, M.r32, stream);
-                launch_begin(d_tab + k, 1, M.iters, std::max(M.tol * 0.5, 1e-2 * rn), stream);
+                launch_begin(d_tab + k, 1, M.iters, std::max(M.tol * 0.5, (msg_bf16 ? 3e-2 : 1e-2) * rn), stream);
                 launches += 2;
                 ++run;
                 continue;
@@ -586,8 +588,9 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
     gabp_svm_opts_default(&o);
     if (opts) o = *opts;
     if (o.diag_delta == 0) o.diag_delta = 0.1;
-    if (o.q_mode < 0 || o.q_mode > 2 || o.refine < 0 || o.refine > 64) {
-        set_last_error("gabp_batch_solve: bad q_mode or refine");
+    if (o.q_mode < 0 || o.q_mode > 2 || o.refine < 0 || o.refine > 64 || o.msg_bf16 < 0 || o.msg_bf16 > 1 ||
+        (o.msg_bf16 && o.q_mode == 0)) {
+        set_last_error("gabp_batch_solve: bad q_mode, refine or msg_bf16");
         return GABP_EINVAL;
     }
     long long tiles = 0, nblk = 0;
@@ -601,7 +604,7 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
         const long long Nt = (p.n + T - 1) / T;
         tiles += tri_tiles(Nt);
         nblk += (p.n + 31) / 32;
-        bytes += member_plan(p.n, p.m, o.q_mode).total;
+        bytes += member_plan(p.n, p.m, o.q_mode, o.msg_bf16).total;
     }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -634,7 +637,7 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
         if (gabp_status st = E.activate((int)k, iters, tol)) return st;
     if (o.chunk <= 0) {
         if (gabp_status st = E.autotune(iters)) return st;
-        const double t0 = (o.q_mode != 0 && o.refine > 0) ? std::max(tol, 1e-4) : tol;
+        const double t0 = (o.q_mode != 0 && o.refine > 0) ? std::max(tol, o.msg_bf16 ? 1e-3 : 1e-4) : tol;
         for (int64_t k = 0; k < count; ++k) gabp::launch_begin(E.d_tab + k, 1, iters, t0, E.stream);
     } else {
         E.chunk = o.chunk;
@@ -677,7 +680,8 @@ gabp_status gabp_server_create(const gabp_server_cfg* cfg, gabp_server_t* out)
     *out = nullptr;
     gabp_server_cfg c = *cfg;
     if (c.max_members <= 0) c.max_members = 64;
-    if (c.max_members > 4096 || c.iters < 0 || std::isnan(c.tol) || c.opts.q_mode < 0 || c.opts.q_mode > 2) {
+    if (c.max_members > 4096 || c.iters < 0 || std::isnan(c.tol) || c.opts.q_mode < 0 || c.opts.q_mode > 2 ||
+        (c.opts.msg_bf16 && c.opts.q_mode == 0)) {
         set_last_error("gabp_server_create: bad configuration");
         return GABP_EINVAL;
     }
@@ -689,7 +693,7 @@ gabp_status gabp_server_create(const gabp_server_cfg* cfg, gabp_server_t* out)
     size_t budget = c.hbm_budget_bytes > 0 ? (size_t)c.hbm_budget_bytes : (size_t)(0.8 * (double)free_b);
     if (budget + ((size_t)1 << 30) > free_b) budget = free_b > ((size_t)2 << 30) ? free_b - ((size_t)2 << 30) : 0;
     // list capacities: every tile of state costs TT * 16 bytes, so the budget bounds them
-    const long long cap_tiles = (long long)(budget / ((size_t)TT * 16)) + 1;
+    const long long cap_tiles = (long long)(budget / ((size_t)TT * (c.opts.msg_bf16 ? 8 : 16))) + 1;
     const int cap_nblk = (int)std::min<long long>(cap_tiles * 4 + 1024, 1LL << 28);
     gabp_server_t s = new gabp_server_s();
     if (gabp_status st = s->E.init(c.max_members, cap_tiles, cap_nblk, c.opts)) { delete s; return st; }
@@ -724,7 +728,7 @@ gabp_status gabp_server_step(gabp_server_t s, int32_t* active, int32_t* queued, 
     // 1. admission, first come first served, by device-memory budget and free slots
     while (!s->queue.empty()) {
         const auto& front = s->queue.front();
-        const size_t need = member_plan(front.second.n, front.second.m, s->cfg.opts.q_mode).total;
+        const size_t need = member_plan(front.second.n, front.second.m, s->cfg.opts.q_mode, s->cfg.opts.msg_bf16).total;
         if (need > s->budget) {
             gabp_result r{};
             r.status = GABP_ENOMEM;

@@ -72,8 +72,8 @@ struct Inst {
     const float* y;   // labels +-1
     const float* b;   // right-hand side (ones for the SVM)
     float* qdiag;     // Q_ii
-    float2* Pst;      // ntiles * TT precision messages {P_ij, P_ji}
-    float2* Hst;      // ntiles * TT information messages {H_ij, H_ji}
+    void* Pst;        // ntiles * TT precision messages {P_ij, P_ji} (float2, or bf16x2 when msg_bf16)
+    void* Hst;        // ntiles * TT information messages {H_ij, H_ji}
     void* qstore;     // ntiles * TT values of Q (float or bf16), or nullptr
     float* agg;       // [2][3][npad]: double-buffered {Ptilde, htilde, mutilde}
     float* part;      // [4][Nt][n] partial sums
@@ -86,6 +86,7 @@ struct Inst {
     const void* Xp;   // BF16 features packed in tensor-core operand blocks (precision form)
     const float* sqb; // ||bf16(x_i)||^2
     int nkc;          // 64-feature chunks of Xp
+    int msg_bf16;     // messages stored in BF16 (precision forms)
 };
 
 // Work of one round over a set of instances (device resident, so that a
@@ -146,7 +147,7 @@ cudaError_t prepare_sweep_rc();
 // per-node finalize.  When ev is not null, ev[0] is recorded before and
 // ev[1] after the pair sweep.
 void launch_round(const Inst* tab, const int4* work, const int2* nbl, const Sched* sched, const RoundGrid& g,
-                  int q_mode, cudaStream_t s, cudaEvent_t* ev = nullptr);
+                  int q_mode, int msg_bf16, cudaStream_t s, cudaEvent_t* ev = nullptr);
 // Final FP32-Gram residual r = 1 - Q mu (FP64 sums), dual objective and
 // alpha = clip(mu, 0, C) for the means mu; out3 = {||r||_inf, objective, #SV};
 // r_out (optional) receives r in FP32.

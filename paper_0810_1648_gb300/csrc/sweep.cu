@@ -59,8 +59,34 @@ constexpr int RC = NWARPS;                    // rows per chunk, one per consume
 constexpr int STAGES = 4;
 constexpr int SWEEP_THREADS = NTHREADS + 32;  // + one producer warp
 constexpr int SWEEP_CTAS_PER_SM = 2;
-constexpr size_t PCHUNK = (size_t)RC * T * sizeof(float2);        // 8 KB of P messages
-constexpr size_t STATE_CHUNK = 2 * PCHUNK;                          // + 8 KB of H messages
+// Message storage: FP32 pairs (plain and precision forms) or BF16 pairs
+// (precision forms with refinement).  Arithmetic is FP32 either way; sums use
+// the stored (rounded) values so that the aggregates match the messages the
+// next round reads.
+struct MsgF32 {
+    using T2 = float2;
+    static __device__ __forceinline__ float2 load(const T2& v) { return v; }
+    static __device__ __forceinline__ float2 round(float a, float b) { return make_float2(a, b); }
+    static __device__ __forceinline__ void store(T2* p, float2 v) { __stcs(p, v); }
+};
+struct MsgBF16 {
+    using T2 = __nv_bfloat162;
+    static __device__ __forceinline__ float2 load(const T2& v) { return __bfloat1622float2(v); }
+    static __device__ __forceinline__ float2 round(float a, float b)
+    {
+        return __bfloat1622float2(__floats2bfloat162_rn(a, b));
+    }
+    static __device__ __forceinline__ void store(T2* p, float2 v)
+    {
+        const T2 h = __floats2bfloat162_rn(v.x, v.y);   // exact: v is already rounded
+        __stcs(reinterpret_cast<unsigned int*>(p), *reinterpret_cast<const unsigned int*>(&h));
+    }
+};
+
+template <class MSG>
+__host__ __device__ constexpr size_t pchunk() { return (size_t)RC * T * sizeof(typename MSG::T2); }
+template <class MSG>
+__host__ __device__ constexpr size_t state_chunk() { return 2 * pchunk<MSG>(); }
 
 struct SweepTail {
     unsigned long long full[STAGES], empty[STAGES];
@@ -75,19 +101,24 @@ struct QBytes { static constexpr size_t v = sizeof(QT); };
 template <>
 struct QBytes<void> { static constexpr size_t v = 0; };
 
-template <typename QT>
-__host__ __device__ constexpr size_t stage_bytes() { return STATE_CHUNK + (size_t)RC * T * QBytes<QT>::v; }
+template <typename QT, class MSG>
+__host__ __device__ constexpr size_t stage_bytes() { return state_chunk<MSG>() + (size_t)RC * T * QBytes<QT>::v; }
 
-template <typename QT>
-__host__ __device__ constexpr size_t sweep_smem_bytes() { return 128 + STAGES * stage_bytes<QT>() + sizeof(SweepTail); }
+template <typename QT, class MSG>
+__host__ __device__ constexpr size_t sweep_smem_bytes()
+{
+    return 128 + STAGES * stage_bytes<QT, MSG>() + sizeof(SweepTail);
+}
 
 // Producer (one thread).  QT = void: messages only.
-template <typename QT, size_t SB>
+template <typename QT, class MSG, size_t SB>
 __device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, const int4* __restrict__ work,
                                                long long ntiles, SweepTail& sm, unsigned char* ring,
                                                volatile int* abort_flag)
 {
     constexpr size_t QB = QBytes<QT>::v;
+    constexpr size_t MB = sizeof(typename MSG::T2);
+    constexpr size_t SC = state_chunk<MSG>(), PC = pchunk<MSG>();
     const uint64_t pol = l2_evict_first_policy();
     int stage = 0;
     uint32_t phase = 0;
@@ -99,8 +130,8 @@ __device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, con
         const int n = p.n, I = w.y, J = w.z;
         const int rows = min(T, n - I * T), cols = min(T, n - J * T);
         const bool diag = (I == J);
-        const float2* sp = p.Pst + (size_t)w.w * TT;
-        const float2* sh = p.Hst + (size_t)w.w * TT;
+        const typename MSG::T2* sp = static_cast<const typename MSG::T2*>(p.Pst) + (size_t)w.w * TT;
+        const typename MSG::T2* sh = static_cast<const typename MSG::T2*>(p.Hst) + (size_t)w.w * TT;
         const unsigned char* qt = QB ? static_cast<const unsigned char*>(p.qstore) + (size_t)w.w * TT * QB : nullptr;
         const int nch = (rows + RC - 1) / RC;
         for (int c = 0; c < nch; ++c) {
@@ -114,12 +145,12 @@ __device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, con
             const int r0 = c * RC, nr = min(RC, rows - r0);
             if (!diag && cols == T) {
                 const uint32_t bq = (uint32_t)(nr * T * QB);
-                const uint32_t bs = zero ? 0u : (uint32_t)(nr * T * sizeof(float2));
+                const uint32_t bs = zero ? 0u : (uint32_t)(nr * T * MB);
                 mbar_arrive_expect_tx(bar, bq + 2 * bs);
-                if (QB) bulk_load(S + STATE_CHUNK, qt + (size_t)r0 * T * QB, bq, bar, pol);
+                if (QB) bulk_load(S + SC, qt + (size_t)r0 * T * QB, bq, bar, pol);
                 if (!zero) {
                     bulk_load(S, sp + (size_t)r0 * T, bs, bar, pol);
-                    bulk_load(S + PCHUNK, sh + (size_t)r0 * T, bs, bar, pol);
+                    bulk_load(S + PC, sh + (size_t)r0 * T, bs, bar, pol);
                 }
             } else {
                 // per row: columns [c0, c1) with c0, c1 multiples of 8 (16-byte
@@ -129,20 +160,20 @@ __device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, con
                 for (int k = 0; k < nr; ++k) {
                     const int r = r0 + k, c0 = diag ? ((r + 1) & ~7) : 0;
                     if (c0 < c1 && (!diag || r + 1 < cols))
-                        bytes += (uint32_t)((c1 - c0) * (QB + (zero ? 0 : 2 * sizeof(float2))));
+                        bytes += (uint32_t)((c1 - c0) * (QB + (zero ? 0 : 2 * MB)));
                 }
                 mbar_arrive_expect_tx(bar, bytes);
                 for (int k = 0; k < nr; ++k) {
                     const int r = r0 + k, c0 = diag ? ((r + 1) & ~7) : 0;
                     if (!(c0 < c1 && (!diag || r + 1 < cols))) continue;
                     if (QB)
-                        bulk_load(S + STATE_CHUNK + ((size_t)k * T + c0) * QB, qt + ((size_t)r * T + c0) * QB,
+                        bulk_load(S + SC + ((size_t)k * T + c0) * QB, qt + ((size_t)r * T + c0) * QB,
                                   (uint32_t)((c1 - c0) * QB), bar, pol);
                     if (!zero) {
-                        const size_t o = ((size_t)k * T + c0) * sizeof(float2);
-                        const uint32_t b2 = (uint32_t)((c1 - c0) * sizeof(float2));
+                        const size_t o = ((size_t)k * T + c0) * MB;
+                        const uint32_t b2 = (uint32_t)((c1 - c0) * MB);
                         bulk_load(S + o, sp + (size_t)r * T + c0, b2, bar, pol);
-                        bulk_load(S + PCHUNK + o, sh + (size_t)r * T + c0, b2, bar, pol);
+                        bulk_load(S + PC + o, sh + (size_t)r * T + c0, b2, bar, pol);
                     }
                 }
             }
@@ -203,40 +234,40 @@ struct ColVals {
 // interior tile, every column valid (no predicates); FROZEN: the P messages
 // are at their fixed point (no P stores, no P sums).  Adds the lane's share
 // of the row sums to rs[0..2] (P, H, residual).
-template <bool FULL, bool FROZEN, class QSrc>
+template <bool FULL, bool FROZEN, class MSG, class QSrc>
 __device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char* S, int cw, int lane, int r,
                                            int cols, bool diag, int it, bool zero, bool zero_h, float rP,
-                                           float rH, float rM, ColVals& cv, float2* __restrict__ gp,
-                                           float2* __restrict__ gh, float (&rs)[3], bool& bad, bool& changed)
+                                           float rH, float rM, ColVals& cv, typename MSG::T2* __restrict__ gp,
+                                           typename MSG::T2* __restrict__ gh, float (&rs)[3], bool& bad,
+                                           bool& changed)
 {
-    const float2* Sp = reinterpret_cast<const float2*>(S) + (size_t)cw * T;
-    const float2* Sh = reinterpret_cast<const float2*>(S + PCHUNK) + (size_t)cw * T;
+    using T2 = typename MSG::T2;
+    const T2* Sp = reinterpret_cast<const T2*>(S) + (size_t)cw * T;
+    const T2* Sh = reinterpret_cast<const T2*>(S + pchunk<MSG>()) + (size_t)cw * T;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int c = lane + 32 * k;
         if (FULL || (c < cols && (!diag || c > r))) {
             const float q = qsrc.q(S, cw, r, c, it);
-            const float2 pv = zero ? make_float2(0.f, 0.f) : Sp[c];                 // {P_ij, P_ji}
-            const float2 hv = (zero || zero_h) ? make_float2(0.f, 0.f) : Sh[c];     // {H_ij, H_ji}
+            const float2 pv = zero ? make_float2(0.f, 0.f) : MSG::load(Sp[c]);              // {P_ij, P_ji}
+            const float2 hv = (zero || zero_h) ? make_float2(0.f, 0.f) : MSG::load(Sh[c]);  // {H_ij, H_ji}
             const float di = rP - pv.y;        // cavity Ptilde_i - P_ji
             const float dj = cv.P[k] - pv.x;   // cavity Ptilde_j - P_ij
             bad |= !((di > 0.f) & (dj > 0.f));
             const float ii = rcp_nr(di), ij = rcp_nr(dj);
-            const float nHij = -q * (rH - hv.y) * ii;
-            const float nHji = -q * (cv.H[k] - hv.x) * ij;
-            __stcs(&gh[r * T + c], make_float2(nHij, nHji));
+            const float2 nh = MSG::round(-q * (rH - hv.y) * ii, -q * (cv.H[k] - hv.x) * ij);   // {H_ij, H_ji}
+            MSG::store(&gh[r * T + c], nh);
             if (!FROZEN) {
                 const float q2 = q * q;
-                const float nPij = -q2 * ii;
-                const float nPji = -q2 * ij;
-                __stcs(&gp[r * T + c], make_float2(nPij, nPji));
-                changed |= (nPij != pv.x) | (nPji != pv.y);
-                rs[0] += nPji;
-                cv.aP[k] += nPij;
+                const float2 np = MSG::round(-q2 * ii, -q2 * ij);                            // {P_ij, P_ji}
+                MSG::store(&gp[r * T + c], np);
+                changed |= (np.x != pv.x) | (np.y != pv.y);
+                rs[0] += np.y;
+                cv.aP[k] += np.x;
             }
-            rs[1] += nHji;
+            rs[1] += nh.y;
             rs[2] = fmaf(q, cv.M[k], rs[2]);
-            cv.aH[k] += nHij;
+            cv.aH[k] += nh.x;
             cv.aR[k] = fmaf(q, rM, cv.aR[k]);
         }
     }
@@ -244,7 +275,7 @@ __device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char
 
 // Consumers (256 threads, ctid = 0..255, consumer warp cw = ctid / 32).
 // QSrc supplies q for a pair and the per-tile hand-shake of a recomputed Q tile.
-template <size_t SB, class QSrc>
+template <size_t SB, class MSG, class QSrc>
 __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, const int4* __restrict__ work,
                                                 long long ntiles, SweepTail& sm, const unsigned char* ring,
                                                 int ctid, QSrc& qsrc)
@@ -297,8 +328,8 @@ __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, co
             cv.M[k] = sm.col[2][c];
             cv.aP[k] = cv.aH[k] = cv.aR[k] = 0.f;
         }
-        float2* gp = p.Pst + (size_t)w.w * TT;
-        float2* gh = p.Hst + (size_t)w.w * TT;
+        typename MSG::T2* gp = static_cast<typename MSG::T2*>(p.Pst) + (size_t)w.w * TT;
+        typename MSG::T2* gh = static_cast<typename MSG::T2*>(p.Hst) + (size_t)w.w * TT;
         const int nch = (rows + RC - 1) / RC;
         float rowacc[16];   // row sums of 4 consecutive chunks: [g*4 + {P, H, R, -}]
         for (int ch = 0; ch < nch; ++ch) {
@@ -318,17 +349,17 @@ __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, co
                 const float rP = sm.row[0][r], rH = sm.row[1][r], rM = sm.row[2][r];
                 if (full) {
                     if (frozen)
-                        update_row<true, true>(qsrc, S, cw, lane, r, cols, diag, it, zero, zero_h, rP, rH, rM, cv,
+                        update_row<true, true, MSG>(qsrc, S, cw, lane, r, cols, diag, it, zero, zero_h, rP, rH, rM, cv,
                                                gp, gh, rs, bad, changed);
                     else
-                        update_row<true, false>(qsrc, S, cw, lane, r, cols, diag, it, zero, zero_h, rP, rH, rM, cv,
+                        update_row<true, false, MSG>(qsrc, S, cw, lane, r, cols, diag, it, zero, zero_h, rP, rH, rM, cv,
                                                 gp, gh, rs, bad, changed);
                 } else {
                     if (frozen)
-                        update_row<false, true>(qsrc, S, cw, lane, r, cols, diag, it, zero, zero_h, rP, rH, rM, cv,
+                        update_row<false, true, MSG>(qsrc, S, cw, lane, r, cols, diag, it, zero, zero_h, rP, rH, rM, cv,
                                                 gp, gh, rs, bad, changed);
                     else
-                        update_row<false, false>(qsrc, S, cw, lane, r, cols, diag, it, zero, zero_h, rP, rH, rM,
+                        update_row<false, false, MSG>(qsrc, S, cw, lane, r, cols, diag, it, zero, zero_h, rP, rH, rM,
                                                  cv, gp, gh, rs, bad, changed);
                 }
             }
@@ -396,13 +427,13 @@ __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, co
 }
 
 // Q streamed with the messages: it sits after the messages in each ring stage.
-template <typename QT>
+template <typename QT, class MSG>
 struct StoredQ {
     __device__ __forceinline__ bool tile_begin(int, int) { return true; }
     __device__ __forceinline__ void tile_end(int, int) {}
     __device__ __forceinline__ float q(const unsigned char* S, int cw, int, int c, int) const
     {
-        return to_f(reinterpret_cast<const QT*>(S + STATE_CHUNK)[(size_t)cw * T + c]);
+        return to_f(reinterpret_cast<const QT*>(S + state_chunk<MSG>())[(size_t)cw * T + c]);
     }
 };
 
@@ -411,12 +442,12 @@ __device__ __forceinline__ unsigned char* align_smem(unsigned char* raw, uintptr
     return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + a - 1) & ~(a - 1));
 }
 
-template <typename QT>
+template <typename QT, class MSG>
 __global__ void __launch_bounds__(SWEEP_THREADS, SWEEP_CTAS_PER_SM)
     k_sweep(const Inst* __restrict__ tab, const int4* __restrict__ work, const Sched* __restrict__ sched)
 {
     const long long ntiles = sched->ntiles;
-    constexpr size_t SB = stage_bytes<QT>();
+    constexpr size_t SB = stage_bytes<QT, MSG>();
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* ring = align_smem(smem_raw, 128);
@@ -432,11 +463,11 @@ __global__ void __launch_bounds__(SWEEP_THREADS, SWEEP_CTAS_PER_SM)
     }
     __syncthreads();
     if (warp == NWARPS) {
-        if (lane == 0) sweep_producer<QT, SB>(tab, work, ntiles, sm, ring, nullptr);
+        if (lane == 0) sweep_producer<QT, MSG, SB>(tab, work, ntiles, sm, ring, nullptr);
         return;
     }
-    StoredQ<QT> qsrc;
-    sweep_consumers<SB>(tab, work, ntiles, sm, ring, tid, qsrc);
+    StoredQ<QT, MSG> qsrc;
+    sweep_consumers<SB, MSG>(tab, work, ntiles, sm, ring, tid, qsrc);
 }
 
 // ---- fused recompute ------------------------------------------------------
@@ -454,9 +485,10 @@ struct RcExtra {
     int abort;
 };
 
+template <class MSG>
 __host__ __device__ constexpr size_t rc_smem_bytes()
 {
-    return 1024 + STAGES * STATE_CHUNK + RC_XSTAGES * 2 * BLK_BYTES + 2 * RC_QTILE + sizeof(SweepTail) +
+    return 1024 + STAGES * state_chunk<MSG>() + RC_XSTAGES * 2 * BLK_BYTES + 2 * RC_QTILE + sizeof(SweepTail) +
            sizeof(RcExtra);
 }
 
@@ -478,6 +510,7 @@ struct RecomputedQ {
     }
 };
 
+template <class MSG>
 __global__ void __launch_bounds__(RC_THREADS, 1)
     k_sweep_rc(const Inst* __restrict__ tab, const int4* __restrict__ work, const Sched* __restrict__ sched)
 {
@@ -485,7 +518,7 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* ring = align_smem(smem_raw, 1024);
-    unsigned char* xops = ring + STAGES * STATE_CHUNK;                       // [2][A, B]
+    unsigned char* xops = ring + STAGES * state_chunk<MSG>();                // [2][A, B]
     __nv_bfloat16* qtile = reinterpret_cast<__nv_bfloat16*>(xops + RC_XSTAGES * 2 * BLK_BYTES);
     SweepTail& sm = *reinterpret_cast<SweepTail*>(reinterpret_cast<unsigned char*>(qtile) + 2 * RC_QTILE);
     RcExtra& ex = *reinterpret_cast<RcExtra*>(reinterpret_cast<unsigned char*>(&sm) + sizeof(SweepTail));
@@ -515,7 +548,7 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
     volatile int* abort_flag = &ex.abort;
 
     if (warp == 0) {
-        if (lane == 0) sweep_producer<void, STATE_CHUNK>(tab, work, ntiles, sm, ring, abort_flag);
+        if (lane == 0) sweep_producer<void, MSG, state_chunk<MSG>()>(tab, work, ntiles, sm, ring, abort_flag);
     } else if (warp == 1) {
         // feature blocks of each tile
         if (lane == 0) {
@@ -641,7 +674,7 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
         }
     } else {
         RecomputedQ qsrc{qtile, &ex};
-        sweep_consumers<STATE_CHUNK>(tab, work, ntiles, sm, ring, tid - 7 * 32, qsrc);
+        sweep_consumers<state_chunk<MSG>(), MSG>(tab, work, ntiles, sm, ring, tid - 7 * 32, qsrc);
     }
     tc_fence_before();
     __syncthreads();
@@ -911,7 +944,15 @@ __global__ void k_get_pairs(Inst p, const long long* __restrict__ ij, long long 
     if (p.ctrl->t == 0) {
         out[e] = make_float4(0.f, 0.f, 0.f, 0.f);
     } else {
-        const float2 a = p.Pst[L * TT + r * T + c], b = p.Hst[L * TT + r * T + c];
+        const size_t o = (size_t)L * TT + r * T + c;
+        float2 a, b;
+        if (p.msg_bf16) {
+            a = __bfloat1622float2(static_cast<const __nv_bfloat162*>(p.Pst)[o]);
+            b = __bfloat1622float2(static_cast<const __nv_bfloat162*>(p.Hst)[o]);
+        } else {
+            a = static_cast<const float2*>(p.Pst)[o];
+            b = static_cast<const float2*>(p.Hst)[o];
+        }
         out[e] = make_float4(a.x, a.y, b.x, b.y);
     }
 }
@@ -966,28 +1007,42 @@ RoundGrid round_grid(long long max_tiles, int max_nblocks, int q_mode, int ctas_
 
 cudaError_t prepare_sweep_rc()
 {
-    return cudaFuncSetAttribute(k_sweep_rc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rc_smem_bytes());
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_rc<MsgF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)rc_smem_bytes<MsgF32>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_sweep_rc<MsgBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)rc_smem_bytes<MsgBF16>());
 }
 
 cudaError_t prepare_sweep()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_sweep<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sweep_smem_bytes<float>());
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_sweep<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sweep_smem_bytes<__nv_bfloat16>());
+    cudaError_t e = cudaFuncSetAttribute(k_sweep<float, MsgF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sweep_smem_bytes<float, MsgF32>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sweep<__nv_bfloat16, MsgF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sweep_smem_bytes<__nv_bfloat16, MsgF32>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sweep<__nv_bfloat16, MsgBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sweep_smem_bytes<__nv_bfloat16, MsgBF16>());
+    return e;
 }
 
 void launch_round(const Inst* tab, const int4* work, const int2* nbl, const Sched* sched, const RoundGrid& g,
-                  int q_mode, cudaStream_t s, cudaEvent_t* ev)
+                  int q_mode, int msg_bf16, cudaStream_t s, cudaEvent_t* ev)
 {
     if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
-    if (q_mode == 2)
-        k_sweep_rc<<<g.sweep, RC_THREADS, rc_smem_bytes(), s>>>(tab, work, sched);
+    if (q_mode == 2 && msg_bf16)
+        k_sweep_rc<MsgBF16><<<g.sweep, RC_THREADS, rc_smem_bytes<MsgBF16>(), s>>>(tab, work, sched);
+    else if (q_mode == 2)
+        k_sweep_rc<MsgF32><<<g.sweep, RC_THREADS, rc_smem_bytes<MsgF32>(), s>>>(tab, work, sched);
+    else if (q_mode == 1 && msg_bf16)
+        k_sweep<__nv_bfloat16, MsgBF16>
+            <<<g.sweep, SWEEP_THREADS, sweep_smem_bytes<__nv_bfloat16, MsgBF16>(), s>>>(tab, work, sched);
     else if (q_mode == 1)
-        k_sweep<__nv_bfloat16><<<g.sweep, SWEEP_THREADS, sweep_smem_bytes<__nv_bfloat16>(), s>>>(tab, work, sched);
+        k_sweep<__nv_bfloat16, MsgF32>
+            <<<g.sweep, SWEEP_THREADS, sweep_smem_bytes<__nv_bfloat16, MsgF32>(), s>>>(tab, work, sched);
     else
-        k_sweep<float><<<g.sweep, SWEEP_THREADS, sweep_smem_bytes<float>(), s>>>(tab, work, sched);
+        k_sweep<float, MsgF32><<<g.sweep, SWEEP_THREADS, sweep_smem_bytes<float, MsgF32>(), s>>>(tab, work, sched);
     if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
     k_finalize<<<g.finalize, 256, 0, s>>>(tab, nbl, sched);
 }

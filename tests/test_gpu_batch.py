@@ -107,3 +107,14 @@ def test_server_results_equal_alone():
         single, _, _ = gabp.GabpSVM(p.X, p.y, p.gamma, p.C, chunk=4).solve(300, 1e-6)
         np.testing.assert_array_equal(a, single)
     srv.close()
+
+
+def test_batch_bf16_messages_refined():
+    probs = _mix(6, 5)
+    alphas, res, rc = gabp.batch_solve(probs, 300, 1e-6, chunk=8, q_mode=gabp.Q_BF16, refine=10, msg_bf16=1)
+    assert rc == gabp.OK
+    for p, a, r in zip(probs, alphas, res):
+        Qx = oracle.build_q(p.X.astype(np.float64), p.y.astype(np.float64), p.gamma, p.C)
+        ref = np.linalg.solve(Qx, np.ones(p.n))
+        assert r["residual_inf"] < 1e-6 and r["converged"] == 1
+        assert np.max(np.abs(a - np.clip(ref, 0, p.C))) <= 1e-4 * p.C

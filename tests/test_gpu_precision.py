@@ -117,3 +117,30 @@ def test_refined_recompute_reaches_fp64_fixed_point():
     assert np.max(np.abs(mu - ref)) / np.max(np.abs(ref)) <= 2e-5
     assert np.max(np.abs(alpha.astype(np.float64) - np.clip(ref, 0, p.C))) <= 1e-4 * p.C
     assert rinf < 1e-6
+
+
+@pytest.mark.parametrize("q_mode", [gabp.Q_BF16, gabp.Q_RECOMPUTE])
+@pytest.mark.parametrize("n,m,C", [(300, 64, 1.0), (1000, 10, 1.0), (777, 33, 10.0)])
+def test_bf16_messages_refined_reach_fp64_fixed_point(q_mode, n, m, C):
+    """Messages stored in BF16 (arithmetic FP32): the rounding error of the
+    stored messages is removed by the defect correction on the FP32-Gram
+    residual, so the answer meets the same FP32 bars as the plain form."""
+    p = workloads.mixture(n, m, seed=90 + n, C=C)
+    s = gabp.GabpSVM(p.X, p.y, p.gamma, p.C, q_mode=q_mode, refine=10, msg_bf16=1)
+    alpha, rinf, k = s.solve(300, 1e-6)
+    mu = s.mean().astype(np.float64)
+    Qx = oracle.build_q(p.X.astype(np.float64), p.y.astype(np.float64), p.gamma, p.C)
+    ref = np.linalg.solve(Qx, np.ones(p.n))
+    assert np.max(np.abs(mu - ref)) / np.max(np.abs(ref)) <= 2e-5
+    a_ref = np.clip(ref, 0, p.C)
+    assert np.max(np.abs(alpha.astype(np.float64) - a_ref)) <= 1e-4 * p.C
+    clear = np.abs(ref) > 1e-5 * np.max(np.abs(ref))
+    assert np.array_equal((alpha > 0)[clear], (a_ref > 0)[clear])
+    assert rinf < 1e-6 and s.stats()["converged"] == 1
+
+
+def test_bf16_messages_rejected_for_plain_form():
+    p = workloads.mixture(50, 3, seed=99)
+    with pytest.raises(gabp.GabpError) as ei:
+        gabp.GabpSVM(p.X, p.y, p.gamma, p.C, msg_bf16=1)
+    assert ei.value.status == gabp.EINVAL
