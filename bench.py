@@ -411,7 +411,10 @@ def run_ours(args):
         peak, peak_src = 6800.0, "fallback"
     traffic = _traffic_from_profile(os.path.join(ROOT, "paper_0810_1648_gb300", "csrc", "sweep.cu"))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": traffic if (args.workload == "plain_large" and args.q_mode == "f32") else None,
+            "traffic_note": "ncu dram read+write of one frozen-P launch of this workload "
+                            "(profiles/k_sweep_plain_large.txt); null if the kernel source changed since",
             "kernel": {"f32": "k_sweep<float>", "bf16": "k_sweep<bf16>", "recompute": "k_sweep_rc"}[args.q_mode]
                       + " (pair sweep)", "peak_source": peak_src,
             "bytes_per_pair": {"round0": 2 * mb + qb, "p_live": 4 * mb + qb, "p_frozen": 3 * mb + qb},
