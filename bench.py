@@ -254,6 +254,7 @@ def run_batch(args):
             last = res
         conv = sum(r["converged"] for r in last)
         out[mode] = {"solves_per_s": len(probs) / float(np.median(times)), "ms_per_batch": 1e3 * float(np.median(times)),
+                     "phases_ms": gabp.batch_last_phases(),
                      "converged": conv, "max_residual": max(r["residual_inf"] for r in last),
                      "mean_rounds": float(np.mean([r["iters_done"] for r in last]))}
     n2 = sum(p.n * p.n for p in probs)

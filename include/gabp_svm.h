@@ -222,6 +222,11 @@ typedef struct {
 GABP_API gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gabp_svm_opts* opts,
                                       int32_t iters, double tol, gabp_result* results);
 
+/* Host wall time (ms) of the phases of this thread's last gabp_batch_solve:
+ * out6 = {formation, schedule tuning, rounds, stop handling (final residuals,
+ * refinement set-up, result copies), total, number of round chunks}. */
+GABP_API gabp_status gabp_batch_last_phases(double* out6);
+
 /*
  * Continuous-batching server.  Requests queue in arrival order; each
  * gabp_server_step() admits queued requests while free slots and the device

@@ -66,6 +66,8 @@ struct gabp_svm_s {
     int4* work = nullptr;           // tile list {0, I, J, L}
     int2* nbl = nullptr;            // node blocks {0, b}
     Sched* sched = nullptr;
+    StopOp* d_ops = nullptr;        // end-of-solve operation of the one instance
+    int* d_members = nullptr;       // {0}
     RoundGrid grid{};
     float* alpha = nullptr;
     double* final3 = nullptr;
@@ -113,7 +115,7 @@ Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_m
         : q_mode == GABP_Q_BF16 ? align_up((size_t)ntiles * TT * sizeof(__nv_bfloat16), 256)
         : 0;
     p.work = align_up((size_t)ntiles * sizeof(int4), 256);
-    p.tab = align_up(sizeof(Inst) + sizeof(Sched), 256);
+    p.tab = align_up(sizeof(Inst) + sizeof(Sched) + sizeof(StopOp) + 64, 256);
     p.nbl = align_up((size_t)((n + 31) / 32) * sizeof(int2), 256);
     p.ctrl = align_up(sizeof(Ctrl), 256);
     p.rhist = align_up((size_t)kRhistCap * sizeof(double), 256);
@@ -422,6 +424,8 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
         char* tb = (char*)take(pl.tab);
         h->d_tab = (Inst*)tb;
         h->sched = (Sched*)(tb + align_up(sizeof(Inst), 16));
+        h->d_ops = (StopOp*)(tb + align_up(sizeof(Inst), 16) + align_up(sizeof(Sched), 16));
+        h->d_members = (int*)((char*)h->d_ops + align_up(sizeof(StopOp), 16));
     }
     h->nbl = (int2*)take(pl.nbl);
     p.ctrl = (Ctrl*)take(pl.ctrl);
@@ -448,6 +452,8 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     e = cudaMemcpyAsync(h->work, wl.data(), wl.size() * sizeof(int4), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->nbl, nb.data(), nb.size() * sizeof(int2), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->sched, &sc, sizeof sc, cudaMemcpyHostToDevice, h->stream);
+    const int zero_slot = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_members, &zero_slot, sizeof(int), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) { destroy_all(h); return fail(GABP_ECUDA, "work list copy: %s", cudaGetErrorString(e)); }
 
@@ -500,35 +506,56 @@ gabp_status gabp_svm_solve(gabp_svm_t h, int32_t iters, double tol, float* alpha
     h->kstar = c.kstar;
     const float* mu = p.agg + (size_t)(c.kstar & 1) * 3 * p.npad + 2 * (size_t)p.npad;
     int refine_done = 0;
+    StopOp op{};
+    op.alpha = h->alpha;
+    op.blockbuf = h->blockbuf;
+    op.final3 = h->final3;
+    op.sv_threshold = (float)h->opts.sv_threshold;
+    const int nblk = (int)((h->n + 31) / 32);
+    auto final_pass = [&](const StopOp& o) -> gabp_status {
+        CK(cudaMemcpyAsync(h->d_ops, &o, sizeof(StopOp), cudaMemcpyHostToDevice, s));
+        if (o.acc) launch_axpy_list(h->d_tab, h->d_ops, h->nbl, nblk, s);
+        launch_final(h->d_tab, h->d_ops, h->work, h->ntiles, h->nbl, nblk, h->d_members, 1, nullptr, s);
+        h->prof.kernel_launches += o.acc ? 4 : 3;
+        CK(cudaGetLastError());
+        return GABP_OK;
+    };
     if (refine) {
         // Defect correction: mu_acc solves the BF16 system; r = 1 - Q32 mu_acc
         // with the FP32-Gram matrix and FP64 sums; GaBP on the BF16 system with
         // right-hand side r (P messages kept, H restarted) gives the
         // correction d; mu_acc += d; repeat until ||r||_inf < tol.
-        launch_axpy_mu(p, c.kstar, h->mu_acc, 1, s);
-        for (int it = 0; it < h->opts.refine; ++it) {
-            launch_final(p, h->work, h->ntiles, h->mu_acc, h->alpha, h->final3, h->blockbuf,
-                         (float)h->opts.sv_threshold, h->r32, s);
+        int buf = c.kstar, first = 1;
+        for (int it = 0; it <= h->opts.refine; ++it) {
+            StopOp o = op;
+            o.mu = h->mu_acc;
+            o.acc = h->mu_acc;
+            o.axpy_buf = buf;
+            o.axpy_first = first;
+            o.r_out = h->r32;
+            if (gabp_status st = final_pass(o)) return st;
+            if (!first) ++refine_done;
+            first = 0;
             CK(cudaMemcpyAsync(h->hfinal, h->final3, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
-            h->prof.kernel_launches += 4;
             const double rn = h->hfinal[0];
-            if (!(rn >= tol)) break;
-            launch_refine_rhs(p, h->r32, s);
+            if (!(rn >= tol) || it == h->opts.refine) break;
+            StopOp rr = op;
+            rr.r_out = h->r32;
+            CK(cudaMemcpyAsync(h->d_ops, &rr, sizeof(StopOp), cudaMemcpyHostToDevice, s));
+            launch_refine_rhs_list(h->d_tab, h->d_ops, h->nbl, nblk, s);
             h->prof.kernel_launches += 1;
             const double inner = std::max(tol * 0.5, (h->opts.msg_bf16 ? 3e-2 : 1e-2) * rn);
             Ctrl ci{};
             if (gabp_status st = run_rounds(h, iters, inner, &ci)) return st;
-            launch_axpy_mu(p, ci.kstar, h->mu_acc, 0, s);
-            h->prof.kernel_launches += 1;
-            ++refine_done;
+            buf = ci.kstar;
         }
         mu = h->mu_acc;
+    } else {
+        StopOp o = op;
+        o.mu = mu;
+        if (gabp_status st = final_pass(o)) return st;
     }
-    launch_final(p, h->work, h->ntiles, mu, h->alpha, h->final3, h->blockbuf, (float)h->opts.sv_threshold,
-                 nullptr, s);
-    h->prof.kernel_launches += 3;
-    CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->hfinal, h->final3, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (alpha)
         CK(cudaMemcpyAsync(alpha, h->alpha, (size_t)h->n * sizeof(float),

@@ -89,6 +89,7 @@ struct Member {
     int refine_left = 0;
     int refine_done = 0;
     bool refining = false;
+    bool staged = false;     // rows checked and normed already (FP64 / device input)
     int t_first_stop = 0;
     gabp_result res{};
     float* out_alpha = nullptr;  // caller buffer
@@ -111,6 +112,18 @@ struct TuneVal {
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune_cache;
+
+// Host wall time of the phases of the last gabp_batch_solve (milliseconds).
+struct BatchPhases {
+    double form_ms, tune_ms, rounds_ms, stop_ms, total_ms;
+    int64_t chunks, launches;
+};
+thread_local BatchPhases g_last_phases{};
+
+double ms_since(std::chrono::steady_clock::time_point t0)
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
 
 }  // namespace
 
@@ -144,11 +157,20 @@ class Engine {
     Sched* d_sched = nullptr;
     Ctrl* h_ctrl = nullptr;       // pinned mirror
     double* h_f3 = nullptr;       // pinned {residual, objective, #SV} per slot
+    StopOp* h_ops = nullptr;      // pinned end-of-solve operations per slot
+    StopOp* d_ops = nullptr;
+    double* d_f3 = nullptr;
+    int4* d_stop_tiles = nullptr; // lists of the instances being finished
+    int2* d_stop_nbl = nullptr;
+    int* d_stop_members = nullptr;
+    int2* d_begin_list = nullptr;
+    double* d_begin_tol = nullptr;
     std::vector<Member> mem;
     RoundGrid grid{};
     int ctas_per_sm = 0;
     int chunk = 16;
     std::map<int, cudaGraphExec_t> graphs;
+    std::vector<int> pending;     // added, Q not formed yet
     long long live_tiles = 0;     // tiles in the current lists
     bool lists_dirty = true;
     size_t bytes_in_use = 0;
@@ -164,6 +186,7 @@ class Engine {
         if (d_tab) cudaFree(d_tab);
         if (h_ctrl) cudaFreeHost(h_ctrl);
         if (h_f3) cudaFreeHost(h_f3);
+        if (h_ops) cudaFreeHost(h_ops);
         if (side) cudaStreamDestroy(side);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
@@ -202,17 +225,33 @@ class Engine {
         const size_t b_ctrl = aup((size_t)cap_members * sizeof(Ctrl), 256);
         const size_t b_work = aup((size_t)cap_tiles * sizeof(int4), 256);
         const size_t b_nbl = aup((size_t)cap_nblk * sizeof(int2), 256);
+        const size_t b_ops = aup((size_t)cap_members * sizeof(StopOp), 256);
+        const size_t b_f3 = aup((size_t)cap_members * 3 * sizeof(double), 256);
+        const size_t b_mem = aup((size_t)cap_members * sizeof(int), 256);
+        const size_t b_bl = aup((size_t)cap_members * sizeof(int2), 256);
+        const size_t b_bt = aup((size_t)cap_members * sizeof(double), 256);
         char* base = nullptr;
-        EK(cudaMalloc((void**)&base, b_tab + b_ctrl + b_work + b_nbl + 256));
-        d_tab = (Inst*)base;
-        d_ctrl = (Ctrl*)(base + b_tab);
-        d_work = (int4*)(base + b_tab + b_ctrl);
-        d_nbl = (int2*)(base + b_tab + b_ctrl + b_work);
-        d_sched = (Sched*)(base + b_tab + b_ctrl + b_work + b_nbl);
+        EK(cudaMalloc((void**)&base, b_tab + b_ctrl + 2 * b_work + 2 * b_nbl + b_ops + b_f3 + b_mem + b_bl + b_bt + 256));
+        size_t off = 0;
+        auto carve = [&](size_t bytes) { char* r = base + off; off += bytes; return r; };
+        d_tab = (Inst*)carve(b_tab);
+        d_ctrl = (Ctrl*)carve(b_ctrl);
+        d_work = (int4*)carve(b_work);
+        d_nbl = (int2*)carve(b_nbl);
+        d_stop_tiles = (int4*)carve(b_work);
+        d_stop_nbl = (int2*)carve(b_nbl);
+        d_ops = (StopOp*)carve(b_ops);
+        d_f3 = (double*)carve(b_f3);
+        d_stop_members = (int*)carve(b_mem);
+        d_begin_list = (int2*)carve(b_bl);
+        d_begin_tol = (double*)carve(b_bt);
+        d_sched = (Sched*)carve(256);
         EK(cudaMemsetAsync(d_ctrl, 0, b_ctrl, stream));
         EK(cudaMemsetAsync(d_sched, 0, sizeof(Sched), stream));
         EK(cudaMallocHost((void**)&h_ctrl, (size_t)cap_members * sizeof(Ctrl)));
         EK(cudaMallocHost((void**)&h_f3, (size_t)cap_members * 3 * sizeof(double)));
+        EK(cudaMallocHost((void**)&h_ops, (size_t)cap_members * sizeof(StopOp)));
+        std::memset(h_ops, 0, (size_t)cap_members * sizeof(StopOp));
         mem.resize((size_t)cap_members);
         set_grid(0);
         EK(cudaStreamSynchronize(stream));
@@ -308,28 +347,73 @@ class Engine {
         EK(cudaMemcpyAsync(d_tab + slot, &p, sizeof(Inst), cudaMemcpyHostToDevice, s));
         EK(cudaMemcpyAsync(M.work, wl.data(), wl.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
         EK(cudaMemcpyAsync((void*)p.y, pr.y, (size_t)n * 4, ptr_mode ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-        const void* src = pr.X;
-        void* tmp = nullptr;
-        if (!ptr_mode) {
-            if (x_f64) {
+        if (pl.xp) EK(cudaMemsetAsync((void*)p.Xp, 0, pl.xp, s));   // padding rows and features stay 0
+        if (!ptr_mode && !x_f64) {
+            // FP32 rows straight into X; the batched staging of form_pending() checks them
+            EK(cudaMemcpyAsync((void*)p.X, pr.X, (size_t)n * m * 4, cudaMemcpyHostToDevice, s));
+        } else {
+            // FP64 or device input: convert / copy and check now
+            const void* src = pr.X;
+            void* tmp = nullptr;
+            if (!ptr_mode) {
                 EK(cudaMallocAsync(&tmp, (size_t)n * m * 8, s));
                 EK(cudaMemcpyAsync(tmp, pr.X, (size_t)n * m * 8, cudaMemcpyHostToDevice, s));
                 src = tmp;
-            } else {
-                EK(cudaMemcpyAsync((void*)p.X, pr.X, (size_t)n * m * 4, cudaMemcpyHostToDevice, s));
-                src = p.X;
+            }
+            launch_stage(src, x_f64, (int)n, (int)m, p.y, (float*)p.X, (float*)p.sq, (float*)p.b, p.ctrl, s);
+            ++launches;
+            if (tmp) EK(cudaFreeAsync(tmp, s));
+            M.staged = true;
+        }
+        EK(cudaEventCreateWithFlags(&M.ready, cudaEventDisableTiming));
+        pending.push_back(slot);
+        return GABP_OK;
+    }
+
+    // Forms Q for every instance added since the last call, one launch per
+    // kernel over all of them (staging checks, BF16 packing, FP32 Gram / row
+    // sums, diagonal rule + Step 1, tensor-core BF16 Q), on the side stream.
+    gabp_status form_pending()
+    {
+        if (pending.empty()) return GABP_OK;
+        cudaStream_t s = side;
+        std::vector<int4> tiles;
+        std::vector<int2> nb, nb_stage;
+        for (int k : pending) {
+            const Member& M = mem[(size_t)k];
+            const int Nt = M.inst.Nt;
+            int L = 0;
+            for (int I = 0; I < Nt; ++I)
+                for (int J = I; J < Nt; ++J, ++L) tiles.push_back(make_int4(k, I, J, L));
+            for (int b = 0; b < M.nblk; ++b) {
+                nb.push_back(make_int2(k, b));
+                if (!M.staged) nb_stage.push_back(make_int2(k, b));
             }
         }
-        launch_stage(src, x_f64, (int)n, (int)m, p.y, (float*)p.X, (float*)p.sq, (float*)p.b, p.ctrl, s);
-        if (tmp) EK(cudaFreeAsync(tmp, s));
-        if (q_mode != 0) EK(launch_pack_bf16(p.X, (int)n, (int)m, p.nkc, p.Nt, (void*)p.Xp, (float*)p.sqb, s));
-        launch_form_q(d_tab, M.work, M.ntiles, q_mode == 0 ? 1 : 0, s);
-        launch_init(p, diag_rule, (float)delta, s);
-        if (q_mode == 1) EK(launch_form_q_tc(d_tab, M.work, M.ntiles, s));
-        launches += q_mode == 0 ? 3 : (q_mode == 1 ? 6 : 5);
+        int4* d_t = nullptr;
+        int2* d_n = nullptr;
+        int2* d_ns = nullptr;
+        EK(cudaMallocAsync((void**)&d_t, tiles.size() * sizeof(int4) + 16, s));
+        EK(cudaMallocAsync((void**)&d_n, nb.size() * sizeof(int2) + 16, s));
+        EK(cudaMallocAsync((void**)&d_ns, nb_stage.size() * sizeof(int2) + 16, s));
+        EK(cudaMemcpyAsync(d_t, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+        EK(cudaMemcpyAsync(d_n, nb.data(), nb.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+        if (!nb_stage.empty())
+            EK(cudaMemcpyAsync(d_ns, nb_stage.data(), nb_stage.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+        launch_stage_list(d_tab, d_ns, (int)nb_stage.size(), s);
+        if (q_mode != 0) EK(launch_pack_list(d_tab, d_n, (int)nb.size(), s));
+        launch_form_q(d_tab, d_t, (long long)tiles.size(), q_mode == 0 ? 1 : 0, s);
+        launch_init_list(d_tab, d_n, (int)nb.size(), diag_rule, (float)delta, s);
+        if (q_mode == 1) EK(launch_form_q_tc(d_tab, d_t, (long long)tiles.size(), s));
+        launches += q_mode == 0 ? 3 : (q_mode == 1 ? 5 : 4);
         EK(cudaGetLastError());
-        EK(cudaEventCreateWithFlags(&M.ready, cudaEventDisableTiming));
-        EK(cudaEventRecord(M.ready, s));
+        for (int k : pending) EK(cudaEventRecord(mem[(size_t)k].ready, s));
+        EK(cudaFreeAsync(d_t, s));
+        EK(cudaFreeAsync(d_n, s));
+        EK(cudaFreeAsync(d_ns, s));
+        // (pageable host-to-device copies return once the data is staged, so
+        // the host lists may go out of scope; the kernels run on asynchronously)
+        pending.clear();
         return GABP_OK;
     }
 
@@ -345,6 +429,30 @@ class Engine {
         ++launches;
         M.formed = true;
         M.active = true;
+        lists_dirty = true;
+        return GABP_OK;
+    }
+
+    // Arms several formed instances with one launch (their own iters / tol).
+    gabp_status activate_list(const std::vector<int>& slots)
+    {
+        if (slots.empty()) return GABP_OK;
+        std::vector<int2> bl;
+        std::vector<double> bt;
+        for (int k : slots) {
+            Member& M = mem[(size_t)k];
+            EK(cudaStreamWaitEvent(stream, M.ready, 0));
+            const double t0 = (q_mode != 0 && M.refine_left > 0) ? std::max(M.tol, msg_bf16 ? 1e-3 : kRefineStart)
+                                                                   : M.tol;
+            bl.push_back(make_int2(k, M.iters));
+            bt.push_back(t0);
+            M.formed = true;
+            M.active = true;
+        }
+        EK(cudaMemcpyAsync(d_begin_list, bl.data(), bl.size() * sizeof(int2), cudaMemcpyHostToDevice, stream));
+        EK(cudaMemcpyAsync(d_begin_tol, bt.data(), bt.size() * sizeof(double), cudaMemcpyHostToDevice, stream));
+        launch_begin_list(d_tab, d_begin_list, d_begin_tol, (int)bl.size(), stream);
+        ++launches;
         lists_dirty = true;
         return GABP_OK;
     }
@@ -436,8 +544,9 @@ class Engine {
     }
 
     // After a chunk: instances that stopped either start a refinement pass
-    // (precision form) or finish.  All their device work is queued first and
-    // waited for once.  Returns the number still running.
+    // (precision form) or finish.  The end-of-solve work of all of them runs
+    // as one launch per kernel over lists of their tiles, node blocks and
+    // slots, waited for once.  Returns the number still running.
     gabp_status advance(int* running, std::vector<int>* finished = nullptr)
     {
         int run = 0;
@@ -450,40 +559,66 @@ class Engine {
         }
         if (stopped.empty()) { *running = run; return GABP_OK; }
         // 1. final residual (and, in the precision form, the refined means)
-        for (int k : stopped) {
+        std::vector<int4> tiles;
+        std::vector<int2> nb;
+        std::vector<char> ref(stopped.size(), 0);
+        for (size_t u = 0; u < stopped.size(); ++u) {
+            const int k = stopped[u];
             Member& M = mem[(size_t)k];
             const Ctrl& c = h_ctrl[k];
-            const bool ref = c.status == 0 && q_mode != 0 && (M.refining || M.refine_left > 0);
-            const float* mu = M.inst.agg + (size_t)(c.kstar & 1) * 3 * M.inst.npad + 2 * (size_t)M.inst.npad;
-            if (ref) {
+            StopOp& op = h_ops[(size_t)k];
+            op = StopOp{};
+            op.alpha = M.alpha;
+            op.blockbuf = M.blockbuf;
+            op.final3 = M.final3;
+            op.sv_threshold = (float)sv_threshold;
+            ref[u] = c.status == 0 && q_mode != 0 && (M.refining || M.refine_left > 0);
+            if (ref[u]) {
                 // Defect correction on the FP32-Gram residual: accumulate the
                 // means (or the correction) and form r = 1 - Q32 mu_acc.
-                launch_axpy_mu(M.inst, c.kstar, M.mu_acc, M.refining ? 0 : 1, stream);
+                op.acc = M.mu_acc;
+                op.axpy_buf = c.kstar;
+                op.axpy_first = M.refining ? 0 : 1;
+                op.mu = M.mu_acc;
+                op.r_out = M.r32;
                 if (M.refining) ++M.refine_done;
                 M.refining = true;
-                mu = M.mu_acc;
-                ++launches;
-            } else if (M.refining) {
-                mu = M.mu_acc;
+            } else {
+                op.mu = M.refining ? M.mu_acc
+                                   : M.inst.agg + (size_t)(c.kstar & 1) * 3 * M.inst.npad + 2 * (size_t)M.inst.npad;
             }
-            launch_final(M.inst, M.work, M.ntiles, mu, M.alpha, M.final3, M.blockbuf, (float)sv_threshold,
-                         ref ? M.r32 : nullptr, stream);
-            launches += 3;
-            EK(cudaMemcpyAsync(h_f3 + 3 * (size_t)k, M.final3, 3 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+            const int Nt = M.inst.Nt;
+            int L = 0;
+            for (int I = 0; I < Nt; ++I)
+                for (int J = I; J < Nt; ++J, ++L) tiles.push_back(make_int4(k, I, J, L));
+            for (int b = 0; b < M.nblk; ++b) nb.push_back(make_int2(k, b));
         }
+        EK(cudaMemcpyAsync(d_ops, h_ops, (size_t)cap_members * sizeof(StopOp), cudaMemcpyHostToDevice, stream));
+        EK(cudaMemcpyAsync(d_stop_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
+        EK(cudaMemcpyAsync(d_stop_nbl, nb.data(), nb.size() * sizeof(int2), cudaMemcpyHostToDevice, stream));
+        EK(cudaMemcpyAsync(d_stop_members, stopped.data(), stopped.size() * sizeof(int), cudaMemcpyHostToDevice,
+                           stream));
+        launch_axpy_list(d_tab, d_ops, d_stop_nbl, (int)nb.size(), stream);
+        launch_final(d_tab, d_ops, d_stop_tiles, (long long)tiles.size(), d_stop_nbl, (int)nb.size(), d_stop_members,
+                     (int)stopped.size(), d_f3, stream);
+        launches += 4;
+        EK(cudaGetLastError());
+        EK(cudaMemcpyAsync(h_f3, d_f3, (size_t)cap_members * 3 * sizeof(double), cudaMemcpyDeviceToHost, stream));
         EK(cudaStreamSynchronize(stream));
         // 2. next correction pass, or done
+        std::vector<int2> rnb, blist;
+        std::vector<double> btol;
         bool copies = false;
-        for (int k : stopped) {
+        for (size_t u = 0; u < stopped.size(); ++u) {
+            const int k = stopped[u];
             Member& M = mem[(size_t)k];
-            const Ctrl& c = h_ctrl[k];
             const double rn = h_f3[3 * (size_t)k];
-            if (c.status == 0 && M.refining && rn >= M.tol && M.refine_left > 0) {
+            if (ref[u] && rn >= M.tol && M.refine_left > 0) {
                 // solve Q_bf d = r with the P messages kept (H restarted)
                 --M.refine_left;
-                launch_refine_rhs(M.inst, M.r32, stream);
-                launch_begin(d_tab + k, 1, M.iters, std::max(M.tol * 0.5, (msg_bf16 ? 3e-2 : 1e-2) * rn), stream);
-                launches += 2;
+                for (int b = 0; b < M.nblk; ++b) rnb.push_back(make_int2(k, b));
+                blist.push_back(make_int2(k, M.iters));
+                btol.push_back(std::max(M.tol * 0.5, (msg_bf16 ? 3e-2 : 1e-2) * rn));
                 ++run;
                 continue;
             }
@@ -491,7 +626,17 @@ class Engine {
             copies = true;
             if (finished) finished->push_back(k);
         }
-        if (copies) EK(cudaStreamSynchronize(stream));
+        if (!blist.empty()) {
+            EK(cudaMemcpyAsync(d_stop_nbl, rnb.data(), rnb.size() * sizeof(int2), cudaMemcpyHostToDevice, stream));
+            EK(cudaMemcpyAsync(d_begin_list, blist.data(), blist.size() * sizeof(int2), cudaMemcpyHostToDevice, stream));
+            EK(cudaMemcpyAsync(d_begin_tol, btol.data(), btol.size() * sizeof(double), cudaMemcpyHostToDevice, stream));
+            launch_refine_rhs_list(d_tab, d_ops, d_stop_nbl, (int)rnb.size(), stream);
+            launch_begin_list(d_tab, d_begin_list, d_begin_tol, (int)blist.size(), stream);
+            launches += 2;
+            EK(cudaGetLastError());
+        }
+        EK(cudaStreamSynchronize(stream));   // host vectors above go out of scope
+        (void)copies;
         *running = run;
         return GABP_OK;
     }
@@ -568,6 +713,7 @@ class Engine {
 }  // namespace gabp
 
 using gabp::Engine;
+using gabp::ms_since;
 
 extern "C" {
 
@@ -617,8 +763,12 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
         set_last_error(("gabp_batch_solve: needs " + std::to_string(bytes / 1e9) + " GB of device memory").c_str());
         return GABP_ENOMEM;
     }
+    using clk = std::chrono::steady_clock;
+    const auto t_all = clk::now();
+    BatchPhases ph{};
     Engine E;
     if (gabp_status st = E.init((int)count, tiles, (int)nblk, o)) return st;
+    auto t0 = clk::now();
     for (int64_t k = 0; k < count; ++k) {
         if (gabp_status st = E.add((int)k, probs[k], results[k].alpha, o.ptr_mode)) return st;
         E.mem[(size_t)k].iters = iters;
@@ -626,6 +776,7 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
         E.mem[(size_t)k].refine_left = o.q_mode != 0 ? o.refine : 0;
         E.mem[(size_t)k].ticket = k;
     }
+    if (gabp_status st = E.form_pending()) return st;
     if (cudaStreamSynchronize(E.side) != cudaSuccess) return E.fail(GABP_ECUDA, "formation failed");
     // labels / features validated by the staging kernels
     if (cudaMemcpy(E.h_ctrl, E.d_ctrl, (size_t)count * sizeof(Ctrl), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -633,8 +784,14 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
     for (int64_t k = 0; k < count; ++k)
         if (E.h_ctrl[k].status != 0)
             return E.fail(GABP_EINVAL, "problem " + std::to_string(k) + ": non-finite feature or label not +-1");
-    for (int64_t k = 0; k < count; ++k)
-        if (gabp_status st = E.activate((int)k, iters, tol)) return st;
+    {
+        std::vector<int> all((size_t)count);
+        for (int64_t k = 0; k < count; ++k) all[(size_t)k] = (int)k;
+        if (gabp_status st = E.activate_list(all)) return st;
+    }
+    cudaStreamSynchronize(E.stream);
+    ph.form_ms = ms_since(t0);
+    t0 = clk::now();
     if (o.chunk <= 0) {
         if (gabp_status st = E.autotune(iters)) return st;
         const double t0 = (o.q_mode != 0 && o.refine > 0) ? std::max(tol, o.msg_bf16 ? 1e-3 : 1e-4) : tol;
@@ -642,12 +799,21 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
     } else {
         E.chunk = o.chunk;
     }
+    ph.tune_ms = ms_since(t0);
     const int max_loops = (int)(((long long)iters * (1 + o.refine)) / std::max(1, E.chunk) + 4 * (2 + o.refine) + 8);
     int running = (int)count;
     for (int loop = 0; loop < max_loops && running > 0; ++loop) {
+        t0 = clk::now();
         if (gabp_status st = E.run_chunk(E.chunk)) return st;
+        ph.rounds_ms += ms_since(t0);
+        t0 = clk::now();
         if (gabp_status st = E.advance(&running)) return st;
+        ph.stop_ms += ms_since(t0);
+        ++ph.chunks;
     }
+    ph.launches = E.launches;
+    ph.total_ms = ms_since(t_all);
+    g_last_phases = ph;
     if (running > 0) return E.fail(GABP_ECUDA, "batch did not reach its stop condition");
     gabp_status worst = GABP_OK;
     for (int64_t k = 0; k < count; ++k) {
@@ -658,6 +824,19 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
     }
     if (worst != GABP_OK) set_last_error("one or more problems failed; see their result status");
     return worst;
+}
+
+gabp_status gabp_batch_last_phases(double* out6)
+{
+    if (!out6) return GABP_EINVAL;
+    const gabp::BatchPhases& p = gabp::g_last_phases;
+    out6[0] = p.form_ms;
+    out6[1] = p.tune_ms;
+    out6[2] = p.rounds_ms;
+    out6[3] = p.stop_ms;
+    out6[4] = p.total_ms;
+    out6[5] = (double)p.chunks;
+    return GABP_OK;
 }
 
 // ------------------------------------------------------------------ server
@@ -749,12 +928,14 @@ gabp_status gabp_server_step(gabp_server_t s, int32_t* active, int32_t* queued, 
         s->forming.push_back(slot);
         s->queue.pop_front();
     }
+    if (gabp_status st = E.form_pending()) return st;
     // 2. instances whose Q is ready join the sweeps
+    std::vector<int> ready;
     for (size_t k = 0; k < s->forming.size();) {
         const int slot = s->forming[k];
         cudaError_t q = cudaEventQuery(E.mem[(size_t)slot].ready);
         if (q == cudaSuccess) {
-            if (gabp_status st = E.activate(slot, s->cfg.iters, s->cfg.tol)) return st;
+            ready.push_back(slot);
             s->forming.erase(s->forming.begin() + (long)k);
         } else if (q == cudaErrorNotReady) {
             ++k;
@@ -762,6 +943,7 @@ gabp_status gabp_server_step(gabp_server_t s, int32_t* active, int32_t* queued, 
             return E.fail(GABP_ECUDA, std::string("formation: ") + cudaGetErrorString(q));
         }
     }
+    if (gabp_status st = E.activate_list(ready)) return st;
     // 3. one chunk of rounds over every live instance, then retire the finished
     int running = 0;
     bool any = false;

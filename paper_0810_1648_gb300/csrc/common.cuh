@@ -99,6 +99,22 @@ struct Sched {
     int ninst;
 };
 
+// What the end-of-solve kernels do for one instance (indexed by its slot):
+// final residual / objective / alpha of the means `mu`, the FP32 residual to
+// r_out when not null, and (refinement) acc = mu(axpy_buf) or acc += it first.
+struct StopOp {
+    const float* mu;
+    float* r_out;
+    float* alpha;
+    double* blockbuf;
+    double* final3;
+    float* acc;
+    int axpy_buf;
+    int axpy_first;
+    float sv_threshold;
+    int pad;
+};
+
 // Launch shapes of one round (persistent sweep CTAs, finalize CTAs).
 struct RoundGrid {
     int sweep = 1;
@@ -126,11 +142,7 @@ int bf16_chunks(int m);
 size_t bf16_pack_bytes(int Nt, int m);
 // Restart: Step-1 aggregates from the stored diagonal and b, t = 0.
 void launch_reset(const Inst& p, cudaStream_t s);
-// Refinement: b := r (FP32 residual of the accurate Q), htilde := b, next sweep
-// restarts the H messages (the P messages, independent of b, are kept).
-void launch_refine_rhs(const Inst& p, const float* r, cudaStream_t s);
-// acc += mutilde of buffer buf (n entries).
-void launch_axpy_mu(const Inst& p, int buf, float* acc, int first, cudaStream_t s);
+
 // Diagonal rule, Step-1 aggregates and control reset.
 void launch_init(const Inst& p, int diag_rule, float delta, cudaStream_t s);
 // Solve control: arm the control blocks of tab[0..ninst) for `iters` more rounds with tolerance `tol`.
@@ -149,10 +161,21 @@ cudaError_t prepare_sweep_rc();
 void launch_round(const Inst* tab, const int4* work, const int2* nbl, const Sched* sched, const RoundGrid& g,
                   int q_mode, int msg_bf16, cudaStream_t s, cudaEvent_t* ev = nullptr);
 // Final FP32-Gram residual r = 1 - Q mu (FP64 sums), dual objective and
-// alpha = clip(mu, 0, C) for the means mu; out3 = {||r||_inf, objective, #SV};
-// r_out (optional) receives r in FP32.
-void launch_final(const Inst& p, const int4* work, long long ntiles, const float* mu, float* alpha,
-                  double* out3, double* blockbuf, float sv_threshold, float* r_out, cudaStream_t s);
+// alpha = clip(mu, 0, C) of the listed instances (their tiles, node blocks
+// and slots), per ops[slot]; results in ops[slot].final3 and f3_all[3 slot].
+void launch_final(const Inst* tab, const StopOp* ops, const int4* tiles, long long ntiles, const int2* nbl,
+                  int nblocks, const int* members, int nmembers, double* f3_all, cudaStream_t s);
+// Refinement over listed node blocks: acc (+)= mutilde (ops[slot].axpy_*).
+void launch_axpy_list(const Inst* tab, const StopOp* ops, const int2* nbl, int nblocks, cudaStream_t s);
+// Refinement over listed node blocks: b := ops[slot].r_out, H restarts.
+void launch_refine_rhs_list(const Inst* tab, const StopOp* ops, const int2* nbl, int nblocks, cudaStream_t s);
+// Formation over listed node blocks of several instances (FP32 rows already in X):
+// staging checks / norms / b = 1; BF16 packing + norms; diagonal rule + Step 1.
+void launch_stage_list(const Inst* tab, const int2* nbl, int nblocks, cudaStream_t s);
+cudaError_t launch_pack_list(const Inst* tab, const int2* nbl, int nblocks, cudaStream_t s);
+void launch_init_list(const Inst* tab, const int2* nbl, int nblocks, int diag_rule, float delta, cudaStream_t s);
+// Arms listed instances: list entries {slot, iters} with their tolerances.
+void launch_begin_list(Inst* tab, const int2* list, const double* tols, int count, cudaStream_t s);
 // Decision values for t test rows (Xt FP32, sqt norms) using alpha.
 void launch_decision(const Inst& p, const float* Xt, const float* sqt, int t, const float* alpha,
                      const int2* work, long long ntiles, float* part, float* out, cudaStream_t s);

@@ -149,12 +149,13 @@ __device__ __forceinline__ void reduce_and_write(EpiSmem& es, float (&rs)[NQ][8]
 }
 
 // ---------------------------------------------------------------- staging
-__global__ void k_stage(const void* __restrict__ X, int x_f64, int n, int m, const float* __restrict__ y,
-                        float* __restrict__ Xf, float* __restrict__ sq, float* __restrict__ b, Ctrl* ctrl)
+// One row: FP32 copy (from FP32 or FP64 input), squared norm, finiteness and
+// label checks, b_i = 1 (the SVM right-hand side: the linear term 1'h of the dual).
+__device__ __forceinline__ void stage_row(const void* __restrict__ X, int x_f64, int i, int m,
+                                          const float* __restrict__ y, float* __restrict__ Xf,
+                                          float* __restrict__ sq, float* __restrict__ b, Ctrl* ctrl)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if (b) b[i] = 1.f;   // SVM right-hand side: the linear term 1'h of the dual
+    if (b) b[i] = 1.f;
     float s = 0.f;
     bool ok = true;
     for (int k = 0; k < m; ++k) {
@@ -170,6 +171,24 @@ __global__ void k_stage(const void* __restrict__ X, int x_f64, int n, int m, con
         ok &= (yi == 1.f || yi == -1.f);
     }
     if (!ok && atomicCAS(&ctrl->status, 0, (int)ST_EINVAL) == 0) ctrl->bad_index = i;
+}
+
+__global__ void k_stage(const void* __restrict__ X, int x_f64, int n, int m, const float* __restrict__ y,
+                        float* __restrict__ Xf, float* __restrict__ sq, float* __restrict__ b, Ctrl* ctrl)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) stage_row(X, x_f64, i, m, y, Xf, sq, b, ctrl);
+}
+
+// Listed node blocks of instances whose FP32 rows already sit in their X.
+__global__ void k_stage_list(const Inst* __restrict__ tab, const int2* __restrict__ nbl)
+{
+    const int2 nb = nbl[blockIdx.x];
+    const Inst& p = tab[nb.x];
+    const int i = nb.y * 32 + threadIdx.x;
+    if (threadIdx.x < 32 && i < p.n)
+        stage_row(p.X, 0, i, p.m, p.y, const_cast<float*>(p.X), const_cast<float*>(p.sq), const_cast<float*>(p.b),
+                  p.ctrl);
 }
 
 // ------------------------------------------------------- Q tile formation
@@ -225,14 +244,19 @@ __global__ void __launch_bounds__(NTHREADS) k_form_q(const Inst* __restrict__ ta
 }
 
 // ------------------------------------------- final residual and Q alpha
-// Off-diagonal sums sum_{j != i} Q_ij mu_j (-> part[0]) and
-// sum_{j != i} Q_ij alpha_j (-> part[1]) with alpha = clip(mu, 0, C), Q
-// recomputed in FP32 (bitwise equal to the stored FP32 tiles).
-__global__ void __launch_bounds__(NTHREADS) k_final_tiles(Inst p, const int4* __restrict__ work,
-                                                          const float* __restrict__ mu)
+// For every instance k listed: off-diagonal sums sum_{j != i} Q_ij mu_j
+// (-> part[0]) and sum_{j != i} Q_ij alpha_j (-> part[1]) with
+// alpha = clip(mu, 0, C) and mu = ops[k].mu, Q recomputed in FP32 (bitwise
+// equal to the stored FP32 tiles).  One CTA per listed tile.
+__global__ void __launch_bounds__(NTHREADS) k_final_tiles(const Inst* __restrict__ tab,
+                                                          const StopOp* __restrict__ ops,
+                                                          const int4* __restrict__ work)
 {
     __shared__ __align__(16) TileSmem sm;
-    const int I = work[blockIdx.x].y, J = work[blockIdx.x].z, n = p.n;
+    const int4 w = work[blockIdx.x];
+    const Inst& p = tab[w.x];
+    const float* __restrict__ mu = ops[w.x].mu;
+    const int I = w.y, J = w.z, n = p.n;
     const GramSide S{p.X, p.sq, n};
     float acc[8][8];
     gram_tile(S, S, p.m, I, J, sm.g, acc);
@@ -275,14 +299,20 @@ __global__ void __launch_bounds__(NTHREADS) k_final_tiles(Inst p, const int4* __
     reduce_and_write<2>(sm.e, rs, cs, parts, n, I, J);
 }
 
-// Per node: r_i = b_i - Q_ii mu_i - sum part0, (Q alpha)_i = Q_ii alpha_i + sum part1;
-// writes alpha; block partials {max |r_i|, sum alpha_i - 1/2 alpha_i (Q alpha)_i, #SV}.
-__global__ void __launch_bounds__(256) k_final_nodes(Inst p, const float* __restrict__ mu,
-                                                     float* __restrict__ alpha, double* __restrict__ blockbuf,
-                                                     float sv_threshold, float* __restrict__ r_out)
+// Per node of a listed node block: r_i = 1 - Q_ii mu_i - sum part0,
+// (Q alpha)_i = Q_ii alpha_i + sum part1; writes alpha (and r in FP32 when
+// requested); block partials {max |r_i|, sum alpha_i - 1/2 alpha_i (Q alpha)_i,
+// #SV} into the instance's block buffer.
+__global__ void __launch_bounds__(256) k_final_nodes(const Inst* __restrict__ tab,
+                                                     const StopOp* __restrict__ ops,
+                                                     const int2* __restrict__ nbl)
 {
+    const int2 nb = nbl[blockIdx.x];
+    const Inst& p = tab[nb.x];
+    const StopOp& op = ops[nb.x];
+    const float* __restrict__ mu = op.mu;
     const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
-    const int x = blockIdx.x * 32 + lane, n = p.n, Nt = p.Nt;
+    const int x = nb.y * 32 + lane, n = p.n, Nt = p.Nt;
     const float* p0 = p.part;
     const float* p1 = p.part + (size_t)Nt * n;
     double s0 = 0.0, s1 = 0.0;
@@ -303,14 +333,14 @@ __global__ void __launch_bounds__(256) k_final_nodes(Inst p, const float* __rest
             const double qd = p.qdiag[x], m = mu[x];
             const float af = fminf(fmaxf(mu[x], 0.f), p.C);
             const double al = af;
-            alpha[x] = af;
+            op.alpha[x] = af;
             const double r = 1.0 - qd * m - a0;   // residual of the SVM system Q mu = 1
-            if (r_out) r_out[x] = (float)r;
+            if (op.r_out) op.r_out[x] = (float)r;
             absr = fabs(r);
             if (!(absr <= DBL_MAX)) absr = INFINITY;
             const double qa = qd * al + a1;
             obj = al - 0.5 * al * qa;
-            nsv = af > sv_threshold ? 1.0 : 0.0;
+            nsv = af > op.sv_threshold ? 1.0 : 0.0;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -319,23 +349,28 @@ __global__ void __launch_bounds__(256) k_final_nodes(Inst p, const float* __rest
             nsv += __shfl_xor_sync(0xffffffffu, nsv, o);
         }
         if (lane == 0) {
-            blockbuf[3 * blockIdx.x + 0] = absr;
-            blockbuf[3 * blockIdx.x + 1] = obj;
-            blockbuf[3 * blockIdx.x + 2] = nsv;
+            op.blockbuf[3 * nb.y + 0] = absr;
+            op.blockbuf[3 * nb.y + 1] = obj;
+            op.blockbuf[3 * nb.y + 2] = nsv;
         }
     }
 }
 
-// Fixed-order reduction of the block partials -> out3 = {rinf, objective, nsv}.
-__global__ void k_final_reduce(const double* __restrict__ blockbuf, int nb, double* __restrict__ out3)
+// One CTA per listed instance: fixed-order reduction of its block partials
+// -> final3 = {||r||_inf, objective, #SV}, also copied to f3_all[3 * slot].
+__global__ void k_final_reduce(const Inst* __restrict__ tab, const StopOp* __restrict__ ops,
+                               const int* __restrict__ members, double* __restrict__ f3_all)
 {
     __shared__ double s[3][256];
+    const int slot = members[blockIdx.x];
+    const StopOp& op = ops[slot];
+    const int nb = (tab[slot].n + 31) / 32;
     const int tid = threadIdx.x;
     double m = 0.0, o = 0.0, c = 0.0;
     for (int k = tid; k < nb; k += 256) {
-        m = fmax(m, blockbuf[3 * k]);
-        o += blockbuf[3 * k + 1];
-        c += blockbuf[3 * k + 2];
+        m = fmax(m, op.blockbuf[3 * k]);
+        o += op.blockbuf[3 * k + 1];
+        c += op.blockbuf[3 * k + 2];
     }
     s[0][tid] = m; s[1][tid] = o; s[2][tid] = c;
     __syncthreads();
@@ -347,7 +382,12 @@ __global__ void k_final_reduce(const double* __restrict__ blockbuf, int nb, doub
         }
         __syncthreads();
     }
-    if (tid == 0) { out3[0] = s[0][0]; out3[1] = s[1][0]; out3[2] = s[2][0]; }
+    if (tid == 0) {
+        for (int q = 0; q < 3; ++q) {
+            op.final3[q] = s[q][0];
+            if (f3_all) f3_all[3 * slot + q] = s[q][0];
+        }
+    }
 }
 
 // ----------------------------------------------------------------- decision
@@ -426,6 +466,11 @@ __global__ void k_get_q(Inst p, const int4* __restrict__ work, int q_bf16, float
 
 }  // namespace
 
+void launch_stage_list(const Inst* tab, const int2* nbl, int nblocks, cudaStream_t s)
+{
+    if (nblocks > 0) k_stage_list<<<nblocks, 32, 0, s>>>(tab, nbl);
+}
+
 void launch_stage(const void* X, int x_f64, int n, int m, const float* y, float* Xf, float* sq,
                   float* b, Ctrl* ctrl, cudaStream_t s)
 {
@@ -437,13 +482,12 @@ void launch_form_q(const Inst* tab, const int4* work, long long ntiles, int stor
     if (ntiles > 0) k_form_q<<<(unsigned)ntiles, NTHREADS, 0, s>>>(tab, work, store_f32);
 }
 
-void launch_final(const Inst& p, const int4* work, long long ntiles, const float* mu, float* alpha,
-                  double* out3, double* blockbuf, float sv_threshold, float* r_out, cudaStream_t s)
+void launch_final(const Inst* tab, const StopOp* ops, const int4* tiles, long long ntiles, const int2* nbl,
+                  int nblocks, const int* members, int nmembers, double* f3_all, cudaStream_t s)
 {
-    k_final_tiles<<<(unsigned)ntiles, NTHREADS, 0, s>>>(p, work, mu);
-    const int nb = (p.n + 31) / 32;
-    k_final_nodes<<<nb, 256, 0, s>>>(p, mu, alpha, blockbuf, sv_threshold, r_out);
-    k_final_reduce<<<1, 256, 0, s>>>(blockbuf, nb, out3);
+    if (ntiles > 0) k_final_tiles<<<(unsigned)ntiles, NTHREADS, 0, s>>>(tab, ops, tiles);
+    if (nblocks > 0) k_final_nodes<<<nblocks, 256, 0, s>>>(tab, ops, nbl);
+    if (nmembers > 0) k_final_reduce<<<nmembers, 256, 0, s>>>(tab, ops, members, f3_all);
 }
 
 void launch_decision(const Inst& p, const float* Xt, const float* sqt, int t, const float* alpha,

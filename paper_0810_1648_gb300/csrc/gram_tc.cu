@@ -55,6 +55,41 @@ __global__ void k_pack_bf16(const float* __restrict__ Xf, int n, int m, int nkc,
     Xp[off16] = *reinterpret_cast<const uint4*>(v);
 }
 
+// Listed node blocks (32 rows): packing (8 threads per row over the 8-feature
+// groups) and the BF16 row norms.
+__global__ void k_pack_list(const Inst* __restrict__ tab, const int2* __restrict__ nbl)
+{
+    const int2 nb = nbl[blockIdx.x];
+    const Inst& p = tab[nb.x];
+    const int rl = threadIdx.x >> 3, gsub = threadIdx.x & 7;
+    const int r = nb.y * 32 + rl, n = p.n, m = p.m, nkc = p.nkc;
+    const int Nt = p.Nt;
+    if (r >= Nt * T) return;
+    const float* Xf = p.X;
+    uint4* Xp = static_cast<uint4*>(const_cast<void*>(p.Xp));
+    const int groups = nkc * (KCH / 8);
+    const int I = r / T, rr = r % T;
+    for (int gk = gsub; gk < groups; gk += 8) {
+        const int kc = gk / (KCH / 8), kg = gk % (KCH / 8);
+        __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = kc * KCH + kg * 8 + u;
+            v[u] = __float2bfloat16_rn((r < n && k < m) ? Xf[(size_t)r * m + k] : 0.f);
+        }
+        const size_t blk = (size_t)I * nkc + kc;
+        Xp[blk * (BLK_BYTES / 16) + (size_t)((rr / 8) * (KCH / 8) + kg) * 8 + (rr % 8)] = *reinterpret_cast<const uint4*>(v);
+    }
+    if (gsub == 0 && r < n) {
+        float sacc = 0.f;
+        for (int k = 0; k < m; ++k) {
+            const float v = __bfloat162float(__float2bfloat16_rn(Xf[(size_t)r * m + k]));
+            sacc = fmaf(v, v, sacc);
+        }
+        const_cast<float*>(p.sqb)[r] = sacc;
+    }
+}
+
 // ||bf16(x_i)||^2 in FP32 from the rounded values.
 __global__ void k_norms_bf16(const float* __restrict__ Xf, int n, int m, float* __restrict__ sqb)
 {
@@ -231,6 +266,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 constexpr size_t tc_smem_bytes() { return 1024 + XSTAGES * 2 * BLK_BYTES + sizeof(TcSmem); }
 
 }  // namespace
+
+cudaError_t launch_pack_list(const Inst* tab, const int2* nbl, int nblocks, cudaStream_t s)
+{
+    if (nblocks > 0) k_pack_list<<<nblocks, 256, 0, s>>>(tab, nbl);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pack_bf16(const float* Xf, int n, int m, int nkc, int Nt, void* Xp, float* sqb, cudaStream_t s)
 {

@@ -244,6 +244,29 @@ __device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char
     using T2 = typename MSG::T2;
     const T2* Sp = reinterpret_cast<const T2*>(S) + (size_t)cw * T;
     const T2* Sh = reinterpret_cast<const T2*>(S + pchunk<MSG>()) + (size_t)cw * T;
+    if (FROZEN) {
+        // With P at its fixed point, P_ij = -q^2 / d_i, so the H update
+        // -q (htilde_i - H_ji) / d_i equals P_ij (htilde_i - H_ji) / q: one
+        // reciprocal per pair, no cavity subtraction (the cavities were
+        // checked when these P values were formed).  q = 0 gives P = 0, H = 0.
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = lane + 32 * k;
+            if (FULL || (c < cols && (!diag || c > r))) {
+                const float q = qsrc.q(S, cw, r, c, it);
+                const float qi = q != 0.f ? rcp_nr(q) : 0.f;
+                const float2 pv = MSG::load(Sp[c]);                                            // {P_ij, P_ji}
+                const float2 hv = zero_h ? make_float2(0.f, 0.f) : MSG::load(Sh[c]);           // {H_ij, H_ji}
+                const float2 nh = MSG::round(pv.x * (rH - hv.y) * qi, pv.y * (cv.H[k] - hv.x) * qi);
+                MSG::store(&gh[r * T + c], nh);
+                rs[1] += nh.y;
+                rs[2] = fmaf(q, cv.M[k], rs[2]);
+                cv.aH[k] += nh.x;
+                cv.aR[k] = fmaf(q, rM, cv.aR[k]);
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int c = lane + 32 * k;
@@ -257,7 +280,7 @@ __device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char
             const float ii = rcp_nr(di), ij = rcp_nr(dj);
             const float2 nh = MSG::round(-q * (rH - hv.y) * ii, -q * (cv.H[k] - hv.x) * ij);   // {H_ij, H_ji}
             MSG::store(&gh[r * T + c], nh);
-            if (!FROZEN) {
+            {
                 const float q2 = q * q;
                 const float2 np = MSG::round(-q2 * ii, -q2 * ij);                            // {P_ij, P_ji}
                 MSG::store(&gp[r * T + c], np);
@@ -840,27 +863,36 @@ __global__ void k_reset(Inst p)
 }
 
 // Correction system Q d = r with the current P messages: b := r, the H
-// messages restart from 0, so htilde = b and mutilde = b / Ptilde.
-__global__ void k_refine_rhs(Inst p, const float* __restrict__ r)
+// messages restart from 0, so htilde = b and mutilde = b / Ptilde.  Over a
+// list of node blocks; block 0 of an instance flags the H restart.
+__global__ void k_refine_rhs_list(const Inst* __restrict__ tab, const StopOp* __restrict__ ops,
+                                  const int2* __restrict__ nbl)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int2 nb = nbl[blockIdx.x];
+    const Inst& p = tab[nb.x];
     Ctrl* c = p.ctrl;
     const int t = *(volatile int*)&c->t;
-    if (blockIdx.x == 0 && threadIdx.x == 0) c->zero_h = 1;
-    if (x >= p.n) return;
+    const int x = nb.y * 32 + threadIdx.x;
+    if (nb.y == 0 && threadIdx.x == 0) c->zero_h = 1;
+    if (threadIdx.x >= 32 || x >= p.n) return;
     float* cur = p.agg + (size_t)(t & 1) * 3 * p.npad;
-    const float bx = r[x];
+    const float bx = ops[nb.x].r_out[x];
     const_cast<float*>(p.b)[x] = bx;
     cur[p.npad + x] = bx;
     cur[2 * p.npad + x] = bx / cur[x];
 }
 
-__global__ void k_axpy_mu(Inst p, int buf, float* __restrict__ acc, int first)
+// acc = mutilde(buf) (first pass) or acc += mutilde(buf), over node blocks.
+__global__ void k_axpy_list(const Inst* __restrict__ tab, const StopOp* __restrict__ ops,
+                            const int2* __restrict__ nbl)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= p.n) return;
-    const float m = p.agg[(size_t)(buf & 1) * 3 * p.npad + 2 * (size_t)p.npad + x];
-    acc[x] = first ? m : acc[x] + m;
+    const int2 nb = nbl[blockIdx.x];
+    const Inst& p = tab[nb.x];
+    const StopOp& op = ops[nb.x];
+    const int x = nb.y * 32 + threadIdx.x;
+    if (threadIdx.x >= 32 || x >= p.n || !op.acc) return;
+    const float m = p.agg[(size_t)(op.axpy_buf & 1) * 3 * p.npad + 2 * (size_t)p.npad + x];
+    op.acc[x] = op.axpy_first ? m : op.acc[x] + m;
 }
 
 // Failure-detection self test: one thread waits, with the same bounded wait
@@ -918,6 +950,57 @@ __global__ void k_init(Inst p, int diag_rule, float delta)
     p.agg[2 * p.npad + x] = bx / qf;
 }
 
+// k_init over listed node blocks (block 0 of an instance resets its control block).
+__global__ void k_init_list(const Inst* __restrict__ tab, const int2* __restrict__ nbl, int diag_rule, float delta)
+{
+    const int2 nb = nbl[blockIdx.x];
+    const Inst& p = tab[nb.x];
+    if (nb.y == 0 && threadIdx.x == 0) {
+        Ctrl* c = p.ctrl;
+        c->t = 0;
+        c->done = 1;
+        c->limit = 0;
+        c->kstar = 0;
+        c->converged = 0;
+        c->rmax_bits = 0ull;
+        c->blocks_done = 0u;
+        c->tol = 0.0;
+        c->rinf = -1.0;
+    }
+    const int x = nb.y * 32 + threadIdx.x;
+    if (threadIdx.x >= 32 || x >= p.n) return;
+    double R = 0.0;
+    for (int k = 0; k < p.Nt; ++k) R += (double)p.part[(size_t)k * p.n + x];
+    const double lam2 = p.lam2;
+    const double base = 1.0 + lam2 + 1.0 / (double)p.C;
+    double qd = base;
+    if (diag_rule == 0) {
+        const double dom = (1.0 + (double)delta) * R;
+        qd = dom > base ? dom : base;
+    }
+    const float qf = (float)qd, bx = p.b[x];
+    p.qdiag[x] = qf;
+    p.agg[x] = qf;
+    p.agg[p.npad + x] = bx;
+    p.agg[2 * p.npad + x] = bx / qf;
+}
+
+__global__ void k_begin_list(Inst* tab, const int2* __restrict__ list, const double* __restrict__ tols, int count)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    Ctrl* c = tab[list[k].x].ctrl;
+    const int iters = list[k].y;
+    c->limit = c->t + iters;
+    c->tol = tols[k];
+    c->converged = 0;
+    c->kstar = c->t;
+    c->rinf = -1.0;
+    c->rmax_bits = 0ull;
+    c->blocks_done = 0u;
+    c->done = (c->status != 0 || iters <= 0) ? 1 : 0;
+}
+
 __global__ void k_begin(Inst* tab, int ninst, int iters, double tol)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -966,14 +1049,24 @@ void launch_init(const Inst& p, int diag_rule, float delta, cudaStream_t s)
 
 void launch_reset(const Inst& p, cudaStream_t s) { k_reset<<<(p.n + 255) / 256, 256, 0, s>>>(p); }
 
-void launch_refine_rhs(const Inst& p, const float* r, cudaStream_t s)
+void launch_refine_rhs_list(const Inst* tab, const StopOp* ops, const int2* nbl, int nblocks, cudaStream_t s)
 {
-    k_refine_rhs<<<(p.n + 255) / 256, 256, 0, s>>>(p, r);
+    if (nblocks > 0) k_refine_rhs_list<<<nblocks, 32, 0, s>>>(tab, ops, nbl);
 }
 
-void launch_axpy_mu(const Inst& p, int buf, float* acc, int first, cudaStream_t s)
+void launch_axpy_list(const Inst* tab, const StopOp* ops, const int2* nbl, int nblocks, cudaStream_t s)
 {
-    k_axpy_mu<<<(p.n + 255) / 256, 256, 0, s>>>(p, buf, acc, first);
+    if (nblocks > 0) k_axpy_list<<<nblocks, 32, 0, s>>>(tab, ops, nbl);
+}
+
+void launch_init_list(const Inst* tab, const int2* nbl, int nblocks, int diag_rule, float delta, cudaStream_t s)
+{
+    if (nblocks > 0) k_init_list<<<nblocks, 32, 0, s>>>(tab, nbl, diag_rule, delta);
+}
+
+void launch_begin_list(Inst* tab, const int2* list, const double* tols, int count, cudaStream_t s)
+{
+    if (count > 0) k_begin_list<<<(count + 127) / 128, 128, 0, s>>>(tab, list, tols, count);
 }
 
 void launch_begin(Inst* tab, int ninst, int iters, double tol, cudaStream_t s)

@@ -126,6 +126,7 @@ def load():
         "gabp_selftest_bounded_wait": (st, [I64]),
         "gabp_selftest_reciprocal": (st, [V, V, I64]),
         "gabp_batch_solve": (st, [P(Problem), I64, P(Opts), I32, D, P(Result)]),
+        "gabp_batch_last_phases": (st, [V]),
         "gabp_server_create": (st, [P(ServerCfg), P(V)]),
         "gabp_server_submit": (st, [V, P(Problem), V, P(I64)]),
         "gabp_server_step": (st, [V, P(I32), P(I32), P(I32)]),
@@ -336,6 +337,12 @@ def batch_solve(problems, iters: int, tol: float, **opts):
     if rc not in (OK, ENUMERIC):
         _check(rc)
     return alphas, [res[k].as_dict() for k in range(len(problems))], rc
+
+
+def batch_last_phases() -> dict:
+    out = np.zeros(6)
+    _check(load().gabp_batch_last_phases(_ptr(out)))
+    return dict(zip(["form_ms", "tune_ms", "rounds_ms", "stop_ms", "total_ms", "chunks"], out.tolist()))
 
 
 class Server:
