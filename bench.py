@@ -216,7 +216,8 @@ def run_profile_small(args):
     if not os.path.exists(gabp.LIB_PATH):
         gbuild.build()
     p = workloads.mixture(6144, 128, seed=1, gamma=1.0 / 128, C=10.0)
-    h = gabp.svm_create(p.X, p.y, p.gamma, p.C, gabp.opts_default(chunk=8, q_mode=Q_MODES[args.q_mode]))
+    h = gabp.svm_create(p.X, p.y, p.gamma, p.C, gabp.opts_default(chunk=8, q_mode=Q_MODES[args.q_mode],
+                                                                 msg_bf16=1 if args.msg_bf16 else 0))
     alpha = np.empty(p.n, dtype=np.float32)
     rinf, k = gabp.svm_solve(h, 8, 0.0, alpha)
     gabp.svm_destroy(h)

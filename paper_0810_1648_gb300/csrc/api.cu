@@ -448,7 +448,7 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     std::vector<int2> nb((size_t)nblk);
     for (int b = 0; b < nblk; ++b) nb[(size_t)b] = make_int2(0, b);
     Sched sc{h->ntiles, nblk, 1};
-    h->grid = round_grid(h->ntiles, nblk, o.q_mode, 0);
+    h->grid = round_grid(h->ntiles, nblk, o.q_mode, 0, o.msg_bf16);
     e = cudaMemcpyAsync(h->work, wl.data(), wl.size() * sizeof(int4), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->nbl, nb.data(), nb.size() * sizeof(int2), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->sched, &sc, sizeof sc, cudaMemcpyHostToDevice, h->stream);

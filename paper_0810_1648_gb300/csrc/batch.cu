@@ -261,7 +261,7 @@ class Engine {
     void set_grid(int cps)
     {
         ctas_per_sm = cps;
-        grid = round_grid(cap_tiles, cap_nblk, q_mode, cps);
+        grid = round_grid(cap_tiles, cap_nblk, q_mode, cps, msg_bf16);
     }
 
     void release(Member& m)
@@ -673,7 +673,8 @@ class Engine {
             }
         }
         const int probe = std::max(1, std::min(4, iters));
-        std::vector<int> cands = q_mode == 2 ? std::vector<int>{1} : std::vector<int>{1, 2};
+        std::vector<int> cands = q_mode == 2 ? std::vector<int>{1}
+                                 : (msg_bf16 ? std::vector<int>{1, 2, 3} : std::vector<int>{1, 2});
         float best = 1e30f;
         int best_c = cands[0];
         cudaEvent_t e0, e1;

@@ -150,7 +150,7 @@ void launch_begin(Inst* tab, int ninst, int iters, double tol, cudaStream_t s);
 int num_sms();
 // Grid of a round for up to max_tiles tiles and max_nblocks node blocks
 // (ctas_per_sm: sweep CTAs per SM for the stored-Q kernels, 0 = default).
-RoundGrid round_grid(long long max_tiles, int max_nblocks, int q_mode, int ctas_per_sm);
+RoundGrid round_grid(long long max_tiles, int max_nblocks, int q_mode, int ctas_per_sm, int msg_bf16);
 // Raises the dynamic shared-memory limit of the pair-sweep kernels (once per device).
 cudaError_t prepare_sweep();
 // Fused-recompute form: also raises the shared-memory limit of its sweep kernel.

@@ -27,6 +27,7 @@
 #include "common.cuh"
 #include "ptx.cuh"
 
+#include <algorithm>
 #include <float.h>
 #include <type_traits>
 
@@ -68,6 +69,21 @@ struct MsgF32 {
     static __device__ __forceinline__ float2 load(const T2& v) { return v; }
     static __device__ __forceinline__ float2 round(float a, float b) { return make_float2(a, b); }
     static __device__ __forceinline__ void store(T2* p, float2 v) { __stcs(p, v); }
+    // a lane's pairs of a row: columns 2 lane + {0, 1} and 64 + 2 lane + {0, 1}
+    // (each access of the warp is one contiguous 512-byte span)
+    static constexpr int G = 2;
+    static __device__ __forceinline__ void load4(const T2* row, int lane, float2 (&v)[4])
+    {
+        const float4 a = *reinterpret_cast<const float4*>(row + 2 * lane);
+        const float4 b = *reinterpret_cast<const float4*>(row + 64 + 2 * lane);
+        v[0] = make_float2(a.x, a.y); v[1] = make_float2(a.z, a.w);
+        v[2] = make_float2(b.x, b.y); v[3] = make_float2(b.z, b.w);
+    }
+    static __device__ __forceinline__ void store4(T2* row, int lane, const float2 (&v)[4])
+    {
+        __stcs(reinterpret_cast<float4*>(row + 2 * lane), make_float4(v[0].x, v[0].y, v[1].x, v[1].y));
+        __stcs(reinterpret_cast<float4*>(row + 64 + 2 * lane), make_float4(v[2].x, v[2].y, v[3].x, v[3].y));
+    }
 };
 struct MsgBF16 {
     using T2 = __nv_bfloat162;
@@ -81,10 +97,35 @@ struct MsgBF16 {
         const T2 h = __floats2bfloat162_rn(v.x, v.y);   // exact: v is already rounded
         __stcs(reinterpret_cast<unsigned int*>(p), *reinterpret_cast<const unsigned int*>(&h));
     }
+    // a lane's pairs of a row: columns 4 lane + {0 .. 3} (16 bytes; each
+    // access of the warp is one contiguous 512-byte span)
+    static constexpr int G = 4;
+    static __device__ __forceinline__ void load4(const T2* row, int lane, float2 (&v)[4])
+    {
+        const uint4 u = *reinterpret_cast<const uint4*>(row + 4 * lane);
+        const unsigned w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = __bfloat1622float2(*reinterpret_cast<const T2*>(&w[k]));
+    }
+    static __device__ __forceinline__ void store4(T2* row, int lane, const float2 (&v)[4])
+    {
+        unsigned w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const T2 h = __floats2bfloat162_rn(v[k].x, v[k].y);   // exact: already rounded
+            w[k] = *reinterpret_cast<const unsigned*>(&h);
+        }
+        __stcs(reinterpret_cast<uint4*>(row + 4 * lane), make_uint4(w[0], w[1], w[2], w[3]));
+    }
 };
 
 template <class MSG>
 __host__ __device__ constexpr size_t pchunk() { return (size_t)RC * T * sizeof(typename MSG::T2); }
+
+// Resident sweep CTAs per SM: two for both message types (three for the
+// BF16-message kernel spilled registers and ran slower than two).
+template <class MSG>
+__host__ __device__ constexpr int sweep_ctas() { return 2; }
 template <class MSG>
 __host__ __device__ constexpr size_t state_chunk() { return 2 * pchunk<MSG>(); }
 
@@ -225,15 +266,81 @@ __device__ __forceinline__ float reduce_scatter16(float (&a)[16], int lane)
 }
 
 // Per-tile values a consumer needs for its row updates.
+// Column slot k = 0..3 of a lane in a 128-column row: G consecutive columns
+// in each of 4 / G groups of 32 G columns (G = 2 for FP32 messages, 4 for
+// BF16 messages), so that every warp access to a row is contiguous.
+template <int G>
+__device__ __forceinline__ constexpr int lane_col(int lane, int k)
+{
+    return (k / G) * 32 * G + G * lane + k % G;
+}
+
+// The four slot values of a lane from / to a row of FP32 or BF16 scalars.
+template <int G>
+__device__ __forceinline__ void ld4(const float* row, int lane, float (&o)[4])
+{
+    if constexpr (G == 4) {
+        const float4 a = *reinterpret_cast<const float4*>(row + 4 * lane);
+        o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+    } else {
+        const float2 a = *reinterpret_cast<const float2*>(row + 2 * lane);
+        const float2 b = *reinterpret_cast<const float2*>(row + 64 + 2 * lane);
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+    }
+}
+template <int G>
+__device__ __forceinline__ void ld4(const __nv_bfloat16* row, int lane, float (&o)[4])
+{
+    if constexpr (G == 4) {
+        const uint2 u = *reinterpret_cast<const uint2*>(row + 4 * lane);
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+    } else {
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(row + 2 * lane));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(row + 64 + 2 * lane));
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+    }
+}
+template <int G>
+__device__ __forceinline__ void st4(float* row, int lane, const float (&o)[4])
+{
+    if constexpr (G == 4) {
+        *reinterpret_cast<float4*>(row + 4 * lane) = make_float4(o[0], o[1], o[2], o[3]);
+    } else {
+        *reinterpret_cast<float2*>(row + 2 * lane) = make_float2(o[0], o[1]);
+        *reinterpret_cast<float2*>(row + 64 + 2 * lane) = make_float2(o[2], o[3]);
+    }
+}
+
+// Sums {a, b, c, 0} over the warp in a fixed order: afterwards every lane of
+// the group lane / 8 = k holds the total of quantity k (six shuffles).
+__device__ __forceinline__ float reduce_scatter4(float a, float b, float c, int lane)
+{
+    const bool hi = (lane & 16) != 0;
+    const float k0 = hi ? c : a, k1 = hi ? 0.f : b;
+    const float s0 = hi ? a : c, s1 = hi ? b : 0.f;
+    const float x0 = k0 + __shfl_xor_sync(0xffffffffu, s0, 16);
+    const float x1 = k1 + __shfl_xor_sync(0xffffffffu, s1, 16);
+    const bool b3 = (lane & 8) != 0;
+    float v = (b3 ? x1 : x0) + __shfl_xor_sync(0xffffffffu, b3 ? x0 : x1, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v;
+}
+
 struct ColVals {
     float P[4], H[4], M[4];      // aggregates of the lane's four columns
     float aP[4], aH[4], aR[4];   // column partial sums
 };
 
-// Updates the pairs of row r (one chunk row) held in shared memory.  FULL:
-// interior tile, every column valid (no predicates); FROZEN: the P messages
-// are at their fixed point (no P stores, no P sums).  Adds the lane's share
-// of the row sums to rs[0..2] (P, H, residual).
+// Updates the lane's four pairs (r, lane_col(lane, k)) of chunk row r held in
+// shared memory.  FULL: interior tile, every column valid (no
+// predicates); FROZEN: the P messages are at their fixed point (no P stores,
+// no P sums).  Adds the lane's share of the row sums to rs[0..2] (P, H,
+// residual).  Whole 4-pair groups are stored: on diagonal and edge tiles the
+// slots outside the pair set are never read, so writing them is harmless.
 template <bool FULL, bool FROZEN, class MSG, class QSrc>
 __device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char* S, int cw, int lane, int r,
                                            int cols, bool diag, int it, bool zero, bool zero_h, float rP,
@@ -244,56 +351,134 @@ __device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char
     using T2 = typename MSG::T2;
     const T2* Sp = reinterpret_cast<const T2*>(S) + (size_t)cw * T;
     const T2* Sh = reinterpret_cast<const T2*>(S + pchunk<MSG>()) + (size_t)cw * T;
+    float q[4];
+    qsrc.template q4<MSG::G>(S, cw, r, lane, it, q);
+    bool v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int c = lane_col<MSG::G>(lane, k);
+        v[k] = FULL || (c < cols && (!diag || c > r));
+    }
+    float2 pv[4], hv[4], nh[4];
+    if (zero) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) pv[k] = make_float2(0.f, 0.f);
+    } else {
+        MSG::load4(Sp, lane, pv);                                     // {P_ij, P_ji}
+    }
     if (FROZEN) {
+        if (zero_h) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) hv[k] = make_float2(0.f, 0.f);
+        } else {
+            MSG::load4(Sh, lane, hv);                                 // {H_ij, H_ji}
+        }
         // With P at its fixed point, P_ij = -q^2 / d_i, so the H update
         // -q (htilde_i - H_ji) / d_i equals P_ij (htilde_i - H_ji) / q: one
         // reciprocal per pair, no cavity subtraction (the cavities were
         // checked when these P values were formed).  q = 0 gives P = 0, H = 0.
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const int c = lane + 32 * k;
-            if (FULL || (c < cols && (!diag || c > r))) {
-                const float q = qsrc.q(S, cw, r, c, it);
-                const float qi = q != 0.f ? rcp_nr(q) : 0.f;
-                const float2 pv = MSG::load(Sp[c]);                                            // {P_ij, P_ji}
-                const float2 hv = zero_h ? make_float2(0.f, 0.f) : MSG::load(Sh[c]);           // {H_ij, H_ji}
-                const float2 nh = MSG::round(pv.x * (rH - hv.y) * qi, pv.y * (cv.H[k] - hv.x) * qi);
-                MSG::store(&gh[r * T + c], nh);
-                rs[1] += nh.y;
-                rs[2] = fmaf(q, cv.M[k], rs[2]);
-                cv.aH[k] += nh.x;
-                cv.aR[k] = fmaf(q, rM, cv.aR[k]);
-            }
+            const float qi = q[k] != 0.f ? rcp_nr(q[k]) : 0.f;
+            nh[k] = MSG::round(pv[k].x * (rH - hv[k].y) * qi, pv[k].y * (cv.H[k] - hv[k].x) * qi);
         }
-        return;
+    } else {
+        float2 inv[4];
+        {
+            float2 np[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float di = rP - pv[k].y;        // cavity Ptilde_i - P_ji
+                const float dj = cv.P[k] - pv[k].x;   // cavity Ptilde_j - P_ij
+                bad |= v[k] & !((di > 0.f) & (dj > 0.f));
+                inv[k] = make_float2(rcp_nr(di), rcp_nr(dj));
+                const float q2 = q[k] * q[k];
+                np[k] = MSG::round(-q2 * inv[k].x, -q2 * inv[k].y);
+                if (v[k]) {
+                    changed |= (np[k].x != pv[k].x) | (np[k].y != pv[k].y);
+                    rs[0] += np[k].y;
+                    cv.aP[k] += np[k].x;
+                }
+            }
+            MSG::store4(gp + r * T, lane, np);
+        }
+        if (zero || zero_h) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) hv[k] = make_float2(0.f, 0.f);
+        } else {
+            MSG::load4(Sh, lane, hv);                                 // {H_ij, H_ji}
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            nh[k] = MSG::round(-q[k] * (rH - hv[k].y) * inv[k].x, -q[k] * (cv.H[k] - hv[k].x) * inv[k].y);
     }
+    MSG::store4(gh + r * T, lane, nh);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const int c = lane + 32 * k;
-        if (FULL || (c < cols && (!diag || c > r))) {
-            const float q = qsrc.q(S, cw, r, c, it);
-            const float2 pv = zero ? make_float2(0.f, 0.f) : MSG::load(Sp[c]);              // {P_ij, P_ji}
-            const float2 hv = (zero || zero_h) ? make_float2(0.f, 0.f) : MSG::load(Sh[c]);  // {H_ij, H_ji}
-            const float di = rP - pv.y;        // cavity Ptilde_i - P_ji
-            const float dj = cv.P[k] - pv.x;   // cavity Ptilde_j - P_ij
-            bad |= !((di > 0.f) & (dj > 0.f));
-            const float ii = rcp_nr(di), ij = rcp_nr(dj);
-            const float2 nh = MSG::round(-q * (rH - hv.y) * ii, -q * (cv.H[k] - hv.x) * ij);   // {H_ij, H_ji}
-            MSG::store(&gh[r * T + c], nh);
-            {
-                const float q2 = q * q;
-                const float2 np = MSG::round(-q2 * ii, -q2 * ij);                            // {P_ij, P_ji}
-                MSG::store(&gp[r * T + c], np);
-                changed |= (np.x != pv.x) | (np.y != pv.y);
-                rs[0] += np.y;
-                cv.aP[k] += np.x;
-            }
-            rs[1] += nh.y;
-            rs[2] = fmaf(q, cv.M[k], rs[2]);
-            cv.aH[k] += nh.x;
-            cv.aR[k] = fmaf(q, rM, cv.aR[k]);
+        if (v[k]) {
+            rs[1] += nh[k].y;
+            rs[2] = fmaf(q[k], cv.M[k], rs[2]);
+            cv.aH[k] += nh[k].x;
+            cv.aR[k] = fmaf(q[k], rM, cv.aR[k]);
         }
     }
+}
+
+// Per-tile constants of one consumer warp.
+struct TileCtx {
+    int cw, lane, rows, cols;
+    bool diag;
+    int it;
+    bool zero, zero_h;
+    Ctrl* ctrl;
+    long long L;
+};
+
+// One tile's chunk rows for one consumer warp: waits for each ring stage,
+// updates its row, releases the stage; leaves the warp's row sums in
+// sm.rp/rh/rr and its column partials in sm.cp (not when FROZEN), sm.ch and
+// sm.cr.  Specialised per tile kind so that a frozen-P tile keeps neither the
+// column P values nor their sums in registers.
+template <bool FULL, bool FROZEN, int SB, class MSG, class QSrc>
+__device__ __forceinline__ void consume_tile(const QSrc& qsrc, SweepTail& sm, const unsigned char* ring,
+                                             const TileCtx& tc, typename MSG::T2* __restrict__ gp,
+                                             typename MSG::T2* __restrict__ gh, int& stage, uint32_t& phase,
+                                             bool& abort, bool& bad, bool& changed)
+{
+    const int cw = tc.cw, lane = tc.lane, rows = tc.rows;
+    constexpr int G = MSG::G;
+    ColVals cv;
+    ld4<G>(sm.col[1], lane, cv.H);
+    ld4<G>(sm.col[2], lane, cv.M);
+    if (!FROZEN) ld4<G>(sm.col[0], lane, cv.P);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) cv.aP[k] = cv.aH[k] = cv.aR[k] = 0.f;
+    const int nch = (rows + RC - 1) / RC;
+    const int qv = lane >> 3;   // quantity this lane holds after the row reduction
+    float* rdst = qv == 0 ? sm.rp : (qv == 1 ? sm.rh : sm.rr);
+#pragma unroll 1
+    for (int ch = 0; ch < nch; ++ch) {
+        if (!abort && !mbar_wait_warp(&sm.full[stage], phase)) {
+            abort = true;
+            if (lane == 0) record_error(tc.ctrl, ST_ETIMEOUT, tc.L);
+        }
+        const int r = ch * RC + cw;
+        float rs[3] = {0.f, 0.f, 0.f};
+        if (!abort && r < rows) {
+            const unsigned char* S = ring + (size_t)stage * SB;
+            update_row<FULL, FROZEN, MSG>(qsrc, S, cw, lane, r, tc.cols, tc.diag, tc.it, tc.zero, tc.zero_h,
+                                          sm.row[0][r], sm.row[1][r], sm.row[2][r], cv, gp, gh, rs, bad, changed);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.empty[stage]);
+        if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        // row sums of row r: {P, H, R} over the warp, quantity lane / 8
+        const float v = reduce_scatter4(rs[0], rs[1], rs[2], lane);
+        if ((lane & 7) == 0 && qv < 3 && r < rows) rdst[r] = v;
+    }
+    if (!FROZEN) st4<G>(sm.cp[cw], lane, cv.aP);
+    st4<G>(sm.ch[cw], lane, cv.aH);
+    st4<G>(sm.cr[cw], lane, cv.aR);
 }
 
 // Consumers (256 threads, ctid = 0..255, consumer warp cw = ctid / 32).
@@ -342,73 +527,15 @@ __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, co
             abort = true;
             if (lane == 0) record_error(ctrl, ST_ETIMEOUT, L);
         }
-        ColVals cv;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int c = lane + 32 * k;
-            cv.P[k] = sm.col[0][c];
-            cv.H[k] = sm.col[1][c];
-            cv.M[k] = sm.col[2][c];
-            cv.aP[k] = cv.aH[k] = cv.aR[k] = 0.f;
-        }
         typename MSG::T2* gp = static_cast<typename MSG::T2*>(p.Pst) + (size_t)w.w * TT;
         typename MSG::T2* gh = static_cast<typename MSG::T2*>(p.Hst) + (size_t)w.w * TT;
-        const int nch = (rows + RC - 1) / RC;
-        float rowacc[16];   // row sums of 4 consecutive chunks: [g*4 + {P, H, R, -}]
-        for (int ch = 0; ch < nch; ++ch) {
-            if (!abort && !mbar_wait_warp(&sm.full[stage], phase)) {
-                abort = true;
-                if (lane == 0) record_error(ctrl, ST_ETIMEOUT, L);
-            }
-            const int g = ch & 3;
-            if (g == 0) {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) rowacc[i] = 0.f;
-            }
-            const int r = ch * RC + cw;
-            float rs[3] = {0.f, 0.f, 0.f};
-            if (!abort && r < rows) {
-                const unsigned char* S = ring + (size_t)stage * SB;
-                const float rP = sm.row[0][r], rH = sm.row[1][r], rM = sm.row[2][r];
-                if (full) {
-                    if (frozen)
-                        update_row<true, true, MSG>(qsrc, S, cw, lane, r, cols, diag, it, zero, zero_h, rP, rH, rM, cv,
-                                               gp, gh, rs, bad, changed);
-                    else
-                        update_row<true, false, MSG>(qsrc, S, cw, lane, r, cols, diag, it, zero, zero_h, rP, rH, rM, cv,
-                                                gp, gh, rs, bad, changed);
-                } else {
-                    if (frozen)
-                        update_row<false, true, MSG>(qsrc, S, cw, lane, r, cols, diag, it, zero, zero_h, rP, rH, rM, cv,
-                                                gp, gh, rs, bad, changed);
-                    else
-                        update_row<false, false, MSG>(qsrc, S, cw, lane, r, cols, diag, it, zero, zero_h, rP, rH, rM,
-                                                 cv, gp, gh, rs, bad, changed);
-                }
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&sm.empty[stage]);
-            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
-#pragma unroll
-            for (int gg = 0; gg < 4; ++gg)
-                if (gg == g) { rowacc[4 * gg] = rs[0]; rowacc[4 * gg + 1] = rs[1]; rowacc[4 * gg + 2] = rs[2]; }
-            if (g == 3 || ch == nch - 1) {
-                // row sums of this warp's last (up to) four rows
-                const float v = reduce_scatter16(rowacc, lane);
-                const int gv = lane >> 3, qv = (lane >> 1) & 3;
-                const int rr = (ch - g + gv) * RC + cw;
-                if ((lane & 1) == 0 && qv < 3 && gv <= g && rr < rows) {
-                    float* dst = qv == 0 ? sm.rp : (qv == 1 ? sm.rh : sm.rr);
-                    dst[rr] = v;
-                }
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int c = lane + 32 * k;
-            sm.cp[cw][c] = cv.aP[k];
-            sm.ch[cw][c] = cv.aH[k];
-            sm.cr[cw][c] = cv.aR[k];
+        TileCtx tc{cw, lane, rows, cols, diag, it, zero, zero_h, ctrl, L};
+        if (full) {
+            if (frozen) consume_tile<true, true, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
+            else consume_tile<true, false, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
+        } else {
+            if (frozen) consume_tile<false, true, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
+            else consume_tile<false, false, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
         }
         __syncwarp();
         qsrc.tile_end(it, lane);
@@ -454,9 +581,11 @@ template <typename QT, class MSG>
 struct StoredQ {
     __device__ __forceinline__ bool tile_begin(int, int) { return true; }
     __device__ __forceinline__ void tile_end(int, int) {}
-    __device__ __forceinline__ float q(const unsigned char* S, int cw, int, int c, int) const
+    // q of the lane's four pairs of chunk row cw
+    template <int G>
+    __device__ __forceinline__ void q4(const unsigned char* S, int cw, int, int lane, int, float (&q)[4]) const
     {
-        return to_f(reinterpret_cast<const QT*>(S + state_chunk<MSG>())[(size_t)cw * T + c]);
+        ld4<G>(reinterpret_cast<const QT*>(S + state_chunk<MSG>()) + (size_t)cw * T, lane, q);
     }
 };
 
@@ -466,7 +595,7 @@ __device__ __forceinline__ unsigned char* align_smem(unsigned char* raw, uintptr
 }
 
 template <typename QT, class MSG>
-__global__ void __launch_bounds__(SWEEP_THREADS, SWEEP_CTAS_PER_SM)
+__global__ void __launch_bounds__(SWEEP_THREADS, sweep_ctas<MSG>())
     k_sweep(const Inst* __restrict__ tab, const int4* __restrict__ work, const Sched* __restrict__ sched)
 {
     const long long ntiles = sched->ntiles;
@@ -527,9 +656,10 @@ struct RecomputedQ {
     {
         if (lane == 0) mbar_arrive(&ex->qempty[it & 1]);
     }
-    __device__ __forceinline__ float q(const unsigned char*, int, int r, int c, int it) const
+    template <int G>
+    __device__ __forceinline__ void q4(const unsigned char*, int, int r, int lane, int it, float (&q)[4]) const
     {
-        return __bfloat162float(qtile[(size_t)(it & 1) * TT + (size_t)r * T + c]);
+        ld4<G>(qtile + (size_t)(it & 1) * TT + (size_t)r * T, lane, q);
     }
 };
 
@@ -1086,11 +1216,12 @@ int num_sms()
     return sms;
 }
 
-RoundGrid round_grid(long long max_tiles, int max_nblocks, int q_mode, int ctas_per_sm)
+RoundGrid round_grid(long long max_tiles, int max_nblocks, int q_mode, int ctas_per_sm, int msg_bf16)
 {
     const int sms = num_sms();
     RoundGrid g;
-    const long long per_sm = q_mode == 2 ? 1 : (ctas_per_sm > 0 ? ctas_per_sm : SWEEP_CTAS_PER_SM);
+    const int dflt = msg_bf16 ? sweep_ctas<MsgBF16>() : sweep_ctas<MsgF32>();
+    const long long per_sm = q_mode == 2 ? 1 : (ctas_per_sm > 0 ? std::min(ctas_per_sm, dflt) : dflt);
     const long long gs = (long long)sms * per_sm;
     g.sweep = (int)(max_tiles < gs ? (max_tiles > 0 ? max_tiles : 1) : gs);
     const int gf = sms * 8;
