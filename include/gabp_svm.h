@@ -90,7 +90,13 @@ typedef struct {
     int32_t chunk;         /* sweeps per captured CUDA graph replay between convergence checks; 0 = 16 */
     int32_t msg_bf16;      /* precision forms only: store the messages in BF16 (arithmetic stays FP32);
                               use with refine > 0, which removes the rounding error */
-    int32_t reserved[6];
+    float   refine_handover; /* refinement only: the first solve hands over to the defect correction
+                                once its in-sweep ||r||_inf < refine_handover (never below tol);
+                                0 = 1e-3 with BF16 messages, 1e-4 with FP32 messages */
+    float   refine_inner;  /* refinement only: each correction pass stops once its residual is below
+                              refine_inner * ||r||_inf of its right-hand side (never below tol / 2);
+                              0 = 3e-2 with BF16 messages, 1e-2 with FP32 messages */
+    int32_t reserved[4];
 } gabp_svm_opts;
 
 typedef struct gabp_svm_s* gabp_svm_t;

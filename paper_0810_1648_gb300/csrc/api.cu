@@ -99,7 +99,7 @@ gabp_status check_handle(gabp_svm_t h)
 
 // Device memory plan of one handle (bytes, 256-aligned sub-buffers).
 struct Plan {
-    size_t X, vec, agg, part, state, q, work, ctrl, rhist, final3, blockbuf, xp, tab, nbl, total;
+    size_t X, vec, agg, part, state, q, qref, work, ctrl, rhist, final3, blockbuf, xp, tab, nbl, total;
 };
 
 Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_mode, int msg_bf16)
@@ -114,6 +114,8 @@ Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_m
     p.q = q_mode == GABP_Q_F32 ? align_up((size_t)ntiles * TT * sizeof(float), 256)
         : q_mode == GABP_Q_BF16 ? align_up((size_t)ntiles * TT * sizeof(__nv_bfloat16), 256)
         : 0;
+    // the BF16 store keeps an FP32 copy for the refinement residuals
+    p.qref = q_mode == GABP_Q_BF16 ? align_up((size_t)ntiles * TT * sizeof(float), 256) : 0;
     p.work = align_up((size_t)ntiles * sizeof(int4), 256);
     p.tab = align_up(sizeof(Inst) + sizeof(Sched) + sizeof(StopOp) + 64, 256);
     p.nbl = align_up((size_t)((n + 31) / 32) * sizeof(int2), 256);
@@ -121,7 +123,7 @@ Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_m
     p.rhist = align_up((size_t)kRhistCap * sizeof(double), 256);
     p.final3 = 256;
     p.blockbuf = align_up((size_t)3 * ((n + 31) / 32) * sizeof(double), 256);
-    p.total = p.X + 9 * p.vec + p.agg + p.part + p.state + p.q + p.work + p.ctrl + p.rhist +
+    p.total = p.X + 9 * p.vec + p.agg + p.part + p.state + p.q + p.qref + p.work + p.ctrl + p.rhist +
               p.final3 + p.blockbuf + p.xp + p.tab + p.nbl + 1024;
     return p;
 }
@@ -177,17 +179,18 @@ gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
         return fail(GABP_EINVAL, "row %lld: non-finite feature or label not +-1",
                     (long long)h->hctrl->bad_index);
     if (h->opts.q_mode == GABP_Q_F32) {
-        launch_form_q(h->d_tab, h->work, h->ntiles, 1, s);
+        launch_form_q(h->d_tab, h->work, h->ntiles, s);
         CK(cudaGetLastError());
         launch_init(p, h->opts.diag_rule, (float)h->delta, s);
         h->prof.kernel_launches += 2;
         CK(cudaGetLastError());
     } else {
         // Precision form: the diagonal weighting uses the FP32 Gram's row sums
-        // (the accurate matrix); the off-diagonal entries come from the BF16
-        // tensor-core Gram.
+        // (the accurate matrix), whose tiles the BF16 store also keeps as the
+        // FP32 copy for its refinement residuals; the off-diagonal entries
+        // the sweeps read come from the BF16 tensor-core Gram.
         CK(launch_pack_bf16(p.X, (int)n, (int)m, p.nkc, h->Nt, (void*)p.Xp, (float*)p.sqb, s));
-        launch_form_q(h->d_tab, h->work, h->ntiles, 0, s);
+        launch_form_q(h->d_tab, h->work, h->ntiles, s);
         CK(cudaGetLastError());
         launch_init(p, h->opts.diag_rule, (float)h->delta, s);
         CK(cudaGetLastError());
@@ -419,6 +422,7 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     p.Hst = take(pl.state / 2);
     p.msg_bf16 = o.msg_bf16;
     p.qstore = pl.q ? take(pl.q) : nullptr;
+    p.qref = pl.qref ? (float*)take(pl.qref) : (o.q_mode == GABP_Q_F32 ? (float*)p.qstore : nullptr);
     h->work = (int4*)take(pl.work);
     {
         char* tb = (char*)take(pl.tab);
@@ -500,8 +504,8 @@ gabp_status gabp_svm_solve(gabp_svm_t h, int32_t iters, double tol, float* alpha
         return fail(GABP_EINVAL, "too many rounds");
     Ctrl c{};
     // With refinement ahead, the BF16 solve only needs to reach about the BF16
-    // error level of its matrix (1e-4) before the first correction.
-    const double handover = h->opts.msg_bf16 ? 1e-3 : 1e-4;
+    // error level of its matrix (and messages) before the first correction.
+    const double handover = refine_handover(h->opts.refine_handover, h->opts.msg_bf16);
     if (gabp_status st = run_rounds(h, iters, refine ? std::max(tol, handover) : tol, &c)) return st;
     h->kstar = c.kstar;
     const float* mu = p.agg + (size_t)(c.kstar & 1) * 3 * p.npad + 2 * (size_t)p.npad;
@@ -545,7 +549,7 @@ gabp_status gabp_svm_solve(gabp_svm_t h, int32_t iters, double tol, float* alpha
             CK(cudaMemcpyAsync(h->d_ops, &rr, sizeof(StopOp), cudaMemcpyHostToDevice, s));
             launch_refine_rhs_list(h->d_tab, h->d_ops, h->nbl, nblk, s);
             h->prof.kernel_launches += 1;
-            const double inner = std::max(tol * 0.5, (h->opts.msg_bf16 ? 3e-2 : 1e-2) * rn);
+            const double inner = std::max(tol * 0.5, refine_inner(h->opts.refine_inner, h->opts.msg_bf16) * rn);
             Ctrl ci{};
             if (gabp_status st = run_rounds(h, iters, inner, &ci)) return st;
             buf = ci.kstar;

@@ -37,12 +37,9 @@ namespace {
 
 size_t aup(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// Residual at which a refined BF16 solve hands over to defect correction.
-constexpr double kRefineStart = 1e-4;
-
 // Device memory of one instance (one allocation), carved like the handle's.
 struct MemberPlan {
-    size_t X, vec, agg, part, state, q, work, rhist, final3, blockbuf, xp, total;
+    size_t X, vec, agg, part, state, q, qref, work, rhist, final3, blockbuf, xp, total;
 };
 
 MemberPlan member_plan(int64_t n, int64_t m, int q_mode, int msg_bf16)
@@ -57,12 +54,13 @@ MemberPlan member_plan(int64_t n, int64_t m, int q_mode, int msg_bf16)
     p.part = aup((size_t)4 * Nt * n * 4, 256);
     p.state = 2 * aup((size_t)nt * TT * (msg_bf16 ? 4 : 8), 256);
     p.q = q_mode == 0 ? aup((size_t)nt * TT * 4, 256) : q_mode == 1 ? aup((size_t)nt * TT * 2, 256) : 0;
+    p.qref = q_mode == 1 ? aup((size_t)nt * TT * 4, 256) : 0;   // FP32 copy for the refinement residuals
     p.work = aup((size_t)nt * sizeof(int4), 256);
     p.rhist = 0;
     p.final3 = 256;
     p.blockbuf = aup((size_t)3 * ((n + 31) / 32) * 8, 256);
     p.xp = q_mode != 0 ? aup(bf16_pack_bytes(Nt, (int)m), 1024) : 0;
-    p.total = p.X + 9 * p.vec + p.agg + p.part + p.state + p.q + p.work + p.final3 + p.blockbuf + p.xp + 2048;
+    p.total = p.X + 9 * p.vec + p.agg + p.part + p.state + p.q + p.qref + p.work + p.final3 + p.blockbuf + p.xp + 2048;
     return p;
 }
 
@@ -145,6 +143,7 @@ class Engine {
 
     int q_mode = 0, diag_rule = 0, x_f64 = 0, ptr_mode = 0, msg_bf16 = 0;
     double delta = 0.1, sv_threshold = 0.0;
+    double handover = 1e-4, inner = 1e-2;   // refinement schedule
     int cap_members = 0;
     long long cap_tiles = 0;
     int cap_nblk = 0;
@@ -200,6 +199,8 @@ class Engine {
         x_f64 = o.x_dtype;
         ptr_mode = o.ptr_mode;
         sv_threshold = o.sv_threshold;
+        handover = refine_handover(o.refine_handover, o.msg_bf16);
+        inner = refine_inner(o.refine_inner, o.msg_bf16);
         cap_members = members;
         cap_tiles = std::max<long long>(tiles, 1);
         cap_nblk = std::max(nblk, 1);
@@ -317,6 +318,7 @@ class Engine {
         p.Hst = take(pl.state / 2);
         p.msg_bf16 = msg_bf16;
         p.qstore = pl.q ? take(pl.q) : nullptr;
+        p.qref = pl.qref ? (float*)take(pl.qref) : (q_mode == 0 ? (float*)p.qstore : nullptr);
         M.work = (int4*)take(pl.work);
         M.final3 = (double*)take(pl.final3);
         M.blockbuf = (double*)take(pl.blockbuf);
@@ -402,7 +404,7 @@ class Engine {
             EK(cudaMemcpyAsync(d_ns, nb_stage.data(), nb_stage.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
         launch_stage_list(d_tab, d_ns, (int)nb_stage.size(), s);
         if (q_mode != 0) EK(launch_pack_list(d_tab, d_n, (int)nb.size(), s));
-        launch_form_q(d_tab, d_t, (long long)tiles.size(), q_mode == 0 ? 1 : 0, s);
+        launch_form_q(d_tab, d_t, (long long)tiles.size(), s);
         launch_init_list(d_tab, d_n, (int)nb.size(), diag_rule, (float)delta, s);
         if (q_mode == 1) EK(launch_form_q_tc(d_tab, d_t, (long long)tiles.size(), s));
         launches += q_mode == 0 ? 3 : (q_mode == 1 ? 5 : 4);
@@ -424,7 +426,7 @@ class Engine {
         EK(cudaStreamWaitEvent(stream, M.ready, 0));
         // With refinement ahead, the BF16 solve only needs to reach about the
         // BF16 error level of its matrix before the first correction.
-        const double t0 = (q_mode != 0 && M.refine_left > 0) ? std::max(tol, msg_bf16 ? 1e-3 : kRefineStart) : tol;
+        const double t0 = (q_mode != 0 && M.refine_left > 0) ? std::max(tol, handover) : tol;
         launch_begin(d_tab + slot, 1, iters, t0, stream);
         ++launches;
         M.formed = true;
@@ -442,8 +444,7 @@ class Engine {
         for (int k : slots) {
             Member& M = mem[(size_t)k];
             EK(cudaStreamWaitEvent(stream, M.ready, 0));
-            const double t0 = (q_mode != 0 && M.refine_left > 0) ? std::max(M.tol, msg_bf16 ? 1e-3 : kRefineStart)
-                                                                   : M.tol;
+            const double t0 = (q_mode != 0 && M.refine_left > 0) ? std::max(M.tol, handover) : M.tol;
             bl.push_back(make_int2(k, M.iters));
             bt.push_back(t0);
             M.formed = true;
@@ -618,7 +619,7 @@ class Engine {
                 --M.refine_left;
                 for (int b = 0; b < M.nblk; ++b) rnb.push_back(make_int2(k, b));
                 blist.push_back(make_int2(k, M.iters));
-                btol.push_back(std::max(M.tol * 0.5, (msg_bf16 ? 3e-2 : 1e-2) * rn));
+                btol.push_back(std::max(M.tol * 0.5, inner * rn));
                 ++run;
                 continue;
             }
@@ -795,7 +796,7 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
     t0 = clk::now();
     if (o.chunk <= 0) {
         if (gabp_status st = E.autotune(iters)) return st;
-        const double t0 = (o.q_mode != 0 && o.refine > 0) ? std::max(tol, o.msg_bf16 ? 1e-3 : 1e-4) : tol;
+        const double t0 = (o.q_mode != 0 && o.refine > 0) ? std::max(tol, E.handover) : tol;
         for (int64_t k = 0; k < count; ++k) gabp::launch_begin(E.d_tab + k, 1, iters, t0, E.stream);
     } else {
         E.chunk = o.chunk;

@@ -75,6 +75,9 @@ struct Inst {
     void* Pst;        // ntiles * TT precision messages {P_ij, P_ji} (float2, or bf16x2 when msg_bf16)
     void* Hst;        // ntiles * TT information messages {H_ij, H_ji}
     void* qstore;     // ntiles * TT values of Q (float or bf16), or nullptr
+    float* qref;      // ntiles * TT FP32 values of Q for the residual passes (the FP32
+                      // store itself, a separate copy beside the BF16 store, or nullptr
+                      // when Q is recomputed)
     float* agg;       // [2][3][npad]: double-buffered {Ptilde, htilde, mutilde}
     float* part;      // [4][Nt][n] partial sums
     Ctrl* ctrl;
@@ -132,9 +135,16 @@ struct GramSide {
 // Inputs: convert/validate X and y, row norms.  Returns nothing; errors go to ctrl->status.
 void launch_stage(const void* X, int x_f64, int n, int m, const float* y, float* Xf, float* sq,
                   float* b, Ctrl* ctrl, cudaStream_t s);
+// Refinement schedule of the precision forms (0 selects the default): the
+// first solve hands over to the defect correction at ||r||_inf < handover, each
+// correction pass stops at inner * ||r||_inf of its right-hand side.
+inline double refine_handover(float opt, int msg_bf16) { return opt > 0 ? opt : (msg_bf16 ? 1e-3 : 1e-4); }
+inline double refine_inner(float opt, int msg_bf16) { return opt > 0 ? opt : (msg_bf16 ? 3e-2 : 1e-2); }
+
 // Q formation (FP32 SIMT Gram fused with exp, labels and bias) + |Q| row-sum partials;
-// store_f32 = 0 computes only the row sums.
-void launch_form_q(const Inst* tab, const int4* work, long long ntiles, int store_f32, cudaStream_t s);
+// the FP32 tiles are stored into Inst::qref where it is set (the FP32 store, or the
+// FP32 copy the BF16 store keeps for its refinement residuals).
+void launch_form_q(const Inst* tab, const int4* work, long long ntiles, cudaStream_t s);
 // Precision form: BF16 operand packing + norms, and the tensor-core Q formation (BF16 store).
 cudaError_t launch_pack_bf16(const float* Xf, int n, int m, int nkc, int Nt, void* Xp, float* sqb, cudaStream_t s);
 cudaError_t launch_form_q_tc(const Inst* tab, const int4* work, long long ntiles, cudaStream_t s);

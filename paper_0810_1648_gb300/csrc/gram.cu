@@ -192,8 +192,7 @@ __global__ void k_stage_list(const Inst* __restrict__ tab, const int2* __restric
 }
 
 // ------------------------------------------------------- Q tile formation
-__global__ void __launch_bounds__(NTHREADS) k_form_q(const Inst* __restrict__ tab, const int4* __restrict__ work,
-                                                     int store)
+__global__ void __launch_bounds__(NTHREADS) k_form_q(const Inst* __restrict__ tab, const int4* __restrict__ work)
 {
     __shared__ __align__(16) TileSmem sm;
     const int4 w = work[blockIdx.x];
@@ -215,7 +214,7 @@ __global__ void __launch_bounds__(NTHREADS) k_form_q(const Inst* __restrict__ ta
     float rs[1][8], cs[1][8];
 #pragma unroll
     for (int b = 0; b < 8; ++b) cs[0][b] = 0.f;
-    float* qt = static_cast<float*>(p.qstore) + (size_t)L * TT;
+    float* qt = p.qref ? p.qref + (size_t)L * TT : nullptr;   // FP32 Q kept for the sweeps / residuals
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
         const int r = ty * 8 + a, i = I * T + r;
@@ -232,7 +231,7 @@ __global__ void __launch_bounds__(NTHREADS) k_form_q(const Inst* __restrict__ ta
             cs[0][b] += fabsf(out[b]);
         }
         rs[0][a] = racc;
-        if (store) {
+        if (qt) {
             float4* dst = reinterpret_cast<float4*>(qt + r * T + tx * 8);
             dst[0] = make_float4(out[0], out[1], out[2], out[3]);
             dst[1] = make_float4(out[4], out[5], out[6], out[7]);
@@ -257,11 +256,15 @@ __global__ void __launch_bounds__(NTHREADS) k_final_tiles(const Inst* __restrict
     const Inst& p = tab[w.x];
     const float* __restrict__ mu = ops[w.x].mu;
     const int I = w.y, J = w.z, n = p.n;
-    const GramSide S{p.X, p.sq, n};
-    float acc[8][8];
-    gram_tile(S, S, p.m, I, J, sm.g, acc);
-
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    // Q of the tile: read back from the FP32 store where one is kept (the same
+    // values the Gram below gives), else recomputed
+    const float* qt = p.qref ? p.qref + (size_t)w.w * TT : nullptr;
+    float acc[8][8];
+    if (!qt) {
+        const GramSide S{p.X, p.sq, n};
+        gram_tile(S, S, p.m, I, J, sm.g, acc);
+    }
     float yj[8], sj[8], mj[8], aj[8];
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
@@ -280,11 +283,18 @@ __global__ void __launch_bounds__(NTHREADS) k_final_tiles(const Inst* __restrict
         const float yi = i < n ? p.y[i] : 0.f, si = i < n ? p.sq[i] : 0.f;
         const float mi = i < n ? mu[i] : 0.f, ai = fminf(fmaxf(mi, 0.f), p.C);
         float rm = 0.f, ra = 0.f;
+        float qs[8];
+        if (qt) {
+            const float4 u0 = *reinterpret_cast<const float4*>(qt + r * T + tx * 8);
+            const float4 u1 = *reinterpret_cast<const float4*>(qt + r * T + tx * 8 + 4);
+            qs[0] = u0.x; qs[1] = u0.y; qs[2] = u0.z; qs[3] = u0.w;
+            qs[4] = u1.x; qs[5] = u1.y; qs[6] = u1.z; qs[7] = u1.w;
+        }
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
             const int c = tx * 8 + b, j = J * T + c;
             const bool v = i < n && j < n && (I != J || c > r);
-            const float q0 = yi * yj[b] * (rbf_from_gram(acc[a][b], si, sj[b], p.gamma) + p.lam2);
+            const float q0 = qt ? qs[b] : yi * yj[b] * (rbf_from_gram(acc[a][b], si, sj[b], p.gamma) + p.lam2);
             const float q = v ? q0 : 0.f;
             rm = fmaf(q, mj[b], rm);
             ra = fmaf(q, aj[b], ra);
@@ -295,7 +305,7 @@ __global__ void __launch_bounds__(NTHREADS) k_final_tiles(const Inst* __restrict
         rs[1][a] = ra;
     }
     float* const parts[2] = {p.part, p.part + (size_t)p.Nt * n};
-    __syncthreads();
+    __syncthreads();   // Gram smem is reused by the epilogue
     reduce_and_write<2>(sm.e, rs, cs, parts, n, I, J);
 }
 
@@ -477,9 +487,9 @@ void launch_stage(const void* X, int x_f64, int n, int m, const float* y, float*
     k_stage<<<(n + 255) / 256, 256, 0, s>>>(X, x_f64, n, m, y, Xf, sq, b, ctrl);
 }
 
-void launch_form_q(const Inst* tab, const int4* work, long long ntiles, int store_f32, cudaStream_t s)
+void launch_form_q(const Inst* tab, const int4* work, long long ntiles, cudaStream_t s)
 {
-    if (ntiles > 0) k_form_q<<<(unsigned)ntiles, NTHREADS, 0, s>>>(tab, work, store_f32);
+    if (ntiles > 0) k_form_q<<<(unsigned)ntiles, NTHREADS, 0, s>>>(tab, work);
 }
 
 void launch_final(const Inst* tab, const StopOp* ops, const int4* tiles, long long ntiles, const int2* nbl,

@@ -59,63 +59,54 @@ __device__ __forceinline__ void consumer_bar() { asm volatile("bar.sync 1, %0;" 
 constexpr int RC = NWARPS;                    // rows per chunk, one per consumer warp
 constexpr int STAGES = 4;
 constexpr int SWEEP_THREADS = NTHREADS + 32;  // + one producer warp
-constexpr int SWEEP_CTAS_PER_SM = 2;
 // Message storage: FP32 pairs (plain and precision forms) or BF16 pairs
 // (precision forms with refinement).  Arithmetic is FP32 either way; sums use
 // the stored (rounded) values so that the aggregates match the messages the
 // next round reads.
 struct MsgF32 {
     using T2 = float2;
-    static __device__ __forceinline__ float2 load(const T2& v) { return v; }
-    static __device__ __forceinline__ float2 round(float a, float b) { return make_float2(a, b); }
-    static __device__ __forceinline__ void store(T2* p, float2 v) { __stcs(p, v); }
+    static __device__ __forceinline__ T2 pack(float a, float b) { return make_float2(a, b); }
+    static __device__ __forceinline__ float2 unpack(T2 v) { return v; }
+    static __device__ __forceinline__ bool same(T2 a, T2 b) { return (a.x == b.x) & (a.y == b.y); }
     // a lane's pairs of a row: columns 2 lane + {0, 1} and 64 + 2 lane + {0, 1}
     // (each access of the warp is one contiguous 512-byte span)
     static constexpr int G = 2;
-    static __device__ __forceinline__ void load4(const T2* row, int lane, float2 (&v)[4])
+    static __device__ __forceinline__ void load4(const T2* row, int lane, T2 (&v)[4])
     {
         const float4 a = *reinterpret_cast<const float4*>(row + 2 * lane);
         const float4 b = *reinterpret_cast<const float4*>(row + 64 + 2 * lane);
         v[0] = make_float2(a.x, a.y); v[1] = make_float2(a.z, a.w);
         v[2] = make_float2(b.x, b.y); v[3] = make_float2(b.z, b.w);
     }
-    static __device__ __forceinline__ void store4(T2* row, int lane, const float2 (&v)[4])
+    static __device__ __forceinline__ void store4(T2* row, int lane, const T2 (&v)[4])
     {
         __stcs(reinterpret_cast<float4*>(row + 2 * lane), make_float4(v[0].x, v[0].y, v[1].x, v[1].y));
         __stcs(reinterpret_cast<float4*>(row + 64 + 2 * lane), make_float4(v[2].x, v[2].y, v[3].x, v[3].y));
     }
 };
 struct MsgBF16 {
-    using T2 = __nv_bfloat162;
-    static __device__ __forceinline__ float2 load(const T2& v) { return __bfloat1622float2(v); }
-    static __device__ __forceinline__ float2 round(float a, float b)
+    using T2 = unsigned;   // two BF16 values, the first in the low half
+    static __device__ __forceinline__ T2 pack(float a, float b)
     {
-        return __bfloat1622float2(__floats2bfloat162_rn(a, b));
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<const unsigned*>(&h);
     }
-    static __device__ __forceinline__ void store(T2* p, float2 v)
+    static __device__ __forceinline__ float2 unpack(T2 v)
     {
-        const T2 h = __floats2bfloat162_rn(v.x, v.y);   // exact: v is already rounded
-        __stcs(reinterpret_cast<unsigned int*>(p), *reinterpret_cast<const unsigned int*>(&h));
+        return make_float2(__uint_as_float(v << 16), __uint_as_float(v & 0xffff0000u));
     }
+    static __device__ __forceinline__ bool same(T2 a, T2 b) { return a == b; }
     // a lane's pairs of a row: columns 4 lane + {0 .. 3} (16 bytes; each
     // access of the warp is one contiguous 512-byte span)
     static constexpr int G = 4;
-    static __device__ __forceinline__ void load4(const T2* row, int lane, float2 (&v)[4])
+    static __device__ __forceinline__ void load4(const T2* row, int lane, T2 (&v)[4])
     {
         const uint4 u = *reinterpret_cast<const uint4*>(row + 4 * lane);
-        const unsigned w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = __bfloat1622float2(*reinterpret_cast<const T2*>(&w[k]));
+        v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w;
     }
-    static __device__ __forceinline__ void store4(T2* row, int lane, const float2 (&v)[4])
+    static __device__ __forceinline__ void store4(T2* row, int lane, const T2 (&v)[4])
     {
-        unsigned w[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const T2 h = __floats2bfloat162_rn(v[k].x, v[k].y);   // exact: already rounded
-            w[k] = *reinterpret_cast<const unsigned*>(&h);
-        }
-        __stcs(reinterpret_cast<uint4*>(row + 4 * lane), make_uint4(w[0], w[1], w[2], w[3]));
+        __stcs(reinterpret_cast<uint4*>(row + 4 * lane), make_uint4(v[0], v[1], v[2], v[3]));
     }
 };
 
@@ -129,12 +120,41 @@ __host__ __device__ constexpr int sweep_ctas() { return 2; }
 template <class MSG>
 __host__ __device__ constexpr size_t state_chunk() { return 2 * pchunk<MSG>(); }
 
+// What the producer publishes to the consumers for each tile it streams
+// (double-buffered by tile parity, completed through tfull[slot]).
+struct TileInfo {
+    void* Pst;          // the tile's P message block
+    void* Hst;          // the tile's H message block
+    float* part;        // the instance's partial sums
+    Ctrl* ctrl;
+    long long L;        // work-list index (error records)
+    int n, Nt, I, J;
+    int t, zero_h, frozen, end;
+};
+
 struct SweepTail {
     unsigned long long full[STAGES], empty[STAGES];
-    float row[3][T], col[3][T];
+    unsigned long long tfull[2], tempty[2];
+    int cabort;                        // consumer-side stop, decided at a tile barrier
+    TileInfo info[2];
+    alignas(16) float agg[2][6][T];    // per slot: row block {Ptilde, htilde, mu}, column block {same}
     float cp[NWARPS][T], ch[NWARPS][T], cr[NWARPS][T];
     float rp[T], rh[T], rr[T];
 };
+
+// Barriers and flags of the stage ring and the tile slots (one thread).
+__device__ __forceinline__ void init_tail(SweepTail& sm)
+{
+    for (int s = 0; s < STAGES; ++s) {
+        mbar_init(&sm.full[s], 1);
+        mbar_init(&sm.empty[s], NWARPS);
+    }
+    for (int s = 0; s < 2; ++s) {
+        mbar_init(&sm.tfull[s], 1);
+        mbar_init(&sm.tempty[s], NWARPS);
+    }
+    sm.cabort = 0;
+}
 
 // Ring stage = P messages of RC rows, their H messages, then (stored Q) their Q values.
 template <typename QT>
@@ -151,34 +171,74 @@ __host__ __device__ constexpr size_t sweep_smem_bytes()
     return 128 + STAGES * stage_bytes<QT, MSG>() + sizeof(SweepTail);
 }
 
-// Producer (one thread).  QT = void: messages only.
+// Producer (one warp).  For every tile it streams: publishes the tile's
+// parameters and bulk-copies its row and column aggregates into the tile slot,
+// then streams the message (and stored Q) rows through the stage ring.
+// Interior tiles move RC whole rows per copy; diagonal and edge tiles copy each
+// row's needed span, one row per lane.  QT = void: messages only.
 template <typename QT, class MSG, size_t SB>
 __device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, const int4* __restrict__ work,
                                                long long ntiles, SweepTail& sm, unsigned char* ring,
-                                               volatile int* abort_flag)
+                                               volatile int* abort_flag, int lane)
 {
     constexpr size_t QB = QBytes<QT>::v;
     constexpr size_t MB = sizeof(typename MSG::T2);
     constexpr size_t SC = state_chunk<MSG>(), PC = pchunk<MSG>();
     const uint64_t pol = l2_evict_first_policy();
-    int stage = 0;
-    uint32_t phase = 0;
+    const uint64_t pol_keep = l2_evict_last_policy();
+    int stage = 0, slot = 0;
+    uint32_t phase = 0, tph = 0;
+    auto stopped = [&]() { return __shfl_sync(0xffffffffu, abort_flag ? *abort_flag : 0, 0) != 0; };
     for (long long L = blockIdx.x; L < ntiles; L += gridDim.x) {
         const int4 w = work[L];
         const Inst& p = tab[w.x];
-        if (*(volatile const int*)&p.ctrl->done) continue;      // instance finished: tile skipped
-        const bool zero = *(volatile const int*)&p.ctrl->t == 0;
+        Ctrl* ctrl = p.ctrl;
+        if (*(volatile const int*)&ctrl->done) continue;      // instance finished: tile skipped
+        const int t = *(volatile const int*)&ctrl->t;
+        const bool zero = t == 0;
         const int n = p.n, I = w.y, J = w.z;
         const int rows = min(T, n - I * T), cols = min(T, n - J * T);
         const bool diag = (I == J);
         const typename MSG::T2* sp = static_cast<const typename MSG::T2*>(p.Pst) + (size_t)w.w * TT;
         const typename MSG::T2* sh = static_cast<const typename MSG::T2*>(p.Hst) + (size_t)w.w * TT;
         const unsigned char* qt = QB ? static_cast<const unsigned char*>(p.qstore) + (size_t)w.w * TT * QB : nullptr;
+        // tile slot: parameters + aggregates
+        if (stopped() || !mbar_wait_warp(&sm.tempty[slot], tph ^ 1u)) {
+            if (lane == 0) {
+                record_error(ctrl, ST_ETIMEOUT, L);
+                if (abort_flag) *abort_flag = 1;
+            }
+            return;
+        }
+        if (lane == 0) {
+            TileInfo& ti = sm.info[slot];
+            ti.Pst = const_cast<typename MSG::T2*>(sp);
+            ti.Hst = const_cast<typename MSG::T2*>(sh);
+            ti.part = p.part;
+            ti.ctrl = ctrl;
+            ti.L = L;
+            ti.n = n; ti.Nt = p.Nt; ti.I = I; ti.J = J;
+            ti.t = t;
+            ti.zero_h = *(volatile const int*)&ctrl->zero_h;
+            ti.frozen = *(volatile const int*)&ctrl->p_frozen;
+            ti.end = 0;
+            mbar_arrive_expect_tx(&sm.tfull[slot], 6 * T * sizeof(float));
+        }
+        __syncwarp();
+        if (lane < 6) {
+            const float* agg = p.agg + (size_t)(t & 1) * 3 * p.npad + (size_t)(lane % 3) * p.npad +
+                               (size_t)(lane < 3 ? I : J) * T;
+            bulk_load(&sm.agg[slot][lane][0], agg, T * sizeof(float), &sm.tfull[slot], pol_keep);
+        }
+        if (++slot == 2) { slot = 0; tph ^= 1u; }
+        // message / Q rows
         const int nch = (rows + RC - 1) / RC;
         for (int c = 0; c < nch; ++c) {
-            if ((abort_flag && *abort_flag) || !mbar_wait(&sm.empty[stage], phase ^ 1u)) {
-                record_error(p.ctrl, ST_ETIMEOUT, L);
-                if (abort_flag) *abort_flag = 1;
+            if (stopped() || !mbar_wait_warp(&sm.empty[stage], phase ^ 1u)) {
+                if (lane == 0) {
+                    record_error(ctrl, ST_ETIMEOUT, L);
+                    if (abort_flag) *abort_flag = 1;
+                }
                 return;
             }
             unsigned char* S = ring + (size_t)stage * SB;
@@ -187,31 +247,27 @@ __device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, con
             if (!diag && cols == T) {
                 const uint32_t bq = (uint32_t)(nr * T * QB);
                 const uint32_t bs = zero ? 0u : (uint32_t)(nr * T * MB);
-                mbar_arrive_expect_tx(bar, bq + 2 * bs);
-                if (QB) bulk_load(S + SC, qt + (size_t)r0 * T * QB, bq, bar, pol);
-                if (!zero) {
-                    bulk_load(S, sp + (size_t)r0 * T, bs, bar, pol);
-                    bulk_load(S + PC, sh + (size_t)r0 * T, bs, bar, pol);
-                }
+                if (lane == 0) mbar_arrive_expect_tx(bar, bq + 2 * bs);
+                __syncwarp();
+                if (QB && lane == 0) bulk_load(S + SC, qt + (size_t)r0 * T * QB, bq, bar, pol);
+                if (!zero && lane == 1) bulk_load(S, sp + (size_t)r0 * T, bs, bar, pol);
+                if (!zero && lane == 2) bulk_load(S + PC, sh + (size_t)r0 * T, bs, bar, pol);
             } else {
-                // per row: columns [c0, c1) with c0, c1 multiples of 8 (16-byte
-                // granules of both arrays) covering the pairs the row owns
+                // row r0 + lane: columns [c0, c1) with c0, c1 multiples of 8
+                // (16-byte granules of every array) covering the pairs it owns
                 const int c1 = min(T, (cols + 7) & ~7);
-                uint32_t bytes = 0;
-                for (int k = 0; k < nr; ++k) {
-                    const int r = r0 + k, c0 = diag ? ((r + 1) & ~7) : 0;
-                    if (c0 < c1 && (!diag || r + 1 < cols))
-                        bytes += (uint32_t)((c1 - c0) * (QB + (zero ? 0 : 2 * MB)));
-                }
-                mbar_arrive_expect_tx(bar, bytes);
-                for (int k = 0; k < nr; ++k) {
-                    const int r = r0 + k, c0 = diag ? ((r + 1) & ~7) : 0;
-                    if (!(c0 < c1 && (!diag || r + 1 < cols))) continue;
+                const int r = r0 + lane, c0 = diag ? ((r + 1) & ~7) : 0;
+                const bool has = lane < nr && c0 < c1 && (!diag || r + 1 < cols);
+                const uint32_t mine = has ? (uint32_t)((c1 - c0) * (QB + (zero ? 0 : 2 * MB))) : 0u;
+                const uint32_t bytes = __reduce_add_sync(0xffffffffu, mine);
+                if (lane == 0) mbar_arrive_expect_tx(bar, bytes);
+                __syncwarp();
+                if (has) {
                     if (QB)
-                        bulk_load(S + SC + ((size_t)k * T + c0) * QB, qt + ((size_t)r * T + c0) * QB,
+                        bulk_load(S + SC + ((size_t)lane * T + c0) * QB, qt + ((size_t)r * T + c0) * QB,
                                   (uint32_t)((c1 - c0) * QB), bar, pol);
                     if (!zero) {
-                        const size_t o = ((size_t)k * T + c0) * MB;
+                        const size_t o = ((size_t)lane * T + c0) * MB;
                         const uint32_t b2 = (uint32_t)((c1 - c0) * MB);
                         bulk_load(S + o, sp + (size_t)r * T + c0, b2, bar, pol);
                         bulk_load(S + PC + o, sh + (size_t)r * T + c0, b2, bar, pol);
@@ -220,6 +276,11 @@ __device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, con
             }
             if (++stage == STAGES) { stage = 0; phase ^= 1u; }
         }
+    }
+    // end of this CTA's tiles
+    if (!stopped() && mbar_wait_warp(&sm.tempty[slot], tph ^ 1u) && lane == 0) {
+        sm.info[slot].end = 1;
+        mbar_arrive(&sm.tfull[slot]);
     }
 }
 
@@ -234,38 +295,6 @@ __device__ __forceinline__ float rcp_nr(float d)
     return fmaf(r, fmaf(-d, r, 1.0f), r);
 }
 
-// Sums 16 values over the 32 lanes of a warp with the same pairing as a
-// butterfly all-reduce (xor 16, 8, 4, 2, 1), but halving the set at every
-// step: afterwards lanes 2v and 2v+1 hold the total of value v.
-__device__ __forceinline__ float reduce_scatter16(float (&a)[16], int lane)
-{
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const bool up = lane & 16;
-        const float send = up ? a[i] : a[i + 8], keep = up ? a[i + 8] : a[i];
-        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const bool up = lane & 8;
-        const float send = up ? a[i] : a[i + 4], keep = up ? a[i + 4] : a[i];
-        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const bool up = lane & 4;
-        const float send = up ? a[i] : a[i + 2], keep = up ? a[i + 2] : a[i];
-        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
-    {
-        const bool up = lane & 2;
-        const float send = up ? a[0] : a[1], keep = up ? a[1] : a[0];
-        a[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-    }
-    return a[0] + __shfl_xor_sync(0xffffffffu, a[0], 1);
-}
-
-// Per-tile values a consumer needs for its row updates.
 // Column slot k = 0..3 of a lane in a 128-column row: G consecutive columns
 // in each of 4 / G groups of 32 G columns (G = 2 for FP32 messages, 4 for
 // BF16 messages), so that every warp access to a row is contiguous.
@@ -330,6 +359,7 @@ __device__ __forceinline__ float reduce_scatter4(float a, float b, float c, int 
     return v;
 }
 
+// Per-tile column values a consumer lane needs for its row updates.
 struct ColVals {
     float P[4], H[4], M[4];      // aggregates of the lane's four columns
     float aP[4], aH[4], aR[4];   // column partial sums
@@ -359,19 +389,24 @@ __device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char
         const int c = lane_col<MSG::G>(lane, k);
         v[k] = FULL || (c < cols && (!diag || c > r));
     }
+    T2 pw[4], hw[4], nw[4];   // stored words
     float2 pv[4], hv[4], nh[4];
     if (zero) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) pv[k] = make_float2(0.f, 0.f);
+        for (int k = 0; k < 4; ++k) { pw[k] = MSG::pack(0.f, 0.f); pv[k] = make_float2(0.f, 0.f); }
     } else {
-        MSG::load4(Sp, lane, pv);                                     // {P_ij, P_ji}
+        MSG::load4(Sp, lane, pw);                               // {P_ij, P_ji}
+#pragma unroll
+        for (int k = 0; k < 4; ++k) pv[k] = MSG::unpack(pw[k]);
     }
     if (FROZEN) {
         if (zero_h) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) hv[k] = make_float2(0.f, 0.f);
         } else {
-            MSG::load4(Sh, lane, hv);                                 // {H_ij, H_ji}
+            MSG::load4(Sh, lane, hw);                           // {H_ij, H_ji}
+#pragma unroll
+            for (int k = 0; k < 4; ++k) hv[k] = MSG::unpack(hw[k]);
         }
         // With P at its fixed point, P_ij = -q^2 / d_i, so the H update
         // -q (htilde_i - H_ji) / d_i equals P_ij (htilde_i - H_ji) / q: one
@@ -380,12 +415,12 @@ __device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const float qi = q[k] != 0.f ? rcp_nr(q[k]) : 0.f;
-            nh[k] = MSG::round(pv[k].x * (rH - hv[k].y) * qi, pv[k].y * (cv.H[k] - hv[k].x) * qi);
+            nw[k] = MSG::pack(pv[k].x * (rH - hv[k].y) * qi, pv[k].y * (cv.H[k] - hv[k].x) * qi);
         }
     } else {
         float2 inv[4];
         {
-            float2 np[4];
+            T2 npw[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const float di = rP - pv[k].y;        // cavity Ptilde_i - P_ji
@@ -393,29 +428,33 @@ __device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char
                 bad |= v[k] & !((di > 0.f) & (dj > 0.f));
                 inv[k] = make_float2(rcp_nr(di), rcp_nr(dj));
                 const float q2 = q[k] * q[k];
-                np[k] = MSG::round(-q2 * inv[k].x, -q2 * inv[k].y);
+                npw[k] = MSG::pack(-q2 * inv[k].x, -q2 * inv[k].y);
                 if (v[k]) {
-                    changed |= (np[k].x != pv[k].x) | (np[k].y != pv[k].y);
-                    rs[0] += np[k].y;
-                    cv.aP[k] += np[k].x;
+                    const float2 np = MSG::unpack(npw[k]);
+                    changed |= !MSG::same(npw[k], pw[k]);
+                    rs[0] += np.y;
+                    cv.aP[k] += np.x;
                 }
             }
-            MSG::store4(gp + r * T, lane, np);
+            MSG::store4(gp + r * T, lane, npw);
         }
         if (zero || zero_h) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) hv[k] = make_float2(0.f, 0.f);
         } else {
-            MSG::load4(Sh, lane, hv);                                 // {H_ij, H_ji}
+            MSG::load4(Sh, lane, hw);                           // {H_ij, H_ji}
+#pragma unroll
+            for (int k = 0; k < 4; ++k) hv[k] = MSG::unpack(hw[k]);
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            nh[k] = MSG::round(-q[k] * (rH - hv[k].y) * inv[k].x, -q[k] * (cv.H[k] - hv[k].x) * inv[k].y);
+            nw[k] = MSG::pack(-q[k] * (rH - hv[k].y) * inv[k].x, -q[k] * (cv.H[k] - hv[k].x) * inv[k].y);
     }
-    MSG::store4(gh + r * T, lane, nh);
+    MSG::store4(gh + r * T, lane, nw);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         if (v[k]) {
+            nh[k] = MSG::unpack(nw[k]);
             rs[1] += nh[k].y;
             rs[2] = fmaf(q[k], cv.M[k], rs[2]);
             cv.aH[k] += nh[k].x;
@@ -432,6 +471,7 @@ struct TileCtx {
     bool zero, zero_h;
     Ctrl* ctrl;
     long long L;
+    const float (*ag)[T];   // the tile slot's aggregates: rows 0..2, columns 3..5
 };
 
 // One tile's chunk rows for one consumer warp: waits for each ring stage,
@@ -448,9 +488,9 @@ __device__ __forceinline__ void consume_tile(const QSrc& qsrc, SweepTail& sm, co
     const int cw = tc.cw, lane = tc.lane, rows = tc.rows;
     constexpr int G = MSG::G;
     ColVals cv;
-    ld4<G>(sm.col[1], lane, cv.H);
-    ld4<G>(sm.col[2], lane, cv.M);
-    if (!FROZEN) ld4<G>(sm.col[0], lane, cv.P);
+    ld4<G>(tc.ag[4], lane, cv.H);
+    ld4<G>(tc.ag[5], lane, cv.M);
+    if (!FROZEN) ld4<G>(tc.ag[3], lane, cv.P);
 #pragma unroll
     for (int k = 0; k < 4; ++k) cv.aP[k] = cv.aH[k] = cv.aR[k] = 0.f;
     const int nch = (rows + RC - 1) / RC;
@@ -467,7 +507,7 @@ __device__ __forceinline__ void consume_tile(const QSrc& qsrc, SweepTail& sm, co
         if (!abort && r < rows) {
             const unsigned char* S = ring + (size_t)stage * SB;
             update_row<FULL, FROZEN, MSG>(qsrc, S, cw, lane, r, tc.cols, tc.diag, tc.it, tc.zero, tc.zero_h,
-                                          sm.row[0][r], sm.row[1][r], sm.row[2][r], cv, gp, gh, rs, bad, changed);
+                                          tc.ag[0][r], tc.ag[1][r], tc.ag[2][r], cv, gp, gh, rs, bad, changed);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.empty[stage]);
@@ -492,44 +532,42 @@ __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, co
     int stage = 0;
     uint32_t phase = 0;
     bool abort = false;
-    int it = 0;
-    for (long long L = blockIdx.x; L < ntiles; L += gridDim.x) {
-        const int4 w = work[L];
-        const Inst& p = tab[w.x];
-        Ctrl* ctrl = p.ctrl;
-        if (*(volatile const int*)&ctrl->done) continue;
-        const int t = *(volatile const int*)&ctrl->t;
+    int it = 0, slot = 0;
+    uint32_t tph = 0;
+    for (;;) {
+        // next tile from the producer (bounded wait; the stop is taken by all
+        // consumer warps together at the tile barrier)
+        if (!mbar_wait_warp(&sm.tfull[slot], tph) && lane == 0) {
+            sm.cabort = 1;
+            if (blockIdx.x < ntiles) record_error(tab[work[blockIdx.x].x].ctrl, ST_ETIMEOUT, -1);
+        }
+        consumer_bar();   // also: the previous tile's sums are read out
+        if (*(volatile int*)&sm.cabort) break;
+        const TileInfo ti = sm.info[slot];
+        if (ti.end) break;
+        Ctrl* ctrl = ti.ctrl;
+        const long long L = ti.L;
+        const int t = ti.t;
         const bool zero = (t == 0);   // Step 1: all messages 0, nothing to read
-        const bool zero_h = *(volatile const int*)&ctrl->zero_h != 0;
-        const bool frozen = *(volatile const int*)&ctrl->p_frozen != 0;
+        const bool zero_h = ti.zero_h != 0;
+        const bool frozen = ti.frozen != 0;
         bool changed = false;
-        const float* agg = p.agg + (size_t)(t & 1) * 3 * p.npad;
-        const int n = p.n;
-        float* partP = p.part;
-        float* partH = partP + (size_t)p.Nt * n;
-        float* partR = partH + (size_t)p.Nt * n;
+        const int n = ti.n, Nt = ti.Nt;
+        float* partP = ti.part;
+        float* partH = partP + (size_t)Nt * n;
+        float* partR = partH + (size_t)Nt * n;
         bool bad = false;
-        const int I = w.y, J = w.z;
+        const int I = ti.I, J = ti.J;
         const int rows = min(T, n - I * T), cols = min(T, n - J * T);
         const bool diag = (I == J);
         const bool full = !diag && cols == T;
-        {
-            const int rc = ctid < T ? ctid : ctid - T;
-            const int x = (ctid < T ? I : J) * T + rc;
-            const bool v = x < n;
-            float(*dst)[T] = ctid < T ? sm.row : sm.col;
-            dst[0][rc] = v ? agg[x] : 1.f;
-            dst[1][rc] = v ? agg[p.npad + x] : 0.f;
-            dst[2][rc] = v ? agg[2 * p.npad + x] : 0.f;
-        }
-        consumer_bar();
         if (!abort && !qsrc.tile_begin(it, lane)) {
             abort = true;
             if (lane == 0) record_error(ctrl, ST_ETIMEOUT, L);
         }
-        typename MSG::T2* gp = static_cast<typename MSG::T2*>(p.Pst) + (size_t)w.w * TT;
-        typename MSG::T2* gh = static_cast<typename MSG::T2*>(p.Hst) + (size_t)w.w * TT;
-        TileCtx tc{cw, lane, rows, cols, diag, it, zero, zero_h, ctrl, L};
+        typename MSG::T2* gp = static_cast<typename MSG::T2*>(ti.Pst);
+        typename MSG::T2* gh = static_cast<typename MSG::T2*>(ti.Hst);
+        TileCtx tc{cw, lane, rows, cols, diag, it, zero, zero_h, ctrl, L, sm.agg[slot]};
         if (full) {
             if (frozen) consume_tile<true, true, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
             else consume_tile<true, false, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
@@ -537,6 +575,9 @@ __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, co
             if (frozen) consume_tile<false, true, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
             else consume_tile<false, false, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
         }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.tempty[slot]);   // tile slot free for the producer
+        if (++slot == 2) { slot = 0; tph ^= 1u; }
         __syncwarp();
         qsrc.tile_end(it, lane);
         consumer_bar();
@@ -607,15 +648,12 @@ __global__ void __launch_bounds__(SWEEP_THREADS, sweep_ctas<MSG>())
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&sm.full[s], 1);
-            mbar_init(&sm.empty[s], NWARPS);
-        }
+        init_tail(sm);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     if (warp == NWARPS) {
-        if (lane == 0) sweep_producer<QT, MSG, SB>(tab, work, ntiles, sm, ring, nullptr);
+        sweep_producer<QT, MSG, SB>(tab, work, ntiles, sm, ring, nullptr, lane);
         return;
     }
     StoredQ<QT, MSG> qsrc;
@@ -678,10 +716,7 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&sm.full[s], 1);
-            mbar_init(&sm.empty[s], NWARPS);
-        }
+        init_tail(sm);
         for (int s = 0; s < RC_XSTAGES; ++s) { mbar_init(&ex.xfull[s], 1); mbar_init(&ex.xempty[s], 1); }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&ex.accfull[b], 1);
@@ -701,7 +736,7 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
     volatile int* abort_flag = &ex.abort;
 
     if (warp == 0) {
-        if (lane == 0) sweep_producer<void, MSG, state_chunk<MSG>()>(tab, work, ntiles, sm, ring, abort_flag);
+        sweep_producer<void, MSG, state_chunk<MSG>()>(tab, work, ntiles, sm, ring, abort_flag, lane);
     } else if (warp == 1) {
         // feature blocks of each tile
         if (lane == 0) {

@@ -41,7 +41,9 @@ class Opts(ctypes.Structure):
                 ("diag_delta", ctypes.c_double), ("bias_mode", ctypes.c_int32),
                 ("bias_lambda", ctypes.c_double), ("q_mode", ctypes.c_int32),
                 ("refine", ctypes.c_int32), ("sv_threshold", ctypes.c_double),
-                ("chunk", ctypes.c_int32), ("msg_bf16", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("chunk", ctypes.c_int32), ("msg_bf16", ctypes.c_int32),
+                ("refine_handover", ctypes.c_float), ("refine_inner", ctypes.c_float),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class Profile(ctypes.Structure):
