@@ -206,23 +206,25 @@ def run_reference(args):
 
 
 def run_profile_small(args):
-    """One short solve on a smaller set (n=6144, 8 rounds, so that the last
-    rounds run with frozen P messages) for ncu captures: the message state
-    (0.3 GB) is still above L2, the device footprint small."""
+    """One short solve on a smaller set (n=6144 by default, --profile-n; 8
+    rounds, so that the last rounds run with frozen P messages) for ncu
+    captures: the message state (0.3 GB at n=6144) is still above L2, the
+    device footprint small."""
     import torch
 
     from paper_0810_1648_gb300 import build as gbuild
     from paper_0810_1648_gb300 import gabp
     if not os.path.exists(gabp.LIB_PATH):
         gbuild.build()
-    p = workloads.mixture(6144, 128, seed=1, gamma=1.0 / 128, C=10.0)
+    n = args.profile_n
+    p = workloads.mixture(n, 128, seed=1, gamma=1.0 / 128, C=10.0)
     h = gabp.svm_create(p.X, p.y, p.gamma, p.C, gabp.opts_default(chunk=8, q_mode=Q_MODES[args.q_mode],
                                                                  msg_bf16=1 if args.msg_bf16 else 0))
     alpha = np.empty(p.n, dtype=np.float32)
     rinf, k = gabp.svm_solve(h, 8, 0.0, alpha)
     gabp.svm_destroy(h)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": f"n=6144 m=128 mixture, 8 rounds, q_mode {args.q_mode}", "rounds": k,
+    print(json.dumps({"profile_case": f"n={n} m=128 mixture, 8 rounds, q_mode {args.q_mode}", "rounds": k,
                       "residual_inf": rinf}), flush=True)
     return 0
 
@@ -302,9 +304,8 @@ def run_serve(args):
             sub[t] = r.t_arrive
             nxt += 1
         active, queued, completed = srv.step()
-        for t in list(sub):
-            res = srv.poll(t)
-            if res is not None:
+        for t in srv.completed():
+            if srv.poll(t) is not None:
                 lat.append(time.perf_counter() - t0 - sub.pop(t))
                 done_n += 1
         if active == 0 and queued == 0 and nxt < len(reqs):
@@ -507,7 +508,8 @@ def main():
     ap.add_argument("--msg-bf16", action="store_true", help="precision forms: BF16 message storage")
     ap.add_argument("--q-mode", default=None, choices=list(Q_MODES))
     ap.add_argument("--profile-small", action="store_true",
-                    help="one 3-round solve at n=6144 (for ncu captures), no JSON bench line")
+                    help="one 8-round solve at n=--profile-n (for ncu captures), no JSON bench line")
+    ap.add_argument("--profile-n", type=int, default=6144, help="n of the --profile-small case")
     args = ap.parse_args()
     if args.q_mode is None:
         args.q_mode = "f32" if args.workload == "plain_large" else "bf16"

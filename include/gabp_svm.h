@@ -256,6 +256,11 @@ GABP_API gabp_status gabp_server_submit(gabp_server_t s, const gabp_problem* p, 
 GABP_API gabp_status gabp_server_step(gabp_server_t s, int32_t* active, int32_t* queued, int32_t* completed);
 /* done = 1 once the ticket finished; then *res holds its result. */
 GABP_API gabp_status gabp_server_poll(gabp_server_t s, int64_t ticket, gabp_result* res, int32_t* done);
+/* Tickets finished since the previous call, in completion order: up to `cap`
+ * of them are written to tickets[] and *count says how many; the rest stay for
+ * the next call.  Lets a caller with many requests in flight poll only the
+ * finished ones. */
+GABP_API gabp_status gabp_server_completed(gabp_server_t s, int64_t* tickets, int32_t cap, int32_t* count);
 GABP_API gabp_status gabp_server_destroy(gabp_server_t s);
 
 /*

@@ -849,6 +849,7 @@ struct gabp_server_s {
     std::deque<std::pair<int64_t, gabp_problem>> queue;
     std::map<int64_t, float*> outs;
     std::map<int64_t, gabp_result> done;
+    std::deque<int64_t> fresh;   // finished, not yet reported by gabp_server_completed
     std::vector<int> forming;   // slots whose Q formation runs on the side stream
     int64_t next_ticket = 0;
 };
@@ -915,6 +916,7 @@ gabp_status gabp_server_step(gabp_server_t s, int32_t* active, int32_t* queued, 
             r.status = GABP_ENOMEM;
             r.alpha = s->outs[front.first];
             s->done[front.first] = r;
+            s->fresh.push_back(front.first);
             s->queue.pop_front();
             continue;
         }
@@ -959,6 +961,7 @@ gabp_status gabp_server_step(gabp_server_t s, int32_t* active, int32_t* queued, 
             gabp_result r = M.res;
             r.alpha = M.out_alpha;
             s->done[M.ticket] = r;
+            s->fresh.push_back(M.ticket);
             E.release(M);
         }
     }
@@ -977,6 +980,22 @@ gabp_status gabp_server_poll(gabp_server_t s, int64_t ticket, gabp_result* res, 
     auto it = s->done.find(ticket);
     *done = it != s->done.end() ? 1 : 0;
     if (*done && res) *res = it->second;
+    return GABP_OK;
+}
+
+gabp_status gabp_server_completed(gabp_server_t s, int64_t* tickets, int32_t cap, int32_t* count)
+{
+    gabp::set_last_error("");
+    if (!s || !count || (cap > 0 && !tickets) || cap < 0) {
+        gabp::set_last_error("gabp_server_completed: bad argument");
+        return GABP_EINVAL;
+    }
+    int32_t k = 0;
+    while (k < cap && !s->fresh.empty()) {
+        tickets[k++] = s->fresh.front();
+        s->fresh.pop_front();
+    }
+    *count = k;
     return GABP_OK;
 }
 

@@ -21,6 +21,7 @@
 // so the epilogue of one tile overlaps the MMAs of the next.
 #include "common.cuh"
 #include "ptx.cuh"
+#include "qtile_epi.cuh"
 
 #include <float.h>
 
@@ -29,7 +30,8 @@ namespace gabp {
 namespace {
 
 constexpr int XSTAGES = 4;
-constexpr int TC_THREADS = 6 * 32;
+constexpr int TC_THREADS = 10 * 32;   // producer, MMA issuer, 8 epilogue warps
+constexpr int TC_EPI_WARPS = 8;
 constexpr uint32_t TMEM_COLS = 256;
 constexpr uint32_t IDESC = idesc_bf16_f32(T, T);
 
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     if (tid == 0) {
         for (int s = 0; s < XSTAGES; ++s) { mbar_init(&sm.xfull[s], 1); mbar_init(&sm.xempty[s], 1); }
-        for (int b = 0; b < 2; ++b) { mbar_init(&sm.accfull[b], 1); mbar_init(&sm.accempty[b], 4); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&sm.accfull[b], 1); mbar_init(&sm.accempty[b], TC_EPI_WARPS); }
         mbar_init(&sm.drain, 1);
         sm.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -207,7 +209,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else {
         // --------------------------------------------------------- epilogue
-        const int g = warp & 3;
+        // warp w may read TMEM lanes 32 (w % 4) ..: two warps per lane
+        // quarter, one per half of the 128 columns
+        const int g = warp & 3, half = (warp - 2) >> 2;
         const int r = 32 * g + lane;
         int acc = 0;
         uint32_t aph = 0;
@@ -232,22 +236,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const float yi = i < n ? p.y[i] : 0.f, si = i < n ? sqb[i] : 0.f;
             __nv_bfloat16* qrow = qs + (size_t)w.w * TT + (size_t)r * T;
 #pragma unroll 1
-            for (int cc = 0; cc < T / 32; ++cc) {
+            for (int cc = 2 * half; cc < 2 * half + 2; ++cc) {
                 float v[32];
                 tmem_ld32(tbase + (uint32_t)acc * T + ((uint32_t)(32 * g) << 16) + (uint32_t)(32 * cc), v);
-                __align__(16) __nv_bfloat16 out[32];
-#pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    const int col = 32 * cc + c, j = J * T + col;
-                    const bool valid = i < n && j < n && (I != J || col > r);
-                    const float yj = j < n ? p.y[j] : 0.f, sj = j < n ? sqb[j] : 0.f;
-                    const float d2 = fmaxf(0.f, si + sj - 2.f * v[c]);
-                    const float q = yi * yj * (expf(-p.gamma * d2) + p.lam2);
-                    out[c] = __float2bfloat16_rn(valid ? q : 0.f);
-                }
+                const int jl = J * T + 32 * cc + lane;
+                const float yl = jl < n ? p.y[jl] : 0.f, sl = jl < n ? sqb[jl] : 0.f;
+                uint4 out[4];
+                q_chunk_bf16(v, yi, si, yl, sl, p.gamma, p.lam2, chunk_valid(n, I, J, r, cc), out);
                 uint4* dst = reinterpret_cast<uint4*>(qrow + 32 * cc);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) dst[u] = reinterpret_cast<const uint4*>(out)[u];
+                for (int u = 0; u < 4; ++u) dst[u] = out[u];
             }
             tc_fence_before();
             __syncwarp();

@@ -26,6 +26,7 @@
 // (common.cuh), so the reduction order is fixed and the result reproducible.
 #include "common.cuh"
 #include "ptx.cuh"
+#include "qtile_epi.cuh"
 
 #include <algorithm>
 #include <float.h>
@@ -838,19 +839,13 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
             for (int cc = 0; cc < T / 32; ++cc) {
                 float v[32];
                 tmem_ld32(tbase + (uint32_t)acc * T + ((uint32_t)(32 * g) << 16) + (uint32_t)(32 * cc), v);
-                __align__(16) __nv_bfloat16 out[32];
-#pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    const int col = 32 * cc + c, j = J * T + col;
-                    const bool valid = i < n && j < n && (I != J || col > r);
-                    const float yj = j < n ? p.y[j] : 0.f, sj = j < n ? p.sqb[j] : 0.f;
-                    const float d2 = fmaxf(0.f, si + sj - 2.f * v[c]);
-                    const float q = yi * yj * (expf(-p.gamma * d2) + p.lam2);
-                    out[c] = __float2bfloat16_rn(valid ? q : 0.f);
-                }
+                const int jl = J * T + 32 * cc + lane;
+                const float yl = jl < n ? p.y[jl] : 0.f, sl = jl < n ? p.sqb[jl] : 0.f;
+                uint4 out[4];
+                q_chunk_bf16(v, yi, si, yl, sl, p.gamma, p.lam2, chunk_valid(n, I, J, r, cc), out);
                 uint4* dst = reinterpret_cast<uint4*>(qrow + 32 * cc);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) dst[u] = reinterpret_cast<const uint4*>(out)[u];
+                for (int u = 0; u < 4; ++u) dst[u] = out[u];
             }
             tc_fence_before();
             __syncwarp();

@@ -133,6 +133,7 @@ def load():
         "gabp_server_submit": (st, [V, P(Problem), V, P(I64)]),
         "gabp_server_step": (st, [V, P(I32), P(I32), P(I32)]),
         "gabp_server_poll": (st, [V, I64, P(Result), P(I32)]),
+        "gabp_server_completed": (st, [V, V, I32, P(I32)]),
         "gabp_server_destroy": (st, [V]),
         "gabp_last_error": (ctypes.c_char_p, []),
         "gabp_version": (I32, []),
@@ -376,6 +377,17 @@ class Server:
         a, q, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         _check(load().gabp_server_step(self.h, ctypes.byref(a), ctypes.byref(q), ctypes.byref(c)))
         return a.value, q.value, c.value
+
+    def completed(self, cap=4096):
+        """Tickets finished since the previous call."""
+        buf = (ctypes.c_int64 * cap)()
+        out = []
+        while True:
+            k = ctypes.c_int32()
+            _check(load().gabp_server_completed(self.h, ctypes.cast(buf, ctypes.c_void_p), cap, ctypes.byref(k)))
+            out.extend(buf[i] for i in range(k.value))
+            if k.value < cap:
+                return out
 
     def poll(self, ticket):
         r = Result()

@@ -95,14 +95,19 @@ def test_server_results_equal_alone():
             pending = pending[2:]
         active, queued, done = srv.step()
         assert active <= 4
+        fresh = srv.completed()
+        new = []
         for t in tickets:
             if t not in out:
                 r = srv.poll(t)
                 if r is not None:
                     out[t] = r
+                    new.append(t)
+        assert sorted(fresh) == sorted(new)   # completed() reports exactly the newly finished
         if len(out) == len(probs) and not pending:
             break
     assert len(out) == len(probs)
+    assert srv.completed() == []
     for t, p in zip(tickets, probs):
         a, r = out[t]
         assert r["status"] == 0 and r["converged"] == 1
