@@ -17,12 +17,13 @@
 //
 // The sweep is bound by HBM bandwidth: per pair it reads 16 B of messages and
 // 4 B of Q (2 B in BF16) and writes 16 B; once the P messages sit at their
-// fixed point it writes only the 8 B of H.  Messages and Q arrive in shared
-// memory through bulk copies issued by a producer warp well ahead of use;
-// consumer warp w takes one row of each 8-row chunk, lane l the columns l,
-// l+32, l+64, l+96, so every message store of a warp covers 512 contiguous
-// bytes.  Row sums go through warp shuffles, column sums stay in registers
-// and meet in shared memory, and each node's per-tile sums go to its own slot
+// fixed point it writes only the 8 B of H (messages stored in BF16 halve the
+// message bytes).  Messages and Q arrive in shared memory through bulk copies
+// issued by a producer warp well ahead of use; consumer warp w takes one row
+// of each 8-row chunk, each lane four of its columns laid out so that every
+// warp access to a row is one contiguous 512-byte span (lane_col).  Row sums
+// go through one warp reduction per row, column sums stay in registers and
+// meet in shared memory, and each node's per-tile sums go to its own slot
 // (common.cuh), so the reduction order is fixed and the result reproducible.
 #include "common.cuh"
 #include "ptx.cuh"
@@ -41,13 +42,16 @@ __device__ __forceinline__ void consumer_bar() { asm volatile("bar.sync 1, %0;" 
 
 // ---- pair sweep -----------------------------------------------------------
 // Persistent CTAs walk the tile list with stride gridDim.x.  A producer warp
-// streams every tile as chunks of RC rows of messages (and, when Q is stored,
-// of Q) into a STAGES-deep shared-memory ring with bulk copies, running ahead
-// across tile boundaries; eight consumer warps take one row of each chunk,
-// update its pairs from shared memory and store the new messages straight to
-// global memory with 128-bit streaming stores.  Only the pairs the tile owns
-// are copied: whole chunks for interior tiles, the c > r part of each row on
-// diagonal tiles, the first `cols` columns on the last tile column.
+// publishes each tile's parameters and bulk-copies its row and column
+// aggregates into a double-buffered tile slot, then streams the tile as
+// chunks of RC rows of messages (and, when Q is stored, of Q) into a
+// STAGES-deep shared-memory ring, running ahead across tile boundaries; the
+// consumers follow the tiles it publishes.  Eight consumer warps take one row
+// of each chunk, update its pairs from shared memory and store the new
+// messages straight to global memory with 128-bit streaming stores.  Only the
+// pairs the tile owns are copied: whole chunks for interior tiles, the c > r
+// part of each row on diagonal tiles, the first `cols` columns on the last
+// tile column (one row per producer lane).
 //
 // Two kernels share the producer and consumer code:
 //   k_sweep<QT>   Q stored (FP32 or BF16) and streamed with the messages;
