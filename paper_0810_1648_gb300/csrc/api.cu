@@ -519,7 +519,8 @@ gabp_status gabp_svm_solve(gabp_svm_t h, int32_t iters, double tol, float* alpha
     auto final_pass = [&](const StopOp& o) -> gabp_status {
         CK(cudaMemcpyAsync(h->d_ops, &o, sizeof(StopOp), cudaMemcpyHostToDevice, s));
         if (o.acc) launch_axpy_list(h->d_tab, h->d_ops, h->nbl, nblk, s);
-        launch_final(h->d_tab, h->d_ops, h->work, h->ntiles, h->nbl, nblk, h->d_members, 1, nullptr, s);
+        launch_final(h->d_tab, h->d_ops, h->work, h->ntiles, h->nbl, nblk, h->d_members, 1, nullptr,
+                     h->inst.qref != nullptr, s);
         h->prof.kernel_launches += o.acc ? 4 : 3;
         CK(cudaGetLastError());
         return GABP_OK;

@@ -601,7 +601,7 @@ class Engine {
                            stream));
         launch_axpy_list(d_tab, d_ops, d_stop_nbl, (int)nb.size(), stream);
         launch_final(d_tab, d_ops, d_stop_tiles, (long long)tiles.size(), d_stop_nbl, (int)nb.size(), d_stop_members,
-                     (int)stopped.size(), d_f3, stream);
+                     (int)stopped.size(), d_f3, q_mode != 2, stream);   // FP32 tiles kept unless recomputing
         launches += 4;
         EK(cudaGetLastError());
         EK(cudaMemcpyAsync(h_f3, d_f3, (size_t)cap_members * 3 * sizeof(double), cudaMemcpyDeviceToHost, stream));

@@ -173,8 +173,10 @@ void launch_round(const Inst* tab, const int4* work, const int2* nbl, const Sche
 // Final FP32-Gram residual r = 1 - Q mu (FP64 sums), dual objective and
 // alpha = clip(mu, 0, C) of the listed instances (their tiles, node blocks
 // and slots), per ops[slot]; results in ops[slot].final3 and f3_all[3 slot].
+// q_stored: the instances keep FP32 Q tiles (Inst::qref), read instead of
+// recomputing the Gram.
 void launch_final(const Inst* tab, const StopOp* ops, const int4* tiles, long long ntiles, const int2* nbl,
-                  int nblocks, const int* members, int nmembers, double* f3_all, cudaStream_t s);
+                  int nblocks, const int* members, int nmembers, double* f3_all, int q_stored, cudaStream_t s);
 // Refinement over listed node blocks: acc (+)= mutilde (ops[slot].axpy_*).
 void launch_axpy_list(const Inst* tab, const StopOp* ops, const int2* nbl, int nblocks, cudaStream_t s);
 // Refinement over listed node blocks: b := ops[slot].r_out, H restarts.

@@ -244,27 +244,19 @@ __global__ void __launch_bounds__(NTHREADS) k_form_q(const Inst* __restrict__ ta
 
 // ------------------------------------------- final residual and Q alpha
 // For every instance k listed: off-diagonal sums sum_{j != i} Q_ij mu_j
-// (-> part[0]) and sum_{j != i} Q_ij alpha_j (-> part[1]) with
-// alpha = clip(mu, 0, C) and mu = ops[k].mu, Q recomputed in FP32 (bitwise
-// equal to the stored FP32 tiles).  One CTA per listed tile.
-__global__ void __launch_bounds__(NTHREADS) k_final_tiles(const Inst* __restrict__ tab,
-                                                          const StopOp* __restrict__ ops,
-                                                          const int4* __restrict__ work)
+// (-> part[0]) and sum_{j != i} Q_ij alpha_j (-> part[1]).
+//
+// Per listed tile: partial sums of (Q mu)_i and (Q alpha)_i over the tile's
+// pairs (both roles) into the slot partials, with alpha = clip(mu, 0, C) and
+// mu = ops[k].mu.  acc holds the tile's stored FP32 Q values (STORED) or its
+// FP32 Gram values, from which Q is formed exactly as at formation, so both
+// give the same values.
+template <bool STORED>
+__device__ __forceinline__ void final_tile_sums(const Inst& p, const float* __restrict__ mu, int I, int J,
+                                                float (&acc)[8][8], EpiSmem& es)
 {
-    __shared__ __align__(16) TileSmem sm;
-    const int4 w = work[blockIdx.x];
-    const Inst& p = tab[w.x];
-    const float* __restrict__ mu = ops[w.x].mu;
-    const int I = w.y, J = w.z, n = p.n;
+    const int n = p.n;
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    // Q of the tile: read back from the FP32 store where one is kept (the same
-    // values the Gram below gives), else recomputed
-    const float* qt = p.qref ? p.qref + (size_t)w.w * TT : nullptr;
-    float acc[8][8];
-    if (!qt) {
-        const GramSide S{p.X, p.sq, n};
-        gram_tile(S, S, p.m, I, J, sm.g, acc);
-    }
     float yj[8], sj[8], mj[8], aj[8];
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
@@ -283,18 +275,12 @@ __global__ void __launch_bounds__(NTHREADS) k_final_tiles(const Inst* __restrict
         const float yi = i < n ? p.y[i] : 0.f, si = i < n ? p.sq[i] : 0.f;
         const float mi = i < n ? mu[i] : 0.f, ai = fminf(fmaxf(mi, 0.f), p.C);
         float rm = 0.f, ra = 0.f;
-        float qs[8];
-        if (qt) {
-            const float4 u0 = *reinterpret_cast<const float4*>(qt + r * T + tx * 8);
-            const float4 u1 = *reinterpret_cast<const float4*>(qt + r * T + tx * 8 + 4);
-            qs[0] = u0.x; qs[1] = u0.y; qs[2] = u0.z; qs[3] = u0.w;
-            qs[4] = u1.x; qs[5] = u1.y; qs[6] = u1.z; qs[7] = u1.w;
-        }
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
             const int c = tx * 8 + b, j = J * T + c;
             const bool v = i < n && j < n && (I != J || c > r);
-            const float q0 = qt ? qs[b] : yi * yj[b] * (rbf_from_gram(acc[a][b], si, sj[b], p.gamma) + p.lam2);
+            const float q0 =
+                STORED ? acc[a][b] : yi * yj[b] * (rbf_from_gram(acc[a][b], si, sj[b], p.gamma) + p.lam2);
             const float q = v ? q0 : 0.f;
             rm = fmaf(q, mj[b], rm);
             ra = fmaf(q, aj[b], ra);
@@ -305,8 +291,45 @@ __global__ void __launch_bounds__(NTHREADS) k_final_tiles(const Inst* __restrict
         rs[1][a] = ra;
     }
     float* const parts[2] = {p.part, p.part + (size_t)p.Nt * n};
+    reduce_and_write<2>(es, rs, cs, parts, n, I, J);
+}
+
+// Q recomputed by the FP32 Gram (forms without an FP32 store).  One CTA per
+// listed tile.
+__global__ void __launch_bounds__(NTHREADS) k_final_tiles(const Inst* __restrict__ tab,
+                                                          const StopOp* __restrict__ ops,
+                                                          const int4* __restrict__ work)
+{
+    __shared__ __align__(16) TileSmem sm;
+    const int4 w = work[blockIdx.x];
+    const Inst& p = tab[w.x];
+    float acc[8][8];
+    const GramSide S{p.X, p.sq, p.n};
+    gram_tile(S, S, p.m, w.y, w.z, sm.g, acc);
     __syncthreads();   // Gram smem is reused by the epilogue
-    reduce_and_write<2>(sm.e, rs, cs, parts, n, I, J);
+    final_tile_sums<false>(p, ops[w.x].mu, w.y, w.z, acc, sm.e);
+}
+
+// Q read back from the FP32 tiles (Inst::qref): no Gram, small footprint, so
+// several CTAs share an SM and the pass runs at memory speed.
+__global__ void __launch_bounds__(NTHREADS, 2) k_final_tiles_q(const Inst* __restrict__ tab,
+                                                               const StopOp* __restrict__ ops,
+                                                               const int4* __restrict__ work)
+{
+    __shared__ __align__(16) EpiSmem es;
+    const int4 w = work[blockIdx.x];
+    const Inst& p = tab[w.x];
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    const float* qt = p.qref + (size_t)w.w * TT;
+    float acc[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const float4 u0 = *reinterpret_cast<const float4*>(qt + (ty * 8 + a) * T + tx * 8);
+        const float4 u1 = *reinterpret_cast<const float4*>(qt + (ty * 8 + a) * T + tx * 8 + 4);
+        acc[a][0] = u0.x; acc[a][1] = u0.y; acc[a][2] = u0.z; acc[a][3] = u0.w;
+        acc[a][4] = u1.x; acc[a][5] = u1.y; acc[a][6] = u1.z; acc[a][7] = u1.w;
+    }
+    final_tile_sums<true>(p, ops[w.x].mu, w.y, w.z, acc, es);
 }
 
 // Per node of a listed node block: r_i = 1 - Q_ii mu_i - sum part0,
@@ -493,9 +516,14 @@ void launch_form_q(const Inst* tab, const int4* work, long long ntiles, cudaStre
 }
 
 void launch_final(const Inst* tab, const StopOp* ops, const int4* tiles, long long ntiles, const int2* nbl,
-                  int nblocks, const int* members, int nmembers, double* f3_all, cudaStream_t s)
+                  int nblocks, const int* members, int nmembers, double* f3_all, int q_stored, cudaStream_t s)
 {
-    if (ntiles > 0) k_final_tiles<<<(unsigned)ntiles, NTHREADS, 0, s>>>(tab, ops, tiles);
+    if (ntiles > 0) {
+        if (q_stored)
+            k_final_tiles_q<<<(unsigned)ntiles, NTHREADS, 0, s>>>(tab, ops, tiles);
+        else
+            k_final_tiles<<<(unsigned)ntiles, NTHREADS, 0, s>>>(tab, ops, tiles);
+    }
     if (nblocks > 0) k_final_nodes<<<nblocks, 256, 0, s>>>(tab, ops, nbl);
     if (nmembers > 0) k_final_reduce<<<nmembers, 256, 0, s>>>(tab, ops, members, f3_all);
 }
