@@ -883,7 +883,7 @@ __device__ __forceinline__ void acc2(float& s, float& c, float x)
 }
 
 // Per node x: compensated sums of its Nt slots (32 nodes x 8 slot groups per
-// CTA, eight slots in flight per thread), next aggregates, residual r_x(t) in
+// CTA, four slots in flight per thread), next aggregates, residual r_x(t) in
 // FP64, CTA max |r| -> ctrl, the last CTA to finish decides.
 __global__ void __launch_bounds__(256)
     k_finalize(const Inst* __restrict__ tab, const int2* __restrict__ nbl, const Sched* __restrict__ sched)
@@ -905,20 +905,24 @@ __global__ void __launch_bounds__(256)
     const float* partR = partH + (size_t)Nt * n;
     float sP = 0.f, cPs = 0.f, sH = 0.f, cHs = 0.f, sR = 0.f, cRs = 0.f;
     if (x < n) {
-        // eight slots in flight per thread; slots past Nt add exact zeros
-        for (int k = g; k < Nt; k += 64) {
-            float vp[8], vh[8], vr[8];
+        int k = g;
+        for (; k + 24 < Nt; k += 32) {
+            float vp[4], vh[4], vr[4];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int kk = k + 8 * u;
-                const size_t o = (size_t)kk * n + x;
-                const bool in = kk < Nt;
-                vp[u] = in && !frozen ? partP[o] : 0.f;
-                vh[u] = in ? partH[o] : 0.f;
-                vr[u] = in ? partR[o] : 0.f;
+            for (int u = 0; u < 4; ++u) {
+                const size_t o = (size_t)(k + 8 * u) * n + x;
+                vp[u] = frozen ? 0.f : partP[o];
+                vh[u] = partH[o];
+                vr[u] = partR[o];
             }
 #pragma unroll
-            for (int u = 0; u < 8; ++u) { acc2(sP, cPs, vp[u]); acc2(sH, cHs, vh[u]); acc2(sR, cRs, vr[u]); }
+            for (int u = 0; u < 4; ++u) { acc2(sP, cPs, vp[u]); acc2(sH, cHs, vh[u]); acc2(sR, cRs, vr[u]); }
+        }
+        for (; k < Nt; k += 8) {
+            const size_t o = (size_t)k * n + x;
+            acc2(sP, cPs, frozen ? 0.f : partP[o]);
+            acc2(sH, cHs, partH[o]);
+            acc2(sR, cRs, partR[o]);
         }
     }
     __syncthreads();   // red[] of the previous node block is consumed
