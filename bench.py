@@ -291,6 +291,7 @@ def run_serve(args):
                       refine=8 if args.q_mode != "f32" else 0, msg_bf16=1 if args.msg_bf16 else 0, chunk=4)
     t0 = time.perf_counter()
     sub, lat, nxt = {}, [], 0
+    rounds, passes, conv = [], [], 0
     done_n = 0
     while done_n < len(reqs):
         now = time.perf_counter() - t0
@@ -305,12 +306,17 @@ def run_serve(args):
             nxt += 1
         active, queued, completed = srv.step()
         for t in srv.completed():
-            if srv.poll(t) is not None:
+            res = srv.poll(t)
+            if res is not None:
                 lat.append(time.perf_counter() - t0 - sub.pop(t))
+                rounds.append(res[1]["iters_done"])
+                passes.append(res[1]["refine_passes"])
+                conv += res[1]["converged"]
                 done_n += 1
         if active == 0 and queued == 0 and nxt < len(reqs):
             time.sleep(max(0.0, min(0.01, reqs[nxt].t_arrive - (time.perf_counter() - t0))))
     wall = time.perf_counter() - t0
+    phases = srv.phases()
     srv.close()
     lat = np.array(lat)
     line = {"metric": METRIC, "value": len(reqs) / wall, "unit": "solves/s", "n_gpus": 1, "steps": 1,
@@ -322,7 +328,9 @@ def run_serve(args):
                        "requests": len(reqs), "q_mode": args.q_mode, "max_members": args.max_members},
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "max": float(lat.max())},
-            "wall_s": wall, "offered_per_s": args.rate}
+            "wall_s": wall, "offered_per_s": args.rate, "server_phases_ms": phases,
+            "mean_rounds": float(np.mean(rounds)), "mean_refine_passes": float(np.mean(passes)),
+            "converged": int(conv)}
     print(json.dumps(line), flush=True)
     return 0
 

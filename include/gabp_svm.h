@@ -235,12 +235,13 @@ GABP_API gabp_status gabp_batch_last_phases(double* out6);
 
 /*
  * Continuous-batching server.  Requests queue in arrival order; each
- * gabp_server_step() admits queued requests while free slots and the device
- * memory budget allow (their Q is formed on a side stream while the other
- * instances keep sweeping), runs one chunk of rounds over every live
- * instance, and retires the instances that stopped (their alpha is copied to
- * the caller's buffer).  The problem's X and y must stay valid until its
- * ticket completes.
+ * gabp_server_step() launches one chunk of rounds over every live instance,
+ * admits queued requests while it runs (free slots and the device memory
+ * budget permitting; their Q is formed on a side stream while the other
+ * instances keep sweeping), retires the instances that stopped (their alpha
+ * is copied to the caller's buffer), and lets instances whose formation has
+ * finished join from the next chunk.  The problem's X and y must stay valid
+ * until its ticket completes.
  */
 typedef struct gabp_server_s* gabp_server_t;
 typedef struct {
@@ -261,6 +262,12 @@ GABP_API gabp_status gabp_server_poll(gabp_server_t s, int64_t ticket, gabp_resu
  * the next call.  Lets a caller with many requests in flight poll only the
  * finished ones. */
 GABP_API gabp_status gabp_server_completed(gabp_server_t s, int64_t* tickets, int32_t cap, int32_t* count);
+/* Host wall time (ms) spent in the phases of gabp_server_step since the
+ * server was created: out8 = {admission (device allocation, input copies,
+ * formation launches), activation, round-list rebuilds, rounds (the chunk and
+ * its wait), stop handling (final residuals, refinement, retiring), total,
+ * number of steps, number of list rebuilds}. */
+GABP_API gabp_status gabp_server_phases(gabp_server_t s, double* out8);
 GABP_API gabp_status gabp_server_destroy(gabp_server_t s);
 
 /*

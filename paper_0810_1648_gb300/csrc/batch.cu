@@ -144,6 +144,8 @@ class Engine {
     int q_mode = 0, diag_rule = 0, x_f64 = 0, ptr_mode = 0, msg_bf16 = 0;
     double delta = 0.1, sv_threshold = 0.0;
     double handover = 1e-4, inner = 1e-2;   // refinement schedule
+    double t_rebuild = 0;                    // host ms spent rebuilding the round lists
+    int64_t rebuilds = 0;
     int cap_members = 0;
     long long cap_tiles = 0;
     int cap_nblk = 0;
@@ -461,6 +463,13 @@ class Engine {
     gabp_status rebuild()
     {
         if (!lists_dirty) return GABP_OK;
+        const auto t0 = std::chrono::steady_clock::now();
+        struct Acc {   // host time of the list rebuilds
+            double& t;
+            std::chrono::steady_clock::time_point t0;
+            ~Acc() { t += ms_since(t0); }
+        } acc{t_rebuild, t0};
+        ++rebuilds;
         std::vector<int4> wl;
         std::vector<int2> nb;
         for (int k = 0; k < cap_members; ++k) {
@@ -502,8 +511,9 @@ class Engine {
         return GABP_OK;
     }
 
-    // One captured chunk of rounds over the live lists, then reads every control block.
-    gabp_status run_chunk(int rounds)
+    // One captured chunk of rounds over the live lists, then every control
+    // block read back; launch_chunk returns at once, wait_chunk waits.
+    gabp_status launch_chunk(int rounds)
     {
         if (gabp_status st = rebuild()) return st;
         if (live_tiles > 0) {
@@ -513,8 +523,17 @@ class Engine {
             launches += 2LL * rounds;
         }
         EK(cudaMemcpyAsync(h_ctrl, d_ctrl, (size_t)cap_members * sizeof(Ctrl), cudaMemcpyDeviceToHost, stream));
+        return GABP_OK;
+    }
+    gabp_status wait_chunk()
+    {
         EK(cudaStreamSynchronize(stream));
         return GABP_OK;
+    }
+    gabp_status run_chunk(int rounds)
+    {
+        if (gabp_status st = launch_chunk(rounds)) return st;
+        return wait_chunk();
     }
 
     // Records the results of a stopped instance from its final residual /
@@ -852,6 +871,9 @@ struct gabp_server_s {
     std::deque<int64_t> fresh;   // finished, not yet reported by gabp_server_completed
     std::vector<int> forming;   // slots whose Q formation runs on the side stream
     int64_t next_ticket = 0;
+    // host wall time (ms) per phase of gabp_server_step, since creation
+    double t_admit = 0, t_activate = 0, t_rounds = 0, t_stop = 0, t_total = 0;
+    int64_t steps = 0;
 };
 
 gabp_status gabp_server_create(const gabp_server_cfg* cfg, gabp_server_t* out)
@@ -907,7 +929,20 @@ gabp_status gabp_server_step(gabp_server_t s, int32_t* active, int32_t* queued, 
     set_last_error("");
     if (!s) { set_last_error("gabp_server_step: null server"); return GABP_EINVAL; }
     Engine& E = s->E;
-    // 1. admission, first come first served, by device-memory budget and free slots
+    using clk = std::chrono::steady_clock;
+    const auto t_step = clk::now();
+    auto t0 = t_step;
+    // 1. one chunk of rounds over every live instance: launched now, waited
+    //    for after the admission work below, which overlaps it
+    bool any = false;
+    for (auto& M : E.mem) any |= (M.used && M.active);
+    if (any) {
+        if (gabp_status st = E.launch_chunk(E.chunk)) return st;
+        s->t_rounds += ms_since(t0);
+    }
+    // 2. admission, first come first served, by device-memory budget and free
+    //    slots; formation on the side stream
+    t0 = clk::now();
     while (!s->queue.empty()) {
         const auto& front = s->queue.front();
         const size_t need = member_plan(front.second.n, front.second.m, s->cfg.opts.q_mode, s->cfg.opts.msg_bf16).total;
@@ -933,7 +968,28 @@ gabp_status gabp_server_step(gabp_server_t s, int32_t* active, int32_t* queued, 
         s->queue.pop_front();
     }
     if (gabp_status st = E.form_pending()) return st;
-    // 2. instances whose Q is ready join the sweeps
+    s->t_admit += ms_since(t0);
+    // 3. end of the chunk: retire the instances that stopped
+    if (any) {
+        t0 = clk::now();
+        if (gabp_status st = E.wait_chunk()) return st;
+        s->t_rounds += ms_since(t0);
+        t0 = clk::now();
+        int running = 0;
+        std::vector<int> fin;
+        if (gabp_status st = E.advance(&running, &fin)) return st;
+        for (int slot : fin) {
+            Member& M = E.mem[(size_t)slot];
+            gabp_result r = M.res;
+            r.alpha = M.out_alpha;
+            s->done[M.ticket] = r;
+            s->fresh.push_back(M.ticket);
+            E.release(M);
+        }
+        s->t_stop += ms_since(t0);
+    }
+    // 4. instances whose Q is ready join the sweeps from the next chunk
+    t0 = clk::now();
     std::vector<int> ready;
     for (size_t k = 0; k < s->forming.size();) {
         const int slot = s->forming[k];
@@ -948,23 +1004,9 @@ gabp_status gabp_server_step(gabp_server_t s, int32_t* active, int32_t* queued, 
         }
     }
     if (gabp_status st = E.activate_list(ready)) return st;
-    // 3. one chunk of rounds over every live instance, then retire the finished
-    int running = 0;
-    bool any = false;
-    for (auto& M : E.mem) any |= (M.used && M.active);
-    if (any) {
-        if (gabp_status st = E.run_chunk(E.chunk)) return st;
-        std::vector<int> fin;
-        if (gabp_status st = E.advance(&running, &fin)) return st;
-        for (int slot : fin) {
-            Member& M = E.mem[(size_t)slot];
-            gabp_result r = M.res;
-            r.alpha = M.out_alpha;
-            s->done[M.ticket] = r;
-            s->fresh.push_back(M.ticket);
-            E.release(M);
-        }
-    }
+    s->t_activate += ms_since(t0);
+    s->t_total += ms_since(t_step);
+    ++s->steps;
     int act = 0;
     for (auto& M : E.mem) act += M.used ? 1 : 0;
     if (active) *active = act;
@@ -996,6 +1038,21 @@ gabp_status gabp_server_completed(gabp_server_t s, int64_t* tickets, int32_t cap
         s->fresh.pop_front();
     }
     *count = k;
+    return GABP_OK;
+}
+
+gabp_status gabp_server_phases(gabp_server_t s, double* out8)
+{
+    gabp::set_last_error("");
+    if (!s || !out8) { gabp::set_last_error("gabp_server_phases: null argument"); return GABP_EINVAL; }
+    out8[0] = s->t_admit;
+    out8[1] = s->t_activate;
+    out8[2] = s->E.t_rebuild;
+    out8[3] = s->t_rounds - s->E.t_rebuild;
+    out8[4] = s->t_stop;
+    out8[5] = s->t_total;
+    out8[6] = (double)s->steps;
+    out8[7] = (double)s->E.rebuilds;
     return GABP_OK;
 }
 

@@ -134,6 +134,7 @@ def load():
         "gabp_server_step": (st, [V, P(I32), P(I32), P(I32)]),
         "gabp_server_poll": (st, [V, I64, P(Result), P(I32)]),
         "gabp_server_completed": (st, [V, V, I32, P(I32)]),
+        "gabp_server_phases": (st, [V, V]),
         "gabp_server_destroy": (st, [V]),
         "gabp_last_error": (ctypes.c_char_p, []),
         "gabp_version": (I32, []),
@@ -388,6 +389,13 @@ class Server:
             out.extend(buf[i] for i in range(k.value))
             if k.value < cap:
                 return out
+
+    def phases(self):
+        """Host wall time (ms) per phase of the steps so far."""
+        out = (ctypes.c_double * 8)()
+        _check(load().gabp_server_phases(self.h, ctypes.cast(out, ctypes.c_void_p)))
+        keys = ("admit_ms", "activate_ms", "rebuild_ms", "rounds_ms", "stop_ms", "total_ms", "steps", "rebuilds")
+        return dict(zip(keys, list(out)))
 
     def poll(self, ticket):
         r = Result()
