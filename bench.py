@@ -140,9 +140,9 @@ def _traffic_from_profile(kernel_src: str):
     return float(m_b.group(1)) if sha == m_sha.group(1) else None
 
 
-def _oracle_sample(p, sweeps: int):
+def _oracle_sample(p, sweeps: int, single: bool = False):
     """Times the FP64 oracle: Q formation for the whole set + `sweeps` rounds.
-    Returns (t_q, t_per_sweep, threads)."""
+    Returns (t_q, t_per_sweep, threads[, t_per_sweep with one thread])."""
     import oracle
     X = p.X.astype(np.float64)
     y = p.y.astype(np.float64)
@@ -151,8 +151,19 @@ def _oracle_sample(p, sweeps: int):
     t1 = time.perf_counter()
     oracle.gabp(Q, np.ones(p.n), iters=sweeps, tol=0.0)
     t2 = time.perf_counter()
+    th = oracle.threads()
+    if not single:
+        del Q
+        return t1 - t0, (t2 - t1) / max(sweeps, 1), th
+    oracle.set_threads(1)
+    try:
+        t3 = time.perf_counter()
+        oracle.gabp(Q, np.ones(p.n), iters=1, tol=0.0)
+        t4 = time.perf_counter()
+    finally:
+        oracle.set_threads(th)
     del Q
-    return t1 - t0, (t2 - t1) / max(sweeps, 1), oracle.threads()
+    return t1 - t0, (t2 - t1) / max(sweeps, 1), th, t4 - t3
 
 
 def _host_mem_gb():
@@ -170,12 +181,13 @@ def _cpu_baseline(p, sweeps: int):
     if _host_mem_gb() < need_gb * 1.3:
         return {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
                 "sample": f"skipped: the FP64 oracle needs {need_gb:.0f} GB of host memory"}
-    tq, ts, th = _oracle_sample(p, sweeps)
+    tq, ts, th, t1 = _oracle_sample(p, sweeps, single=True)
     v = ROUNDS / (tq + ROUNDS * ts)
     return {"value": v, "unit": UNIT, "cores": th, "kind": "oracle",
             "sample": f"FP64 oracle on the same workload: Q formation for all n=20000 points "
                       f"({tq:.1f} s) + {sweeps} synchronous rounds ({ts:.2f} s each), "
-                      f"scaled to one {ROUNDS}-round solve"}
+                      f"scaled to one {ROUNDS}-round solve",
+            "single_thread_s_per_sweep": t1}
 
 
 def run_reference(args):
