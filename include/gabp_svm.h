@@ -68,6 +68,18 @@ typedef enum {
     GABP_Q_RECOMPUTE = 2   /* not stored: every sweep recomputes Q tiles on the tensor cores (BF16 Gram, FP32 accumulate) */
 } gabp_q_mode;
 
+/* The problem solved on the same sweep.  SVM (Section 1.1, 3): y are labels
+ * +-1, Q_ij = y_i y_j (K + lambda^2), right-hand side 1, alpha = clip(mu, 0,
+ * C).  KRR, kernel ridge regression (Section 1.2): y are real targets, the
+ * C argument is the ridge lambda_r, Q = K + lambda_r I (under the soft2 rule;
+ * the dominant rule raises the diagonal as for the SVM), right-hand side y,
+ * alpha = c = Q^-1 y unclipped, the bias term off unless bias_mode = 1, and
+ * f(x) = sum_i c_i K(x_i, x). */
+typedef enum {
+    GABP_TASK_SVM = 0,
+    GABP_TASK_KRR = 1
+} gabp_task;
+
 typedef enum {
     GABP_DIAG_DOMINANT = 0, /* Q_ii = max(1 + lambda^2 + 1/C, (1 + delta) sum_{j!=i} |Q_ij|) */
     GABP_DIAG_SOFT2 = 1     /* Q_ii = 1 + lambda^2 + 1/C (2-norm soft margin only) */
@@ -96,7 +108,8 @@ typedef struct {
     float   refine_inner;  /* refinement only: each correction pass stops once its residual is below
                               refine_inner * ||r||_inf of its right-hand side (never below tol / 2);
                               0 = 3e-2 with BF16 messages, 1e-2 with FP32 messages */
-    int32_t reserved[4];
+    int32_t task;          /* gabp_task, default GABP_TASK_SVM */
+    int32_t reserved[3];
 } gabp_svm_opts;
 
 typedef struct gabp_svm_s* gabp_svm_t;
@@ -121,7 +134,9 @@ GABP_API void gabp_svm_opts_default(gabp_svm_opts* opts);
 
 /*
  * Create a solver for the n x m training set X (row-major) with labels y
- * (n floats, each +1 or -1), RBF width gamma > 0 and box constant C > 0.
+ * (n floats, each +1 or -1), RBF width gamma > 0 and box constant C > 0
+ * (with opts->task = GABP_TASK_KRR: y are finite real targets and C > 0 is
+ * the ridge lambda_r).
  * Forms Q on the device (Gram kernel fused with exp, bias and labels), weights
  * its diagonal (Section 3.1) and sets the GaBP state to Algorithm 2's Step 1
  * (all messages 0).  Requires n >= 2, m >= 1.
@@ -147,9 +162,11 @@ GABP_API gabp_status gabp_svm_refit(gabp_svm_t h, const void* X, const float* y,
 /*
  * Run synchronous broadcast-GaBP rounds (Algorithm 2, Steps 2-3) from the
  * handle's current state.  Round t forms the aggregates Ptilde_i, mutilde_i of
- * the current messages and the residual r(t) = 1 - Q mutilde(t); it stops at
+ * the current messages and the residual r(t) = b - Q mutilde(t) (b = 1 for
+ * the SVM, the targets for KRR); it stops at
  * the first t with ||r(t)||_inf < tol (tol <= 0: never), or after `iters`
- * message updates.  Writes alpha = clip(mutilde(kstar), 0, C) (n floats) and,
+ * message updates.  Writes alpha = clip(mutilde(kstar), 0, C) (KRR: the
+ * unclipped mutilde(kstar)) (n floats) and,
  * when non-NULL, ||r(kstar)||_inf (FP64) and the number of updates done in
  * this call.  Calling again continues from the current messages.
  * GABP_ENUMERIC if a cavity precision went nonpositive (the matrix is then
@@ -165,11 +182,13 @@ GABP_API gabp_status gabp_svm_get_mean(gabp_svm_t h, float* mu);
 
 /* Decision values f(x) = sum_i alpha_i y_i (K(x_i, x) + lambda^2) for t test
  * rows Xtest (t x m, same dtype and pointer mode as X) with the alpha of the
- * last solve; the predicted label is sign(f).  out: t floats. */
+ * last solve; the predicted label is sign(f).  KRR: the prediction
+ * f(x) = sum_i c_i K(x_i, x) (+ lambda^2 sum_i c_i with the bias on).
+ * out: t floats. */
 GABP_API gabp_status gabp_svm_decision(gabp_svm_t h, const void* Xtest, int64_t t, float* out);
 
-/* Indices i with alpha_i > sv_threshold, ascending (host memory). Writes up to
- * cap indices and the total count. */
+/* Indices i with alpha_i > sv_threshold (KRR: |c_i| > sv_threshold),
+ * ascending (host memory). Writes up to cap indices and the total count. */
 GABP_API gabp_status gabp_svm_support(gabp_svm_t h, int32_t* idx, int64_t cap, int64_t* count);
 
 GABP_API gabp_status gabp_svm_get_stats(gabp_svm_t h, gabp_svm_stats* stats);

@@ -288,3 +288,22 @@ def solve_svm(X, y, gamma, C, iters=200, tol=1e-6, lam=None,
     """
     Q = build_q(X, y, gamma, C, lam, diag_rule, delta)
     return Q, gabp(Q, np.ones(Q.shape[0]), iters, tol)
+
+
+def build_q_krr(X, gamma, ridge, lam=0.0, diag_rule=DIAG_DOMINANT, delta=0.1):
+    """Dense FP64 matrix of kernel ridge regression (Section 1.2) on the same
+    kernel: off-diagonal K_ij (+ lam^2 with the bias feature on), diagonal
+    K_ii + ridge = 1 + ridge under the soft2 rule, raised to (1 + delta) times
+    the row's off-diagonal sum under the dominant rule (Section 3.1 weighting).
+    No labels enter the matrix; the ridge takes the place of 1/C."""
+    X = np.asarray(X, dtype=np.float64)
+    return build_q(X, np.ones(X.shape[0]), gamma, 1.0 / ridge, lam, diag_rule, delta)
+
+
+def solve_krr(X, t, gamma, ridge, iters=200, tol=1e-6, lam=0.0,
+              diag_rule=DIAG_DOMINANT, delta=0.1):
+    """KRR solve: the matrix above, then Algorithm 2 with b = the targets.
+    Returns (Q, GabpResult); the coefficients are result.mu (unclipped) and
+    the prediction is f(x) = sum_i c_i (K(x_i, x) + lam^2)."""
+    Q = build_q_krr(X, gamma, ridge, lam, diag_rule, delta)
+    return Q, gabp(Q, np.asarray(t, dtype=np.float64), iters, tol)

@@ -123,7 +123,7 @@ Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_m
     p.rhist = align_up((size_t)kRhistCap * sizeof(double), 256);
     p.final3 = 256;
     p.blockbuf = align_up((size_t)3 * ((n + 31) / 32) * sizeof(double), 256);
-    p.total = p.X + 9 * p.vec + p.agg + p.part + p.state + p.q + p.qref + p.work + p.ctrl + p.rhist +
+    p.total = p.X + 10 * p.vec + p.agg + p.part + p.state + p.q + p.qref + p.work + p.ctrl + p.rhist +
               p.final3 + p.blockbuf + p.xp + p.tab + p.nbl + 1024;
     return p;
 }
@@ -146,7 +146,10 @@ gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
     Inst& p = h->inst;
     p.gamma = (float)h->gamma;
     p.lam2 = (float)(h->lambda * h->lambda);
-    p.C = (float)h->C;
+    // KRR: C is the ridge lambda_r; inside, 1/C enters the diagonal floor
+    // 1 + lambda^2 + 1/C as the SVM's 2-norm soft margin does
+    p.C = (float)(h->opts.task == GABP_TASK_KRR ? 1.0 / h->C : h->C);
+    p.task = h->opts.task;
     clear_graphs(h);
     h->solved = false;
     h->kstar = 0;
@@ -169,14 +172,16 @@ gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
             src = p.X;
         }
     }
-    launch_stage(src, f64 ? 1 : 0, (int)n, (int)m, p.y, (float*)p.X, (float*)p.sq, (float*)p.b, p.ctrl, s);
+    launch_stage(src, f64 ? 1 : 0, (int)n, (int)m, const_cast<float*>(p.y), (float*)p.X, (float*)p.sq, (float*)p.b,
+                 const_cast<float*>(p.b0), p.task, p.ctrl, s);
     h->prof.kernel_launches += 1;
     CK(cudaGetLastError());
     if (tmp) CK(cudaFreeAsync(tmp, s));
     CK(cudaMemcpyAsync(h->hctrl, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (h->hctrl->status != 0)
-        return fail(GABP_EINVAL, "row %lld: non-finite feature or label not +-1",
+        return fail(GABP_EINVAL, h->opts.task == GABP_TASK_KRR ? "row %lld: non-finite feature or target"
+                                                                : "row %lld: non-finite feature or label not +-1",
                     (long long)h->hctrl->bad_index);
     if (h->opts.q_mode == GABP_Q_F32) {
         launch_form_q(h->d_tab, h->work, h->ntiles, s);
@@ -351,6 +356,7 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     if (o.refine < 0 || o.refine > 64) return fail(GABP_EINVAL, "refine must be in [0, 64]");
     if (o.msg_bf16 != 0 && (o.msg_bf16 != 1 || o.q_mode == GABP_Q_F32))
         return fail(GABP_EINVAL, "msg_bf16 = 1 needs a precision form (q_mode BF16 or recompute)");
+    if (o.task != GABP_TASK_SVM && o.task != GABP_TASK_KRR) return fail(GABP_EINVAL, "unknown task %d", o.task);
 
     int dev = 0, ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -364,11 +370,11 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     h->n = n;
     h->m = m;
     h->Nt = (int)((n + T - 1) / T);
-    h->npad = (int)align_up((size_t)n, 64);
+    h->npad = (int)align_up((size_t)n, T);   // whole tiles: the sweep copies aggregate blocks of T
     h->ntiles = tri_tiles(h->Nt);
     h->gamma = gamma;
     h->C = C;
-    h->lambda = o.bias_mode == 1 ? o.bias_lambda : 1.0 / (double)n;
+    h->lambda = o.bias_mode == 1 ? o.bias_lambda : (o.task == GABP_TASK_KRR ? 0.0 : 1.0 / (double)n);
     h->delta = o.diag_delta;
 
     const Plan pl = make_plan(n, m, h->Nt, h->ntiles, h->npad, o.q_mode, o.msg_bf16);
@@ -410,6 +416,7 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     p.sq = (const float*)take(pl.vec);
     p.y = (const float*)take(pl.vec);
     p.b = (const float*)take(pl.vec);
+    p.b0 = (const float*)take(pl.vec);
     p.qdiag = (float*)take(pl.vec);
     h->alpha = (float*)take(pl.vec);
     take(pl.vec);
@@ -658,7 +665,7 @@ gabp_status gabp_svm_decision(gabp_svm_t h, const void* Xtest, int64_t t, float*
         CK(cudaMemcpyAsync(h->hctrl, h->inst.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         const int saved_status = h->hctrl->status;
-        launch_stage(src, f64 ? 1 : 0, (int)t, (int)m, nullptr, Xt, sqt, nullptr, h->inst.ctrl, s);
+        launch_stage(src, f64 ? 1 : 0, (int)t, (int)m, nullptr, Xt, sqt, nullptr, nullptr, 0, h->inst.ctrl, s);
         h->prof.kernel_launches += 1;
         CK(cudaMemcpyAsync(h->hctrl, h->inst.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -691,8 +698,9 @@ gabp_status gabp_svm_support(gabp_svm_t h, int32_t* idx, int64_t cap, int64_t* c
     CK(cudaStreamSynchronize(h->stream));
     int64_t c = 0;
     const float th = (float)h->opts.sv_threshold;
+    const bool krr = h->opts.task == GABP_TASK_KRR;
     for (int64_t i = 0; i < h->n; ++i)
-        if (a[(size_t)i] > th) {
+        if ((krr ? std::fabs(a[(size_t)i]) : a[(size_t)i]) > th) {
             if (c < cap) idx[c] = (int32_t)i;
             ++c;
         }

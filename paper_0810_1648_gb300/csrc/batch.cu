@@ -60,7 +60,7 @@ MemberPlan member_plan(int64_t n, int64_t m, int q_mode, int msg_bf16)
     p.final3 = 256;
     p.blockbuf = aup((size_t)3 * ((n + 31) / 32) * 8, 256);
     p.xp = q_mode != 0 ? aup(bf16_pack_bytes(Nt, (int)m), 1024) : 0;
-    p.total = p.X + 9 * p.vec + p.agg + p.part + p.state + p.q + p.qref + p.work + p.final3 + p.blockbuf + p.xp + 2048;
+    p.total = p.X + 10 * p.vec + p.agg + p.part + p.state + p.q + p.qref + p.work + p.final3 + p.blockbuf + p.xp + 2048;
     return p;
 }
 
@@ -141,8 +141,8 @@ class Engine {
         if (e_ != cudaSuccess) return fail(GABP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-    int q_mode = 0, diag_rule = 0, x_f64 = 0, ptr_mode = 0, msg_bf16 = 0;
-    double delta = 0.1, sv_threshold = 0.0;
+    int q_mode = 0, diag_rule = 0, x_f64 = 0, ptr_mode = 0, msg_bf16 = 0, task = 0, bias_mode = 0;
+    double delta = 0.1, sv_threshold = 0.0, bias_lambda = 0.0;
     double handover = 1e-4, inner = 1e-2;   // refinement schedule
     double t_rebuild = 0;                    // host ms spent rebuilding the round lists
     int64_t rebuilds = 0;
@@ -196,6 +196,9 @@ class Engine {
     {
         q_mode = o.q_mode;
         msg_bf16 = o.msg_bf16;
+        task = o.task;
+        bias_mode = o.bias_mode;
+        bias_lambda = o.bias_lambda;
         diag_rule = o.diag_rule;
         delta = o.diag_delta > 0 ? o.diag_delta : 0.1;
         x_f64 = o.x_dtype;
@@ -308,6 +311,7 @@ class Engine {
         p.sq = (const float*)take(pl.vec);
         p.y = (const float*)take(pl.vec);
         p.b = (const float*)take(pl.vec);
+        p.b0 = (const float*)take(pl.vec);
         p.qdiag = (float*)take(pl.vec);
         M.alpha = (float*)take(pl.vec);
         p.sqb = (const float*)take(pl.vec);
@@ -332,10 +336,12 @@ class Engine {
         p.ctrl = d_ctrl + slot;
         p.rhist = nullptr;
         p.rhist_cap = 0;
-        const double lam = 1.0 / (double)n;
+        // bias feature lambda (Section 3): 1/n for the SVM, off for KRR unless set
+        const double lam = bias_mode == 1 ? bias_lambda : (task == GABP_TASK_KRR ? 0.0 : 1.0 / (double)n);
         p.gamma = (float)pr.gamma;
         p.lam2 = (float)(lam * lam);
-        p.C = (float)pr.C;
+        p.C = (float)(task == GABP_TASK_KRR ? 1.0 / pr.C : pr.C);   // KRR: C is the ridge
+        p.task = task;
         M.ntiles = tri_tiles(p.Nt);
         M.nblk = (int)((n + 31) / 32);
         M.out_alpha = out_alpha;
@@ -364,7 +370,8 @@ class Engine {
                 EK(cudaMemcpyAsync(tmp, pr.X, (size_t)n * m * 8, cudaMemcpyHostToDevice, s));
                 src = tmp;
             }
-            launch_stage(src, x_f64, (int)n, (int)m, p.y, (float*)p.X, (float*)p.sq, (float*)p.b, p.ctrl, s);
+            launch_stage(src, x_f64, (int)n, (int)m, const_cast<float*>(p.y), (float*)p.X, (float*)p.sq,
+                         (float*)p.b, const_cast<float*>(p.b0), p.task, p.ctrl, s);
             ++launches;
             if (tmp) EK(cudaFreeAsync(tmp, s));
             M.staged = true;
@@ -756,8 +763,9 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
     if (opts) o = *opts;
     if (o.diag_delta == 0) o.diag_delta = 0.1;
     if (o.q_mode < 0 || o.q_mode > 2 || o.refine < 0 || o.refine > 64 || o.msg_bf16 < 0 || o.msg_bf16 > 1 ||
-        (o.msg_bf16 && o.q_mode == 0)) {
-        set_last_error("gabp_batch_solve: bad q_mode, refine or msg_bf16");
+        (o.msg_bf16 && o.q_mode == 0) || o.task < 0 || o.task > 1 ||
+        (o.bias_mode == 1 && (!(o.bias_lambda >= 0) || !std::isfinite(o.bias_lambda)))) {
+        set_last_error("gabp_batch_solve: bad q_mode, refine, msg_bf16, task or bias");
         return GABP_EINVAL;
     }
     long long tiles = 0, nblk = 0;
@@ -885,7 +893,8 @@ gabp_status gabp_server_create(const gabp_server_cfg* cfg, gabp_server_t* out)
     gabp_server_cfg c = *cfg;
     if (c.max_members <= 0) c.max_members = 64;
     if (c.max_members > 4096 || c.iters < 0 || std::isnan(c.tol) || c.opts.q_mode < 0 || c.opts.q_mode > 2 ||
-        (c.opts.msg_bf16 && c.opts.q_mode == 0)) {
+        (c.opts.msg_bf16 && c.opts.q_mode == 0) || c.opts.task < 0 || c.opts.task > 1 ||
+        (c.opts.bias_mode == 1 && (!(c.opts.bias_lambda >= 0) || !std::isfinite(c.opts.bias_lambda)))) {
         set_last_error("gabp_server_create: bad configuration");
         return GABP_EINVAL;
     }

@@ -70,7 +70,8 @@ struct Inst {
     const float* X;   // n x m FP32, row-major
     const float* sq;  // ||x_i||^2 of the FP32 rows
     const float* y;   // labels +-1
-    const float* b;   // right-hand side (ones for the SVM)
+    const float* b;   // working right-hand side (b0, or a refinement residual)
+    const float* b0;  // the problem's right-hand side: ones (SVM), the targets (KRR)
     float* qdiag;     // Q_ii
     void* Pst;        // ntiles * TT precision messages {P_ij, P_ji} (float2, or bf16x2 when msg_bf16)
     void* Hst;        // ntiles * TT information messages {H_ij, H_ji}
@@ -90,6 +91,7 @@ struct Inst {
     const float* sqb; // ||bf16(x_i)||^2
     int nkc;          // 64-feature chunks of Xp
     int msg_bf16;     // messages stored in BF16 (precision forms)
+    int task;         // 0 SVM (labels in Q, alpha clipped to [0, C]), 1 KRR (y = 1 in Q, alpha unclipped)
 };
 
 // Work of one round over a set of instances (device resident, so that a
@@ -132,9 +134,12 @@ struct GramSide {
 };
 
 // ---- launchers (defined in the .cu files) --------------------------------
-// Inputs: convert/validate X and y, row norms.  Returns nothing; errors go to ctrl->status.
-void launch_stage(const void* X, int x_f64, int n, int m, const float* y, float* Xf, float* sq,
-                  float* b, Ctrl* ctrl, cudaStream_t s);
+// Inputs: convert/validate X and y, row norms, right-hand sides.  SVM (task 0):
+// y must be +-1, b = b0 = 1.  KRR (task 1): y holds finite targets, which move
+// to b and b0, and y becomes 1 (no labels in Q).  y, b, b0 may be null (test
+// points).  Returns nothing; errors go to ctrl->status.
+void launch_stage(const void* X, int x_f64, int n, int m, float* y, float* Xf, float* sq,
+                  float* b, float* b0, int task, Ctrl* ctrl, cudaStream_t s);
 // Refinement schedule of the precision forms (0 selects the default): the
 // first solve hands over to the defect correction at ||r||_inf < handover, each
 // correction pass stops at inner * ||r||_inf of its right-hand side.

@@ -152,10 +152,10 @@ __device__ __forceinline__ void reduce_and_write(EpiSmem& es, float (&rs)[NQ][8]
 // One row: FP32 copy (from FP32 or FP64 input), squared norm, finiteness and
 // label checks, b_i = 1 (the SVM right-hand side: the linear term 1'h of the dual).
 __device__ __forceinline__ void stage_row(const void* __restrict__ X, int x_f64, int i, int m,
-                                          const float* __restrict__ y, float* __restrict__ Xf,
-                                          float* __restrict__ sq, float* __restrict__ b, Ctrl* ctrl)
+                                          float* __restrict__ y, float* __restrict__ Xf,
+                                          float* __restrict__ sq, float* __restrict__ b,
+                                          float* __restrict__ b0, int task, Ctrl* ctrl)
 {
-    if (b) b[i] = 1.f;
     float s = 0.f;
     bool ok = true;
     for (int k = 0; k < m; ++k) {
@@ -166,18 +166,28 @@ __device__ __forceinline__ void stage_row(const void* __restrict__ X, int x_f64,
         s = fmaf(v, v, s);
     }
     sq[i] = s;
+    float rhs = 1.f;   // SVM: Q alpha = 1 (Section 3)
     if (y) {
         const float yi = y[i];
-        ok &= (yi == 1.f || yi == -1.f);
+        if (task) {    // KRR: (K + lambda_r I) c = y (Section 1.2)
+            ok &= isfinite(yi);
+            rhs = yi;
+            y[i] = 1.f;
+        } else {
+            ok &= (yi == 1.f || yi == -1.f);
+        }
     }
+    if (b) b[i] = rhs;
+    if (b0) b0[i] = rhs;
     if (!ok && atomicCAS(&ctrl->status, 0, (int)ST_EINVAL) == 0) ctrl->bad_index = i;
 }
 
-__global__ void k_stage(const void* __restrict__ X, int x_f64, int n, int m, const float* __restrict__ y,
-                        float* __restrict__ Xf, float* __restrict__ sq, float* __restrict__ b, Ctrl* ctrl)
+__global__ void k_stage(const void* __restrict__ X, int x_f64, int n, int m, float* __restrict__ y,
+                        float* __restrict__ Xf, float* __restrict__ sq, float* __restrict__ b,
+                        float* __restrict__ b0, int task, Ctrl* ctrl)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) stage_row(X, x_f64, i, m, y, Xf, sq, b, ctrl);
+    if (i < n) stage_row(X, x_f64, i, m, y, Xf, sq, b, b0, task, ctrl);
 }
 
 // Listed node blocks of instances whose FP32 rows already sit in their X.
@@ -187,8 +197,8 @@ __global__ void k_stage_list(const Inst* __restrict__ tab, const int2* __restric
     const Inst& p = tab[nb.x];
     const int i = nb.y * 32 + threadIdx.x;
     if (threadIdx.x < 32 && i < p.n)
-        stage_row(p.X, 0, i, p.m, p.y, const_cast<float*>(p.X), const_cast<float*>(p.sq), const_cast<float*>(p.b),
-                  p.ctrl);
+        stage_row(p.X, 0, i, p.m, const_cast<float*>(p.y), const_cast<float*>(p.X), const_cast<float*>(p.sq),
+                  const_cast<float*>(p.b), const_cast<float*>(p.b0), p.task, p.ctrl);
 }
 
 // ------------------------------------------------------- Q tile formation
@@ -264,7 +274,7 @@ __device__ __forceinline__ void final_tile_sums(const Inst& p, const float* __re
         yj[b] = j < n ? p.y[j] : 0.f;
         sj[b] = j < n ? p.sq[j] : 0.f;
         mj[b] = j < n ? mu[j] : 0.f;
-        aj[b] = fminf(fmaxf(mj[b], 0.f), p.C);
+        aj[b] = p.task ? mj[b] : fminf(fmaxf(mj[b], 0.f), p.C);
     }
     float rs[2][8], cs[2][8];
 #pragma unroll
@@ -273,7 +283,7 @@ __device__ __forceinline__ void final_tile_sums(const Inst& p, const float* __re
     for (int a = 0; a < 8; ++a) {
         const int r = ty * 8 + a, i = I * T + r;
         const float yi = i < n ? p.y[i] : 0.f, si = i < n ? p.sq[i] : 0.f;
-        const float mi = i < n ? mu[i] : 0.f, ai = fminf(fmaxf(mi, 0.f), p.C);
+        const float mi = i < n ? mu[i] : 0.f, ai = p.task ? mi : fminf(fmaxf(mi, 0.f), p.C);
         float rm = 0.f, ra = 0.f;
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
@@ -332,10 +342,12 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_final_tiles_q(const Inst* __res
     final_tile_sums<true>(p, ops[w.x].mu, w.y, w.z, acc, es);
 }
 
-// Per node of a listed node block: r_i = 1 - Q_ii mu_i - sum part0,
+// Per node of a listed node block: r_i = b0_i - Q_ii mu_i - sum part0,
 // (Q alpha)_i = Q_ii alpha_i + sum part1; writes alpha (and r in FP32 when
-// requested); block partials {max |r_i|, sum alpha_i - 1/2 alpha_i (Q alpha)_i,
-// #SV} into the instance's block buffer.
+// requested); block partials {max |r_i|, sum b0_i alpha_i - 1/2 alpha_i
+// (Q alpha)_i, #SV} into the instance's block buffer.  SVM: b0 = 1, alpha =
+// clip(mu, 0, C), SV where alpha_i > threshold; KRR: b0 = the targets, alpha =
+// mu, counted where |alpha_i| > threshold.
 __global__ void __launch_bounds__(256) k_final_nodes(const Inst* __restrict__ tab,
                                                      const StopOp* __restrict__ ops,
                                                      const int2* __restrict__ nbl)
@@ -363,17 +375,17 @@ __global__ void __launch_bounds__(256) k_final_nodes(const Inst* __restrict__ ta
         if (x < n) {
             double a0 = 0.0, a1 = 0.0;
             for (int w = 0; w < 8; ++w) { a0 += red[0][w][lane]; a1 += red[1][w][lane]; }
-            const double qd = p.qdiag[x], m = mu[x];
-            const float af = fminf(fmaxf(mu[x], 0.f), p.C);
+            const double qd = p.qdiag[x], m = mu[x], bx = p.b0[x];
+            const float af = p.task ? mu[x] : fminf(fmaxf(mu[x], 0.f), p.C);
             const double al = af;
             op.alpha[x] = af;
-            const double r = 1.0 - qd * m - a0;   // residual of the SVM system Q mu = 1
+            const double r = bx - qd * m - a0;   // residual of the system Q mu = b0
             if (op.r_out) op.r_out[x] = (float)r;
             absr = fabs(r);
             if (!(absr <= DBL_MAX)) absr = INFINITY;
             const double qa = qd * al + a1;
-            obj = al - 0.5 * al * qa;
-            nsv = af > op.sv_threshold ? 1.0 : 0.0;
+            obj = bx * al - 0.5 * al * qa;
+            nsv = (p.task ? fabsf(af) : af) > op.sv_threshold ? 1.0 : 0.0;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -504,10 +516,10 @@ void launch_stage_list(const Inst* tab, const int2* nbl, int nblocks, cudaStream
     if (nblocks > 0) k_stage_list<<<nblocks, 32, 0, s>>>(tab, nbl);
 }
 
-void launch_stage(const void* X, int x_f64, int n, int m, const float* y, float* Xf, float* sq,
-                  float* b, Ctrl* ctrl, cudaStream_t s)
+void launch_stage(const void* X, int x_f64, int n, int m, float* y, float* Xf, float* sq,
+                  float* b, float* b0, int task, Ctrl* ctrl, cudaStream_t s)
 {
-    k_stage<<<(n + 255) / 256, 256, 0, s>>>(X, x_f64, n, m, y, Xf, sq, b, ctrl);
+    k_stage<<<(n + 255) / 256, 256, 0, s>>>(X, x_f64, n, m, y, Xf, sq, b, b0, task, ctrl);
 }
 
 void launch_form_q(const Inst* tab, const int4* work, long long ntiles, cudaStream_t s)

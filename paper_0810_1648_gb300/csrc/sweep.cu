@@ -1019,11 +1019,11 @@ __global__ void k_reset(Inst p)
         c->blocks_done = 0u;
     }
     if (x >= p.n) return;
-    const float qd = p.qdiag[x];
-    const_cast<float*>(p.b)[x] = 1.f;
+    const float qd = p.qdiag[x], bx = p.b0[x];
+    const_cast<float*>(p.b)[x] = bx;
     p.agg[x] = qd;
-    p.agg[p.npad + x] = 1.f;
-    p.agg[2 * p.npad + x] = 1.f / qd;
+    p.agg[p.npad + x] = bx;
+    p.agg[2 * p.npad + x] = bx / qd;
 }
 
 // Correction system Q d = r with the current P messages: b := r, the H

@@ -26,6 +26,7 @@ STATUS_NAMES = {0: "GABP_OK", 1: "GABP_EINVAL", 2: "GABP_ENOMEM", 3: "GABP_ECUDA
                 4: "GABP_ENUMERIC", 5: "GABP_ETIMEOUT", 6: "GABP_ESTATE"}
 Q_F32, Q_BF16, Q_RECOMPUTE = 0, 1, 2
 DIAG_DOMINANT, DIAG_SOFT2 = 0, 1
+TASK_SVM, TASK_KRR = 0, 1
 
 
 class GabpError(RuntimeError):
@@ -43,7 +44,7 @@ class Opts(ctypes.Structure):
                 ("refine", ctypes.c_int32), ("sv_threshold", ctypes.c_double),
                 ("chunk", ctypes.c_int32), ("msg_bf16", ctypes.c_int32),
                 ("refine_handover", ctypes.c_float), ("refine_inner", ctypes.c_float),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("task", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class Profile(ctypes.Structure):

@@ -18,6 +18,9 @@ generators stand in for them):
                       from {8, 32, 128, 256}, a C x gamma grid per data set.
 * ``poisson_requests`` arrival times and shapes of a stream of training
                       requests.
+* ``krr_targets``     real regression targets for the kernel ridge
+                      regression task: a smooth random function of the
+                      features plus noise.
 
 Labels are +-1, rows are shuffled, every draw comes from
 ``numpy.random.default_rng(seed)``.
@@ -32,12 +35,13 @@ import numpy as np
 
 @dataclasses.dataclass
 class Problem:
-    """One SVM training set plus its RBF width and box constant."""
+    """One training set plus its RBF width and box constant (for the
+    regression task: targets in y and the ridge in C)."""
 
     X: np.ndarray          # n x m, row-major
-    y: np.ndarray          # n, float32 with values +-1
+    y: np.ndarray          # n, float32: labels +-1 (SVM) or real targets (KRR)
     gamma: float           # RBF: K(a, b) = exp(-gamma * ||a - b||^2)
-    C: float               # box constant 0 <= alpha <= C
+    C: float               # box constant 0 <= alpha <= C (SVM) or ridge lambda_r (KRR)
     name: str = ""
 
     @property
@@ -157,3 +161,13 @@ def test_points(p: Problem, t: int, seed: int) -> np.ndarray:
     idx = rng.integers(0, p.n, size=t)
     Xt = p.X[idx].astype(np.float64) + 0.5 * rng.standard_normal((t, p.m))
     return Xt.astype(p.X.dtype)
+
+
+def krr_targets(p: Problem, seed: int, noise: float = 0.1) -> np.ndarray:
+    """Real targets t_i = sin(<w, x_i>) + noise * N(0, 1) with w ~ N(0, I/m):
+    a smooth function of the features for the regression task (float32)."""
+    rng = np.random.default_rng(seed)
+    X = np.asarray(p.X, dtype=np.float64)
+    w = rng.standard_normal(X.shape[1]) / math.sqrt(X.shape[1])
+    t = np.sin(X @ w) + noise * rng.standard_normal(X.shape[0])
+    return t.astype(np.float32)

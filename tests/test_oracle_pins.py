@@ -308,3 +308,66 @@ def test_boxqp_equals_clipped_gabp_when_inside_box():
         pytest.skip("optimum not inside the box for this draw")
     a, _ = oracle.boxqp_bruteforce(Q, C)
     np.testing.assert_allclose(a, r.alpha(C), rtol=1e-9, atol=1e-12)
+
+
+# ------------------------------------------------- kernel ridge regression task
+def _rbf(A, B, gamma):
+    from scipy.spatial.distance import cdist
+    return np.exp(-gamma * cdist(A, B, "sqeuclidean"))
+
+
+def test_krr_two_points_closed_form():
+    """Section 1.2 with two points: (K + l I) c = t solved by hand."""
+    X = np.array([[0.0, 0.0], [1.0, 2.0]])
+    gamma, ridge = 0.3, 0.7
+    k = np.exp(-gamma * 5.0)
+    t = np.array([0.4, -1.3])
+    det = (1 + ridge) ** 2 - k * k
+    c = np.array([((1 + ridge) * t[0] - k * t[1]) / det, ((1 + ridge) * t[1] - k * t[0]) / det])
+    Q, r = oracle.solve_krr(X, t, gamma, ridge, iters=5, tol=0.0, diag_rule=oracle.DIAG_SOFT2)
+    np.testing.assert_allclose(Q, [[1 + ridge, k], [k, 1 + ridge]], rtol=1e-15)
+    np.testing.assert_allclose(r.mu, c, rtol=1e-14)    # a tree: exact after one round
+
+
+@pytest.mark.parametrize("n,m,seed", [(40, 3, 1), (120, 8, 2)])
+def test_krr_fixed_point_is_ridge_solve(n, m, seed):
+    """With a ridge large enough for diagonal dominance, GaBP converges to
+    (K + ridge I)^-1 t, K from scipy's distances and the solve by LAPACK."""
+    p = workloads.mixture(n, m, seed=seed)
+    X = p.X.astype(np.float64)
+    t = workloads.krr_targets(p, seed + 10).astype(np.float64)
+    K = _rbf(X, X, p.gamma)
+    ridge = 1.2 * (K.sum(1) - 1).max()
+    ref = np.linalg.solve(K + ridge * np.eye(n), t)
+    Q, r = oracle.solve_krr(X, t, p.gamma, ridge, iters=3000, tol=1e-13, diag_rule=oracle.DIAG_SOFT2)
+    assert r.kstar < 3000
+    np.testing.assert_allclose(Q, K + ridge * np.eye(n), rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(r.mu, ref, rtol=1e-9, atol=1e-12)
+
+
+def test_krr_dominant_rule_keeps_kernel_and_solves_its_matrix():
+    """Dominant rule: the off-diagonal is the bare kernel (no labels, no bias),
+    the diagonal at least 1 + ridge, and GaBP reaches that matrix's solve."""
+    p = workloads.mixture(150, 6, seed=5)
+    X = p.X.astype(np.float64)
+    t = workloads.krr_targets(p, 6).astype(np.float64)
+    Q, r = oracle.solve_krr(X, t, p.gamma, 0.5, iters=3000, tol=1e-12)
+    off = ~np.eye(p.n, dtype=bool)
+    np.testing.assert_allclose(Q[off], _rbf(X, X, p.gamma)[off], rtol=1e-13)
+    assert np.all(np.diag(Q) >= 1.5 - 1e-12)
+    np.testing.assert_allclose(r.mu, np.linalg.solve(Q, t), rtol=1e-9, atol=1e-12)
+
+
+def test_krr_prediction_matches_section_1_2_formula():
+    """f(x) = t^T (K + l I)^-1 k(x) (Section 1.2) equals sum_i c_i K(x_i, x)
+    with the oracle's coefficients."""
+    p = workloads.mixture(60, 4, seed=8)
+    X = p.X.astype(np.float64)
+    t = workloads.krr_targets(p, 9).astype(np.float64)
+    K = _rbf(X, X, p.gamma)
+    ridge = 1.2 * (K.sum(1) - 1).max()
+    _, r = oracle.solve_krr(X, t, p.gamma, ridge, iters=3000, tol=1e-13, diag_rule=oracle.DIAG_SOFT2)
+    Xt = workloads.test_points(p, 25, seed=10).astype(np.float64)
+    f_ref = t @ np.linalg.solve(K + ridge * np.eye(p.n), _rbf(X, Xt, p.gamma))
+    f = oracle.decision(X, np.ones(p.n), r.mu, Xt, p.gamma, lam=0.0)
+    np.testing.assert_allclose(f, f_ref, rtol=1e-9, atol=1e-12)
