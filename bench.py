@@ -53,6 +53,7 @@ PRECISION_WORKLOAD = {
 # Stored bytes of one Q entry per unordered pair, by Q mode.
 Q_BYTES = {"f32": 4, "bf16": 2, "recompute": 0}
 Q_MODES = {"f32": 0, "bf16": 1, "recompute": 2}
+TASKS = {"svm": 0, "krr": 1}
 
 
 def _dist():
@@ -369,6 +370,11 @@ def run_ours(args):
     else:
         p = workloads.mixture(20000, 128, seed=1 + rank, gamma=1.0 / 128, C=10.0)
         wl = dict(WORKLOAD, q_mode=args.q_mode)
+    if args.task == "krr":
+        # kernel ridge regression on the same features: real targets, ridge 1
+        p = workloads.Problem(p.X, workloads.krr_targets(p, 11 + rank), p.gamma, 1.0, name="krr")
+        wl = dict(wl, task="krr", workload="kernel ridge regression (Section 1.2) on the same features: targets "
+                  "sin(<w, x>) + 0.1 N(0, 1) (w ~ N(0, I/m), seed 11), ridge 1, dominant diagonal; " + wl["workload"])
     qb = Q_BYTES[args.q_mode]
     mb = 4 if args.msg_bf16 else 8     # bytes of one stored message pair
     n = p.n
@@ -378,7 +384,7 @@ def run_ours(args):
     alpha_d = torch.empty(n, dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
     opts = gabp.opts_default(stream=stream.cuda_stream, chunk=ROUNDS, q_mode=Q_MODES[args.q_mode],
-                             msg_bf16=1 if args.msg_bf16 else 0)
+                             msg_bf16=1 if args.msg_bf16 else 0, task=TASKS[args.task])
     h = gabp.svm_create(Xd, yd, p.gamma, p.C, opts)
     gabp.svm_set_profiling(h, True)
 
@@ -452,9 +458,14 @@ def run_ours(args):
         e2e = _e2e(args, p, stream, dev, ws, gabp, torch)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = (_cpu_baseline(p, args.cpu_sweeps) if args.workload == "plain_large" else
-               {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
-                "sample": "skipped: the FP64 oracle of n=100000 needs 240 GB of host memory"})
+        if args.workload != "plain_large":
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
+                   "sample": "skipped: the FP64 oracle of n=100000 needs 240 GB of host memory"}
+        elif args.task != "svm":
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
+                   "sample": "skipped: the regression task runs the same oracle arithmetic as the default line"}
+        else:
+            cpu = _cpu_baseline(p, args.cpu_sweeps)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -479,6 +490,7 @@ def _e2e(args, p, stream, dev, ws, gabp, torch):
     yh = torch.from_numpy(p.y).pin_memory()
     ah = torch.empty(n, dtype=torch.float32).pin_memory()
     opts2 = gabp.opts_default(stream=stream.cuda_stream, chunk=ROUNDS, q_mode=Q_MODES[args.q_mode],
+                              task=TASKS[args.task],
                               msg_bf16=1 if args.msg_bf16 else 0)
     h2 = gabp.svm_create(Xh, yh, p.gamma, p.C, opts2)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -526,6 +538,8 @@ def main():
     ap.add_argument("--duration", type=float, default=60.0)
     ap.add_argument("--max-members", type=int, default=64)
     ap.add_argument("--msg-bf16", action="store_true", help="precision forms: BF16 message storage")
+    ap.add_argument("--task", default="svm", choices=list(TASKS),
+                    help="svm (default) or krr: kernel ridge regression on the same features and sweep")
     ap.add_argument("--q-mode", default=None, choices=list(Q_MODES))
     ap.add_argument("--profile-small", action="store_true",
                     help="one 8-round solve at n=--profile-n (for ncu captures), no JSON bench line")
