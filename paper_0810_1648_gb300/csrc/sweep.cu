@@ -44,7 +44,7 @@ __device__ __forceinline__ void consumer_bar() { asm volatile("bar.sync 1, %0;" 
 // Persistent CTAs walk the tile list with stride gridDim.x.  A producer warp
 // publishes each tile's parameters and bulk-copies its row and column
 // aggregates into a double-buffered tile slot, then streams the tile as
-// chunks of RC rows of messages (and, when Q is stored, of Q) into a
+// chunks of rc<MSG>() rows of messages (and, when Q is stored, of Q) into a
 // STAGES-deep shared-memory ring, running ahead across tile boundaries; the
 // consumers follow the tiles it publishes.  Eight consumer warps take one row
 // of each chunk, update its pairs from shared memory and store the new
@@ -61,7 +61,9 @@ __device__ __forceinline__ void consumer_bar() { asm volatile("bar.sync 1, %0;" 
 //                 turn the Gram rows into BF16 Q values in a double-buffered
 //                 shared-memory Q tile, which the consumers read in place of
 //                 a stored tile (bitwise the same values as the BF16 store).
-constexpr int RC = NWARPS;                    // rows per chunk, one per consumer warp
+// Rows per ring stage: MSG::RPW per consumer warp (rc<MSG>() in total).
+template <class MSG>
+__host__ __device__ constexpr int rc() { return NWARPS * MSG::RPW; }
 constexpr int STAGES = 4;
 constexpr int SWEEP_THREADS = NTHREADS + 32;  // + one producer warp
 // Message storage: FP32 pairs (plain and precision forms) or BF16 pairs
@@ -76,6 +78,7 @@ struct MsgF32 {
     // a lane's pairs of a row: columns 2 lane + {0, 1} and 64 + 2 lane + {0, 1}
     // (each access of the warp is one contiguous 512-byte span)
     static constexpr int G = 2;
+    static constexpr int RPW = 1;   // rows per consumer warp and ring stage
     static __device__ __forceinline__ void load4(const T2* row, int lane, T2 (&v)[4])
     {
         const float4 a = *reinterpret_cast<const float4*>(row + 2 * lane);
@@ -104,6 +107,7 @@ struct MsgBF16 {
     // a lane's pairs of a row: columns 4 lane + {0 .. 3} (16 bytes; each
     // access of the warp is one contiguous 512-byte span)
     static constexpr int G = 4;
+    static constexpr int RPW = 2;   // rows per consumer warp and ring stage (halves the per-row overhead)
     static __device__ __forceinline__ void load4(const T2* row, int lane, T2 (&v)[4])
     {
         const uint4 u = *reinterpret_cast<const uint4*>(row + 4 * lane);
@@ -116,7 +120,7 @@ struct MsgBF16 {
 };
 
 template <class MSG>
-__host__ __device__ constexpr size_t pchunk() { return (size_t)RC * T * sizeof(typename MSG::T2); }
+__host__ __device__ constexpr size_t pchunk() { return (size_t)rc<MSG>() * T * sizeof(typename MSG::T2); }
 
 // Resident sweep CTAs per SM: two for both message types (three for the
 // BF16-message kernel spilled registers and ran slower than two).
@@ -161,14 +165,14 @@ __device__ __forceinline__ void init_tail(SweepTail& sm)
     sm.cabort = 0;
 }
 
-// Ring stage = P messages of RC rows, their H messages, then (stored Q) their Q values.
+// Ring stage = P messages of rc<MSG>() rows, their H messages, then (stored Q) their Q values.
 template <typename QT>
 struct QBytes { static constexpr size_t v = sizeof(QT); };
 template <>
 struct QBytes<void> { static constexpr size_t v = 0; };
 
 template <typename QT, class MSG>
-__host__ __device__ constexpr size_t stage_bytes() { return state_chunk<MSG>() + (size_t)RC * T * QBytes<QT>::v; }
+__host__ __device__ constexpr size_t stage_bytes() { return state_chunk<MSG>() + (size_t)rc<MSG>() * T * QBytes<QT>::v; }
 
 template <typename QT, class MSG>
 __host__ __device__ constexpr size_t sweep_smem_bytes()
@@ -179,7 +183,7 @@ __host__ __device__ constexpr size_t sweep_smem_bytes()
 // Producer (one warp).  For every tile it streams: publishes the tile's
 // parameters and bulk-copies its row and column aggregates into the tile slot,
 // then streams the message (and stored Q) rows through the stage ring.
-// Interior tiles move RC whole rows per copy; diagonal and edge tiles copy each
+// Interior tiles move rc<MSG>() whole rows per copy; diagonal and edge tiles copy each
 // row's needed span, one row per lane.  QT = void: messages only.
 template <typename QT, class MSG, size_t SB>
 __device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, const int4* __restrict__ work,
@@ -237,6 +241,7 @@ __device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, con
         }
         if (++slot == 2) { slot = 0; tph ^= 1u; }
         // message / Q rows
+        constexpr int RC = rc<MSG>();
         const int nch = (rows + RC - 1) / RC;
         for (int c = 0; c < nch; ++c) {
             if (stopped() || !mbar_wait_warp(&sm.empty[stage], phase ^ 1u)) {
@@ -364,6 +369,30 @@ __device__ __forceinline__ float reduce_scatter4(float a, float b, float c, int 
     return v;
 }
 
+// Sums the eight values {a0, a1, a2, 0, b0, b1, b2, 0} over the warp in a
+// fixed order: afterwards every lane of the group (lane / 4) % 8 = k holds the
+// total of value k (nine shuffles for two rows).
+__device__ __forceinline__ float reduce_scatter8(float a0, float a1, float a2, float b0, float b1, float b2,
+                                                 int lane)
+{
+    const float x[8] = {a0, a1, a2, 0.f, b0, b1, b2, 0.f};
+    const bool hi = (lane & 16) != 0;
+    float y[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        y[k] = (hi ? x[k + 4] : x[k]) + __shfl_xor_sync(0xffffffffu, hi ? x[k] : x[k + 4], 16);
+    const bool b8 = (lane & 8) != 0;
+    float z[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+        z[k] = (b8 ? y[k + 2] : y[k]) + __shfl_xor_sync(0xffffffffu, b8 ? y[k] : y[k + 2], 8);
+    const bool b4 = (lane & 4) != 0;
+    float v = (b4 ? z[1] : z[0]) + __shfl_xor_sync(0xffffffffu, b4 ? z[0] : z[1], 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v;
+}
+
 // Per-tile column values a consumer lane needs for its row updates.
 struct ColVals {
     float P[4], H[4], M[4];      // aggregates of the lane's four columns
@@ -377,17 +406,17 @@ struct ColVals {
 // residual).  Whole 4-pair groups are stored: on diagonal and edge tiles the
 // slots outside the pair set are never read, so writing them is harmless.
 template <bool FULL, bool FROZEN, class MSG, class QSrc>
-__device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char* S, int cw, int lane, int r,
+__device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char* S, int lr, int lane, int r,
                                            int cols, bool diag, int it, bool zero, bool zero_h, float rP,
                                            float rH, float rM, ColVals& cv, typename MSG::T2* __restrict__ gp,
                                            typename MSG::T2* __restrict__ gh, float (&rs)[3], bool& bad,
                                            bool& changed)
 {
     using T2 = typename MSG::T2;
-    const T2* Sp = reinterpret_cast<const T2*>(S) + (size_t)cw * T;
-    const T2* Sh = reinterpret_cast<const T2*>(S + pchunk<MSG>()) + (size_t)cw * T;
+    const T2* Sp = reinterpret_cast<const T2*>(S) + (size_t)lr * T;
+    const T2* Sh = reinterpret_cast<const T2*>(S + pchunk<MSG>()) + (size_t)lr * T;
     float q[4];
-    qsrc.template q4<MSG::G>(S, cw, r, lane, it, q);
+    qsrc.template q4<MSG::G>(S, lr, r, lane, it, q);
     bool v[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -498,28 +527,40 @@ __device__ __forceinline__ void consume_tile(const QSrc& qsrc, SweepTail& sm, co
     if (!FROZEN) ld4<G>(tc.ag[3], lane, cv.P);
 #pragma unroll
     for (int k = 0; k < 4; ++k) cv.aP[k] = cv.aH[k] = cv.aR[k] = 0.f;
+    constexpr int RC = rc<MSG>(), RPW = MSG::RPW;
     const int nch = (rows + RC - 1) / RC;
-    const int qv = lane >> 3;   // quantity this lane holds after the row reduction
-    float* rdst = qv == 0 ? sm.rp : (qv == 1 ? sm.rh : sm.rr);
 #pragma unroll 1
     for (int ch = 0; ch < nch; ++ch) {
         if (!abort && !mbar_wait_warp(&sm.full[stage], phase)) {
             abort = true;
             if (lane == 0) record_error(tc.ctrl, ST_ETIMEOUT, tc.L);
         }
-        const int r = ch * RC + cw;
-        float rs[3] = {0.f, 0.f, 0.f};
-        if (!abort && r < rows) {
-            const unsigned char* S = ring + (size_t)stage * SB;
-            update_row<FULL, FROZEN, MSG>(qsrc, S, cw, lane, r, tc.cols, tc.diag, tc.it, tc.zero, tc.zero_h,
-                                          tc.ag[0][r], tc.ag[1][r], tc.ag[2][r], cv, gp, gh, rs, bad, changed);
+        // this warp's rows of the stage: cw, cw + NWARPS, ...
+        float rs[RPW][3];
+#pragma unroll
+        for (int u = 0; u < RPW; ++u) {
+            const int lr = cw + NWARPS * u, r = ch * RC + lr;
+            rs[u][0] = rs[u][1] = rs[u][2] = 0.f;
+            if (!abort && r < rows) {
+                const unsigned char* S = ring + (size_t)stage * SB;
+                update_row<FULL, FROZEN, MSG>(qsrc, S, lr, lane, r, tc.cols, tc.diag, tc.it, tc.zero, tc.zero_h,
+                                              tc.ag[0][r], tc.ag[1][r], tc.ag[2][r], cv, gp, gh, rs[u], bad,
+                                              changed);
+            }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.empty[stage]);
         if (++stage == STAGES) { stage = 0; phase ^= 1u; }
-        // row sums of row r: {P, H, R} over the warp, quantity lane / 8
-        const float v = reduce_scatter4(rs[0], rs[1], rs[2], lane);
-        if ((lane & 7) == 0 && qv < 3 && r < rows) rdst[r] = v;
+        // row sums {P, H, R} of the warp's rows over the warp
+        if constexpr (RPW == 1) {
+            const float v = reduce_scatter4(rs[0][0], rs[0][1], rs[0][2], lane);
+            const int qv = lane >> 3, r = ch * RC + cw;
+            if ((lane & 7) == 0 && qv < 3 && r < rows) (qv == 0 ? sm.rp : (qv == 1 ? sm.rh : sm.rr))[r] = v;
+        } else {
+            const float v = reduce_scatter8(rs[0][0], rs[0][1], rs[0][2], rs[1][0], rs[1][1], rs[1][2], lane);
+            const int qi = (lane >> 2) & 7, qv = qi & 3, r = ch * RC + cw + NWARPS * (qi >> 2);
+            if ((lane & 3) == 0 && qv < 3 && r < rows) (qv == 0 ? sm.rp : (qv == 1 ? sm.rh : sm.rr))[r] = v;
+        }
     }
     if (!FROZEN) st4<G>(sm.cp[cw], lane, cv.aP);
     st4<G>(sm.ch[cw], lane, cv.aH);
