@@ -19,10 +19,10 @@
 // 4 B of Q (2 B in BF16) and writes 16 B; once the P messages sit at their
 // fixed point it writes only the 8 B of H (messages stored in BF16 halve the
 // message bytes).  Messages and Q arrive in shared memory through bulk copies
-// issued by a producer warp well ahead of use; consumer warp w takes one row
-// of each 8-row chunk, each lane four of its columns laid out so that every
-// warp access to a row is one contiguous 512-byte span (lane_col).  Row sums
-// go through one warp reduction per row, column sums stay in registers and
+// issued by a producer warp well ahead of use; consumer warp w takes rows w
+// and w + 8 of each 16-row chunk, each lane four of their columns laid out so
+// that every warp access to a row is one contiguous 512-byte span (lane_col).
+// Row sums go through one warp reduction per two rows, column sums stay in registers and
 // meet in shared memory, and each node's per-tile sums go to its own slot
 // (common.cuh), so the reduction order is fixed and the result reproducible.
 #include "common.cuh"
@@ -45,9 +45,9 @@ __device__ __forceinline__ void consumer_bar() { asm volatile("bar.sync 1, %0;" 
 // publishes each tile's parameters and bulk-copies its row and column
 // aggregates into a double-buffered tile slot, then streams the tile as
 // chunks of rc<MSG>() rows of messages (and, when Q is stored, of Q) into a
-// STAGES-deep shared-memory ring, running ahead across tile boundaries; the
-// consumers follow the tiles it publishes.  Eight consumer warps take one row
-// of each chunk, update its pairs from shared memory and store the new
+// stages<MSG>()-deep shared-memory ring, running ahead across tile boundaries;
+// the consumers follow the tiles it publishes.  Eight consumer warps take two
+// rows of each chunk, update their pairs from shared memory and store the new
 // messages straight to global memory with 128-bit streaming stores.  Only the
 // pairs the tile owns are copied: whole chunks for interior tiles, the c > r
 // part of each row on diagonal tiles, the first `cols` columns on the last
@@ -64,7 +64,10 @@ __device__ __forceinline__ void consumer_bar() { asm volatile("bar.sync 1, %0;" 
 // Rows per ring stage: MSG::RPW per consumer warp (rc<MSG>() in total).
 template <class MSG>
 __host__ __device__ constexpr int rc() { return NWARPS * MSG::RPW; }
-constexpr int STAGES = 4;
+constexpr int STAGES = 4;                     // barrier slots of the stage ring (upper bound)
+// Ring stages used by a message type (both keep ~80 KB of rows in flight).
+template <class MSG>
+__host__ __device__ constexpr int stages() { return MSG::NSTAGE; }
 constexpr int SWEEP_THREADS = NTHREADS + 32;  // + one producer warp
 // Message storage: FP32 pairs (plain and precision forms) or BF16 pairs
 // (precision forms with refinement).  Arithmetic is FP32 either way; sums use
@@ -78,7 +81,8 @@ struct MsgF32 {
     // a lane's pairs of a row: columns 2 lane + {0, 1} and 64 + 2 lane + {0, 1}
     // (each access of the warp is one contiguous 512-byte span)
     static constexpr int G = 2;
-    static constexpr int RPW = 1;   // rows per consumer warp and ring stage
+    static constexpr int RPW = 2;      // rows per consumer warp and ring stage
+    static constexpr int NSTAGE = 2;   // ring stages of 16 rows (40 KB with FP32 Q)
     static __device__ __forceinline__ void load4(const T2* row, int lane, T2 (&v)[4])
     {
         const float4 a = *reinterpret_cast<const float4*>(row + 2 * lane);
@@ -107,7 +111,8 @@ struct MsgBF16 {
     // a lane's pairs of a row: columns 4 lane + {0 .. 3} (16 bytes; each
     // access of the warp is one contiguous 512-byte span)
     static constexpr int G = 4;
-    static constexpr int RPW = 2;   // rows per consumer warp and ring stage (halves the per-row overhead)
+    static constexpr int RPW = 2;      // rows per consumer warp and ring stage (halves the per-row overhead)
+    static constexpr int NSTAGE = 4;   // ring stages of 16 rows (20 KB with BF16 Q)
     static __device__ __forceinline__ void load4(const T2* row, int lane, T2 (&v)[4])
     {
         const uint4 u = *reinterpret_cast<const uint4*>(row + 4 * lane);
@@ -177,7 +182,7 @@ __host__ __device__ constexpr size_t stage_bytes() { return state_chunk<MSG>() +
 template <typename QT, class MSG>
 __host__ __device__ constexpr size_t sweep_smem_bytes()
 {
-    return 128 + STAGES * stage_bytes<QT, MSG>() + sizeof(SweepTail);
+    return 128 + stages<MSG>() * stage_bytes<QT, MSG>() + sizeof(SweepTail);
 }
 
 // Producer (one warp).  For every tile it streams: publishes the tile's
@@ -284,7 +289,7 @@ __device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, con
                     }
                 }
             }
-            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+            if (++stage == stages<MSG>()) { stage = 0; phase ^= 1u; }
         }
     }
     // end of this CTA's tiles
@@ -550,7 +555,7 @@ __device__ __forceinline__ void consume_tile(const QSrc& qsrc, SweepTail& sm, co
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.empty[stage]);
-        if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        if (++stage == stages<MSG>()) { stage = 0; phase ^= 1u; }
         // row sums {P, H, R} of the warp's rows over the warp
         if constexpr (RPW == 1) {
             const float v = reduce_scatter4(rs[0][0], rs[0][1], rs[0][2], lane);
@@ -690,7 +695,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, sweep_ctas<MSG>())
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* ring = align_smem(smem_raw, 128);
-    SweepTail& sm = *reinterpret_cast<SweepTail*>(ring + STAGES * SB);
+    SweepTail& sm = *reinterpret_cast<SweepTail*>(ring + stages<MSG>() * SB);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
@@ -724,7 +729,7 @@ struct RcExtra {
 template <class MSG>
 __host__ __device__ constexpr size_t rc_smem_bytes()
 {
-    return 1024 + STAGES * state_chunk<MSG>() + RC_XSTAGES * 2 * BLK_BYTES + 2 * RC_QTILE + sizeof(SweepTail) +
+    return 1024 + stages<MSG>() * state_chunk<MSG>() + RC_XSTAGES * 2 * BLK_BYTES + 2 * RC_QTILE + sizeof(SweepTail) +
            sizeof(RcExtra);
 }
 
@@ -755,7 +760,7 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* ring = align_smem(smem_raw, 1024);
-    unsigned char* xops = ring + STAGES * state_chunk<MSG>();                // [2][A, B]
+    unsigned char* xops = ring + stages<MSG>() * state_chunk<MSG>();                // [2][A, B]
     __nv_bfloat16* qtile = reinterpret_cast<__nv_bfloat16*>(xops + RC_XSTAGES * 2 * BLK_BYTES);
     SweepTail& sm = *reinterpret_cast<SweepTail*>(reinterpret_cast<unsigned char*>(qtile) + 2 * RC_QTILE);
     RcExtra& ex = *reinterpret_cast<RcExtra*>(reinterpret_cast<unsigned char*>(&sm) + sizeof(SweepTail));
