@@ -68,6 +68,8 @@ def _load():
         "orc_build_q": (i32, [D, D, L, L, f64, f64, f64, i32, f64, D]),
         "orc_gabp_info": (i32, [D, D, L, i32, f64, D, D, I, D, D, D, D]),
         "orc_gabp_literal": (i32, [D, D, L, i32, D, D]),
+        "orc_gabp_staged": (i32, [D, D, L, i32, f64, i32, L, D, D, I, D, D, D, D]),
+        "orc_stage_bounds": (None, [L, i32, ctypes.POINTER(ctypes.c_long)]),
         "orc_gabp_alg1": (i32, [D, D, L, i32, D, D]),
         "orc_pair_update": (None, [f64, f64, f64, f64, f64, D, D]),
         "orc_cholesky_solve": (i32, [D, D, L, D]),
@@ -307,3 +309,31 @@ def solve_krr(X, t, gamma, ridge, iters=200, tol=1e-6, lam=0.0,
     the prediction is f(x) = sum_i c_i (K(x_i, x) + lam^2)."""
     Q = build_q_krr(X, gamma, ridge, lam, diag_rule, delta)
     return Q, gabp(Q, np.asarray(t, dtype=np.float64), iters, tol)
+
+
+def stage_bounds(nt: int, stages: int):
+    """Block boundaries B[0..S] of the staged schedule (see gabp_oracle.c)."""
+    B = (ctypes.c_long * (stages + 1))()
+    _load().orc_stage_bounds(int(nt), int(stages), B)
+    return list(B)
+
+
+def gabp_staged(Q, b=None, iters=100, tol=0.0, stages=2, block=128, keep_messages=False):
+    """Algorithm 2 under the block Gauss-Seidel schedule (stages = 1: synchronous)."""
+    Q, pq = _d(Q)
+    n = Q.shape[0]
+    b = np.ones(n) if b is None else b
+    b, pb = _d(b)
+    mu, Pt = np.empty(n), np.empty(n)
+    rhist = np.full(iters + 1, np.nan)
+    k = ctypes.c_int(0)
+    rinf = ctypes.c_double(0)
+    Pin = np.empty((n, n)) if keep_messages else None
+    Hin = np.empty((n, n)) if keep_messages else None
+    P = ctypes.POINTER(ctypes.c_double)
+    rc = _load().orc_gabp_staged(
+        pq, pb, n, int(iters), float(tol), int(stages), int(block), mu.ctypes.data_as(P), Pt.ctypes.data_as(P),
+        ctypes.byref(k), ctypes.byref(rinf), rhist.ctypes.data_as(P),
+        Pin.ctypes.data_as(P) if keep_messages else None, Hin.ctypes.data_as(P) if keep_messages else None)
+    _check(rc, "gabp_staged")
+    return GabpResult(mu, Pt, k.value, rinf.value, rhist[:k.value + 1], Pin, Hin)

@@ -223,6 +223,118 @@ done:
 }
 
 /*
+ * Stage boundaries of the block Gauss-Seidel schedule below: nodes form
+ * blocks of `block` consecutive indices (Nt blocks); B[0] = 0, B[S] = Nt and
+ * B[s] is the smallest b with S * b (b + 1) / 2 >= s * Nt (Nt + 1) / 2, so
+ * that the stages hold about equal numbers of block pairs (J, I <= J).
+ */
+void orc_stage_bounds(long Nt, int S, long* B)
+{
+    const long tot = Nt * (Nt + 1) / 2;
+    B[0] = 0;
+    for (int s = 1; s < S; ++s) {
+        long b = B[s - 1];
+        while (b < Nt && (long)S * (b * (b + 1) / 2) < (long)s * tot) ++b;
+        B[s] = b;
+    }
+    B[S] = Nt;
+}
+
+/*
+ * Algorithm 2 under a block Gauss-Seidel schedule.  Section 3.2 shows that
+ * GaBP also converges when messages are not all updated together, and the
+ * paper names asynchronous schedules as the faster ones.  Here one round still
+ * updates every pair exactly once, in S stages: with node blocks as in
+ * orc_stage_bounds, the pair {i < j} is updated in the stage whose range
+ * [B[s], B[s+1]) holds the block of j.  A stage updates its pairs from the
+ * current aggregates (Step 2, information form as in orc_gabp_info), and the
+ * aggregates are formed again from all messages before the next stage, so
+ * later stages see the messages of earlier ones.  The residual test of Step 3
+ * is taken at the start of every round, on the aggregates of all messages.
+ * S = 1 is the synchronous schedule of orc_gabp_info.  Arguments and outputs
+ * as for orc_gabp_info.
+ */
+int orc_gabp_staged(const double* Q, const double* b, long n, int iters, double tol, int S, long block,
+                    double* mu, double* Pt_out, int* kstar, double* rinf, double* rhist,
+                    double* Pin_io, double* Hin_io)
+{
+    if (n < 1 || iters < 0 || S < 1 || block < 1) return ORC_EINVAL;
+    const long Nt = (n + block - 1) / block;
+    size_t nn = (size_t)n * (size_t)n;
+    double* Pin = Pin_io ? Pin_io : (double*)malloc(nn * sizeof(double));
+    double* Hin = Hin_io ? Hin_io : (double*)malloc(nn * sizeof(double));
+    double* Pt = (double*)malloc((size_t)n * sizeof(double));
+    double* ht = (double*)malloc((size_t)n * sizeof(double));
+    long* B = (long*)malloc((size_t)(S + 1) * sizeof(long));
+    int rc = ORC_OK;
+    if (!Pin || !Hin || !Pt || !ht || !B) { rc = ORC_ENOMEM; goto done; }
+    memset(Pin, 0, nn * sizeof(double));
+    memset(Hin, 0, nn * sizeof(double));
+    orc_stage_bounds(Nt, S, B);
+
+    for (int t = 0;; ++t) {
+        /* aggregates of all messages (Step 2) and the residual test (Step 3) */
+        for (long i = 0; i < n; ++i) {
+            double P = Q[i * n + i], h = b[i];
+            for (long k = 0; k < n; ++k) {
+                if (k == i) continue;
+                P += Pin[i * n + k];
+                h += Hin[i * n + k];
+            }
+            Pt[i] = P;
+            ht[i] = h;
+            mu[i] = h / P;
+        }
+        double rn = residual(Q, b, mu, n, NULL);
+        if (rhist) rhist[t] = rn;
+        if (rn < tol || t == iters) {
+            *kstar = t;
+            *rinf = rn;
+            break;
+        }
+        int bad = 0;
+        for (int s = 0; s < S; ++s) {
+            const long j0 = B[s] * block, j1 = B[s + 1] * block < n ? B[s + 1] * block : n;
+            /* the pairs {i < j} with j in this stage's blocks */
+            for (long j = j0; j < j1; ++j) {
+                for (long i = 0; i < j; ++i) {
+                    double q = Q[i * n + j];
+                    double P_ij = Pin[j * n + i], P_ji = Pin[i * n + j];
+                    double H_ij = Hin[j * n + i], H_ji = Hin[i * n + j];
+                    double di = Pt[i] - P_ji;
+                    double dj = Pt[j] - P_ij;
+                    if (!(di > 0.0) || !(dj > 0.0) || !isfinite(di) || !isfinite(dj)) bad = 1;
+                    Pin[j * n + i] = -q * q / di;
+                    Hin[j * n + i] = -q * (ht[i] - H_ji) / di;
+                    Pin[i * n + j] = -q * q / dj;
+                    Hin[i * n + j] = -q * (ht[j] - H_ij) / dj;
+                }
+            }
+            /* aggregates again, for the next stage */
+            for (long i = 0; i < n; ++i) {
+                double P = Q[i * n + i], h = b[i];
+                for (long k = 0; k < n; ++k) {
+                    if (k == i) continue;
+                    P += Pin[i * n + k];
+                    h += Hin[i * n + k];
+                }
+                Pt[i] = P;
+                ht[i] = h;
+            }
+        }
+        if (bad) { rc = ORC_ENUMERIC; *kstar = t; *rinf = rn; break; }
+    }
+    if (Pt_out) memcpy(Pt_out, Pt, (size_t)n * sizeof(double));
+done:
+    if (!Pin_io) free(Pin);
+    if (!Hin_io) free(Hin);
+    free(Pt);
+    free(ht);
+    free(B);
+    return rc;
+}
+
+/*
  * Algorithm 2 exactly as printed, with the message means mu_ij as state:
  *   mu_ij <- (Ptilde_i mutilde_i - P_ji mu_ji) / Q_ij.
  * Only pairs with Q_ij != 0 are neighbours (Step 1).  Runs `iters` updates

@@ -125,3 +125,32 @@ def test_batch_bf16_messages_refined():
         ref = np.linalg.solve(Qx, np.ones(p.n))
         assert r["residual_inf"] < 1e-6 and r["converged"] == 1
         assert np.max(np.abs(a - np.clip(ref, 0, p.C))) <= 1e-4 * p.C
+
+
+def test_server_krr_and_phases():
+    """The regression task through the server equals the single solve, and the
+    server reports its phase times."""
+    srv = gabp.Server(iters=300, tol=1e-6, max_members=3, chunk=4, task=gabp.TASK_KRR)
+    probs, tickets = [], []
+    for k, (n, m) in enumerate([(200, 8), (350, 16), (500, 32), (260, 8)]):
+        p = workloads.mixture(n, m, seed=70 + k)
+        t = workloads.krr_targets(p, 80 + k)
+        probs.append((p, t))
+        tickets.append(srv.submit(p.X, t, p.gamma, 0.5))
+    out = {}
+    for _ in range(2000):
+        srv.step()
+        for t in srv.completed():
+            out[t] = srv.poll(t)
+        if len(out) == len(tickets):
+            break
+    assert len(out) == len(tickets)
+    ph = srv.phases()
+    assert ph["steps"] >= 1 and ph["total_ms"] > 0 and ph["rounds_ms"] > 0
+    assert all(ph[k] >= 0 for k in ph)
+    for t, (p, tg) in zip(tickets, probs):
+        a, r = out[t]
+        assert r["status"] == 0 and r["converged"] == 1
+        single, _, _ = gabp.GabpSVM(p.X, tg, p.gamma, 0.5, task=gabp.TASK_KRR, chunk=4).solve(300, 1e-6)
+        np.testing.assert_array_equal(a, single)
+    srv.close()

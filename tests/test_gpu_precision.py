@@ -144,3 +144,19 @@ def test_bf16_messages_rejected_for_plain_form():
     with pytest.raises(gabp.GabpError) as ei:
         gabp.GabpSVM(p.X, p.y, p.gamma, p.C, msg_bf16=1)
     assert ei.value.status == gabp.EINVAL
+
+
+@pytest.mark.parametrize("handover,inner", [(1e-2, 1e-2), (1e-5, 3e-3)])
+def test_refinement_schedule_options_keep_the_bars(handover, inner):
+    """The refinement thresholds are options; any schedule still ends at the
+    FP64 fixed point within the FP32 bars (only the round count changes)."""
+    p = workloads.mixture(600, 24, seed=95, C=1.0)
+    s = gabp.GabpSVM(p.X, p.y, p.gamma, p.C, q_mode=gabp.Q_BF16, refine=12, msg_bf16=1,
+                     refine_handover=handover, refine_inner=inner)
+    alpha, rinf, k = s.solve(400, 1e-6)
+    Qx = oracle.build_q(p.X.astype(np.float64), p.y.astype(np.float64), p.gamma, p.C)
+    ref = np.linalg.solve(Qx, np.ones(p.n))
+    mu = s.mean().astype(np.float64)
+    assert np.max(np.abs(mu - ref)) / np.max(np.abs(ref)) <= 2e-5
+    assert np.max(np.abs(alpha.astype(np.float64) - np.clip(ref, 0, p.C))) <= 1e-4 * p.C
+    assert rinf < 1e-6 and s.stats()["converged"] == 1

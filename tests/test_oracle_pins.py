@@ -371,3 +371,53 @@ def test_krr_prediction_matches_section_1_2_formula():
     f_ref = t @ np.linalg.solve(K + ridge * np.eye(p.n), _rbf(X, Xt, p.gamma))
     f = oracle.decision(X, np.ones(p.n), r.mu, Xt, p.gamma, lam=0.0)
     np.testing.assert_allclose(f, f_ref, rtol=1e-9, atol=1e-12)
+
+
+# ------------------------------------------- block Gauss-Seidel (staged) schedule
+def test_stage_bounds_balance_block_pairs():
+    for nt, s in [(157, 4), (32, 2), (3, 4), (1, 2), (782, 8)]:
+        B = oracle.stage_bounds(nt, s)
+        assert B[0] == 0 and B[-1] == nt and all(B[k] <= B[k + 1] for k in range(s))
+        tot = nt * (nt + 1) // 2
+        for k in range(1, s):
+            b = B[k]
+            assert s * (b * (b + 1) // 2) >= k * tot                      # reaches its share ...
+            assert b == 0 or s * ((b - 1) * b // 2) < k * tot             # ... and no earlier block does
+
+
+@pytest.mark.parametrize("n,seed", [(17, 2), (64, 3), (130, 4)])
+def test_staged_one_stage_is_the_synchronous_schedule(n, seed):
+    Q = _dd_matrix(n, seed)
+    b = np.random.default_rng(seed).standard_normal(n)
+    for iters in (0, 1, 5):
+        r1 = oracle.gabp(Q, b, iters=iters)
+        r2 = oracle.gabp_staged(Q, b, iters=iters, stages=1, block=8)
+        np.testing.assert_array_equal(r1.mu, r2.mu)
+        np.testing.assert_array_equal(r1.Pt, r2.Pt)
+    # a single block puts every pair in one stage, whatever the stage count
+    r3 = oracle.gabp_staged(Q, b, iters=4, stages=4, block=n)
+    np.testing.assert_array_equal(oracle.gabp(Q, b, iters=4).mu, r3.mu)
+
+
+@pytest.mark.parametrize("n,seed,stages,block", [(64, 3, 2, 8), (130, 4, 4, 16), (200, 5, 8, 8)])
+def test_staged_fixed_point_is_linear_solve(n, seed, stages, block):
+    Q = _dd_matrix(n, seed)
+    b = np.random.default_rng(seed + 1).standard_normal(n)
+    r = oracle.gabp_staged(Q, b, iters=2000, tol=1e-13, stages=stages, block=block)
+    assert r.kstar < 2000
+    np.testing.assert_allclose(r.mu, np.linalg.solve(Q, b), rtol=1e-10, atol=1e-12)
+    # the invariants of the synchronous schedule hold too
+    r2 = oracle.gabp_staged(Q, 3.0 * b, iters=7, stages=stages, block=block)
+    r1 = oracle.gabp_staged(Q, b, iters=7, stages=stages, block=block)
+    np.testing.assert_allclose(r2.mu, 3.0 * r1.mu, rtol=1e-12, atol=1e-14)
+    np.testing.assert_array_equal(r2.Pt, r1.Pt)
+
+
+def test_staged_schedule_needs_fewer_rounds_on_the_svm_matrix():
+    """Section 3.2's point that non-synchronous schedules converge faster, on
+    a seeded SVM matrix of the mixture workload."""
+    p = workloads.mixture(600, 16, seed=12, C=1.0)
+    Q = oracle.build_q(p.X.astype(np.float64), p.y.astype(np.float64), p.gamma, p.C)
+    k1 = oracle.gabp(Q, np.ones(p.n), iters=500, tol=1e-8).kstar
+    k4 = oracle.gabp_staged(Q, np.ones(p.n), iters=500, tol=1e-8, stages=4, block=128).kstar
+    assert k4 < k1 < 500
