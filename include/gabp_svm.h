@@ -109,7 +109,12 @@ typedef struct {
                               refine_inner * ||r||_inf of its right-hand side (never below tol / 2);
                               0 = 3e-2 with BF16 messages, 1e-2 with FP32 messages */
     int32_t task;          /* gabp_task, default GABP_TASK_SVM */
-    int32_t reserved[3];
+    int32_t stages;        /* message schedule: 0 or 1 = synchronous (Algorithm 2 as in Section 5's
+                              experiments, default); S = 2..16 = block Gauss-Seidel: a round updates
+                              every pair once, in S stages over bands of tile columns, and later stages
+                              use the aggregates of the earlier ones (Section 3.2: GaBP also converges
+                              under non-synchronous schedules).  Same fixed point, fewer rounds */
+    int32_t reserved[2];
 } gabp_svm_opts;
 
 typedef struct gabp_svm_s* gabp_svm_t;

@@ -65,7 +65,8 @@ struct gabp_svm_s {
     Inst* d_tab = nullptr;          // device copy of inst (a one-instance batch)
     int4* work = nullptr;           // tile list {0, I, J, L}
     int2* nbl = nullptr;            // node blocks {0, b}
-    Sched* sched = nullptr;
+    Sched* sched = nullptr;   // one per stage
+    int nstages = 1;
     StopOp* d_ops = nullptr;        // end-of-solve operation of the one instance
     int* d_members = nullptr;       // {0}
     RoundGrid grid{};
@@ -108,7 +109,7 @@ Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_m
     p.xp = q_mode != GABP_Q_F32 ? align_up(bf16_pack_bytes(Nt, (int)m), 1024) : 0;
     p.X = align_up((size_t)n * m * sizeof(float), 256);
     p.vec = align_up((size_t)npad * sizeof(float), 256);
-    p.agg = align_up((size_t)6 * npad * sizeof(float), 256);
+    p.agg = align_up((size_t)8 * npad * sizeof(float), 256);   // 2 x {P, h, mu} + staged {P, h}
     p.part = align_up((size_t)4 * Nt * n * sizeof(float), 256);
     p.state = 2 * align_up((size_t)ntiles * TT * (msg_bf16 ? 4 : 8), 256);
     p.q = q_mode == GABP_Q_F32 ? align_up((size_t)ntiles * TT * sizeof(float), 256)
@@ -117,7 +118,7 @@ Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_m
     // the BF16 store keeps an FP32 copy for the refinement residuals
     p.qref = q_mode == GABP_Q_BF16 ? align_up((size_t)ntiles * TT * sizeof(float), 256) : 0;
     p.work = align_up((size_t)ntiles * sizeof(int4), 256);
-    p.tab = align_up(sizeof(Inst) + sizeof(Sched) + sizeof(StopOp) + 64, 256);
+    p.tab = align_up(align_up(sizeof(Inst), 16) + kMaxStages * align_up(sizeof(Sched), 16) + sizeof(StopOp) + 64, 256);
     p.nbl = align_up((size_t)((n + 31) / 32) * sizeof(int2), 256);
     p.ctrl = align_up(sizeof(Ctrl), 256);
     p.rhist = align_up((size_t)kRhistCap * sizeof(double), 256);
@@ -236,8 +237,8 @@ gabp_status get_graph(gabp_svm_t h, int rounds, gabp_svm_s::Graph** out)
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < rounds; ++k)
-        launch_round(h->d_tab, h->work, h->nbl, h->sched, h->grid, h->opts.q_mode, h->opts.msg_bf16, h->stream,
-                     h->profiling ? &G.ev[(size_t)2 * k] : nullptr);
+        launch_round(h->d_tab, h->work, h->nbl, h->sched, h->nstages, h->grid, h->opts.q_mode, h->opts.msg_bf16,
+                     h->stream, h->profiling ? &G.ev[(size_t)2 * k] : nullptr);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (e != cudaSuccess) return fail(GABP_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
     e = cudaGraphInstantiate(&G.exec, g, 0);
@@ -357,6 +358,7 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     if (o.msg_bf16 != 0 && (o.msg_bf16 != 1 || o.q_mode == GABP_Q_F32))
         return fail(GABP_EINVAL, "msg_bf16 = 1 needs a precision form (q_mode BF16 or recompute)");
     if (o.task != GABP_TASK_SVM && o.task != GABP_TASK_KRR) return fail(GABP_EINVAL, "unknown task %d", o.task);
+    if (o.stages < 0 || o.stages > kMaxStages) return fail(GABP_EINVAL, "stages must be in [0, %d]", kMaxStages);
 
     int dev = 0, ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -376,6 +378,7 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     h->C = C;
     h->lambda = o.bias_mode == 1 ? o.bias_lambda : (o.task == GABP_TASK_KRR ? 0.0 : 1.0 / (double)n);
     h->delta = o.diag_delta;
+    h->nstages = o.stages > 1 ? o.stages : 1;
 
     const Plan pl = make_plan(n, m, h->Nt, h->ntiles, h->npad, o.q_mode, o.msg_bf16);
     size_t free_b = 0, total_b = 0;
@@ -424,6 +427,7 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     h->mu_acc = (float*)take(pl.vec);
     h->r32 = (float*)take(pl.vec);
     p.agg = (float*)take(pl.agg);
+    p.aggmid = p.agg + (size_t)6 * h->npad;
     p.part = (float*)take(pl.part);
     p.Pst = take(pl.state / 2);
     p.Hst = take(pl.state / 2);
@@ -434,8 +438,8 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     {
         char* tb = (char*)take(pl.tab);
         h->d_tab = (Inst*)tb;
-        h->sched = (Sched*)(tb + align_up(sizeof(Inst), 16));
-        h->d_ops = (StopOp*)(tb + align_up(sizeof(Inst), 16) + align_up(sizeof(Sched), 16));
+        h->sched = (Sched*)(tb + align_up(sizeof(Inst), 16));   // one per stage
+        h->d_ops = (StopOp*)(tb + align_up(sizeof(Inst), 16) + kMaxStages * align_up(sizeof(Sched), 16));
         h->d_members = (int*)((char*)h->d_ops + align_up(sizeof(StopOp), 16));
     }
     h->nbl = (int2*)take(pl.nbl);
@@ -450,19 +454,29 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
         p.nkc = bf16_chunks((int)m);
     }
 
-    // Tile work list: the upper triangle, row by row; L(I,J) = I*Nt - I(I-1)/2 + (J-I).
-    std::vector<int4> wl((size_t)h->ntiles);
-    size_t k = 0;
-    for (int I = 0; I < h->Nt; ++I)
-        for (int J = I; J < h->Nt; ++J, ++k) wl[k] = make_int4(0, I, J, (int)k);
+    // Tile work list: the upper triangle, row by row within each stage (one
+    // stage = all of it under the synchronous schedule); tile storage index
+    // L(I,J) = I*Nt - I(I-1)/2 + (J-I).
+    std::vector<int4> wl;
+    wl.reserve((size_t)h->ntiles);
+    int B[kMaxStages + 1];
+    stage_bounds(h->Nt, h->nstages, B);
     const int nblk = (int)((n + 31) / 32);
+    Sched sc[kMaxStages];
+    for (int st = 0; st < h->nstages; ++st) {
+        const long long off = (long long)wl.size();
+        for (int I = 0; I < h->Nt; ++I)
+            for (int J = std::max(I, B[st]); J < B[st + 1]; ++J)
+                wl.push_back(make_int4(0, I, J, (int)((long long)I * h->Nt - (long long)I * (I - 1) / 2 + (J - I))));
+        sc[st] = Sched{(long long)wl.size() - off, nblk, 1, off};
+    }
     std::vector<int2> nb((size_t)nblk);
     for (int b = 0; b < nblk; ++b) nb[(size_t)b] = make_int2(0, b);
-    Sched sc{h->ntiles, nblk, 1};
     h->grid = round_grid(h->ntiles, nblk, o.q_mode, 0, o.msg_bf16);
     e = cudaMemcpyAsync(h->work, wl.data(), wl.size() * sizeof(int4), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->nbl, nb.data(), nb.size() * sizeof(int2), cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->sched, &sc, sizeof sc, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->sched, sc, (size_t)h->nstages * sizeof(Sched), cudaMemcpyHostToDevice, h->stream);
     const int zero_slot = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_members, &zero_slot, sizeof(int), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

@@ -50,7 +50,7 @@ MemberPlan member_plan(int64_t n, int64_t m, int q_mode, int msg_bf16)
     MemberPlan p{};
     p.X = aup((size_t)n * m * 4, 256);
     p.vec = aup(npad * 4, 256);
-    p.agg = aup(6 * npad * 4, 256);
+    p.agg = aup(8 * npad * 4, 256);   // 2 x {P, h, mu} + staged {P, h}
     p.part = aup((size_t)4 * Nt * n * 4, 256);
     p.state = 2 * aup((size_t)nt * TT * (msg_bf16 ? 4 : 8), 256);
     p.q = q_mode == 0 ? aup((size_t)nt * TT * 4, 256) : q_mode == 1 ? aup((size_t)nt * TT * 2, 256) : 0;
@@ -97,11 +97,14 @@ struct Member {
 
 struct TuneKey {
     int q_mode;
+    int msg_bf16;
+    int nstages;
     long long tiles_bucket;
     int members_bucket;
     bool operator<(const TuneKey& o) const
     {
-        return std::tie(q_mode, tiles_bucket, members_bucket) < std::tie(o.q_mode, o.tiles_bucket, o.members_bucket);
+        return std::tie(q_mode, msg_bf16, nstages, tiles_bucket, members_bucket) <
+               std::tie(o.q_mode, o.msg_bf16, o.nstages, o.tiles_bucket, o.members_bucket);
     }
 };
 struct TuneVal {
@@ -142,6 +145,7 @@ class Engine {
     } while (0)
 
     int q_mode = 0, diag_rule = 0, x_f64 = 0, ptr_mode = 0, msg_bf16 = 0, task = 0, bias_mode = 0;
+    int nstages = 1;   // message schedule: 1 synchronous, > 1 staged
     double delta = 0.1, sv_threshold = 0.0, bias_lambda = 0.0;
     double handover = 1e-4, inner = 1e-2;   // refinement schedule
     double t_rebuild = 0;                    // host ms spent rebuilding the round lists
@@ -197,6 +201,7 @@ class Engine {
         q_mode = o.q_mode;
         msg_bf16 = o.msg_bf16;
         task = o.task;
+        nstages = o.stages > 1 ? o.stages : 1;
         bias_mode = o.bias_mode;
         bias_lambda = o.bias_lambda;
         diag_rule = o.diag_rule;
@@ -237,7 +242,9 @@ class Engine {
         const size_t b_bl = aup((size_t)cap_members * sizeof(int2), 256);
         const size_t b_bt = aup((size_t)cap_members * sizeof(double), 256);
         char* base = nullptr;
-        EK(cudaMalloc((void**)&base, b_tab + b_ctrl + 2 * b_work + 2 * b_nbl + b_ops + b_f3 + b_mem + b_bl + b_bt + 256));
+        const size_t b_sched = aup((size_t)kMaxStages * sizeof(Sched), 256);
+        EK(cudaMalloc((void**)&base,
+                      b_tab + b_ctrl + 2 * b_work + 2 * b_nbl + b_ops + b_f3 + b_mem + b_bl + b_bt + b_sched));
         size_t off = 0;
         auto carve = [&](size_t bytes) { char* r = base + off; off += bytes; return r; };
         d_tab = (Inst*)carve(b_tab);
@@ -251,9 +258,9 @@ class Engine {
         d_stop_members = (int*)carve(b_mem);
         d_begin_list = (int2*)carve(b_bl);
         d_begin_tol = (double*)carve(b_bt);
-        d_sched = (Sched*)carve(256);
+        d_sched = (Sched*)carve(b_sched);   // one per stage
         EK(cudaMemsetAsync(d_ctrl, 0, b_ctrl, stream));
-        EK(cudaMemsetAsync(d_sched, 0, sizeof(Sched), stream));
+        EK(cudaMemsetAsync(d_sched, 0, b_sched, stream));
         EK(cudaMallocHost((void**)&h_ctrl, (size_t)cap_members * sizeof(Ctrl)));
         EK(cudaMallocHost((void**)&h_f3, (size_t)cap_members * 3 * sizeof(double)));
         EK(cudaMallocHost((void**)&h_ops, (size_t)cap_members * sizeof(StopOp)));
@@ -319,6 +326,7 @@ class Engine {
         M.r32 = (float*)take(pl.vec);
         take(pl.vec);
         p.agg = (float*)take(pl.agg);
+        p.aggmid = p.agg + (size_t)6 * p.npad;
         p.part = (float*)take(pl.part);
         p.Pst = take(pl.state / 2);
         p.Hst = take(pl.state / 2);
@@ -477,23 +485,36 @@ class Engine {
             ~Acc() { t += ms_since(t0); }
         } acc{t_rebuild, t0};
         ++rebuilds;
+        // tiles grouped by stage (one stage under the synchronous schedule),
+        // every instance with its own stage bounds; node blocks of all
         std::vector<int4> wl;
         std::vector<int2> nb;
+        Sched sc[kMaxStages];
+        for (int st = 0; st < nstages; ++st) {
+            const long long off = (long long)wl.size();
+            for (int k = 0; k < cap_members; ++k) {
+                const Member& M = mem[(size_t)k];
+                if (!M.used || !M.active) continue;
+                const int Nt = M.inst.Nt;
+                int B[kMaxStages + 1];
+                stage_bounds(Nt, nstages, B);
+                for (int I = 0; I < Nt; ++I)
+                    for (int J = std::max(I, B[st]); J < B[st + 1]; ++J)
+                        wl.push_back(make_int4(k, I, J, (int)((long long)I * Nt - (long long)I * (I - 1) / 2 + (J - I))));
+            }
+            sc[st] = Sched{(long long)wl.size() - off, 0, cap_members, off};
+        }
         for (int k = 0; k < cap_members; ++k) {
             const Member& M = mem[(size_t)k];
             if (!M.used || !M.active) continue;
-            const int Nt = M.inst.Nt;
-            long long L = 0;
-            for (int I = 0; I < Nt; ++I)
-                for (int J = I; J < Nt; ++J, ++L) wl.push_back(make_int4(k, I, J, (int)L));
             for (int b = 0; b < M.nblk; ++b) nb.push_back(make_int2(k, b));
         }
+        for (int st = 0; st < nstages; ++st) sc[st].nblocks = (int)nb.size();
         if ((long long)wl.size() > cap_tiles || (int)nb.size() > cap_nblk)
             return fail(GABP_ENOMEM, "batch lists exceed their capacity");
-        Sched sc{(long long)wl.size(), (int)nb.size(), cap_members};
         if (!wl.empty()) EK(cudaMemcpyAsync(d_work, wl.data(), wl.size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
         if (!nb.empty()) EK(cudaMemcpyAsync(d_nbl, nb.data(), nb.size() * sizeof(int2), cudaMemcpyHostToDevice, stream));
-        EK(cudaMemcpyAsync(d_sched, &sc, sizeof sc, cudaMemcpyHostToDevice, stream));
+        EK(cudaMemcpyAsync(d_sched, sc, (size_t)nstages * sizeof(Sched), cudaMemcpyHostToDevice, stream));
         EK(cudaStreamSynchronize(stream));   // host vectors go out of scope
         live_tiles = (long long)wl.size();
         lists_dirty = false;
@@ -507,7 +528,8 @@ class Engine {
         if (it != graphs.end()) { *out = it->second; return GABP_OK; }
         cudaGraph_t g = nullptr;
         EK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
-        for (int k = 0; k < rounds; ++k) launch_round(d_tab, d_work, d_nbl, d_sched, grid, q_mode, msg_bf16, stream);
+        for (int k = 0; k < rounds; ++k)
+            launch_round(d_tab, d_work, d_nbl, d_sched, nstages, grid, q_mode, msg_bf16, stream);
         EK(cudaStreamEndCapture(stream, &g));
         cudaGraphExec_t ex = nullptr;
         cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
@@ -689,7 +711,7 @@ class Engine {
         int members = 0;
         for (auto& M : mem)
             if (M.used && M.active) { tiles += M.ntiles; ++members; }
-        TuneKey key{q_mode, tiles >> 8, members >> 3};
+        TuneKey key{q_mode, msg_bf16, nstages, tiles >> 8, members >> 3};
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             auto it = g_tune_cache.find(key);
@@ -763,7 +785,7 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
     if (opts) o = *opts;
     if (o.diag_delta == 0) o.diag_delta = 0.1;
     if (o.q_mode < 0 || o.q_mode > 2 || o.refine < 0 || o.refine > 64 || o.msg_bf16 < 0 || o.msg_bf16 > 1 ||
-        (o.msg_bf16 && o.q_mode == 0) || o.task < 0 || o.task > 1 ||
+        (o.msg_bf16 && o.q_mode == 0) || o.task < 0 || o.task > 1 || o.stages < 0 || o.stages > kMaxStages ||
         (o.bias_mode == 1 && (!(o.bias_lambda >= 0) || !std::isfinite(o.bias_lambda)))) {
         set_last_error("gabp_batch_solve: bad q_mode, refine, msg_bf16, task or bias");
         return GABP_EINVAL;
@@ -893,7 +915,8 @@ gabp_status gabp_server_create(const gabp_server_cfg* cfg, gabp_server_t* out)
     gabp_server_cfg c = *cfg;
     if (c.max_members <= 0) c.max_members = 64;
     if (c.max_members > 4096 || c.iters < 0 || std::isnan(c.tol) || c.opts.q_mode < 0 || c.opts.q_mode > 2 ||
-        (c.opts.msg_bf16 && c.opts.q_mode == 0) || c.opts.task < 0 || c.opts.task > 1 ||
+        (c.opts.msg_bf16 && c.opts.q_mode == 0) || c.opts.task < 0 || c.opts.task > 1 || c.opts.stages < 0 ||
+        c.opts.stages > kMaxStages ||
         (c.opts.bias_mode == 1 && (!(c.opts.bias_lambda >= 0) || !std::isfinite(c.opts.bias_lambda)))) {
         set_last_error("gabp_server_create: bad configuration");
         return GABP_EINVAL;

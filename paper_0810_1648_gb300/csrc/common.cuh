@@ -80,6 +80,7 @@ struct Inst {
                       // store itself, a separate copy beside the BF16 store, or nullptr
                       // when Q is recomputed)
     float* agg;       // [2][3][npad]: double-buffered {Ptilde, htilde, mutilde}
+    float* aggmid;    // [2][npad]: {Ptilde, htilde} between the stages of a staged round
     float* part;      // [4][Nt][n] partial sums
     Ctrl* ctrl;
     double* rhist;    // ||r(t)||_inf per round (rhist_cap entries)
@@ -98,11 +99,31 @@ struct Inst {
 // captured round stays valid while the set changes).  Tile list entries are
 // int4 {instance, I, J, tile index within the instance}; node-block list
 // entries are int2 {instance, block of 32 nodes}.
+// Under the staged (block Gauss-Seidel) schedule a round has one Sched per
+// stage, each naming its segment [off, off + ntiles) of the tile list.
 struct Sched {
     long long ntiles;
     int nblocks;
     int ninst;
+    long long off;
 };
+constexpr int kMaxStages = 16;
+
+// Stage boundaries of the staged schedule for Nt tile rows: B[0] = 0,
+// B[S] = Nt, B[s] = the smallest b with S b (b + 1) / 2 >= s Nt (Nt + 1) / 2
+// (about equal tile counts per stage); tile (I, J) runs in the stage whose
+// range [B[s], B[s+1]) holds J.
+inline void stage_bounds(int Nt, int S, int* B)
+{
+    const long long tot = (long long)Nt * (Nt + 1) / 2;
+    B[0] = 0;
+    for (int s = 1; s < S; ++s) {
+        long long b = B[s - 1];
+        while (b < Nt && (long long)S * (b * (b + 1) / 2) < (long long)s * tot) ++b;
+        B[s] = (int)b;
+    }
+    B[S] = Nt;
+}
 
 // What the end-of-solve kernels do for one instance (indexed by its slot):
 // final residual / objective / alpha of the means `mu`, the FP32 residual to
@@ -170,11 +191,13 @@ RoundGrid round_grid(long long max_tiles, int max_nblocks, int q_mode, int ctas_
 cudaError_t prepare_sweep();
 // Fused-recompute form: also raises the shared-memory limit of its sweep kernel.
 cudaError_t prepare_sweep_rc();
-// One synchronous round over every live instance of tab: pair sweep then
-// per-node finalize.  When ev is not null, ev[0] is recorded before and
-// ev[1] after the pair sweep.
-void launch_round(const Inst* tab, const int4* work, const int2* nbl, const Sched* sched, const RoundGrid& g,
-                  int q_mode, int msg_bf16, cudaStream_t s, cudaEvent_t* ev = nullptr);
+// One round over every live instance of tab: pair sweep then per-node
+// finalize.  When ev is not null, ev[0] is recorded before the (first stage's)
+// pair sweep and ev[1] after the (last stage's) pair sweep.
+// nstages > 1: the staged schedule, sched[0 .. nstages-1] one per stage, a
+// stage finalize (aggregates only) between the stages.
+void launch_round(const Inst* tab, const int4* work, const int2* nbl, const Sched* sched, int nstages,
+                  const RoundGrid& g, int q_mode, int msg_bf16, cudaStream_t s, cudaEvent_t* ev = nullptr);
 // Final FP32-Gram residual r = 1 - Q mu (FP64 sums), dual objective and
 // alpha = clip(mu, 0, C) of the listed instances (their tiles, node blocks
 // and slots), per ops[slot]; results in ops[slot].final3 and f3_all[3 slot].

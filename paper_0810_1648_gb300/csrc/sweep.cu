@@ -193,7 +193,7 @@ __host__ __device__ constexpr size_t sweep_smem_bytes()
 template <typename QT, class MSG, size_t SB>
 __device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, const int4* __restrict__ work,
                                                long long ntiles, SweepTail& sm, unsigned char* ring,
-                                               volatile int* abort_flag, int lane)
+                                               volatile int* abort_flag, int lane, int stage_no)
 {
     constexpr size_t QB = QBytes<QT>::v;
     constexpr size_t MB = sizeof(typename MSG::T2);
@@ -240,8 +240,12 @@ __device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, con
         }
         __syncwarp();
         if (lane < 6) {
-            const float* agg = p.agg + (size_t)(t & 1) * 3 * p.npad + (size_t)(lane % 3) * p.npad +
-                               (size_t)(lane < 3 ? I : J) * T;
+            // Ptilde and htilde from the previous stage's aggregates in a
+            // staged round; mutilde (residual partials) from the round's start
+            const int a = lane % 3;
+            const float* base = (stage_no > 0 && a < 2) ? p.aggmid + (size_t)a * p.npad
+                                                        : p.agg + (size_t)(t & 1) * 3 * p.npad + (size_t)a * p.npad;
+            const float* agg = base + (size_t)(lane < 3 ? I : J) * T;
             bulk_load(&sm.agg[slot][lane][0], agg, T * sizeof(float), &sm.tfull[slot], pol_keep);
         }
         if (++slot == 2) { slot = 0; tph ^= 1u; }
@@ -688,9 +692,10 @@ __device__ __forceinline__ unsigned char* align_smem(unsigned char* raw, uintptr
 
 template <typename QT, class MSG>
 __global__ void __launch_bounds__(SWEEP_THREADS, sweep_ctas<MSG>())
-    k_sweep(const Inst* __restrict__ tab, const int4* __restrict__ work, const Sched* __restrict__ sched)
+    k_sweep(const Inst* __restrict__ tab, const int4* __restrict__ work, const Sched* __restrict__ sched, int stage_no)
 {
     const long long ntiles = sched->ntiles;
+    work += sched->off;
     constexpr size_t SB = stage_bytes<QT, MSG>();
 
     extern __shared__ unsigned char smem_raw[];
@@ -704,7 +709,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, sweep_ctas<MSG>())
     }
     __syncthreads();
     if (warp == NWARPS) {
-        sweep_producer<QT, MSG, SB>(tab, work, ntiles, sm, ring, nullptr, lane);
+        sweep_producer<QT, MSG, SB>(tab, work, ntiles, sm, ring, nullptr, lane, stage_no);
         return;
     }
     StoredQ<QT, MSG> qsrc;
@@ -754,9 +759,11 @@ struct RecomputedQ {
 
 template <class MSG>
 __global__ void __launch_bounds__(RC_THREADS, 1)
-    k_sweep_rc(const Inst* __restrict__ tab, const int4* __restrict__ work, const Sched* __restrict__ sched)
+    k_sweep_rc(const Inst* __restrict__ tab, const int4* __restrict__ work, const Sched* __restrict__ sched,
+               int stage_no)
 {
     const long long ntiles = sched->ntiles;
+    work += sched->off;
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* ring = align_smem(smem_raw, 1024);
@@ -787,7 +794,7 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
     volatile int* abort_flag = &ex.abort;
 
     if (warp == 0) {
-        sweep_producer<void, MSG, state_chunk<MSG>()>(tab, work, ntiles, sm, ring, abort_flag, lane);
+        sweep_producer<void, MSG, state_chunk<MSG>()>(tab, work, ntiles, sm, ring, abort_flag, lane, stage_no);
     } else if (warp == 1) {
         // feature blocks of each tile
         if (lane == 0) {
@@ -1049,6 +1056,80 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Node x's P (when `with_p`) and H slot partials := 0, the sums of all-zero
+// messages: the staged schedule's stage finalize reads the slots of tiles not
+// yet swept in a round.
+__device__ __forceinline__ void zero_slots(const Inst& p, int x, bool with_p)
+{
+    float* partP = p.part;
+    float* partH = partP + (size_t)p.Nt * p.n;
+    for (int k = 0; k < p.Nt; ++k) {
+        if (with_p) partP[(size_t)k * p.n + x] = 0.f;
+        partH[(size_t)k * p.n + x] = 0.f;
+    }
+}
+
+// Between the stages of a staged round: Ptilde and htilde of every node from
+// all of its slot partials (slots of tiles not yet swept in this round still
+// hold the sums of their current messages) into aggmid, for the next stage;
+// with frozen P, Ptilde is kept.  No residual and no stop test: those come
+// with the round's last stage (k_finalize).
+__global__ void __launch_bounds__(256)
+    k_finalize_stage(const Inst* __restrict__ tab, const int2* __restrict__ nbl, const Sched* __restrict__ sched)
+{
+    const int nblocks = sched->nblocks;
+    __shared__ float red[4][8][32];
+    for (int bi = blockIdx.x; bi < nblocks; bi += gridDim.x) {
+        const int2 nb = nbl[bi];
+        const Inst& p = tab[nb.x];
+        Ctrl* ctrl = p.ctrl;
+        if (*(volatile int*)&ctrl->done) continue;   // the same node block for the whole CTA
+        const int t = *(volatile int*)&ctrl->t;
+        const bool frozen = *(volatile int*)&ctrl->p_frozen != 0;
+        const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
+        const int x = nb.y * 32 + lane, n = p.n, Nt = p.Nt;
+        const float* partP = p.part;
+        const float* partH = partP + (size_t)Nt * n;
+        float sP = 0.f, cPs = 0.f, sH = 0.f, cHs = 0.f;
+        if (x < n) {
+            int k = g;
+            for (; k + 24 < Nt; k += 32) {
+                float vp[4], vh[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const size_t o = (size_t)(k + 8 * u) * n + x;
+                    vp[u] = frozen ? 0.f : partP[o];
+                    vh[u] = partH[o];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) { acc2(sP, cPs, vp[u]); acc2(sH, cHs, vh[u]); }
+            }
+            for (; k < Nt; k += 8) {
+                const size_t o = (size_t)k * n + x;
+                acc2(sP, cPs, frozen ? 0.f : partP[o]);
+                acc2(sH, cHs, partH[o]);
+            }
+        }
+        __syncthreads();   // red[] of the previous node block is consumed
+        red[0][g][lane] = sP; red[1][g][lane] = cPs;
+        red[2][g][lane] = sH; red[3][g][lane] = cHs;
+        __syncthreads();
+        if (g == 0 && x < n) {
+            float a[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                acc2(a[0], a[1], red[0][w][lane]); a[1] += red[1][w][lane];
+                acc2(a[2], a[3], red[2][w][lane]); a[3] += red[3][w][lane];
+            }
+            const double P = (double)a[0] + (double)a[1];
+            const double H = (double)a[2] + (double)a[3];
+            const float* cur = p.agg + (size_t)(t & 1) * 3 * p.npad;
+            p.aggmid[x] = frozen ? cur[x] : (float)((double)p.qdiag[x] + P);
+            p.aggmid[p.npad + x] = (float)((double)p.b[x] + H);
+        }
+    }
+}
+
 __global__ void k_reset(Inst p)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1065,6 +1146,7 @@ __global__ void k_reset(Inst p)
         c->blocks_done = 0u;
     }
     if (x >= p.n) return;
+    zero_slots(p, x, true);
     const float qd = p.qdiag[x], bx = p.b0[x];
     const_cast<float*>(p.b)[x] = bx;
     p.agg[x] = qd;
@@ -1085,6 +1167,7 @@ __global__ void k_refine_rhs_list(const Inst* __restrict__ tab, const StopOp* __
     const int x = nb.y * 32 + threadIdx.x;
     if (nb.y == 0 && threadIdx.x == 0) c->zero_h = 1;
     if (threadIdx.x >= 32 || x >= p.n) return;
+    zero_slots(p, x, false);   // the H messages restart from 0
     float* cur = p.agg + (size_t)(t & 1) * 3 * p.npad;
     const float bx = ops[nb.x].r_out[x];
     const_cast<float*>(p.b)[x] = bx;
@@ -1146,6 +1229,7 @@ __global__ void k_init(Inst p, int diag_rule, float delta)
     if (x >= p.n) return;
     double R = 0.0;
     for (int k = 0; k < p.Nt; ++k) R += (double)p.part[(size_t)k * p.n + x];
+    zero_slots(p, x, true);   // all messages start at 0
     const double lam2 = p.lam2;
     const double base = 1.0 + lam2 + 1.0 / (double)p.C;
     double qd = base;
@@ -1181,6 +1265,7 @@ __global__ void k_init_list(const Inst* __restrict__ tab, const int2* __restrict
     if (threadIdx.x >= 32 || x >= p.n) return;
     double R = 0.0;
     for (int k = 0; k < p.Nt; ++k) R += (double)p.part[(size_t)k * p.n + x];
+    zero_slots(p, x, true);   // all messages start at 0
     const double lam2 = p.lam2;
     const double base = 1.0 + lam2 + 1.0 / (double)p.C;
     double qd = base;
@@ -1331,24 +1416,31 @@ cudaError_t prepare_sweep()
     return e;
 }
 
-void launch_round(const Inst* tab, const int4* work, const int2* nbl, const Sched* sched, const RoundGrid& g,
-                  int q_mode, int msg_bf16, cudaStream_t s, cudaEvent_t* ev)
+void launch_round(const Inst* tab, const int4* work, const int2* nbl, const Sched* sched, int nstages,
+                  const RoundGrid& g, int q_mode, int msg_bf16, cudaStream_t s, cudaEvent_t* ev)
 {
-    if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
-    if (q_mode == 2 && msg_bf16)
-        k_sweep_rc<MsgBF16><<<g.sweep, RC_THREADS, rc_smem_bytes<MsgBF16>(), s>>>(tab, work, sched);
-    else if (q_mode == 2)
-        k_sweep_rc<MsgF32><<<g.sweep, RC_THREADS, rc_smem_bytes<MsgF32>(), s>>>(tab, work, sched);
-    else if (q_mode == 1 && msg_bf16)
-        k_sweep<__nv_bfloat16, MsgBF16>
-            <<<g.sweep, SWEEP_THREADS, sweep_smem_bytes<__nv_bfloat16, MsgBF16>(), s>>>(tab, work, sched);
-    else if (q_mode == 1)
-        k_sweep<__nv_bfloat16, MsgF32>
-            <<<g.sweep, SWEEP_THREADS, sweep_smem_bytes<__nv_bfloat16, MsgF32>(), s>>>(tab, work, sched);
-    else
-        k_sweep<float, MsgF32><<<g.sweep, SWEEP_THREADS, sweep_smem_bytes<float, MsgF32>(), s>>>(tab, work, sched);
-    if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
-    k_finalize<<<g.finalize, 256, 0, s>>>(tab, nbl, sched);
+    for (int st = 0; st < nstages; ++st) {
+        const Sched* sc = sched + st;
+        if (ev && st == 0) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
+        if (q_mode == 2 && msg_bf16)
+            k_sweep_rc<MsgBF16><<<g.sweep, RC_THREADS, rc_smem_bytes<MsgBF16>(), s>>>(tab, work, sc, st);
+        else if (q_mode == 2)
+            k_sweep_rc<MsgF32><<<g.sweep, RC_THREADS, rc_smem_bytes<MsgF32>(), s>>>(tab, work, sc, st);
+        else if (q_mode == 1 && msg_bf16)
+            k_sweep<__nv_bfloat16, MsgBF16>
+                <<<g.sweep, SWEEP_THREADS, sweep_smem_bytes<__nv_bfloat16, MsgBF16>(), s>>>(tab, work, sc, st);
+        else if (q_mode == 1)
+            k_sweep<__nv_bfloat16, MsgF32>
+                <<<g.sweep, SWEEP_THREADS, sweep_smem_bytes<__nv_bfloat16, MsgF32>(), s>>>(tab, work, sc, st);
+        else
+            k_sweep<float, MsgF32>
+                <<<g.sweep, SWEEP_THREADS, sweep_smem_bytes<float, MsgF32>(), s>>>(tab, work, sc, st);
+        if (ev && st == nstages - 1) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
+        if (st < nstages - 1)
+            k_finalize_stage<<<g.finalize, 256, 0, s>>>(tab, nbl, sched);
+        else
+            k_finalize<<<g.finalize, 256, 0, s>>>(tab, nbl, sched);
+    }
 }
 
 void launch_get_pairs(const Inst& p, const long long* ij, long long cnt, float4* out, cudaStream_t s)

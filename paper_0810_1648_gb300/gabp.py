@@ -44,7 +44,7 @@ class Opts(ctypes.Structure):
                 ("refine", ctypes.c_int32), ("sv_threshold", ctypes.c_double),
                 ("chunk", ctypes.c_int32), ("msg_bf16", ctypes.c_int32),
                 ("refine_handover", ctypes.c_float), ("refine_inner", ctypes.c_float),
-                ("task", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("task", ctypes.c_int32), ("stages", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class Profile(ctypes.Structure):
