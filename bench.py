@@ -256,8 +256,11 @@ def run_batch(args):
     probs = workloads.batch_grid()
     stream = torch.cuda.Stream()
     out = {}
+    st = args.stages if args.stages > 1 else 4
     for mode, kw in (("f32", dict(q_mode=0)), ("bf16q_refined", dict(q_mode=1, refine=8)),
-                     ("bf16_refined", dict(q_mode=1, refine=8, msg_bf16=1))):
+                     ("bf16_refined", dict(q_mode=1, refine=8, msg_bf16=1)),
+                     ("f32_staged", dict(q_mode=0, stages=st)),
+                     ("bf16_refined_staged", dict(q_mode=1, refine=8, msg_bf16=1, stages=st))):
         for _ in range(args.warmup):
             gabp.batch_solve(probs, 200, 1e-6, chunk=0, stream=stream.cuda_stream, **kw)
         times, last = [], None
@@ -281,9 +284,14 @@ def run_batch(args):
                                    "gamma {0.1,0.5,1,2}/m, n log-uniform [200,4000], m in {8,32,128,256}, "
                                    "tol 1e-6 or 200 rounds, one persistent launch per round, autotuned schedule; "
                                    "modes: plain FP32; BF16 Q + refinement; BF16 Q and BF16 messages + refinement "
-                                   "(all to ||1 - Q mu||_inf < 1e-6 with the FP32-Gram Q)",
-                       "instances": len(probs), "sum_n2": n2},
-            "modes": out, "bf16_over_f32": out["bf16_refined"]["solves_per_s"] / out["f32"]["solves_per_s"]}
+                                   "(all to ||1 - Q mu||_inf < 1e-6 with the FP32-Gram Q), under the synchronous "
+                                   f"schedule and the {st}-stage block Gauss-Seidel schedule",
+                       "instances": len(probs), "sum_n2": n2, "stages": st},
+            "modes": out, "bf16_over_f32": out["bf16_refined"]["solves_per_s"] / out["f32"]["solves_per_s"],
+            "bf16_over_f32_staged": out["bf16_refined_staged"]["solves_per_s"] / out["f32_staged"]["solves_per_s"],
+            "staged_over_synchronous": {"f32": out["f32_staged"]["solves_per_s"] / out["f32"]["solves_per_s"],
+                                        "bf16": out["bf16_refined_staged"]["solves_per_s"] /
+                                        out["bf16_refined"]["solves_per_s"]}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -301,7 +309,8 @@ def run_serve(args):
     rng = np.random.default_rng(8)
     starts = [int(rng.integers(0, 50000 - r.n + 1)) for r in reqs]
     srv = gabp.Server(iters=200, tol=1e-6, max_members=args.max_members, q_mode=Q_MODES[args.q_mode],
-                      refine=8 if args.q_mode != "f32" else 0, msg_bf16=1 if args.msg_bf16 else 0, chunk=4)
+                      refine=8 if args.q_mode != "f32" else 0, msg_bf16=1 if args.msg_bf16 else 0, chunk=4,
+                      stages=args.stages)
     t0 = time.perf_counter()
     sub, lat, nxt = {}, [], 0
     rounds, passes, conv = [], [], 0
@@ -338,7 +347,8 @@ def run_serve(args):
             "config": {"workload": f"serving form: Poisson arrivals rate {args.rate}/s for {args.duration} s, "
                                    "n log-uniform [500,50000], m log-uniform [16,512], C log-uniform [0.1,100], "
                                    "gamma 1/m, tol 1e-6 or 200 rounds, admission by device memory",
-                       "requests": len(reqs), "q_mode": args.q_mode, "max_members": args.max_members},
+                       "requests": len(reqs), "q_mode": args.q_mode, "max_members": args.max_members,
+                       "stages": max(args.stages, 1)},
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "max": float(lat.max())},
             "wall_s": wall, "offered_per_s": args.rate, "server_phases_ms": phases,
@@ -538,6 +548,9 @@ def main():
     ap.add_argument("--duration", type=float, default=60.0)
     ap.add_argument("--max-members", type=int, default=64)
     ap.add_argument("--msg-bf16", action="store_true", help="precision forms: BF16 message storage")
+    ap.add_argument("--stages", type=int, default=0,
+                    help="message schedule: 0/1 synchronous (default), S > 1 block Gauss-Seidel in S stages "
+                         "(serve; the batch workload always adds S-stage modes, S = 4 by default)")
     ap.add_argument("--task", default="svm", choices=list(TASKS),
                     help="svm (default) or krr: kernel ridge regression on the same features and sweep")
     ap.add_argument("--q-mode", default=None, choices=list(Q_MODES))
