@@ -463,6 +463,7 @@ def run_ours(args):
             "share_of_step": (prof["sweep_ms"] / ms) if ms > 0 else None}
 
     gabp.svm_destroy(h)
+    to_tol = None if args.no_to_tol else _to_tolerance(args, Xd, yd, p, stream, gabp, torch)
     e2e = None
     if not args.no_e2e:
         e2e = _e2e(args, p, stream, dev, ws, gabp, torch)
@@ -483,13 +484,41 @@ def run_ours(args):
                 "data": "synthetic", "config": dict(wl, parallelism=f"replicas{ws}"),
                 "edge_updates_per_s": value * n * (n - 1),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(launches), "clocks": clk,
+                "gpu_launches": int(launches), "clocks": clk, "solve_to_tolerance": to_tol,
                 "result": {"residual_inf": st["residual_inf"], "dual_objective": st["dual_objective"],
                            "n_support": st["n_support"]}}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def _to_tolerance(args, Xd, yd, p, stream, gabp, torch):
+    """Outside the timed region: one whole solve of the same workload to
+    ||r||_inf < 1e-6 (formation included; refinement in the precision forms)
+    under the synchronous and the 4-stage block Gauss-Seidel schedules, timed
+    with CUDA events on the solver's stream after one warm-up solve."""
+    out = {}
+    refine = 0 if args.q_mode == "f32" else 10
+    for name, stages in (("synchronous", 0), ("staged4", 4)):
+        opts = gabp.opts_default(stream=stream.cuda_stream, chunk=8, q_mode=Q_MODES[args.q_mode], refine=refine,
+                                 msg_bf16=1 if args.msg_bf16 else 0, task=TASKS[args.task], stages=stages)
+        h = gabp.svm_create(Xd, yd, p.gamma, p.C, opts)
+        alpha = torch.empty(p.n, dtype=torch.float32, device=Xd.device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for rep in range(2):
+            torch.cuda.synchronize()
+            e0.record(stream)
+            gabp.svm_refit(h, Xd, yd, p.gamma, p.C)
+            rinf, k = gabp.svm_solve(h, 400, 1e-6, alpha)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        st = gabp.svm_get_stats(h)
+        out[name] = {"ms": float(e0.elapsed_time(e1)), "rounds": int(k), "residual_inf": float(rinf),
+                     "converged": int(st["converged"]), "refine_passes": int(st["refine_passes"])}
+        gabp.svm_destroy(h)
+    out["staged_speedup"] = out["synchronous"]["ms"] / out["staged4"]["ms"]
+    return out
 
 
 def _e2e(args, p, stream, dev, ws, gabp, torch):
@@ -542,6 +571,7 @@ def main():
     ap.add_argument("--ref-sweeps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-to-tol", action="store_true", help="skip the solve-to-tolerance extra measurement")
     ap.add_argument("--workload", default="plain_large",
                     choices=["plain_large", "precision_large", "batch_grid", "serve"])
     ap.add_argument("--rate", type=float, default=200.0)
