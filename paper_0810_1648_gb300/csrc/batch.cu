@@ -366,11 +366,13 @@ class Engine {
         EK(cudaMemcpyAsync(M.work, wl.data(), wl.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
         EK(cudaMemcpyAsync((void*)p.y, pr.y, (size_t)n * 4, ptr_mode ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
         if (pl.xp) EK(cudaMemsetAsync((void*)p.Xp, 0, pl.xp, s));   // padding rows and features stay 0
-        if (!ptr_mode && !x_f64) {
-            // FP32 rows straight into X; the batched staging of form_pending() checks them
-            EK(cudaMemcpyAsync((void*)p.X, pr.X, (size_t)n * m * 4, cudaMemcpyHostToDevice, s));
+        if (!x_f64) {
+            // FP32 rows straight into X (from host or device memory); the
+            // batched staging of form_pending() checks them
+            EK(cudaMemcpyAsync((void*)p.X, pr.X, (size_t)n * m * 4,
+                               ptr_mode ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
         } else {
-            // FP64 or device input: convert / copy and check now
+            // FP64 input: convert and check now
             const void* src = pr.X;
             void* tmp = nullptr;
             if (!ptr_mode) {

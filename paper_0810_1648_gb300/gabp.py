@@ -318,13 +318,26 @@ def selftest_bounded_wait(limit_ns: int) -> int:
 
 
 def batch_solve(problems, iters: int, tol: float, **opts):
-    """gabp_batch_solve over a list of workloads.Problem-like objects (numpy
-    X float32/float64, y).  Returns (list of alpha arrays, list of result dicts,
-    overall status)."""
+    """gabp_batch_solve over a list of workloads.Problem-like objects: numpy X
+    (float32/float64) and y, or float32 torch CUDA tensors for all of them
+    (device pointer mode; alphas then come back as CUDA tensors).  Returns
+    (list of alpha arrays, list of result dicts, overall status)."""
     probs = (Problem * len(problems))()
     keep, alphas = [], []
     f64 = None
+    dev = len(problems) > 0 and _is_cuda(problems[0].X)
+    if dev:
+        import torch
     for k, p in enumerate(problems):
+        if dev:
+            X = p.X.contiguous()
+            y = p.y.contiguous()
+            assert X.dtype == torch.float32 and y.dtype == torch.float32 and y.is_cuda
+            f64 = False
+            keep += [X, y]
+            probs[k] = Problem(X.data_ptr(), y.data_ptr(), X.shape[0], X.shape[1], float(p.gamma), float(p.C))
+            alphas.append(torch.empty(X.shape[0], dtype=torch.float32, device=X.device))
+            continue
         X = np.ascontiguousarray(p.X)
         if f64 is None:
             f64 = X.dtype == np.float64
@@ -333,11 +346,15 @@ def batch_solve(problems, iters: int, tol: float, **opts):
         keep += [X, y]
         probs[k] = Problem(X.ctypes.data, y.ctypes.data, X.shape[0], X.shape[1], float(p.gamma), float(p.C))
         alphas.append(np.empty(X.shape[0], dtype=np.float32))
+    if dev:
+        _sync_torch(*keep)
     res = (Result * len(problems))()
     for k in range(len(problems)):
-        res[k].alpha = alphas[k].ctypes.data
+        res[k].alpha = alphas[k].data_ptr() if dev else alphas[k].ctypes.data
     o = opts_default(**opts)
     o.x_dtype = 1 if f64 else 0
+    if dev:
+        o.ptr_mode = 1
     rc = load().gabp_batch_solve(probs, len(problems), ctypes.byref(o), int(iters), float(tol), res)
     if rc not in (OK, ENUMERIC):
         _check(rc)

@@ -154,3 +154,17 @@ def test_server_krr_and_phases():
         single, _, _ = gabp.GabpSVM(p.X, tg, p.gamma, 0.5, task=gabp.TASK_KRR, chunk=4).solve(300, 1e-6)
         np.testing.assert_array_equal(a, single)
     srv.close()
+
+
+def test_batch_device_pointers_equal_host():
+    torch = pytest.importorskip("torch")
+    probs = _mix(5, 6)
+    a_host, r_host, rc = gabp.batch_solve(probs, 60, 1e-6, chunk=8)
+    assert rc == gabp.OK
+    dprobs = [workloads.Problem(torch.from_numpy(p.X).cuda(), torch.from_numpy(p.y).cuda(), p.gamma, p.C)
+              for p in probs]
+    a_dev, r_dev, rc = gabp.batch_solve(dprobs, 60, 1e-6, chunk=8)
+    assert rc == gabp.OK
+    for ah, ad, rh, rd in zip(a_host, a_dev, r_host, r_dev):
+        np.testing.assert_array_equal(ah, ad.cpu().numpy())
+        assert rh["iters_done"] == rd["iters_done"]
