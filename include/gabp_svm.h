@@ -253,9 +253,10 @@ GABP_API gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, 
                                       int32_t iters, double tol, gabp_result* results);
 
 /* Host wall time (ms) of the phases of this thread's last gabp_batch_solve:
- * out6 = {formation, schedule tuning, rounds, stop handling (final residuals,
- * refinement set-up, result copies), total, number of round chunks}. */
-GABP_API gabp_status gabp_batch_last_phases(double* out6);
+ * out7 = {formation, schedule tuning, rounds, stop handling (final residuals,
+ * refinement set-up, result copies), total, number of round chunks, the host
+ * part of formation (allocating and enqueuing the instances)}. */
+GABP_API gabp_status gabp_batch_last_phases(double* out7);
 
 /*
  * Continuous-batching server.  Requests queue in arrival order; each

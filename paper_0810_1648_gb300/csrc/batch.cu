@@ -39,7 +39,7 @@ size_t aup(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Device memory of one instance (one allocation), carved like the handle's.
 struct MemberPlan {
-    size_t X, vec, agg, part, state, q, qref, work, rhist, final3, blockbuf, xp, total;
+    size_t X, vec, agg, part, state, q, qref, rhist, final3, blockbuf, xp, total;
 };
 
 MemberPlan member_plan(int64_t n, int64_t m, int q_mode, int msg_bf16)
@@ -55,12 +55,11 @@ MemberPlan member_plan(int64_t n, int64_t m, int q_mode, int msg_bf16)
     p.state = 2 * aup((size_t)nt * TT * (msg_bf16 ? 4 : 8), 256);
     p.q = q_mode == 0 ? aup((size_t)nt * TT * 4, 256) : q_mode == 1 ? aup((size_t)nt * TT * 2, 256) : 0;
     p.qref = q_mode == 1 ? aup((size_t)nt * TT * 4, 256) : 0;   // FP32 copy for the refinement residuals
-    p.work = aup((size_t)nt * sizeof(int4), 256);
     p.rhist = 0;
     p.final3 = 256;
     p.blockbuf = aup((size_t)3 * ((n + 31) / 32) * 8, 256);
     p.xp = q_mode != 0 ? aup(bf16_pack_bytes(Nt, (int)m), 1024) : 0;
-    p.total = p.X + 10 * p.vec + p.agg + p.part + p.state + p.q + p.qref + p.work + p.final3 + p.blockbuf + p.xp + 2048;
+    p.total = p.X + 10 * p.vec + p.agg + p.part + p.state + p.q + p.qref + p.final3 + p.blockbuf + p.xp + 2048;
     return p;
 }
 
@@ -72,7 +71,6 @@ struct Member {
     Inst inst{};
     void* mem = nullptr;
     size_t bytes = 0;
-    int4* work = nullptr;    // own tile list {slot, I, J, L}
     long long ntiles = 0;
     int nblk = 0;
     float* alpha = nullptr;
@@ -118,6 +116,7 @@ std::map<TuneKey, TuneVal> g_tune_cache;
 struct BatchPhases {
     double form_ms, tune_ms, rounds_ms, stop_ms, total_ms;
     int64_t chunks, launches;
+    double add_ms;   // host part of form_ms: allocating and enqueuing every instance
 };
 thread_local BatchPhases g_last_phases{};
 
@@ -333,7 +332,6 @@ class Engine {
         p.msg_bf16 = msg_bf16;
         p.qstore = pl.q ? take(pl.q) : nullptr;
         p.qref = pl.qref ? (float*)take(pl.qref) : (q_mode == 0 ? (float*)p.qstore : nullptr);
-        M.work = (int4*)take(pl.work);
         M.final3 = (double*)take(pl.final3);
         M.blockbuf = (double*)take(pl.blockbuf);
         if (pl.xp) {
@@ -356,14 +354,8 @@ class Engine {
         M.out_dev = out_dev;
         M.res.status = GABP_OK;
         M.res.alpha = out_alpha;
-        // tile list of the instance (inst field = its slot in the table)
-        std::vector<int4> wl((size_t)M.ntiles);
-        size_t k = 0;
-        for (int I = 0; I < p.Nt; ++I)
-            for (int J = I; J < p.Nt; ++J, ++k) wl[k] = make_int4(slot, I, J, (int)k);
         EK(cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), s));
         EK(cudaMemcpyAsync(d_tab + slot, &p, sizeof(Inst), cudaMemcpyHostToDevice, s));
-        EK(cudaMemcpyAsync(M.work, wl.data(), wl.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
         EK(cudaMemcpyAsync((void*)p.y, pr.y, (size_t)n * 4, ptr_mode ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
         if (pl.xp) EK(cudaMemsetAsync((void*)p.Xp, 0, pl.xp, s));   // padding rows and features stay 0
         if (!x_f64) {
@@ -828,7 +820,11 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
         E.mem[(size_t)k].tol = tol;
         E.mem[(size_t)k].refine_left = o.q_mode != 0 ? o.refine : 0;
         E.mem[(size_t)k].ticket = k;
+        // formation of each group of instances starts while the next are added
+        if ((k + 1) % 64 == 0)
+            if (gabp_status st = E.form_pending()) return st;
     }
+    ph.add_ms = ms_since(t0);
     if (gabp_status st = E.form_pending()) return st;
     if (cudaStreamSynchronize(E.side) != cudaSuccess) return E.fail(GABP_ECUDA, "formation failed");
     // labels / features validated by the staging kernels
@@ -879,16 +875,17 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
     return worst;
 }
 
-gabp_status gabp_batch_last_phases(double* out6)
+gabp_status gabp_batch_last_phases(double* out7)
 {
-    if (!out6) return GABP_EINVAL;
+    if (!out7) return GABP_EINVAL;
     const gabp::BatchPhases& p = gabp::g_last_phases;
-    out6[0] = p.form_ms;
-    out6[1] = p.tune_ms;
-    out6[2] = p.rounds_ms;
-    out6[3] = p.stop_ms;
-    out6[4] = p.total_ms;
-    out6[5] = (double)p.chunks;
+    out7[0] = p.form_ms;
+    out7[1] = p.tune_ms;
+    out7[2] = p.rounds_ms;
+    out7[3] = p.stop_ms;
+    out7[4] = p.total_ms;
+    out7[5] = (double)p.chunks;
+    out7[6] = p.add_ms;
     return GABP_OK;
 }
 

@@ -362,9 +362,9 @@ def batch_solve(problems, iters: int, tol: float, **opts):
 
 
 def batch_last_phases() -> dict:
-    out = np.zeros(6)
+    out = np.zeros(7)
     _check(load().gabp_batch_last_phases(_ptr(out)))
-    return dict(zip(["form_ms", "tune_ms", "rounds_ms", "stop_ms", "total_ms", "chunks"], out.tolist()))
+    return dict(zip(["form_ms", "tune_ms", "rounds_ms", "stop_ms", "total_ms", "chunks", "add_ms"], out.tolist()))
 
 
 class Server:
