@@ -44,9 +44,20 @@ def test_argument_errors_before_device_work(lib):
     o = gabp.opts_default(q_mode=7)
     assert lib.gabp_svm_create_ex(V(X.ctypes.data), V(y.ctypes.data), 4, 3, 1.0, 1.0,
                                   ctypes.byref(o), ctypes.byref(h)) == gabp.EINVAL
-    # null handles
+    for bad in (dict(task=2), dict(stages=17), dict(stages=-1), dict(msg_bf16=1), dict(refine=65)):
+        o = gabp.opts_default(**bad)
+        assert lib.gabp_svm_create_ex(V(X.ctypes.data), V(y.ctypes.data), 4, 3, 1.0, 1.0,
+                                      ctypes.byref(o), ctypes.byref(h)) == gabp.EINVAL, bad
+    cfg = gabp.ServerCfg()
+    cfg.max_members = 4
+    cfg.opts = gabp.opts_default(stages=99)
+    srv = ctypes.c_void_p()
+    assert lib.gabp_server_create(ctypes.byref(cfg), ctypes.byref(srv)) == gabp.EINVAL
+    # null handles and outputs
     assert lib.gabp_svm_solve(None, 1, 0.0, None, None, None) == gabp.EINVAL
     assert lib.gabp_svm_destroy(None) == gabp.OK
+    assert lib.gabp_server_completed(None, None, 0, None) == gabp.EINVAL
+    assert lib.gabp_server_phases(None, None) == gabp.EINVAL
 
 
 def test_no_gpu_fails_loudly(lib):
