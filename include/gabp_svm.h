@@ -114,7 +114,13 @@ typedef struct {
                               every pair once, in S stages over bands of tile columns, and later stages
                               use the aggregates of the earlier ones (Section 3.2: GaBP also converges
                               under non-synchronous schedules).  Same fixed point, fewer rounds */
-    int32_t reserved[2];
+    float   sparse_tau;    /* tile-sparse kernel (Section 6's sparsified kernel, at the granularity of the
+                              128 x 128 tiles): every off-diagonal tile whose largest |Q_ij| <= sparse_tau
+                              is dropped, i.e. solved as 0 (its messages stay 0 and are never swept);
+                              the diagonal rule then uses the kept entries.  Effective when rows are
+                              ordered so that near points share tiles.  0 = dense (default).  Single-
+                              instance API only (not the batched or served forms) */
+    int32_t reserved[1];
 } gabp_svm_opts;
 
 typedef struct gabp_svm_s* gabp_svm_t;
@@ -132,6 +138,8 @@ typedef struct {
     int64_t device_bytes;      /* device memory held by the handle */
     int32_t q_mode, diag_rule;
     int32_t refine_passes;     /* defect-correction passes done by the last solve */
+    int64_t tiles_total;       /* upper-triangle 128 x 128 tiles of Q */
+    int64_t tiles_kept;        /* tiles swept (all of them unless sparse_tau > 0) */
 } gabp_svm_stats;
 
 /* Default options. */

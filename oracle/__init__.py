@@ -337,3 +337,34 @@ def gabp_staged(Q, b=None, iters=100, tol=0.0, stages=2, block=128, keep_message
         Pin.ctypes.data_as(P) if keep_messages else None, Hin.ctypes.data_as(P) if keep_messages else None)
     _check(rc, "gabp_staged")
     return GabpResult(mu, Pt, k.value, rinf.value, rhist[:k.value + 1], Pin, Hin)
+
+
+def build_q_tile_sparse(X, y, gamma, C, tau, block=128, lam=None, diag_rule=DIAG_DOMINANT, delta=0.1):
+    """The SVM matrix with the tile-sparse reading of Section 6's sparsified
+    kernel: the off-diagonal entries are grouped in block x block tiles of the
+    upper triangle (and their mirrors); a tile whose largest |Q_ij| is <= tau
+    is dropped (all its entries 0), diagonal tiles are always kept, and the
+    diagonal rule is applied to the kept entries.  Returns (Q, keep) with
+    keep[I, J] for I <= J."""
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
+    lam_v = default_lambda(n) if lam is None else lam
+    Q = build_q(X, y, gamma, C, lam_v, diag_rule, delta)
+    nt = (n + block - 1) // block
+    keep = np.zeros((nt, nt), dtype=bool)
+    for I in range(nt):
+        for J in range(I, nt):
+            sl_i, sl_j = slice(I * block, (I + 1) * block), slice(J * block, (J + 1) * block)
+            B = np.abs(Q[sl_i, sl_j])
+            if I == J:
+                B = np.triu(B, 1)
+            keep[I, J] = I == J or B.max() > tau
+            if not keep[I, J]:
+                Q[sl_i, sl_j] = 0.0
+                Q[sl_j, sl_i] = 0.0
+    A = np.abs(Q)
+    np.fill_diagonal(A, 0.0)
+    R = np.cumsum(A, axis=1)[:, -1]   # sequential row sums, in the order build_q takes them
+    for i in range(n):
+        Q[i, i] = q_diag(R[i], lam_v, C, diag_rule, delta)
+    return Q, keep

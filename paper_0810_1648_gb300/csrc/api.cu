@@ -63,7 +63,9 @@ struct gabp_svm_s {
     size_t pool_bytes = 0;
     Inst inst{};
     Inst* d_tab = nullptr;          // device copy of inst (a one-instance batch)
-    int4* work = nullptr;           // tile list {0, I, J, L}
+    int4* work_all = nullptr;       // every tile {0, I, J, L}, row by row (formation)
+    int4* work = nullptr;           // the swept tiles, grouped by stage (= work_all's tiles when dense)
+    long long nlive = 0;            // tiles in `work`
     int2* nbl = nullptr;            // node blocks {0, b}
     Sched* sched = nullptr;   // one per stage
     int nstages = 1;
@@ -100,12 +102,14 @@ gabp_status check_handle(gabp_svm_t h)
 
 // Device memory plan of one handle (bytes, 256-aligned sub-buffers).
 struct Plan {
-    size_t X, vec, agg, part, state, q, qref, work, ctrl, rhist, final3, blockbuf, xp, tab, nbl, total;
+    size_t X, vec, agg, part, state, q, qref, work, tilemax, ctrl, rhist, final3, blockbuf, xp, tab, nbl, total;
 };
 
-Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_mode, int msg_bf16)
+Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_mode, int msg_bf16, bool sparse)
 {
     Plan p{};
+    // the tile-sparse option keeps a second tile list (the swept tiles) and the tile maxima
+    p.tilemax = sparse ? align_up((size_t)ntiles * sizeof(float), 256) : 0;
     p.xp = q_mode != GABP_Q_F32 ? align_up(bf16_pack_bytes(Nt, (int)m), 1024) : 0;
     p.X = align_up((size_t)n * m * sizeof(float), 256);
     p.vec = align_up((size_t)npad * sizeof(float), 256);
@@ -117,14 +121,14 @@ Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_m
         : 0;
     // the BF16 store keeps an FP32 copy for the refinement residuals
     p.qref = q_mode == GABP_Q_BF16 ? align_up((size_t)ntiles * TT * sizeof(float), 256) : 0;
-    p.work = align_up((size_t)ntiles * sizeof(int4), 256);
+    p.work = (sparse ? 2 : 1) * align_up((size_t)ntiles * sizeof(int4), 256);
     p.tab = align_up(align_up(sizeof(Inst), 16) + kMaxStages * align_up(sizeof(Sched), 16) + sizeof(StopOp) + 64, 256);
     p.nbl = align_up((size_t)((n + 31) / 32) * sizeof(int2), 256);
     p.ctrl = align_up(sizeof(Ctrl), 256);
     p.rhist = align_up((size_t)kRhistCap * sizeof(double), 256);
     p.final3 = 256;
     p.blockbuf = align_up((size_t)3 * ((n + 31) / 32) * sizeof(double), 256);
-    p.total = p.X + 10 * p.vec + p.agg + p.part + p.state + p.q + p.qref + p.work + p.ctrl + p.rhist +
+    p.total = p.X + 10 * p.vec + p.agg + p.part + p.state + p.q + p.qref + p.work + p.tilemax + p.ctrl + p.rhist +
               p.final3 + p.blockbuf + p.xp + p.tab + p.nbl + 1024;
     return p;
 }
@@ -136,6 +140,58 @@ void clear_graphs(gabp_svm_t h)
         for (auto e : kv.second.ev) cudaEventDestroy(e);
     }
     h->graphs.clear();
+}
+
+// The swept tile list after formation.  Dense: every tile (the list built at
+// create, grouped by stage).  Tile-sparse: the diagonal tiles and every tile
+// whose largest |Q_ij| exceeds sparse_tau, grouped by stage; the dropped
+// tiles' |Q| row sums are zeroed so that the diagonal rule sees the kept
+// entries.  Must run between the FP32 formation and the diagonal rule.
+gabp_status build_sweep_list(gabp_svm_t h)
+{
+    h->stats.tiles_total = h->ntiles;
+    if (!(h->opts.sparse_tau > 0)) {
+        h->nlive = h->ntiles;
+        h->stats.tiles_kept = h->ntiles;
+        return GABP_OK;
+    }
+    cudaStream_t s = h->stream;
+    std::vector<float> mx((size_t)h->ntiles);
+    CK(cudaMemcpyAsync(mx.data(), h->inst.tilemax, mx.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int Nt = h->Nt;
+    auto L_of = [Nt](int I, int J) { return (long long)I * Nt - (long long)I * (I - 1) / 2 + (J - I); };
+    const float tau = h->opts.sparse_tau;
+    std::vector<int4> wl, dropped;
+    int B[kMaxStages + 1];
+    stage_bounds(Nt, h->nstages, B);
+    const int nblk = (int)((h->n + 31) / 32);
+    Sched sc[kMaxStages];
+    for (int st = 0; st < h->nstages; ++st) {
+        const long long off = (long long)wl.size();
+        for (int I = 0; I < Nt; ++I)
+            for (int J = std::max(I, B[st]); J < B[st + 1]; ++J) {
+                const long long L = L_of(I, J);
+                const int4 t = make_int4(0, I, J, (int)L);
+                if (I == J || mx[(size_t)L] > tau) wl.push_back(t);
+                else dropped.push_back(t);
+            }
+        sc[st] = Sched{(long long)wl.size() - off, nblk, 1, off};
+    }
+    h->nlive = (long long)wl.size();
+    h->stats.tiles_kept = h->nlive;
+    CK(cudaMemcpyAsync(h->work, wl.data(), wl.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->sched, sc, (size_t)h->nstages * sizeof(Sched), cudaMemcpyHostToDevice, s));
+    if (!dropped.empty()) {
+        int4* d = nullptr;
+        CK(cudaMallocAsync((void**)&d, dropped.size() * sizeof(int4), s));
+        CK(cudaMemcpyAsync(d, dropped.data(), dropped.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+        launch_zero_tile_sums(h->d_tab, d, (long long)dropped.size(), s);
+        CK(cudaGetLastError());
+        CK(cudaFreeAsync(d, s));
+    }
+    CK(cudaStreamSynchronize(s));   // the host lists go out of scope
+    return GABP_OK;
 }
 
 gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
@@ -185,8 +241,9 @@ gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
                                                                 : "row %lld: non-finite feature or label not +-1",
                     (long long)h->hctrl->bad_index);
     if (h->opts.q_mode == GABP_Q_F32) {
-        launch_form_q(h->d_tab, h->work, h->ntiles, s);
+        launch_form_q(h->d_tab, h->work_all, h->ntiles, s);
         CK(cudaGetLastError());
+        if (gabp_status st = build_sweep_list(h)) return st;
         launch_init(p, h->opts.diag_rule, (float)h->delta, s);
         h->prof.kernel_launches += 2;
         CK(cudaGetLastError());
@@ -196,13 +253,14 @@ gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
         // FP32 copy for its refinement residuals; the off-diagonal entries
         // the sweeps read come from the BF16 tensor-core Gram.
         CK(launch_pack_bf16(p.X, (int)n, (int)m, p.nkc, h->Nt, (void*)p.Xp, (float*)p.sqb, s));
-        launch_form_q(h->d_tab, h->work, h->ntiles, s);
+        launch_form_q(h->d_tab, h->work_all, h->ntiles, s);
         CK(cudaGetLastError());
+        if (gabp_status st = build_sweep_list(h)) return st;
         launch_init(p, h->opts.diag_rule, (float)h->delta, s);
         CK(cudaGetLastError());
         h->prof.kernel_launches += 4;
         if (h->opts.q_mode == GABP_Q_BF16) {
-            CK(launch_form_q_tc(h->d_tab, h->work, h->ntiles, s));
+            CK(launch_form_q_tc(h->d_tab, h->work_all, h->ntiles, s));
             h->prof.kernel_launches += 1;
         }
     }
@@ -359,6 +417,7 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
         return fail(GABP_EINVAL, "msg_bf16 = 1 needs a precision form (q_mode BF16 or recompute)");
     if (o.task != GABP_TASK_SVM && o.task != GABP_TASK_KRR) return fail(GABP_EINVAL, "unknown task %d", o.task);
     if (o.stages < 0 || o.stages > kMaxStages) return fail(GABP_EINVAL, "stages must be in [0, %d]", kMaxStages);
+    if (!(o.sparse_tau >= 0) || !std::isfinite(o.sparse_tau)) return fail(GABP_EINVAL, "sparse_tau must be >= 0");
 
     int dev = 0, ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -380,7 +439,7 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     h->delta = o.diag_delta;
     h->nstages = o.stages > 1 ? o.stages : 1;
 
-    const Plan pl = make_plan(n, m, h->Nt, h->ntiles, h->npad, o.q_mode, o.msg_bf16);
+    const Plan pl = make_plan(n, m, h->Nt, h->ntiles, h->npad, o.q_mode, o.msg_bf16, o.sparse_tau > 0);
     size_t free_b = 0, total_b = 0;
     e = cudaMemGetInfo(&free_b, &total_b);
     if (e != cudaSuccess) { destroy_all(h); return fail(GABP_ECUDA, "cudaMemGetInfo: %s", cudaGetErrorString(e)); }
@@ -434,7 +493,13 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     p.msg_bf16 = o.msg_bf16;
     p.qstore = pl.q ? take(pl.q) : nullptr;
     p.qref = pl.qref ? (float*)take(pl.qref) : (o.q_mode == GABP_Q_F32 ? (float*)p.qstore : nullptr);
-    h->work = (int4*)take(pl.work);
+    if (o.sparse_tau > 0) {
+        h->work_all = (int4*)take(pl.work / 2);
+        h->work = (int4*)take(pl.work / 2);
+        p.tilemax = (float*)take(pl.tilemax);
+    } else {
+        h->work = h->work_all = (int4*)take(pl.work);   // formation walks the swept list
+    }
     {
         char* tb = (char*)take(pl.tab);
         h->d_tab = (Inst*)tb;
@@ -473,7 +538,8 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     std::vector<int2> nb((size_t)nblk);
     for (int b = 0; b < nblk; ++b) nb[(size_t)b] = make_int2(0, b);
     h->grid = round_grid(h->ntiles, nblk, o.q_mode, 0, o.msg_bf16);
-    e = cudaMemcpyAsync(h->work, wl.data(), wl.size() * sizeof(int4), cudaMemcpyHostToDevice, h->stream);
+    h->nlive = h->ntiles;
+    e = cudaMemcpyAsync(h->work_all, wl.data(), wl.size() * sizeof(int4), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->nbl, nb.data(), nb.size() * sizeof(int2), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->sched, sc, (size_t)h->nstages * sizeof(Sched), cudaMemcpyHostToDevice, h->stream);
@@ -540,7 +606,7 @@ gabp_status gabp_svm_solve(gabp_svm_t h, int32_t iters, double tol, float* alpha
     auto final_pass = [&](const StopOp& o) -> gabp_status {
         CK(cudaMemcpyAsync(h->d_ops, &o, sizeof(StopOp), cudaMemcpyHostToDevice, s));
         if (o.acc) launch_axpy_list(h->d_tab, h->d_ops, h->nbl, nblk, s);
-        launch_final(h->d_tab, h->d_ops, h->work, h->ntiles, h->nbl, nblk, h->d_members, 1, nullptr,
+        launch_final(h->d_tab, h->d_ops, h->work, h->nlive, h->nbl, nblk, h->d_members, 1, nullptr,
                      h->inst.qref != nullptr, s);
         h->prof.kernel_launches += o.acc ? 4 : 3;
         CK(cudaGetLastError());
@@ -751,7 +817,7 @@ gabp_status gabp_svm_get_q(gabp_svm_t h, float* Q)
     float* d = nullptr;
     CK(cudaMallocAsync((void**)&d, bytes, h->stream));
     CK(cudaMemsetAsync(d, 0, bytes, h->stream));
-    launch_get_q(h->inst, h->work, h->ntiles, h->opts.q_mode == GABP_Q_BF16, d, h->stream);
+    launch_get_q(h->inst, h->work, h->nlive, h->opts.q_mode == GABP_Q_BF16, d, h->stream);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(Q, d, bytes, h->opts.ptr_mode == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,

@@ -780,6 +780,7 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
     if (o.diag_delta == 0) o.diag_delta = 0.1;
     if (o.q_mode < 0 || o.q_mode > 2 || o.refine < 0 || o.refine > 64 || o.msg_bf16 < 0 || o.msg_bf16 > 1 ||
         (o.msg_bf16 && o.q_mode == 0) || o.task < 0 || o.task > 1 || o.stages < 0 || o.stages > kMaxStages ||
+        o.sparse_tau != 0.f ||
         (o.bias_mode == 1 && (!(o.bias_lambda >= 0) || !std::isfinite(o.bias_lambda)))) {
         set_last_error("gabp_batch_solve: bad q_mode, refine, msg_bf16, task or bias");
         return GABP_EINVAL;
@@ -915,7 +916,7 @@ gabp_status gabp_server_create(const gabp_server_cfg* cfg, gabp_server_t* out)
     if (c.max_members <= 0) c.max_members = 64;
     if (c.max_members > 4096 || c.iters < 0 || std::isnan(c.tol) || c.opts.q_mode < 0 || c.opts.q_mode > 2 ||
         (c.opts.msg_bf16 && c.opts.q_mode == 0) || c.opts.task < 0 || c.opts.task > 1 || c.opts.stages < 0 ||
-        c.opts.stages > kMaxStages ||
+        c.opts.stages > kMaxStages || c.opts.sparse_tau != 0.f ||
         (c.opts.bias_mode == 1 && (!(c.opts.bias_lambda >= 0) || !std::isfinite(c.opts.bias_lambda)))) {
         set_last_error("gabp_server_create: bad configuration");
         return GABP_EINVAL;

@@ -76,6 +76,7 @@ struct Inst {
     void* Pst;        // ntiles * TT precision messages {P_ij, P_ji} (float2, or bf16x2 when msg_bf16)
     void* Hst;        // ntiles * TT information messages {H_ij, H_ji}
     void* qstore;     // ntiles * TT values of Q (float or bf16), or nullptr
+    float* tilemax;   // per tile, the largest off-diagonal |Q_ij| (tile-sparse option), or nullptr
     float* qref;      // ntiles * TT FP32 values of Q for the residual passes (the FP32
                       // store itself, a separate copy beside the BF16 store, or nullptr
                       // when Q is recomputed)
@@ -167,6 +168,9 @@ void launch_stage(const void* X, int x_f64, int n, int m, float* y, float* Xf, f
 inline double refine_handover(float opt, int msg_bf16) { return opt > 0 ? opt : (msg_bf16 ? 1e-3 : 1e-4); }
 inline double refine_inner(float opt, int msg_bf16) { return opt > 0 ? opt : (msg_bf16 ? 3e-2 : 1e-2); }
 
+// Tile-sparse option: the |Q| row-sum partials of the listed (dropped) tiles
+// := 0, so that the diagonal rule sees the kept entries only.
+void launch_zero_tile_sums(const Inst* tab, const int4* tiles, long long ntiles, cudaStream_t s);
 // Q formation (FP32 SIMT Gram fused with exp, labels and bias) + |Q| row-sum partials;
 // the FP32 tiles are stored into Inst::qref where it is set (the FP32 store, or the
 // FP32 copy the BF16 store keeps for its refinement residuals).
@@ -237,6 +241,13 @@ __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_max_f(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 

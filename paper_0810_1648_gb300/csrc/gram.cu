@@ -224,6 +224,7 @@ __global__ void __launch_bounds__(NTHREADS) k_form_q(const Inst* __restrict__ ta
     float rs[1][8], cs[1][8];
 #pragma unroll
     for (int b = 0; b < 8; ++b) cs[0][b] = 0.f;
+    float tmx = 0.f;    // largest |Q_ij| of the thread's pairs (the tile-sparse option)
     float* qt = p.qref ? p.qref + (size_t)L * TT : nullptr;   // FP32 Q kept for the sweeps / residuals
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
@@ -239,6 +240,7 @@ __global__ void __launch_bounds__(NTHREADS) k_form_q(const Inst* __restrict__ ta
             out[b] = v ? q : 0.f;
             racc += fabsf(out[b]);
             cs[0][b] += fabsf(out[b]);
+            tmx = fmaxf(tmx, fabsf(out[b]));
         }
         rs[0][a] = racc;
         if (qt) {
@@ -250,6 +252,18 @@ __global__ void __launch_bounds__(NTHREADS) k_form_q(const Inst* __restrict__ ta
     float* const parts[1] = {p.part};
     __syncthreads();   // Gram smem is reused by the epilogue
     reduce_and_write<1>(sm.e, rs, cs, parts, n, I, J);
+    if (p.tilemax) {
+        // largest |Q_ij| of the tile's pairs (the tile-sparse option)
+        const float mx = warp_max_f(tmx);
+        __syncthreads();
+        if ((tid & 31) == 0) sm.e.rowv[0][tid >> 5] = mx;
+        __syncthreads();
+        if (tid == 0) {
+            float m2 = 0.f;
+            for (int w = 0; w < NWARPS; ++w) m2 = fmaxf(m2, sm.e.rowv[0][w]);
+            p.tilemax[L] = m2;
+        }
+    }
 }
 
 // ------------------------------------------- final residual and Q alpha
@@ -489,6 +503,21 @@ __global__ void k_decision_sum(const float* __restrict__ part, int t, int Ntrain
 }
 
 // ---------------------------------------------------------------- inspection
+// Tile-sparse option: the dropped tiles' |Q| row-sum partials := 0 (rows of
+// block I in slot J, columns of block J in slot I; slot I of both on the
+// diagonal, which is never dropped).  One CTA per listed tile.
+__global__ void k_zero_tile_sums(const Inst* __restrict__ tab, const int4* __restrict__ tiles)
+{
+    const int4 w = tiles[blockIdx.x];
+    const Inst& p = tab[w.x];
+    const int I = w.y, J = w.z, n = p.n;
+    for (int c = threadIdx.x; c < T; c += blockDim.x) {
+        const int xr = I * T + c, xc = J * T + c;
+        if (xr < n) p.part[(size_t)J * n + xr] = 0.f;
+        if (xc < n) p.part[(size_t)I * n + xc] = 0.f;
+    }
+}
+
 __global__ void k_get_q(Inst p, const int4* __restrict__ work, int q_bf16, float* __restrict__ Qd)
 {
     const long long L = work[blockIdx.x].w;
@@ -510,6 +539,11 @@ __global__ void k_get_q(Inst p, const int4* __restrict__ work, int q_bf16, float
 }
 
 }  // namespace
+
+void launch_zero_tile_sums(const Inst* tab, const int4* tiles, long long ntiles, cudaStream_t s)
+{
+    if (ntiles > 0) k_zero_tile_sums<<<(unsigned)ntiles, 128, 0, s>>>(tab, tiles);
+}
 
 void launch_stage_list(const Inst* tab, const int2* nbl, int nblocks, cudaStream_t s)
 {

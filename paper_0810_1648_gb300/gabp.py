@@ -44,7 +44,8 @@ class Opts(ctypes.Structure):
                 ("refine", ctypes.c_int32), ("sv_threshold", ctypes.c_double),
                 ("chunk", ctypes.c_int32), ("msg_bf16", ctypes.c_int32),
                 ("refine_handover", ctypes.c_float), ("refine_inner", ctypes.c_float),
-                ("task", ctypes.c_int32), ("stages", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("task", ctypes.c_int32), ("stages", ctypes.c_int32), ("sparse_tau", ctypes.c_float),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class Profile(ctypes.Structure):
@@ -63,7 +64,8 @@ class Stats(ctypes.Structure):
                 ("n_support", ctypes.c_int64), ("lambda_", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("C", ctypes.c_double), ("diag_delta", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("q_mode", ctypes.c_int32),
-                ("diag_rule", ctypes.c_int32), ("refine_passes", ctypes.c_int32)]
+                ("diag_rule", ctypes.c_int32), ("refine_passes", ctypes.c_int32),
+                ("tiles_total", ctypes.c_int64), ("tiles_kept", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

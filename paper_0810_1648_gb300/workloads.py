@@ -18,6 +18,8 @@ generators stand in for them):
                       from {8, 32, 128, 256}, a C x gamma grid per data set.
 * ``poisson_requests`` arrival times and shapes of a stream of training
                       requests.
+* ``clustered_mixture`` the mixture with rows grouped by component (the
+                      input order the tile-sparse option needs).
 * ``krr_targets``     real regression targets for the kernel ridge
                       regression task: a smooth random function of the
                       features plus noise.
@@ -82,6 +84,22 @@ def mixture(n: int, m: int, seed: int, gamma: float | None = None, C: float = 1.
     g = (1.0 / m) if gamma is None else gamma
     return Problem(X[perm].astype(dtype), y[perm].copy(), g, C,
                    f"mixture_n{n}_m{m}_s{seed}")
+
+
+def clustered_mixture(n: int, m: int, seed: int, gamma: float, C: float = 1.0, comps: int = 3,
+                      sigma: float = 0.7) -> Problem:
+    """The mixture above with its rows grouped by component (class, then
+    component), so that points that are near share 128-row tiles: the input
+    order under which a narrow kernel leaves whole tiles near zero."""
+    rng = np.random.default_rng(seed)
+    y = _labels(n)
+    means = rng.standard_normal((2, comps, m))
+    cls = (y < 0).astype(np.int64)
+    comp = rng.integers(0, comps, size=n)
+    X = means[cls, comp] + sigma * rng.standard_normal((n, m))
+    order = np.lexsort((rng.random(n), comp, cls))
+    return Problem(X[order].astype(np.float32), y[order].copy(), gamma, C,
+                   f"clustered_n{n}_m{m}_s{seed}")
 
 
 # The five workloads, by what they are.

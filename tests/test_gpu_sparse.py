@@ -1,0 +1,102 @@
+"""Tile-sparse kernel (Section 6's sparsified kernel at the granularity of the
+128 x 128 tiles) against the oracle's tile-sparse matrix.
+
+Which tiles are dropped is decided by a comparison of each tile's largest
+|Q_ij| with tau, in FP32 on the GPU and FP64 in the oracle; the test data and
+tau are chosen with a wide gap in the tile maxima around tau (checked), so
+both sides keep the same tiles.  Then the bars of the dense form apply:
+relative mean error 2e-5, |dalpha|_inf <= 1e-4 C, Q entries 1e-5 of max |Q|.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0810_1648_gb300 import gabp, workloads
+
+pytestmark = pytest.mark.gpu
+
+REL = 2e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_0810_1648_gb300 import build as gbuild
+    gbuild.build()
+
+
+def _case(n, m, gamma, tau, seed=3):
+    p = workloads.clustered_mixture(n, m, seed=seed, gamma=gamma)
+    X, y = p.X.astype(np.float64), p.y.astype(np.float64)
+    Qd = oracle.build_q(X, y, p.gamma, p.C)
+    nt = math.ceil(n / 128)
+    mx = [np.abs(Qd[I * 128:(I + 1) * 128, J * 128:(J + 1) * 128]).max()
+          for I in range(nt) for J in range(I + 1, nt)]
+    assert not any(tau / 5 <= v <= tau * 5 for v in mx)   # no tile near the threshold
+    Q, keep = oracle.build_q_tile_sparse(X, y, p.gamma, p.C, tau)
+    return p, Q, keep
+
+
+def _rel(a, b):
+    return np.max(np.abs(np.asarray(a, np.float64) - b)) / np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("n,m,gamma,tau", [(1500, 64, 0.15, 1e-4), (2000, 32, 0.25, 3e-3)])
+def test_tile_sparse_matches_oracle(n, m, gamma, tau):
+    p, Q, keep = _case(n, m, gamma, tau)
+    s = gabp.GabpSVM(p.X, p.y, p.gamma, p.C, sparse_tau=tau)
+    st = s.stats()
+    assert st["tiles_total"] == keep.shape[0] * (keep.shape[0] + 1) // 2
+    assert st["tiles_kept"] == int(keep[np.triu_indices(keep.shape[0])].sum()) < st["tiles_total"]
+    Qg = gabp.svm_get_q(s.h, n).astype(np.float64)
+    assert np.max(np.abs(Qg - Q)) / np.max(np.abs(Q)) <= 1e-5
+    assert np.all(Qg[Q == 0] == 0)
+    for iters in (1, 10):
+        s2 = gabp.GabpSVM(p.X, p.y, p.gamma, p.C, sparse_tau=tau)
+        alpha, rinf, k = s2.solve(iters, 0.0)
+        r = oracle.gabp(Q, np.ones(n), iters=iters)
+        assert _rel(s2.mean(), r.mu) <= REL
+        assert np.max(np.abs(alpha.astype(np.float64) - r.alpha(p.C))) <= 1e-4 * p.C
+    alpha, rinf, k = s.solve(300, 1e-6)
+    r = oracle.gabp(Q, np.ones(n), iters=300, tol=1e-6)
+    assert abs(k - r.kstar) <= 1 and s.stats()["converged"] == 1
+    assert _rel(s.mean(), np.linalg.solve(Q, np.ones(n))) <= REL
+
+
+def test_threshold_below_every_entry_is_the_dense_solve():
+    p = workloads.clustered_mixture(900, 16, seed=4, gamma=0.1)
+    a0, _, _ = gabp.GabpSVM(p.X, p.y, p.gamma, p.C).solve(15, 0.0)
+    s = gabp.GabpSVM(p.X, p.y, p.gamma, p.C, sparse_tau=1e-30)
+    a1, _, _ = s.solve(15, 0.0)
+    np.testing.assert_array_equal(a0, a1)
+    assert s.stats()["tiles_kept"] == s.stats()["tiles_total"]
+
+
+@pytest.mark.parametrize("kw", [dict(stages=4), dict(q_mode=gabp.Q_BF16, refine=10, msg_bf16=1),
+                                dict(q_mode=gabp.Q_RECOMPUTE, refine=10)])
+def test_tile_sparse_with_other_options(kw):
+    p, Q, keep = _case(1500, 64, 0.15, 1e-4)
+    s = gabp.GabpSVM(p.X, p.y, p.gamma, p.C, sparse_tau=1e-4, **kw)
+    alpha, rinf, k = s.solve(300, 1e-6)
+    assert s.stats()["converged"] == 1 and rinf < 1.1e-6
+    assert _rel(s.mean(), np.linalg.solve(Q, np.ones(p.n))) <= REL
+
+
+def test_tile_sparse_refit_rebuilds_the_kept_list():
+    p, Q, keep = _case(1500, 64, 0.15, 1e-4)
+    s = gabp.GabpSVM(p.X, p.y, p.gamma, p.C, sparse_tau=1e-4)
+    kept = s.stats()["tiles_kept"]
+    q = workloads.mixture(1500, 64, seed=9, gamma=0.15)     # unordered rows: nothing to drop
+    s.refit(q.X, q.y, q.gamma, q.C)
+    assert s.stats()["tiles_kept"] > kept
+    a1, _, _ = s.solve(12, 0.0)
+    a2, _, _ = gabp.GabpSVM(q.X, q.y, q.gamma, q.C, sparse_tau=1e-4).solve(12, 0.0)
+    np.testing.assert_array_equal(a1, a2)
+
+
+def test_batched_forms_reject_the_tile_sparse_option():
+    p = workloads.mixture(200, 8, seed=1)
+    with pytest.raises(gabp.GabpError) as ei:
+        gabp.batch_solve([p], 10, 0.0, sparse_tau=1e-4)
+    assert ei.value.status == gabp.EINVAL

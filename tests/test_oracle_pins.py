@@ -421,3 +421,33 @@ def test_staged_schedule_needs_fewer_rounds_on_the_svm_matrix():
     k1 = oracle.gabp(Q, np.ones(p.n), iters=500, tol=1e-8).kstar
     k4 = oracle.gabp_staged(Q, np.ones(p.n), iters=500, tol=1e-8, stages=4, block=128).kstar
     assert k4 < k1 < 500
+
+
+# ------------------------------------------------------------ tile-sparse kernel
+def test_tile_sparse_matrix_pins():
+    p = workloads.clustered_mixture(1500, 64, seed=3, gamma=0.15)
+    X, y = p.X.astype(np.float64), p.y.astype(np.float64)
+    Qd = oracle.build_q(X, y, p.gamma, p.C)
+    # a threshold below every entry keeps the dense matrix
+    Q0, keep0 = oracle.build_q_tile_sparse(X, y, p.gamma, p.C, 0.0)
+    np.testing.assert_array_equal(Q0, Qd)
+    assert keep0.sum() == keep0.shape[0] * (keep0.shape[0] + 1) // 2
+    tau = 1e-4
+    Q, keep = oracle.build_q_tile_sparse(X, y, p.gamma, p.C, tau)
+    assert 0 < (~keep[np.triu_indices(keep.shape[0], 1)]).sum()
+    np.testing.assert_array_equal(Q, Q.T)
+    off = ~np.eye(p.n, dtype=bool)
+    kept = Q[off] != 0
+    np.testing.assert_array_equal(Q[off][kept], Qd[off][kept])      # kept entries unchanged
+    assert np.abs(Qd[off][~kept]).max() <= tau                       # dropped ones were small
+    # the diagonal rule on fewer entries: between the floor and the dense diagonal
+    floor = 1.0 + (1.0 / p.n) ** 2 + 1.0 / p.C
+    assert np.all(np.diag(Q) >= floor - 1e-12) and np.all(np.diag(Q) <= np.diag(Qd) + 1e-12)
+    # soft2: the diagonal does not depend on the entries at all
+    Qs, _ = oracle.build_q_tile_sparse(X, y, p.gamma, p.C, tau, diag_rule=oracle.DIAG_SOFT2)
+    Qsd = oracle.build_q(X, y, p.gamma, p.C, diag_rule=oracle.DIAG_SOFT2)
+    np.testing.assert_array_equal(np.diag(Qs), np.diag(Qsd))
+    # GaBP on the sparse matrix reaches its linear solve
+    r = oracle.gabp(Q, np.ones(p.n), iters=500, tol=1e-12)
+    assert r.kstar < 500
+    np.testing.assert_allclose(r.mu, np.linalg.solve(Q, np.ones(p.n)), rtol=1e-9, atol=1e-12)
