@@ -117,7 +117,8 @@ typedef struct {
     float   sparse_tau;    /* tile-sparse kernel (Section 6's sparsified kernel, at the granularity of the
                               128 x 128 tiles): every off-diagonal tile whose largest |Q_ij| <= sparse_tau
                               is dropped, i.e. solved as 0 (its messages stay 0 and are never swept);
-                              the diagonal rule then uses the kept entries.  Effective when rows are
+                              the diagonal keeps the row sums of the whole matrix, so the matrix stays
+                              diagonally dominant and only the dropped entries change.  Effective when rows are
                               ordered so that near points share tiles.  0 = dense (default).  Single-
                               instance API only (not the batched or served forms) */
     int32_t reserved[1];

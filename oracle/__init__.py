@@ -344,8 +344,9 @@ def build_q_tile_sparse(X, y, gamma, C, tau, block=128, lam=None, diag_rule=DIAG
     kernel: the off-diagonal entries are grouped in block x block tiles of the
     upper triangle (and their mirrors); a tile whose largest |Q_ij| is <= tau
     is dropped (all its entries 0), diagonal tiles are always kept, and the
-    diagonal rule is applied to the kept entries.  Returns (Q, keep) with
-    keep[I, J] for I <= J."""
+    diagonal keeps its value from the whole matrix (the rule on all row sums),
+    so only the dropped entries change.  Returns (Q, keep) with keep[I, J] for
+    I <= J."""
     X = np.asarray(X, dtype=np.float64)
     n = X.shape[0]
     lam_v = default_lambda(n) if lam is None else lam
@@ -362,9 +363,4 @@ def build_q_tile_sparse(X, y, gamma, C, tau, block=128, lam=None, diag_rule=DIAG
             if not keep[I, J]:
                 Q[sl_i, sl_j] = 0.0
                 Q[sl_j, sl_i] = 0.0
-    A = np.abs(Q)
-    np.fill_diagonal(A, 0.0)
-    R = np.cumsum(A, axis=1)[:, -1]   # sequential row sums, in the order build_q takes them
-    for i in range(n):
-        Q[i, i] = q_diag(R[i], lam_v, C, diag_rule, delta)
     return Q, keep

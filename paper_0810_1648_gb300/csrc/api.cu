@@ -144,9 +144,9 @@ void clear_graphs(gabp_svm_t h)
 
 // The swept tile list after formation.  Dense: every tile (the list built at
 // create, grouped by stage).  Tile-sparse: the diagonal tiles and every tile
-// whose largest |Q_ij| exceeds sparse_tau, grouped by stage; the dropped
-// tiles' |Q| row sums are zeroed so that the diagonal rule sees the kept
-// entries.  Must run between the FP32 formation and the diagonal rule.
+// whose largest |Q_ij| exceeds sparse_tau, grouped by stage.  The diagonal
+// rule keeps the row sums of the whole matrix, so dropping a tile changes
+// only its own entries (and the matrix stays diagonally dominant).
 gabp_status build_sweep_list(gabp_svm_t h)
 {
     h->stats.tiles_total = h->ntiles;
@@ -162,7 +162,7 @@ gabp_status build_sweep_list(gabp_svm_t h)
     const int Nt = h->Nt;
     auto L_of = [Nt](int I, int J) { return (long long)I * Nt - (long long)I * (I - 1) / 2 + (J - I); };
     const float tau = h->opts.sparse_tau;
-    std::vector<int4> wl, dropped;
+    std::vector<int4> wl;
     int B[kMaxStages + 1];
     stage_bounds(Nt, h->nstages, B);
     const int nblk = (int)((h->n + 31) / 32);
@@ -174,7 +174,6 @@ gabp_status build_sweep_list(gabp_svm_t h)
                 const long long L = L_of(I, J);
                 const int4 t = make_int4(0, I, J, (int)L);
                 if (I == J || mx[(size_t)L] > tau) wl.push_back(t);
-                else dropped.push_back(t);
             }
         sc[st] = Sched{(long long)wl.size() - off, nblk, 1, off};
     }
@@ -182,14 +181,6 @@ gabp_status build_sweep_list(gabp_svm_t h)
     h->stats.tiles_kept = h->nlive;
     CK(cudaMemcpyAsync(h->work, wl.data(), wl.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(h->sched, sc, (size_t)h->nstages * sizeof(Sched), cudaMemcpyHostToDevice, s));
-    if (!dropped.empty()) {
-        int4* d = nullptr;
-        CK(cudaMallocAsync((void**)&d, dropped.size() * sizeof(int4), s));
-        CK(cudaMemcpyAsync(d, dropped.data(), dropped.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
-        launch_zero_tile_sums(h->d_tab, d, (long long)dropped.size(), s);
-        CK(cudaGetLastError());
-        CK(cudaFreeAsync(d, s));
-    }
     CK(cudaStreamSynchronize(s));   // the host lists go out of scope
     return GABP_OK;
 }

@@ -168,9 +168,6 @@ void launch_stage(const void* X, int x_f64, int n, int m, float* y, float* Xf, f
 inline double refine_handover(float opt, int msg_bf16) { return opt > 0 ? opt : (msg_bf16 ? 1e-3 : 1e-4); }
 inline double refine_inner(float opt, int msg_bf16) { return opt > 0 ? opt : (msg_bf16 ? 3e-2 : 1e-2); }
 
-// Tile-sparse option: the |Q| row-sum partials of the listed (dropped) tiles
-// := 0, so that the diagonal rule sees the kept entries only.
-void launch_zero_tile_sums(const Inst* tab, const int4* tiles, long long ntiles, cudaStream_t s);
 // Q formation (FP32 SIMT Gram fused with exp, labels and bias) + |Q| row-sum partials;
 // the FP32 tiles are stored into Inst::qref where it is set (the FP32 store, or the
 // FP32 copy the BF16 store keeps for its refinement residuals).

@@ -503,21 +503,6 @@ __global__ void k_decision_sum(const float* __restrict__ part, int t, int Ntrain
 }
 
 // ---------------------------------------------------------------- inspection
-// Tile-sparse option: the dropped tiles' |Q| row-sum partials := 0 (rows of
-// block I in slot J, columns of block J in slot I; slot I of both on the
-// diagonal, which is never dropped).  One CTA per listed tile.
-__global__ void k_zero_tile_sums(const Inst* __restrict__ tab, const int4* __restrict__ tiles)
-{
-    const int4 w = tiles[blockIdx.x];
-    const Inst& p = tab[w.x];
-    const int I = w.y, J = w.z, n = p.n;
-    for (int c = threadIdx.x; c < T; c += blockDim.x) {
-        const int xr = I * T + c, xc = J * T + c;
-        if (xr < n) p.part[(size_t)J * n + xr] = 0.f;
-        if (xc < n) p.part[(size_t)I * n + xc] = 0.f;
-    }
-}
-
 __global__ void k_get_q(Inst p, const int4* __restrict__ work, int q_bf16, float* __restrict__ Qd)
 {
     const long long L = work[blockIdx.x].w;
@@ -539,11 +524,6 @@ __global__ void k_get_q(Inst p, const int4* __restrict__ work, int q_bf16, float
 }
 
 }  // namespace
-
-void launch_zero_tile_sums(const Inst* tab, const int4* tiles, long long ntiles, cudaStream_t s)
-{
-    if (ntiles > 0) k_zero_tile_sums<<<(unsigned)ntiles, 128, 0, s>>>(tab, tiles);
-}
 
 void launch_stage_list(const Inst* tab, const int2* nbl, int nblocks, cudaStream_t s)
 {
