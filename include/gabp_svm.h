@@ -16,6 +16,12 @@
  *   - the weights alpha = clip(mean, 0, C) and the decision function
  *     f(x) = sum_i alpha_i y_i K'(x_i, x) (Section 1.1).
  *
+ * Options extend it along the paper's own directions: BF16 tensor-core Q and
+ * BF16 messages with defect correction (the precision forms), a block
+ * Gauss-Seidel message schedule (Section 3.2), kernel ridge regression on
+ * the same solver (Section 1.2), a tile-sparse kernel (Section 6), and the
+ * batched and served forms for many instances.
+ *
  * Everything after create() runs on one CUDA device in hand-written kernels.
  * There is no CPU fallback: every call that needs the GPU fails with
  * GABP_ECUDA when there is none.
@@ -43,7 +49,7 @@
 extern "C" {
 #endif
 
-#define GABP_SVM_VERSION 1
+#define GABP_SVM_VERSION 2
 
 #if defined(__GNUC__)
 #define GABP_API __attribute__((visibility("default")))
