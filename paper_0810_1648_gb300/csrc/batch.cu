@@ -42,13 +42,16 @@ struct MemberPlan {
     size_t X, vec, agg, part, state, q, qref, rhist, final3, blockbuf, xp, total;
 };
 
-MemberPlan member_plan(int64_t n, int64_t m, int q_mode, int msg_bf16)
+// alias_x: FP32 features in device memory are read in place (no copy).
+// The total is a multiple of 1024 bytes, so instances can be packed into one
+// allocation back to back.
+MemberPlan member_plan(int64_t n, int64_t m, int q_mode, int msg_bf16, bool alias_x)
 {
     const int Nt = (int)((n + T - 1) / T);
     const long long nt = tri_tiles(Nt);
     const size_t npad = aup((size_t)n, 128);
     MemberPlan p{};
-    p.X = aup((size_t)n * m * 4, 256);
+    p.X = alias_x ? 0 : aup((size_t)n * m * 4, 256);
     p.vec = aup(npad * 4, 256);
     p.agg = aup(8 * npad * 4, 256);   // 2 x {P, h, mu} + staged {P, h}
     p.part = aup((size_t)4 * Nt * n * 4, 256);
@@ -59,7 +62,7 @@ MemberPlan member_plan(int64_t n, int64_t m, int q_mode, int msg_bf16)
     p.final3 = 256;
     p.blockbuf = aup((size_t)3 * ((n + 31) / 32) * 8, 256);
     p.xp = q_mode != 0 ? aup(bf16_pack_bytes(Nt, (int)m), 1024) : 0;
-    p.total = p.X + 10 * p.vec + p.agg + p.part + p.state + p.q + p.qref + p.final3 + p.blockbuf + p.xp + 2048;
+    p.total = aup(p.X + 10 * p.vec + p.agg + p.part + p.state + p.q + p.qref + p.final3 + p.blockbuf + p.xp + 2048, 1024);
     return p;
 }
 
@@ -78,7 +81,8 @@ struct Member {
     float* r32 = nullptr;
     double* final3 = nullptr;
     double* blockbuf = nullptr;
-    cudaEvent_t ready = nullptr;
+    cudaEvent_t ready = nullptr;   // formation done (shared by the instances formed together)
+    int evg = -1;                  // its group, while the instance still holds it
     // request bookkeeping
     int iters = 0;
     double tol = 0;
@@ -160,6 +164,7 @@ class Engine {
     int2* d_nbl = nullptr;
     Sched* d_sched = nullptr;
     Ctrl* h_ctrl = nullptr;       // pinned mirror
+    Inst* h_tab = nullptr;        // pinned staging of the instance table (uploaded per formation group)
     double* h_f3 = nullptr;       // pinned {residual, objective, #SV} per slot
     StopOp* h_ops = nullptr;      // pinned end-of-solve operations per slot
     StopOp* d_ops = nullptr;
@@ -175,6 +180,13 @@ class Engine {
     int chunk = 16;
     std::map<int, cudaGraphExec_t> graphs;
     std::vector<int> pending;     // added, Q not formed yet
+    char* arena = nullptr;        // one allocation for a known set of instances (gabp_batch_solve)
+    size_t arena_size = 0, arena_off = 0;
+    struct EvGroup {
+        cudaEvent_t ev = nullptr;
+        int refs = 0;             // instances not yet activated or released
+    };
+    std::vector<EvGroup> evg;
     long long live_tiles = 0;     // tiles in the current lists
     bool lists_dirty = true;
     size_t bytes_in_use = 0;
@@ -186,8 +198,11 @@ class Engine {
         if (side) cudaStreamSynchronize(side);
         for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
         for (auto& m : mem) release(m);
+        if (arena) cudaFreeAsync(arena, stream);
         if (stream) cudaStreamSynchronize(stream);
         if (d_tab) cudaFree(d_tab);
+        for (auto& g : evg) cudaEventDestroy(g.ev);
+        if (h_tab) cudaFreeHost(h_tab);
         if (h_ctrl) cudaFreeHost(h_ctrl);
         if (h_f3) cudaFreeHost(h_f3);
         if (h_ops) cudaFreeHost(h_ops);
@@ -261,6 +276,7 @@ class Engine {
         EK(cudaMemsetAsync(d_ctrl, 0, b_ctrl, stream));
         EK(cudaMemsetAsync(d_sched, 0, b_sched, stream));
         EK(cudaMallocHost((void**)&h_ctrl, (size_t)cap_members * sizeof(Ctrl)));
+        EK(cudaMallocHost((void**)&h_tab, (size_t)cap_members * sizeof(Inst)));
         EK(cudaMallocHost((void**)&h_f3, (size_t)cap_members * 3 * sizeof(double)));
         EK(cudaMallocHost((void**)&h_ops, (size_t)cap_members * sizeof(StopOp)));
         std::memset(h_ops, 0, (size_t)cap_members * sizeof(StopOp));
@@ -279,9 +295,30 @@ class Engine {
     void release(Member& m)
     {
         if (m.mem) cudaFreeAsync(m.mem, stream);
-        if (m.ready) cudaEventDestroy(m.ready);
+        drop_ready(m);
         if (m.used) bytes_in_use -= m.bytes;
         m = Member{};
+    }
+
+    // The instance no longer needs its formation event (its wait is enqueued,
+    // or it is released); the event of a group is reused once all let go.
+    void drop_ready(Member& m)
+    {
+        if (m.evg >= 0) --evg[(size_t)m.evg].refs;
+        m.evg = -1;
+    }
+
+    bool alias_x() const { return ptr_mode == 1 && x_f64 == 0; }
+    // labels in device memory are read in place unless the task rewrites them
+    bool alias_y() const { return ptr_mode == 1 && task != GABP_TASK_KRR; }
+
+    // Instance memory of a known set in one allocation (carved by add()).
+    gabp_status reserve(size_t bytes)
+    {
+        EK(cudaMallocAsync((void**)&arena, bytes, side));
+        arena_size = bytes;
+        arena_off = 0;
+        return GABP_OK;
     }
 
     int free_slot() const
@@ -298,14 +335,21 @@ class Engine {
         const int64_t n = pr.n, m = pr.m;
         if (n < 2 || m < 1 || !pr.X || !pr.y) return fail(GABP_EINVAL, "problem needs n >= 2, m >= 1, X and y");
         if (!(pr.gamma > 0) || !(pr.C > 0)) return fail(GABP_EINVAL, "problem needs gamma > 0 and C > 0");
-        const MemberPlan pl = member_plan(n, m, q_mode, msg_bf16);
+        const MemberPlan pl = member_plan(n, m, q_mode, msg_bf16, alias_x());
         M = Member{};
         M.used = true;
         M.bytes = pl.total;
         bytes_in_use += pl.total;
         cudaStream_t s = side;
-        EK(cudaMallocAsync(&M.mem, pl.total, s));
-        char* b = static_cast<char*>(M.mem);
+        char* b = nullptr;
+        if (arena) {
+            if (arena_off + pl.total > arena_size) return fail(GABP_ENOMEM, "instance memory exhausted");
+            b = arena + arena_off;
+            arena_off += pl.total;
+        } else {
+            EK(cudaMallocAsync(&M.mem, pl.total, s));
+            b = static_cast<char*>(M.mem);
+        }
         size_t off = 0;
         auto take = [&](size_t bytes) { void* r = b + off; off += bytes; return r; };
         Inst& p = M.inst;
@@ -313,9 +357,9 @@ class Engine {
         p.Nt = (int)((n + T - 1) / T);
         p.m = (int)m;
         p.npad = (int)aup((size_t)n, 128);
-        p.X = (const float*)take(pl.X);
+        p.X = alias_x() ? static_cast<const float*>(pr.X) : (const float*)take(pl.X);
         p.sq = (const float*)take(pl.vec);
-        p.y = (const float*)take(pl.vec);
+        p.y = alias_y() ? pr.y : (const float*)take(pl.vec);
         p.b = (const float*)take(pl.vec);
         p.b0 = (const float*)take(pl.vec);
         p.qdiag = (float*)take(pl.vec);
@@ -354,17 +398,18 @@ class Engine {
         M.out_dev = out_dev;
         M.res.status = GABP_OK;
         M.res.alpha = out_alpha;
-        EK(cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), s));
-        EK(cudaMemcpyAsync(d_tab + slot, &p, sizeof(Inst), cudaMemcpyHostToDevice, s));
-        EK(cudaMemcpyAsync((void*)p.y, pr.y, (size_t)n * 4, ptr_mode ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-        if (pl.xp) EK(cudaMemsetAsync((void*)p.Xp, 0, pl.xp, s));   // padding rows and features stay 0
-        if (!x_f64) {
-            // FP32 rows straight into X (from host or device memory); the
-            // batched staging of form_pending() checks them
-            EK(cudaMemcpyAsync((void*)p.X, pr.X, (size_t)n * m * 4,
+        // (the table entry and the control block are uploaded by form_pending)
+        h_tab[slot] = p;
+        if (!alias_y())
+            EK(cudaMemcpyAsync((void*)p.y, pr.y, (size_t)n * 4,
                                ptr_mode ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        if (!x_f64) {
+            // FP32 rows: read in place from device memory, else copied into X;
+            // the batched staging of form_pending() checks them
+            if (!alias_x()) EK(cudaMemcpyAsync((void*)p.X, pr.X, (size_t)n * m * 4, cudaMemcpyHostToDevice, s));
         } else {
             // FP64 input: convert and check now
+            EK(cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), s));
             const void* src = pr.X;
             void* tmp = nullptr;
             if (!ptr_mode) {
@@ -378,7 +423,6 @@ class Engine {
             if (tmp) EK(cudaFreeAsync(tmp, s));
             M.staged = true;
         }
-        EK(cudaEventCreateWithFlags(&M.ready, cudaEventDisableTiming));
         pending.push_back(slot);
         return GABP_OK;
     }
@@ -390,6 +434,23 @@ class Engine {
     {
         if (pending.empty()) return GABP_OK;
         cudaStream_t s = side;
+        // table entries (one copy per run of consecutive slots) and control
+        // blocks of the FP32-input instances (one memset per run)
+        std::vector<int> sl(pending);
+        std::sort(sl.begin(), sl.end());
+        for (size_t a = 0; a < sl.size();) {
+            size_t e = a + 1;
+            while (e < sl.size() && sl[e] == sl[e - 1] + 1) ++e;
+            EK(cudaMemcpyAsync(d_tab + sl[a], h_tab + sl[a], (e - a) * sizeof(Inst), cudaMemcpyHostToDevice, s));
+            a = e;
+        }
+        for (size_t a = 0; a < sl.size();) {
+            if (mem[(size_t)sl[a]].staged) { ++a; continue; }
+            size_t e = a + 1;
+            while (e < sl.size() && sl[e] == sl[e - 1] + 1 && !mem[(size_t)sl[e]].staged) ++e;
+            EK(cudaMemsetAsync(d_ctrl + sl[a], 0, (e - a) * sizeof(Ctrl), s));
+            a = e;
+        }
         std::vector<int4> tiles;
         std::vector<int2> nb, nb_stage;
         for (int k : pending) {
@@ -420,7 +481,18 @@ class Engine {
         if (q_mode == 1) EK(launch_form_q_tc(d_tab, d_t, (long long)tiles.size(), s));
         launches += q_mode == 0 ? 3 : (q_mode == 1 ? 5 : 4);
         EK(cudaGetLastError());
-        for (int k : pending) EK(cudaEventRecord(mem[(size_t)k].ready, s));
+        size_t g = 0;
+        while (g < evg.size() && evg[g].refs > 0) ++g;
+        if (g == evg.size()) {
+            evg.emplace_back();
+            EK(cudaEventCreateWithFlags(&evg[g].ev, cudaEventDisableTiming));
+        }
+        EK(cudaEventRecord(evg[g].ev, s));
+        evg[g].refs = (int)pending.size();
+        for (int k : pending) {
+            mem[(size_t)k].ready = evg[g].ev;
+            mem[(size_t)k].evg = (int)g;
+        }
         EK(cudaFreeAsync(d_t, s));
         EK(cudaFreeAsync(d_n, s));
         EK(cudaFreeAsync(d_ns, s));
@@ -435,6 +507,7 @@ class Engine {
     {
         Member& M = mem[(size_t)slot];
         EK(cudaStreamWaitEvent(stream, M.ready, 0));
+        drop_ready(M);
         // With refinement ahead, the BF16 solve only needs to reach about the
         // BF16 error level of its matrix before the first correction.
         const double t0 = (q_mode != 0 && M.refine_left > 0) ? std::max(tol, handover) : tol;
@@ -455,6 +528,7 @@ class Engine {
         for (int k : slots) {
             Member& M = mem[(size_t)k];
             EK(cudaStreamWaitEvent(stream, M.ready, 0));
+            drop_ready(M);
             const double t0 = (q_mode != 0 && M.refine_left > 0) ? std::max(M.tol, handover) : M.tol;
             bl.push_back(make_int2(k, M.iters));
             bt.push_back(t0);
@@ -796,7 +870,7 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
         const long long Nt = (p.n + T - 1) / T;
         tiles += tri_tiles(Nt);
         nblk += (p.n + 31) / 32;
-        bytes += member_plan(p.n, p.m, o.q_mode, o.msg_bf16).total;
+        bytes += member_plan(p.n, p.m, o.q_mode, o.msg_bf16, o.ptr_mode == 1 && o.x_dtype == 0).total;
     }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -815,6 +889,7 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
     Engine E;
     if (gabp_status st = E.init((int)count, tiles, (int)nblk, o)) return st;
     auto t0 = clk::now();
+    if (gabp_status st = E.reserve(bytes)) return st;
     for (int64_t k = 0; k < count; ++k) {
         if (gabp_status st = E.add((int)k, probs[k], results[k].alpha, o.ptr_mode)) return st;
         E.mem[(size_t)k].iters = iters;
@@ -977,7 +1052,8 @@ gabp_status gabp_server_step(gabp_server_t s, int32_t* active, int32_t* queued, 
     t0 = clk::now();
     while (!s->queue.empty()) {
         const auto& front = s->queue.front();
-        const size_t need = member_plan(front.second.n, front.second.m, s->cfg.opts.q_mode, s->cfg.opts.msg_bf16).total;
+        const size_t need = member_plan(front.second.n, front.second.m, s->cfg.opts.q_mode, s->cfg.opts.msg_bf16,
+                                        E.alias_x()).total;
         if (need > s->budget) {
             gabp_result r{};
             r.status = GABP_ENOMEM;

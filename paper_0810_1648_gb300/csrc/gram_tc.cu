@@ -58,7 +58,9 @@ __global__ void k_pack_bf16(const float* __restrict__ Xf, int n, int m, int nkc,
 }
 
 // Listed node blocks (32 rows): packing (8 threads per row over the 8-feature
-// groups) and the BF16 row norms.
+// groups) and the BF16 row norms.  The last block of an instance also writes
+// the zero rows that pad its last 128-row tile, so the packed operand needs no
+// clearing beforehand.
 __global__ void k_pack_list(const Inst* __restrict__ tab, const int2* __restrict__ nbl)
 {
     const int2 nb = nbl[blockIdx.x];
@@ -66,21 +68,25 @@ __global__ void k_pack_list(const Inst* __restrict__ tab, const int2* __restrict
     const int rl = threadIdx.x >> 3, gsub = threadIdx.x & 7;
     const int r = nb.y * 32 + rl, n = p.n, m = p.m, nkc = p.nkc;
     const int Nt = p.Nt;
-    if (r >= Nt * T) return;
+    const bool last = nb.y == (n - 1) / 32;
     const float* Xf = p.X;
     uint4* Xp = static_cast<uint4*>(const_cast<void*>(p.Xp));
     const int groups = nkc * (KCH / 8);
-    const int I = r / T, rr = r % T;
-    for (int gk = gsub; gk < groups; gk += 8) {
-        const int kc = gk / (KCH / 8), kg = gk % (KCH / 8);
-        __align__(16) __nv_bfloat16 v[8];
+    for (int rw = r; rw < Nt * T; rw += 32) {
+        const int I = rw / T, rr = rw % T;
+        for (int gk = gsub; gk < groups; gk += 8) {
+            const int kc = gk / (KCH / 8), kg = gk % (KCH / 8);
+            __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int k = kc * KCH + kg * 8 + u;
-            v[u] = __float2bfloat16_rn((r < n && k < m) ? Xf[(size_t)r * m + k] : 0.f);
+            for (int u = 0; u < 8; ++u) {
+                const int k = kc * KCH + kg * 8 + u;
+                v[u] = __float2bfloat16_rn((rw < n && k < m) ? Xf[(size_t)rw * m + k] : 0.f);
+            }
+            const size_t blk = (size_t)I * nkc + kc;
+            Xp[blk * (BLK_BYTES / 16) + (size_t)((rr / 8) * (KCH / 8) + kg) * 8 + (rr % 8)] =
+                *reinterpret_cast<const uint4*>(v);
         }
-        const size_t blk = (size_t)I * nkc + kc;
-        Xp[blk * (BLK_BYTES / 16) + (size_t)((rr / 8) * (KCH / 8) + kg) * 8 + (rr % 8)] = *reinterpret_cast<const uint4*>(v);
+        if (!last) break;
     }
     if (gsub == 0 && r < n) {
         float sacc = 0.f;
