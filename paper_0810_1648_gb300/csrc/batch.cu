@@ -90,6 +90,7 @@ struct Member {
     int refine_done = 0;
     bool refining = false;
     bool staged = false;     // rows checked and normed already (FP64 / device input)
+    const void* src_x = nullptr;  // the caller's features (instances over the same ones share Gram tiles)
     int t_first_stop = 0;
     gabp_result res{};
     float* out_alpha = nullptr;  // caller buffer
@@ -396,6 +397,7 @@ class Engine {
         M.nblk = (int)((n + 31) / 32);
         M.out_alpha = out_alpha;
         M.out_dev = out_dev;
+        M.src_x = pr.X;
         M.res.status = GABP_OK;
         M.res.alpha = out_alpha;
         // (the table entry and the control block are uploaded by form_pending)
@@ -434,6 +436,24 @@ class Engine {
     {
         if (pending.empty()) return GABP_OK;
         cudaStream_t s = side;
+        // Instances over the same features (a parameter grid) are chained
+        // behind the first: the FP32 and the tensor-core Gram tiles are
+        // computed once for all (form_next goes up with the table entries).
+        std::map<std::tuple<const void*, int, int>, int> tail;
+        std::vector<int> leaders;
+        for (int k : pending) {
+            const Member& M = mem[(size_t)k];
+            auto key = std::make_tuple(M.src_x, M.inst.n, M.inst.m);
+            auto it = tail.find(key);
+            h_tab[k].form_next = 0;
+            if (it == tail.end()) {
+                tail.emplace(key, k);
+                leaders.push_back(k);
+            } else {
+                h_tab[it->second].form_next = k + 1;
+                it->second = k;
+            }
+        }
         // table entries (one copy per run of consecutive slots) and control
         // blocks of the FP32-input instances (one memset per run)
         std::vector<int> sl(pending);
@@ -451,34 +471,36 @@ class Engine {
             EK(cudaMemsetAsync(d_ctrl + sl[a], 0, (e - a) * sizeof(Ctrl), s));
             a = e;
         }
-        std::vector<int4> tiles;
+        std::vector<int4> tiles_lead;
         std::vector<int2> nb, nb_stage;
-        for (int k : pending) {
-            const Member& M = mem[(size_t)k];
-            const int Nt = M.inst.Nt;
+        for (int k : leaders) {
+            const int Nt = mem[(size_t)k].inst.Nt;
             int L = 0;
             for (int I = 0; I < Nt; ++I)
-                for (int J = I; J < Nt; ++J, ++L) tiles.push_back(make_int4(k, I, J, L));
+                for (int J = I; J < Nt; ++J, ++L) tiles_lead.push_back(make_int4(k, I, J, L));
+        }
+        for (int k : pending) {
+            const Member& M = mem[(size_t)k];
             for (int b = 0; b < M.nblk; ++b) {
                 nb.push_back(make_int2(k, b));
                 if (!M.staged) nb_stage.push_back(make_int2(k, b));
             }
         }
-        int4* d_t = nullptr;
+        int4* d_tl = nullptr;
         int2* d_n = nullptr;
         int2* d_ns = nullptr;
-        EK(cudaMallocAsync((void**)&d_t, tiles.size() * sizeof(int4) + 16, s));
+        EK(cudaMallocAsync((void**)&d_tl, tiles_lead.size() * sizeof(int4) + 16, s));
         EK(cudaMallocAsync((void**)&d_n, nb.size() * sizeof(int2) + 16, s));
         EK(cudaMallocAsync((void**)&d_ns, nb_stage.size() * sizeof(int2) + 16, s));
-        EK(cudaMemcpyAsync(d_t, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+        EK(cudaMemcpyAsync(d_tl, tiles_lead.data(), tiles_lead.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
         EK(cudaMemcpyAsync(d_n, nb.data(), nb.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
         if (!nb_stage.empty())
             EK(cudaMemcpyAsync(d_ns, nb_stage.data(), nb_stage.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
         launch_stage_list(d_tab, d_ns, (int)nb_stage.size(), s);
         if (q_mode != 0) EK(launch_pack_list(d_tab, d_n, (int)nb.size(), s));
-        launch_form_q(d_tab, d_t, (long long)tiles.size(), s);
+        launch_form_q(d_tab, d_tl, (long long)tiles_lead.size(), s);
         launch_init_list(d_tab, d_n, (int)nb.size(), diag_rule, (float)delta, s);
-        if (q_mode == 1) EK(launch_form_q_tc(d_tab, d_t, (long long)tiles.size(), s));
+        if (q_mode == 1) EK(launch_form_q_tc(d_tab, d_tl, (long long)tiles_lead.size(), s));
         launches += q_mode == 0 ? 3 : (q_mode == 1 ? 5 : 4);
         EK(cudaGetLastError());
         size_t g = 0;
@@ -493,7 +515,7 @@ class Engine {
             mem[(size_t)k].ready = evg[g].ev;
             mem[(size_t)k].evg = (int)g;
         }
-        EK(cudaFreeAsync(d_t, s));
+        EK(cudaFreeAsync(d_tl, s));
         EK(cudaFreeAsync(d_n, s));
         EK(cudaFreeAsync(d_ns, s));
         // (pageable host-to-device copies return once the data is staged, so

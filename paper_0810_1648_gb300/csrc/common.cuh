@@ -94,6 +94,8 @@ struct Inst {
     int nkc;          // 64-feature chunks of Xp
     int msg_bf16;     // messages stored in BF16 (precision forms)
     int task;         // 0 SVM (labels in Q, alpha clipped to [0, C]), 1 KRR (y = 1 in Q, alpha unclipped)
+    int form_next;    // formation: 1 + the next instance built from the same features (its Q
+                      // tiles come from the same Gram tiles), 0 = none
 };
 
 // Work of one round over a set of instances (device resident, so that a

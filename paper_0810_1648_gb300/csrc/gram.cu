@@ -202,67 +202,76 @@ __global__ void k_stage_list(const Inst* __restrict__ tab, const int2* __restric
 }
 
 // ------------------------------------------------------- Q tile formation
+// One Gram tile per work item; every instance chained through form_next (the
+// points of a parameter grid over the same features) takes its Q tile, row
+// and column sums and tile maximum from it in turn.
 __global__ void __launch_bounds__(NTHREADS) k_form_q(const Inst* __restrict__ tab, const int4* __restrict__ work)
 {
     __shared__ __align__(16) TileSmem sm;
     const int4 w = work[blockIdx.x];
-    const Inst& p = tab[w.x];
     const long long L = w.w;
-    const int I = w.y, J = w.z, n = p.n;
-    const GramSide S{p.X, p.sq, n};
+    const int I = w.y, J = w.z;
     float acc[8][8];
-    gram_tile(S, S, p.m, I, J, sm.g, acc);
-
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    float yj[8], sj[8];
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-        const int j = J * T + tx * 8 + b;
-        yj[b] = j < n ? p.y[j] : 0.f;
-        sj[b] = j < n ? p.sq[j] : 0.f;
+    {
+        const Inst& p0 = tab[w.x];
+        const GramSide S{p0.X, p0.sq, p0.n};
+        gram_tile(S, S, p0.m, I, J, sm.g, acc);
     }
-    float rs[1][8], cs[1][8];
-#pragma unroll
-    for (int b = 0; b < 8; ++b) cs[0][b] = 0.f;
-    float tmx = 0.f;    // largest |Q_ij| of the thread's pairs (the tile-sparse option)
-    float* qt = p.qref ? p.qref + (size_t)L * TT : nullptr;   // FP32 Q kept for the sweeps / residuals
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-        const int r = ty * 8 + a, i = I * T + r;
-        const float yi = i < n ? p.y[i] : 0.f, si = i < n ? p.sq[i] : 0.f;
-        float out[8];
-        float racc = 0.f;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    for (int k = w.x; k >= 0;) {
+        const Inst& p = tab[k];
+        const int n = p.n;
+        float yj[8], sj[8];
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
-            const int c = tx * 8 + b, j = J * T + c;
-            const bool v = i < n && j < n && (I != J || c > r);
-            const float q = yi * yj[b] * (rbf_from_gram(acc[a][b], si, sj[b], p.gamma) + p.lam2);
-            out[b] = v ? q : 0.f;
-            racc += fabsf(out[b]);
-            cs[0][b] += fabsf(out[b]);
-            tmx = fmaxf(tmx, fabsf(out[b]));
+            const int j = J * T + tx * 8 + b;
+            yj[b] = j < n ? p.y[j] : 0.f;
+            sj[b] = j < n ? p.sq[j] : 0.f;
         }
-        rs[0][a] = racc;
-        if (qt) {
-            float4* dst = reinterpret_cast<float4*>(qt + r * T + tx * 8);
-            dst[0] = make_float4(out[0], out[1], out[2], out[3]);
-            dst[1] = make_float4(out[4], out[5], out[6], out[7]);
+        float rs[1][8], cs[1][8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) cs[0][b] = 0.f;
+        float tmx = 0.f;    // largest |Q_ij| of the thread's pairs (the tile-sparse option)
+        float* qt = p.qref ? p.qref + (size_t)L * TT : nullptr;   // FP32 Q kept for the sweeps / residuals
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const int r = ty * 8 + a, i = I * T + r;
+            const float yi = i < n ? p.y[i] : 0.f, si = i < n ? p.sq[i] : 0.f;
+            float out[8];
+            float racc = 0.f;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const int c = tx * 8 + b, j = J * T + c;
+                const bool v = i < n && j < n && (I != J || c > r);
+                const float q = yi * yj[b] * (rbf_from_gram(acc[a][b], si, sj[b], p.gamma) + p.lam2);
+                out[b] = v ? q : 0.f;
+                racc += fabsf(out[b]);
+                cs[0][b] += fabsf(out[b]);
+                tmx = fmaxf(tmx, fabsf(out[b]));
+            }
+            rs[0][a] = racc;
+            if (qt) {
+                float4* dst = reinterpret_cast<float4*>(qt + r * T + tx * 8);
+                dst[0] = make_float4(out[0], out[1], out[2], out[3]);
+                dst[1] = make_float4(out[4], out[5], out[6], out[7]);
+            }
         }
-    }
-    float* const parts[1] = {p.part};
-    __syncthreads();   // Gram smem is reused by the epilogue
-    reduce_and_write<1>(sm.e, rs, cs, parts, n, I, J);
-    if (p.tilemax) {
-        // largest |Q_ij| of the tile's pairs (the tile-sparse option)
-        const float mx = warp_max_f(tmx);
-        __syncthreads();
-        if ((tid & 31) == 0) sm.e.rowv[0][tid >> 5] = mx;
-        __syncthreads();
-        if (tid == 0) {
-            float m2 = 0.f;
-            for (int w = 0; w < NWARPS; ++w) m2 = fmaxf(m2, sm.e.rowv[0][w]);
-            p.tilemax[L] = m2;
+        float* const parts[1] = {p.part};
+        __syncthreads();   // Gram smem (first pass) or the previous instance's sums are done with
+        reduce_and_write<1>(sm.e, rs, cs, parts, n, I, J);
+        if (p.tilemax) {
+            // largest |Q_ij| of the tile's pairs (the tile-sparse option)
+            const float mx = warp_max_f(tmx);
+            __syncthreads();
+            if ((tid & 31) == 0) sm.e.rowv[0][tid >> 5] = mx;
+            __syncthreads();
+            if (tid == 0) {
+                float m2 = 0.f;
+                for (int w2 = 0; w2 < NWARPS; ++w2) m2 = fmaxf(m2, sm.e.rowv[0][w2]);
+                p.tilemax[L] = m2;
+            }
         }
+        k = p.form_next - 1;
     }
 }
 

@@ -223,35 +223,38 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         uint32_t aph = 0;
         for (long long L = blockIdx.x; L < ntiles; L += gridDim.x) {
             const int4 w = work[L];
-            const Inst& p = tab[w.x];
-            Ctrl* ctrl = p.ctrl;
-            const int n = p.n;
-            const float* sqb = p.sqb;
-            __nv_bfloat16* qs = static_cast<__nv_bfloat16*>(p.qstore);
             const bool stop = __shfl_sync(0xffffffffu, *(volatile int*)&sm.abort, 0) != 0;
             if (stop || !mbar_wait_warp(&sm.accfull[acc], aph)) {
                 if (lane == 0) {
                     sm.abort = 1;
-                    record_error(ctrl, ST_ETIMEOUT, L);
+                    record_error(tab[w.x].ctrl, ST_ETIMEOUT, L);
                 }
                 break;
             }
             tc_fence_after();
             const int I = w.y, J = w.z;
             const int i = I * T + r;
-            const float yi = i < n ? p.y[i] : 0.f, si = i < n ? sqb[i] : 0.f;
-            __nv_bfloat16* qrow = qs + (size_t)w.w * TT + (size_t)r * T;
+            // the listed instance and every one chained behind it (same
+            // features) take their BF16 Q tile from this accumulator
+            for (int k = w.x; k >= 0;) {
+                const Inst& p = tab[k];
+                const int n = p.n;
+                const float* sqb = p.sqb;
+                const float yi = i < n ? p.y[i] : 0.f, si = i < n ? sqb[i] : 0.f;
+                __nv_bfloat16* qrow = static_cast<__nv_bfloat16*>(p.qstore) + (size_t)w.w * TT + (size_t)r * T;
 #pragma unroll 1
-            for (int cc = 2 * half; cc < 2 * half + 2; ++cc) {
-                float v[32];
-                tmem_ld32(tbase + (uint32_t)acc * T + ((uint32_t)(32 * g) << 16) + (uint32_t)(32 * cc), v);
-                const int jl = J * T + 32 * cc + lane;
-                const float yl = jl < n ? p.y[jl] : 0.f, sl = jl < n ? sqb[jl] : 0.f;
-                uint4 out[4];
-                q_chunk_bf16(v, yi, si, yl, sl, p.gamma, p.lam2, chunk_valid(n, I, J, r, cc), out);
-                uint4* dst = reinterpret_cast<uint4*>(qrow + 32 * cc);
+                for (int cc = 2 * half; cc < 2 * half + 2; ++cc) {
+                    float v[32];
+                    tmem_ld32(tbase + (uint32_t)acc * T + ((uint32_t)(32 * g) << 16) + (uint32_t)(32 * cc), v);
+                    const int jl = J * T + 32 * cc + lane;
+                    const float yl = jl < n ? p.y[jl] : 0.f, sl = jl < n ? sqb[jl] : 0.f;
+                    uint4 out[4];
+                    q_chunk_bf16(v, yi, si, yl, sl, p.gamma, p.lam2, chunk_valid(n, I, J, r, cc), out);
+                    uint4* dst = reinterpret_cast<uint4*>(qrow + 32 * cc);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) dst[u] = out[u];
+                    for (int u = 0; u < 4; ++u) dst[u] = out[u];
+                }
+                k = p.form_next - 1;
             }
             tc_fence_before();
             __syncwarp();

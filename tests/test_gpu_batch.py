@@ -168,3 +168,80 @@ def test_batch_device_pointers_equal_host():
     for ah, ad, rh, rd in zip(a_host, a_dev, r_host, r_dev):
         np.testing.assert_array_equal(ah, ad.cpu().numpy())
         assert rh["iters_done"] == rd["iters_done"]
+
+
+def _grid(seeds=(31, 32), n=(300, 170), m=(32, 8)):
+    """Parameter grids (C x gamma) over shared feature arrays: the instances
+    of one grid pass the same X, so formation computes their Gram tiles once."""
+    out = []
+    for s, nn, mm in zip(seeds, n, m):
+        base = workloads.mixture(nn, mm, seed=s)
+        for C in (0.1, 1.0, 10.0):
+            for g in (0.5, 1.0, 2.0):
+                out.append(workloads.Problem(base.X, base.y, g / mm, C))
+    return out
+
+
+@pytest.mark.parametrize("kw", [dict(q_mode=0), dict(q_mode=1, refine=4), dict(q_mode=2, refine=4),
+                                dict(q_mode=0, task=gabp.TASK_KRR)])
+def test_batch_parameter_grid_shares_gram(kw):
+    torch = pytest.importorskip("torch")
+    grid = _grid()
+    assert grid[0].X is grid[1].X
+    if kw.get("task") == gabp.TASK_KRR:
+        grid = [workloads.Problem(p.X, workloads.krr_targets(p, seed=5), p.gamma, p.C) for p in grid]
+    # the same problems with private copies of their features (no sharing)
+    private = [workloads.Problem(p.X.copy(), p.y.copy(), p.gamma, p.C) for p in grid]
+    a_sh, r_sh, rc = gabp.batch_solve(grid, 40, 0.0, chunk=8, **kw)
+    assert rc == gabp.OK
+    a_pr, r_pr, rc = gabp.batch_solve(private, 40, 0.0, chunk=8, **kw)
+    assert rc == gabp.OK
+    # device arrays shared per grid, as a parameter search passes them
+    dev = {}
+    for p in grid:
+        if id(p.X) not in dev:
+            dev[id(p.X)] = (torch.from_numpy(p.X).cuda(), torch.from_numpy(np.ascontiguousarray(p.y)).cuda())
+    dgrid = []
+    for p in grid:
+        X, y = dev[id(p.X)]
+        if kw.get("task") == gabp.TASK_KRR:
+            y = torch.from_numpy(np.ascontiguousarray(p.y)).cuda()
+        dgrid.append(workloads.Problem(X, y, p.gamma, p.C))
+    a_dv, r_dv, rc = gabp.batch_solve(dgrid, 40, 0.0, chunk=8, **kw)
+    assert rc == gabp.OK
+    for p, a, b, d, rs, rp in zip(grid, a_sh, a_pr, a_dv, r_sh, r_pr):
+        np.testing.assert_array_equal(a, b)
+        np.testing.assert_array_equal(a, d.cpu().numpy())
+        assert rs["residual_inf"] == rp["residual_inf"] and rs["iters_done"] == rp["iters_done"]
+    if kw.get("q_mode", 0) == 0:
+        # and each equals its oracle iterate at the FP32 bar
+        for p, a in list(zip(grid, a_sh))[::4]:
+            if kw.get("task") == gabp.TASK_KRR:
+                # (C is the ridge for this task)
+                _, ro = oracle.solve_krr(p.X.astype(np.float64), p.y.astype(np.float64), p.gamma, p.C, iters=40,
+                                         tol=0.0)
+                assert np.max(np.abs(a - ro.mu)) <= 2e-5 * np.max(np.abs(ro.mu))
+            else:
+                _, ro = oracle.solve_svm(p.X.astype(np.float64), p.y.astype(np.float64), p.gamma, p.C, iters=40,
+                                         tol=0.0)
+                assert np.max(np.abs(a - ro.alpha(p.C))) <= 1e-4 * p.C
+
+
+def test_server_parameter_grid_shares_gram():
+    grid = _grid(seeds=(41,), n=(260,), m=(16,))
+    srv = gabp.Server(iters=60, tol=1e-6, max_members=4, chunk=4)
+    tickets = [srv.submit(p.X, p.y, p.gamma, p.C) for p in grid]
+    out = {}
+    for _ in range(2000):
+        srv.step()
+        for t in srv.completed():
+            out[t] = srv.poll(t)
+        if len(out) == len(grid):
+            break
+    srv.close()
+    assert len(out) == len(grid)
+    for p, t in zip(grid, tickets):
+        a, r = out[t]
+        assert r["status"] == 0
+        single, _, _ = gabp.GabpSVM(p.X, p.y, p.gamma, p.C, chunk=4).solve(60, 1e-6)
+        np.testing.assert_array_equal(a, single)
