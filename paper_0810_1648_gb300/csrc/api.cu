@@ -175,7 +175,7 @@ gabp_status build_sweep_list(gabp_svm_t h)
                 const int4 t = make_int4(0, I, J, (int)L);
                 if (I == J || mx[(size_t)L] > tau) wl.push_back(t);
             }
-        sc[st] = Sched{(long long)wl.size() - off, nblk, 1, off};
+        sc[st] = Sched{(long long)wl.size() - off, nblk, 1, off, Nt <= kWarpFinNt ? nblk : 0, 0};
     }
     h->nlive = (long long)wl.size();
     h->stats.tiles_kept = h->nlive;
@@ -524,7 +524,7 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
         for (int I = 0; I < h->Nt; ++I)
             for (int J = std::max(I, B[st]); J < B[st + 1]; ++J)
                 wl.push_back(make_int4(0, I, J, (int)((long long)I * h->Nt - (long long)I * (I - 1) / 2 + (J - I))));
-        sc[st] = Sched{(long long)wl.size() - off, nblk, 1, off};
+        sc[st] = Sched{(long long)wl.size() - off, nblk, 1, off, h->Nt <= kWarpFinNt ? nblk : 0, 0};
     }
     std::vector<int2> nb((size_t)nblk);
     for (int b = 0; b < nblk; ++b) nb[(size_t)b] = make_int2(0, b);

@@ -594,12 +594,20 @@ class Engine {
             }
             sc[st] = Sched{(long long)wl.size() - off, 0, cap_members, off};
         }
-        for (int k = 0; k < cap_members; ++k) {
-            const Member& M = mem[(size_t)k];
-            if (!M.used || !M.active) continue;
-            for (int b = 0; b < M.nblk; ++b) nb.push_back(make_int2(k, b));
+        // node blocks of the instances finalized one warp per block first
+        int nsmall = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int k = 0; k < cap_members; ++k) {
+                const Member& M = mem[(size_t)k];
+                if (!M.used || !M.active || (M.inst.Nt <= kWarpFinNt) != (pass == 0)) continue;
+                for (int b = 0; b < M.nblk; ++b) nb.push_back(make_int2(k, b));
+            }
+            if (pass == 0) nsmall = (int)nb.size();
         }
-        for (int st = 0; st < nstages; ++st) sc[st].nblocks = (int)nb.size();
+        for (int st = 0; st < nstages; ++st) {
+            sc[st].nblocks = (int)nb.size();
+            sc[st].nsmall = nsmall;
+        }
         if ((long long)wl.size() > cap_tiles || (int)nb.size() > cap_nblk)
             return fail(GABP_ENOMEM, "batch lists exceed their capacity");
         if (!wl.empty()) EK(cudaMemcpyAsync(d_work, wl.data(), wl.size() * sizeof(int4), cudaMemcpyHostToDevice, stream));

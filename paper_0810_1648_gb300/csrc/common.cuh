@@ -109,7 +109,10 @@ struct Sched {
     int nblocks;
     int ninst;
     long long off;
+    int nsmall;   // node blocks [0, nsmall) of the list: instances with Nt <= kWarpFinNt (one warp each at finalize)
+    int pad_;
 };
+constexpr int kWarpFinNt = 32;
 constexpr int kMaxStages = 16;
 
 // Stage boundaries of the staged schedule for Nt tile rows: B[0] = 0,

@@ -935,124 +935,191 @@ __device__ __forceinline__ void acc2(float& s, float& c, float x)
     s = t;
 }
 
-// Per node x: compensated sums of its Nt slots (32 nodes x 8 slot groups per
-// CTA, four slots in flight per thread), next aggregates, residual r_x(t) in
-// FP64, CTA max |r| -> ctrl, the last CTA to finish decides.
-__global__ void __launch_bounds__(256)
+// Node x's next aggregates {Ptilde, htilde, mutilde} from its slot sums (P,
+// H) and its residual r_x(t) = b_x - Q_xx mutilde_x(t) - R in FP64; returns
+// |r_x| (inf for a non-finite one) and flags a non-positive or non-finite
+// aggregate.
+__device__ __forceinline__ double finalize_node(const Inst& p, Ctrl* ctrl, int x, int t, bool frozen, double P,
+                                                double H, double R)
+{
+    const float* cur = p.agg + (size_t)(t & 1) * 3 * p.npad;
+    float* nxt = p.agg + (size_t)((t + 1) & 1) * 3 * p.npad;
+    const double qd = p.qdiag[x], bx = p.b[x];
+    const float Pn = frozen ? cur[x] : (float)(qd + P);
+    const float hn = (float)(bx + H);
+    const float mn = hn / Pn;
+    nxt[x] = Pn;
+    nxt[p.npad + x] = hn;
+    nxt[2 * p.npad + x] = mn;
+    const double r = bx - qd * (double)cur[2 * p.npad + x] - R;
+    double absr = fabs(r);
+    if (!(absr <= DBL_MAX)) absr = INFINITY;
+    if (!(Pn > 0.f) || !isfinite(Pn) || !isfinite(mn)) record_error(ctrl, ST_ENUMERIC, x);
+    return absr;
+}
+
+// Run by the last node block of an instance to finish a round: ||r(t)||_inf,
+// the stop test (Step 3: k* = t when it is below tol, the limit otherwise),
+// the exact P-freeze flag, and the round counter.
+__device__ __forceinline__ void finalize_decide(const Inst& p, Ctrl* ctrl, int t)
+{
+    __threadfence();
+    const double rmax = __longlong_as_double((long long)atomicAdd(&ctrl->rmax_bits, 0ull));
+    const int status = atomicAdd(&ctrl->status, 0);
+    if (p.rhist && t < p.rhist_cap) p.rhist[t] = rmax;
+    if (status != 0) {
+        ctrl->done = 1;
+        ctrl->kstar = t;
+        ctrl->rinf = rmax;
+    } else if (rmax < ctrl->tol) {
+        ctrl->done = 1;
+        ctrl->kstar = t;
+        ctrl->converged = 1;
+        ctrl->rinf = rmax;
+    } else if (t + 1 >= ctrl->limit) {
+        ctrl->done = 1;
+        ctrl->kstar = t + 1;
+    }
+    // No P message changed in this round: P is at its floating-point fixed
+    // point (its recursion does not involve b or H), so later rounds would
+    // rewrite the same values; they stop writing them.
+    if (!ctrl->p_frozen && t > 0 && atomicAdd(&ctrl->p_changed, 0) == 0) {
+        ctrl->p_frozen = 1;
+        ctrl->t_frozen = t + 1;
+    }
+    ctrl->p_changed = 0;
+    ctrl->t = t + 1;
+    ctrl->zero_h = 0;
+    ctrl->rmax_bits = 0ull;
+    ctrl->blocks_done = 0u;
+    __threadfence();
+}
+
+// Compensated sums of node x's slots k = k0, k0 + step, ... < Nt of NA
+// partial arrays (P, H[, R]), eight loads of each in flight; P reads as 0
+// when frozen (Ptilde is kept then).
+template <int NA>
+__device__ __forceinline__ void slot_sums(const Inst& p, int x, int k0, int step, bool frozen, float (&s)[NA],
+                                          float (&c)[NA])
+{
+    const int n = p.n, Nt = p.Nt;
+    const float* part = p.part;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) s[a] = c[a] = 0.f;
+    int k = k0;
+    for (; k + 7 * step < Nt; k += 8 * step) {
+        float v[NA][8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                const size_t o = ((size_t)a * Nt + k + u * step) * n + x;
+                v[a][u] = (a == 0 && frozen) ? 0.f : part[o];
+            }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int a = 0; a < NA; ++a) acc2(s[a], c[a], v[a][u]);
+    }
+    for (; k < Nt; k += step)
+#pragma unroll
+        for (int a = 0; a < NA; ++a) acc2(s[a], c[a], (a == 0 && frozen) ? 0.f : part[((size_t)a * Nt + k) * n + x]);
+}
+
+// Node-block units of a round's finalize.  Blocks [0, nsmall) of the list
+// belong to instances with at most kWarpFinNt tile rows and are finalized one
+// warp per block, eight blocks per unit; the others take a whole CTA each
+// (eight warps over the slots, then one reduction).  An instance's blocks all
+// take the same mode, so its arithmetic does not depend on the other
+// instances of the list.
+__device__ __forceinline__ int fin_units(const Sched* sc, int& usmall)
+{
+    usmall = (sc->nsmall + 7) / 8;
+    return usmall + (sc->nblocks - sc->nsmall);
+}
+
+// Per node x: compensated sums of its Nt slots, next aggregates, residual
+// r_x(t) in FP64, max |r| -> ctrl; the last node block of an instance to
+// finish decides.
+__global__ void __launch_bounds__(256, 4)
     k_finalize(const Inst* __restrict__ tab, const int2* __restrict__ nbl, const Sched* __restrict__ sched)
 {
-    const int nblocks = sched->nblocks;
+    int usmall;
+    const int units = fin_units(sched, usmall), nsmall = sched->nsmall;
     __shared__ float red[6][8][32];
     __shared__ int s_last;
-    for (int bi = blockIdx.x; bi < nblocks; bi += gridDim.x) {
-    const int2 nb = nbl[bi];
-    const Inst& p = tab[nb.x];
-    Ctrl* ctrl = p.ctrl;
-    if (*(volatile int*)&ctrl->done) continue;
-    const int t = *(volatile int*)&ctrl->t;
-    const bool frozen = *(volatile int*)&ctrl->p_frozen != 0;   // P sums unchanged: Ptilde kept
     const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
-    const int x = nb.y * 32 + lane, n = p.n, Nt = p.Nt;
-    const float* partP = p.part;
-    const float* partH = partP + (size_t)Nt * n;
-    const float* partR = partH + (size_t)Nt * n;
-    float sP = 0.f, cPs = 0.f, sH = 0.f, cHs = 0.f, sR = 0.f, cRs = 0.f;
-    if (x < n) {
-        int k = g;
-        for (; k + 24 < Nt; k += 32) {
-            float vp[4], vh[4], vr[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const size_t o = (size_t)(k + 8 * u) * n + x;
-                vp[u] = frozen ? 0.f : partP[o];
-                vh[u] = partH[o];
-                vr[u] = partR[o];
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        if (u < usmall) {
+            // ---- one warp per node block
+            const int bi = 8 * u + g;
+            if (bi >= nsmall) continue;
+            const int2 nb = nbl[bi];
+            const Inst& p = tab[nb.x];
+            Ctrl* ctrl = p.ctrl;
+            if (*(volatile int*)&ctrl->done) continue;
+            const int t = *(volatile int*)&ctrl->t;
+            const bool frozen = *(volatile int*)&ctrl->p_frozen != 0;
+            const int x = nb.y * 32 + lane, n = p.n;
+            double absr = 0.0;
+            if (x < n) {
+                float sv[3], cv[3];
+                slot_sums<3>(p, x, 0, 1, frozen, sv, cv);
+                absr = finalize_node(p, ctrl, x, t, frozen, (double)sv[0] + (double)cv[0],
+                                     (double)sv[1] + (double)cv[1], (double)sv[2] + (double)cv[2]);
             }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) { acc2(sP, cPs, vp[u]); acc2(sH, cHs, vh[u]); acc2(sR, cRs, vr[u]); }
-        }
-        for (; k < Nt; k += 8) {
-            const size_t o = (size_t)k * n + x;
-            acc2(sP, cPs, frozen ? 0.f : partP[o]);
-            acc2(sH, cHs, partH[o]);
-            acc2(sR, cRs, partR[o]);
-        }
-    }
-    __syncthreads();   // red[] of the previous node block is consumed
-    red[0][g][lane] = sP; red[1][g][lane] = cPs;
-    red[2][g][lane] = sH; red[3][g][lane] = cHs;
-    red[4][g][lane] = sR; red[5][g][lane] = cRs;
-    __syncthreads();
-    if (g == 0) {
-        double absr = 0.0;
-        if (x < n) {
-            float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int w = 0; w < 8; ++w) {
-                acc2(a[0], a[1], red[0][w][lane]); a[1] += red[1][w][lane];
-                acc2(a[2], a[3], red[2][w][lane]); a[3] += red[3][w][lane];
-                acc2(a[4], a[5], red[4][w][lane]); a[5] += red[5][w][lane];
+            absr = warp_max_d(absr);
+            if (lane == 0) atomicMax(&ctrl->rmax_bits, (unsigned long long)__double_as_longlong(absr));
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) {
+                const unsigned prev = atomicAdd(&ctrl->blocks_done, 1u);
+                if (prev == (unsigned)((n + 31) / 32 - 1)) finalize_decide(p, ctrl, t);
             }
-            const double P = (double)a[0] + (double)a[1];
-            const double H = (double)a[2] + (double)a[3];
-            const double R = (double)a[4] + (double)a[5];
-            const float* cur = p.agg + (size_t)(t & 1) * 3 * p.npad;
-            float* nxt = p.agg + (size_t)((t + 1) & 1) * 3 * p.npad;
-            const double qd = p.qdiag[x], bx = p.b[x];
-            const float Pn = frozen ? cur[x] : (float)(qd + P);
-            const float hn = (float)(bx + H);
-            const float mn = hn / Pn;
-            nxt[x] = Pn;
-            nxt[p.npad + x] = hn;
-            nxt[2 * p.npad + x] = mn;
-            const double r = bx - qd * (double)cur[2 * p.npad + x] - R;
-            absr = fabs(r);
-            if (!(absr <= DBL_MAX)) absr = INFINITY;
-            if (!(Pn > 0.f) || !isfinite(Pn) || !isfinite(mn)) record_error(ctrl, ST_ENUMERIC, x);
+            continue;
         }
-        absr = warp_max_d(absr);
-        if (lane == 0)
-            atomicMax(&ctrl->rmax_bits, (unsigned long long)__double_as_longlong(absr));
-    }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) {
-        const unsigned prev = atomicAdd(&ctrl->blocks_done, 1u);
-        s_last = (prev == (unsigned)((n + 31) / 32 - 1));
-    }
-    __syncthreads();
-    if (s_last && tid == 0) {
+        // ---- one CTA per node block: warp g sums slots g, g + 8, ...
+        const int2 nb = nbl[nsmall + (u - usmall)];
+        const Inst& p = tab[nb.x];
+        Ctrl* ctrl = p.ctrl;
+        if (*(volatile int*)&ctrl->done) continue;
+        const int t = *(volatile int*)&ctrl->t;
+        const bool frozen = *(volatile int*)&ctrl->p_frozen != 0;
+        const int x = nb.y * 32 + lane, n = p.n;
+        float sv[3] = {0.f, 0.f, 0.f}, cv[3] = {0.f, 0.f, 0.f};
+        if (x < n) slot_sums<3>(p, x, g, 8, frozen, sv, cv);
+        __syncthreads();   // red[] of the previous node block is consumed
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            red[2 * a][g][lane] = sv[a];
+            red[2 * a + 1][g][lane] = cv[a];
+        }
+        __syncthreads();
+        if (g == 0) {
+            double absr = 0.0;
+            if (x < n) {
+                float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int w = 0; w < 8; ++w) {
+                    acc2(a[0], a[1], red[0][w][lane]); a[1] += red[1][w][lane];
+                    acc2(a[2], a[3], red[2][w][lane]); a[3] += red[3][w][lane];
+                    acc2(a[4], a[5], red[4][w][lane]); a[5] += red[5][w][lane];
+                }
+                absr = finalize_node(p, ctrl, x, t, frozen, (double)a[0] + (double)a[1], (double)a[2] + (double)a[3],
+                                     (double)a[4] + (double)a[5]);
+            }
+            absr = warp_max_d(absr);
+            if (lane == 0)
+                atomicMax(&ctrl->rmax_bits, (unsigned long long)__double_as_longlong(absr));
+        }
         __threadfence();
-        const double rmax = __longlong_as_double((long long)atomicAdd(&ctrl->rmax_bits, 0ull));
-        const int status = atomicAdd(&ctrl->status, 0);
-        if (p.rhist && t < p.rhist_cap) p.rhist[t] = rmax;
-        if (status != 0) {
-            ctrl->done = 1;
-            ctrl->kstar = t;
-            ctrl->rinf = rmax;
-        } else if (rmax < ctrl->tol) {
-            ctrl->done = 1;
-            ctrl->kstar = t;
-            ctrl->converged = 1;
-            ctrl->rinf = rmax;
-        } else if (t + 1 >= ctrl->limit) {
-            ctrl->done = 1;
-            ctrl->kstar = t + 1;
+        __syncthreads();
+        if (tid == 0) {
+            const unsigned prev = atomicAdd(&ctrl->blocks_done, 1u);
+            s_last = (prev == (unsigned)((n + 31) / 32 - 1));
         }
-        // No P message changed in this round: P is at its floating-point fixed
-        // point (its recursion does not involve b or H), so later rounds would
-        // rewrite the same values; they stop writing them.
-        if (!ctrl->p_frozen && t > 0 && atomicAdd(&ctrl->p_changed, 0) == 0) {
-            ctrl->p_frozen = 1;
-            ctrl->t_frozen = t + 1;
-        }
-        ctrl->p_changed = 0;
-        ctrl->t = t + 1;
-        ctrl->zero_h = 0;
-        ctrl->rmax_bits = 0ull;
-        ctrl->blocks_done = 0u;
-        __threadfence();
-    }
+        __syncthreads();
+        if (s_last && tid == 0) finalize_decide(p, ctrl, t);
     }
 }
 
@@ -1073,46 +1140,51 @@ __device__ __forceinline__ void zero_slots(const Inst& p, int x, bool with_p)
 // all of its slot partials (slots of tiles not yet swept in this round still
 // hold the sums of their current messages) into aggmid, for the next stage;
 // with frozen P, Ptilde is kept.  No residual and no stop test: those come
-// with the round's last stage (k_finalize).
+// with the round's last stage (k_finalize).  Same node-block units as
+// k_finalize.
+__device__ __forceinline__ void stage_node(const Inst& p, int x, int t, bool frozen, double P, double H)
+{
+    const float* cur = p.agg + (size_t)(t & 1) * 3 * p.npad;
+    p.aggmid[x] = frozen ? cur[x] : (float)((double)p.qdiag[x] + P);
+    p.aggmid[p.npad + x] = (float)((double)p.b[x] + H);
+}
+
 __global__ void __launch_bounds__(256)
     k_finalize_stage(const Inst* __restrict__ tab, const int2* __restrict__ nbl, const Sched* __restrict__ sched)
 {
-    const int nblocks = sched->nblocks;
+    int usmall;
+    const int units = fin_units(sched, usmall), nsmall = sched->nsmall;
     __shared__ float red[4][8][32];
-    for (int bi = blockIdx.x; bi < nblocks; bi += gridDim.x) {
-        const int2 nb = nbl[bi];
+    const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        if (u < usmall) {
+            const int bi = 8 * u + g;
+            if (bi >= nsmall) continue;
+            const int2 nb = nbl[bi];
+            const Inst& p = tab[nb.x];
+            if (*(volatile int*)&p.ctrl->done) continue;
+            const int t = *(volatile int*)&p.ctrl->t;
+            const bool frozen = *(volatile int*)&p.ctrl->p_frozen != 0;
+            const int x = nb.y * 32 + lane;
+            if (x < p.n) {
+                float sv[2], cv[2];
+                slot_sums<2>(p, x, 0, 1, frozen, sv, cv);
+                stage_node(p, x, t, frozen, (double)sv[0] + (double)cv[0], (double)sv[1] + (double)cv[1]);
+            }
+            continue;
+        }
+        const int2 nb = nbl[nsmall + (u - usmall)];
         const Inst& p = tab[nb.x];
         Ctrl* ctrl = p.ctrl;
         if (*(volatile int*)&ctrl->done) continue;   // the same node block for the whole CTA
         const int t = *(volatile int*)&ctrl->t;
         const bool frozen = *(volatile int*)&ctrl->p_frozen != 0;
-        const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
-        const int x = nb.y * 32 + lane, n = p.n, Nt = p.Nt;
-        const float* partP = p.part;
-        const float* partH = partP + (size_t)Nt * n;
-        float sP = 0.f, cPs = 0.f, sH = 0.f, cHs = 0.f;
-        if (x < n) {
-            int k = g;
-            for (; k + 24 < Nt; k += 32) {
-                float vp[4], vh[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const size_t o = (size_t)(k + 8 * u) * n + x;
-                    vp[u] = frozen ? 0.f : partP[o];
-                    vh[u] = partH[o];
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) { acc2(sP, cPs, vp[u]); acc2(sH, cHs, vh[u]); }
-            }
-            for (; k < Nt; k += 8) {
-                const size_t o = (size_t)k * n + x;
-                acc2(sP, cPs, frozen ? 0.f : partP[o]);
-                acc2(sH, cHs, partH[o]);
-            }
-        }
+        const int x = nb.y * 32 + lane, n = p.n;
+        float sv[2] = {0.f, 0.f}, cv[2] = {0.f, 0.f};
+        if (x < n) slot_sums<2>(p, x, g, 8, frozen, sv, cv);
         __syncthreads();   // red[] of the previous node block is consumed
-        red[0][g][lane] = sP; red[1][g][lane] = cPs;
-        red[2][g][lane] = sH; red[3][g][lane] = cHs;
+        red[0][g][lane] = sv[0]; red[1][g][lane] = cv[0];
+        red[2][g][lane] = sv[1]; red[3][g][lane] = cv[1];
         __syncthreads();
         if (g == 0 && x < n) {
             float a[4] = {0.f, 0.f, 0.f, 0.f};
@@ -1121,11 +1193,7 @@ __global__ void __launch_bounds__(256)
                 acc2(a[0], a[1], red[0][w][lane]); a[1] += red[1][w][lane];
                 acc2(a[2], a[3], red[2][w][lane]); a[3] += red[3][w][lane];
             }
-            const double P = (double)a[0] + (double)a[1];
-            const double H = (double)a[2] + (double)a[3];
-            const float* cur = p.agg + (size_t)(t & 1) * 3 * p.npad;
-            p.aggmid[x] = frozen ? cur[x] : (float)((double)p.qdiag[x] + P);
-            p.aggmid[p.npad + x] = (float)((double)p.b[x] + H);
+            stage_node(p, x, t, frozen, (double)a[0] + (double)a[1], (double)a[2] + (double)a[3]);
         }
     }
 }
