@@ -289,17 +289,23 @@ def run_batch(args):
             last = res
         conv = sum(r["converged"] for r in last)
         ph = gabp.batch_last_phases()
-        # algorithmic bytes of all the rounds run: per pair and round the
-        # message state is read and written once and Q read once
-        b_pair = (16 if kw.get("msg_bf16") else 32) + (2 if kw.get("q_mode", 0) == 1 else 4)
-        alg = sum(r["iters_done"] * p.n * (p.n - 1) / 2 * b_pair for p, r in zip(probs, last))
+        # algorithmic bytes of all the rounds run, per pair and round: Q once,
+        # the message state read once and written once while P changes, only
+        # H written after the exact P-freeze (a few rounds in): the two give a
+        # range, since the freeze round of each instance is not reported
+        qb = 2 if kw.get("q_mode", 0) == 1 else 4
+        ms = 4 if kw.get("msg_bf16") else 8
+        b_live, b_frozen = qb + 4 * ms, qb + 3 * ms
+        pair_rounds = sum(r["iters_done"] * p.n * (p.n - 1) / 2 for p, r in zip(probs, last))
+        rs = ph["rounds_ms"] / 1e3
         out[mode] = {"solves_per_s": len(probs) / float(np.median(times)), "ms_per_batch": 1e3 * float(np.median(times)),
                      "phases_ms": ph,
                      "converged": conv, "max_residual": max(r["residual_inf"] for r in last),
                      "mean_rounds": float(np.mean([r["iters_done"] for r in last])),
-                     "rounds_hbm": {"bytes_per_pair_round": b_pair, "algorithmic_GB": alg / 1e9,
-                                    "GBps_over_rounds_phase": alg / (ph["rounds_ms"] / 1e3) / 1e9,
-                                    "frac_of_measured_peak": alg / (ph["rounds_ms"] / 1e3) / 1e9 / _peak_gbs()}}
+                     "rounds_hbm": {"pair_rounds": pair_rounds, "bytes_per_pair_round": [b_frozen, b_live],
+                                    "GBps_over_rounds_phase": [pair_rounds * b / rs / 1e9 for b in (b_frozen, b_live)],
+                                    "frac_of_measured_peak": [pair_rounds * b / rs / 1e9 / _peak_gbs()
+                                                              for b in (b_frozen, b_live)]}}
     # end to end: host (numpy) inputs, their copies inside the timed solves
     e2e_t = []
     kw_e2e = dict(q_mode=1, refine=8, msg_bf16=1)

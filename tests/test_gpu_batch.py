@@ -245,3 +245,19 @@ def test_server_parameter_grid_shares_gram():
         assert r["status"] == 0
         single, _, _ = gabp.GabpSVM(p.X, p.y, p.gamma, p.C, chunk=4).solve(60, 1e-6)
         np.testing.assert_array_equal(a, single)
+
+
+def test_batch_mixes_finalize_modes():
+    """Instances with at most 32 tile rows are finalized one warp per node
+    block, larger ones one CTA per block; a list holding both gives each
+    instance the same result as solving it alone (synchronous and staged)."""
+    probs = [workloads.mixture(300, 16, seed=61), workloads.mixture(4500, 8, seed=62),
+             workloads.mixture(4097, 8, seed=63), workloads.mixture(4096, 8, seed=64)]
+    for stages in (1, 3):
+        alphas, res, rc = gabp.batch_solve(probs, 30, 1e-7, chunk=4, stages=stages)
+        assert rc == gabp.OK
+        for p, a, r in zip(probs, alphas, res):
+            single, rinf, k = gabp.GabpSVM(p.X, p.y, p.gamma, p.C, chunk=4, stages=stages).solve(30, 1e-7)
+            np.testing.assert_array_equal(a, single)
+            assert r["iters_done"] == k
+            assert r["residual_inf"] == pytest.approx(rinf, rel=1e-6)
