@@ -74,6 +74,7 @@ def _load():
         "orc_pair_update": (None, [f64, f64, f64, f64, f64, D, D]),
         "orc_cholesky_solve": (i32, [D, D, L, D]),
         "orc_q_row": (None, [D, D, L, L, f64, f64, f64, i32, f64, L, D]),
+        "orc_q_diag_all": (i32, [D, D, L, L, f64, f64, f64, i32, f64, D, D]),
         "orc_cg_rbf": (i32, [D, D, L, L, f64, f64, f64, i32, f64, D, f64, i32, D, I]),
         "orc_dual_objective": (f64, [D, D, L]),
         "orc_decision": (i32, [D, D, D, L, L, D, L, f64, f64, D]),
@@ -147,6 +148,20 @@ def q_row(X, y, i, gamma, C, lam=None, diag_rule=DIAG_DOMINANT, delta=0.1):
     _load().orc_q_row(px, py, n, m, gamma, lam, C, diag_rule, delta, int(i),
                       row.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     return row
+
+
+def q_diag_all(X, y, gamma, C, lam=None, diag_rule=DIAG_DOMINANT, delta=0.1):
+    """(diag, R): Q_ii and R_i = sum_{j != i} |Q_ij| of every row, Q not stored."""
+    X, px = _d(X)
+    y, py = _d(y)
+    n, m = X.shape
+    lam = default_lambda(n) if lam is None else lam
+    diag, R = np.empty(n), np.empty(n)
+    rc = _load().orc_q_diag_all(px, py, n, m, gamma, lam, C, diag_rule, delta,
+                                diag.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                R.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    _check(rc, "q_diag_all")
+    return diag, R
 
 
 class GabpResult:

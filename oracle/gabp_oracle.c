@@ -112,6 +112,41 @@ int orc_build_q(const double* X, const double* y, long n, long m, double gamma,
     return ORC_OK;
 }
 
+/* The diagonal of Q and the off-diagonal absolute row sums R_i of every row,
+ * without storing Q: each unordered pair's |Q_ij| is formed once and added to
+ * both rows (per-thread row-sum arrays, summed at the end).  O(n^2 m) time,
+ * O(n T) memory for T threads.  The diagonal follows orc_q_diag. */
+int orc_q_diag_all(const double* X, const double* y, long n, long m, double gamma,
+                   double lam, double C, int diag_rule, double delta, double* diag, double* R)
+{
+    if (n < 1 || m < 1 || !(gamma > 0) || !(C > 0)) return ORC_EINVAL;
+    const int T = omp_get_max_threads();
+    double* acc = (double*)calloc((size_t)T * (size_t)n, sizeof(double));
+    if (!acc) return ORC_ENOMEM;
+#pragma omp parallel
+    {
+        double* mine = acc + (size_t)omp_get_thread_num() * (size_t)n;
+#pragma omp for schedule(dynamic, 16)
+        for (long i = 0; i < n; ++i) {
+            double ri = 0.0;
+            for (long j = i + 1; j < n; ++j) {
+                double q = fabs(orc_q_offdiag(X + i * m, X + j * m, y[i], y[j], m, gamma, lam));
+                ri += q;
+                mine[j] += q;
+            }
+            mine[i] += ri;
+        }
+    }
+    for (long i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int t = 0; t < T; ++t) s += acc[(size_t)t * (size_t)n + i];
+        R[i] = s;
+        diag[i] = orc_q_diag(s, lam, C, diag_rule, delta);
+    }
+    free(acc);
+    return ORC_OK;
+}
+
 /* r = b - Q mu, returns ||r||_inf.  The paper's Step 3 tests the messages for
  * convergence without naming a norm; the reading used throughout is the
  * infinity norm of the linear-system residual of the current means. */

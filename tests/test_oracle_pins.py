@@ -277,6 +277,26 @@ def test_matrix_free_cg_matches_dense_solve():
     np.testing.assert_allclose(row, Q[17], rtol=1e-14)
 
 
+def test_q_diag_all_rows():
+    """The all-row diagonal pass: closed form on identical patterns (every
+    K = 1, so R_i = (n - 1)(1 + lambda^2)), the dense matrix's diagonal and row
+    sums otherwise, and the Varah bound it feeds (||Q^-1||_inf <= 1 /
+    min_i (Q_ii - R_i) for strictly diagonally dominant Q)."""
+    n, lam, C = 37, 1.0 / 37, 0.5
+    X = np.tile(np.array([[0.3, -1.2, 2.0]]), (n, 1))
+    y = np.where(np.arange(n) % 3 == 0, -1.0, 1.0)
+    d, R = oracle.q_diag_all(X, y, 0.7, C)
+    np.testing.assert_allclose(R, (n - 1) * (1 + lam * lam), rtol=1e-14)
+    np.testing.assert_allclose(d, max(1 + lam * lam + 1 / C, 1.1 * (n - 1) * (1 + lam * lam)), rtol=1e-14)
+    p = workloads.mixture(140, 9, seed=12, C=3.0)
+    Q = oracle.build_q(p.X, p.y, p.gamma, p.C)
+    d, R = oracle.q_diag_all(p.X, p.y, p.gamma, p.C)
+    np.testing.assert_allclose(d, np.diag(Q), rtol=1e-13)
+    np.testing.assert_allclose(R, np.abs(Q).sum(1) - np.abs(np.diag(Q)), rtol=1e-13)
+    inv_norm = np.abs(np.linalg.inv(Q)).sum(1).max()
+    assert inv_norm <= 1.0 / np.min(d - R) * (1 + 1e-12)
+
+
 # ------------------------------------------------------------------ box QP
 @pytest.mark.parametrize("n,seed,C", [(6, 51, 0.05), (9, 52, 0.3), (11, 53, 10.0)])
 def test_boxqp_bruteforce_against_scipy_and_kkt(n, seed, C):
