@@ -83,6 +83,9 @@ struct MsgF32 {
     static constexpr int G = 2;
     static constexpr int RPW = 2;      // rows per consumer warp and ring stage
     static constexpr int NSTAGE = 2;   // ring stages of 16 rows (40 KB with FP32 Q)
+    // diagonal and edge tiles: only the owned pairs of each row are copied
+    // (one copy per row; the form is bandwidth bound, so bytes count)
+    static constexpr bool WHOLE_ROWS = false;
     static __device__ __forceinline__ void load4(const T2* row, int lane, T2 (&v)[4])
     {
         const float4 a = *reinterpret_cast<const float4*>(row + 2 * lane);
@@ -113,6 +116,10 @@ struct MsgBF16 {
     static constexpr int G = 4;
     static constexpr int RPW = 2;      // rows per consumer warp and ring stage (halves the per-row overhead)
     static constexpr int NSTAGE = 4;   // ring stages of 16 rows (20 KB with BF16 Q)
+    // diagonal and edge tiles also move 16 whole rows per copy (the unowned
+    // entries are masked by the consumers): sixteen times fewer bulk copies
+    // for a few percent more bytes, faster for this instruction-heavy form
+    static constexpr bool WHOLE_ROWS = true;
     static __device__ __forceinline__ void load4(const T2* row, int lane, T2 (&v)[4])
     {
         const uint4 u = *reinterpret_cast<const uint4*>(row + 4 * lane);
@@ -263,7 +270,7 @@ __device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, con
             unsigned char* S = ring + (size_t)stage * SB;
             unsigned long long* bar = &sm.full[stage];
             const int r0 = c * RC, nr = min(RC, rows - r0);
-            if (!diag && cols == T) {
+            if (MSG::WHOLE_ROWS || (!diag && cols == T)) {
                 const uint32_t bq = (uint32_t)(nr * T * QB);
                 const uint32_t bs = zero ? 0u : (uint32_t)(nr * T * MB);
                 if (lane == 0) mbar_arrive_expect_tx(bar, bq + 2 * bs);
