@@ -273,6 +273,15 @@ GABP_API gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, 
  * part of formation (allocating and enqueuing the instances)}. */
 GABP_API gabp_status gabp_batch_last_phases(double* out7);
 
+/* gabp_batch_solve keeps its engine (instance table, tile and node lists,
+ * control blocks, pinned mirrors, streams, captured round graphs: a few MB,
+ * growing with the largest batch) per calling thread for the next call with
+ * compatible sizes and options; instance memory is returned to the CUDA
+ * stream-ordered pool at the end of every call.  This frees the calling
+ * thread's kept engine (a thread that exits without calling it leaves it
+ * allocated until the process ends).  Always GABP_OK. */
+GABP_API gabp_status gabp_batch_release(void);
+
 /*
  * Continuous-batching server.  Requests queue in arrival order; each
  * gabp_server_step() launches one chunk of rounds over every live instance,

@@ -26,6 +26,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <tuple>
@@ -319,6 +320,56 @@ class Engine {
         EK(cudaMallocAsync((void**)&arena, bytes, side));
         arena_size = bytes;
         arena_off = 0;
+        return GABP_OK;
+    }
+
+    // Whether this engine, kept from an earlier gabp_batch_solve of the same
+    // thread, can serve a call with these sizes and options as it is.
+    bool compatible(int members, long long tiles, int nblk, const gabp_svm_opts& o) const
+    {
+        const bool same_stream = o.stream ? (!own_stream && stream == (cudaStream_t)o.stream) : own_stream;
+        return same_stream && members <= cap_members && cap_members <= 2 * members + 64 && tiles <= cap_tiles &&
+               nblk <= cap_nblk && q_mode == o.q_mode && msg_bf16 == o.msg_bf16 && task == o.task &&
+               nstages == (o.stages > 1 ? o.stages : 1) && bias_mode == o.bias_mode &&
+               bias_lambda == o.bias_lambda && diag_rule == o.diag_rule &&
+               delta == (o.diag_delta > 0 ? o.diag_delta : 0.1) && x_f64 == o.x_dtype && ptr_mode == o.ptr_mode &&
+               sv_threshold == o.sv_threshold && handover == refine_handover(o.refine_handover, o.msg_bf16) &&
+               inner == refine_inner(o.refine_inner, o.msg_bf16);
+    }
+
+    // Ready for the next call: no instances, zeroed control blocks, the
+    // default schedule; buffers, streams, events and captured graphs stay.
+    gabp_status reuse()
+    {
+        for (auto& m : mem) m = Member{};
+        pending.clear();
+        for (auto& g : evg) g.refs = 0;
+        lists_dirty = true;
+        live_tiles = 0;
+        bytes_in_use = 0;
+        launches = 0;
+        t_rebuild = 0;
+        rebuilds = 0;
+        chunk = 16;
+        set_grid(0);
+        std::memset(h_ops, 0, (size_t)cap_members * sizeof(StopOp));
+        EK(cudaMemsetAsync(d_ctrl, 0, (size_t)cap_members * sizeof(Ctrl), stream));
+        EK(cudaMemsetAsync(d_sched, 0, (size_t)kMaxStages * sizeof(Sched), stream));
+        return GABP_OK;
+    }
+
+    // End of a call: instance memory back to the pool, every copy to the
+    // caller's buffers done.
+    gabp_status end_call()
+    {
+        for (auto& m : mem) release(m);
+        if (arena) {
+            EK(cudaFreeAsync(arena, stream));
+            arena = nullptr;
+            arena_size = arena_off = 0;
+        }
+        EK(cudaStreamSynchronize(side));
+        EK(cudaStreamSynchronize(stream));
         return GABP_OK;
     }
 
@@ -858,6 +909,13 @@ class Engine {
     }
 };
 
+// The engine of this thread's last gabp_batch_solve, kept for the next call
+// with compatible sizes and options (its lists, tables, streams and captured
+// round graphs are reused; instance memory is not kept).  Freed by
+// gabp_batch_release; deliberately not destroyed at thread exit, where the
+// CUDA runtime may already be shut down.
+thread_local Engine* g_batch_engine = nullptr;
+
 }  // namespace gabp
 
 using gabp::Engine;
@@ -916,8 +974,18 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
     using clk = std::chrono::steady_clock;
     const auto t_all = clk::now();
     BatchPhases ph{};
-    Engine E;
-    if (gabp_status st = E.init((int)count, tiles, (int)nblk, o)) return st;
+    std::unique_ptr<Engine> Ep;
+    if (g_batch_engine && g_batch_engine->compatible((int)count, tiles, (int)nblk, o)) {
+        Ep.reset(g_batch_engine);
+        g_batch_engine = nullptr;
+        if (gabp_status st = Ep->reuse()) return st;
+    } else {
+        delete g_batch_engine;
+        g_batch_engine = nullptr;
+        Ep.reset(new Engine);
+        if (gabp_status st = Ep->init((int)count, tiles, (int)nblk, o)) return st;
+    }
+    Engine& E = *Ep;
     auto t0 = clk::now();
     if (gabp_status st = E.reserve(bytes)) return st;
     for (int64_t k = 0; k < count; ++k) {
@@ -977,8 +1045,18 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
         results[k] = r;
         if (r.status != GABP_OK && worst == GABP_OK) worst = (gabp_status)r.status;
     }
+    if (gabp_status st = E.end_call()) return st;
+    g_batch_engine = Ep.release();
     if (worst != GABP_OK) set_last_error("one or more problems failed; see their result status");
     return worst;
+}
+
+gabp_status gabp_batch_release(void)
+{
+    gabp::set_last_error("");
+    delete gabp::g_batch_engine;
+    gabp::g_batch_engine = nullptr;
+    return GABP_OK;
 }
 
 gabp_status gabp_batch_last_phases(double* out7)

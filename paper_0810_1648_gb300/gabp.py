@@ -132,6 +132,7 @@ def load():
         "gabp_selftest_reciprocal": (st, [V, V, I64]),
         "gabp_batch_solve": (st, [P(Problem), I64, P(Opts), I32, D, P(Result)]),
         "gabp_batch_last_phases": (st, [V]),
+        "gabp_batch_release": (st, []),
         "gabp_server_create": (st, [P(ServerCfg), P(V)]),
         "gabp_server_submit": (st, [V, P(Problem), V, P(I64)]),
         "gabp_server_step": (st, [V, P(I32), P(I32), P(I32)]),
@@ -361,6 +362,11 @@ def batch_solve(problems, iters: int, tol: float, **opts):
     if rc not in (OK, ENUMERIC):
         _check(rc)
     return alphas, [res[k].as_dict() for k in range(len(problems))], rc
+
+
+def batch_release():
+    """gabp_batch_release: frees this thread's kept batch engine."""
+    _check(load().gabp_batch_release())
 
 
 def batch_last_phases() -> dict:

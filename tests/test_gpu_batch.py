@@ -261,3 +261,26 @@ def test_batch_mixes_finalize_modes():
             np.testing.assert_array_equal(a, single)
             assert r["iters_done"] == k
             assert r["residual_inf"] == pytest.approx(rinf, rel=1e-6)
+
+
+def test_batch_engine_kept_between_calls():
+    """The engine kept from one gabp_batch_solve serves the next compatible
+    call (same or fewer instances) and gives the same results as a fresh one;
+    other options build a new engine."""
+    probs = _mix(6, 9)
+    gabp.batch_release()
+    a0, r0, rc = gabp.batch_solve(probs, 40, 1e-6, chunk=0)
+    assert rc == gabp.OK
+    a1, r1, _ = gabp.batch_solve(probs, 40, 1e-6, chunk=0)
+    a2, r2, _ = gabp.batch_solve(probs[:3], 40, 1e-6, chunk=0)
+    gabp.batch_solve(probs, 40, 1e-6, chunk=0, q_mode=gabp.Q_BF16, refine=4)
+    a3, r3, _ = gabp.batch_solve(probs, 40, 1e-6, chunk=4)
+    gabp.batch_release()
+    gabp.batch_release()
+    for a in (a1, a3):
+        for x, y in zip(a, a0):
+            np.testing.assert_array_equal(x, y)
+    for x, y in zip(a2, a0[:3]):
+        np.testing.assert_array_equal(x, y)
+    for r in (r1, r3):
+        assert [q["iters_done"] for q in r] == [q["iters_done"] for q in r0]
