@@ -176,6 +176,9 @@ class Engine {
     int* d_stop_members = nullptr;
     int2* d_begin_list = nullptr;
     double* d_begin_tol = nullptr;
+    int2* d_restart_list = nullptr;   // the refinement restarts' begin list (stop handling)
+    double* d_restart_tol = nullptr;
+    cudaStream_t sstream = nullptr;   // end-of-solve handling beside the rounds
     std::vector<Member> mem;
     RoundGrid grid{};
     int ctas_per_sm = 0;
@@ -198,6 +201,7 @@ class Engine {
     {
         if (stream) cudaStreamSynchronize(stream);
         if (side) cudaStreamSynchronize(side);
+        if (sstream) cudaStreamSynchronize(sstream);
         for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
         for (auto& m : mem) release(m);
         if (arena) cudaFreeAsync(arena, stream);
@@ -209,6 +213,8 @@ class Engine {
         if (h_f3) cudaFreeHost(h_f3);
         if (h_ops) cudaFreeHost(h_ops);
         if (side) cudaStreamDestroy(side);
+        if (sstream) cudaStreamDestroy(sstream);
+        if (rejoin_ev) cudaEventDestroy(rejoin_ev);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 
@@ -237,6 +243,8 @@ class Engine {
             own_stream = true;
         }
         EK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+        EK(cudaStreamCreateWithFlags(&sstream, cudaStreamNonBlocking));
+        EK(cudaEventCreateWithFlags(&rejoin_ev, cudaEventDisableTiming));
         {
             // keep freed instance memory in the stream-ordered pool for reuse
             int dev = 0;
@@ -260,7 +268,7 @@ class Engine {
         char* base = nullptr;
         const size_t b_sched = aup((size_t)kMaxStages * sizeof(Sched), 256);
         EK(cudaMalloc((void**)&base,
-                      b_tab + b_ctrl + 2 * b_work + 2 * b_nbl + b_ops + b_f3 + b_mem + b_bl + b_bt + b_sched));
+                      b_tab + b_ctrl + 2 * b_work + 2 * b_nbl + b_ops + b_f3 + b_mem + 2 * b_bl + 2 * b_bt + b_sched));
         size_t off = 0;
         auto carve = [&](size_t bytes) { char* r = base + off; off += bytes; return r; };
         d_tab = (Inst*)carve(b_tab);
@@ -274,6 +282,8 @@ class Engine {
         d_stop_members = (int*)carve(b_mem);
         d_begin_list = (int2*)carve(b_bl);
         d_begin_tol = (double*)carve(b_bt);
+        d_restart_list = (int2*)carve(b_bl);
+        d_restart_tol = (double*)carve(b_bt);
         d_sched = (Sched*)carve(b_sched);   // one per stage
         EK(cudaMemsetAsync(d_ctrl, 0, b_ctrl, stream));
         EK(cudaMemsetAsync(d_sched, 0, b_sched, stream));
@@ -343,6 +353,9 @@ class Engine {
     {
         for (auto& m : mem) m = Member{};
         pending.clear();
+        sb.stopped.clear();
+        rejoin.clear();
+        rejoin_event = false;
         for (auto& g : evg) g.refs = 0;
         lists_dirty = true;
         live_tiles = 0;
@@ -369,6 +382,7 @@ class Engine {
             arena_size = arena_off = 0;
         }
         EK(cudaStreamSynchronize(side));
+        EK(cudaStreamSynchronize(sstream));
         EK(cudaStreamSynchronize(stream));
         return GABP_OK;
     }
@@ -693,6 +707,7 @@ class Engine {
     // block read back; launch_chunk returns at once, wait_chunk waits.
     gabp_status launch_chunk(int rounds)
     {
+        if (gabp_status st = take_rejoin()) return st;
         if (gabp_status st = rebuild()) return st;
         if (live_tiles > 0) {
             cudaGraphExec_t g = nullptr;
@@ -716,14 +731,13 @@ class Engine {
 
     // Records the results of a stopped instance from its final residual /
     // objective / #SV (in h_f3) and queues the copy of alpha to the caller.
-    gabp_status finish(int slot)
+    gabp_status finish(int slot, const Ctrl& c, cudaStream_t ss)
     {
         Member& M = mem[(size_t)slot];
-        const Ctrl& c = h_ctrl[slot];
         const double* f3 = h_f3 + 3 * (size_t)slot;
         if (M.out_alpha)
             EK(cudaMemcpyAsync(M.out_alpha, M.alpha, (size_t)M.inst.n * 4,
-                               M.out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream));
+                               M.out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ss));
         M.res.residual_inf = f3[0];
         M.res.dual_objective = f3[1];
         M.res.n_support = (int64_t)std::llround(f3[2]);
@@ -741,37 +755,62 @@ class Engine {
         return GABP_OK;
     }
 
-    // After a chunk: instances that stopped either start a refinement pass
-    // (precision form) or finish.  The end-of-solve work of all of them runs
-    // as one launch per kernel over lists of their tiles, node blocks and
-    // slots, waited for once.  Returns the number still running.
-    gabp_status advance(int* running, std::vector<int>* finished = nullptr)
+    // End-of-solve handling of the instances that stopped in a chunk, in two
+    // halves so that it can run on its own stream while the other instances
+    // sweep the next chunk:
+    //   stop_begin (after the chunk's control blocks were read): the stopped
+    //     instances leave the lists; their final passes (refinement axpy,
+    //     final residual / objective / #SV) are queued on `ss`, one launch per
+    //     kernel over all of them;
+    //   stop_end: waits for those passes and decides per instance: the next
+    //     defect-correction pass (right-hand side and restart queued on `ss`;
+    //     the instance rejoins the lists at the next chunk launch) or finish
+    //     (results recorded, alpha copied to the caller's buffer on `ss`).
+    // advance() runs both halves back to back on the main stream.
+    struct StopBatch {
+        std::vector<int> stopped;
+        std::vector<char> ref;
+        std::vector<Ctrl> snap;   // control blocks as the chunk left them
+        std::vector<int4> tiles;
+        std::vector<int2> nb;
+    } sb;
+    std::vector<int> rejoin;      // restarted, join the lists at the next launch
+    bool rejoin_event = false;    // rejoin_ev orders their restart before that launch
+    cudaEvent_t rejoin_ev = nullptr;
+
+    gabp_status stop_begin(cudaStream_t ss, int* running)
     {
         int run = 0;
-        std::vector<int> stopped;
+        sb.stopped.clear();
+        sb.ref.clear();
+        sb.snap.clear();
+        sb.tiles.clear();
+        sb.nb.clear();
         for (int k = 0; k < cap_members; ++k) {
             Member& M = mem[(size_t)k];
             if (!M.used || !M.active) continue;
             if (!h_ctrl[k].done) { ++run; continue; }
-            stopped.push_back(k);
+            sb.stopped.push_back(k);
         }
-        if (stopped.empty()) { *running = run; return GABP_OK; }
+        if (running) *running = run;
+        if (sb.stopped.empty()) return GABP_OK;
         // 1. final residual (and, in the precision form, the refined means)
-        std::vector<int4> tiles;
-        std::vector<int2> nb;
-        std::vector<char> ref(stopped.size(), 0);
-        for (size_t u = 0; u < stopped.size(); ++u) {
-            const int k = stopped[u];
+        for (size_t u = 0; u < sb.stopped.size(); ++u) {
+            const int k = sb.stopped[u];
             Member& M = mem[(size_t)k];
             const Ctrl& c = h_ctrl[k];
+            sb.snap.push_back(c);
+            M.active = false;
+            lists_dirty = true;
             StopOp& op = h_ops[(size_t)k];
             op = StopOp{};
             op.alpha = M.alpha;
             op.blockbuf = M.blockbuf;
             op.final3 = M.final3;
             op.sv_threshold = (float)sv_threshold;
-            ref[u] = c.status == 0 && q_mode != 0 && (M.refining || M.refine_left > 0);
-            if (ref[u]) {
+            const bool ref = c.status == 0 && q_mode != 0 && (M.refining || M.refine_left > 0);
+            sb.ref.push_back(ref ? 1 : 0);
+            if (ref) {
                 // Defect correction on the FP32-Gram residual: accumulate the
                 // means (or the correction) and form r = 1 - Q32 mu_acc.
                 op.acc = M.mu_acc;
@@ -788,55 +827,94 @@ class Engine {
             const int Nt = M.inst.Nt;
             int L = 0;
             for (int I = 0; I < Nt; ++I)
-                for (int J = I; J < Nt; ++J, ++L) tiles.push_back(make_int4(k, I, J, L));
-            for (int b = 0; b < M.nblk; ++b) nb.push_back(make_int2(k, b));
+                for (int J = I; J < Nt; ++J, ++L) sb.tiles.push_back(make_int4(k, I, J, L));
+            for (int b = 0; b < M.nblk; ++b) sb.nb.push_back(make_int2(k, b));
         }
-        EK(cudaMemcpyAsync(d_ops, h_ops, (size_t)cap_members * sizeof(StopOp), cudaMemcpyHostToDevice, stream));
-        EK(cudaMemcpyAsync(d_stop_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
-        EK(cudaMemcpyAsync(d_stop_nbl, nb.data(), nb.size() * sizeof(int2), cudaMemcpyHostToDevice, stream));
-        EK(cudaMemcpyAsync(d_stop_members, stopped.data(), stopped.size() * sizeof(int), cudaMemcpyHostToDevice,
-                           stream));
-        launch_axpy_list(d_tab, d_ops, d_stop_nbl, (int)nb.size(), stream);
-        launch_final(d_tab, d_ops, d_stop_tiles, (long long)tiles.size(), d_stop_nbl, (int)nb.size(), d_stop_members,
-                     (int)stopped.size(), d_f3, q_mode != 2, stream);   // FP32 tiles kept unless recomputing
+        EK(cudaMemcpyAsync(d_ops, h_ops, (size_t)cap_members * sizeof(StopOp), cudaMemcpyHostToDevice, ss));
+        EK(cudaMemcpyAsync(d_stop_tiles, sb.tiles.data(), sb.tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, ss));
+        EK(cudaMemcpyAsync(d_stop_nbl, sb.nb.data(), sb.nb.size() * sizeof(int2), cudaMemcpyHostToDevice, ss));
+        EK(cudaMemcpyAsync(d_stop_members, sb.stopped.data(), sb.stopped.size() * sizeof(int), cudaMemcpyHostToDevice,
+                           ss));
+        launch_axpy_list(d_tab, d_ops, d_stop_nbl, (int)sb.nb.size(), ss);
+        launch_final(d_tab, d_ops, d_stop_tiles, (long long)sb.tiles.size(), d_stop_nbl, (int)sb.nb.size(),
+                     d_stop_members, (int)sb.stopped.size(), d_f3, q_mode != 2, ss);   // FP32 tiles kept unless recomputing
         launches += 4;
         EK(cudaGetLastError());
-        EK(cudaMemcpyAsync(h_f3, d_f3, (size_t)cap_members * 3 * sizeof(double), cudaMemcpyDeviceToHost, stream));
-        EK(cudaStreamSynchronize(stream));
+        EK(cudaMemcpyAsync(h_f3, d_f3, (size_t)cap_members * 3 * sizeof(double), cudaMemcpyDeviceToHost, ss));
+        return GABP_OK;
+    }
+
+    gabp_status stop_end(cudaStream_t ss, std::vector<int>* finished)
+    {
+        if (sb.stopped.empty()) return GABP_OK;
+        EK(cudaStreamSynchronize(ss));
         // 2. next correction pass, or done
         std::vector<int2> rnb, blist;
         std::vector<double> btol;
-        bool copies = false;
-        for (size_t u = 0; u < stopped.size(); ++u) {
-            const int k = stopped[u];
+        for (size_t u = 0; u < sb.stopped.size(); ++u) {
+            const int k = sb.stopped[u];
             Member& M = mem[(size_t)k];
             const double rn = h_f3[3 * (size_t)k];
-            if (ref[u] && rn >= M.tol && M.refine_left > 0) {
+            if (sb.ref[u] && rn >= M.tol && M.refine_left > 0) {
                 // solve Q_bf d = r with the P messages kept (H restarted)
                 --M.refine_left;
                 for (int b = 0; b < M.nblk; ++b) rnb.push_back(make_int2(k, b));
                 blist.push_back(make_int2(k, M.iters));
                 btol.push_back(std::max(M.tol * 0.5, inner * rn));
-                ++run;
+                rejoin.push_back(k);
                 continue;
             }
-            if (gabp_status st = finish(k)) return st;
-            copies = true;
+            if (gabp_status st = finish(k, sb.snap[u], ss)) return st;
             if (finished) finished->push_back(k);
         }
         if (!blist.empty()) {
-            EK(cudaMemcpyAsync(d_stop_nbl, rnb.data(), rnb.size() * sizeof(int2), cudaMemcpyHostToDevice, stream));
-            EK(cudaMemcpyAsync(d_begin_list, blist.data(), blist.size() * sizeof(int2), cudaMemcpyHostToDevice, stream));
-            EK(cudaMemcpyAsync(d_begin_tol, btol.data(), btol.size() * sizeof(double), cudaMemcpyHostToDevice, stream));
-            launch_refine_rhs_list(d_tab, d_ops, d_stop_nbl, (int)rnb.size(), stream);
-            launch_begin_list(d_tab, d_begin_list, d_begin_tol, (int)blist.size(), stream);
+            EK(cudaMemcpyAsync(d_stop_nbl, rnb.data(), rnb.size() * sizeof(int2), cudaMemcpyHostToDevice, ss));
+            EK(cudaMemcpyAsync(d_restart_list, blist.data(), blist.size() * sizeof(int2), cudaMemcpyHostToDevice, ss));
+            EK(cudaMemcpyAsync(d_restart_tol, btol.data(), btol.size() * sizeof(double), cudaMemcpyHostToDevice, ss));
+            launch_refine_rhs_list(d_tab, d_ops, d_stop_nbl, (int)rnb.size(), ss);
+            launch_begin_list(d_tab, d_restart_list, d_restart_tol, (int)blist.size(), ss);
             launches += 2;
             EK(cudaGetLastError());
+            if (ss != stream) {
+                EK(cudaEventRecord(rejoin_ev, ss));
+                rejoin_event = true;
+            }
         }
-        EK(cudaStreamSynchronize(stream));   // host vectors above go out of scope
-        (void)copies;
-        *running = run;
+        sb.stopped.clear();
+        // (pageable host-to-device copies return once their data is staged,
+        // so the host lists above may go out of scope)
         return GABP_OK;
+    }
+
+    // Restarted instances join the lists (before a chunk launch).
+    gabp_status take_rejoin()
+    {
+        if (rejoin.empty()) return GABP_OK;
+        if (rejoin_event) EK(cudaStreamWaitEvent(stream, rejoin_ev, 0));
+        rejoin_event = false;
+        for (int k : rejoin) mem[(size_t)k].active = true;
+        rejoin.clear();
+        lists_dirty = true;
+        return GABP_OK;
+    }
+
+    // Both halves on the main stream (the server's step).
+    gabp_status advance(int* running, std::vector<int>* finished = nullptr)
+    {
+        if (gabp_status st = stop_begin(stream, running)) return st;
+        if (gabp_status st = stop_end(stream, finished)) return st;
+        *running += (int)rejoin.size();
+        if (gabp_status st = take_rejoin()) return st;
+        EK(cudaStreamSynchronize(stream));
+        return GABP_OK;
+    }
+
+    // Instances not finished yet.
+    int unfinished() const
+    {
+        int u = 0;
+        for (const auto& M : mem) u += (M.used && !M.finished) ? 1 : 0;
+        return u;
     }
 
     // Restart every active instance from Step 1 (used after tuning runs).
@@ -1023,15 +1101,25 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
         E.chunk = o.chunk;
     }
     ph.tune_ms = ms_since(t0);
-    const int max_loops = (int)(((long long)iters * (1 + o.refine)) / std::max(1, E.chunk) + 4 * (2 + o.refine) + 8);
+    // The end-of-solve work of the instances that stopped in one chunk runs
+    // on its own stream while the others sweep the next chunk; restarted
+    // instances (refinement) join again one chunk later.
+    const int max_loops = (int)(((long long)iters * (1 + o.refine)) / std::max(1, E.chunk) + 8 * (2 + o.refine) + 8);
     int running = (int)count;
     for (int loop = 0; loop < max_loops && running > 0; ++loop) {
         t0 = clk::now();
-        if (gabp_status st = E.run_chunk(E.chunk)) return st;
+        if (gabp_status st = E.launch_chunk(E.chunk)) return st;
         ph.rounds_ms += ms_since(t0);
         t0 = clk::now();
-        if (gabp_status st = E.advance(&running)) return st;
+        if (gabp_status st = E.stop_end(E.sstream, nullptr)) return st;
         ph.stop_ms += ms_since(t0);
+        t0 = clk::now();
+        if (gabp_status st = E.wait_chunk()) return st;
+        ph.rounds_ms += ms_since(t0);
+        t0 = clk::now();
+        if (gabp_status st = E.stop_begin(E.sstream, nullptr)) return st;
+        ph.stop_ms += ms_since(t0);
+        running = E.unfinished();
         ++ph.chunks;
     }
     ph.launches = E.launches;
