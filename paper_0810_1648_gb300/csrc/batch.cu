@@ -375,14 +375,14 @@ class Engine {
     // caller's buffers done.
     gabp_status end_call()
     {
+        EK(cudaStreamSynchronize(side));
+        EK(cudaStreamSynchronize(sstream));
         for (auto& m : mem) release(m);
         if (arena) {
             EK(cudaFreeAsync(arena, stream));
             arena = nullptr;
             arena_size = arena_off = 0;
         }
-        EK(cudaStreamSynchronize(side));
-        EK(cudaStreamSynchronize(sstream));
         EK(cudaStreamSynchronize(stream));
         return GABP_OK;
     }
@@ -1235,13 +1235,35 @@ gabp_status gabp_server_step(gabp_server_t s, int32_t* active, int32_t* queued, 
     using clk = std::chrono::steady_clock;
     const auto t_step = clk::now();
     auto t0 = t_step;
-    // 1. one chunk of rounds over every live instance: launched now, waited
-    //    for after the admission work below, which overlaps it
+    // 1. one chunk of rounds over every live instance (with the ones the
+    //    previous step restarted): launched now, waited for after the work
+    //    below, which overlaps it
+    if (gabp_status st = E.take_rejoin()) return st;
     bool any = false;
     for (auto& M : E.mem) any |= (M.used && M.active);
     if (any) {
         if (gabp_status st = E.launch_chunk(E.chunk)) return st;
         s->t_rounds += ms_since(t0);
+    }
+    // 1b. the instances that stopped in the previous chunk: results or the
+    //     next refinement pass (their final passes ran on the stop stream)
+    {
+        t0 = clk::now();
+        std::vector<int> fin;
+        if (gabp_status st = E.stop_end(E.sstream, &fin)) return st;
+        if (!fin.empty()) {
+            // alpha copies done before the memory is released
+            if (cudaStreamSynchronize(E.sstream) != cudaSuccess) return E.fail(GABP_ECUDA, "result copies failed");
+            for (int slot : fin) {
+                Member& M = E.mem[(size_t)slot];
+                gabp_result r = M.res;
+                r.alpha = M.out_alpha;
+                s->done[M.ticket] = r;
+                s->fresh.push_back(M.ticket);
+                E.release(M);
+            }
+        }
+        s->t_stop += ms_since(t0);
     }
     // 2. admission, first come first served, by device-memory budget and free
     //    slots; formation on the side stream
@@ -1273,23 +1295,14 @@ gabp_status gabp_server_step(gabp_server_t s, int32_t* active, int32_t* queued, 
     }
     if (gabp_status st = E.form_pending()) return st;
     s->t_admit += ms_since(t0);
-    // 3. end of the chunk: retire the instances that stopped
+    // 3. end of the chunk: the instances that stopped leave the lists, their
+    //    final passes go to the stop stream (finished at the next step)
     if (any) {
         t0 = clk::now();
         if (gabp_status st = E.wait_chunk()) return st;
         s->t_rounds += ms_since(t0);
         t0 = clk::now();
-        int running = 0;
-        std::vector<int> fin;
-        if (gabp_status st = E.advance(&running, &fin)) return st;
-        for (int slot : fin) {
-            Member& M = E.mem[(size_t)slot];
-            gabp_result r = M.res;
-            r.alpha = M.out_alpha;
-            s->done[M.ticket] = r;
-            s->fresh.push_back(M.ticket);
-            E.release(M);
-        }
+        if (gabp_status st = E.stop_begin(E.sstream, nullptr)) return st;
         s->t_stop += ms_since(t0);
     }
     // 4. instances whose Q is ready join the sweeps from the next chunk
