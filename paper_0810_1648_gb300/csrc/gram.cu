@@ -8,7 +8,8 @@
 //     (Section 1.1).
 //
 // One CTA computes one 128 x 128 Gram tile G = X_I X_J^T by SIMT FP32 FMAs
-// (8 x 8 outputs per thread, K-chunks of 16 staged in shared memory), then
+// (8 x 8 outputs per thread, K-chunks of 16 double-buffered in shared memory,
+// two CTAs per SM for the formation kernel), then
 // runs an epilogue on the 64 values it holds: d^2 = max(0, s_i + s_j - 2 G),
 // K = expf(-gamma d^2), Q_ij = y_i y_j (K + lambda^2).  The distances use the
 // norm expansion with norms of the same FP32 rows, so d^2_ii is 0 up to
@@ -27,8 +28,8 @@ namespace {
 constexpr int KC = 16;
 
 struct GramSmem {
-    float A[KC][T + 4];
-    float B[KC][T + 4];
+    float A[2][KC][T + 4];   // double-buffered K-chunks
+    float B[2][KC][T + 4];
 };
 
 struct EpiSmem {
@@ -42,32 +43,53 @@ union TileSmem {
     EpiSmem e;
 };
 
-// acc[a][b] = <x_{I*T + ty*8 + a}, x_{J*T + tx*8 + b}>
+// acc[a][b] = <x_{I*T + ty*8 + a}, x_{J*T + tx*8 + b}>.  K-chunks of KC
+// features go through two shared-memory buffers: the next chunk's global
+// loads are in flight (in registers) while the current chunk's FMAs run, and
+// one barrier per chunk separates the buffer swaps.  Every output sums its
+// products in ascending k, as a plain loop would.
 __device__ __forceinline__ void gram_tile(const GramSide& A, const GramSide& B, int m, int I, int J,
                                           GramSmem& sm, float (&acc)[8][8])
 {
+    constexpr int LD = (T * KC) / NTHREADS;   // elements of each operand a thread stages per chunk
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
-
-    for (int k0 = 0; k0 < m; k0 += KC) {
+    float ra[LD], rb[LD];
+    auto load = [&](int k0) {
 #pragma unroll
-        for (int u = 0; u < (T * KC) / NTHREADS; ++u) {
+        for (int u = 0; u < LD; ++u) {
             const int e = tid + NTHREADS * u;
             const int row = e / KC, kk = e % KC, k = k0 + kk;
             const int ga = I * T + row, gb = J * T + row;
-            sm.A[kk][row] = (ga < A.n && k < m) ? A.X[(size_t)ga * m + k] : 0.f;
-            sm.B[kk][row] = (gb < B.n && k < m) ? B.X[(size_t)gb * m + k] : 0.f;
+            ra[u] = (ga < A.n && k < m) ? A.X[(size_t)ga * m + k] : 0.f;
+            rb[u] = (gb < B.n && k < m) ? B.X[(size_t)gb * m + k] : 0.f;
         }
-        __syncthreads();
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int u = 0; u < LD; ++u) {
+            const int e = tid + NTHREADS * u;
+            const int row = e / KC, kk = e % KC;
+            sm.A[buf][kk][row] = ra[u];
+            sm.B[buf][kk][row] = rb[u];
+        }
+    };
+    const int nch = (m + KC - 1) / KC;
+    load(0);
+    store(0);
+    __syncthreads();
+    for (int c = 0; c < nch; ++c) {
+        const int buf = c & 1;
+        if (c + 1 < nch) load((c + 1) * KC);
 #pragma unroll
         for (int kk = 0; kk < KC; ++kk) {
-            const float4 a0 = *reinterpret_cast<const float4*>(&sm.A[kk][ty * 8]);
-            const float4 a1 = *reinterpret_cast<const float4*>(&sm.A[kk][ty * 8 + 4]);
-            const float4 b0 = *reinterpret_cast<const float4*>(&sm.B[kk][tx * 8]);
-            const float4 b1 = *reinterpret_cast<const float4*>(&sm.B[kk][tx * 8 + 4]);
+            const float4 a0 = *reinterpret_cast<const float4*>(&sm.A[buf][kk][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&sm.A[buf][kk][ty * 8 + 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&sm.B[buf][kk][tx * 8]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&sm.B[buf][kk][tx * 8 + 4]);
             const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -75,6 +97,7 @@ __device__ __forceinline__ void gram_tile(const GramSide& A, const GramSide& B, 
 #pragma unroll
                 for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
         }
+        if (c + 1 < nch) store(buf ^ 1);
         __syncthreads();
     }
 }
@@ -205,7 +228,7 @@ __global__ void k_stage_list(const Inst* __restrict__ tab, const int2* __restric
 // One Gram tile per work item; every instance chained through form_next (the
 // points of a parameter grid over the same features) takes its Q tile, row
 // and column sums and tile maximum from it in turn.
-__global__ void __launch_bounds__(NTHREADS) k_form_q(const Inst* __restrict__ tab, const int4* __restrict__ work)
+__global__ void __launch_bounds__(NTHREADS, 2) k_form_q(const Inst* __restrict__ tab, const int4* __restrict__ work)
 {
     __shared__ __align__(16) TileSmem sm;
     const int4 w = work[blockIdx.x];
