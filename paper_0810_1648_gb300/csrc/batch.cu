@@ -589,23 +589,6 @@ class Engine {
         return GABP_OK;
     }
 
-    // Arms a formed instance for `iters` rounds and puts it in the lists.
-    gabp_status activate(int slot, int iters, double tol)
-    {
-        Member& M = mem[(size_t)slot];
-        EK(cudaStreamWaitEvent(stream, M.ready, 0));
-        drop_ready(M);
-        // With refinement ahead, the BF16 solve only needs to reach about the
-        // BF16 error level of its matrix before the first correction.
-        const double t0 = (q_mode != 0 && M.refine_left > 0) ? std::max(tol, handover) : tol;
-        launch_begin(d_tab + slot, 1, iters, t0, stream);
-        ++launches;
-        M.formed = true;
-        M.active = true;
-        lists_dirty = true;
-        return GABP_OK;
-    }
-
     // Arms several formed instances with one launch (their own iters / tol).
     gabp_status activate_list(const std::vector<int>& slots)
     {
@@ -723,11 +706,6 @@ class Engine {
         EK(cudaStreamSynchronize(stream));
         return GABP_OK;
     }
-    gabp_status run_chunk(int rounds)
-    {
-        if (gabp_status st = launch_chunk(rounds)) return st;
-        return wait_chunk();
-    }
 
     // Records the results of a stopped instance from its final residual /
     // objective / #SV (in h_f3) and queues the copy of alpha to the caller.
@@ -766,7 +744,6 @@ class Engine {
     //     defect-correction pass (right-hand side and restart queued on `ss`;
     //     the instance rejoins the lists at the next chunk launch) or finish
     //     (results recorded, alpha copied to the caller's buffer on `ss`).
-    // advance() runs both halves back to back on the main stream.
     struct StopBatch {
         std::vector<int> stopped;
         std::vector<char> ref;
@@ -895,17 +872,6 @@ class Engine {
         for (int k : rejoin) mem[(size_t)k].active = true;
         rejoin.clear();
         lists_dirty = true;
-        return GABP_OK;
-    }
-
-    // Both halves on the main stream (the server's step).
-    gabp_status advance(int* running, std::vector<int>* finished = nullptr)
-    {
-        if (gabp_status st = stop_begin(stream, running)) return st;
-        if (gabp_status st = stop_end(stream, finished)) return st;
-        *running += (int)rejoin.size();
-        if (gabp_status st = take_rejoin()) return st;
-        EK(cudaStreamSynchronize(stream));
         return GABP_OK;
     }
 
