@@ -64,6 +64,21 @@ def _dist():
     return ws, rank, local
 
 
+def _job_rate(units, ms, ws, device):
+    """Whole-job rate over all ranks: the units every rank processed, summed,
+    over the slowest rank's elapsed time (max over ranks).  Returns (rate per
+    second, max ms)."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    return float(u.item()) / (ms_max / 1e3), ms_max
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -544,11 +559,7 @@ def run_ours(args):
     prof = gabp.svm_get_profile(h)
     launches = prof["kernel_launches"] - launches0
     st = gabp.svm_get_stats(h)
-    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t_max.item())
-    value = ws * ROUNDS * args.steps / (ms_max / 1e3)
+    value, ms_max = _job_rate(ROUNDS * args.steps, ms, ws, dev)
 
     # roofline of the dominant kernel (the pair sweep), timed live by events
     pairs = n * (n - 1) // 2
@@ -670,10 +681,7 @@ def _e2e(args, p, stream, dev, ws, gabp, torch):
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ms2 = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(ms2, op=torch.distributed.ReduceOp.MAX)
-    e2e_value = ws * ROUNDS * args.steps / (float(ms2.item()) / 1e3)
+    e2e_value, _ = _job_rate(ROUNDS * args.steps, e0.elapsed_time(e1), ws, dev)
     gabp.svm_destroy(h2)
     return {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(p.X.nbytes + p.y.nbytes),
             "d2h_bytes_per_step": int(4 * n)}
