@@ -288,10 +288,14 @@ def run_batch(args):
     stream = torch.cuda.Stream()
     out = {}
     st = args.stages if args.stages > 1 else 4
-    for mode, kw in (("f32", dict(q_mode=0)), ("bf16q_refined", dict(q_mode=1, refine=8)),
-                     ("bf16_refined", dict(q_mode=1, refine=8, msg_bf16=1)),
-                     ("f32_staged", dict(q_mode=0, stages=st)),
-                     ("bf16_refined_staged", dict(q_mode=1, refine=8, msg_bf16=1, stages=st))):
+    all_modes = (("f32", dict(q_mode=0)), ("bf16q_refined", dict(q_mode=1, refine=8)),
+                 ("bf16_refined", dict(q_mode=1, refine=8, msg_bf16=1)),
+                 ("f32_staged", dict(q_mode=0, stages=st)),
+                 ("bf16_refined_staged", dict(q_mode=1, refine=8, msg_bf16=1, stages=st)))
+    chosen = args.batch_modes.split(",") if args.batch_modes else [m for m, _ in all_modes]
+    for mode, kw in all_modes:
+        if mode not in chosen:
+            continue
         for _ in range(args.warmup):
             gabp.batch_solve(dprobs, 200, 1e-6, chunk=0, stream=stream.cuda_stream, **kw)
         times, last = [], None
@@ -324,16 +328,21 @@ def run_batch(args):
     # end to end: host (numpy) inputs, their copies inside the timed solves
     e2e_t = []
     kw_e2e = dict(q_mode=1, refine=8, msg_bf16=1)
-    gabp.batch_solve(probs, 200, 1e-6, chunk=0, stream=stream.cuda_stream, **kw_e2e)
-    for _ in range(args.steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+    if "bf16_refined" in out:
         gabp.batch_solve(probs, 200, 1e-6, chunk=0, stream=stream.cuda_stream, **kw_e2e)
-        torch.cuda.synchronize()
-        e2e_t.append(time.perf_counter() - t0)
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            gabp.batch_solve(probs, 200, 1e-6, chunk=0, stream=stream.cuda_stream, **kw_e2e)
+            torch.cuda.synchronize()
+            e2e_t.append(time.perf_counter() - t0)
+
+    def ratio(a, b):
+        return out[a]["solves_per_s"] / out[b]["solves_per_s"] if a in out and b in out else None
     h2d = int(sum(p.X.nbytes + p.y.nbytes for p in probs))
     n2 = sum(p.n * p.n for p in probs)
-    line = {"metric": METRIC, "value": out["bf16_refined"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+    head = "bf16_refined" if "bf16_refined" in out else next(iter(out))
+    line = {"metric": METRIC, "value": out[head]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
             "config": {"workload": "batched form: 512 instances, 32 mixture data sets x C {0.1,1,10,100} x "
@@ -343,13 +352,13 @@ def run_batch(args):
                                    "(all to ||1 - Q mu||_inf < 1e-6 with the FP32-Gram Q), under the synchronous "
                                    f"schedule and the {st}-stage block Gauss-Seidel schedule",
                        "instances": len(probs), "sum_n2": n2, "stages": st},
-            "modes": out, "bf16_over_f32": out["bf16_refined"]["solves_per_s"] / out["f32"]["solves_per_s"],
-            "e2e": {"value": len(probs) / float(np.median(e2e_t)), "unit": "solves/s", "mode": "bf16_refined",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(sum(4 * p.n for p in probs))},
-            "bf16_over_f32_staged": out["bf16_refined_staged"]["solves_per_s"] / out["f32_staged"]["solves_per_s"],
-            "staged_over_synchronous": {"f32": out["f32_staged"]["solves_per_s"] / out["f32"]["solves_per_s"],
-                                        "bf16": out["bf16_refined_staged"]["solves_per_s"] /
-                                        out["bf16_refined"]["solves_per_s"]}}
+            "value_mode": head, "modes": out, "bf16_over_f32": ratio("bf16_refined", "f32"),
+            "e2e": ({"value": len(probs) / float(np.median(e2e_t)), "unit": "solves/s", "mode": "bf16_refined",
+                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(sum(4 * p.n for p in probs))}
+                    if e2e_t else None),
+            "bf16_over_f32_staged": ratio("bf16_refined_staged", "f32_staged"),
+            "staged_over_synchronous": {"f32": ratio("f32_staged", "f32"),
+                                        "bf16": ratio("bf16_refined_staged", "bf16_refined")}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -700,6 +709,9 @@ def main():
     ap.add_argument("--no-to-tol", action="store_true", help="skip the solve-to-tolerance extra measurement")
     ap.add_argument("--workload", default="plain_large",
                     choices=["plain_large", "precision_large", "batch_grid", "serve", "sparse_large"])
+    ap.add_argument("--batch-modes", default="",
+                    help="batch_grid: comma-separated subset of f32, bf16q_refined, bf16_refined, f32_staged, "
+                         "bf16_refined_staged (default all)")
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--duration", type=float, default=60.0)
     ap.add_argument("--max-members", type=int, default=64)
