@@ -320,10 +320,14 @@ GABP_API gabp_status gabp_server_phases(gabp_server_t s, double* out8);
 GABP_API gabp_status gabp_server_destroy(gabp_server_t s);
 
 /*
- * Instrumentation.  With profiling on, every pair-sweep kernel of a solve is
- * bracketed by CUDA events recorded on the handle's stream (inside the
- * captured graphs) and its device time is summed here.  kernel_launches counts
- * every kernel the handle has launched since create (always on).
+ * Instrumentation.  gabp_svm_set_profiling(h, k): k = 0 off; k >= 1 brackets
+ * the pair-sweep kernel of every k-th round (rounds k-1, 2k-1, ... of each
+ * captured chunk; k = 1: every round) by CUDA events recorded on the handle's
+ * stream inside the captured graphs, and sums their device time here (the
+ * counts below are of the bracketed sweeps).  Each event pair costs the graph
+ * a few microseconds, so a stride above 1 keeps the timed solve close to an
+ * unprofiled one.  k < 0 is GABP_EINVAL.  kernel_launches counts every kernel
+ * the handle has launched since create (always on).
  */
 typedef struct {
     int64_t sweep_launches;            /* pair sweeps timed */

@@ -79,10 +79,10 @@ struct gabp_svm_s {
     double* hfinal = nullptr;       // pinned {rinf, objective, nsv}
     struct Graph {
         cudaGraphExec_t exec = nullptr;
-        std::vector<cudaEvent_t> ev;   // 2 per round when captured with profiling on
+        std::vector<cudaEvent_t> ev;   // 2 per bracketed round when captured with profiling on
     };
-    std::map<std::pair<int, bool>, Graph> graphs;
-    bool profiling = false;
+    std::map<std::pair<int, int>, Graph> graphs;   // by (rounds, profiling stride)
+    int profiling = 0;   // 0 off, k >= 1: the pair sweep of every k-th round is bracketed by events
     gabp_svm_profile prof{};
     bool solved = false;
     int kstar = 0;
@@ -271,23 +271,29 @@ void destroy_all(gabp_svm_t h)
     delete h;
 }
 
-// A captured chunk of `rounds` synchronous rounds; with profiling on, every
-// pair sweep in it is bracketed by two event-record nodes.
+// Whether round k of a captured chunk has its pair sweep bracketed by events
+// (every `stride`-th round: k = stride - 1, 2 stride - 1, ...), and its pair.
+static bool bracketed(int stride, int k) { return stride > 0 && k % stride == stride - 1; }
+
+// A captured chunk of `rounds` synchronous rounds; with profiling on, the
+// pair sweep of every profiling-th round in it is bracketed by two
+// event-record nodes.
 gabp_status get_graph(gabp_svm_t h, int rounds, gabp_svm_s::Graph** out)
 {
-    const auto key = std::make_pair(rounds, h->profiling);
+    const int stride = h->profiling;
+    const auto key = std::make_pair(rounds, stride);
     auto it = h->graphs.find(key);
     if (it != h->graphs.end()) { *out = &it->second; return GABP_OK; }
     gabp_svm_s::Graph G;
-    if (h->profiling) {
-        G.ev.resize((size_t)2 * rounds);
+    if (stride > 0) {
+        G.ev.resize((size_t)2 * (rounds / stride));
         for (auto& e : G.ev) CK(cudaEventCreate(&e));
     }
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < rounds; ++k)
         launch_round(h->d_tab, h->work, h->nbl, h->sched, h->nstages, h->grid, h->opts.q_mode, h->opts.msg_bf16,
-                     h->stream, h->profiling ? &G.ev[(size_t)2 * k] : nullptr);
+                     h->stream, bracketed(stride, k) ? &G.ev[(size_t)2 * (k / stride)] : nullptr);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (e != cudaSuccess) return fail(GABP_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
     e = cudaGraphInstantiate(&G.exec, g, 0);
@@ -323,9 +329,11 @@ gabp_status run_rounds(gabp_svm_t h, int iters, double tol, Ctrl* out)
             CK(cudaStreamSynchronize(s));
             const int ran = h->hctrl->t - t_before;
             if (!g->ev.empty()) {
+                const int stride = h->profiling;
                 for (int k = 0; k < ran && k < len; ++k) {
+                    if (!bracketed(stride, k)) continue;
                     float ms = 0.f;
-                    CK(cudaEventElapsedTime(&ms, g->ev[(size_t)2 * k], g->ev[(size_t)2 * k + 1]));
+                    CK(cudaEventElapsedTime(&ms, g->ev[(size_t)2 * (k / stride)], g->ev[(size_t)2 * (k / stride) + 1]));
                     h->prof.sweep_ms += ms;
                     h->prof.sweep_launches += 1;
                     if (t_before + k == 0) h->prof.sweep_launches_zero_state += 1;
@@ -851,7 +859,8 @@ gabp_status gabp_svm_set_profiling(gabp_svm_t h, int32_t on)
 {
     g_err.clear();
     if (gabp_status s = check_handle(h)) return s;
-    h->profiling = on != 0;
+    if (on < 0) return fail(GABP_EINVAL, "profiling stride must be >= 0");
+    h->profiling = on;
     return GABP_OK;
 }
 

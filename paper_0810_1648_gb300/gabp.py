@@ -296,8 +296,9 @@ def svm_get_aggregates(h, n: int):
     return Pt, ht, mu
 
 
-def svm_set_profiling(h, on: bool):
-    _check(load().gabp_svm_set_profiling(ctypes.c_void_p(h), 1 if on else 0))
+def svm_set_profiling(h, on):
+    """on: False / 0 off, True / 1 every round's pair sweep timed, k > 1 every k-th round's."""
+    _check(load().gabp_svm_set_profiling(ctypes.c_void_p(h), int(on)))
 
 
 def svm_get_profile(h, reset: bool = False) -> dict:
