@@ -131,6 +131,126 @@ double ms_since(std::chrono::steady_clock::time_point t0)
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
+
+// The round lists of the live instances (live[k] != 0), built on the device
+// so that a membership change costs one small copy and one launch instead of
+// host loops over every tile: tiles grouped by stage and, within a stage, by
+// instance in slot order, each instance's tiles (I, J) of the stage's band
+// I-major (the order the sweeps' results do not depend on, kept anyway);
+// node blocks of the instances finalized one warp per block first; and every
+// stage's Sched.  One CTA: the instances go through in chunks of blockDim
+// with a block-wide scan for their offsets, one warp writes one instance's
+// entries.
+constexpr int kListThreads = 1024;
+
+__device__ __forceinline__ long long block_scan_excl(long long v, long long* sc)
+{
+    const int tid = threadIdx.x;
+    sc[tid] = v;
+    __syncthreads();
+    for (int d = 1; d < (int)blockDim.x; d <<= 1) {
+        const long long a = tid >= d ? sc[tid - d] : 0;
+        __syncthreads();
+        sc[tid] += a;
+        __syncthreads();
+    }
+    return sc[tid] - v;   // sc[blockDim - 1] holds the chunk's total until the next call
+}
+
+__global__ void __launch_bounds__(kListThreads)
+    k_build_lists(const Inst* __restrict__ tab, const int* __restrict__ live, int cap, int S,
+                  int4* __restrict__ work, int2* __restrict__ nbl, Sched* __restrict__ sched)
+{
+    __shared__ long long sc[kListThreads];
+    __shared__ long long m_off[kListThreads];
+    __shared__ int m_k[kListThreads], m_a[kListThreads], m_b[kListThreads], m_c[kListThreads];
+    __shared__ long long s_tiles[kMaxStages];
+    __shared__ long long s_blocks[2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (int)blockDim.x >> 5;
+    // ---- tiles, stage by stage
+    long long base = 0;
+    for (int s = 0; s < S; ++s) {
+        long long carry = 0;
+        for (int c0 = 0; c0 < cap; c0 += (int)blockDim.x) {
+            const int k = c0 + tid;
+            long long cnt = 0;
+            int Nt = 0, Bs = 0, Be = 0;
+            if (k < cap && live[k]) {
+                Nt = tab[k].Nt;
+                int B[kMaxStages + 1];
+                stage_bounds(Nt, S, B);
+                Bs = B[s];
+                Be = B[s + 1];
+                const long long w = Be - Bs;
+                cnt = (long long)Bs * w + w * (w + 1) / 2;
+            }
+            const long long ex = block_scan_excl(cnt, sc);
+            m_off[tid] = base + carry + ex;
+            m_k[tid] = cnt > 0 ? k : -1;
+            m_a[tid] = Nt;
+            m_b[tid] = Bs;
+            m_c[tid] = Be;
+            const long long total = sc[blockDim.x - 1];
+            __syncthreads();
+            for (int i = warp; i < (int)blockDim.x; i += nw) {
+                if (m_k[i] < 0) continue;
+                const int kk = m_k[i], nt = m_a[i], bs = m_b[i], be = m_c[i];
+                long long o = m_off[i];
+                for (int I = 0; I < be; ++I) {
+                    const int J0 = I > bs ? I : bs;
+                    const long long Lrow = (long long)I * nt - (long long)I * (I - 1) / 2 - I;
+                    for (int J = J0 + lane; J < be; J += 32)
+                        work[o + (J - J0)] = make_int4(kk, I, J, (int)(Lrow + J));
+                    o += be - J0;
+                }
+            }
+            carry += total;
+            __syncthreads();
+        }
+        if (tid == 0) s_tiles[s] = carry;
+        base += carry;
+    }
+    // ---- node blocks: instances with at most kWarpFinNt tile rows first
+    long long bbase = 0;
+    for (int g = 0; g < 2; ++g) {
+        long long carry = 0;
+        for (int c0 = 0; c0 < cap; c0 += (int)blockDim.x) {
+            const int k = c0 + tid;
+            long long cnt = 0;
+            if (k < cap && live[k]) {
+                const int Nt = tab[k].Nt;
+                if ((Nt <= kWarpFinNt) == (g == 0)) cnt = (tab[k].n + 31) / 32;
+            }
+            const long long ex = block_scan_excl(cnt, sc);
+            m_off[tid] = bbase + carry + ex;
+            m_k[tid] = cnt > 0 ? k : -1;
+            m_a[tid] = (int)cnt;
+            const long long total = sc[blockDim.x - 1];
+            __syncthreads();
+            for (int i = warp; i < (int)blockDim.x; i += nw) {
+                if (m_k[i] < 0) continue;
+                for (int b = lane; b < m_a[i]; b += 32) nbl[m_off[i] + b] = make_int2(m_k[i], b);
+            }
+            carry += total;
+            __syncthreads();
+        }
+        if (tid == 0) s_blocks[g] = carry;
+        bbase += carry;
+    }
+    __syncthreads();
+    if (tid < S) {
+        long long off = 0;
+        for (int s2 = 0; s2 < tid; ++s2) off += s_tiles[s2];
+        Sched q{};
+        q.ntiles = s_tiles[tid];
+        q.nblocks = (int)(s_blocks[0] + s_blocks[1]);
+        q.ninst = cap;
+        q.off = off;
+        q.nsmall = (int)s_blocks[0];
+        sched[tid] = q;
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- Engine
@@ -165,6 +285,8 @@ class Engine {
     int4* d_work = nullptr;
     int2* d_nbl = nullptr;
     Sched* d_sched = nullptr;
+    int* d_live = nullptr;        // instances in the round lists (list build input)
+    int* h_live = nullptr;        // its pinned mirror
     Ctrl* h_ctrl = nullptr;       // pinned mirror
     Inst* h_tab = nullptr;        // pinned staging of the instance table (uploaded per formation group)
     double* h_f3 = nullptr;       // pinned {residual, objective, #SV} per slot
@@ -209,6 +331,7 @@ class Engine {
         if (d_tab) cudaFree(d_tab);
         for (auto& g : evg) cudaEventDestroy(g.ev);
         if (h_tab) cudaFreeHost(h_tab);
+        if (h_live) cudaFreeHost(h_live);
         if (h_ctrl) cudaFreeHost(h_ctrl);
         if (h_f3) cudaFreeHost(h_f3);
         if (h_ops) cudaFreeHost(h_ops);
@@ -267,8 +390,9 @@ class Engine {
         const size_t b_bt = aup((size_t)cap_members * sizeof(double), 256);
         char* base = nullptr;
         const size_t b_sched = aup((size_t)kMaxStages * sizeof(Sched), 256);
+        const size_t b_live = aup((size_t)cap_members * sizeof(int), 256);
         EK(cudaMalloc((void**)&base,
-                      b_tab + b_ctrl + 2 * b_work + 2 * b_nbl + b_ops + b_f3 + b_mem + 2 * b_bl + 2 * b_bt + b_sched));
+                      b_tab + b_ctrl + 2 * b_work + 2 * b_nbl + b_ops + b_f3 + b_mem + 2 * b_bl + 2 * b_bt + b_sched + b_live));
         size_t off = 0;
         auto carve = [&](size_t bytes) { char* r = base + off; off += bytes; return r; };
         d_tab = (Inst*)carve(b_tab);
@@ -285,10 +409,12 @@ class Engine {
         d_restart_list = (int2*)carve(b_bl);
         d_restart_tol = (double*)carve(b_bt);
         d_sched = (Sched*)carve(b_sched);   // one per stage
+        d_live = (int*)carve(b_live);
         EK(cudaMemsetAsync(d_ctrl, 0, b_ctrl, stream));
         EK(cudaMemsetAsync(d_sched, 0, b_sched, stream));
         EK(cudaMallocHost((void**)&h_ctrl, (size_t)cap_members * sizeof(Ctrl)));
         EK(cudaMallocHost((void**)&h_tab, (size_t)cap_members * sizeof(Inst)));
+        EK(cudaMallocHost((void**)&h_live, (size_t)cap_members * sizeof(int)));
         EK(cudaMallocHost((void**)&h_f3, (size_t)cap_members * 3 * sizeof(double)));
         EK(cudaMallocHost((void**)&h_ops, (size_t)cap_members * sizeof(StopOp)));
         std::memset(h_ops, 0, (size_t)cap_members * sizeof(StopOp));
@@ -623,46 +749,24 @@ class Engine {
             ~Acc() { t += ms_since(t0); }
         } acc{t_rebuild, t0};
         ++rebuilds;
-        // tiles grouped by stage (one stage under the synchronous schedule),
-        // every instance with its own stage bounds; node blocks of all
-        std::vector<int4> wl;
-        std::vector<int2> nb;
-        Sched sc[kMaxStages];
-        for (int st = 0; st < nstages; ++st) {
-            const long long off = (long long)wl.size();
-            for (int k = 0; k < cap_members; ++k) {
-                const Member& M = mem[(size_t)k];
-                if (!M.used || !M.active) continue;
-                const int Nt = M.inst.Nt;
-                int B[kMaxStages + 1];
-                stage_bounds(Nt, nstages, B);
-                for (int I = 0; I < Nt; ++I)
-                    for (int J = std::max(I, B[st]); J < B[st + 1]; ++J)
-                        wl.push_back(make_int4(k, I, J, (int)((long long)I * Nt - (long long)I * (I - 1) / 2 + (J - I))));
+        // membership on the host, the lists themselves on the device (in
+        // stream order before the next chunk)
+        long long tiles = 0, blocks = 0;
+        for (int k = 0; k < cap_members; ++k) {
+            const Member& M = mem[(size_t)k];
+            const bool in = M.used && M.active;
+            h_live[k] = in ? 1 : 0;
+            if (in) {
+                tiles += M.ntiles;
+                blocks += M.nblk;
             }
-            sc[st] = Sched{(long long)wl.size() - off, 0, cap_members, off};
         }
-        // node blocks of the instances finalized one warp per block first
-        int nsmall = 0;
-        for (int pass = 0; pass < 2; ++pass) {
-            for (int k = 0; k < cap_members; ++k) {
-                const Member& M = mem[(size_t)k];
-                if (!M.used || !M.active || (M.inst.Nt <= kWarpFinNt) != (pass == 0)) continue;
-                for (int b = 0; b < M.nblk; ++b) nb.push_back(make_int2(k, b));
-            }
-            if (pass == 0) nsmall = (int)nb.size();
-        }
-        for (int st = 0; st < nstages; ++st) {
-            sc[st].nblocks = (int)nb.size();
-            sc[st].nsmall = nsmall;
-        }
-        if ((long long)wl.size() > cap_tiles || (int)nb.size() > cap_nblk)
-            return fail(GABP_ENOMEM, "batch lists exceed their capacity");
-        if (!wl.empty()) EK(cudaMemcpyAsync(d_work, wl.data(), wl.size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
-        if (!nb.empty()) EK(cudaMemcpyAsync(d_nbl, nb.data(), nb.size() * sizeof(int2), cudaMemcpyHostToDevice, stream));
-        EK(cudaMemcpyAsync(d_sched, sc, (size_t)nstages * sizeof(Sched), cudaMemcpyHostToDevice, stream));
-        EK(cudaStreamSynchronize(stream));   // host vectors go out of scope
-        live_tiles = (long long)wl.size();
+        if (tiles > cap_tiles || blocks > cap_nblk) return fail(GABP_ENOMEM, "batch lists exceed their capacity");
+        EK(cudaMemcpyAsync(d_live, h_live, (size_t)cap_members * sizeof(int), cudaMemcpyHostToDevice, stream));
+        k_build_lists<<<1, kListThreads, 0, stream>>>(d_tab, d_live, cap_members, nstages, d_work, d_nbl, d_sched);
+        EK(cudaGetLastError());
+        ++launches;
+        live_tiles = tiles;
         lists_dirty = false;
         return GABP_OK;
     }

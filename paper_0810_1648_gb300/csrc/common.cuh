@@ -119,7 +119,7 @@ constexpr int kMaxStages = 16;
 // B[S] = Nt, B[s] = the smallest b with S b (b + 1) / 2 >= s Nt (Nt + 1) / 2
 // (about equal tile counts per stage); tile (I, J) runs in the stage whose
 // range [B[s], B[s+1]) holds J.
-inline void stage_bounds(int Nt, int S, int* B)
+__host__ __device__ inline void stage_bounds(int Nt, int S, int* B)
 {
     const long long tot = (long long)Nt * (Nt + 1) / 2;
     B[0] = 0;
