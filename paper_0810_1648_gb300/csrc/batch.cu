@@ -132,6 +132,16 @@ double ms_since(std::chrono::steady_clock::time_point t0)
 }
 
 
+// Copies `count` words of W bytes from a host buffer the GPU reads coherently
+// (pageable memory on a system with cudaDevAttrPageableMemoryAccess) into
+// device memory; grid-stride.
+template <class W>
+__global__ void k_fetch(const W* __restrict__ src, W* __restrict__ dst, size_t count)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
 // The round lists of the live instances (live[k] != 0), built on the device
 // so that a membership change costs one small copy and one launch instead of
 // host loops over every tile: tiles grouped by stage and, within a stage, by
@@ -270,6 +280,7 @@ class Engine {
     } while (0)
 
     int q_mode = 0, diag_rule = 0, x_f64 = 0, ptr_mode = 0, msg_bf16 = 0, task = 0, bias_mode = 0;
+    bool host_direct = false;   // the GPU reads pageable host memory coherently
     int nstages = 1;   // message schedule: 1 synchronous, > 1 staged
     double delta = 0.1, sv_threshold = 0.0, bias_lambda = 0.0;
     double handover = 1e-4, inner = 1e-2;   // refinement schedule
@@ -366,6 +377,12 @@ class Engine {
             own_stream = true;
         }
         EK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+        {
+            int dev = 0, pma = 0;
+            EK(cudaGetDevice(&dev));
+            if (cudaDeviceGetAttribute(&pma, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) pma = 0;
+            host_direct = pma != 0;
+        }
         EK(cudaStreamCreateWithFlags(&sstream, cudaStreamNonBlocking));
         EK(cudaEventCreateWithFlags(&rejoin_ev, cudaEventDisableTiming));
         {
@@ -447,6 +464,39 @@ class Engine {
     }
 
     bool alias_x() const { return ptr_mode == 1 && x_f64 == 0; }
+
+    // Host-to-device copy of an input array.  Where the GPU reads pageable
+    // host memory coherently (cudaDevAttrPageableMemoryAccess, e.g. a Grace
+    // CPU over NVLink-C2C), unregistered host buffers are pulled by a kernel
+    // instead of the driver's staged copy, which blocks the calling thread;
+    // pinned or registered buffers go by DMA.
+    gabp_status fetch(void* dst, const void* src, size_t bytes, cudaStream_t s)
+    {
+        cudaPointerAttributes a{};
+        const bool pageable = host_direct && cudaPointerGetAttributes(&a, src) == cudaSuccess &&
+                              a.type == cudaMemoryTypeUnregistered;
+        cudaGetLastError();   // clear a failed attribute query
+        if (!pageable || bytes % 4 != 0 || ((uintptr_t)src | (uintptr_t)dst) % 4 != 0) {
+            EK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+            return GABP_OK;
+        }
+        // a few CTAs: enough loads in flight for the link, few SM slots taken
+        // from the sweeps that run beside admission
+        constexpr size_t kFetchCtas = 32;
+        if ((((uintptr_t)src | (uintptr_t)dst) % 16) == 0 && bytes % 16 == 0) {
+            const size_t c = bytes / 16;
+            const unsigned g = (unsigned)std::min<size_t>((c + 255) / 256, kFetchCtas);
+            k_fetch<uint4><<<std::max(1u, g), 256, 0, s>>>(static_cast<const uint4*>(src), static_cast<uint4*>(dst), c);
+        } else {
+            const size_t c = bytes / 4;
+            const unsigned g = (unsigned)std::min<size_t>((c + 255) / 256, kFetchCtas);
+            k_fetch<unsigned><<<std::max(1u, g), 256, 0, s>>>(static_cast<const unsigned*>(src),
+                                                               static_cast<unsigned*>(dst), c);
+        }
+        EK(cudaGetLastError());
+        ++launches;
+        return GABP_OK;
+    }
     // labels in device memory are read in place unless the task rewrites them
     bool alias_y() const { return ptr_mode == 1 && task != GABP_TASK_KRR; }
 
@@ -593,13 +643,15 @@ class Engine {
         M.res.alpha = out_alpha;
         // (the table entry and the control block are uploaded by form_pending)
         h_tab[slot] = p;
-        if (!alias_y())
-            EK(cudaMemcpyAsync((void*)p.y, pr.y, (size_t)n * 4,
-                               ptr_mode ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        if (!alias_y()) {
+            if (ptr_mode) EK(cudaMemcpyAsync((void*)p.y, pr.y, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+            else if (gabp_status st = fetch((void*)p.y, pr.y, (size_t)n * 4, s)) return st;
+        }
         if (!x_f64) {
             // FP32 rows: read in place from device memory, else copied into X;
             // the batched staging of form_pending() checks them
-            if (!alias_x()) EK(cudaMemcpyAsync((void*)p.X, pr.X, (size_t)n * m * 4, cudaMemcpyHostToDevice, s));
+            if (!alias_x())
+                if (gabp_status st = fetch((void*)p.X, pr.X, (size_t)n * m * 4, s)) return st;
         } else {
             // FP64 input: convert and check now
             EK(cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), s));
@@ -607,7 +659,7 @@ class Engine {
             void* tmp = nullptr;
             if (!ptr_mode) {
                 EK(cudaMallocAsync(&tmp, (size_t)n * m * 8, s));
-                EK(cudaMemcpyAsync(tmp, pr.X, (size_t)n * m * 8, cudaMemcpyHostToDevice, s));
+                if (gabp_status st = fetch(tmp, pr.X, (size_t)n * m * 8, s)) return st;
                 src = tmp;
             }
             launch_stage(src, x_f64, (int)n, (int)m, const_cast<float*>(p.y), (float*)p.X, (float*)p.sq,
