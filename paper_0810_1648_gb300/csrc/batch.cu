@@ -14,9 +14,13 @@
 // gabp_batch_solve runs a fixed set to completion; gabp_server_* admits
 // instances as they arrive, by device-memory budget, forms their Q on a side
 // stream while the others keep sweeping, and retires them as they converge
-// (continuous batching).  The schedule knobs (persistent sweep CTAs per SM,
-// rounds per convergence check) are chosen by measuring candidates on the
-// actual set; results are cached per shape signature.
+// (continuous batching).  The end-of-solve work of the instances that stopped
+// in a chunk (final residual, refinement restart, result copy) runs on a
+// third stream during the next chunk; the round lists are rebuilt on the
+// device from a membership mask.  The schedule knobs (persistent sweep CTAs
+// per SM, rounds per convergence check) are chosen by measuring candidates on
+// the actual set; results are cached per shape signature.  The engine of a
+// thread's last gabp_batch_solve is kept for its next compatible call.
 #include "common.cuh"
 #include "gabp_svm.h"
 
