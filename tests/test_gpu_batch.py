@@ -284,3 +284,30 @@ def test_batch_engine_kept_between_calls():
         np.testing.assert_array_equal(x, y)
     for r in (r1, r3):
         assert [q["iters_done"] for q in r] == [q["iters_done"] for q in r0]
+
+
+def _offset_copy(a, offset_bytes):
+    """A C-contiguous copy of `a` whose data starts `offset_bytes` past a
+    64-byte boundary (host inputs not aligned to 16 bytes)."""
+    buf = np.zeros(a.nbytes + 128, dtype=np.uint8)
+    start = (-buf.ctypes.data) % 64 + offset_bytes
+    out = np.frombuffer(buf.data, dtype=a.dtype, count=a.size, offset=start).reshape(a.shape)
+    out[...] = a
+    assert out.ctypes.data % 16 == offset_bytes % 16
+    return out
+
+
+def test_batch_host_inputs_any_alignment():
+    """Host (pageable) inputs are copied in whatever way the platform offers
+    (a copy kernel where the GPU reads pageable memory, 16-byte or 4-byte
+    words, else the driver's copy); misaligned buffers give the same results
+    as aligned ones."""
+    probs = _mix(4, 11)
+    a0, r0, rc = gabp.batch_solve(probs, 30, 1e-6, chunk=4)
+    assert rc == gabp.OK
+    mis = [workloads.Problem(_offset_copy(p.X, 4), _offset_copy(np.asarray(p.y, np.float32), 8), p.gamma, p.C)
+           for p in probs]
+    a1, r1, rc = gabp.batch_solve(mis, 30, 1e-6, chunk=4)
+    assert rc == gabp.OK
+    for x, y in zip(a0, a1):
+        np.testing.assert_array_equal(x, y)
