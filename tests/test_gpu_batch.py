@@ -311,3 +311,23 @@ def test_batch_host_inputs_any_alignment():
     assert rc == gabp.OK
     for x, y in zip(a0, a1):
         np.testing.assert_array_equal(x, y)
+
+
+def test_batch_grid_fp64_inputs_share_gram():
+    """FP64 host features (converted on the device while the instances are
+    added) shared by a grid give the same results as private copies, and as
+    the FP32 rounding of the same features."""
+    grid = _grid(seeds=(51,), n=(230,), m=(12,))
+    g64 = [workloads.Problem(grid[0].X.astype(np.float64), p.y, p.gamma, p.C) for p in grid]
+    for p in g64[1:]:
+        p.X = g64[0].X
+    private = [workloads.Problem(p.X.copy(), p.y, p.gamma, p.C) for p in g64]
+    a_sh, _, rc = gabp.batch_solve(g64, 30, 0.0, chunk=8)
+    assert rc == gabp.OK
+    a_pr, _, rc = gabp.batch_solve(private, 30, 0.0, chunk=8)
+    assert rc == gabp.OK
+    a_32, _, rc = gabp.batch_solve(grid, 30, 0.0, chunk=8)
+    assert rc == gabp.OK
+    for x, y, z in zip(a_sh, a_pr, a_32):
+        np.testing.assert_array_equal(x, y)
+        np.testing.assert_array_equal(x, z)
