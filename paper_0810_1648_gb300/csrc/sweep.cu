@@ -368,23 +368,6 @@ __device__ __forceinline__ void st4(float* row, int lane, const float (&o)[4])
     }
 }
 
-// Sums {a, b, c, 0} over the warp in a fixed order: afterwards every lane of
-// the group lane / 8 = k holds the total of quantity k (six shuffles).
-__device__ __forceinline__ float reduce_scatter4(float a, float b, float c, int lane)
-{
-    const bool hi = (lane & 16) != 0;
-    const float k0 = hi ? c : a, k1 = hi ? 0.f : b;
-    const float s0 = hi ? a : c, s1 = hi ? b : 0.f;
-    const float x0 = k0 + __shfl_xor_sync(0xffffffffu, s0, 16);
-    const float x1 = k1 + __shfl_xor_sync(0xffffffffu, s1, 16);
-    const bool b3 = (lane & 8) != 0;
-    float v = (b3 ? x1 : x0) + __shfl_xor_sync(0xffffffffu, b3 ? x0 : x1, 8);
-    v += __shfl_xor_sync(0xffffffffu, v, 4);
-    v += __shfl_xor_sync(0xffffffffu, v, 2);
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    return v;
-}
-
 // Sums the eight values {a0, a1, a2, 0, b0, b1, b2, 0} over the warp in a
 // fixed order: afterwards every lane of the group (lane / 4) % 8 = k holds the
 // total of value k (nine shuffles for two rows).
