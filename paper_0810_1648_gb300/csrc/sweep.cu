@@ -550,12 +550,9 @@ __device__ __forceinline__ void consume_tile(const QSrc& qsrc, SweepTail& sm, co
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.empty[stage]);
         if (++stage == stages<MSG>()) { stage = 0; phase ^= 1u; }
-        // row sums {P, H, R} of the warp's rows over the warp
-        if constexpr (RPW == 1) {
-            const float v = reduce_scatter4(rs[0][0], rs[0][1], rs[0][2], lane);
-            const int qv = lane >> 3, r = ch * RC + cw;
-            if ((lane & 7) == 0 && qv < 3 && r < rows) (qv == 0 ? sm.rp : (qv == 1 ? sm.rh : sm.rr))[r] = v;
-        } else {
+        // row sums {P, H, R} of the warp's two rows over the warp
+        static_assert(RPW == 2, "two rows per consumer warp and ring stage");
+        {
             const float v = reduce_scatter8(rs[0][0], rs[0][1], rs[0][2], rs[1][0], rs[1][1], rs[1][2], lane);
             const int qi = (lane >> 2) & 7, qv = qi & 3, r = ch * RC + cw + NWARPS * (qi >> 2);
             if ((lane & 3) == 0 && qv < 3 && r < rows) (qv == 0 ? sm.rp : (qv == 1 ? sm.rh : sm.rr))[r] = v;
