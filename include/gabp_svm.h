@@ -285,12 +285,16 @@ GABP_API gabp_status gabp_batch_release(void);
 /*
  * Continuous-batching server.  Requests queue in arrival order; each
  * gabp_server_step() launches one chunk of rounds over every live instance,
- * admits queued requests while it runs (free slots and the device memory
- * budget permitting; their Q is formed on a side stream while the other
- * instances keep sweeping), retires the instances that stopped (their alpha
- * is copied to the caller's buffer), and lets instances whose formation has
- * finished join from the next chunk.  The problem's X and y must stay valid
- * until its ticket completes.
+ * and while it runs finishes the instances that stopped in the previous
+ * chunk (their final passes ran on a stop stream meanwhile: results recorded,
+ * alpha copied to the caller's buffer, or the next refinement pass started)
+ * and admits queued requests (free slots and the device memory budget
+ * permitting; their Q is formed on a side stream while the other instances
+ * keep sweeping); after the chunk it takes the instances that stopped out of
+ * the sweeps and queues their final passes, and lets instances whose
+ * formation has finished join from the next chunk.  A ticket therefore
+ * completes one step after its instance stopped.  The problem's X and y must
+ * stay valid until its ticket completes.
  */
 typedef struct gabp_server_s* gabp_server_t;
 typedef struct {
