@@ -349,9 +349,9 @@ GABP_API gabp_status gabp_svm_get_profile(gabp_svm_t h, gabp_svm_profile* out, i
 /*
  * Decision values with no device allocation (the paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory,
- * e.g. code running during CUDA graph capture, plugins whose host framework
- * owns all device memory, or loops that cannot afford cudaMalloc's implicit
- * synchronisation).
+ * e.g. plugins inside a host framework that owns all device memory through
+ * its own allocator, or serving loops that cannot afford the device-wide
+ * synchronisation that cudaMalloc and cudaFree imply).
  *
  * Computes out[s] = sum_i alpha_i y_i (exp(-gamma ||x_i - xt_s||^2) + lambda^2)
  * for s < t, like gabp_svm_decision, but without a handle.  All pointers are

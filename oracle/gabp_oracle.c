@@ -50,6 +50,16 @@ void orc_set_threads(int t)
 #endif
 }
 
+/* Index of the calling thread inside a parallel region (0 without OpenMP). */
+static int orc_thread_id(void)
+{
+#ifdef _OPENMP
+    return omp_get_thread_num();
+#else
+    return 0;
+#endif
+}
+
 /* RBF kernel value K(a, b) = exp(-gamma ||a - b||^2) by the direct difference
  * (Section 1.1 names the radial-basis kernel; Section 5 uses it for every
  * experiment). */
@@ -120,12 +130,12 @@ int orc_q_diag_all(const double* X, const double* y, long n, long m, double gamm
                    double lam, double C, int diag_rule, double delta, double* diag, double* R)
 {
     if (n < 1 || m < 1 || !(gamma > 0) || !(C > 0)) return ORC_EINVAL;
-    const int T = omp_get_max_threads();
+    const int T = orc_threads();
     double* acc = (double*)calloc((size_t)T * (size_t)n, sizeof(double));
     if (!acc) return ORC_ENOMEM;
 #pragma omp parallel
     {
-        double* mine = acc + (size_t)omp_get_thread_num() * (size_t)n;
+        double* mine = acc + (size_t)orc_thread_id() * (size_t)n;
 #pragma omp for schedule(dynamic, 16)
         for (long i = 0; i < n; ++i) {
             double ri = 0.0;

@@ -604,11 +604,10 @@ void launch_get_q(const Inst& p, const int4* work, long long ntiles, int q_bf16,
 // ---------------------------------------------------------------------------
 // Decision values with no device allocation.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured (allocation calls are not allowed there), plugins inside a
-// host framework that owns all device memory through its own allocator, and
-// latency-critical loops that cannot afford the implicit device-wide
-// synchronisation of cudaMalloc/cudaFree.  gabp_decision_noalloc serves them:
+// Some callers cannot call cudaMalloc: plugins inside a host framework that
+// owns all device memory through its own allocator, and latency-critical
+// loops that cannot afford the implicit device-wide synchronisation of
+// cudaMalloc/cudaFree.  gabp_decision_noalloc serves them:
 // the caller passes every input and output as device memory, and the
 // temporaries (row norms and per-tile partial sums) live in the file-scope
 // array below, which every GPU that loads this library holds until the

@@ -444,10 +444,14 @@ __device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char
         // With P at its fixed point, P_ij = -q^2 / d_i, so the H update
         // -q (htilde_i - H_ji) / d_i equals P_ij (htilde_i - H_ji) / q: one
         // reciprocal per pair, no cavity subtraction (the cavities were
-        // checked when these P values were formed).  q = 0 gives P = 0, H = 0.
+        // checked when these P values were formed).  For |q| below the
+        // smallest normal float (q = 0, or an RBF value exp(-gamma d^2) that
+        // underflowed to a subnormal) q^2 is 0, so P = 0 and H is taken as 0:
+        // the hardware reciprocal would flush such a q and give inf, and
+        // 0 * inf a NaN.
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const float qi = q[k] != 0.f ? rcp_nr(q[k]) : 0.f;
+            const float qi = fabsf(q[k]) >= FLT_MIN ? rcp_nr(q[k]) : 0.f;
             nw[k] = MSG::pack(pv[k].x * (rH - hv[k].y) * qi, pv[k].y * (cv.H[k] - hv[k].x) * qi);
         }
     } else {

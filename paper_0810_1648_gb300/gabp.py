@@ -307,8 +307,34 @@ def svm_get_profile(h, reset: bool = False) -> dict:
     return p.as_dict()
 
 
+def _check_noalloc_args(X, y, alpha, Xt, out):
+    """The arguments of decision_noalloc: contiguous float32 CUDA tensors on one
+    device, X (n x m) and Xt (t x m) with the same m, y and alpha of length n,
+    out of length t.  Raises GabpError(EINVAL) before any library call."""
+    def bad(msg):
+        raise GabpError(EINVAL, "decision_noalloc: " + msg)
+    ts = {"X": X, "y": y, "alpha": alpha, "Xt": Xt, "out": out}
+    for k, v in ts.items():
+        if not _is_torch(v) or not v.is_cuda:
+            bad(f"{k} must be a CUDA tensor")
+        if str(v.dtype) != "torch.float32":
+            bad(f"{k} must be float32 (got {v.dtype})")
+        if not v.is_contiguous():
+            bad(f"{k} must be contiguous")
+    if len({v.device for v in ts.values()}) != 1:
+        bad("all tensors must be on one device")
+    if X.dim() != 2 or Xt.dim() != 2 or X.shape[1] != Xt.shape[1]:
+        bad("X and Xt must be 2-D with the same number of columns")
+    n, t = int(X.shape[0]), int(Xt.shape[0])
+    if y.numel() != n or alpha.numel() != n:
+        bad(f"y and alpha need {n} entries")
+    if out.numel() != t:
+        bad(f"out needs {t} entries")
+
+
 def decision_noalloc(X, y, alpha, Xt, gamma: float, lam: float, out, stream=None):
     """gabp_decision_noalloc: torch CUDA float32 tensors, no allocation in the library."""
+    _check_noalloc_args(X, y, alpha, Xt, out)
     _sync_torch(X, y, alpha, Xt)
     _check(load().gabp_decision_noalloc(_ptr(X), _ptr(y), _ptr(alpha), int(X.shape[0]), int(X.shape[1]),
                                         _ptr(Xt), int(Xt.shape[0]), float(gamma), float(lam), _ptr(out),

@@ -69,3 +69,18 @@ def test_no_gpu_fails_loudly(lib):
     with pytest.raises(gabp.GabpError) as ei:
         gabp.svm_create(X, y, 0.5, 1.0)
     assert ei.value.status == gabp.ECUDA
+
+
+def test_noalloc_binding_rejects_bad_arguments():
+    """decision_noalloc checks dtype, device and shapes before the call: a CPU
+    or float64 tensor, or mismatched sizes, never reach the kernels."""
+    torch = pytest.importorskip("torch")
+    X = torch.zeros((8, 3))
+    y, a = torch.ones(8), torch.zeros(8)
+    Xt, out = torch.zeros((5, 3)), torch.zeros(5)
+    with pytest.raises(gabp.GabpError) as ei:
+        gabp.decision_noalloc(X, y, a, Xt, 0.5, 0.0, out)
+    assert ei.value.status == gabp.EINVAL and "CUDA" in ei.value.message
+    with pytest.raises(gabp.GabpError) as ei:
+        gabp.decision_noalloc(np.zeros((8, 3), np.float32), y, a, Xt, 0.5, 0.0, out)
+    assert ei.value.status == gabp.EINVAL

@@ -109,6 +109,43 @@ def test_plain_small_workload_to_tolerance():
     np.testing.assert_array_equal(s.support(), np.nonzero(alpha > 0)[0])
 
 
+def _far_point(p, t=95.0):
+    """p with its last point moved so that gamma ||x_last - x_j||^2 is about t
+    for every other j: exp(-t) then lies below the smallest normal FP32 value
+    (for t between about 87.3 and 103.3) while staying nonzero."""
+    X = p.X.copy()
+    u = np.zeros(X.shape[1], dtype=np.float32)
+    u[0] = 1.0
+    c = np.sqrt(max(t / p.gamma - float(np.mean(np.sum(X[:-1] ** 2, axis=1))), 1.0))
+    X[-1] = c * u
+    return workloads.Problem(X, p.y, p.gamma, p.C)
+
+
+@pytest.mark.parametrize("task", ["svm_no_bias", "krr"])
+def test_subnormal_entries_past_the_p_freeze(task):
+    """Kernel entries that underflow to subnormal FP32 values (no bias term:
+    the SVM with lambda = 0, and kernel ridge regression) through the rounds
+    after the P messages froze (a few rounds in), against the oracle."""
+    p = _far_point(workloads.mixture(300, 16, seed=21, C=1.0))
+    X64 = p.X.astype(np.float64)
+    d2 = np.sum((X64[:-1] - X64[-1]) ** 2, axis=1)
+    k32 = np.exp(-p.gamma * d2).astype(np.float32)
+    assert int(np.sum((k32 != 0) & (np.abs(k32) < np.finfo(np.float32).tiny))) > 100
+    iters = 40
+    if task == "krr":
+        t = workloads.krr_targets(p, 3)
+        s = gabp.GabpSVM(p.X, t, p.gamma, 1.0, task=gabp.TASK_KRR)
+        _, r = oracle.solve_krr(p.X.astype(np.float64), t.astype(np.float64), p.gamma, 1.0, iters=iters, tol=0.0)
+    else:
+        s = gabp.GabpSVM(p.X, p.y, p.gamma, p.C, bias_mode=1, bias_lambda=0.0)
+        _, r = oracle.solve_svm(X64, p.y.astype(np.float64), p.gamma, p.C, iters=iters, tol=0.0, lam=0.0)
+    _, rinf, k = s.solve(iters, 0.0)
+    mu = s.mean().astype(np.float64)
+    assert k == iters and np.all(np.isfinite(mu))
+    rel = np.max(np.abs(mu - r.mu)) / np.max(np.abs(r.mu))
+    assert rel <= REL_MU, rel
+
+
 def test_decision_matches_oracle():
     p = workloads.mixture(700, 16, seed=11, C=1.0)
     s = gabp.GabpSVM(p.X, p.y, p.gamma, p.C)

@@ -467,3 +467,29 @@ def test_tile_sparse_matrix_pins():
     r = oracle.gabp(Q, np.ones(p.n), iters=500, tol=1e-12)
     assert r.kstar < 500
     np.testing.assert_allclose(r.mu, np.linalg.solve(Q, np.ones(p.n)), rtol=1e-9, atol=1e-12)
+
+
+def test_oracle_builds_and_agrees_without_openmp(tmp_path):
+    """The C oracle compiles without OpenMP (one thread) and its all-row
+    diagonal pass gives the same values as the OpenMP build."""
+    import ctypes
+    import subprocess
+    src = os.path.join(os.path.dirname(oracle.__file__), "gabp_oracle.c")
+    so = str(tmp_path / "liboracle_serial.so")
+    subprocess.run(["gcc", "-O2", "-shared", "-fPIC", "-std=c11", "-Wno-unknown-pragmas",
+                    "-fno-fast-math", "-ffp-contract=off", src, "-o", so, "-lm"], check=True)
+    lib = ctypes.CDLL(so)
+    assert lib.orc_threads() == 1
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((57, 5))
+    y = np.where(rng.random(57) < 0.5, 1.0, -1.0)
+    D = ctypes.POINTER(ctypes.c_double)
+    d1, R1 = np.empty(57), np.empty(57)
+    lib.orc_q_diag_all.argtypes = [D, D, ctypes.c_long, ctypes.c_long, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_int, ctypes.c_double, D, D]
+    rc = lib.orc_q_diag_all(X.ctypes.data_as(D), y.ctypes.data_as(D), 57, 5, 0.3, 1.0 / 57, 2.0, 0, 0.1,
+                            d1.ctypes.data_as(D), R1.ctypes.data_as(D))
+    assert rc == 0
+    d2, R2 = oracle.q_diag_all(X, y, 0.3, 2.0)
+    np.testing.assert_allclose(R1, R2, rtol=1e-13)
+    np.testing.assert_allclose(d1, d2, rtol=1e-13)

@@ -1,6 +1,6 @@
 """gabp_decision_noalloc: decision values for callers that cannot allocate
-device memory (graph-capture regions, host frameworks that own all device
-memory, loops that cannot pay for cudaMalloc's synchronisation).
+device memory (plugins in host frameworks that own all device memory, loops
+that cannot pay for cudaMalloc's synchronisation).
 
 Checks, through the C ABI, that two calls in a row give the same values as
 the handle-based gabp_svm_decision within the decision tolerance, and that
