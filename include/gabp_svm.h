@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define GABP_SVM_VERSION 2
+#define GABP_SVM_VERSION 3
 
 #if defined(__GNUC__)
 #define GABP_API __attribute__((visibility("default")))
@@ -137,7 +137,9 @@ typedef struct {
     int64_t n, m;
     int64_t sweeps_total;      /* message updates applied to the state since the last create/refit */
     int32_t kstar;             /* round whose means were returned (counted since create/refit) */
-    int32_t converged;         /* 1 if ||r(kstar)||_inf < tol stopped the last solve */
+    int32_t converged;         /* 1 if the last solve stopped on its tolerance; then residual_inf < tol
+                                  (except an unrefined BF16 / recompute solve, which stops on its BF16
+                                  matrix while residual_inf is that of the FP32-Gram matrix) */
     double  residual_inf;      /* ||1 - Q mu(kstar)||_inf, FP64 sums */
     double  dual_objective;    /* sum_i alpha_i - 1/2 alpha' Q alpha for alpha = clip(mu(kstar), 0, C), FP64 */
     int64_t n_support;         /* #{i : alpha_i > sv_threshold} */
@@ -147,6 +149,12 @@ typedef struct {
     int32_t refine_passes;     /* defect-correction passes done by the last solve */
     int64_t tiles_total;       /* upper-triangle 128 x 128 tiles of Q */
     int64_t tiles_kept;        /* tiles swept (all of them unless sparse_tau > 0) */
+    double  margin;            /* min_i (Q_ii - sum_{j != i} |Q_ij|) of the FP32-Gram matrix, FP64 sums
+                                  (whole-matrix row sums, so also a lower bound for the tile-sparse
+                                  matrix); <= 0 when Q is not strictly diagonally dominant */
+    double  err_bound;         /* Varah's bound on ||mu(kstar) - Q^-1 b||_inf for that matrix:
+                                  residual_inf / margin (+inf when margin <= 0); alpha = clip(mu, 0, C)
+                                  is within the same distance of clip(Q^-1 b, 0, C) */
 } gabp_svm_stats;
 
 /* Default options. */
@@ -185,7 +193,13 @@ GABP_API gabp_status gabp_svm_refit(gabp_svm_t h, const void* X, const float* y,
  * the current messages and the residual r(t) = b - Q mutilde(t) (b = 1 for
  * the SVM, the targets for KRR); it stops at
  * the first t with ||r(t)||_inf < tol (tol <= 0: never), or after `iters`
- * message updates.  Writes alpha = clip(mutilde(kstar), 0, C) (KRR: the
+ * message updates.  The stop test runs inside the rounds on compensated FP32
+ * tile sums; a stop is confirmed by the final residual (FP64 sums of FP32
+ * tile partials, the residual_inf reported), and while that one is still
+ * >= tol the rounds go on (within the `iters` limit), so a converged solve
+ * reports residual_inf < tol.  (An unrefined BF16 or recompute solve stops on
+ * the BF16 matrix it sweeps; its residual_inf is that of the FP32-Gram
+ * matrix.  With refine > 0 the stop is on the FP32-Gram residual.)  Writes alpha = clip(mutilde(kstar), 0, C) (KRR: the
  * unclipped mutilde(kstar)) (n floats) and,
  * when non-NULL, ||r(kstar)||_inf (FP64) and the number of updates done in
  * this call.  Calling again continues from the current messages.
@@ -251,6 +265,9 @@ typedef struct {
     int32_t converged;      /* residual_inf < tol */
     int32_t status;         /* gabp_status of this problem */
     int32_t refine_passes;
+    float*  mu;             /* caller buffer for the n unclipped means (same memory kind as alpha), may be NULL */
+    double  margin;         /* min_i (Q_ii - sum_{j != i} |Q_ij|), as in gabp_svm_stats */
+    double  err_bound;      /* residual_inf / margin: Varah's bound on ||mu - Q^-1 b||_inf (+inf if margin <= 0) */
 } gabp_result;
 
 /*
@@ -307,6 +324,10 @@ typedef struct {
 
 GABP_API gabp_status gabp_server_create(const gabp_server_cfg* cfg, gabp_server_t* out);
 GABP_API gabp_status gabp_server_submit(gabp_server_t s, const gabp_problem* p, float* alpha_out, int64_t* ticket);
+/* As gabp_server_submit; mu_out (may be NULL) also receives the n unclipped
+ * means of the answer (host or device memory like alpha_out). */
+GABP_API gabp_status gabp_server_submit_ex(gabp_server_t s, const gabp_problem* p, float* alpha_out,
+                                           float* mu_out, int64_t* ticket);
 GABP_API gabp_status gabp_server_step(gabp_server_t s, int32_t* active, int32_t* queued, int32_t* completed);
 /* done = 1 once the ticket finished; then *res holds its result. */
 GABP_API gabp_status gabp_server_poll(gabp_server_t s, int64_t ticket, gabp_result* res, int32_t* done);

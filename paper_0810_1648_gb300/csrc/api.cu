@@ -578,6 +578,7 @@ gabp_status gabp_svm_solve(gabp_svm_t h, int32_t iters, double tol, float* alpha
     CK(cudaStreamSynchronize(s));
     if (h->hctrl->status != 0) return fail(GABP_ESTATE, "state is invalid after an earlier failure; refit first");
     const bool refine = h->opts.q_mode != GABP_Q_F32 && h->opts.refine > 0;
+    const bool same_matrix = h->opts.q_mode == GABP_Q_F32;   // the sweeps and the final pass see one Q
     if (refine) {
         // The refined solve always starts from Step 1 (b = 1, messages 0).
         launch_reset(p, s);
@@ -643,9 +644,26 @@ gabp_status gabp_svm_solve(gabp_svm_t h, int32_t iters, double tol, float* alpha
         }
         mu = h->mu_acc;
     } else {
-        StopOp o = op;
-        o.mu = mu;
-        if (gabp_status st = final_pass(o)) return st;
+        // The stop test of the rounds sums the residual in compensated FP32;
+        // the reported residual comes from the final pass (FP32 tile
+        // partials, FP64 sums).  When both are residuals of the same matrix
+        // (Q stored in FP32), a stop counts once the reported residual is
+        // below tol too; until then the rounds go on from where they stopped
+        // (Algorithm 2, Step 3), within the iteration limit.  (An unrefined
+        // BF16 solve stops on its own matrix; its reported residual is that
+        // of the FP32-Gram matrix.)
+        for (;;) {
+            StopOp o = op;
+            o.mu = mu;
+            if (gabp_status st = final_pass(o)) return st;
+            CK(cudaMemcpyAsync(h->hfinal, h->final3, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            const long long left = (long long)t0 + iters - (long long)c.t;
+            if (!same_matrix || !c.converged || h->hfinal[0] < tol || left <= 0) break;
+            if (gabp_status st = run_rounds(h, (int)left, tol, &c)) return st;
+            h->kstar = c.kstar;
+            mu = p.agg + (size_t)(c.kstar & 1) * 3 * p.npad + 2 * (size_t)p.npad;
+        }
     }
     CK(cudaMemcpyAsync(h->hfinal, h->final3, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (alpha)
@@ -660,8 +678,15 @@ gabp_status gabp_svm_solve(gabp_svm_t h, int32_t iters, double tol, float* alpha
     S.m = h->m;
     S.sweeps_total = h->hctrl->t;
     S.kstar = c.kstar;
-    S.converged = refine ? (h->hfinal[0] < tol ? 1 : 0) : c.converged;
+    S.converged = refine ? (h->hfinal[0] < tol ? 1 : 0)
+                         : (c.converged && (!same_matrix || h->hfinal[0] < tol)) ? 1 : 0;
     S.residual_inf = h->hfinal[0];
+    {
+        double inv = 0.0;
+        std::memcpy(&inv, &h->hctrl->inv_margin_bits, sizeof inv);
+        S.margin = inv > 0 ? 1.0 / inv : 0.0;   // 1/inf = 0: some row is not strictly dominant
+        S.err_bound = S.margin > 0 ? S.residual_inf / S.margin : INFINITY;
+    }
     S.dual_objective = h->hfinal[1];
     S.n_support = (int64_t)std::llround(h->hfinal[2]);
     S.refine_passes = refine_done;

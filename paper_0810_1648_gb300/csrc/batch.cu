@@ -99,6 +99,7 @@ struct Member {
     int t_first_stop = 0;
     gabp_result res{};
     float* out_alpha = nullptr;  // caller buffer
+    float* out_mu = nullptr;     // caller buffer for the unclipped means, or null
     int out_dev = 0;
     int64_t ticket = -1;
 };
@@ -575,7 +576,7 @@ class Engine {
     }
 
     // Allocates and forms one instance in `slot` on the side stream.
-    gabp_status add(int slot, const gabp_problem& pr, float* out_alpha, int out_dev)
+    gabp_status add(int slot, const gabp_problem& pr, float* out_alpha, float* out_mu, int out_dev)
     {
         Member& M = mem[(size_t)slot];
         const int64_t n = pr.n, m = pr.m;
@@ -641,10 +642,12 @@ class Engine {
         M.ntiles = tri_tiles(p.Nt);
         M.nblk = (int)((n + 31) / 32);
         M.out_alpha = out_alpha;
+        M.out_mu = out_mu;
         M.out_dev = out_dev;
         M.src_x = pr.X;
         M.res.status = GABP_OK;
         M.res.alpha = out_alpha;
+        M.res.mu = out_mu;
         // (the table entry and the control block are uploaded by form_pending)
         h_tab[slot] = p;
         if (!alias_y()) {
@@ -873,16 +876,26 @@ class Engine {
     {
         Member& M = mem[(size_t)slot];
         const double* f3 = h_f3 + 3 * (size_t)slot;
-        if (M.out_alpha)
-            EK(cudaMemcpyAsync(M.out_alpha, M.alpha, (size_t)M.inst.n * 4,
-                               M.out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ss));
+        const cudaMemcpyKind kind = M.out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (M.out_alpha) EK(cudaMemcpyAsync(M.out_alpha, M.alpha, (size_t)M.inst.n * 4, kind, ss));
+        // the means the final pass used (the refined accumulator or the round k* aggregates)
+        if (M.out_mu && h_ops[(size_t)slot].mu)
+            EK(cudaMemcpyAsync(M.out_mu, h_ops[(size_t)slot].mu, (size_t)M.inst.n * 4, kind, ss));
         M.res.residual_inf = f3[0];
         M.res.dual_objective = f3[1];
         M.res.n_support = (int64_t)std::llround(f3[2]);
         M.res.iters_done = c.t;
-        // the stop test's own decision (Step 3), or the accurate residual after refinement
-        M.res.converged = M.refining ? (f3[0] < M.tol ? 1 : 0) : c.converged;
+        // a stop on the tolerance (Step 3), confirmed by the final FP64-summed residual
+        // (an unrefined BF16 solve stops on its own matrix; residual_inf is the FP32-Gram one)
+        M.res.converged = M.refining ? (f3[0] < M.tol ? 1 : 0)
+                                     : (c.converged && (q_mode != 0 || f3[0] < M.tol)) ? 1 : 0;
         M.res.refine_passes = M.refine_done;
+        {
+            double inv = 0.0;
+            std::memcpy(&inv, &c.inv_margin_bits, sizeof inv);
+            M.res.margin = inv > 0 ? 1.0 / inv : 0.0;
+            M.res.err_bound = M.res.margin > 0 ? f3[0] / M.res.margin : INFINITY;
+        }
         if (c.status == ST_ENUMERIC) M.res.status = GABP_ENUMERIC;
         else if (c.status == ST_EINVAL) M.res.status = GABP_EINVAL;
         else if (c.status == ST_ETIMEOUT) M.res.status = GABP_ETIMEOUT;
@@ -1001,11 +1014,22 @@ class Engine {
                 rejoin.push_back(k);
                 continue;
             }
+            const Ctrl& c = sb.snap[u];
+            if (!sb.ref[u] && q_mode == 0 && c.status == 0 && c.converged && rn >= M.tol && c.t < M.iters) {
+                // the in-round stop test (compensated FP32 sums) passed, the
+                // final FP64-summed residual did not: the same solve goes on
+                // from its current messages (Algorithm 2, Step 3)
+                blist.push_back(make_int2(k, M.iters - c.t));
+                btol.push_back(M.tol);
+                rejoin.push_back(k);
+                continue;
+            }
             if (gabp_status st = finish(k, sb.snap[u], ss)) return st;
             if (finished) finished->push_back(k);
         }
         if (!blist.empty()) {
-            EK(cudaMemcpyAsync(d_stop_nbl, rnb.data(), rnb.size() * sizeof(int2), cudaMemcpyHostToDevice, ss));
+            if (!rnb.empty())
+                EK(cudaMemcpyAsync(d_stop_nbl, rnb.data(), rnb.size() * sizeof(int2), cudaMemcpyHostToDevice, ss));
             EK(cudaMemcpyAsync(d_restart_list, blist.data(), blist.size() * sizeof(int2), cudaMemcpyHostToDevice, ss));
             EK(cudaMemcpyAsync(d_restart_tol, btol.data(), btol.size() * sizeof(double), cudaMemcpyHostToDevice, ss));
             launch_refine_rhs_list(d_tab, d_ops, d_stop_nbl, (int)rnb.size(), ss);
@@ -1193,7 +1217,7 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
     auto t0 = clk::now();
     if (gabp_status st = E.reserve(bytes)) return st;
     for (int64_t k = 0; k < count; ++k) {
-        if (gabp_status st = E.add((int)k, probs[k], results[k].alpha, o.ptr_mode)) return st;
+        if (gabp_status st = E.add((int)k, probs[k], results[k].alpha, results[k].mu, o.ptr_mode)) return st;
         E.mem[(size_t)k].iters = iters;
         E.mem[(size_t)k].tol = tol;
         E.mem[(size_t)k].refine_left = o.q_mode != 0 ? o.refine : 0;
@@ -1256,6 +1280,7 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
     for (int64_t k = 0; k < count; ++k) {
         gabp_result r = E.mem[(size_t)k].res;
         r.alpha = results[k].alpha;
+        r.mu = results[k].mu;
         results[k] = r;
         if (r.status != GABP_OK && worst == GABP_OK) worst = (gabp_status)r.status;
     }
@@ -1293,7 +1318,7 @@ struct gabp_server_s {
     gabp_server_cfg cfg{};
     size_t budget = 0;
     std::deque<std::pair<int64_t, gabp_problem>> queue;
-    std::map<int64_t, float*> outs;
+    std::map<int64_t, std::pair<float*, float*>> outs;   // {alpha, mu} caller buffers
     std::map<int64_t, gabp_result> done;
     std::deque<int64_t> fresh;   // finished, not yet reported by gabp_server_completed
     std::vector<int> forming;   // slots whose Q formation runs on the side stream
@@ -1339,6 +1364,12 @@ gabp_status gabp_server_create(const gabp_server_cfg* cfg, gabp_server_t* out)
 
 gabp_status gabp_server_submit(gabp_server_t s, const gabp_problem* p, float* alpha_out, int64_t* ticket)
 {
+    return gabp_server_submit_ex(s, p, alpha_out, nullptr, ticket);
+}
+
+gabp_status gabp_server_submit_ex(gabp_server_t s, const gabp_problem* p, float* alpha_out, float* mu_out,
+                                  int64_t* ticket)
+{
     gabp::set_last_error("");
     if (!s || !p || !ticket) { gabp::set_last_error("gabp_server_submit: null argument"); return GABP_EINVAL; }
     if (p->n < 2 || p->m < 1 || !p->X || !p->y || !(p->gamma > 0) || !(p->C > 0)) {
@@ -1347,7 +1378,7 @@ gabp_status gabp_server_submit(gabp_server_t s, const gabp_problem* p, float* al
     }
     const int64_t t = s->next_ticket++;
     s->queue.emplace_back(t, *p);
-    s->outs[t] = alpha_out;
+    s->outs[t] = std::make_pair(alpha_out, mu_out);
     *ticket = t;
     return GABP_OK;
 }
@@ -1384,6 +1415,7 @@ gabp_status gabp_server_step(gabp_server_t s, int32_t* active, int32_t* queued, 
                 Member& M = E.mem[(size_t)slot];
                 gabp_result r = M.res;
                 r.alpha = M.out_alpha;
+                r.mu = M.out_mu;
                 s->done[M.ticket] = r;
                 s->fresh.push_back(M.ticket);
                 E.release(M);
@@ -1401,7 +1433,8 @@ gabp_status gabp_server_step(gabp_server_t s, int32_t* active, int32_t* queued, 
         if (need > s->budget) {
             gabp_result r{};
             r.status = GABP_ENOMEM;
-            r.alpha = s->outs[front.first];
+            r.alpha = s->outs[front.first].first;
+            r.mu = s->outs[front.first].second;
             s->done[front.first] = r;
             s->fresh.push_back(front.first);
             s->queue.pop_front();
@@ -1410,7 +1443,8 @@ gabp_status gabp_server_step(gabp_server_t s, int32_t* active, int32_t* queued, 
         const int slot = E.free_slot();
         if (slot < 0 || E.bytes_in_use + need > s->budget) break;
         const int64_t t = front.first;
-        if (gabp_status st = E.add(slot, front.second, s->outs[t], s->cfg.opts.ptr_mode)) return st;
+        if (gabp_status st = E.add(slot, front.second, s->outs[t].first, s->outs[t].second, s->cfg.opts.ptr_mode))
+            return st;
         Member& M = E.mem[(size_t)slot];
         M.ticket = t;
         M.iters = s->cfg.iters;

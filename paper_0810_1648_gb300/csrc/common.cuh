@@ -57,6 +57,10 @@ struct Ctrl {
     long long bad_index;      // offending node (or pair row) of the first error
     unsigned int blocks_done; // last-block-done counter of the finalize kernel
     unsigned long long rmax_bits;  // running max |r_i| of the round (bits of a nonnegative double)
+    unsigned long long inv_margin_bits;  // max_i 1 / (Q_ii - R_i), R_i = sum_{j != i} |Q_ij| (bits of a
+                                         // nonnegative double; +inf where a row is not strictly dominant),
+                                         // set at formation: Varah's bound ||mu - Q^-1 b||_inf <=
+                                         // ||b - Q mu||_inf * it
     double tol;
     double rinf;              // ||r(kstar)||_inf as seen by the convergence test
 };

@@ -1267,6 +1267,18 @@ __global__ void k_selftest_rcp(const float* __restrict__ d, float* __restrict__ 
     if (i < cnt) out[i] = rcp_nr(d[i]);
 }
 
+// Row x's diagonal margin Q_xx - R_x into the instance's running
+// max_i 1 / (Q_ii - R_i) (the control block is zeroed before formation):
+// with all margins positive Q is strictly diagonally dominant and Varah's
+// bound ||mu - Q^-1 b||_inf <= ||b - Q mu||_inf / min_i (Q_ii - R_i) holds for
+// any mu; a row without a positive margin records +inf (no bound).
+__device__ __forceinline__ void note_margin(Ctrl* c, float qd, double R)
+{
+    const double mg = (double)qd - R;
+    const double inv = mg > 0.0 ? 1.0 / mg : INFINITY;
+    atomicMax(&c->inv_margin_bits, (unsigned long long)__double_as_longlong(inv));
+}
+
 // Diagonal rule (Section 3.1) from the |Q| row-sum partials of the Q
 // formation, then Algorithm 2 Step 1: messages 0, so Ptilde = Q_ii,
 // htilde = b_i, mutilde = b_i / Q_ii.  CTA 0 resets the control block.
@@ -1301,6 +1313,7 @@ __global__ void k_init(Inst p, int diag_rule, float delta)
     p.agg[x] = qf;
     p.agg[p.npad + x] = bx;
     p.agg[2 * p.npad + x] = bx / qf;
+    note_margin(p.ctrl, qf, R);
 }
 
 // k_init over listed node blocks (block 0 of an instance resets its control block).
@@ -1337,6 +1350,7 @@ __global__ void k_init_list(const Inst* __restrict__ tab, const int2* __restrict
     p.agg[x] = qf;
     p.agg[p.npad + x] = bx;
     p.agg[2 * p.npad + x] = bx / qf;
+    note_margin(p.ctrl, qf, R);
 }
 
 __global__ void k_begin_list(Inst* tab, const int2* __restrict__ list, const double* __restrict__ tols, int count)

@@ -65,7 +65,8 @@ class Stats(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("C", ctypes.c_double), ("diag_delta", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("q_mode", ctypes.c_int32),
                 ("diag_rule", ctypes.c_int32), ("refine_passes", ctypes.c_int32),
-                ("tiles_total", ctypes.c_int64), ("tiles_kept", ctypes.c_int64)]
+                ("tiles_total", ctypes.c_int64), ("tiles_kept", ctypes.c_int64),
+                ("margin", ctypes.c_double), ("err_bound", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -80,10 +81,11 @@ class Result(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_void_p), ("residual_inf", ctypes.c_double),
                 ("dual_objective", ctypes.c_double), ("n_support", ctypes.c_int64),
                 ("iters_done", ctypes.c_int32), ("converged", ctypes.c_int32),
-                ("status", ctypes.c_int32), ("refine_passes", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("refine_passes", ctypes.c_int32),
+                ("mu", ctypes.c_void_p), ("margin", ctypes.c_double), ("err_bound", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "alpha"}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k not in ("alpha", "mu")}
 
 
 class ServerCfg(ctypes.Structure):
@@ -135,6 +137,7 @@ def load():
         "gabp_batch_release": (st, []),
         "gabp_server_create": (st, [P(ServerCfg), P(V)]),
         "gabp_server_submit": (st, [V, P(Problem), V, P(I64)]),
+        "gabp_server_submit_ex": (st, [V, P(Problem), V, V, P(I64)]),
         "gabp_server_step": (st, [V, P(I32), P(I32), P(I32)]),
         "gabp_server_poll": (st, [V, I64, P(Result), P(I32)]),
         "gabp_server_completed": (st, [V, V, I32, P(I32)]),
@@ -347,13 +350,15 @@ def selftest_bounded_wait(limit_ns: int) -> int:
     return rc
 
 
-def batch_solve(problems, iters: int, tol: float, **opts):
+def batch_solve(problems, iters: int, tol: float, means: bool = False, **opts):
     """gabp_batch_solve over a list of workloads.Problem-like objects: numpy X
     (float32/float64) and y, or float32 torch CUDA tensors for all of them
     (device pointer mode; alphas then come back as CUDA tensors).  Returns
-    (list of alpha arrays, list of result dicts, overall status)."""
+    (list of alpha arrays, list of result dicts, overall status); with
+    means=True each result dict also carries the unclipped means under "mu"
+    (same array kind as alpha)."""
     probs = (Problem * len(problems))()
-    keep, alphas = [], []
+    keep, alphas, mus = [], [], []
     f64 = None
     dev = len(problems) > 0 and _is_cuda(problems[0].X)
     if dev:
@@ -367,6 +372,8 @@ def batch_solve(problems, iters: int, tol: float, **opts):
             keep += [X, y]
             probs[k] = Problem(X.data_ptr(), y.data_ptr(), X.shape[0], X.shape[1], float(p.gamma), float(p.C))
             alphas.append(torch.empty(X.shape[0], dtype=torch.float32, device=X.device))
+            if means:
+                mus.append(torch.empty(X.shape[0], dtype=torch.float32, device=X.device))
             continue
         X = np.ascontiguousarray(p.X)
         if f64 is None:
@@ -376,11 +383,15 @@ def batch_solve(problems, iters: int, tol: float, **opts):
         keep += [X, y]
         probs[k] = Problem(X.ctypes.data, y.ctypes.data, X.shape[0], X.shape[1], float(p.gamma), float(p.C))
         alphas.append(np.empty(X.shape[0], dtype=np.float32))
+        if means:
+            mus.append(np.empty(X.shape[0], dtype=np.float32))
     if dev:
         _sync_torch(*keep)
     res = (Result * len(problems))()
     for k in range(len(problems)):
         res[k].alpha = alphas[k].data_ptr() if dev else alphas[k].ctypes.data
+        if means:
+            res[k].mu = mus[k].data_ptr() if dev else mus[k].ctypes.data
     o = opts_default(**opts)
     o.x_dtype = 1 if f64 else 0
     if dev:
@@ -388,7 +399,11 @@ def batch_solve(problems, iters: int, tol: float, **opts):
     rc = load().gabp_batch_solve(probs, len(problems), ctypes.byref(o), int(iters), float(tol), res)
     if rc not in (OK, ENUMERIC):
         _check(rc)
-    return alphas, [res[k].as_dict() for k in range(len(problems))], rc
+    out = [res[k].as_dict() for k in range(len(problems))]
+    if means:
+        for d, mu in zip(out, mus):
+            d["mu"] = mu
+    return alphas, out, rc
 
 
 def batch_release():
@@ -416,15 +431,19 @@ class Server:
         _check(load().gabp_server_create(ctypes.byref(cfg), ctypes.byref(self.h)))
         self._keep = {}
 
-    def submit(self, X, y, gamma, C):
+    def submit(self, X, y, gamma, C, means: bool = False):
+        """Queues one problem; with means=True its poll() result dict also
+        carries the unclipped means under "mu" (gabp_server_submit_ex)."""
         X = np.ascontiguousarray(X, dtype=np.float32)
         y = np.ascontiguousarray(y, dtype=np.float32)
         alpha = np.empty(X.shape[0], dtype=np.float32)
+        mu = np.empty(X.shape[0], dtype=np.float32) if means else None
         pr = Problem(X.ctypes.data, y.ctypes.data, X.shape[0], X.shape[1], float(gamma), float(C))
         t = ctypes.c_int64()
-        _check(load().gabp_server_submit(self.h, ctypes.byref(pr), ctypes.c_void_p(alpha.ctypes.data),
-                                         ctypes.byref(t)))
-        self._keep[t.value] = (X, y, alpha)
+        _check(load().gabp_server_submit_ex(self.h, ctypes.byref(pr), ctypes.c_void_p(alpha.ctypes.data),
+                                            ctypes.c_void_p(mu.ctypes.data) if means else None,
+                                            ctypes.byref(t)))
+        self._keep[t.value] = (X, y, alpha, mu)
         return t.value
 
     def step(self):
@@ -456,8 +475,11 @@ class Server:
         _check(load().gabp_server_poll(self.h, int(ticket), ctypes.byref(r), ctypes.byref(d)))
         if not d.value:
             return None
-        X, y, alpha = self._keep.pop(ticket)
-        return alpha, r.as_dict()
+        X, y, alpha, mu = self._keep.pop(ticket)
+        d = r.as_dict()
+        if mu is not None:
+            d["mu"] = mu
+        return alpha, d
 
     def close(self):
         if self.h:

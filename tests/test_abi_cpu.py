@@ -21,7 +21,7 @@ def test_exports_every_declared_symbol(lib):
     assert len(names) >= 15
     for nm in names:
         assert hasattr(lib, nm), nm
-    assert lib.gabp_version() == 2
+    assert lib.gabp_version() == 3
 
 
 def test_opts_default(lib):

@@ -10,19 +10,23 @@ samples:
 * Under the dominant diagonal rule Q is strictly diagonally dominant with
   Q_ii >= max(1 + lambda^2 + 1/C, (1 + delta) R_i), R_i = sum_{j != i} |Q_ij|,
   and (Varah, 1975) ||mu - mu*||_inf <= ||b - Q mu||_inf / min_i (Q_ii - R_i).
-  The margin min_i (Q_ii - R_i) is the oracle's, from all rows (n = 100000),
-  or its floor delta / (1 + delta) * (1 + lambda^2 + 1/C) (batched and
-  serving instances).
+  The margin min_i (Q_ii - R_i) is the oracle's, from all rows of each
+  matrix (its all-row pass for n = 100000 and the served requests, the dense
+  matrix for the batched instances).
 * ||b - Q mu||_inf is the solver's FP64-accumulated residual against its FP32
   matrix (at most 1e-6 at the stop) plus the FP32-vs-FP64 entry error, at most
   R_ERR = 4e-6 here (entries carry about 1e-6 relative error and
   sum_j |Q_ij mu_j| stays near 2); the oracle's exact FP64 rows confirm the
   residual on sampled rows.
 * Support vectors: every node whose |mu_i| exceeds the bound has the sign of
-  mu*_i, so the sets {alpha_i > 0} agree outside that band (its size is
-  reported, not asserted).
-Small instances of the same runs are also compared with a dense FP64 solve
-of the oracle's matrix.
+  mu*_i, so the sets {alpha_i > 0} agree outside that band; the band is
+  asserted empty, so the support-vector sets are identical.
+* The solver's own stated error (gabp_result / gabp_svm_stats err_bound =
+  residual / margin with its FP32 row sums) is checked against the oracle's
+  margin and, where the exact solution is at hand, against the true error.
+Every batched instance (n <= 4000) is also compared with a dense FP64 solve
+of the oracle's matrix (alpha to 1e-4 C and identical support-vector sets on
+all nodes), and so are the small served requests.
 """
 import numpy as np
 import pytest
@@ -70,24 +74,29 @@ def _assert_exact(p, alpha, mu):
     Q, ref = _exact(p)
     a_ref = np.clip(ref, 0, p.C)
     assert np.max(np.abs(alpha.astype(np.float64) - a_ref)) <= 1e-4 * p.C
-    clear = np.abs(ref) > 1e-5 * np.max(np.abs(ref))
-    assert np.array_equal((alpha > 0)[clear], (a_ref > 0)[clear])
+    assert np.array_equal(alpha > 0, a_ref > 0)
     if mu is not None:
         assert np.max(np.abs(1.0 - Q @ mu.astype(np.float64))) < 1e-6 + R_ERR
 
 
-@pytest.mark.parametrize("mode", ["f32", "bf16_refined", "bf16_refined_staged4"])
+PRECISION_MODES = {
+    "f32": dict(q_mode=0),
+    "bf16_refined": dict(q_mode=gabp.Q_BF16, msg_bf16=1, refine=10),
+    "bf16_refined_staged4": dict(q_mode=gabp.Q_BF16, msg_bf16=1, refine=10, stages=4),
+    "recompute_refined": dict(q_mode=gabp.Q_RECOMPUTE, msg_bf16=1, refine=10),
+}
+
+
+@pytest.mark.parametrize("mode", list(PRECISION_MODES))
 def test_precision_workload_full_size(mode, precision_problem):
     """n = 100000, m = 64, gamma = 0.5/64, C = 1 to ||r||_inf < 1e-6: plain
-    FP32, and BF16 Q + BF16 messages with refinement (synchronous and
-    4-stage), as the bench's time-to-tolerance runs do."""
+    FP32, BF16 Q + BF16 messages with refinement (synchronous and 4-stage),
+    and Q recomputed in every sweep (BF16 messages, refinement), as the
+    bench's precision runs do."""
     torch = pytest.importorskip("torch")
     p, margin = precision_problem
     Xd, yd = torch.from_numpy(p.X).cuda(), torch.from_numpy(p.y).cuda()
-    kw = dict(q_mode=0) if mode == "f32" else dict(q_mode=gabp.Q_BF16, msg_bf16=1, refine=10)
-    if mode.endswith("staged4"):
-        kw["stages"] = 4
-    h = gabp.svm_create(Xd, yd, p.gamma, p.C, gabp.opts_default(chunk=8, **kw))
+    h = gabp.svm_create(Xd, yd, p.gamma, p.C, gabp.opts_default(chunk=8, **PRECISION_MODES[mode]))
     alpha = torch.empty(p.n, dtype=torch.float32, device="cuda")
     rinf, k = gabp.svm_solve(h, 400, 1e-6, alpha)
     st = gabp.svm_get_stats(h)
@@ -97,6 +106,9 @@ def test_precision_workload_full_size(mode, precision_problem):
     gabp.svm_destroy(h)
     mu, alpha = mu.cpu().numpy().astype(np.float64), alpha.cpu().numpy()
     assert st["converged"] == 1 and rinf < 1e-6, (rinf, st)
+    # the solver's margin (FP32 row sums) against the oracle's, and its stated error
+    assert st["margin"] == pytest.approx(margin, rel=1e-5)
+    assert st["err_bound"] == pytest.approx(rinf / st["margin"], rel=1e-12)
     # alpha = clip(mu, 0, C) is 1-Lipschitz in mu, so the bound holds for alpha
     b = _bound(rinf, p.n, p.C, margin)
     assert b <= 1e-4 * p.C
@@ -104,7 +116,6 @@ def test_precision_workload_full_size(mode, precision_problem):
     # |mu| is about 1 / R_i)
     assert b <= 1e-3 * np.max(np.abs(mu)), (b, np.max(np.abs(mu)))
     np.testing.assert_array_equal(alpha, np.clip(mu, 0, p.C).astype(np.float32))
-    band = int((np.abs(mu) <= b).sum())   # nodes whose SV membership the bound leaves open
     # the oracle's exact FP64 rows: the residual on sampled rows (and on the
     # rows of the largest means) is within the allowance
     rng = np.random.default_rng(3)
@@ -113,7 +124,9 @@ def test_precision_workload_full_size(mode, precision_problem):
     for i in rows:
         qi = oracle.q_row(X, y, int(i), p.gamma, p.C)
         assert abs(1.0 - qi @ mu) <= rinf + R_ERR, (int(i), 1.0 - qi @ mu)
-    assert band <= p.n // 1000, band
+    # no node within the bound of 0: the support-vector set is that of mu*
+    band = int((np.abs(mu) <= b).sum())
+    assert band == 0, band
 
 
 def _batch_device(probs, torch):
@@ -124,30 +137,51 @@ def _batch_device(probs, torch):
     return [workloads.Problem(*dev[id(p.X)], p.gamma, p.C) for p in probs]
 
 
+@pytest.fixture(scope="module")
+def batch_exact():
+    """The 512 batched instances and, for each, the oracle's matrix margin
+    min_i (Q_ii - R_i) and the exact fixed point mu* = Q^-1 1 (dense FP64
+    solve, n <= 4000)."""
+    probs = workloads.batch_grid()
+    out = []
+    for p in probs:
+        Q = oracle.build_q(p.X.astype(np.float64), np.asarray(p.y, dtype=np.float64), p.gamma, p.C)
+        d = np.diag(Q).copy()
+        margin = float(np.min(2 * d - np.abs(Q).sum(axis=1)))
+        out.append((margin, np.linalg.solve(Q, np.ones(p.n))))
+        del Q
+    return probs, out
+
+
 @pytest.mark.parametrize("kw", [dict(q_mode=0), dict(q_mode=1, refine=8, msg_bf16=1),
                                 dict(q_mode=1, refine=8, msg_bf16=1, stages=4)])
-def test_batch_grid_full_size(kw):
+def test_batch_grid_full_size(kw, batch_exact):
     """All 512 instances of the batched workload (32 data sets x the C x
     gamma grid, n in [200, 4000]) to ||r||_inf < 1e-6 in one batch with the
-    autotuned schedule; every result within the bound, and the grids of the
-    smallest data sets against dense FP64 solves."""
+    autotuned schedule.  Every instance against its dense FP64 solve: alpha
+    within 1e-4 C, identical support-vector sets on every node, no node in
+    the Varah band, and the solver's stated error bound above the true
+    error (up to the FP32-entry allowance)."""
     torch = pytest.importorskip("torch")
-    probs = workloads.batch_grid()
+    probs, exact = batch_exact
     dprobs = _batch_device(probs, torch)
-    alphas, res, rc = gabp.batch_solve(dprobs, 200, 1e-6, chunk=0, **kw)
+    alphas, res, rc = gabp.batch_solve(dprobs, 200, 1e-6, chunk=0, means=True, **kw)
     assert rc == gabp.OK
-    for p, r in zip(probs, res):
-        # the stop test decides on the in-sweep residual (compensated FP32
-        # sums); the reported one is recomputed afterwards in FP64 from the
-        # stored matrix and may differ in its last digits
-        assert r["status"] == 0 and r["converged"] == 1 and r["residual_inf"] < 1.1e-6, r
-        assert _bound(r["residual_inf"], p.n, p.C) <= 1e-4 * p.C
-    # exact comparison on the three smallest data sets (all 16 grid points each)
-    sizes = sorted({(p.n, id(p.X)) for p in probs})[:3]
-    pick = {x for _, x in sizes}
-    for p, a in zip(probs, alphas):
-        if id(p.X) in pick:
-            _assert_exact(p, a.cpu().numpy(), None)
+    bands = []
+    for idx, (p, r, a, (margin, ref)) in enumerate(zip(probs, res, alphas, exact)):
+        assert r["status"] == 0 and r["converged"] == 1 and r["residual_inf"] < 1e-6, (idx, r)
+        assert margin > 0 and r["margin"] == pytest.approx(margin, rel=1e-5), (idx, r["margin"], margin)
+        a = a.cpu().numpy().astype(np.float64)
+        mu = r["mu"].cpu().numpy().astype(np.float64)
+        np.testing.assert_array_equal(a, np.clip(mu, 0, p.C).astype(np.float32).astype(np.float64))
+        a_ref = np.clip(ref, 0, p.C)
+        assert np.max(np.abs(a - a_ref)) <= 1e-4 * p.C, idx
+        assert np.array_equal(a > 0, a_ref > 0), (idx, int(np.sum((a > 0) != (a_ref > 0))))
+        err = float(np.max(np.abs(mu - ref)))
+        assert err <= r["err_bound"] + R_ERR / margin, (idx, err, r["err_bound"])
+        b = _bound(r["residual_inf"], p.n, p.C, margin)
+        bands.append(int((np.abs(mu) <= b).sum()))
+    assert sum(bands) == 0, [(i, c) for i, c in enumerate(bands) if c]
 
 
 def _serve_stream(count):
@@ -172,12 +206,15 @@ def _serve_stream(count):
 def test_serving_stream_results():
     """120 requests of the serving stream through the server as the bench
     configures it (BF16 Q + BF16 messages + refinement, 4 stages, chunk 4, up
-    to 64 members): every result within the bound, small requests against
-    dense FP64 solves, and sampled requests equal when served alone."""
+    to 64 members): every result within the Varah bound with the oracle's
+    margin of its matrix (all rows), no node in the band (identical
+    support-vector sets), the solver's margin equal to the oracle's, small
+    requests against dense FP64 solves, and sampled requests equal when
+    served alone."""
     probs = _serve_stream(120)
     cfg = dict(iters=200, tol=1e-6, max_members=64, q_mode=gabp.Q_BF16, refine=8, msg_bf16=1, chunk=4, stages=4)
     srv = gabp.Server(**cfg)
-    tickets = [srv.submit(p.X, p.y, p.gamma, p.C) for p in probs]
+    tickets = [srv.submit(p.X, p.y, p.gamma, p.C, means=True) for p in probs]
     out = {}
     for _ in range(200000):
         srv.step()
@@ -187,15 +224,23 @@ def test_serving_stream_results():
             break
     srv.close()
     assert len(out) == len(probs)
-    small = []
-    for p, t in zip(probs, tickets):
+    small, bands = [], []
+    for idx, (p, t) in enumerate(zip(probs, tickets)):
         a, r = out[t]
-        assert r["status"] == 0 and r["converged"] == 1 and r["residual_inf"] < 1.1e-6, r
-        assert _bound(r["residual_inf"], p.n, p.C) <= 1e-4 * p.C
+        assert r["status"] == 0 and r["converged"] == 1 and r["residual_inf"] < 1e-6, (idx, r)
+        d, R = oracle.q_diag_all(p.X.astype(np.float64), np.asarray(p.y, dtype=np.float64), p.gamma, p.C)
+        margin = float(np.min(d - R))
+        assert margin > 0 and r["margin"] == pytest.approx(margin, rel=1e-5), (idx, r["margin"], margin)
+        b = _bound(r["residual_inf"], p.n, p.C, margin)
+        assert b <= 1e-4 * p.C, (idx, b)
+        mu = r["mu"].astype(np.float64)
+        np.testing.assert_array_equal(a, np.clip(mu, 0, p.C).astype(np.float32))
+        bands.append(int((np.abs(mu) <= b).sum()))
         if p.n <= 2000:
             small.append((p, a))
+    assert sum(bands) == 0, [(i, c) for i, c in enumerate(bands) if c]
     assert len(small) >= 4
-    for p, a in small[:6]:
+    for p, a in small:
         _assert_exact(p, a, None)
     # the same request alone gives the same result as in the mix
     for p, t in list(zip(probs, tickets))[:3]:

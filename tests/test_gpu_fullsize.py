@@ -58,7 +58,8 @@ def test_full_size_solve_matches_oracle(big):
     assert rel <= 2e-5, rel
     assert np.max(np.abs(a - r.alpha(p.C))) <= 1e-4 * p.C
     clear = np.abs(r.mu) > 1e-5 * np.max(np.abs(r.mu))
-    assert np.array_equal((a > 0)[clear], (r.alpha(p.C) > 0)[clear])
+    assert clear.all()   # no oracle mean near the threshold: the sets are compared on every node
+    assert np.array_equal(a > 0, r.alpha(p.C) > 0)
     assert rinf == pytest.approx(np.max(np.abs(1.0 - Q @ mu.astype(np.float64))), rel=1e-2, abs=1e-6)
 
 
