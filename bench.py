@@ -385,12 +385,15 @@ def run_batch(args):
 
 
 def run_sparse(args):
-    """Tile-sparse kernel against the dense solve on the same clustered data:
+    """Tile-sparse kernel on clustered data.  Default (--sparse-n 20000):
     n=20000, m=64 mixture with rows grouped by component, gamma=0.15, C=1,
-    tau=1e-3.  Sweeps/s of 100 synchronous rounds (inputs resident on the
-    device, CUDA events), the HBM fraction of the sparse sweep for the pairs of
-    its kept tiles, the time to ||r||_inf < 1e-6, and the difference of the two
-    answers."""
+    tau=1e-3, against the dense solve of the same data.  --sparse-n 200000:
+    six tight clusters (sigma 0.5), gamma=0.3, tau=5e-5, a size whose dense
+    message state (8 n^2 bytes) exceeds the device, so no dense solve beside
+    it.  Reports sweeps/s of 100 synchronous rounds (inputs resident on the
+    device, CUDA events), the HBM fraction of the sparse sweep for the pairs
+    of its kept tiles, the device memory held, the time to ||r||_inf < 1e-6
+    and the stated error bound."""
     import torch
 
     from paper_0810_1648_gb300 import build as gbuild
@@ -398,13 +401,26 @@ def run_sparse(args):
     if not os.path.exists(gabp.LIB_PATH):
         gbuild.build()
     gabp.load()
-    tau = 1e-3
-    p = workloads.clustered_mixture(20000, 64, seed=5, gamma=0.15, C=1.0)
+    big = args.sparse_n > 20000
+    if big:
+        tau = 5e-5
+        p = workloads.clustered_mixture(args.sparse_n, 64, seed=5, gamma=0.3, C=1.0, sigma=0.5)
+        names = (("tile_sparse", tau),)
+        desc = (f"tile-sparse kernel: n={p.n}, m=64 mixture (3 components per class, sigma 0.5, seed 5) with "
+                f"rows grouped by component, RBF gamma=0.3, C=1, tiles with max |Q_ij| <= {tau} dropped; "
+                "100 synchronous sweeps per step; the dense message state (8 n^2 bytes) exceeds the device")
+    else:
+        tau = 1e-3
+        p = workloads.clustered_mixture(args.sparse_n, 64, seed=5, gamma=0.15, C=1.0)
+        names = (("dense", 0.0), ("tile_sparse", tau))
+        desc = (f"tile-sparse kernel: n={p.n}, m=64 mixture (3 components per class, sigma 0.7, seed 5) with "
+                f"rows grouped by component, RBF gamma=0.15, C=1, tiles with max |Q_ij| <= {tau} dropped; "
+                "100 synchronous sweeps per step; dense solve of the same data beside it")
     Xd, yd = torch.from_numpy(p.X).cuda(), torch.from_numpy(p.y).cuda()
     stream = torch.cuda.Stream()
     alpha = torch.empty(p.n, dtype=torch.float32, device="cuda")
     out, answers = {}, {}
-    for name, st in (("dense", 0.0), ("tile_sparse", tau)):
+    for name, st in names:
         opts = gabp.opts_default(stream=stream.cuda_stream, chunk=ROUNDS, sparse_tau=st)
         h = gabp.svm_create(Xd, yd, p.gamma, p.C, opts)
         gabp.svm_set_profiling(h, PROFILE_STRIDE)
@@ -428,6 +444,8 @@ def run_sparse(args):
         pairs = (kept - nt) * T_TILE * T_TILE + nt * T_TILE * (T_TILE - 1) // 2   # full-tile count, diagonal halves
         bytes_frozen = 28 * pairs
         sweep_ms = prof["sweep_ms"] / max(prof["sweep_launches"], 1)
+        dev_bytes = int(stt["device_bytes"])
+        gabp.svm_destroy(h)
         # to tolerance
         opts2 = gabp.opts_default(stream=stream.cuda_stream, chunk=8, sparse_tau=st)
         h2 = gabp.svm_create(Xd, yd, p.gamma, p.C, opts2)
@@ -438,45 +456,43 @@ def run_sparse(args):
             rinf, k = gabp.svm_solve(h2, 400, 1e-6, alpha)
             e1.record(stream)
             torch.cuda.synchronize()
+        st2 = gabp.svm_get_stats(h2)
         answers[name] = alpha.cpu().numpy().copy()
         out[name] = {"sweeps_per_s": args.steps * ROUNDS / (ms / 1e3), "tiles_kept": kept, "tiles_total": total,
+                     "device_bytes": dev_bytes, "dense_message_state_bytes": 8 * p.n * p.n,
                      "avg_sweep_ms": sweep_ms, "hbm_frac_frozen_bytes": bytes_frozen / (sweep_ms / 1e3) / 1e9 / _peak_gbs(),
-                     "to_tolerance": {"ms": float(e0.elapsed_time(e1)), "rounds": int(k), "residual_inf": float(rinf)}}
-        gabp.svm_destroy(h)
+                     "to_tolerance": {"ms": float(e0.elapsed_time(e1)), "rounds": int(k), "residual_inf": float(rinf),
+                                      "converged": int(st2["converged"]), "err_bound_over_C": st2["err_bound"] / p.C,
+                                      "margin": st2["margin"]}}
         gabp.svm_destroy(h2)
-    diff = float(np.max(np.abs(answers["dense"] - answers["tile_sparse"]))) / p.C
     line = {"metric": METRIC, "value": out["tile_sparse"]["sweeps_per_s"], "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "tile-sparse kernel: n=20000, m=64 mixture (3 components per class, sigma 0.7, "
-                                   "seed 5) with rows grouped by component, RBF gamma=0.15, C=1, tiles with "
-                                   f"max |Q_ij| <= {tau} dropped; 100 synchronous sweeps per step; dense solve of the "
-                                   "same data beside it", "n": p.n, "m": 64, "sparse_tau": tau},
-            "modes": out, "speedup_sweeps": out["tile_sparse"]["sweeps_per_s"] / out["dense"]["sweeps_per_s"],
-            "speedup_to_tolerance": out["dense"]["to_tolerance"]["ms"] / out["tile_sparse"]["to_tolerance"]["ms"],
-            "max_alpha_difference_over_C": diff}
+            "config": {"workload": desc, "n": p.n, "m": 64, "sparse_tau": tau},
+            "modes": out}
+    if not big:
+        line["speedup_sweeps"] = out["tile_sparse"]["sweeps_per_s"] / out["dense"]["sweeps_per_s"]
+        line["speedup_to_tolerance"] = out["dense"]["to_tolerance"]["ms"] / out["tile_sparse"]["to_tolerance"]["ms"]
+        line["max_alpha_difference_over_C"] = float(np.max(np.abs(answers["dense"] - answers["tile_sparse"]))) / p.C
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_serve(args):
-    """Poisson stream of SVM-training requests replayed in real time through
-    the continuous-batching server; reports p50/p99 latency and solves/s."""
-    from paper_0810_1648_gb300 import build as gbuild
-    from paper_0810_1648_gb300 import gabp
-    if not os.path.exists(gabp.LIB_PATH):
-        gbuild.build()
-    reqs = workloads.poisson_requests(rate=args.rate, duration=args.duration, seed=7)
+def _serve_run(gabp, rate, duration, q_mode, msg_bf16, stages, max_members):
+    """Replays the seeded Poisson stream (rate/s for `duration` s) in real time
+    through the continuous-batching server; returns latency percentiles,
+    solves/s over the wall time, and the largest stated error bound."""
+    reqs = workloads.poisson_requests(rate=rate, duration=duration, seed=7)
     # request data: row/column slices of one seeded mixture pool (labels from it)
     pool = workloads.mixture(50000, 512, seed=7)
     rng = np.random.default_rng(8)
     starts = [int(rng.integers(0, 50000 - r.n + 1)) for r in reqs]
-    srv = gabp.Server(iters=200, tol=1e-6, max_members=args.max_members, q_mode=Q_MODES[args.q_mode],
-                      refine=8 if args.q_mode != "f32" else 0, msg_bf16=1 if args.msg_bf16 else 0, chunk=4,
-                      stages=args.stages)
+    srv = gabp.Server(iters=200, tol=1e-6, max_members=max_members, q_mode=Q_MODES[q_mode],
+                      refine=8 if q_mode != "f32" else 0, msg_bf16=1 if msg_bf16 else 0, chunk=4,
+                      stages=stages)
     t0 = time.perf_counter()
     sub, lat, nxt = {}, [], 0
-    rounds, passes, conv = [], [], 0
+    rounds, passes, conv, errb, resid = [], [], 0, [], []
     done_n = 0
     while done_n < len(reqs):
         now = time.perf_counter() - t0
@@ -487,16 +503,19 @@ def run_serve(args):
             if abs(float(y.sum())) == r.n:          # need both classes
                 y = y.copy(); y[0] = -y[0]
             t = srv.submit(X, y, 1.0 / r.m, r.C)
-            sub[t] = r.t_arrive
+            sub[t] = (r.t_arrive, r.C)
             nxt += 1
         active, queued, completed = srv.step()
         for t in srv.completed():
             res = srv.poll(t)
             if res is not None:
-                lat.append(time.perf_counter() - t0 - sub.pop(t))
+                t_arr, C = sub.pop(t)
+                lat.append(time.perf_counter() - t0 - t_arr)
                 rounds.append(res[1]["iters_done"])
                 passes.append(res[1]["refine_passes"])
                 conv += res[1]["converged"]
+                errb.append(res[1]["err_bound"] / C)
+                resid.append(res[1]["residual_inf"])
                 done_n += 1
         if active == 0 and queued == 0 and nxt < len(reqs):
             time.sleep(max(0.0, min(0.01, reqs[nxt].t_arrive - (time.perf_counter() - t0))))
@@ -504,21 +523,170 @@ def run_serve(args):
     phases = srv.phases()
     srv.close()
     lat = np.array(lat)
-    line = {"metric": METRIC, "value": len(reqs) / wall, "unit": "solves/s", "n_gpus": 1, "steps": 1,
+    return {"requests": len(reqs), "offered_per_s": rate, "duration_s": duration, "wall_s": wall,
+            "solves_per_s": len(reqs) / wall,
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "max": float(lat.max())},
+            "converged": int(conv), "max_residual": float(max(resid)),
+            "max_err_bound_over_C": float(max(errb)),
+            "mean_rounds": float(np.mean(rounds)), "mean_refine_passes": float(np.mean(passes)),
+            "server_phases_ms": phases}
+
+
+def run_serve(args):
+    """Poisson stream of SVM-training requests replayed in real time through
+    the continuous-batching server; reports p50/p99 latency and solves/s."""
+    from paper_0810_1648_gb300 import build as gbuild
+    from paper_0810_1648_gb300 import gabp
+    if not os.path.exists(gabp.LIB_PATH):
+        gbuild.build()
+    r = _serve_run(gabp, args.rate, args.duration, args.q_mode, args.msg_bf16, args.stages, args.max_members)
+    line = {"metric": METRIC, "value": r["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": 1,
             "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.q_mode == "f32" else "bf16+f32", "data": "synthetic",
             "config": {"workload": f"serving form: Poisson arrivals rate {args.rate}/s for {args.duration} s, "
                                    "n log-uniform [500,50000], m log-uniform [16,512], C log-uniform [0.1,100], "
                                    "gamma 1/m, tol 1e-6 or 200 rounds, admission by device memory",
-                       "requests": len(reqs), "q_mode": args.q_mode, "max_members": args.max_members,
+                       "requests": r["requests"], "q_mode": args.q_mode, "max_members": args.max_members,
                        "stages": max(args.stages, 1)},
-            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                          "max": float(lat.max())},
-            "wall_s": wall, "offered_per_s": args.rate, "server_phases_ms": phases,
-            "mean_rounds": float(np.mean(rounds)), "mean_refine_passes": float(np.mean(passes)),
-            "converged": int(conv)}
+            "latency_s": r["latency_s"], "wall_s": r["wall_s"], "offered_per_s": args.rate,
+            "server_phases_ms": r["server_phases_ms"], "mean_rounds": r["mean_rounds"],
+            "mean_refine_passes": r["mean_refine_passes"], "converged": r["converged"],
+            "max_err_bound_over_C": r["max_err_bound_over_C"]}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _extra_batch(gabp, torch, warmup, steps):
+    """The batched workload (512 instances, to ||r||_inf < 1e-6 or 200 rounds)
+    in plain FP32 and in the BF16 form (BF16 Q + BF16 messages + refinement),
+    under the synchronous and the 4-stage schedules: solves/s (median of
+    `steps` timed batches, inputs resident on the device), and each form's
+    stated error: the largest Varah bound residual / margin over the 512
+    results, relative to C."""
+    probs = workloads.batch_grid()
+    dev = {}
+    for p in probs:
+        if id(p.X) not in dev:
+            dev[id(p.X)] = (torch.from_numpy(p.X).cuda(), torch.from_numpy(p.y).cuda())
+    dprobs = [workloads.Problem(*dev[id(p.X)], p.gamma, p.C) for p in probs]
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    modes = (("f32", dict(q_mode=0)), ("bf16_refined", dict(q_mode=1, refine=8, msg_bf16=1)),
+             ("f32_staged4", dict(q_mode=0, stages=4)),
+             ("bf16_refined_staged4", dict(q_mode=1, refine=8, msg_bf16=1, stages=4)))
+    out = {}
+    for name, kw in modes:
+        for _ in range(max(1, warmup)):
+            gabp.batch_solve(dprobs, 200, 1e-6, chunk=0, stream=stream.cuda_stream, **kw)
+        times, res = [], None
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, res, rc = gabp.batch_solve(dprobs, 200, 1e-6, chunk=0, stream=stream.cuda_stream, **kw)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        out[name] = {"solves_per_s": len(probs) / float(np.median(times)),
+                     "ms_per_batch": 1e3 * float(np.median(times)),
+                     "converged": int(sum(r["converged"] for r in res)),
+                     "max_residual": float(max(r["residual_inf"] for r in res)),
+                     "max_err_bound_over_C": float(max(r["err_bound"] / p.C for r, p in zip(res, probs))),
+                     "mean_rounds": float(np.mean([r["iters_done"] for r in res]))}
+    gabp.batch_release()
+    out["instances"] = len(probs)
+    out["workload"] = ("512 instances: 32 mixture data sets x C {0.1,1,10,100} x gamma {0.1,0.5,1,2}/m, "
+                       "n log-uniform [200,4000], m in {8,32,128,256}, tol 1e-6 or 200 rounds, device inputs")
+    out["bf16_over_f32"] = out["bf16_refined"]["solves_per_s"] / out["f32"]["solves_per_s"]
+    out["bf16_over_f32_staged4"] = (out["bf16_refined_staged4"]["solves_per_s"]
+                                    / out["f32_staged4"]["solves_per_s"])
+    out["error_note"] = ("max_err_bound_over_C: max over the instances of ||mu - Q^-1 1||_inf / C bounded by "
+                         "Varah: residual / min_i(Q_ii - R_i) of the FP32-Gram matrix, as each result states it")
+    return out
+
+
+def _extra_precision(gabp, torch, peak):
+    """The precision workload (n=100000, m=64, gamma=0.5/64, C=1): sweeps/s of
+    100 synchronous rounds (one warm-up solve, two timed, CUDA events) and the
+    HBM fraction of the pair sweep (every 4th round bracketed) for FP32 Q,
+    BF16 Q + BF16 messages and Q recomputed per sweep + BF16 messages; then
+    each form to ||r||_inf < 1e-6 (FP32, or refinement on the FP32-Gram
+    residual) with its time, rounds and stated error bound."""
+    p = workloads.precision_large()
+    n = p.n
+    pairs = n * (n - 1) // 2
+    Xd, yd = torch.from_numpy(p.X).cuda(), torch.from_numpy(p.y).cuda()
+    stream = torch.cuda.Stream()
+    alpha = torch.empty(n, dtype=torch.float32, device="cuda")
+    modes = (("f32", 0, 0), ("bf16", 1, 1), ("recompute", 2, 1))
+    out = {}
+    for name, qm, mb16 in modes:
+        qb = Q_BYTES[name]
+        mb = 4 if mb16 else 8
+        h = gabp.svm_create(Xd, yd, p.gamma, p.C, gabp.opts_default(stream=stream.cuda_stream, chunk=ROUNDS,
+                                                                    q_mode=qm, msg_bf16=mb16))
+        gabp.svm_set_profiling(h, PROFILE_STRIDE)
+        gabp.svm_solve(h, ROUNDS, 0.0, alpha)
+        gabp.svm_get_profile(h, reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(2):
+            gabp.svm_refit(h, Xd, yd, p.gamma, p.C)
+            gabp.svm_solve(h, ROUNDS, 0.0, alpha)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = float(e0.elapsed_time(e1))
+        prof = gabp.svm_get_profile(h)
+        gabp.svm_destroy(h)
+        nz, nf, nl = prof["sweep_launches_zero_state"], prof["sweep_launches_p_frozen"], prof["sweep_launches"]
+        alg = pairs * ((4 * mb + qb) * (nl - nz - nf) + (3 * mb + qb) * nf + (2 * mb + qb) * nz)
+        achieved = alg / (prof["sweep_ms"] / 1e3) / 1e9 if prof["sweep_ms"] > 0 else None
+        entry = {"sweeps_per_s": 2 * ROUNDS / (ms / 1e3),
+                 "sweep_hbm": {"achieved_GBps": achieved, "frac_of_measured_peak": achieved / peak if achieved else None,
+                               "avg_launch_ms": prof["sweep_ms"] / max(nl, 1), "launches_timed": nl,
+                               "bytes_per_pair": {"p_live": 4 * mb + qb, "p_frozen": 3 * mb + qb}}}
+        # to tolerance: refinement removes the BF16 error (FP32-Gram residual, FP64 sums)
+        opts = gabp.opts_default(stream=stream.cuda_stream, chunk=8, q_mode=qm, msg_bf16=mb16,
+                                 refine=10 if qm else 0)
+        h = gabp.svm_create(Xd, yd, p.gamma, p.C, opts)
+        for _ in range(2):
+            torch.cuda.synchronize()
+            e0.record(stream)
+            gabp.svm_refit(h, Xd, yd, p.gamma, p.C)
+            rinf, k = gabp.svm_solve(h, 400, 1e-6, alpha)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        st = gabp.svm_get_stats(h)
+        gabp.svm_destroy(h)
+        entry["to_tolerance"] = {"ms": float(e0.elapsed_time(e1)), "rounds": int(k), "residual_inf": float(rinf),
+                                 "converged": int(st["converged"]), "refine_passes": int(st["refine_passes"]),
+                                 "err_bound": float(st["err_bound"]), "err_bound_over_C": float(st["err_bound"] / p.C),
+                                 "margin": float(st["margin"])}
+        out[name] = entry
+    out["workload"] = ("precision form: n=100000, m=64 mixture (seed 2), gamma=0.5/64, C=1; 100 synchronous "
+                       "rounds per timed solve; FP32 Q / BF16 Q + BF16 messages / Q recomputed per sweep on the "
+                       "tensor cores + BF16 messages")
+    out["bf16_over_f32_sweeps"] = out["bf16"]["sweeps_per_s"] / out["f32"]["sweeps_per_s"]
+    out["bf16_over_f32_to_tolerance"] = out["f32"]["to_tolerance"]["ms"] / out["bf16"]["to_tolerance"]["ms"]
+    return out
+
+
+def _extra_serve(gabp):
+    """The serving form, both forms: the first 3 s of the configured stream
+    (200 requests/s: more than one GB300 clears, so solves/s is the
+    sustainable rate) and a sub-saturating 15 requests/s for 8 s (latency)."""
+    out = {}
+    for name, qm, mb16 in (("f32", "f32", False), ("bf16_refined", "bf16", True)):
+        out[name] = {"saturating": _serve_run(gabp, 200.0, 3.0, qm, mb16, 4, 64),
+                     "sub_saturating": _serve_run(gabp, 15.0, 8.0, qm, mb16, 4, 64)}
+        for k in ("saturating", "sub_saturating"):
+            out[name][k].pop("server_phases_ms", None)
+    out["bf16_over_f32_saturating"] = (out["bf16_refined"]["saturating"]["solves_per_s"]
+                                       / out["f32"]["saturating"]["solves_per_s"])
+    out["workload"] = ("serving form: Poisson stream (seed 7), n log-uniform [500,50000], m log-uniform [16,512], "
+                       "C log-uniform [0.1,100], gamma 1/m, tol 1e-6 or 200 rounds, 4-stage schedule, chunk 4, "
+                       "up to 64 members; replayed in real time")
+    return out
 
 
 def run_ours(args):
@@ -629,6 +797,12 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         e2e = _e2e(args, p, stream, dev, ws, gabp, torch)
+    extras = {}
+    if rank == 0 and ws == 1 and not args.no_extras and args.workload == "plain_large" and args.task == "svm":
+        # the other forms of the method, measured in the same run (outside the timed region)
+        extras["batch"] = _extra_batch(gabp, torch, 1, 3)
+        extras["precision"] = _extra_precision(gabp, torch, peak)
+        extras["serve"] = _extra_serve(gabp)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         if args.workload != "plain_large":
@@ -649,6 +823,7 @@ def run_ours(args):
                 "gpu_launches": int(launches), "clocks": clk, "solve_to_tolerance": to_tol,
                 "result": {"residual_inf": st["residual_inf"], "dual_objective": st["dual_objective"],
                            "n_support": st["n_support"]}}
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -731,11 +906,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-to-tol", action="store_true", help="skip the solve-to-tolerance extra measurement")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched, precision and serving measurements added to the default line")
     ap.add_argument("--workload", default="plain_large",
                     choices=["plain_large", "precision_large", "batch_grid", "serve", "sparse_large"])
     ap.add_argument("--batch-modes", default="",
                     help="batch_grid: comma-separated subset of f32, bf16q_refined, bf16_refined, f32_staged, "
                          "bf16_refined_staged (default all)")
+    ap.add_argument("--sparse-n", type=int, default=20000,
+                    help="sparse_large: n of the clustered set (20000, or e.g. 200000 beyond dense memory)")
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--duration", type=float, default=60.0)
     ap.add_argument("--max-members", type=int, default=64)

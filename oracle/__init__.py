@@ -75,6 +75,7 @@ def _load():
         "orc_cholesky_solve": (i32, [D, D, L, D]),
         "orc_q_row": (None, [D, D, L, L, f64, f64, f64, i32, f64, L, D]),
         "orc_q_diag_all": (i32, [D, D, L, L, f64, f64, f64, i32, f64, D, D]),
+        "orc_q_diag_tilemax": (i32, [D, D, L, L, f64, f64, f64, i32, f64, L, D, D, D]),
         "orc_cg_rbf": (i32, [D, D, L, L, f64, f64, f64, i32, f64, D, f64, i32, D, I]),
         "orc_dual_objective": (f64, [D, D, L]),
         "orc_decision": (i32, [D, D, D, L, L, D, L, f64, f64, D]),
@@ -162,6 +163,26 @@ def q_diag_all(X, y, gamma, C, lam=None, diag_rule=DIAG_DOMINANT, delta=0.1):
                                 R.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     _check(rc, "q_diag_all")
     return diag, R
+
+
+def q_diag_tilemax(X, y, gamma, C, block=128, lam=None, diag_rule=DIAG_DOMINANT, delta=0.1):
+    """(diag, R, tmax): as q_diag_all, plus the largest |Q_ij| of every
+    block x block tile of the upper triangle (pairs i < j), as an Nt x Nt
+    array with tmax[I, J] for I <= J (0 below the diagonal), Q not stored."""
+    X, px = _d(X)
+    y, py = _d(y)
+    n, m = X.shape
+    lam = default_lambda(n) if lam is None else lam
+    nt = (n + block - 1) // block
+    diag, R, flat = np.empty(n), np.empty(n), np.empty(nt * (nt + 1) // 2)
+    P = ctypes.POINTER(ctypes.c_double)
+    rc = _load().orc_q_diag_tilemax(px, py, n, m, gamma, lam, C, diag_rule, delta, int(block),
+                                    diag.ctypes.data_as(P), R.ctypes.data_as(P), flat.ctypes.data_as(P))
+    _check(rc, "q_diag_tilemax")
+    tmax = np.zeros((nt, nt))
+    iu = np.triu_indices(nt)
+    tmax[iu] = flat          # row-major upper triangle: L = I Nt - I (I - 1) / 2 + (J - I)
+    return diag, R, tmax
 
 
 class GabpResult:

@@ -157,6 +157,60 @@ int orc_q_diag_all(const double* X, const double* y, long n, long m, double gamm
     return ORC_OK;
 }
 
+/* The diagonal, the off-diagonal absolute row sums R_i and, for the
+ * tile-sparse reading of Section 6's sparsified kernel, the largest |Q_ij| of
+ * every block x block tile (I <= J) of the upper triangle (pairs i < j only;
+ * tile index L = I Nt - I (I - 1) / 2 + (J - I), Nt = ceil(n / block)), in one
+ * pass over the pairs without storing Q.  Row i's pairs go to its own thread,
+ * so each tile maximum is the plain maximum over its rows.  R and the diagonal
+ * follow orc_q_diag_all. */
+int orc_q_diag_tilemax(const double* X, const double* y, long n, long m, double gamma,
+                       double lam, double C, int diag_rule, double delta, long block,
+                       double* diag, double* R, double* tmax)
+{
+    if (n < 1 || m < 1 || block < 1 || !(gamma > 0) || !(C > 0)) return ORC_EINVAL;
+    const long Nt = (n + block - 1) / block;
+    const long ntiles = Nt * (Nt + 1) / 2;
+    const int T = orc_threads();
+    double* acc = (double*)calloc((size_t)T * (size_t)n, sizeof(double));
+    double* tm = (double*)calloc((size_t)T * (size_t)ntiles, sizeof(double));
+    if (!acc || !tm) { free(acc); free(tm); return ORC_ENOMEM; }
+#pragma omp parallel
+    {
+        double* mine = acc + (size_t)orc_thread_id() * (size_t)n;
+        double* mt = tm + (size_t)orc_thread_id() * (size_t)ntiles;
+#pragma omp for schedule(dynamic, 16)
+        for (long i = 0; i < n; ++i) {
+            const long I = i / block;
+            double ri = 0.0;
+            for (long j = i + 1; j < n; ++j) {
+                double q = fabs(orc_q_offdiag(X + i * m, X + j * m, y[i], y[j], m, gamma, lam));
+                ri += q;
+                mine[j] += q;
+                const long J = j / block;
+                const long L = I * Nt - I * (I - 1) / 2 + (J - I);
+                if (q > mt[L]) mt[L] = q;
+            }
+            mine[i] += ri;
+        }
+    }
+    for (long i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int t = 0; t < T; ++t) s += acc[(size_t)t * (size_t)n + i];
+        R[i] = s;
+        diag[i] = orc_q_diag(s, lam, C, diag_rule, delta);
+    }
+    for (long L = 0; L < ntiles; ++L) {
+        double v = 0.0;
+        for (int t = 0; t < T; ++t)
+            if (tm[(size_t)t * (size_t)ntiles + L] > v) v = tm[(size_t)t * (size_t)ntiles + L];
+        tmax[L] = v;
+    }
+    free(acc);
+    free(tm);
+    return ORC_OK;
+}
+
 /* r = b - Q mu, returns ||r||_inf.  The paper's Step 3 tests the messages for
  * convergence without naming a norm; the reading used throughout is the
  * infinity norm of the linear-system residual of the current means. */

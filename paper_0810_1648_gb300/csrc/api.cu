@@ -61,6 +61,12 @@ struct gabp_svm_s {
     double gamma = 0, C = 0, lambda = 0, delta = 0;
     void* pool = nullptr;
     size_t pool_bytes = 0;
+    // tile-sparse option: the message state and Q of the kept tiles live in a
+    // second allocation sized after the tile-maxima pass (grown on refit)
+    void* spool = nullptr;
+    size_t spool_bytes = 0;
+    float* tilemax = nullptr;       // per-tile maxima (formation's first pass)
+    int* slab = nullptr;            // slab of every tile in the compacted storage, -1 = dropped
     Inst inst{};
     Inst* d_tab = nullptr;          // device copy of inst (a one-instance batch)
     int4* work_all = nullptr;       // every tile {0, I, J, L}, row by row (formation)
@@ -85,6 +91,7 @@ struct gabp_svm_s {
     int profiling = 0;   // 0 off, k >= 1: the pair sweep of every k-th round is bracketed by events
     gabp_svm_profile prof{};
     bool solved = false;
+    bool formed = false;            // the last create/refit formed Q completely (else only refit/destroy are valid)
     int kstar = 0;
     float* mu_acc = nullptr;        // refined means (precision form)
     float* r32 = nullptr;           // FP32 residual of the accurate matrix (refinement)
@@ -100,27 +107,48 @@ gabp_status check_handle(gabp_svm_t h)
     return GABP_OK;
 }
 
+// Handle whose last create/refit completed (a failed refit leaves only
+// refit and destroy valid).
+gabp_status check_formed(gabp_svm_t h)
+{
+    if (gabp_status s = check_handle(h)) return s;
+    if (!h->formed) return fail(GABP_ESTATE, "the last refit failed; refit again before using the handle");
+    return GABP_OK;
+}
+
 // Device memory plan of one handle (bytes, 256-aligned sub-buffers).
 struct Plan {
     size_t X, vec, agg, part, state, q, qref, work, tilemax, ctrl, rhist, final3, blockbuf, xp, tab, nbl, total;
 };
 
+// Bytes of the per-pair arrays (messages, stored Q, FP32 copy) for `tiles` tiles.
+size_t pair_bytes(long long tiles, int q_mode, int msg_bf16)
+{
+    const size_t tt = (size_t)tiles * TT;
+    return 2 * align_up(tt * (msg_bf16 ? 4 : 8), 256) +
+           (q_mode == GABP_Q_F32 ? align_up(tt * 4, 256) : q_mode == GABP_Q_BF16 ? align_up(tt * 2, 256) : 0) +
+           (q_mode == GABP_Q_BF16 ? align_up(tt * 4, 256) : 0);
+}
+
 Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_mode, int msg_bf16, bool sparse)
 {
     Plan p{};
-    // the tile-sparse option keeps a second tile list (the swept tiles) and the tile maxima
-    p.tilemax = sparse ? align_up((size_t)ntiles * sizeof(float), 256) : 0;
+    // the tile-sparse option keeps a second tile list (the swept tiles), the
+    // tile maxima and the slab map; its per-pair arrays are allocated later,
+    // for the kept tiles only (pair_bytes)
+    p.tilemax = sparse ? 2 * align_up((size_t)ntiles * sizeof(float), 256) : 0;
     p.xp = q_mode != GABP_Q_F32 ? align_up(bf16_pack_bytes(Nt, (int)m), 1024) : 0;
     p.X = align_up((size_t)n * m * sizeof(float), 256);
     p.vec = align_up((size_t)npad * sizeof(float), 256);
     p.agg = align_up((size_t)8 * npad * sizeof(float), 256);   // 2 x {P, h, mu} + staged {P, h}
     p.part = align_up((size_t)4 * Nt * n * sizeof(float), 256);
-    p.state = 2 * align_up((size_t)ntiles * TT * (msg_bf16 ? 4 : 8), 256);
-    p.q = q_mode == GABP_Q_F32 ? align_up((size_t)ntiles * TT * sizeof(float), 256)
-        : q_mode == GABP_Q_BF16 ? align_up((size_t)ntiles * TT * sizeof(__nv_bfloat16), 256)
+    const long long dense_tiles = sparse ? 0 : ntiles;
+    p.state = 2 * align_up((size_t)dense_tiles * TT * (msg_bf16 ? 4 : 8), 256);
+    p.q = q_mode == GABP_Q_F32 ? align_up((size_t)dense_tiles * TT * sizeof(float), 256)
+        : q_mode == GABP_Q_BF16 ? align_up((size_t)dense_tiles * TT * sizeof(__nv_bfloat16), 256)
         : 0;
     // the BF16 store keeps an FP32 copy for the refinement residuals
-    p.qref = q_mode == GABP_Q_BF16 ? align_up((size_t)ntiles * TT * sizeof(float), 256) : 0;
+    p.qref = q_mode == GABP_Q_BF16 ? align_up((size_t)dense_tiles * TT * sizeof(float), 256) : 0;
     p.work = (sparse ? 2 : 1) * align_up((size_t)ntiles * sizeof(int4), 256);
     p.tab = align_up(align_up(sizeof(Inst), 16) + kMaxStages * align_up(sizeof(Sched), 16) + sizeof(StopOp) + 64, 256);
     p.nbl = align_up((size_t)((n + 31) / 32) * sizeof(int2), 256);
@@ -144,9 +172,11 @@ void clear_graphs(gabp_svm_t h)
 
 // The swept tile list after formation.  Dense: every tile (the list built at
 // create, grouped by stage).  Tile-sparse: the diagonal tiles and every tile
-// whose largest |Q_ij| exceeds sparse_tau, grouped by stage.  The diagonal
-// rule keeps the row sums of the whole matrix, so dropping a tile changes
-// only its own entries (and the matrix stays diagonally dominant).
+// whose largest |Q_ij| exceeds sparse_tau, grouped by stage, each given the
+// next slab of the compacted per-pair storage (h->slab maps every tile to its
+// slab, -1 for a dropped one).  The diagonal rule keeps the row sums of the
+// whole matrix, so dropping a tile changes only its own entries (and the
+// matrix stays diagonally dominant).
 gabp_status build_sweep_list(gabp_svm_t h)
 {
     h->stats.tiles_total = h->ntiles;
@@ -157,12 +187,13 @@ gabp_status build_sweep_list(gabp_svm_t h)
     }
     cudaStream_t s = h->stream;
     std::vector<float> mx((size_t)h->ntiles);
-    CK(cudaMemcpyAsync(mx.data(), h->inst.tilemax, mx.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(mx.data(), h->tilemax, mx.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const int Nt = h->Nt;
     auto L_of = [Nt](int I, int J) { return (long long)I * Nt - (long long)I * (I - 1) / 2 + (J - I); };
     const float tau = h->opts.sparse_tau;
     std::vector<int4> wl;
+    std::vector<int> slab((size_t)h->ntiles, -1);
     int B[kMaxStages + 1];
     stage_bounds(Nt, h->nstages, B);
     const int nblk = (int)((h->n + 31) / 32);
@@ -172,16 +203,60 @@ gabp_status build_sweep_list(gabp_svm_t h)
         for (int I = 0; I < Nt; ++I)
             for (int J = std::max(I, B[st]); J < B[st + 1]; ++J) {
                 const long long L = L_of(I, J);
-                const int4 t = make_int4(0, I, J, (int)L);
-                if (I == J || mx[(size_t)L] > tau) wl.push_back(t);
+                if (I == J || mx[(size_t)L] > tau) {
+                    slab[(size_t)L] = (int)wl.size();
+                    wl.push_back(make_int4(0, I, J, (int)wl.size()));
+                }
             }
         sc[st] = Sched{(long long)wl.size() - off, nblk, 1, off, Nt <= kWarpFinNt ? nblk : 0, 0};
     }
     h->nlive = (long long)wl.size();
     h->stats.tiles_kept = h->nlive;
     CK(cudaMemcpyAsync(h->work, wl.data(), wl.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->slab, slab.data(), slab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(h->sched, sc, (size_t)h->nstages * sizeof(Sched), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));   // the host lists go out of scope
+    return GABP_OK;
+}
+
+// Tile-sparse option: per-pair arrays for the h->nlive kept tiles, in the
+// second allocation (kept when large enough, else replaced).  GABP_ENOMEM when
+// they do not fit in free device memory.
+gabp_status ensure_pair_storage(gabp_svm_t h)
+{
+    Inst& p = h->inst;
+    const int qm = h->opts.q_mode, mb = h->opts.msg_bf16;
+    const size_t need = pair_bytes(h->nlive, qm, mb) + 1024;
+    if (need > h->spool_bytes) {
+        CK(cudaStreamSynchronize(h->stream));
+        if (h->spool) CK(cudaFree(h->spool));
+        h->spool = nullptr;
+        h->spool_bytes = 0;
+        size_t free_b = 0, total_b = 0;
+        CK(cudaMemGetInfo(&free_b, &total_b));
+        const size_t margin = (size_t)256 << 20;
+        if (need + margin > free_b)
+            return fail(GABP_ENOMEM, "the %lld kept tiles need %.2f GB of device memory, %.2f GB free",
+                        h->nlive, need / 1e9, free_b / 1e9);
+        cudaError_t e = cudaMalloc(&h->spool, need);
+        if (e != cudaSuccess) return fail(GABP_ENOMEM, "cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+        h->spool_bytes = need;
+    }
+    const size_t tt = (size_t)h->nlive * TT;
+    char* b = static_cast<char*>(h->spool);
+    const size_t st = align_up(tt * (mb ? 4 : 8), 256);
+    p.Pst = b;
+    p.Hst = b + st;
+    b += 2 * st;
+    p.qstore = nullptr;
+    p.qref = nullptr;
+    if (qm == GABP_Q_F32) {
+        p.qstore = b;
+        p.qref = (float*)b;
+    } else if (qm == GABP_Q_BF16) {
+        p.qstore = b;
+        p.qref = (float*)(b + align_up(tt * 2, 256));
+    }
     return GABP_OK;
 }
 
@@ -200,9 +275,17 @@ gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
     p.task = h->opts.task;
     clear_graphs(h);
     h->solved = false;
+    h->formed = false;
     h->kstar = 0;
     h->mean_src = nullptr;
 
+    if (h->opts.sparse_tau > 0) {
+        // formation's first pass stores nothing and records the tile maxima
+        p.tilemax = h->tilemax;
+        p.slab = nullptr;
+        p.qstore = nullptr;
+        p.qref = nullptr;
+    }
     CK(cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), s));
     CK(cudaMemcpyAsync(h->d_tab, &p, sizeof(Inst), cudaMemcpyHostToDevice, s));
     // labels -> device copy (validated by the staging kernel, which also sets b = 1)
@@ -231,7 +314,36 @@ gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
         return fail(GABP_EINVAL, h->opts.task == GABP_TASK_KRR ? "row %lld: non-finite feature or target"
                                                                 : "row %lld: non-finite feature or label not +-1",
                     (long long)h->hctrl->bad_index);
-    if (h->opts.q_mode == GABP_Q_F32) {
+    if (h->opts.sparse_tau > 0) {
+        // Tile-sparse option.  Pass 1 over every tile: tile maxima and |Q|
+        // row sums (the whole matrix's, for the diagonal rule), nothing
+        // stored.  Then the kept-tile list and its compacted storage, and
+        // pass 2 over the kept tiles only: their FP32 values (the store, or
+        // the FP32 copy beside the BF16 store; the row sums it writes again
+        // are the same values), the diagonal rule and Step 1, and the BF16
+        // tiles.  Recompute needs no second pass.
+        if (h->opts.q_mode != GABP_Q_F32)
+            CK(launch_pack_bf16(p.X, (int)n, (int)m, p.nkc, h->Nt, (void*)p.Xp, (float*)p.sqb, s));
+        launch_form_q(h->d_tab, h->work_all, h->ntiles, s);
+        CK(cudaGetLastError());
+        h->prof.kernel_launches += h->opts.q_mode != GABP_Q_F32 ? 3 : 1;
+        if (gabp_status st = build_sweep_list(h)) return st;
+        if (gabp_status st = ensure_pair_storage(h)) return st;
+        p.tilemax = nullptr;
+        p.slab = h->slab;
+        CK(cudaMemcpyAsync(h->d_tab, &p, sizeof(Inst), cudaMemcpyHostToDevice, s));
+        if (h->opts.q_mode != GABP_Q_RECOMPUTE) {
+            launch_form_q(h->d_tab, h->work, h->nlive, s);
+            h->prof.kernel_launches += 1;
+        }
+        launch_init(p, h->opts.diag_rule, (float)h->delta, s);
+        h->prof.kernel_launches += 1;
+        CK(cudaGetLastError());
+        if (h->opts.q_mode == GABP_Q_BF16) {
+            CK(launch_form_q_tc(h->d_tab, h->work, h->nlive, s));
+            h->prof.kernel_launches += 1;
+        }
+    } else if (h->opts.q_mode == GABP_Q_F32) {
         launch_form_q(h->d_tab, h->work_all, h->ntiles, s);
         CK(cudaGetLastError());
         if (gabp_status st = build_sweep_list(h)) return st;
@@ -256,6 +368,7 @@ gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
         }
     }
     CK(cudaStreamSynchronize(s));
+    h->formed = true;
     return GABP_OK;
 }
 
@@ -265,6 +378,7 @@ void destroy_all(gabp_svm_t h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     clear_graphs(h);
     if (h->pool) cudaFree(h->pool);
+    if (h->spool) cudaFree(h->spool);
     if (h->hctrl) cudaFreeHost(h->hctrl);
     if (h->hfinal) cudaFreeHost(h->hfinal);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -495,7 +609,8 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     if (o.sparse_tau > 0) {
         h->work_all = (int4*)take(pl.work / 2);
         h->work = (int4*)take(pl.work / 2);
-        p.tilemax = (float*)take(pl.tilemax);
+        h->tilemax = (float*)take(pl.tilemax / 2);
+        h->slab = (int*)take(pl.tilemax / 2);
     } else {
         h->work = h->work_all = (int4*)take(pl.work);   // formation walks the swept list
     }
@@ -569,7 +684,7 @@ gabp_status gabp_svm_solve(gabp_svm_t h, int32_t iters, double tol, float* alpha
                            int32_t* iters_done)
 {
     g_err.clear();
-    if (gabp_status s = check_handle(h)) return s;
+    if (gabp_status s = check_formed(h)) return s;
     if (iters < 0) return fail(GABP_EINVAL, "iters must be >= 0");
     if (std::isnan(tol)) return fail(GABP_EINVAL, "tol is NaN");
     cudaStream_t s = h->stream;
@@ -698,7 +813,7 @@ gabp_status gabp_svm_solve(gabp_svm_t h, int32_t iters, double tol, float* alpha
 gabp_status gabp_svm_get_mean(gabp_svm_t h, float* mu)
 {
     g_err.clear();
-    if (gabp_status s = check_handle(h)) return s;
+    if (gabp_status s = check_formed(h)) return s;
     if (!mu) return fail(GABP_EINVAL, "mu is NULL");
     const Inst& p = h->inst;
     const float* src = h->mean_src ? h->mean_src : p.agg + 2 * (size_t)p.npad;
@@ -711,7 +826,7 @@ gabp_status gabp_svm_get_mean(gabp_svm_t h, float* mu)
 gabp_status gabp_svm_get_aggregates(gabp_svm_t h, float* Pt, float* ht, float* mu)
 {
     g_err.clear();
-    if (gabp_status s = check_handle(h)) return s;
+    if (gabp_status s = check_formed(h)) return s;
     const Inst& p = h->inst;
     CK(cudaMemcpyAsync(h->hctrl, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -727,7 +842,7 @@ gabp_status gabp_svm_get_aggregates(gabp_svm_t h, float* Pt, float* ht, float* m
 gabp_status gabp_svm_decision(gabp_svm_t h, const void* Xtest, int64_t t, float* out)
 {
     g_err.clear();
-    if (gabp_status s = check_handle(h)) return s;
+    if (gabp_status s = check_formed(h)) return s;
     if (!h->solved) return fail(GABP_ESTATE, "no solve yet");
     if (t < 0 || (t > 0 && (!Xtest || !out))) return fail(GABP_EINVAL, "bad test set");
     if (t == 0) return GABP_OK;
@@ -823,7 +938,7 @@ gabp_status gabp_svm_get_stats(gabp_svm_t h, gabp_svm_stats* st)
     h->stats.gamma = h->gamma;
     h->stats.C = h->C;
     h->stats.diag_delta = h->delta;
-    h->stats.device_bytes = (int64_t)h->pool_bytes;
+    h->stats.device_bytes = (int64_t)(h->pool_bytes + h->spool_bytes);
     h->stats.q_mode = h->opts.q_mode;
     h->stats.diag_rule = h->opts.diag_rule;
     *st = h->stats;
@@ -833,7 +948,7 @@ gabp_status gabp_svm_get_stats(gabp_svm_t h, gabp_svm_stats* st)
 gabp_status gabp_svm_get_q(gabp_svm_t h, float* Q)
 {
     g_err.clear();
-    if (gabp_status s = check_handle(h)) return s;
+    if (gabp_status s = check_formed(h)) return s;
     if (!Q) return fail(GABP_EINVAL, "Q is NULL");
     if (h->opts.q_mode == GABP_Q_RECOMPUTE) return fail(GABP_ESTATE, "Q is not stored in recompute mode");
     if (h->n > 46340) return fail(GABP_EINVAL, "n too large for a dense copy");
@@ -856,7 +971,7 @@ gabp_status gabp_svm_get_q(gabp_svm_t h, float* Q)
 gabp_status gabp_svm_get_pairs(gabp_svm_t h, const int64_t* i, const int64_t* j, int64_t cnt, float* out)
 {
     g_err.clear();
-    if (gabp_status s = check_handle(h)) return s;
+    if (gabp_status s = check_formed(h)) return s;
     if (cnt < 0 || (cnt > 0 && (!i || !j || !out))) return fail(GABP_EINVAL, "bad pair list");
     if (cnt == 0) return GABP_OK;
     std::vector<long long> ij((size_t)cnt * 2);

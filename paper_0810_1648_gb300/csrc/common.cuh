@@ -81,6 +81,9 @@ struct Inst {
     void* Hst;        // ntiles * TT information messages {H_ij, H_ji}
     void* qstore;     // ntiles * TT values of Q (float or bf16), or nullptr
     float* tilemax;   // per tile, the largest off-diagonal |Q_ij| (tile-sparse option), or nullptr
+    const int* slab;  // tile-sparse option: slab of tile L = I Nt - I (I - 1) / 2 + (J - I) in the
+                      // per-pair arrays (kept tiles are stored compacted), -1 for a dropped
+                      // tile; nullptr = slab L (dense storage)
     float* qref;      // ntiles * TT FP32 values of Q for the residual passes (the FP32
                       // store itself, a separate copy beside the BF16 store, or nullptr
                       // when Q is recomputed)

@@ -117,6 +117,7 @@ struct TcSmem {
     unsigned long long drain;
     uint32_t tmem_base;
     int abort;
+    ColChunk cols[TC_EPI_WARPS];   // column constants, one chunk per epilogue warp
 };
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -236,11 +237,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int i = I * T + r;
             // the listed instance and every one chained behind it (same
             // features) take their BF16 Q tile from this accumulator
+            ColChunk& cs = sm.cols[warp - 2];
             for (int k = w.x; k >= 0;) {
                 const Inst& p = tab[k];
                 const int n = p.n;
                 const float* sqb = p.sqb;
                 const float yi = i < n ? p.y[i] : 0.f, si = i < n ? sqb[i] : 0.f;
+                const float ai = -p.gamma * kLog2e * si, c2 = 2.f * p.gamma * kLog2e;
+                const uint32_t syi = __float_as_uint(yi) & 0x80000000u;
                 __nv_bfloat16* qrow = static_cast<__nv_bfloat16*>(p.qstore) + (size_t)w.w * TT + (size_t)r * T;
 #pragma unroll 1
                 for (int cc = 2 * half; cc < 2 * half + 2; ++cc) {
@@ -248,8 +252,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     tmem_ld32(tbase + (uint32_t)acc * T + ((uint32_t)(32 * g) << 16) + (uint32_t)(32 * cc), v);
                     const int jl = J * T + 32 * cc + lane;
                     const float yl = jl < n ? p.y[jl] : 0.f, sl = jl < n ? sqb[jl] : 0.f;
+                    stage_cols(cs, yl, sl, p.gamma, lane);
                     uint4 out[4];
-                    q_chunk_bf16(v, yi, si, yl, sl, p.gamma, p.lam2, chunk_valid(n, I, J, r, cc), out);
+                    q_chunk_bf16(v, ai, syi, cs, c2, p.lam2, chunk_valid(n, I, J, r, cc), out);
                     uint4* dst = reinterpret_cast<uint4*>(qrow + 32 * cc);
 #pragma unroll
                     for (int u = 0; u < 4; ++u) dst[u] = out[u];

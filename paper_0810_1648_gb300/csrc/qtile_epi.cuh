@@ -22,29 +22,65 @@ __device__ __forceinline__ uint32_t chunk_valid(int n, int I, int J, int r, int 
     return upto & ~((1u << lo) - 1u);   // lo < hi <= 32, so lo < 32
 }
 
+// log2(e): K = exp(-gamma d2) = 2^(-gamma log2(e) d2).
+constexpr float kLog2e = 1.4426950408889634f;
+
+// The column constants of one 32-column chunk, staged in shared memory by
+// the warp that uses them: b[c] = -gamma log2(e) ||x_j||^2 and sy[c] = the
+// sign bit of y_j, for column j = J T + 32 cc + c.
+struct ColChunk {
+    alignas(16) float b[32];
+    alignas(16) uint32_t sy[32];
+};
+
+// Lane c writes column c's constants from its y_j (yl) and ||x_j||^2 (sl)
+// (0 beyond n: such columns are masked out).  The first __syncwarp keeps the
+// previous chunk's constants until every lane has read them.
+__device__ __forceinline__ void stage_cols(ColChunk& cs, float yl, float sl, float gamma, int lane)
+{
+    __syncwarp();
+    cs.b[lane] = -gamma * kLog2e * sl;
+    cs.sy[lane] = __float_as_uint(yl) & 0x80000000u;
+    __syncwarp();
+}
+
+// 2^t by the hardware approximation (relative error of a few units in the
+// last place of FP32, far below the BF16 rounding of the Q entries).
+__device__ __forceinline__ float ex2_approx(float t)
+{
+    float r;
+    asm("ex2.approx.f32 %0, %1;" : "=f"(r) : "f"(t));
+    return r;
+}
+
 // out = BF16 q_ij for the 32 columns of one row chunk (0 where `valid` has no
 // bit): q_ij = y_i y_j (exp(-gamma d2) + lambda^2), d2 = max(0, ||x_i||^2 +
-// ||x_j||^2 - 2 g_ij) with g the Gram values of the chunk.  Lane c of the warp
-// holds y_j and ||x_j||^2 of column c (yl, sl); they reach the other lanes by
-// shuffles.  exp is the hardware-based __expf: its relative error (a few 1e-6
-// for these arguments) is far below the BF16 rounding of the entries.
-__device__ __forceinline__ void q_chunk_bf16(const float (&g)[32], float yi, float si, float yl, float sl,
-                                             float gamma, float lam2, uint32_t valid, uint4 (&out)[4])
+// ||x_j||^2 - 2 g_ij) with g the Gram values of the chunk, evaluated as
+// 2^min(0, a_i + b_j + c2 g_ij) with a_i = -gamma log2(e) ||x_i||^2, b_j from
+// the staged column constants and c2 = 2 gamma log2(e); the label product
+// y_i y_j = +-1 is applied as a sign flip (sign bits syi ^ sy_j).
+__device__ __forceinline__ void q_chunk_bf16(const float (&g)[32], float ai, uint32_t syi, const ColChunk& cs,
+                                             float c2, float lam2, uint32_t valid, uint4 (&out)[4])
 {
     uint32_t w[16];
 #pragma unroll
-    for (int c = 0; c < 32; c += 2) {
-        float q2[2];
+    for (int c = 0; c < 32; c += 4) {
+        const float4 b4 = *reinterpret_cast<const float4*>(&cs.b[c]);
+        const uint4 s4 = *reinterpret_cast<const uint4*>(&cs.sy[c]);
+        const float bj[4] = {b4.x, b4.y, b4.z, b4.w};
+        const uint32_t sj[4] = {s4.x, s4.y, s4.z, s4.w};
+        float q4[4];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const float yj = __shfl_sync(0xffffffffu, yl, c + u);
-            const float sj = __shfl_sync(0xffffffffu, sl, c + u);
-            const float d2 = fmaxf(0.f, si + sj - 2.f * g[c + u]);
-            const float q = yi * yj * (__expf(-gamma * d2) + lam2);
-            q2[u] = ((valid >> (c + u)) & 1u) ? q : 0.f;
+        for (int u = 0; u < 4; ++u) {
+            const float t = fminf(fmaf(c2, g[c + u], bj[u]) + ai, 0.f);
+            const float q = ex2_approx(t) + lam2;
+            const float qs = __uint_as_float(__float_as_uint(q) ^ syi ^ sj[u]);
+            q4[u] = ((valid >> (c + u)) & 1u) ? qs : 0.f;
         }
-        const __nv_bfloat162 h = __floats2bfloat162_rn(q2[0], q2[1]);
-        w[c / 2] = *reinterpret_cast<const uint32_t*>(&h);
+        __nv_bfloat162 h0 = __floats2bfloat162_rn(q4[0], q4[1]);
+        __nv_bfloat162 h1 = __floats2bfloat162_rn(q4[2], q4[3]);
+        w[c / 2] = *reinterpret_cast<const uint32_t*>(&h0);
+        w[c / 2 + 1] = *reinterpret_cast<const uint32_t*>(&h1);
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) out[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);

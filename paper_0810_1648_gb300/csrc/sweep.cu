@@ -720,6 +720,7 @@ struct RcExtra {
     unsigned long long drain;
     uint32_t tmem_base;
     int abort;
+    ColChunk cols[4];   // column constants, one chunk per epilogue warp
 };
 
 template <class MSG>
@@ -882,6 +883,8 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
             tc_fence_after();
             const int I = w.y, J = w.z, i = I * T + r;
             const float yi = i < n ? p.y[i] : 0.f, si = i < n ? p.sqb[i] : 0.f;
+            const float ai = -p.gamma * kLog2e * si, c2 = 2.f * p.gamma * kLog2e;
+            const uint32_t syi = __float_as_uint(yi) & 0x80000000u;
             __nv_bfloat16* qrow = qtile + (size_t)acc * TT + (size_t)r * T;
 #pragma unroll 1
             for (int cc = 0; cc < T / 32; ++cc) {
@@ -889,8 +892,9 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
                 tmem_ld32(tbase + (uint32_t)acc * T + ((uint32_t)(32 * g) << 16) + (uint32_t)(32 * cc), v);
                 const int jl = J * T + 32 * cc + lane;
                 const float yl = jl < n ? p.y[jl] : 0.f, sl = jl < n ? p.sqb[jl] : 0.f;
+                stage_cols(ex.cols[g], yl, sl, p.gamma, lane);
                 uint4 out[4];
-                q_chunk_bf16(v, yi, si, yl, sl, p.gamma, p.lam2, chunk_valid(n, I, J, r, cc), out);
+                q_chunk_bf16(v, ai, syi, ex.cols[g], c2, p.lam2, chunk_valid(n, I, J, r, cc), out);
                 uint4* dst = reinterpret_cast<uint4*>(qrow + 32 * cc);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) dst[u] = out[u];
@@ -1114,15 +1118,20 @@ __global__ void __launch_bounds__(256, 4)
     }
 }
 
-// Node x's P (when `with_p`) and H slot partials := 0, the sums of all-zero
-// messages: the staged schedule's stage finalize reads the slots of tiles not
-// yet swept in a round.
+// Node x's P and residual (when `with_p`) and H slot partials := 0, the sums
+// of all-zero messages: the staged schedule's stage finalize reads the slots
+// of tiles not yet swept in a round, and under the tile-sparse option the
+// slots of dropped tiles are never written by a sweep.
 __device__ __forceinline__ void zero_slots(const Inst& p, int x, bool with_p)
 {
     float* partP = p.part;
     float* partH = partP + (size_t)p.Nt * p.n;
+    float* partR = partH + (size_t)p.Nt * p.n;
     for (int k = 0; k < p.Nt; ++k) {
-        if (with_p) partP[(size_t)k * p.n + x] = 0.f;
+        if (with_p) {
+            partP[(size_t)k * p.n + x] = 0.f;
+            partR[(size_t)k * p.n + x] = 0.f;
+        }
         partH[(size_t)k * p.n + x] = 0.f;
     }
 }
@@ -1390,9 +1399,10 @@ __global__ void k_get_pairs(Inst p, const long long* __restrict__ ij, long long 
     if (e >= cnt) return;
     const long long i = ij[2 * e], j = ij[2 * e + 1];
     const long long I = i / T, J = j / T, Nt = p.Nt;
-    const long long L = I * Nt - I * (I - 1) / 2 + (J - I);
+    long long L = I * Nt - I * (I - 1) / 2 + (J - I);
+    if (p.slab) L = p.slab[L];   // -1: a dropped tile, whose messages are 0
     const int r = (int)(i - I * T), c = (int)(j - J * T);
-    if (p.ctrl->t == 0) {
+    if (p.ctrl->t == 0 || L < 0) {
         out[e] = make_float4(0.f, 0.f, 0.f, 0.f);
     } else {
         const size_t o = (size_t)L * TT + r * T + c;

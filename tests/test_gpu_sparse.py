@@ -55,9 +55,20 @@ def test_tile_sparse_matches_oracle(n, m, gamma, tau):
     for iters in (1, 10):
         s2 = gabp.GabpSVM(p.X, p.y, p.gamma, p.C, sparse_tau=tau)
         alpha, rinf, k = s2.solve(iters, 0.0)
-        r = oracle.gabp(Q, np.ones(n), iters=iters)
+        r = oracle.gabp(Q, np.ones(n), iters=iters, keep_messages=True)
         assert _rel(s2.mean(), r.mu) <= REL
         assert np.max(np.abs(alpha.astype(np.float64) - r.alpha(p.C))) <= 1e-4 * p.C
+        # messages read back from the compacted storage: pairs of kept and of
+        # dropped tiles (the latter 0), against the oracle's messages
+        rng = np.random.default_rng(iters)
+        i = rng.integers(0, n - 1, 300)
+        j = rng.integers(i + 1, n)
+        got = gabp.svm_get_pairs(s2.h, i, j).astype(np.float64)
+        want = np.stack([r.Pin[j, i], r.Pin[i, j], r.Hin[j, i], r.Hin[i, j]], axis=1)
+        dropped = ~keep[i // 128, j // 128]
+        assert dropped.any() and (~dropped).any()
+        assert np.all(got[dropped] == 0)
+        np.testing.assert_allclose(got, want, rtol=1e-4, atol=1e-6 * np.max(np.abs(want)))
     alpha, rinf, k = s.solve(300, 1e-6)
     r = oracle.gabp(Q, np.ones(n), iters=300, tol=1e-6)
     assert abs(k - r.kstar) <= 1 and s.stats()["converged"] == 1
@@ -100,3 +111,63 @@ def test_batched_forms_reject_the_tile_sparse_option():
     with pytest.raises(gabp.GabpError) as ei:
         gabp.batch_solve([p], 10, 0.0, sparse_tau=1e-4)
     assert ei.value.status == gabp.EINVAL
+
+
+def test_tile_sparse_beyond_dense_memory():
+    """Section 6's route to large n: a clustered instance (n = 200000, m = 64,
+    6 tight clusters, gamma = 0.3, tau = 5e-5) whose dense message state alone
+    (8 n^2 bytes = 320 GB) exceeds the device, solved to ||r||_inf < 1e-6 on one
+    GPU with storage for the kept tiles only.
+
+    The oracle's one-pass tile maxima and row sums (Q not stored) give the
+    kept tiles (the maxima leave a gap of more than 20x on both sides of tau,
+    so the FP32 and FP64 decisions agree) and the margin min_i (Q_ii - R_i)
+    of the whole matrix, which is also a margin of the tile-sparse matrix
+    (same diagonal, a subset of the entries).  The answer is then within
+    Varah's bound of the tile-sparse matrix's fixed point, no mean lies in
+    the bound's band around 0 (identical support-vector sets), and the
+    oracle's rows of the tile-sparse matrix confirm the residual on samples.
+    """
+    torch = pytest.importorskip("torch")
+    n, m, gamma, tau, R_ERR = 200000, 64, 0.3, 5e-5, 4e-6
+    assert 8 * n * n > torch.cuda.get_device_properties(0).total_memory
+    p = workloads.clustered_mixture(n, m, seed=5, gamma=gamma, sigma=0.5)
+    X, y = p.X.astype(np.float64), p.y.astype(np.float64)
+    d, R, tmax = oracle.q_diag_tilemax(X, y, p.gamma, p.C)
+    nt = tmax.shape[0]
+    off = tmax[np.triu_indices(nt, 1)]
+    assert not np.any((off >= tau / 20) & (off <= tau * 20))
+    keep = np.triu(tmax > tau) | np.eye(nt, dtype=bool)
+    kept = int(keep.sum())
+    Xd, yd = torch.from_numpy(p.X).cuda(), torch.from_numpy(p.y).cuda()
+    h = gabp.svm_create(Xd, yd, p.gamma, p.C, gabp.opts_default(sparse_tau=tau, chunk=8))
+    try:
+        st = gabp.svm_get_stats(h)
+        assert st["tiles_total"] == nt * (nt + 1) // 2 and st["tiles_kept"] == kept
+        # the per-pair arrays (16 B of messages + 4 B of Q per pair) exist for
+        # the kept tiles only; the rest is O(n) and O(n^2 / 128) bookkeeping
+        assert st["device_bytes"] <= 20 * 128 * 128 * kept + 20 * nt * n + (1 << 30), st["device_bytes"]
+        alpha = torch.empty(n, dtype=torch.float32, device="cuda")
+        rinf, k = gabp.svm_solve(h, 400, 1e-6, alpha)
+        st = gabp.svm_get_stats(h)
+        mu = torch.empty(n, dtype=torch.float32, device="cuda")
+        gabp.svm_get_mean(h, mu)
+        torch.cuda.synchronize()
+    finally:
+        gabp.svm_destroy(h)
+    mu = mu.cpu().numpy().astype(np.float64)
+    assert st["converged"] == 1 and rinf < 1e-6, (rinf, k, st)
+    margin = float(np.min(d - R))
+    assert margin > 0 and st["margin"] == pytest.approx(margin, rel=1e-5)
+    b = (rinf + R_ERR) / margin
+    assert b <= 1e-4 * p.C
+    np.testing.assert_array_equal(alpha.cpu().numpy(), np.clip(mu, 0, p.C).astype(np.float32))
+    assert int((np.abs(mu) <= b).sum()) == 0
+    rng = np.random.default_rng(6)
+    for i in rng.integers(0, n, 40):
+        qi = oracle.q_row(X, y, int(i), p.gamma, p.C)
+        I = int(i) // 128
+        for J in range(nt):
+            if not keep[min(I, J), max(I, J)]:
+                qi[J * 128:(J + 1) * 128] = 0.0
+        assert abs(1.0 - qi @ mu) <= rinf + R_ERR, (int(i), 1.0 - qi @ mu)

@@ -493,3 +493,36 @@ def test_oracle_builds_and_agrees_without_openmp(tmp_path):
     d2, R2 = oracle.q_diag_all(X, y, 0.3, 2.0)
     np.testing.assert_allclose(R1, R2, rtol=1e-13)
     np.testing.assert_allclose(d1, d2, rtol=1e-13)
+
+
+def test_q_diag_tilemax_pass():
+    """The one-pass diagonal, row sums and tile maxima: R and the diagonal
+    equal the all-row pass; every tile maximum equals the largest |K_ij +
+    lambda^2| of its pairs computed from scipy's pairwise distances (strict
+    upper triangle on diagonal tiles), on a ragged size and two block edges;
+    and thresholding them reproduces build_q_tile_sparse's kept tiles."""
+    from scipy.spatial.distance import cdist
+    p = workloads.clustered_mixture(333, 6, seed=14, gamma=0.4)
+    X, y = p.X.astype(np.float64), p.y.astype(np.float64)
+    lam = 1.0 / p.n
+    A = np.abs(np.exp(-p.gamma * cdist(X, X, "sqeuclidean")) + lam * lam)
+    d0, R0 = oracle.q_diag_all(X, y, p.gamma, p.C)
+    for block in (128, 50):
+        d, R, tmax = oracle.q_diag_tilemax(X, y, p.gamma, p.C, block=block)
+        np.testing.assert_allclose(R, R0, rtol=1e-13)
+        np.testing.assert_allclose(d, d0, rtol=1e-13)
+        nt = (p.n + block - 1) // block
+        assert tmax.shape == (nt, nt)
+        for I in range(nt):
+            for J in range(nt):
+                B = A[I * block:(I + 1) * block, J * block:(J + 1) * block]
+                if I == J:
+                    B = np.triu(B, 1)
+                want = B.max() if (I <= J and B.size) else 0.0
+                assert tmax[I, J] == pytest.approx(want, rel=1e-13, abs=1e-300), (block, I, J)
+    _, keep = oracle.build_q_tile_sparse(X, y, p.gamma, p.C, tau=1e-3)
+    _, _, tmax = oracle.q_diag_tilemax(X, y, p.gamma, p.C)
+    nt = keep.shape[0]
+    for I in range(nt):
+        for J in range(I, nt):
+            assert keep[I, J] == (I == J or tmax[I, J] > 1e-3)
