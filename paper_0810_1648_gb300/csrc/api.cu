@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <climits>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -49,6 +50,27 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 }  // namespace
 
 void gabp::set_last_error(const char* msg) { g_err = msg; }
+
+int gabp::fault_mask()
+{
+    const char* v = std::getenv("GABP_FAULT");
+    if (!v || !*v) return 0;
+    int bits = 0;
+    std::string tok;
+    for (const char* c = v;; ++c) {
+        if (*c == ',' || *c == 0) {
+            if (tok == "alloc") bits |= FAULT_ALLOC;
+            else if (tok == "nan") bits |= FAULT_NAN;
+            else if (tok == "timeout") bits |= FAULT_TIMEOUT;
+            else if (!tok.empty()) return -1;
+            tok.clear();
+            if (*c == 0) break;
+        } else {
+            tok += *c;
+        }
+    }
+    return bits;
+}
 
 struct gabp_svm_s {
     int device = 0;
@@ -262,6 +284,7 @@ gabp_status ensure_pair_storage(gabp_svm_t h)
 
 gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
 {
+    NvtxRange nv("gabp.formation");
     cudaStream_t s = h->stream;
     const int64_t n = h->n, m = h->m;
     const bool dev = h->opts.ptr_mode == 1;
@@ -291,6 +314,11 @@ gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
     // labels -> device copy (validated by the staging kernel, which also sets b = 1)
     CK(cudaMemcpyAsync((void*)p.y, y, (size_t)n * sizeof(float),
                        dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    if (fault_mask() > 0 && (fault_mask() & FAULT_NAN)) {
+        // the handle's own copy of the labels (targets) gets a NaN in row n / 2
+        static const float kNaN = NAN;
+        CK(cudaMemcpyAsync((void*)(p.y + n / 2), &kNaN, sizeof(float), cudaMemcpyHostToDevice, s));
+    }
     void* tmp = nullptr;
     const void* src = X;
     if (!dev) {
@@ -423,11 +451,18 @@ gabp_status get_graph(gabp_svm_t h, int rounds, gabp_svm_s::Graph** out)
 // control block after each replay.  *out = the final control block.
 gabp_status run_rounds(gabp_svm_t h, int iters, double tol, Ctrl* out)
 {
+    NvtxRange nv("gabp.rounds");
     cudaStream_t s = h->stream;
     Inst& p = h->inst;
     launch_begin(h->d_tab, 1, iters, tol, s);
     h->prof.kernel_launches += 1;
     CK(cudaGetLastError());
+    if (iters > 0 && fault_mask() > 0 && (fault_mask() & FAULT_TIMEOUT)) {
+        // as if a bounded device wait of the first round ran out: the round's
+        // finalize stops the solve and the status reaches the host
+        static const int kTimeout = ST_ETIMEOUT;
+        CK(cudaMemcpyAsync(&p.ctrl->status, &kTimeout, sizeof(int), cudaMemcpyHostToDevice, s));
+    }
     CK(cudaMemcpyAsync(h->hctrl, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (iters > 0) {
@@ -531,6 +566,8 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     if (o.task != GABP_TASK_SVM && o.task != GABP_TASK_KRR) return fail(GABP_EINVAL, "unknown task %d", o.task);
     if (o.stages < 0 || o.stages > kMaxStages) return fail(GABP_EINVAL, "stages must be in [0, %d]", kMaxStages);
     if (!(o.sparse_tau >= 0) || !std::isfinite(o.sparse_tau)) return fail(GABP_EINVAL, "sparse_tau must be >= 0");
+    const int faults = fault_mask();
+    if (faults < 0) return fail(GABP_EINVAL, "GABP_FAULT holds an unknown token (known: alloc, nan, timeout)");
 
     int dev = 0, ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -571,6 +608,10 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     e = prepare_sweep();
     if (e == cudaSuccess && o.q_mode == GABP_Q_RECOMPUTE) e = prepare_sweep_rc();
     if (e != cudaSuccess) { destroy_all(h); return fail(GABP_ECUDA, "sweep kernel setup: %s", cudaGetErrorString(e)); }
+    if (faults & FAULT_ALLOC) {
+        destroy_all(h);
+        return fail(GABP_ENOMEM, "injected device allocation failure (GABP_FAULT=alloc)");
+    }
     e = cudaMalloc(&h->pool, pl.total);
     if (e != cudaSuccess) { destroy_all(h); return fail(GABP_ENOMEM, "cudaMalloc(%zu): %s", pl.total, cudaGetErrorString(e)); }
     h->pool_bytes = pl.total;
@@ -719,6 +760,7 @@ gabp_status gabp_svm_solve(gabp_svm_t h, int32_t iters, double tol, float* alpha
     op.sv_threshold = (float)h->opts.sv_threshold;
     const int nblk = (int)((h->n + 31) / 32);
     auto final_pass = [&](const StopOp& o) -> gabp_status {
+        NvtxRange nv("gabp.final_pass");
         CK(cudaMemcpyAsync(h->d_ops, &o, sizeof(StopOp), cudaMemcpyHostToDevice, s));
         if (o.acc) launch_axpy_list(h->d_tab, h->d_ops, h->nbl, nblk, s);
         launch_final(h->d_tab, h->d_ops, h->work, h->nlive, h->nbl, nblk, h->d_members, 1, nullptr,
@@ -847,6 +889,7 @@ gabp_status gabp_svm_decision(gabp_svm_t h, const void* Xtest, int64_t t, float*
     if (t < 0 || (t > 0 && (!Xtest || !out))) return fail(GABP_EINVAL, "bad test set");
     if (t == 0) return GABP_OK;
     if (t > ((int64_t)1 << 30)) return fail(GABP_EINVAL, "t too large");
+    NvtxRange nv("gabp.decision");
     cudaStream_t s = h->stream;
     const bool dev = h->opts.ptr_mode == 1, f64 = h->opts.x_dtype == 1;
     const int64_t m = h->m;

@@ -508,6 +508,8 @@ class Engine {
     // Instance memory of a known set in one allocation (carved by add()).
     gabp_status reserve(size_t bytes)
     {
+        if (fault_mask() > 0 && (fault_mask() & FAULT_ALLOC))
+            return fail(GABP_ENOMEM, "injected device allocation failure (GABP_FAULT=alloc)");
         EK(cudaMallocAsync((void**)&arena, bytes, side));
         arena_size = bytes;
         arena_off = 0;
@@ -594,6 +596,11 @@ class Engine {
             b = arena + arena_off;
             arena_off += pl.total;
         } else {
+            if (fault_mask() > 0 && (fault_mask() & FAULT_ALLOC)) {
+                M = Member{};
+                bytes_in_use -= pl.total;
+                return fail(GABP_ENOMEM, "injected device allocation failure (GABP_FAULT=alloc)");
+            }
             EK(cudaMallocAsync(&M.mem, pl.total, s));
             b = static_cast<char*>(M.mem);
         }
@@ -685,6 +692,7 @@ class Engine {
     gabp_status form_pending()
     {
         if (pending.empty()) return GABP_OK;
+        NvtxRange nv("gabp.batch.formation");
         cudaStream_t s = side;
         // Instances over the same features (a parameter grid) are chained
         // behind the first: the FP32 and the tensor-core Gram tiles are
@@ -853,6 +861,7 @@ class Engine {
     // block read back; launch_chunk returns at once, wait_chunk waits.
     gabp_status launch_chunk(int rounds)
     {
+        NvtxRange nv("gabp.batch.launch_rounds");
         if (gabp_status st = take_rejoin()) return st;
         if (gabp_status st = rebuild()) return st;
         if (live_tiles > 0) {
@@ -866,6 +875,7 @@ class Engine {
     }
     gabp_status wait_chunk()
     {
+        NvtxRange nv("gabp.batch.wait_rounds");
         EK(cudaStreamSynchronize(stream));
         return GABP_OK;
     }
@@ -930,6 +940,7 @@ class Engine {
 
     gabp_status stop_begin(cudaStream_t ss, int* running)
     {
+        NvtxRange nv("gabp.batch.stop_begin");
         int run = 0;
         sb.stopped.clear();
         sb.ref.clear();
@@ -997,6 +1008,7 @@ class Engine {
     gabp_status stop_end(cudaStream_t ss, std::vector<int>* finished)
     {
         if (sb.stopped.empty()) return GABP_OK;
+        NvtxRange nv("gabp.batch.stop_end");
         EK(cudaStreamSynchronize(ss));
         // 2. next correction pass, or done
         std::vector<int2> rnb, blist;
@@ -1084,6 +1096,7 @@ class Engine {
     // schedules for a few rounds of the real set (then restarts it).
     gabp_status autotune(int iters)
     {
+        NvtxRange nv("gabp.batch.autotune");
         long long tiles = 0;
         int members = 0;
         for (auto& M : mem)
@@ -1162,6 +1175,10 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
     }
     if (iters < 0 || std::isnan(tol)) {
         set_last_error("gabp_batch_solve: bad iters or tol");
+        return GABP_EINVAL;
+    }
+    if (fault_mask() < 0) {
+        set_last_error("GABP_FAULT holds an unknown token (known: alloc, nan, timeout)");
         return GABP_EINVAL;
     }
     gabp_svm_opts o;
@@ -1443,8 +1460,19 @@ gabp_status gabp_server_step(gabp_server_t s, int32_t* active, int32_t* queued, 
         const int slot = E.free_slot();
         if (slot < 0 || E.bytes_in_use + need > s->budget) break;
         const int64_t t = front.first;
-        if (gabp_status st = E.add(slot, front.second, s->outs[t].first, s->outs[t].second, s->cfg.opts.ptr_mode))
-            return st;
+        if (gabp_status st = E.add(slot, front.second, s->outs[t].first, s->outs[t].second, s->cfg.opts.ptr_mode)) {
+            if (st != GABP_ENOMEM) return st;
+            // the instance's memory could not be had: the request completes with
+            // GABP_ENOMEM and the server goes on with the others
+            gabp_result r{};
+            r.status = GABP_ENOMEM;
+            r.alpha = s->outs[t].first;
+            r.mu = s->outs[t].second;
+            s->done[t] = r;
+            s->fresh.push_back(t);
+            s->queue.pop_front();
+            continue;
+        }
         Member& M = E.mem[(size_t)slot];
         M.ticket = t;
         M.iters = s->cfg.iters;

@@ -24,6 +24,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 namespace gabp {
@@ -244,6 +245,24 @@ cudaError_t launch_selftest_rcp(const float* d, float* out, int cnt, cudaStream_
 cudaError_t launch_selftest_wait(unsigned long long limit_ns, int* status_dev, cudaStream_t s);
 // Sets the thread-local message returned by gabp_last_error().
 void set_last_error(const char* msg);
+// Host-side fault injection for tests of the failure paths: the environment
+// variable GABP_FAULT holds comma-separated tokens, read at each public call:
+//   alloc    the call's device allocation fails (create, batch, server admission)
+//   nan      a non-finite label or target reaches the staging checks (create, refit)
+//   timeout  the device reports a bounded wait that ran out during the next rounds
+// Returns the FAULT_* bits, or -1 for an unknown token.
+enum FaultBits { FAULT_ALLOC = 1, FAULT_NAN = 2, FAULT_TIMEOUT = 4 };
+int fault_mask();
+
+// NVTX range over a host-side phase (formation, rounds, final pass,
+// refinement, decision, batch and server phases), shown by profilers that
+// record NVTX; without one attached a push/pop pair costs a few nanoseconds.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---- small device helpers --------------------------------------------------
 __device__ __forceinline__ float warp_sum(float v)

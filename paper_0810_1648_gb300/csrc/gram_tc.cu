@@ -248,16 +248,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 __nv_bfloat16* qrow = static_cast<__nv_bfloat16*>(p.qstore) + (size_t)w.w * TT + (size_t)r * T;
 #pragma unroll 1
                 for (int cc = 2 * half; cc < 2 * half + 2; ++cc) {
-                    float v[32];
-                    tmem_ld32(tbase + (uint32_t)acc * T + ((uint32_t)(32 * g) << 16) + (uint32_t)(32 * cc), v);
                     const int jl = J * T + 32 * cc + lane;
                     const float yl = jl < n ? p.y[jl] : 0.f, sl = jl < n ? sqb[jl] : 0.f;
                     stage_cols(cs, yl, sl, p.gamma, lane);
-                    uint4 out[4];
-                    q_chunk_bf16(v, ai, syi, cs, c2, p.lam2, chunk_valid(n, I, J, r, cc), out);
+                    const uint32_t valid = chunk_valid(n, I, J, r, cc);
                     uint4* dst = reinterpret_cast<uint4*>(qrow + 32 * cc);
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) dst[u] = out[u];
+                    for (int h = 0; h < 2; ++h) {
+                        float v[16];
+                        tmem_ld16(tbase + (uint32_t)acc * T + ((uint32_t)(32 * g) << 16) + (uint32_t)(32 * cc + 16 * h),
+                                  v);
+                        uint4 out[2];
+                        q_half_bf16(v, 16 * h, ai, syi, cs, c2, p.lam2, valid, out);
+                        dst[2 * h] = out[0];
+                        dst[2 * h + 1] = out[1];
+                    }
                 }
                 k = p.form_next - 1;
             }

@@ -53,20 +53,21 @@ __device__ __forceinline__ float ex2_approx(float t)
     return r;
 }
 
-// out = BF16 q_ij for the 32 columns of one row chunk (0 where `valid` has no
-// bit): q_ij = y_i y_j (exp(-gamma d2) + lambda^2), d2 = max(0, ||x_i||^2 +
-// ||x_j||^2 - 2 g_ij) with g the Gram values of the chunk, evaluated as
-// 2^min(0, a_i + b_j + c2 g_ij) with a_i = -gamma log2(e) ||x_i||^2, b_j from
-// the staged column constants and c2 = 2 gamma log2(e); the label product
-// y_i y_j = +-1 is applied as a sign flip (sign bits syi ^ sy_j).
-__device__ __forceinline__ void q_chunk_bf16(const float (&g)[32], float ai, uint32_t syi, const ColChunk& cs,
-                                             float c2, float lam2, uint32_t valid, uint4 (&out)[4])
+// out = BF16 q_ij for the 16 columns h0 .. h0 + 15 (h0 = 0 or 16) of one row
+// chunk (0 where `valid` has no bit): q_ij = y_i y_j (exp(-gamma d2) +
+// lambda^2), d2 = max(0, ||x_i||^2 + ||x_j||^2 - 2 g_ij) with g the Gram
+// values of those columns, evaluated as 2^min(0, a_i + b_j + c2 g_ij) with
+// a_i = -gamma log2(e) ||x_i||^2, b_j from the staged column constants and
+// c2 = 2 gamma log2(e); the label product y_i y_j = +-1 is applied as a sign
+// flip (sign bits syi ^ sy_j).
+__device__ __forceinline__ void q_half_bf16(const float (&g)[16], int h0, float ai, uint32_t syi, const ColChunk& cs,
+                                            float c2, float lam2, uint32_t valid, uint4 (&out)[2])
 {
-    uint32_t w[16];
+    uint32_t w[8];
 #pragma unroll
-    for (int c = 0; c < 32; c += 4) {
-        const float4 b4 = *reinterpret_cast<const float4*>(&cs.b[c]);
-        const uint4 s4 = *reinterpret_cast<const uint4*>(&cs.sy[c]);
+    for (int c = 0; c < 16; c += 4) {
+        const float4 b4 = *reinterpret_cast<const float4*>(&cs.b[h0 + c]);
+        const uint4 s4 = *reinterpret_cast<const uint4*>(&cs.sy[h0 + c]);
         const float bj[4] = {b4.x, b4.y, b4.z, b4.w};
         const uint32_t sj[4] = {s4.x, s4.y, s4.z, s4.w};
         float q4[4];
@@ -75,15 +76,15 @@ __device__ __forceinline__ void q_chunk_bf16(const float (&g)[32], float ai, uin
             const float t = fminf(fmaf(c2, g[c + u], bj[u]) + ai, 0.f);
             const float q = ex2_approx(t) + lam2;
             const float qs = __uint_as_float(__float_as_uint(q) ^ syi ^ sj[u]);
-            q4[u] = ((valid >> (c + u)) & 1u) ? qs : 0.f;
+            q4[u] = ((valid >> (h0 + c + u)) & 1u) ? qs : 0.f;
         }
-        __nv_bfloat162 h0 = __floats2bfloat162_rn(q4[0], q4[1]);
-        __nv_bfloat162 h1 = __floats2bfloat162_rn(q4[2], q4[3]);
-        w[c / 2] = *reinterpret_cast<const uint32_t*>(&h0);
-        w[c / 2 + 1] = *reinterpret_cast<const uint32_t*>(&h1);
+        __nv_bfloat162 p0 = __floats2bfloat162_rn(q4[0], q4[1]);
+        __nv_bfloat162 p1 = __floats2bfloat162_rn(q4[2], q4[3]);
+        w[c / 2] = *reinterpret_cast<const uint32_t*>(&p0);
+        w[c / 2 + 1] = *reinterpret_cast<const uint32_t*>(&p1);
     }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) out[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+    out[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    out[1] = make_uint4(w[4], w[5], w[6], w[7]);
 }
 
 }  // namespace gabp

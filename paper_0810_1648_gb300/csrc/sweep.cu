@@ -37,7 +37,9 @@ namespace gabp {
 
 namespace {
 
-__device__ __forceinline__ void consumer_bar() { asm volatile("bar.sync 1, %0;" ::"n"(NTHREADS) : "memory"); }
+// Named barrier of the CW consumer warps.
+template <int CW>
+__device__ __forceinline__ void consumer_bar() { asm volatile("bar.sync 1, %0;" ::"n"(CW * 32) : "memory"); }
 
 
 // ---- pair sweep -----------------------------------------------------------
@@ -61,9 +63,11 @@ __device__ __forceinline__ void consumer_bar() { asm volatile("bar.sync 1, %0;" 
 //                 turn the Gram rows into BF16 Q values in a double-buffered
 //                 shared-memory Q tile, which the consumers read in place of
 //                 a stored tile (bitwise the same values as the BF16 store).
-// Rows per ring stage: MSG::RPW per consumer warp (rc<MSG>() in total).
+// Rows per ring stage (16), split over the consumer warps: two per warp
+// with 8 consumer warps (stored Q), one per warp with 16 (recompute).
+constexpr int RC_ROWS = 16;
 template <class MSG>
-__host__ __device__ constexpr int rc() { return NWARPS * MSG::RPW; }
+__host__ __device__ constexpr int rc() { return RC_ROWS; }
 constexpr int STAGES = 4;                     // barrier slots of the stage ring (upper bound)
 // Ring stages used by a message type (both keep ~80 KB of rows in flight).
 template <class MSG>
@@ -81,7 +85,6 @@ struct MsgF32 {
     // a lane's pairs of a row: columns 2 lane + {0, 1} and 64 + 2 lane + {0, 1}
     // (each access of the warp is one contiguous 512-byte span)
     static constexpr int G = 2;
-    static constexpr int RPW = 2;      // rows per consumer warp and ring stage
     static constexpr int NSTAGE = 2;   // ring stages of 16 rows (40 KB with FP32 Q)
     // diagonal and edge tiles: only the owned pairs of each row are copied
     // (one copy per row; the form is bandwidth bound, so bytes count)
@@ -114,7 +117,6 @@ struct MsgBF16 {
     // a lane's pairs of a row: columns 4 lane + {0 .. 3} (16 bytes; each
     // access of the warp is one contiguous 512-byte span)
     static constexpr int G = 4;
-    static constexpr int RPW = 2;      // rows per consumer warp and ring stage (halves the per-row overhead)
     static constexpr int NSTAGE = 4;   // ring stages of 16 rows (20 KB with BF16 Q)
     // diagonal and edge tiles also move 16 whole rows per copy (the unowned
     // entries are masked by the consumers): sixteen times fewer bulk copies
@@ -153,26 +155,30 @@ struct TileInfo {
     int t, zero_h, frozen, end;
 };
 
+// Shared state of the producer and the CW consumer warps.
+template <int CW>
 struct SweepTail {
+    static constexpr int kCW = CW;
     unsigned long long full[STAGES], empty[STAGES];
     unsigned long long tfull[2], tempty[2];
     int cabort;                        // consumer-side stop, decided at a tile barrier
     TileInfo info[2];
     alignas(16) float agg[2][6][T];    // per slot: row block {Ptilde, htilde, mu}, column block {same}
-    float cp[NWARPS][T], ch[NWARPS][T], cr[NWARPS][T];
+    float cp[CW][T], ch[CW][T], cr[CW][T];
     float rp[T], rh[T], rr[T];
 };
 
 // Barriers and flags of the stage ring and the tile slots (one thread).
-__device__ __forceinline__ void init_tail(SweepTail& sm)
+template <int CW>
+__device__ __forceinline__ void init_tail(SweepTail<CW>& sm)
 {
     for (int s = 0; s < STAGES; ++s) {
         mbar_init(&sm.full[s], 1);
-        mbar_init(&sm.empty[s], NWARPS);
+        mbar_init(&sm.empty[s], CW);
     }
     for (int s = 0; s < 2; ++s) {
         mbar_init(&sm.tfull[s], 1);
-        mbar_init(&sm.tempty[s], NWARPS);
+        mbar_init(&sm.tempty[s], CW);
     }
     sm.cabort = 0;
 }
@@ -189,7 +195,7 @@ __host__ __device__ constexpr size_t stage_bytes() { return state_chunk<MSG>() +
 template <typename QT, class MSG>
 __host__ __device__ constexpr size_t sweep_smem_bytes()
 {
-    return 128 + stages<MSG>() * stage_bytes<QT, MSG>() + sizeof(SweepTail);
+    return 128 + stages<MSG>() * stage_bytes<QT, MSG>() + sizeof(SweepTail<NWARPS>);
 }
 
 // Producer (one warp).  For every tile it streams: publishes the tile's
@@ -197,9 +203,9 @@ __host__ __device__ constexpr size_t sweep_smem_bytes()
 // then streams the message (and stored Q) rows through the stage ring.
 // Interior tiles move rc<MSG>() whole rows per copy; diagonal and edge tiles copy each
 // row's needed span, one row per lane.  QT = void: messages only.
-template <typename QT, class MSG, size_t SB>
+template <typename QT, class MSG, size_t SB, class Tail>
 __device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, const int4* __restrict__ work,
-                                               long long ntiles, SweepTail& sm, unsigned char* ring,
+                                               long long ntiles, Tail& sm, unsigned char* ring,
                                                volatile int* abort_flag, int lane, int stage_no)
 {
     constexpr size_t QB = QBytes<QT>::v;
@@ -392,6 +398,25 @@ __device__ __forceinline__ float reduce_scatter8(float a0, float a1, float a2, f
     return v;
 }
 
+// Sums the four values {a0, a1, a2, 0} over the warp in a fixed order:
+// afterwards every lane of the group (lane / 8) % 4 = k holds the total of
+// value k (six shuffles for one row).
+__device__ __forceinline__ float reduce_scatter4(float a0, float a1, float a2, int lane)
+{
+    const float x[4] = {a0, a1, a2, 0.f};
+    const bool hi = (lane & 16) != 0;
+    float y[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+        y[k] = (hi ? x[k + 2] : x[k]) + __shfl_xor_sync(0xffffffffu, hi ? x[k] : x[k + 2], 16);
+    const bool b8 = (lane & 8) != 0;
+    float v = (b8 ? y[1] : y[0]) + __shfl_xor_sync(0xffffffffu, b8 ? y[0] : y[1], 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v;
+}
+
 // Per-tile column values a consumer lane needs for its row updates.
 struct ColVals {
     float P[4], H[4], M[4];      // aggregates of the lane's four columns
@@ -516,8 +541,8 @@ struct TileCtx {
 // sm.rp/rh/rr and its column partials in sm.cp (not when FROZEN), sm.ch and
 // sm.cr.  Specialised per tile kind so that a frozen-P tile keeps neither the
 // column P values nor their sums in registers.
-template <bool FULL, bool FROZEN, int SB, class MSG, class QSrc>
-__device__ __forceinline__ void consume_tile(const QSrc& qsrc, SweepTail& sm, const unsigned char* ring,
+template <int CW, bool FULL, bool FROZEN, int SB, class MSG, class QSrc>
+__device__ __forceinline__ void consume_tile(const QSrc& qsrc, SweepTail<CW>& sm, const unsigned char* ring,
                                              const TileCtx& tc, typename MSG::T2* __restrict__ gp,
                                              typename MSG::T2* __restrict__ gh, int& stage, uint32_t& phase,
                                              bool& abort, bool& bad, bool& changed)
@@ -530,7 +555,8 @@ __device__ __forceinline__ void consume_tile(const QSrc& qsrc, SweepTail& sm, co
     if (!FROZEN) ld4<G>(tc.ag[3], lane, cv.P);
 #pragma unroll
     for (int k = 0; k < 4; ++k) cv.aP[k] = cv.aH[k] = cv.aR[k] = 0.f;
-    constexpr int RC = rc<MSG>(), RPW = MSG::RPW;
+    constexpr int RC = rc<MSG>(), RPW = RC / CW;
+    static_assert(RPW * CW == RC && (RPW == 1 || RPW == 2), "one or two rows per consumer warp and stage");
     const int nch = (rows + RC - 1) / RC;
 #pragma unroll 1
     for (int ch = 0; ch < nch; ++ch) {
@@ -538,11 +564,11 @@ __device__ __forceinline__ void consume_tile(const QSrc& qsrc, SweepTail& sm, co
             abort = true;
             if (lane == 0) record_error(tc.ctrl, ST_ETIMEOUT, tc.L);
         }
-        // this warp's rows of the stage: cw, cw + NWARPS, ...
+        // this warp's rows of the stage: cw, cw + CW, ...
         float rs[RPW][3];
 #pragma unroll
         for (int u = 0; u < RPW; ++u) {
-            const int lr = cw + NWARPS * u, r = ch * RC + lr;
+            const int lr = cw + CW * u, r = ch * RC + lr;
             rs[u][0] = rs[u][1] = rs[u][2] = 0.f;
             if (!abort && r < rows) {
                 const unsigned char* S = ring + (size_t)stage * SB;
@@ -554,12 +580,16 @@ __device__ __forceinline__ void consume_tile(const QSrc& qsrc, SweepTail& sm, co
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.empty[stage]);
         if (++stage == stages<MSG>()) { stage = 0; phase ^= 1u; }
-        // row sums {P, H, R} of the warp's two rows over the warp
-        static_assert(RPW == 2, "two rows per consumer warp and ring stage");
-        {
-            const float v = reduce_scatter8(rs[0][0], rs[0][1], rs[0][2], rs[1][0], rs[1][1], rs[1][2], lane);
-            const int qi = (lane >> 2) & 7, qv = qi & 3, r = ch * RC + cw + NWARPS * (qi >> 2);
+        // row sums {P, H, R} of the warp's rows over the warp
+        if constexpr (RPW == 2) {
+            const float v = reduce_scatter8(rs[0][0], rs[0][1], rs[0][2], rs[RPW - 1][0], rs[RPW - 1][1],
+                                            rs[RPW - 1][2], lane);
+            const int qi = (lane >> 2) & 7, qv = qi & 3, r = ch * RC + cw + CW * (qi >> 2);
             if ((lane & 3) == 0 && qv < 3 && r < rows) (qv == 0 ? sm.rp : (qv == 1 ? sm.rh : sm.rr))[r] = v;
+        } else {
+            const float v = reduce_scatter4(rs[0][0], rs[0][1], rs[0][2], lane);
+            const int qv = (lane >> 3) & 3, r = ch * RC + cw;
+            if ((lane & 7) == 0 && qv < 3 && r < rows) (qv == 0 ? sm.rp : (qv == 1 ? sm.rh : sm.rr))[r] = v;
         }
     }
     if (!FROZEN) st4<G>(sm.cp[cw], lane, cv.aP);
@@ -569,9 +599,9 @@ __device__ __forceinline__ void consume_tile(const QSrc& qsrc, SweepTail& sm, co
 
 // Consumers (256 threads, ctid = 0..255, consumer warp cw = ctid / 32).
 // QSrc supplies q for a pair and the per-tile hand-shake of a recomputed Q tile.
-template <size_t SB, class MSG, class QSrc>
+template <int CW, size_t SB, class MSG, class QSrc>
 __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, const int4* __restrict__ work,
-                                                long long ntiles, SweepTail& sm, const unsigned char* ring,
+                                                long long ntiles, SweepTail<CW>& sm, const unsigned char* ring,
                                                 int ctid, QSrc& qsrc)
 {
     const int cw = ctid >> 5, lane = ctid & 31;
@@ -587,7 +617,7 @@ __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, co
             sm.cabort = 1;
             if (blockIdx.x < ntiles) record_error(tab[work[blockIdx.x].x].ctrl, ST_ETIMEOUT, -1);
         }
-        consumer_bar();   // also: the previous tile's sums are read out
+        consumer_bar<CW>();   // also: the previous tile's sums are read out
         if (*(volatile int*)&sm.cabort) break;
         const TileInfo ti = sm.info[slot];
         if (ti.end) break;
@@ -615,25 +645,25 @@ __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, co
         typename MSG::T2* gh = static_cast<typename MSG::T2*>(ti.Hst);
         TileCtx tc{cw, lane, rows, cols, diag, it, zero, zero_h, ctrl, L, sm.agg[slot]};
         if (full) {
-            if (frozen) consume_tile<true, true, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
-            else consume_tile<true, false, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
+            if (frozen) consume_tile<CW, true, true, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
+            else consume_tile<CW, true, false, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
         } else {
-            if (frozen) consume_tile<false, true, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
-            else consume_tile<false, false, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
+            if (frozen) consume_tile<CW, false, true, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
+            else consume_tile<CW, false, false, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.tempty[slot]);   // tile slot free for the producer
         if (++slot == 2) { slot = 0; tph ^= 1u; }
         __syncwarp();
         qsrc.tile_end(it, lane);
-        consumer_bar();
+        consumer_bar<CW>();
         // With frozen P the P sums are unchanged from the previous round and
         // the finalize keeps Ptilde; the P slots are not written.
         if (diag) {
             if (ctid < rows) {
                 float P = sm.rp[ctid], H = sm.rh[ctid], R = sm.rr[ctid];
 #pragma unroll
-                for (int w = 0; w < NWARPS; ++w) { P += sm.cp[w][ctid]; H += sm.ch[w][ctid]; R += sm.cr[w][ctid]; }
+                for (int w = 0; w < CW; ++w) { P += sm.cp[w][ctid]; H += sm.ch[w][ctid]; R += sm.cr[w][ctid]; }
                 const size_t o = (size_t)I * n + I * T + ctid;
                 if (!frozen) partP[o] = P;
                 partH[o] = H; partR[o] = R;
@@ -649,7 +679,7 @@ __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, co
             if (c < cols) {
                 float P = 0.f, H = 0.f, R = 0.f;
 #pragma unroll
-                for (int w = 0; w < NWARPS; ++w) { P += sm.cp[w][c]; H += sm.ch[w][c]; R += sm.cr[w][c]; }
+                for (int w = 0; w < CW; ++w) { P += sm.cp[w][c]; H += sm.ch[w][c]; R += sm.cr[w][c]; }
                 const size_t o = (size_t)I * n + J * T + c;
                 if (!frozen) partP[o] = P;
                 partH[o] = H; partR[o] = R;
@@ -691,7 +721,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, sweep_ctas<MSG>())
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* ring = align_smem(smem_raw, 128);
-    SweepTail& sm = *reinterpret_cast<SweepTail*>(ring + stages<MSG>() * SB);
+    SweepTail<NWARPS>& sm = *reinterpret_cast<SweepTail<NWARPS>*>(ring + stages<MSG>() * SB);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
@@ -704,12 +734,17 @@ __global__ void __launch_bounds__(SWEEP_THREADS, sweep_ctas<MSG>())
         return;
     }
     StoredQ<QT, MSG> qsrc;
-    sweep_consumers<SB, MSG>(tab, work, ntiles, sm, ring, tid, qsrc);
+    sweep_consumers<NWARPS, SB, MSG>(tab, work, ntiles, sm, ring, tid, qsrc);
 }
 
 // ---- fused recompute ------------------------------------------------------
 constexpr int RC_XSTAGES = 2;
-constexpr int RC_THREADS = 15 * 32;     // 3 role warps + 4 epilogue + 8 consumers
+// Consumer warps (two rows of each 16-row stage each).  Sixteen consumers
+// (one row each, 88 registers a thread) measured slower: 0.71 / 0.51 of the
+// copy peak against 0.77 / 0.53 with eight.  Eight also keep the summation
+// order of the stored-Q sweep, so recomputed and stored forms agree bitwise.
+constexpr int RC_CW = 8;
+constexpr int RC_THREADS = (7 + RC_CW) * 32;   // 3 role warps + 4 epilogue + 8 consumers
 constexpr uint32_t RC_TMEM_COLS = 256;
 constexpr size_t RC_QTILE = (size_t)TT * sizeof(__nv_bfloat16);   // 32 KB
 
@@ -726,7 +761,7 @@ struct RcExtra {
 template <class MSG>
 __host__ __device__ constexpr size_t rc_smem_bytes()
 {
-    return 1024 + stages<MSG>() * state_chunk<MSG>() + RC_XSTAGES * 2 * BLK_BYTES + 2 * RC_QTILE + sizeof(SweepTail) +
+    return 1024 + stages<MSG>() * state_chunk<MSG>() + RC_XSTAGES * 2 * BLK_BYTES + 2 * RC_QTILE + sizeof(SweepTail<RC_CW>) +
            sizeof(RcExtra);
 }
 
@@ -761,8 +796,8 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
     unsigned char* ring = align_smem(smem_raw, 1024);
     unsigned char* xops = ring + stages<MSG>() * state_chunk<MSG>();                // [2][A, B]
     __nv_bfloat16* qtile = reinterpret_cast<__nv_bfloat16*>(xops + RC_XSTAGES * 2 * BLK_BYTES);
-    SweepTail& sm = *reinterpret_cast<SweepTail*>(reinterpret_cast<unsigned char*>(qtile) + 2 * RC_QTILE);
-    RcExtra& ex = *reinterpret_cast<RcExtra*>(reinterpret_cast<unsigned char*>(&sm) + sizeof(SweepTail));
+    SweepTail<RC_CW>& sm = *reinterpret_cast<SweepTail<RC_CW>*>(reinterpret_cast<unsigned char*>(qtile) + 2 * RC_QTILE);
+    RcExtra& ex = *reinterpret_cast<RcExtra*>(reinterpret_cast<unsigned char*>(&sm) + sizeof(SweepTail<RC_CW>));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
@@ -772,7 +807,7 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
             mbar_init(&ex.accfull[b], 1);
             mbar_init(&ex.accempty[b], 4);
             mbar_init(&ex.qfull[b], 4);
-            mbar_init(&ex.qempty[b], NWARPS);
+            mbar_init(&ex.qempty[b], RC_CW);
         }
         mbar_init(&ex.drain, 1);
         ex.abort = 0;
@@ -888,16 +923,20 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
             __nv_bfloat16* qrow = qtile + (size_t)acc * TT + (size_t)r * T;
 #pragma unroll 1
             for (int cc = 0; cc < T / 32; ++cc) {
-                float v[32];
-                tmem_ld32(tbase + (uint32_t)acc * T + ((uint32_t)(32 * g) << 16) + (uint32_t)(32 * cc), v);
                 const int jl = J * T + 32 * cc + lane;
                 const float yl = jl < n ? p.y[jl] : 0.f, sl = jl < n ? p.sqb[jl] : 0.f;
                 stage_cols(ex.cols[g], yl, sl, p.gamma, lane);
-                uint4 out[4];
-                q_chunk_bf16(v, ai, syi, ex.cols[g], c2, p.lam2, chunk_valid(n, I, J, r, cc), out);
+                const uint32_t valid = chunk_valid(n, I, J, r, cc);
                 uint4* dst = reinterpret_cast<uint4*>(qrow + 32 * cc);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) dst[u] = out[u];
+                for (int h = 0; h < 2; ++h) {
+                    float v[16];
+                    tmem_ld16(tbase + (uint32_t)acc * T + ((uint32_t)(32 * g) << 16) + (uint32_t)(32 * cc + 16 * h), v);
+                    uint4 out[2];
+                    q_half_bf16(v, 16 * h, ai, syi, ex.cols[g], c2, p.lam2, valid, out);
+                    dst[2 * h] = out[0];
+                    dst[2 * h + 1] = out[1];
+                }
             }
             tc_fence_before();
             __syncwarp();
@@ -909,7 +948,7 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
         }
     } else {
         RecomputedQ qsrc{qtile, &ex};
-        sweep_consumers<state_chunk<MSG>(), MSG>(tab, work, ntiles, sm, ring, tid - 7 * 32, qsrc);
+        sweep_consumers<RC_CW, state_chunk<MSG>(), MSG>(tab, work, ntiles, sm, ring, tid - 7 * 32, qsrc);
     }
     tc_fence_before();
     __syncthreads();

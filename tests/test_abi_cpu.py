@@ -84,3 +84,34 @@ def test_noalloc_binding_rejects_bad_arguments():
     with pytest.raises(gabp.GabpError) as ei:
         gabp.decision_noalloc(np.zeros((8, 3), np.float32), y, a, Xt, 0.5, 0.0, out)
     assert ei.value.status == gabp.EINVAL
+
+
+def test_unknown_fault_token_rejected_before_device_work(lib, monkeypatch):
+    """GABP_FAULT (host-side fault injection) is parsed before any device
+    call: an unknown token is GABP_EINVAL, with or without a GPU."""
+    X = np.zeros((4, 3), np.float32)
+    y = np.array([1, -1, 1, -1], np.float32)
+    h = ctypes.c_void_p()
+    V = ctypes.c_void_p
+    monkeypatch.setenv("GABP_FAULT", "alloc,bogus")
+    assert lib.gabp_svm_create(V(X.ctypes.data), V(y.ctypes.data), 4, 3, 1.0, 1.0, ctypes.byref(h)) == gabp.EINVAL
+    assert b"GABP_FAULT" in lib.gabp_last_error()
+    pr = (gabp.Problem * 1)(gabp.Problem(X.ctypes.data, y.ctypes.data, 4, 3, 1.0, 1.0))
+    res = (gabp.Result * 1)()
+    assert lib.gabp_batch_solve(pr, 1, None, 5, 0.0, res) == gabp.EINVAL
+    assert b"GABP_FAULT" in lib.gabp_last_error()
+
+
+def test_known_fault_tokens_do_not_mask_a_missing_device(lib, monkeypatch):
+    """With a valid GABP_FAULT and no GPU, create still fails loudly with
+    GABP_ECUDA (the injection sits behind the device checks)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    X = np.random.default_rng(0).standard_normal((8, 3)).astype(np.float32)
+    y = np.array([1, -1] * 4, np.float32)
+    for tok in ("alloc", "nan", "timeout", "alloc,nan"):
+        monkeypatch.setenv("GABP_FAULT", tok)
+        with pytest.raises(gabp.GabpError) as ei:
+            gabp.svm_create(X, y, 0.5, 1.0)
+        assert ei.value.status == gabp.ECUDA, tok

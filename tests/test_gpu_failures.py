@@ -31,3 +31,84 @@ def test_sweep_reciprocal_within_one_ulp_of_ieee_division():
     ulp = np.abs(got.view(np.int32).astype(np.int64) - want.view(np.int32).astype(np.int64))
     assert ulp.max() <= 1, ulp.max()
     assert np.mean(ulp == 0) > 0.9
+
+
+def _free_bytes():
+    import torch
+    torch.cuda.synchronize()
+    return torch.cuda.mem_get_info()[0]
+
+
+def test_over_budget_create_returns_enomem_before_any_device_work():
+    """A dense instance whose plan (8 n^2 bytes of messages + 2 n^2 of FP32 Q
+    at n = 200000: 400 GB) exceeds the device: GABP_ENOMEM from the budget
+    check, no handle, and the device's free memory unchanged."""
+    p = workloads.mixture(200000, 4, seed=1)
+    free0 = _free_bytes()
+    with pytest.raises(gabp.GabpError) as ei:
+        gabp.svm_create(p.X, p.y, p.gamma, p.C)
+    assert ei.value.status == gabp.ENOMEM and "GB of device memory" in ei.value.message
+    assert abs(_free_bytes() - free0) < (64 << 20)
+
+
+def test_injected_alloc_failure(monkeypatch):
+    """GABP_FAULT=alloc: create and the batch solve return GABP_ENOMEM with
+    nothing left allocated; the server completes the request with
+    GABP_ENOMEM and keeps serving; without the fault everything runs."""
+    p = workloads.mixture(300, 6, seed=7)
+    free0 = _free_bytes()
+    monkeypatch.setenv("GABP_FAULT", "alloc")
+    with pytest.raises(gabp.GabpError) as ei:
+        gabp.svm_create(p.X, p.y, p.gamma, p.C)
+    assert ei.value.status == gabp.ENOMEM and "injected" in ei.value.message
+    with pytest.raises(gabp.GabpError) as ei:
+        gabp.batch_solve([p, p], 10, 0.0)
+    assert ei.value.status == gabp.ENOMEM
+    srv = gabp.Server(iters=50, tol=1e-6, max_members=4)
+    t = srv.submit(p.X, p.y, p.gamma, p.C)
+    for _ in range(20):
+        srv.step()
+        if t in srv.completed():
+            break
+    _, r = srv.poll(t)
+    assert r["status"] == gabp.ENOMEM
+    monkeypatch.delenv("GABP_FAULT")
+    t2 = srv.submit(p.X, p.y, p.gamma, p.C)
+    res = None
+    for _ in range(2000):
+        srv.step()
+        if t2 in srv.completed():
+            res = srv.poll(t2)
+            break
+    srv.close()
+    assert res is not None and res[1]["status"] == 0 and res[1]["converged"] == 1
+    assert abs(_free_bytes() - free0) < (256 << 20)
+    s = gabp.GabpSVM(p.X, p.y, p.gamma, p.C)
+    assert s.solve(10, 0.0)[2] == 10
+
+
+def test_injected_nan_is_caught_by_the_staging_checks(monkeypatch):
+    p = workloads.mixture(300, 6, seed=8)
+    monkeypatch.setenv("GABP_FAULT", "nan")
+    with pytest.raises(gabp.GabpError) as ei:
+        gabp.svm_create(p.X, p.y, p.gamma, p.C)
+    assert ei.value.status == gabp.EINVAL and "row 150" in ei.value.message
+
+
+def test_injected_timeout_reaches_the_host_and_refit_recovers(monkeypatch):
+    """GABP_FAULT=timeout: the solve reports GABP_ETIMEOUT (as when a bounded
+    device wait runs out), the handle refuses further solves with
+    GABP_ESTATE, and a refit restores it."""
+    p = workloads.mixture(300, 6, seed=9)
+    s = gabp.GabpSVM(p.X, p.y, p.gamma, p.C)
+    monkeypatch.setenv("GABP_FAULT", "timeout")
+    with pytest.raises(gabp.GabpError) as ei:
+        s.solve(20, 0.0)
+    assert ei.value.status == gabp.ETIMEOUT
+    monkeypatch.delenv("GABP_FAULT")
+    with pytest.raises(gabp.GabpError) as ei:
+        s.solve(20, 0.0)
+    assert ei.value.status == gabp.ESTATE
+    s.refit(p.X, p.y, p.gamma, p.C)
+    alpha, rinf, k = s.solve(20, 0.0)
+    assert k == 20 and np.all(np.isfinite(alpha))
