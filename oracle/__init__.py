@@ -76,6 +76,7 @@ def _load():
         "orc_q_row": (None, [D, D, L, L, f64, f64, f64, i32, f64, L, D]),
         "orc_q_diag_all": (i32, [D, D, L, L, f64, f64, f64, i32, f64, D, D]),
         "orc_q_diag_tilemax": (i32, [D, D, L, L, f64, f64, f64, i32, f64, L, D, D, D]),
+        "orc_residual_tile_sparse": (f64, [D, D, L, L, f64, f64, D, L, ctypes.c_void_p, D, D]),
         "orc_cg_rbf": (i32, [D, D, L, L, f64, f64, f64, i32, f64, D, f64, i32, D, I]),
         "orc_dual_objective": (f64, [D, D, L]),
         "orc_decision": (i32, [D, D, D, L, L, D, L, f64, f64, D]),
@@ -183,6 +184,23 @@ def q_diag_tilemax(X, y, gamma, C, block=128, lam=None, diag_rule=DIAG_DOMINANT,
     iu = np.triu_indices(nt)
     tmax[iu] = flat          # row-major upper triangle: L = I Nt - I (I - 1) / 2 + (J - I)
     return diag, R, tmax
+
+
+def residual_tile_sparse(X, y, gamma, diag, keep, mu, block=128, lam=None):
+    """r = 1 - Q mu (FP64) for the tile-sparse matrix with diagonal `diag` and
+    the kept tiles keep[I, J] (I <= J, upper triangle), visiting kept tiles
+    only.  Returns (r, ||r||_inf)."""
+    X, px = _d(X)
+    y, py = _d(y)
+    n, m = X.shape
+    lam = default_lambda(n) if lam is None else lam
+    diag, pd = _d(diag)
+    mu, pm = _d(mu)
+    kp = np.ascontiguousarray(np.triu(np.asarray(keep, dtype=bool)), dtype=np.uint8)
+    r = np.empty(n)
+    rinf = _load().orc_residual_tile_sparse(px, py, n, m, gamma, lam, pd, int(block), kp.ctypes.data, pm,
+                                            r.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return r, float(rinf)
 
 
 class GabpResult:

@@ -211,6 +211,38 @@ int orc_q_diag_tilemax(const double* X, const double* y, long n, long m, double 
     return ORC_OK;
 }
 
+/* Residual r = 1 - Q mu of the tile-sparse matrix (the reading of Section 6's
+ * sparsified kernel used with orc_q_diag_tilemax): Q_ii = diag[i], and Q_ij
+ * (i != j) is the SVM entry where the block x block tile holding the pair is
+ * kept (keep[I * Nt + J] != 0 for I <= J, the upper-triangle tile of the pair)
+ * and 0 where it is dropped.  Only kept tiles are visited, O(kept pairs m).
+ * Returns ||r||_inf. */
+double orc_residual_tile_sparse(const double* X, const double* y, long n, long m, double gamma,
+                                double lam, const double* diag, long block, const unsigned char* keep,
+                                const double* mu, double* r)
+{
+    const long Nt = (n + block - 1) / block;
+    double rmax = 0.0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(max : rmax)
+    for (long i = 0; i < n; ++i) {
+        const long I = i / block;
+        double s = 1.0 - diag[i] * mu[i];
+        for (long J = 0; J < Nt; ++J) {
+            const long lo = I < J ? I : J, hi = I < J ? J : I;
+            if (!keep[lo * Nt + hi]) continue;
+            const long j1 = (J + 1) * block < n ? (J + 1) * block : n;
+            for (long j = J * block; j < j1; ++j) {
+                if (j == i) continue;
+                s -= orc_q_offdiag(X + i * m, X + j * m, y[i], y[j], m, gamma, lam) * mu[j];
+            }
+        }
+        r[i] = s;
+        const double a = fabs(s);
+        if (a > rmax) rmax = a;
+    }
+    return rmax;
+}
+
 /* r = b - Q mu, returns ||r||_inf.  The paper's Step 3 tests the messages for
  * convergence without naming a norm; the reading used throughout is the
  * infinity norm of the linear-system residual of the current means. */

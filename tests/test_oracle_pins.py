@@ -526,3 +526,18 @@ def test_q_diag_tilemax_pass():
     for I in range(nt):
         for J in range(I, nt):
             assert keep[I, J] == (I == J or tmax[I, J] > 1e-3)
+
+
+def test_residual_tile_sparse_against_dense_matrix():
+    """The kept-tiles-only residual equals 1 - Q mu with the dense tile-sparse
+    matrix of build_q_tile_sparse (ragged n, two block edges)."""
+    p = workloads.clustered_mixture(301, 5, seed=15, gamma=0.4)
+    X, y = p.X.astype(np.float64), p.y.astype(np.float64)
+    mu = np.random.default_rng(16).standard_normal(p.n)
+    for block, tau in ((128, 1e-3), (40, 1e-2)):
+        Q, keep = oracle.build_q_tile_sparse(X, y, p.gamma, p.C, tau, block=block)
+        r, rinf = oracle.residual_tile_sparse(X, y, p.gamma, np.diag(Q), keep, mu, block=block)
+        want = 1.0 - Q @ mu
+        np.testing.assert_allclose(r, want, rtol=1e-12, atol=1e-12 * np.max(np.abs(want)))
+        assert rinf == pytest.approx(np.max(np.abs(want)), rel=1e-12)
+        assert not keep.all()
