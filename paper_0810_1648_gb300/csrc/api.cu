@@ -140,7 +140,7 @@ gabp_status check_formed(gabp_svm_t h)
 
 // Device memory plan of one handle (bytes, 256-aligned sub-buffers).
 struct Plan {
-    size_t X, vec, agg, part, state, q, qref, work, tilemax, ctrl, rhist, final3, blockbuf, xp, tab, nbl, total;
+    size_t X, vec, agg, part, state, q, qref, work, tilemax, ctrl, rhist, final3, blockbuf, xp, xp3, tab, nbl, total;
 };
 
 // Bytes of the per-pair arrays (messages, stored Q, FP32 copy) for `tiles` tiles.
@@ -160,6 +160,7 @@ Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_m
     // for the kept tiles only (pair_bytes)
     p.tilemax = sparse ? 2 * align_up((size_t)ntiles * sizeof(float), 256) : 0;
     p.xp = q_mode != GABP_Q_F32 ? align_up(bf16_pack_bytes(Nt, (int)m), 1024) : 0;
+    p.xp3 = align_up(pack3_bytes(Nt, (int)m), 1024);   // the FP32 Gram's three BF16 planes
     p.X = align_up((size_t)n * m * sizeof(float), 256);
     p.vec = align_up((size_t)npad * sizeof(float), 256);
     p.agg = align_up((size_t)8 * npad * sizeof(float), 256);   // 2 x {P, h, mu} + staged {P, h}
@@ -179,7 +180,7 @@ Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_m
     p.final3 = 256;
     p.blockbuf = align_up((size_t)3 * ((n + 31) / 32) * sizeof(double), 256);
     p.total = p.X + 10 * p.vec + p.agg + p.part + p.state + p.q + p.qref + p.work + p.tilemax + p.ctrl + p.rhist +
-              p.final3 + p.blockbuf + p.xp + p.tab + p.nbl + 1024;
+              p.final3 + p.blockbuf + p.xp + p.xp3 + p.tab + p.nbl + 2048;
     return p;
 }
 
@@ -342,6 +343,9 @@ gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
         return fail(GABP_EINVAL, h->opts.task == GABP_TASK_KRR ? "row %lld: non-finite feature or target"
                                                                 : "row %lld: non-finite feature or label not +-1",
                     (long long)h->hctrl->bad_index);
+    // the FP32 rows as three BF16 planes for the tensor-core FP32 Gram
+    CK(launch_pack3(p.X, (int)n, (int)m, h->Nt, (void*)p.Xp3, s));
+    h->prof.kernel_launches += 1;
     if (h->opts.sparse_tau > 0) {
         // Tile-sparse option.  Pass 1 over every tile: tile maxima and |Q|
         // row sums (the whole matrix's, for the diagonal rule), nothing
@@ -668,11 +672,13 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     p.rhist_cap = kRhistCap;
     h->final3 = (double*)take(pl.final3);
     h->blockbuf = (double*)take(pl.blockbuf);
+    p.nkc = bf16_chunks((int)m);
     if (pl.xp) {
         off = align_up(off, 1024);
         p.Xp = take(pl.xp);
-        p.nkc = bf16_chunks((int)m);
     }
+    off = align_up(off, 1024);
+    p.Xp3 = take(pl.xp3);
 
     // Tile work list: the upper triangle, row by row within each stage (one
     // stage = all of it under the synchronous schedule); tile storage index

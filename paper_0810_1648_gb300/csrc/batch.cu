@@ -44,7 +44,7 @@ size_t aup(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Device memory of one instance (one allocation), carved like the handle's.
 struct MemberPlan {
-    size_t X, vec, agg, part, state, q, qref, rhist, final3, blockbuf, xp, total;
+    size_t X, vec, agg, part, state, q, qref, rhist, final3, blockbuf, xp, xp3, total;
 };
 
 // alias_x: FP32 features in device memory are read in place (no copy).
@@ -67,7 +67,9 @@ MemberPlan member_plan(int64_t n, int64_t m, int q_mode, int msg_bf16, bool alia
     p.final3 = 256;
     p.blockbuf = aup((size_t)3 * ((n + 31) / 32) * 8, 256);
     p.xp = q_mode != 0 ? aup(bf16_pack_bytes(Nt, (int)m), 1024) : 0;
-    p.total = aup(p.X + 10 * p.vec + p.agg + p.part + p.state + p.q + p.qref + p.final3 + p.blockbuf + p.xp + 2048, 1024);
+    p.xp3 = aup(pack3_bytes(Nt, (int)m), 1024);   // the FP32 Gram's three BF16 planes
+    p.total = aup(p.X + 10 * p.vec + p.agg + p.part + p.state + p.q + p.qref + p.final3 + p.blockbuf + p.xp + p.xp3 +
+                  3072, 1024);
     return p;
 }
 
@@ -632,11 +634,13 @@ class Engine {
         p.qref = pl.qref ? (float*)take(pl.qref) : (q_mode == 0 ? (float*)p.qstore : nullptr);
         M.final3 = (double*)take(pl.final3);
         M.blockbuf = (double*)take(pl.blockbuf);
+        p.nkc = bf16_chunks((int)m);
         if (pl.xp) {
             off = aup(off, 1024);
             p.Xp = take(pl.xp);
-            p.nkc = bf16_chunks((int)m);
         }
+        off = aup(off, 1024);
+        p.Xp3 = take(pl.xp3);
         p.ctrl = d_ctrl + slot;
         p.rhist = nullptr;
         p.rhist_cap = 0;
@@ -756,10 +760,11 @@ class Engine {
             EK(cudaMemcpyAsync(d_ns, nb_stage.data(), nb_stage.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
         launch_stage_list(d_tab, d_ns, (int)nb_stage.size(), s);
         if (q_mode != 0) EK(launch_pack_list(d_tab, d_n, (int)nb.size(), s));
+        EK(launch_pack3_list(d_tab, d_n, (int)nb.size(), s));
         launch_form_q(d_tab, d_tl, (long long)tiles_lead.size(), s);
         launch_init_list(d_tab, d_n, (int)nb.size(), diag_rule, (float)delta, s);
         if (q_mode == 1) EK(launch_form_q_tc(d_tab, d_tl, (long long)tiles_lead.size(), s));
-        launches += q_mode == 0 ? 3 : (q_mode == 1 ? 5 : 4);
+        launches += q_mode == 0 ? 4 : (q_mode == 1 ? 6 : 5);
         EK(cudaGetLastError());
         size_t g = 0;
         while (g < evg.size() && evg[g].refs > 0) ++g;

@@ -99,7 +99,8 @@ struct Inst {
     float C;          // box constant
     const void* Xp;   // BF16 features packed in tensor-core operand blocks (precision form)
     const float* sqb; // ||bf16(x_i)||^2
-    int nkc;          // 64-feature chunks of Xp
+    int nkc;          // 64-feature chunks of Xp and Xp3
+    const void* Xp3;  // the FP32 features as three BF16 planes in operand blocks (FP32 Gram on the tensor cores)
     int msg_bf16;     // messages stored in BF16 (precision forms)
     int task;         // 0 SVM (labels in Q, alpha clipped to [0, C]), 1 KRR (y = 1 in Q, alpha unclipped)
     int form_next;    // formation: 1 + the next instance built from the same features (its Q
@@ -181,10 +182,20 @@ void launch_stage(const void* X, int x_f64, int n, int m, float* y, float* Xf, f
 inline double refine_handover(float opt, int msg_bf16) { return opt > 0 ? opt : (msg_bf16 ? 1e-3 : 1e-4); }
 inline double refine_inner(float opt, int msg_bf16) { return opt > 0 ? opt : (msg_bf16 ? 3e-2 : 1e-2); }
 
-// Q formation (FP32 SIMT Gram fused with exp, labels and bias) + |Q| row-sum partials;
-// the FP32 tiles are stored into Inst::qref where it is set (the FP32 store, or the
-// FP32 copy the BF16 store keeps for its refinement residuals).
-void launch_form_q(const Inst* tab, const int4* work, long long ntiles, cudaStream_t s);
+// Q formation (FP32-accurate Gram on the tensor cores from three BF16 planes,
+// fused with exp, labels and bias) + |Q| row-sum partials; the FP32 tiles are
+// stored into Inst::qref where it is set (the FP32 store, or the FP32 copy the
+// BF16 store keeps for its refinement residuals), the tile maxima into
+// Inst::tilemax where it is set.  Needs Inst::Xp3 packed first.
+cudaError_t launch_form_q_tc32(const Inst* tab, const int4* work, long long ntiles, cudaStream_t s);
+inline void launch_form_q(const Inst* tab, const int4* work, long long ntiles, cudaStream_t s)
+{
+    (void)launch_form_q_tc32(tab, work, ntiles, s);   // errors surface at the caller's cudaGetLastError
+}
+// The three BF16 planes of FP32 rows (zero padding to whole tiles and chunks).
+cudaError_t launch_pack3(const float* Xf, int n, int m, int Nt, void* Xp3, cudaStream_t s);
+cudaError_t launch_pack3_list(const Inst* tab, const int2* nbl, int nblocks, cudaStream_t s);
+size_t pack3_bytes(int Nt, int m);
 // Precision form: BF16 operand packing + norms, and the tensor-core Q formation (BF16 store).
 cudaError_t launch_pack_bf16(const float* Xf, int n, int m, int nkc, int Nt, void* Xp, float* sqb, cudaStream_t s);
 cudaError_t launch_form_q_tc(const Inst* tab, const int4* work, long long ntiles, cudaStream_t s);

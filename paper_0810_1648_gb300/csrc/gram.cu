@@ -1,16 +1,14 @@
-// FP32 Gram tiles fused with the RBF kernel, and everything built on them:
+// SIMT FP32 Gram tiles fused with the RBF kernel, and everything built on them:
 //   - input staging (FP64 -> FP32, row norms, label/finiteness checks),
-//   - formation of the stored Q tiles with |Q| row-sum partials (Section 5:
-//     every node computes its rows of D; Section 3.1: those sums set the
-//     weighted diagonal),
-//   - the final residual r = 1 - Q mu and Q alpha for the dual objective,
+//   - the final residual r = 1 - Q mu and Q alpha for the dual objective
+//     (Q read back from the FP32 tiles, or recomputed here when not stored),
 //   - the decision values f(x) = sum_i alpha_i y_i (K(x_i, x) + lambda^2)
 //     (Section 1.1).
+// (The stored Q tiles themselves are formed on the tensor cores: gram_tc32.cu.)
 //
 // One CTA computes one 128 x 128 Gram tile G = X_I X_J^T by SIMT FP32 FMAs
-// (8 x 8 outputs per thread, K-chunks of 16 double-buffered in shared memory,
-// two CTAs per SM for the formation kernel), then
-// runs an epilogue on the 64 values it holds: d^2 = max(0, s_i + s_j - 2 G),
+// (8 x 8 outputs per thread, K-chunks of 16 double-buffered in shared memory),
+// then runs an epilogue on the 64 values it holds: d^2 = max(0, s_i + s_j - 2 G),
 // K = expf(-gamma d^2), Q_ij = y_i y_j (K + lambda^2).  The distances use the
 // norm expansion with norms of the same FP32 rows, so d^2_ii is 0 up to
 // rounding and is clamped at 0.
@@ -222,80 +220,6 @@ __global__ void k_stage_list(const Inst* __restrict__ tab, const int2* __restric
     if (threadIdx.x < 32 && i < p.n)
         stage_row(p.X, 0, i, p.m, const_cast<float*>(p.y), const_cast<float*>(p.X), const_cast<float*>(p.sq),
                   const_cast<float*>(p.b), const_cast<float*>(p.b0), p.task, p.ctrl);
-}
-
-// ------------------------------------------------------- Q tile formation
-// One Gram tile per work item; every instance chained through form_next (the
-// points of a parameter grid over the same features) takes its Q tile, row
-// and column sums and tile maximum from it in turn.
-__global__ void __launch_bounds__(NTHREADS, 2) k_form_q(const Inst* __restrict__ tab, const int4* __restrict__ work)
-{
-    __shared__ __align__(16) TileSmem sm;
-    const int4 w = work[blockIdx.x];
-    const long long L = w.w;
-    const int I = w.y, J = w.z;
-    float acc[8][8];
-    {
-        const Inst& p0 = tab[w.x];
-        const GramSide S{p0.X, p0.sq, p0.n};
-        gram_tile(S, S, p0.m, I, J, sm.g, acc);
-    }
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    for (int k = w.x; k >= 0;) {
-        const Inst& p = tab[k];
-        const int n = p.n;
-        float yj[8], sj[8];
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            const int j = J * T + tx * 8 + b;
-            yj[b] = j < n ? p.y[j] : 0.f;
-            sj[b] = j < n ? p.sq[j] : 0.f;
-        }
-        float rs[1][8], cs[1][8];
-#pragma unroll
-        for (int b = 0; b < 8; ++b) cs[0][b] = 0.f;
-        float tmx = 0.f;    // largest |Q_ij| of the thread's pairs (the tile-sparse option)
-        float* qt = p.qref ? p.qref + (size_t)L * TT : nullptr;   // FP32 Q kept for the sweeps / residuals
-#pragma unroll
-        for (int a = 0; a < 8; ++a) {
-            const int r = ty * 8 + a, i = I * T + r;
-            const float yi = i < n ? p.y[i] : 0.f, si = i < n ? p.sq[i] : 0.f;
-            float out[8];
-            float racc = 0.f;
-#pragma unroll
-            for (int b = 0; b < 8; ++b) {
-                const int c = tx * 8 + b, j = J * T + c;
-                const bool v = i < n && j < n && (I != J || c > r);
-                const float q = yi * yj[b] * (rbf_from_gram(acc[a][b], si, sj[b], p.gamma) + p.lam2);
-                out[b] = v ? q : 0.f;
-                racc += fabsf(out[b]);
-                cs[0][b] += fabsf(out[b]);
-                tmx = fmaxf(tmx, fabsf(out[b]));
-            }
-            rs[0][a] = racc;
-            if (qt) {
-                float4* dst = reinterpret_cast<float4*>(qt + r * T + tx * 8);
-                dst[0] = make_float4(out[0], out[1], out[2], out[3]);
-                dst[1] = make_float4(out[4], out[5], out[6], out[7]);
-            }
-        }
-        float* const parts[1] = {p.part};
-        __syncthreads();   // Gram smem (first pass) or the previous instance's sums are done with
-        reduce_and_write<1>(sm.e, rs, cs, parts, n, I, J);
-        if (p.tilemax) {
-            // largest |Q_ij| of the tile's pairs (the tile-sparse option)
-            const float mx = warp_max_f(tmx);
-            __syncthreads();
-            if ((tid & 31) == 0) sm.e.rowv[0][tid >> 5] = mx;
-            __syncthreads();
-            if (tid == 0) {
-                float m2 = 0.f;
-                for (int w2 = 0; w2 < NWARPS; ++w2) m2 = fmaxf(m2, sm.e.rowv[0][w2]);
-                p.tilemax[L] = m2;
-            }
-        }
-        k = p.form_next - 1;
-    }
 }
 
 // ------------------------------------------- final residual and Q alpha
@@ -566,11 +490,6 @@ void launch_stage(const void* X, int x_f64, int n, int m, float* y, float* Xf, f
                   float* b, float* b0, int task, Ctrl* ctrl, cudaStream_t s)
 {
     k_stage<<<(n + 255) / 256, 256, 0, s>>>(X, x_f64, n, m, y, Xf, sq, b, b0, task, ctrl);
-}
-
-void launch_form_q(const Inst* tab, const int4* work, long long ntiles, cudaStream_t s)
-{
-    if (ntiles > 0) k_form_q<<<(unsigned)ntiles, NTHREADS, 0, s>>>(tab, work);
 }
 
 void launch_final(const Inst* tab, const StopOp* ops, const int4* tiles, long long ntiles, const int2* nbl,

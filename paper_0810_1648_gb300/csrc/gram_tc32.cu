@@ -1,0 +1,407 @@
+// FP32-accurate Gram tiles on the 5th-generation tensor cores (tcgen05),
+// fused with the RBF kernel, labels and bias: the FP32 Q tiles of the plain
+// form, the FP32 copy the BF16 store keeps for its refinement residuals, and
+// the |Q| row sums that set the weighted diagonal (Section 5 computes the
+// kernel matrix once; Section 3.1 weights the diagonal by those sums;
+// Section 1.1 defines D_ij = y_i y_j K(x_i, x_j)).
+//
+// Three BF16 planes.  Every FP32 feature is split as x = x1 + x2 + x3 with
+// x1 = bf16(x), x2 = bf16(x - x1), x3 = bf16(x - x1 - x2) (both differences
+// are exact in FP32), so x1 + x2 + x3 carries x to about 2^-27 of its size.
+// The dot product keeps the six plane products with a + b <= 4,
+//   x.y ~ x1.y3 + x2.y2 + x3.y1 + x1.y2 + x2.y1 + x1.y1,
+// issued smallest first; the dropped ones are below 2^-26 of |x||y|.  The
+// tensor cores multiply BF16 exactly; their FP32 accumulation drops low bits,
+// so each 64-feature chunk gets a fresh accumulator and the chunks are added
+// on the CUDA cores (round to nearest).
+//
+// k_form_q_tc32 is persistent with warp roles: warp 0 streams the six 16 KB
+// operand blocks of each (tile, chunk) into a two-stage shared-memory ring;
+// warp 1 allocates 256 TMEM columns (two 128 x 128 FP32 accumulators) and one
+// thread issues the 24 MMAs of a chunk (6 products x K = 64 in steps of 16);
+// warps 2-9 (two per TMEM lane quarter, one per column half) add each chunk's
+// accumulator into registers, then form the Q entries exactly as the SIMT
+// formation does (norm expansion with the FP32 norms, clamp, expf, bias,
+// labels), store them, and reduce |Q| over rows (in registers), over columns
+// (a warp transpose-sum, then the four lane quarters in shared memory) and to
+// the tile maximum.  Instances chained behind the listed one (the points of a
+// parameter grid over the same features) take their Q tiles from the same
+// Gram sums.
+#include "common.cuh"
+#include "ptx.cuh"
+
+#include <float.h>
+
+namespace gabp {
+
+namespace {
+
+constexpr int NPLANE = 3;
+constexpr int T3_EPI_WARPS = 8;
+constexpr int T3_THREADS = (2 + T3_EPI_WARPS) * 32;
+constexpr int T3_STAGES = 2;
+constexpr size_t T3_STAGE_BYTES = (size_t)2 * NPLANE * BLK_BYTES;   // A planes, then B planes: 96 KB
+constexpr uint32_t T3_TMEM_COLS = 256;
+constexpr uint32_t T3_IDESC = idesc_bf16_f32(T, T);
+constexpr int T3_PRODUCTS = 6;
+
+// Plane pairs (a, b) of the kept products, smallest first.
+__device__ __forceinline__ int prod_a(int q) { return q == 0 ? 0 : q == 1 ? 1 : q == 2 ? 2 : q == 3 ? 0 : q == 4 ? 1 : 0; }
+__device__ __forceinline__ int prod_b(int q) { return q == 0 ? 2 : q == 1 ? 1 : q == 2 ? 0 : q == 3 ? 1 : q == 4 ? 0 : 0; }
+
+// The three BF16 planes of x.
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& b1, __nv_bfloat16& b2, __nv_bfloat16& b3)
+{
+    b1 = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(b1);
+    b2 = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(b2);
+    b3 = __float2bfloat16_rn(r2);
+}
+
+// Offset (in 16-byte units) of row rr's 8-feature group kg inside a packed
+// 128 x 64 block: 8-row x 16-byte core matrices, K-adjacent ones 128 bytes
+// apart, 8-row groups 1024 bytes apart (the canonical K-major layout).
+__device__ __forceinline__ size_t core_off16(int rr, int kg)
+{
+    return (size_t)((rr / 8) * (KCH / 8) + kg) * 8 + (rr % 8);
+}
+
+// Row r (of Nt*T, zero beyond n) and 8-feature group gk of chunk kc -> the
+// three planes' blocks ((I nkc + kc) 3 + plane).
+__device__ __forceinline__ void pack3_group(const float* __restrict__ Xf, int n, int m, int nkc, int r, int gk,
+                                            uint4* __restrict__ Xp3)
+{
+    const int kc = gk / (KCH / 8), kg = gk % (KCH / 8);
+    const int I = r / T, rr = r % T;
+    __align__(16) __nv_bfloat16 v[NPLANE][8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int k = kc * KCH + kg * 8 + u;
+        split3((r < n && k < m) ? Xf[(size_t)r * m + k] : 0.f, v[0][u], v[1][u], v[2][u]);
+    }
+#pragma unroll
+    for (int pl = 0; pl < NPLANE; ++pl) {
+        const size_t blk = ((size_t)I * nkc + kc) * NPLANE + pl;
+        Xp3[blk * (BLK_BYTES / 16) + core_off16(rr, kg)] = *reinterpret_cast<const uint4*>(v[pl]);
+    }
+}
+
+__global__ void k_pack3(const float* __restrict__ Xf, int n, int m, int nkc, int Nt, uint4* __restrict__ Xp3)
+{
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long groups = (long long)nkc * (KCH / 8);
+    if (e >= (long long)Nt * T * groups) return;
+    pack3_group(Xf, n, m, nkc, (int)(e / groups), (int)(e % groups), Xp3);
+}
+
+// Listed node blocks (32 rows, 8 threads a row); the last block of an
+// instance also writes the zero rows that pad its last tile.
+__global__ void k_pack3_list(const Inst* __restrict__ tab, const int2* __restrict__ nbl)
+{
+    const int2 nb = nbl[blockIdx.x];
+    const Inst& p = tab[nb.x];
+    const int rl = threadIdx.x >> 3, gsub = threadIdx.x & 7;
+    const int r = nb.y * 32 + rl, n = p.n;
+    const bool last = nb.y == (n - 1) / 32;
+    uint4* Xp3 = static_cast<uint4*>(const_cast<void*>(p.Xp3));
+    const int groups = p.nkc * (KCH / 8);
+    for (int rw = r; rw < p.Nt * T; rw += 32) {
+        for (int gk = gsub; gk < groups; gk += 8) pack3_group(p.X, n, p.m, p.nkc, rw, gk, Xp3);
+        if (!last) break;
+    }
+}
+
+struct T3Smem {
+    unsigned long long xfull[T3_STAGES], xempty[T3_STAGES];
+    unsigned long long accfull[2], accempty[2];
+    unsigned long long drain;
+    uint32_t tmem_base;
+    int abort;
+    float colsum[4][T];                 // per lane quarter: column sums over its 32 rows
+    float rowsum[2][T];                 // per column half: row sums
+    float tmx[T3_EPI_WARPS];
+    alignas(16) float cy[T3_EPI_WARPS][64];   // a warp's 64 columns: labels
+    alignas(16) float cs[T3_EPI_WARPS][64];   // and FP32 norms
+};
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(T3_EPI_WARPS * 32) : "memory"); }
+
+// After it, lane l of the warp holds the sum over the 32 lanes of v[l]
+// (a fixed butterfly: 31 shuffles for 32 values).
+__device__ __forceinline__ float transpose_sum32(float (&v)[32], int lane)
+{
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const bool hi = (lane & w) != 0;
+#pragma unroll
+        for (int k = 0; k < w; ++k) {
+            const float send = hi ? v[k] : v[k + w];
+            const float keep = hi ? v[k + w] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+        }
+    }
+    return v[0];
+}
+
+__global__ void __launch_bounds__(T3_THREADS, 1)
+    k_form_q_tc32(const Inst* __restrict__ tab, const int4* __restrict__ work, long long ntiles)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* ops = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    T3Smem& sm = *reinterpret_cast<T3Smem*>(ops + T3_STAGES * T3_STAGE_BYTES);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        for (int s = 0; s < T3_STAGES; ++s) { mbar_init(&sm.xfull[s], 1); mbar_init(&sm.xempty[s], 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&sm.accfull[b], 1); mbar_init(&sm.accempty[b], T3_EPI_WARPS); }
+        mbar_init(&sm.drain, 1);
+        sm.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(&sm.tmem_base, T3_TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = sm.tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------------------------ operand producer
+        if (lane == 0) {
+            const uint64_t pol = l2_evict_first_policy();
+            int stage = 0;
+            uint32_t ph = 0;
+            bool run = true;
+            for (long long L = blockIdx.x; L < ntiles && run; L += gridDim.x) {
+                const int4 w = work[L];
+                const Inst& p = tab[w.x];
+                const unsigned char* Xp3 = static_cast<const unsigned char*>(p.Xp3);
+                const int I = w.y, J = w.z, nkc = p.nkc;
+                for (int kc = 0; kc < nkc; ++kc) {
+                    if (*(volatile int*)&sm.abort || !mbar_wait(&sm.xempty[stage], ph ^ 1u)) {
+                        sm.abort = 1;
+                        record_error(p.ctrl, ST_ETIMEOUT, L);
+                        run = false;
+                        break;
+                    }
+                    unsigned char* S = ops + (size_t)stage * T3_STAGE_BYTES;
+                    mbar_arrive_expect_tx(&sm.xfull[stage], (uint32_t)T3_STAGE_BYTES);
+#pragma unroll
+                    for (int pl = 0; pl < NPLANE; ++pl) {
+                        bulk_load(S + (size_t)pl * BLK_BYTES, Xp3 + (((size_t)I * nkc + kc) * NPLANE + pl) * BLK_BYTES,
+                                  BLK_BYTES, &sm.xfull[stage], pol);
+                        bulk_load(S + (size_t)(NPLANE + pl) * BLK_BYTES,
+                                  Xp3 + (((size_t)J * nkc + kc) * NPLANE + pl) * BLK_BYTES, BLK_BYTES, &sm.xfull[stage],
+                                  pol);
+                    }
+                    if (++stage == T3_STAGES) { stage = 0; ph ^= 1u; }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int stage = 0, acc = 0;
+            uint32_t ph = 0, aph = 0;
+            bool run = true;
+            for (long long L = blockIdx.x; L < ntiles && run; L += gridDim.x) {
+                const Inst& p = tab[work[L].x];
+                Ctrl* ctrl = p.ctrl;
+                const int nkc = p.nkc;
+                for (int kc = 0; kc < nkc; ++kc) {
+                    if (*(volatile int*)&sm.abort || !mbar_wait(&sm.accempty[acc], aph ^ 1u) ||
+                        !mbar_wait(&sm.xfull[stage], ph)) {
+                        sm.abort = 1;
+                        record_error(ctrl, ST_ETIMEOUT, L);
+                        run = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const unsigned char* S = ops + (size_t)stage * T3_STAGE_BYTES;
+                    const uint32_t d = tbase + (uint32_t)acc * T;
+#pragma unroll
+                    for (int q = 0; q < T3_PRODUCTS; ++q) {
+#pragma unroll
+                        for (int s = 0; s < KCH / 16; ++s) {
+                            const uint64_t ad = smem_desc(S + (size_t)prod_a(q) * BLK_BYTES + s * 256, 128, 1024);
+                            const uint64_t bd =
+                                smem_desc(S + (size_t)(NPLANE + prod_b(q)) * BLK_BYTES + s * 256, 128, 1024);
+                            tc_mma_bf16(d, ad, bd, T3_IDESC, (q | s) != 0);
+                        }
+                    }
+                    tc_commit(&sm.xempty[stage]);
+                    tc_commit(&sm.accfull[acc]);
+                    if (++stage == T3_STAGES) { stage = 0; ph ^= 1u; }
+                    if (++acc == 2) { acc = 0; aph ^= 1u; }
+                }
+            }
+            // every MMA issued above must finish before the columns are freed
+            tc_commit(&sm.drain);
+            if (!mbar_wait(&sm.drain, 0u)) sm.abort = 1;
+        }
+    } else {
+        // --------------------------------------------------------- epilogue
+        // warp w reads TMEM lanes 32 (w % 4) ..: rows 32 g + lane, columns
+        // [64 half, 64 half + 64)
+        const int ew = warp - 2, g = warp & 3, half = ew >> 2;
+        const int r = 32 * g + lane, c0 = 64 * half;
+        const int etid = tid - 64;
+        int acc = 0;
+        uint32_t aph = 0;
+        for (long long L = blockIdx.x; L < ntiles; L += gridDim.x) {
+            const int4 w = work[L];
+            const int nkc = tab[w.x].nkc;
+            float ga[64];
+#pragma unroll
+            for (int c = 0; c < 64; ++c) ga[c] = 0.f;
+            bool ok = true;
+            for (int kc = 0; kc < nkc; ++kc) {
+                const bool stop = __shfl_sync(0xffffffffu, *(volatile int*)&sm.abort, 0) != 0;
+                if (stop || !mbar_wait_warp(&sm.accfull[acc], aph)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    float v[32];
+                    tmem_ld32(tbase + (uint32_t)acc * T + ((uint32_t)(32 * g) << 16) + (uint32_t)(c0 + 32 * j), v);
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) ga[32 * j + c] = kc == 0 ? v[c] : ga[32 * j + c] + v[c];
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.accempty[acc]);
+                if (++acc == 2) { acc = 0; aph ^= 1u; }
+            }
+            if (!ok && lane == 0) {
+                sm.abort = 1;
+                record_error(tab[w.x].ctrl, ST_ETIMEOUT, L);
+            }
+            epi_bar();   // every epilogue warp takes the stop decision together
+            if (*(volatile int*)&sm.abort) break;
+            const int I = w.y, J = w.z;
+            const int i = I * T + r;
+            for (int k = w.x; k >= 0;) {
+                const Inst& p = tab[k];
+                const int n = p.n;
+                // this warp's 64 column labels and norms
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int j = J * T + c0 + 32 * u + lane;
+                    sm.cy[ew][32 * u + lane] = j < n ? p.y[j] : 0.f;
+                    sm.cs[ew][32 * u + lane] = j < n ? p.sq[j] : 0.f;
+                }
+                __syncwarp();
+                const float yi = i < n ? p.y[i] : 0.f, si = i < n ? p.sq[i] : 0.f;
+                float* qt = p.qref ? p.qref + (size_t)w.w * TT + (size_t)r * T + c0 : nullptr;
+                float rs = 0.f, tmx = 0.f;
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    float q[32];
+#pragma unroll
+                    for (int c4 = 0; c4 < 32; c4 += 4) {
+                        const float4 y4 = *reinterpret_cast<const float4*>(&sm.cy[ew][32 * u + c4]);
+                        const float4 s4 = *reinterpret_cast<const float4*>(&sm.cs[ew][32 * u + c4]);
+                        const float yj[4] = {y4.x, y4.y, y4.z, y4.w};
+                        const float sj[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            const int c = c0 + 32 * u + c4 + t, j = J * T + c;
+                            const bool valid = i < n && j < n && (I != J || c > r);
+                            const float d2 = fmaxf(0.f, si + sj[t] - 2.f * ga[32 * u + c4 + t]);
+                            const float qv = yi * yj[t] * (expf(-p.gamma * d2) + p.lam2);
+                            q[c4 + t] = valid ? qv : 0.f;
+                            rs += fabsf(q[c4 + t]);
+                            tmx = fmaxf(tmx, fabsf(q[c4 + t]));
+                        }
+                    }
+                    if (qt) {
+#pragma unroll
+                        for (int c4 = 0; c4 < 32; c4 += 4)
+                            *reinterpret_cast<float4*>(qt + 32 * u + c4) = make_float4(q[c4], q[c4 + 1], q[c4 + 2], q[c4 + 3]);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) q[c] = fabsf(q[c]);
+                    sm.colsum[g][c0 + 32 * u + lane] = transpose_sum32(q, lane);
+                }
+                sm.rowsum[half][r] = rs;
+                tmx = warp_max_f(tmx);
+                if (lane == 0) sm.tmx[ew] = tmx;
+                epi_bar();
+                // per-node slot partials (fixed order): row sums of the tile's rows,
+                // column sums of its columns; both roles on a diagonal tile
+                float* part = p.part;
+                if (I == J) {
+                    if (etid < T) {
+                        const int x = I * T + etid;
+                        if (x < n)
+                            part[(size_t)I * n + x] = (sm.rowsum[0][etid] + sm.rowsum[1][etid]) +
+                                                      (((sm.colsum[0][etid] + sm.colsum[1][etid]) + sm.colsum[2][etid]) +
+                                                       sm.colsum[3][etid]);
+                    }
+                } else if (etid < T) {
+                    const int x = I * T + etid;
+                    if (x < n) part[(size_t)J * n + x] = sm.rowsum[0][etid] + sm.rowsum[1][etid];
+                } else {
+                    const int c = etid - T, x = J * T + c;
+                    if (x < n)
+                        part[(size_t)I * n + x] =
+                            ((sm.colsum[0][c] + sm.colsum[1][c]) + sm.colsum[2][c]) + sm.colsum[3][c];
+                }
+                if (etid == 0 && p.tilemax) {
+                    float m2 = 0.f;
+                    for (int e = 0; e < T3_EPI_WARPS; ++e) m2 = fmaxf(m2, sm.tmx[e]);
+                    p.tilemax[w.w] = m2;
+                }
+                epi_bar();   // shared sums read before the next instance or tile writes them
+                k = p.form_next - 1;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tbase, T3_TMEM_COLS);
+    }
+}
+
+constexpr size_t t3_smem_bytes() { return 1024 + T3_STAGES * T3_STAGE_BYTES + sizeof(T3Smem); }
+
+}  // namespace
+
+size_t pack3_bytes(int Nt, int m) { return (size_t)NPLANE * Nt * bf16_chunks(m) * BLK_BYTES; }
+
+cudaError_t launch_pack3(const float* Xf, int n, int m, int Nt, void* Xp3, cudaStream_t s)
+{
+    const int nkc = bf16_chunks(m);
+    const long long total = (long long)Nt * T * nkc * (KCH / 8);
+    k_pack3<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(Xf, n, m, nkc, Nt, static_cast<uint4*>(Xp3));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack3_list(const Inst* tab, const int2* nbl, int nblocks, cudaStream_t s)
+{
+    if (nblocks > 0) k_pack3_list<<<nblocks, 256, 0, s>>>(tab, nbl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_form_q_tc32(const Inst* tab, const int4* work, long long ntiles, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_form_q_tc32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)t3_smem_bytes());
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int sms = num_sms();
+    const int grid = (int)(ntiles < sms ? ntiles : sms);
+    k_form_q_tc32<<<grid, T3_THREADS, t3_smem_bytes(), s>>>(tab, work, ntiles);
+    return cudaGetLastError();
+}
+
+}  // namespace gabp
