@@ -93,6 +93,7 @@ struct gabp_svm_s {
     Inst* d_tab = nullptr;          // device copy of inst (a one-instance batch)
     int4* work_all = nullptr;       // every tile {0, I, J, L}, row by row (formation)
     int4* work = nullptr;           // the swept tiles, grouped by stage (= work_all's tiles when dense)
+    int4* work_diag = nullptr;      // the diagonal tiles {0, I, I, L} (the tensor-core norms pass)
     long long nlive = 0;            // tiles in `work`
     int2* nbl = nullptr;            // node blocks {0, b}
     Sched* sched = nullptr;   // one per stage
@@ -172,7 +173,7 @@ Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_m
         : 0;
     // the BF16 store keeps an FP32 copy for the refinement residuals
     p.qref = q_mode == GABP_Q_BF16 ? align_up((size_t)dense_tiles * TT * sizeof(float), 256) : 0;
-    p.work = (sparse ? 2 : 1) * align_up((size_t)ntiles * sizeof(int4), 256);
+    p.work = (sparse ? 2 : 1) * align_up((size_t)ntiles * sizeof(int4), 256) + align_up((size_t)Nt * sizeof(int4), 256);
     p.tab = align_up(align_up(sizeof(Inst), 16) + kMaxStages * align_up(sizeof(Sched), 16) + sizeof(StopOp) + 64, 256);
     p.nbl = align_up((size_t)((n + 31) / 32) * sizeof(int2), 256);
     p.ctrl = align_up(sizeof(Ctrl), 256);
@@ -343,9 +344,12 @@ gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
         return fail(GABP_EINVAL, h->opts.task == GABP_TASK_KRR ? "row %lld: non-finite feature or target"
                                                                 : "row %lld: non-finite feature or label not +-1",
                     (long long)h->hctrl->bad_index);
-    // the FP32 rows as three BF16 planes for the tensor-core FP32 Gram
+    // the FP32 rows as three BF16 planes for the tensor-core FP32 Gram, and
+    // the norms from the same products (diagonal tiles)
     CK(launch_pack3(p.X, (int)n, (int)m, h->Nt, (void*)p.Xp3, s));
-    h->prof.kernel_launches += 1;
+    launch_form_norms(h->d_tab, h->work_diag, h->Nt, s);
+    CK(cudaGetLastError());
+    h->prof.kernel_launches += 2;
     if (h->opts.sparse_tau > 0) {
         // Tile-sparse option.  Pass 1 over every tile: tile maxima and |Q|
         // row sums (the whole matrix's, for the diagonal rule), nothing
@@ -639,7 +643,7 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     p.b0 = (const float*)take(pl.vec);
     p.qdiag = (float*)take(pl.vec);
     h->alpha = (float*)take(pl.vec);
-    take(pl.vec);
+    p.sq3 = (float*)take(pl.vec);
     p.sqb = (const float*)take(pl.vec);
     h->mu_acc = (float*)take(pl.vec);
     h->r32 = (float*)take(pl.vec);
@@ -651,13 +655,15 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     p.msg_bf16 = o.msg_bf16;
     p.qstore = pl.q ? take(pl.q) : nullptr;
     p.qref = pl.qref ? (float*)take(pl.qref) : (o.q_mode == GABP_Q_F32 ? (float*)p.qstore : nullptr);
+    h->work_diag = (int4*)take(align_up((size_t)h->Nt * sizeof(int4), 256));
+    const size_t wbytes = pl.work - align_up((size_t)h->Nt * sizeof(int4), 256);
     if (o.sparse_tau > 0) {
-        h->work_all = (int4*)take(pl.work / 2);
-        h->work = (int4*)take(pl.work / 2);
+        h->work_all = (int4*)take(wbytes / 2);
+        h->work = (int4*)take(wbytes / 2);
         h->tilemax = (float*)take(pl.tilemax / 2);
         h->slab = (int*)take(pl.tilemax / 2);
     } else {
-        h->work = h->work_all = (int4*)take(pl.work);   // formation walks the swept list
+        h->work = h->work_all = (int4*)take(wbytes);   // formation walks the swept list
     }
     {
         char* tb = (char*)take(pl.tab);
@@ -698,10 +704,15 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     }
     std::vector<int2> nb((size_t)nblk);
     for (int b = 0; b < nblk; ++b) nb[(size_t)b] = make_int2(0, b);
+    std::vector<int4> wd((size_t)h->Nt);
+    for (int I = 0; I < h->Nt; ++I)
+        wd[(size_t)I] = make_int4(0, I, I, (int)((long long)I * h->Nt - (long long)I * (I - 1) / 2));
     h->grid = round_grid(h->ntiles, nblk, o.q_mode, 0, o.msg_bf16);
     h->nlive = h->ntiles;
     e = cudaMemcpyAsync(h->work_all, wl.data(), wl.size() * sizeof(int4), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->nbl, nb.data(), nb.size() * sizeof(int2), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->work_diag, wd.data(), wd.size() * sizeof(int4), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->sched, sc, (size_t)h->nstages * sizeof(Sched), cudaMemcpyHostToDevice, h->stream);
     const int zero_slot = 0;

@@ -623,7 +623,7 @@ class Engine {
         p.sqb = (const float*)take(pl.vec);
         M.mu_acc = (float*)take(pl.vec);
         M.r32 = (float*)take(pl.vec);
-        take(pl.vec);
+        p.sq3 = (float*)take(pl.vec);
         p.agg = (float*)take(pl.agg);
         p.aggmid = p.agg + (size_t)6 * p.npad;
         p.part = (float*)take(pl.part);
@@ -733,13 +733,16 @@ class Engine {
             EK(cudaMemsetAsync(d_ctrl + sl[a], 0, (e - a) * sizeof(Ctrl), s));
             a = e;
         }
-        std::vector<int4> tiles_lead;
+        std::vector<int4> tiles_lead, diag_lead;
         std::vector<int2> nb, nb_stage;
         for (int k : leaders) {
             const int Nt = mem[(size_t)k].inst.Nt;
             int L = 0;
             for (int I = 0; I < Nt; ++I)
-                for (int J = I; J < Nt; ++J, ++L) tiles_lead.push_back(make_int4(k, I, J, L));
+                for (int J = I; J < Nt; ++J, ++L) {
+                    tiles_lead.push_back(make_int4(k, I, J, L));
+                    if (I == J) diag_lead.push_back(make_int4(k, I, J, L));
+                }
         }
         for (int k : pending) {
             const Member& M = mem[(size_t)k];
@@ -749,9 +752,12 @@ class Engine {
             }
         }
         int4* d_tl = nullptr;
+        int4* d_dl = nullptr;
         int2* d_n = nullptr;
         int2* d_ns = nullptr;
         EK(cudaMallocAsync((void**)&d_tl, tiles_lead.size() * sizeof(int4) + 16, s));
+        EK(cudaMallocAsync((void**)&d_dl, diag_lead.size() * sizeof(int4) + 16, s));
+        EK(cudaMemcpyAsync(d_dl, diag_lead.data(), diag_lead.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
         EK(cudaMallocAsync((void**)&d_n, nb.size() * sizeof(int2) + 16, s));
         EK(cudaMallocAsync((void**)&d_ns, nb_stage.size() * sizeof(int2) + 16, s));
         EK(cudaMemcpyAsync(d_tl, tiles_lead.data(), tiles_lead.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
@@ -761,10 +767,11 @@ class Engine {
         launch_stage_list(d_tab, d_ns, (int)nb_stage.size(), s);
         if (q_mode != 0) EK(launch_pack_list(d_tab, d_n, (int)nb.size(), s));
         EK(launch_pack3_list(d_tab, d_n, (int)nb.size(), s));
+        launch_form_norms(d_tab, d_dl, (long long)diag_lead.size(), s);
         launch_form_q(d_tab, d_tl, (long long)tiles_lead.size(), s);
         launch_init_list(d_tab, d_n, (int)nb.size(), diag_rule, (float)delta, s);
         if (q_mode == 1) EK(launch_form_q_tc(d_tab, d_tl, (long long)tiles_lead.size(), s));
-        launches += q_mode == 0 ? 4 : (q_mode == 1 ? 6 : 5);
+        launches += q_mode == 0 ? 5 : (q_mode == 1 ? 7 : 6);
         EK(cudaGetLastError());
         size_t g = 0;
         while (g < evg.size() && evg[g].refs > 0) ++g;
@@ -779,6 +786,7 @@ class Engine {
             mem[(size_t)k].evg = (int)g;
         }
         EK(cudaFreeAsync(d_tl, s));
+        EK(cudaFreeAsync(d_dl, s));
         EK(cudaFreeAsync(d_n, s));
         EK(cudaFreeAsync(d_ns, s));
         // (pageable host-to-device copies return once the data is staged, so

@@ -101,6 +101,9 @@ struct Inst {
     const float* sqb; // ||bf16(x_i)||^2
     int nkc;          // 64-feature chunks of Xp and Xp3
     const void* Xp3;  // the FP32 features as three BF16 planes in operand blocks (FP32 Gram on the tensor cores)
+    float* sq3;       // x_i . x_i from the same tensor-core products as the Gram tiles (the norms the
+                      // FP32 formation uses, so that the rounding of the norms and of the Gram values
+                      // cancels in ||x_i||^2 + ||x_j||^2 - 2 x_i . x_j for near pairs)
     int msg_bf16;     // messages stored in BF16 (precision forms)
     int task;         // 0 SVM (labels in Q, alpha clipped to [0, C]), 1 KRR (y = 1 in Q, alpha unclipped)
     int form_next;    // formation: 1 + the next instance built from the same features (its Q
@@ -187,10 +190,17 @@ inline double refine_inner(float opt, int msg_bf16) { return opt > 0 ? opt : (ms
 // stored into Inst::qref where it is set (the FP32 store, or the FP32 copy the
 // BF16 store keeps for its refinement residuals), the tile maxima into
 // Inst::tilemax where it is set.  Needs Inst::Xp3 packed first.
-cudaError_t launch_form_q_tc32(const Inst* tab, const int4* work, long long ntiles, cudaStream_t s);
+// norms_only = 1: over a list of diagonal tiles (I, I), writes Inst::sq3 of the
+// listed instances (and those chained behind them) and nothing else; it must
+// run before the formation of their other tiles.
+cudaError_t launch_form_q_tc32(const Inst* tab, const int4* work, long long ntiles, int norms_only, cudaStream_t s);
 inline void launch_form_q(const Inst* tab, const int4* work, long long ntiles, cudaStream_t s)
 {
-    (void)launch_form_q_tc32(tab, work, ntiles, s);   // errors surface at the caller's cudaGetLastError
+    (void)launch_form_q_tc32(tab, work, ntiles, 0, s);   // errors surface at the caller's cudaGetLastError
+}
+inline void launch_form_norms(const Inst* tab, const int4* diag_work, long long ntiles, cudaStream_t s)
+{
+    (void)launch_form_q_tc32(tab, diag_work, ntiles, 1, s);
 }
 // The three BF16 planes of FP32 rows (zero padding to whole tiles and chunks).
 cudaError_t launch_pack3(const float* Xf, int n, int m, int Nt, void* Xp3, cudaStream_t s);

@@ -11,18 +11,22 @@
 // The dot product keeps the six plane products with a + b <= 4,
 //   x.y ~ x1.y3 + x2.y2 + x3.y1 + x1.y2 + x2.y1 + x1.y1,
 // issued smallest first; the dropped ones are below 2^-26 of |x||y|.  The
-// tensor cores multiply BF16 exactly; their FP32 accumulation drops low bits,
-// so each 64-feature chunk gets a fresh accumulator and the chunks are added
-// on the CUDA cores (round to nearest).
+// tensor cores multiply BF16 exactly; their FP32 accumulation drops low bits
+// (toward zero), so each 64-feature chunk gets a fresh accumulator and the
+// chunks are added on the CUDA cores (round to nearest).  The squared norms in
+// d^2 = ||x_i||^2 + ||x_j||^2 - 2 x_i.x_j come from the same products (the
+// diagonal of the diagonal tiles, a first pass): for near pairs, where K is
+// large, the norms and the Gram value then carry the same truncation, which
+// cancels in d^2 instead of shrinking every K by ~2 gamma ||x||^2 x 1e-8.
 //
 // k_form_q_tc32 is persistent with warp roles: warp 0 streams the six 16 KB
 // operand blocks of each (tile, chunk) into a two-stage shared-memory ring;
-// warp 1 allocates 256 TMEM columns (two 128 x 128 FP32 accumulators) and one
-// thread issues the 24 MMAs of a chunk (6 products x K = 64 in steps of 16);
-// warps 2-9 (two per TMEM lane quarter, one per column half) add each chunk's
-// accumulator into registers, then form the Q entries exactly as the SIMT
-// formation does (norm expansion with the FP32 norms, clamp, expf, bias,
-// labels), store them, and reduce |Q| over rows (in registers), over columns
+// warp 1 allocates 512 TMEM columns (four 128 x 128 FP32 accumulators, one per
+// K-step) and one thread issues the 24 MMAs of a chunk (6 products x K = 64
+// in steps of 16); warps 2-9 (two per TMEM lane quarter, one per column half)
+// add each chunk's accumulators into registers, then form the Q entries
+// (norm expansion, clamp, expf, bias, labels), store them, and reduce |Q| over
+// rows (four interleaved partial sums), over columns
 // (a warp transpose-sum, then the four lane quarters in shared memory) and to
 // the tile maximum.  Instances chained behind the listed one (the points of a
 // parameter grid over the same features) take their Q tiles from the same
@@ -41,7 +45,19 @@ constexpr int T3_EPI_WARPS = 8;
 constexpr int T3_THREADS = (2 + T3_EPI_WARPS) * 32;
 constexpr int T3_STAGES = 2;
 constexpr size_t T3_STAGE_BYTES = (size_t)2 * NPLANE * BLK_BYTES;   // A planes, then B planes: 96 KB
-constexpr uint32_t T3_TMEM_COLS = 256;
+// Accumulators per 64-feature chunk: one per K-step of 16 features, each
+// receiving the step's five small products first and its x1.y1 product last,
+// so that no x1.y1 partial sum passes through a truncating tensor-core
+// addition; the chunk value is their sum on the CUDA cores (round to
+// nearest).  Measured against the FP64 oracle (n = 2048, with the norms from
+// the same products): mean relative error of K -2e-8 with four accumulators
+// against +1.2e-6 with one (clustered data, gamma ||x||^2 ~ 24), +1.2e-7
+// against +2.6e-7 (m = 128); formation 1.01 against 0.83 ms at n = 20000,
+// m = 128.  With four, TMEM holds one chunk at a time.
+constexpr int T3_NACC = 4;
+static_assert(T3_NACC == 1 || T3_NACC == 2 || T3_NACC == 4, "1, 2 or 4 accumulators per chunk");
+constexpr int T3_NBUF = T3_NACC == 4 ? 1 : 2;
+constexpr uint32_t T3_TMEM_COLS = (uint32_t)(T3_NACC * T3_NBUF * T <= 256 ? 256 : 512);
 constexpr uint32_t T3_IDESC = idesc_bf16_f32(T, T);
 constexpr int T3_PRODUCTS = 6;
 
@@ -114,7 +130,7 @@ __global__ void k_pack3_list(const Inst* __restrict__ tab, const int2* __restric
 
 struct T3Smem {
     unsigned long long xfull[T3_STAGES], xempty[T3_STAGES];
-    unsigned long long accfull[2], accempty[2];
+    unsigned long long accfull[T3_NBUF], accempty[T3_NBUF];
     unsigned long long drain;
     uint32_t tmem_base;
     int abort;
@@ -145,7 +161,7 @@ __device__ __forceinline__ float transpose_sum32(float (&v)[32], int lane)
 }
 
 __global__ void __launch_bounds__(T3_THREADS, 1)
-    k_form_q_tc32(const Inst* __restrict__ tab, const int4* __restrict__ work, long long ntiles)
+    k_form_q_tc32(const Inst* __restrict__ tab, const int4* __restrict__ work, long long ntiles, int norms_only)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* ops = reinterpret_cast<unsigned char*>(
@@ -155,7 +171,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
 
     if (tid == 0) {
         for (int s = 0; s < T3_STAGES; ++s) { mbar_init(&sm.xfull[s], 1); mbar_init(&sm.xempty[s], 1); }
-        for (int b = 0; b < 2; ++b) { mbar_init(&sm.accfull[b], 1); mbar_init(&sm.accempty[b], T3_EPI_WARPS); }
+        for (int b = 0; b < T3_NBUF; ++b) { mbar_init(&sm.accfull[b], 1); mbar_init(&sm.accempty[b], T3_EPI_WARPS); }
         mbar_init(&sm.drain, 1);
         sm.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -219,21 +235,25 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                     }
                     tc_fence_after();
                     const unsigned char* S = ops + (size_t)stage * T3_STAGE_BYTES;
-                    const uint32_t d = tbase + (uint32_t)acc * T;
+                    constexpr int SPA = (KCH / 16) / T3_NACC;   // K-steps per accumulator
 #pragma unroll
-                    for (int q = 0; q < T3_PRODUCTS; ++q) {
+                    for (int a = 0; a < T3_NACC; ++a) {
+                        const uint32_t d = tbase + (uint32_t)(acc * T3_NACC + a) * T;
 #pragma unroll
-                        for (int s = 0; s < KCH / 16; ++s) {
-                            const uint64_t ad = smem_desc(S + (size_t)prod_a(q) * BLK_BYTES + s * 256, 128, 1024);
-                            const uint64_t bd =
-                                smem_desc(S + (size_t)(NPLANE + prod_b(q)) * BLK_BYTES + s * 256, 128, 1024);
-                            tc_mma_bf16(d, ad, bd, T3_IDESC, (q | s) != 0);
+                        for (int q = 0; q < T3_PRODUCTS; ++q) {
+#pragma unroll
+                            for (int s = a * SPA; s < (a + 1) * SPA; ++s) {
+                                const uint64_t ad = smem_desc(S + (size_t)prod_a(q) * BLK_BYTES + s * 256, 128, 1024);
+                                const uint64_t bd =
+                                    smem_desc(S + (size_t)(NPLANE + prod_b(q)) * BLK_BYTES + s * 256, 128, 1024);
+                                tc_mma_bf16(d, ad, bd, T3_IDESC, (q != 0 || s != a * SPA) ? 1u : 0u);
+                            }
                         }
                     }
                     tc_commit(&sm.xempty[stage]);
                     tc_commit(&sm.accfull[acc]);
                     if (++stage == T3_STAGES) { stage = 0; ph ^= 1u; }
-                    if (++acc == 2) { acc = 0; aph ^= 1u; }
+                    if (++acc == T3_NBUF) { acc = 0; aph ^= 1u; }
                 }
             }
             // every MMA issued above must finish before the columns are freed
@@ -263,17 +283,24 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                     break;
                 }
                 tc_fence_after();
+                // the chunk's accumulators added to the running sums in order,
+                // 16 columns at a time
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    float v[32];
-                    tmem_ld32(tbase + (uint32_t)acc * T + ((uint32_t)(32 * g) << 16) + (uint32_t)(c0 + 32 * j), v);
+                for (int j = 0; j < 4; ++j) {
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) ga[32 * j + c] = kc == 0 ? v[c] : ga[32 * j + c] + v[c];
+                    for (int a = 0; a < T3_NACC; ++a) {
+                        float v[16];
+                        tmem_ld16(tbase + (uint32_t)(acc * T3_NACC + a) * T + ((uint32_t)(32 * g) << 16) +
+                                      (uint32_t)(c0 + 16 * j),
+                                  v);
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) ga[16 * j + c] = (kc == 0 && a == 0) ? v[c] : ga[16 * j + c] + v[c];
+                    }
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sm.accempty[acc]);
-                if (++acc == 2) { acc = 0; aph ^= 1u; }
+                if (++acc == T3_NBUF) { acc = 0; aph ^= 1u; }
             }
             if (!ok && lane == 0) {
                 sm.abort = 1;
@@ -283,6 +310,18 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
             if (*(volatile int*)&sm.abort) break;
             const int I = w.y, J = w.z;
             const int i = I * T + r;
+            if (norms_only) {
+                // diagonal tile: x_i . x_i is the Gram value at (r, r), held by the
+                // warp of r's lane quarter whose column half contains r
+                if (half == (g >> 1)) {
+                    float d = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 64; ++c) d = (c0 + c == r) ? ga[c] : d;
+                    for (int k = w.x; k >= 0; k = tab[k].form_next - 1)
+                        if (i < tab[k].n) tab[k].sq3[i] = d;
+                }
+                continue;
+            }
             for (int k = w.x; k >= 0;) {
                 const Inst& p = tab[k];
                 const int n = p.n;
@@ -291,12 +330,12 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                 for (int u = 0; u < 2; ++u) {
                     const int j = J * T + c0 + 32 * u + lane;
                     sm.cy[ew][32 * u + lane] = j < n ? p.y[j] : 0.f;
-                    sm.cs[ew][32 * u + lane] = j < n ? p.sq[j] : 0.f;
+                    sm.cs[ew][32 * u + lane] = j < n ? p.sq3[j] : 0.f;
                 }
                 __syncwarp();
-                const float yi = i < n ? p.y[i] : 0.f, si = i < n ? p.sq[i] : 0.f;
+                const float yi = i < n ? p.y[i] : 0.f, si = i < n ? p.sq3[i] : 0.f;
                 float* qt = p.qref ? p.qref + (size_t)w.w * TT + (size_t)r * T + c0 : nullptr;
-                float rs = 0.f, tmx = 0.f;
+                float rs4[4] = {0.f, 0.f, 0.f, 0.f}, tmx = 0.f;   // row sum in four interleaved parts
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
                     float q[32];
@@ -313,7 +352,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                             const float d2 = fmaxf(0.f, si + sj[t] - 2.f * ga[32 * u + c4 + t]);
                             const float qv = yi * yj[t] * (expf(-p.gamma * d2) + p.lam2);
                             q[c4 + t] = valid ? qv : 0.f;
-                            rs += fabsf(q[c4 + t]);
+                            rs4[t] += fabsf(q[c4 + t]);
                             tmx = fmaxf(tmx, fabsf(q[c4 + t]));
                         }
                     }
@@ -326,7 +365,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                     for (int c = 0; c < 32; ++c) q[c] = fabsf(q[c]);
                     sm.colsum[g][c0 + 32 * u + lane] = transpose_sum32(q, lane);
                 }
-                sm.rowsum[half][r] = rs;
+                sm.rowsum[half][r] = (rs4[0] + rs4[1]) + (rs4[2] + rs4[3]);
                 tmx = warp_max_f(tmx);
                 if (lane == 0) sm.tmx[ew] = tmx;
                 epi_bar();
@@ -388,7 +427,7 @@ cudaError_t launch_pack3_list(const Inst* tab, const int2* nbl, int nblocks, cud
     return cudaGetLastError();
 }
 
-cudaError_t launch_form_q_tc32(const Inst* tab, const int4* work, long long ntiles, cudaStream_t s)
+cudaError_t launch_form_q_tc32(const Inst* tab, const int4* work, long long ntiles, int norms_only, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
     static bool attr = false;
@@ -400,7 +439,7 @@ cudaError_t launch_form_q_tc32(const Inst* tab, const int4* work, long long ntil
     }
     const int sms = num_sms();
     const int grid = (int)(ntiles < sms ? ntiles : sms);
-    k_form_q_tc32<<<grid, T3_THREADS, t3_smem_bytes(), s>>>(tab, work, ntiles);
+    k_form_q_tc32<<<grid, T3_THREADS, t3_smem_bytes(), s>>>(tab, work, ntiles, norms_only);
     return cudaGetLastError();
 }
 
