@@ -51,6 +51,31 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 void gabp::set_last_error(const char* msg) { g_err = msg; }
 
+cudaError_t gabp::device_available(size_t* avail, bool trim)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaMemPool_t pool;
+    e = cudaDeviceGetDefaultMemPool(&pool, dev);
+    if (e != cudaSuccess) return e;
+    if (trim) {
+        e = cudaMemPoolTrimTo(pool, 0);
+        if (e != cudaSuccess) return e;
+    }
+    size_t free_b = 0, total_b = 0;
+    e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) return e;
+    uint64_t reserved = 0, used = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) != cudaSuccess ||
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess) {
+        cudaGetLastError();
+        reserved = used = 0;
+    }
+    *avail = free_b + (reserved > used ? (size_t)(reserved - used) : 0);
+    return cudaSuccess;
+}
+
 int gabp::fault_mask()
 {
     const char* v = std::getenv("GABP_FAULT");
@@ -256,8 +281,8 @@ gabp_status ensure_pair_storage(gabp_svm_t h)
         if (h->spool) CK(cudaFree(h->spool));
         h->spool = nullptr;
         h->spool_bytes = 0;
-        size_t free_b = 0, total_b = 0;
-        CK(cudaMemGetInfo(&free_b, &total_b));
+        size_t free_b = 0;
+        CK(device_available(&free_b, true));   // cudaMalloc below: the pool's unused memory back first
         const size_t margin = (size_t)256 << 20;
         if (need + margin > free_b)
             return fail(GABP_ENOMEM, "the %lld kept tiles need %.2f GB of device memory, %.2f GB free",
@@ -598,8 +623,8 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     h->nstages = o.stages > 1 ? o.stages : 1;
 
     const Plan pl = make_plan(n, m, h->Nt, h->ntiles, h->npad, o.q_mode, o.msg_bf16, o.sparse_tau > 0);
-    size_t free_b = 0, total_b = 0;
-    e = cudaMemGetInfo(&free_b, &total_b);
+    size_t free_b = 0;
+    e = device_available(&free_b, true);   // cudaMalloc below: the pool's unused memory back first
     if (e != cudaSuccess) { destroy_all(h); return fail(GABP_ECUDA, "cudaMemGetInfo: %s", cudaGetErrorString(e)); }
     const size_t margin = (size_t)256 << 20;
     if (pl.total + margin > free_b) {

@@ -1223,8 +1223,8 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
         set_last_error("no CUDA device");
         return GABP_ECUDA;
     }
-    size_t free_b = 0, total_b = 0;
-    cudaMemGetInfo(&free_b, &total_b);
+    size_t free_b = 0;
+    device_available(&free_b, false);   // instance memory comes from the stream-ordered pool
     if (bytes + ((size_t)512 << 20) > free_b) {
         set_last_error(("gabp_batch_solve: needs " + std::to_string(bytes / 1e9) + " GB of device memory").c_str());
         return GABP_ENOMEM;
@@ -1376,8 +1376,8 @@ gabp_status gabp_server_create(const gabp_server_cfg* cfg, gabp_server_t* out)
     if (c.opts.diag_delta == 0) c.opts.diag_delta = 0.1;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) { set_last_error("no CUDA device"); return GABP_ECUDA; }
-    size_t free_b = 0, total_b = 0;
-    cudaMemGetInfo(&free_b, &total_b);
+    size_t free_b = 0;
+    device_available(&free_b, false);   // instance memory comes from the stream-ordered pool
     size_t budget = c.hbm_budget_bytes > 0 ? (size_t)c.hbm_budget_bytes : (size_t)(0.8 * (double)free_b);
     if (budget + ((size_t)1 << 30) > free_b) budget = free_b > ((size_t)2 << 30) ? free_b - ((size_t)2 << 30) : 0;
     // list capacities: every tile of state costs TT * 16 bytes, so the budget bounds them

@@ -266,6 +266,12 @@ cudaError_t launch_selftest_rcp(const float* d, float* out, int cnt, cudaStream_
 cudaError_t launch_selftest_wait(unsigned long long limit_ns, int* status_dev, cudaStream_t s);
 // Sets the thread-local message returned by gabp_last_error().
 void set_last_error(const char* msg);
+// Device memory available to the library: cudaMemGetInfo's free bytes plus
+// what the device's default stream-ordered pool holds reserved but unused
+// (instance memory of the batched and served forms goes back to that pool and
+// stays reserved for reuse).  trim = true first returns the pool's unused
+// memory to the device (for plain cudaMalloc callers).
+cudaError_t device_available(size_t* avail, bool trim);
 // Host-side fault injection for tests of the failure paths: the environment
 // variable GABP_FAULT holds comma-separated tokens, read at each public call:
 //   alloc    the call's device allocation fails (create, batch, server admission)
