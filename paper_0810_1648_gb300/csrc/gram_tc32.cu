@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                 } else if (etid < T) {
                     const int x = I * T + etid;
                     if (x < n) part[(size_t)J * n + x] = sm.rowsum[0][etid] + sm.rowsum[1][etid];
-                } else {
+                } else if (etid < 2 * T) {
                     const int c = etid - T, x = J * T + c;
                     if (x < n)
                         part[(size_t)I * n + x] =

@@ -73,6 +73,17 @@ constexpr int STAGES = 4;                     // barrier slots of the stage ring
 template <class MSG>
 __host__ __device__ constexpr int stages() { return MSG::NSTAGE; }
 constexpr int SWEEP_THREADS = NTHREADS + 32;  // + one producer warp
+// 1/d for the cavity precisions: the hardware approximate reciprocal
+// refined by one Newton-Raphson step r <- r (2 - d r) (error within about one
+// unit in the last place for normal positive d; checked against IEEE division
+// by gabp_selftest_reciprocal).
+__device__ __forceinline__ float rcp_nr(float d)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+    return fmaf(r, fmaf(-d, r, 1.0f), r);
+}
+
 // Message storage: FP32 pairs (plain and precision forms) or BF16 pairs
 // (precision forms with refinement).  Arithmetic is FP32 either way; sums use
 // the stored (rounded) values so that the aggregates match the messages the
@@ -82,6 +93,10 @@ struct MsgF32 {
     static __device__ __forceinline__ T2 pack(float a, float b) { return make_float2(a, b); }
     static __device__ __forceinline__ float2 unpack(T2 v) { return v; }
     static __device__ __forceinline__ bool same(T2 a, T2 b) { return (a.x == b.x) & (a.y == b.y); }
+    // 1/q of the frozen-P update: the refined reciprocal; 0 for |q| below the
+    // smallest normal float, where P = -q^2 / d is 0 (the reciprocal of a
+    // flushed subnormal would be inf, and 0 * inf a NaN)
+    static __device__ __forceinline__ float qinv(float q) { return fabsf(q) >= FLT_MIN ? rcp_nr(q) : 0.f; }
     // a lane's pairs of a row: columns 2 lane + {0, 1} and 64 + 2 lane + {0, 1}
     // (each access of the warp is one contiguous 512-byte span)
     static constexpr int G = 2;
@@ -114,6 +129,16 @@ struct MsgBF16 {
         return make_float2(__uint_as_float(v << 16), __uint_as_float(v & 0xffff0000u));
     }
     static __device__ __forceinline__ bool same(T2 a, T2 b) { return a == b; }
+    // 1/q of the frozen-P update: the hardware reciprocal alone (its error,
+    // about 2^-23, vanishes in the BF16 rounding of the stored H), clamped to
+    // +-3e38 so that |q| below the smallest normal float (flushed: inf) gives a
+    // finite factor of P = 0
+    static __device__ __forceinline__ float qinv(float q)
+    {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(q));
+        return fmaxf(fminf(r, 3.0e38f), -3.0e38f);
+    }
     // a lane's pairs of a row: columns 4 lane + {0 .. 3} (16 bytes; each
     // access of the warp is one contiguous 512-byte span)
     static constexpr int G = 4;
@@ -316,17 +341,6 @@ __device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, con
     }
 }
 
-// 1/d for the cavity precisions: the hardware approximate reciprocal
-// refined by one Newton-Raphson step r <- r (2 - d r) (error within about one
-// unit in the last place for normal positive d; checked against IEEE division
-// by gabp_selftest_reciprocal).
-__device__ __forceinline__ float rcp_nr(float d)
-{
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
-    return fmaf(r, fmaf(-d, r, 1.0f), r);
-}
-
 // Column slot k = 0..3 of a lane in a 128-column row: G consecutive columns
 // in each of 4 / G groups of 32 G columns (G = 2 for FP32 messages, 4 for
 // BF16 messages), so that every warp access to a row is contiguous.
@@ -471,12 +485,11 @@ __device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char
         // reciprocal per pair, no cavity subtraction (the cavities were
         // checked when these P values were formed).  For |q| below the
         // smallest normal float (q = 0, or an RBF value exp(-gamma d^2) that
-        // underflowed to a subnormal) q^2 is 0, so P = 0 and H is taken as 0:
-        // the hardware reciprocal would flush such a q and give inf, and
-        // 0 * inf a NaN.
+        // underflowed to a subnormal) q^2 is 0, so P = 0 and H comes out 0
+        // (MSG::qinv keeps the factor finite).
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const float qi = fabsf(q[k]) >= FLT_MIN ? rcp_nr(q[k]) : 0.f;
+            const float qi = MSG::qinv(q[k]);
             nw[k] = MSG::pack(pv[k].x * (rH - hv[k].y) * qi, pv[k].y * (cv.H[k] - hv[k].x) * qi);
         }
     } else {
