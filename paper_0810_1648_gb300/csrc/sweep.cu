@@ -412,12 +412,13 @@ __device__ __forceinline__ float reduce_scatter8(float a0, float a1, float a2, f
     return v;
 }
 
-// Sums the four values {a0, a1, a2, 0} over the warp in a fixed order:
+// Sums the four values {a0, a1, a2, a3} over the warp in a fixed order:
 // afterwards every lane of the group (lane / 8) % 4 = k holds the total of
-// value k (six shuffles for one row).
-__device__ __forceinline__ float reduce_scatter4(float a0, float a1, float a2, int lane)
+// value k (six shuffles: the three sums of one row, or the H and residual
+// sums of two rows once P is frozen).
+__device__ __forceinline__ float reduce_scatter4(float a0, float a1, float a2, float a3, int lane)
 {
-    const float x[4] = {a0, a1, a2, 0.f};
+    const float x[4] = {a0, a1, a2, a3};
     const bool hi = (lane & 16) != 0;
     float y[2];
 #pragma unroll
@@ -437,12 +438,22 @@ struct ColVals {
     float aP[4], aH[4], aR[4];   // column partial sums
 };
 
+// Two-wide FP32 arithmetic (one instruction for two lanes of values; each
+// half rounds exactly as the scalar operation would).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// c - b, bitwise equal to the scalar subtraction (the product -1 * b is exact)
+__device__ __forceinline__ float2 sub2(float2 c, float2 b) { return __ffma2_rn(make_float2(-1.f, -1.f), b, c); }
+
 // Updates the lane's four pairs (r, lane_col(lane, k)) of chunk row r held in
 // shared memory.  FULL: interior tile, every column valid (no
 // predicates); FROZEN: the P messages are at their fixed point (no P stores,
 // no P sums).  Adds the lane's share of the row sums to rs[0..2] (P, H,
 // residual).  Whole 4-pair groups are stored: on diagonal and edge tiles the
 // slots outside the pair set are never read, so writing them is harmless.
+// The arithmetic runs on the column pairs {0, 1} and {2, 3} two at a time; a
+// lane's row sums add columns {0, 2} and {1, 3} first, then the two halves.
 template <bool FULL, bool FROZEN, class MSG, class QSrc>
 __device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char* S, int lr, int lane, int r,
                                            int cols, bool diag, int it, bool zero, bool zero_h, float rP,
@@ -471,6 +482,7 @@ __device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char
 #pragma unroll
         for (int k = 0; k < 4; ++k) pv[k] = MSG::unpack(pw[k]);
     }
+    const float2 rH2 = make_float2(rH, rH);
     if (FROZEN) {
         if (zero_h) {
 #pragma unroll
@@ -488,14 +500,20 @@ __device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char
         // underflowed to a subnormal) q^2 is 0, so P = 0 and H comes out 0
         // (MSG::qinv keeps the factor finite).
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float qi = MSG::qinv(q[k]);
-            nw[k] = MSG::pack(pv[k].x * (rH - hv[k].y) * qi, pv[k].y * (cv.H[k] - hv[k].x) * qi);
+        for (int k = 0; k < 4; k += 2) {
+            const float2 qi = make_float2(MSG::qinv(q[k]), MSG::qinv(q[k + 1]));
+            const float2 dr = sub2(rH2, make_float2(hv[k].y, hv[k + 1].y));              // htilde_i - H_ji
+            const float2 dc = sub2(make_float2(cv.H[k], cv.H[k + 1]), make_float2(hv[k].x, hv[k + 1].x));
+            const float2 hx = mul2(mul2(make_float2(pv[k].x, pv[k + 1].x), dr), qi);   // H_ij
+            const float2 hy = mul2(mul2(make_float2(pv[k].y, pv[k + 1].y), dc), qi);   // H_ji
+            nw[k] = MSG::pack(hx.x, hy.x);
+            nw[k + 1] = MSG::pack(hx.y, hy.y);
         }
     } else {
         float2 inv[4];
         {
             T2 npw[4];
+            float2 sp = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const float di = rP - pv[k].y;        // cavity Ptilde_i - P_ji
@@ -504,14 +522,21 @@ __device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char
                 inv[k] = make_float2(rcp_nr(di), rcp_nr(dj));
                 const float q2 = q[k] * q[k];
                 npw[k] = MSG::pack(-q2 * inv[k].x, -q2 * inv[k].y);
-                if (v[k]) {
-                    const float2 np = MSG::unpack(npw[k]);
-                    changed |= !MSG::same(npw[k], pw[k]);
-                    rs[0] += np.y;
-                    cv.aP[k] += np.x;
-                }
+                changed |= v[k] & !MSG::same(npw[k], pw[k]);
             }
             MSG::store4(gp + r * T, lane, npw);
+#pragma unroll
+            for (int k = 0; k < 4; k += 2) {
+                float2 a = MSG::unpack(npw[k]), b = MSG::unpack(npw[k + 1]);
+                if (!FULL) {
+                    if (!v[k]) a = make_float2(0.f, 0.f);
+                    if (!v[k + 1]) b = make_float2(0.f, 0.f);
+                }
+                sp = add2(sp, make_float2(a.y, b.y));
+                const float2 ap = add2(make_float2(cv.aP[k], cv.aP[k + 1]), make_float2(a.x, b.x));
+                cv.aP[k] = ap.x; cv.aP[k + 1] = ap.y;
+            }
+            rs[0] += sp.x + sp.y;
         }
         if (zero || zero_h) {
 #pragma unroll
@@ -526,16 +551,33 @@ __device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char
             nw[k] = MSG::pack(-q[k] * (rH - hv[k].y) * inv[k].x, -q[k] * (cv.H[k] - hv[k].x) * inv[k].y);
     }
     MSG::store4(gh + r * T, lane, nw);
+    // sums over the valid pairs: H into the row / column sums, q mu of the
+    // other end into the residual sums
+#pragma unroll
+    for (int k = 0; k < 4; ++k) nh[k] = MSG::unpack(nw[k]);
+    // (slots outside the pair set add zeros; their column aggregates may lie
+    // beyond n and are not read)
+    float qv[4], mv[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        if (v[k]) {
-            nh[k] = MSG::unpack(nw[k]);
-            rs[1] += nh[k].y;
-            rs[2] = fmaf(q[k], cv.M[k], rs[2]);
-            cv.aH[k] += nh[k].x;
-            cv.aR[k] = fmaf(q[k], rM, cv.aR[k]);
-        }
+        qv[k] = q[k];
+        mv[k] = cv.M[k];
+        if (!FULL && !v[k]) { nh[k] = make_float2(0.f, 0.f); qv[k] = 0.f; mv[k] = 0.f; }
     }
+    const float2 rM2 = make_float2(rM, rM);
+    float2 sh = make_float2(0.f, 0.f), sr = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 4; k += 2) {
+        const float2 q01 = make_float2(qv[k], qv[k + 1]);
+        sh = add2(sh, make_float2(nh[k].y, nh[k + 1].y));
+        sr = fma2(q01, make_float2(mv[k], mv[k + 1]), sr);
+        const float2 ah = add2(make_float2(cv.aH[k], cv.aH[k + 1]), make_float2(nh[k].x, nh[k + 1].x));
+        const float2 ar = fma2(q01, rM2, make_float2(cv.aR[k], cv.aR[k + 1]));
+        cv.aH[k] = ah.x; cv.aH[k + 1] = ah.y;
+        cv.aR[k] = ar.x; cv.aR[k + 1] = ar.y;
+    }
+    rs[1] += sh.x + sh.y;
+    rs[2] += sr.x + sr.y;
 }
 
 // Per-tile constants of one consumer warp.
@@ -594,13 +636,18 @@ __device__ __forceinline__ void consume_tile(const QSrc& qsrc, SweepTail<CW>& sm
         if (lane == 0) mbar_arrive(&sm.empty[stage]);
         if (++stage == stages<MSG>()) { stage = 0; phase ^= 1u; }
         // row sums {P, H, R} of the warp's rows over the warp
-        if constexpr (RPW == 2) {
+        if constexpr (RPW == 2 && FROZEN) {
+            // the P sums of a frozen round are not needed
+            const float v = reduce_scatter4(rs[0][1], rs[0][2], rs[RPW - 1][1], rs[RPW - 1][2], lane);
+            const int qi = (lane >> 3) & 3, r = ch * RC + cw + CW * (qi >> 1);
+            if ((lane & 7) == 0 && r < rows) ((qi & 1) ? sm.rr : sm.rh)[r] = v;
+        } else if constexpr (RPW == 2) {
             const float v = reduce_scatter8(rs[0][0], rs[0][1], rs[0][2], rs[RPW - 1][0], rs[RPW - 1][1],
                                             rs[RPW - 1][2], lane);
             const int qi = (lane >> 2) & 7, qv = qi & 3, r = ch * RC + cw + CW * (qi >> 2);
             if ((lane & 3) == 0 && qv < 3 && r < rows) (qv == 0 ? sm.rp : (qv == 1 ? sm.rh : sm.rr))[r] = v;
         } else {
-            const float v = reduce_scatter4(rs[0][0], rs[0][1], rs[0][2], lane);
+            const float v = reduce_scatter4(rs[0][0], rs[0][1], rs[0][2], 0.f, lane);
             const int qv = (lane >> 3) & 3, r = ch * RC + cw;
             if ((lane & 7) == 0 && qv < 3 && r < rows) (qv == 0 ? sm.rp : (qv == 1 ? sm.rh : sm.rr))[r] = v;
         }
