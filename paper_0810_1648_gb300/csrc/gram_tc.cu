@@ -117,7 +117,7 @@ struct TcSmem {
     unsigned long long drain;
     uint32_t tmem_base;
     int abort;
-    ColChunk cols[TC_EPI_WARPS];   // column constants, one chunk per epilogue warp
+    ColTile cols[TC_EPI_WARPS];    // column constants of the current tile, one set per epilogue warp
 };
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -237,20 +237,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int i = I * T + r;
             // the listed instance and every one chained behind it (same
             // features) take their BF16 Q tile from this accumulator
-            ColChunk& cs = sm.cols[warp - 2];
+            ColTile& cs = sm.cols[warp - 2];
             for (int k = w.x; k >= 0;) {
                 const Inst& p = tab[k];
                 const int n = p.n;
+                const float* y = p.y;
                 const float* sqb = p.sqb;
-                const float yi = i < n ? p.y[i] : 0.f, si = i < n ? sqb[i] : 0.f;
-                const float ai = -p.gamma * kLog2e * si, c2 = 2.f * p.gamma * kLog2e;
-                const uint32_t syi = __float_as_uint(yi) & 0x80000000u;
+                const float gamma = p.gamma, lam2 = p.lam2;
+                const float yi = i < n ? y[i] : 0.f, si = i < n ? sqb[i] : 0.f;
+                stage_tile_cols(cs, y, sqb, n, J, gamma, lane, 2 * half, 2 * half + 2);
+                const float ai = -gamma * kLog2e * si, c2 = 2.f * gamma * kLog2e;
+                const uint32_t s1 = __float_as_uint(yi) & 0x80000000u, si2 = s1 | (s1 >> 16);
                 __nv_bfloat16* qrow = static_cast<__nv_bfloat16*>(p.qstore) + (size_t)w.w * TT + (size_t)r * T;
 #pragma unroll 1
                 for (int cc = 2 * half; cc < 2 * half + 2; ++cc) {
-                    const int jl = J * T + 32 * cc + lane;
-                    const float yl = jl < n ? p.y[jl] : 0.f, sl = jl < n ? sqb[jl] : 0.f;
-                    stage_cols(cs, yl, sl, p.gamma, lane);
                     const uint32_t valid = chunk_valid(n, I, J, r, cc);
                     uint4* dst = reinterpret_cast<uint4*>(qrow + 32 * cc);
 #pragma unroll
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         tmem_ld16(tbase + (uint32_t)acc * T + ((uint32_t)(32 * g) << 16) + (uint32_t)(32 * cc + 16 * h),
                                   v);
                         uint4 out[2];
-                        q_half_bf16(v, 16 * h, ai, syi, cs, c2, p.lam2, valid, out);
+                        q_half_bf16(v, 32 * cc + 16 * h, ai, si2, cs, c2, lam2, (valid >> (16 * h)) & 0xffffu, out);
                         dst[2 * h] = out[0];
                         dst[2 * h + 1] = out[1];
                     }

@@ -90,6 +90,7 @@ __device__ __forceinline__ float rcp_nr(float d)
 // next round reads.
 struct MsgF32 {
     using T2 = float2;
+    static constexpr bool MIXED = false;   // no BF16 halves to read directly
     static __device__ __forceinline__ T2 pack(float a, float b) { return make_float2(a, b); }
     static __device__ __forceinline__ float2 unpack(T2 v) { return v; }
     static __device__ __forceinline__ bool same(T2 a, T2 b) { return (a.x == b.x) & (a.y == b.y); }
@@ -97,10 +98,13 @@ struct MsgF32 {
     // smallest normal float, where P = -q^2 / d is 0 (the reciprocal of a
     // flushed subnormal would be inf, and 0 * inf a NaN)
     static __device__ __forceinline__ float qinv(float q) { return fabsf(q) >= FLT_MIN ? rcp_nr(q) : 0.f; }
+    // the same where |q| >= FLT_MIN is known (no guard)
+    static __device__ __forceinline__ float qinv_normal(float q) { return rcp_nr(q); }
     // a lane's pairs of a row: columns 2 lane + {0, 1} and 64 + 2 lane + {0, 1}
     // (each access of the warp is one contiguous 512-byte span)
     static constexpr int G = 2;
     static constexpr int NSTAGE = 2;   // ring stages of 16 rows (40 KB with FP32 Q)
+    static constexpr int SPC = 1;      // stages per row-sum reduction
     // diagonal and edge tiles: only the owned pairs of each row are copied
     // (one copy per row; the form is bandwidth bound, so bytes count)
     static constexpr bool WHOLE_ROWS = false;
@@ -119,6 +123,30 @@ struct MsgF32 {
 };
 struct MsgBF16 {
     using T2 = unsigned;   // two BF16 values, the first in the low half
+    // Mixed-precision arithmetic reads a BF16 half of a stored word as an FP32
+    // operand (exact widening) in the same instruction, with no unpacking:
+    // lo_minus / hi_minus = half - c, add_lo / add_hi: s += half.
+    static constexpr bool MIXED = true;
+    static __device__ __forceinline__ float lo_minus(T2 w, float c)
+    {
+        float d;
+        asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %1;\n\tsub.rn.f32.bf16 %0, l, %2;\n\t}" : "=f"(d) : "r"(w), "f"(c));
+        return d;
+    }
+    static __device__ __forceinline__ float hi_minus(T2 w, float c)
+    {
+        float d;
+        asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %1;\n\tsub.rn.f32.bf16 %0, h, %2;\n\t}" : "=f"(d) : "r"(w), "f"(c));
+        return d;
+    }
+    static __device__ __forceinline__ void add_lo(float& s, T2 w)
+    {
+        asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %1;\n\tadd.rn.f32.bf16 %0, l, %0;\n\t}" : "+f"(s) : "r"(w));
+    }
+    static __device__ __forceinline__ void add_hi(float& s, T2 w)
+    {
+        asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %1;\n\tadd.rn.f32.bf16 %0, h, %0;\n\t}" : "+f"(s) : "r"(w));
+    }
     static __device__ __forceinline__ T2 pack(float a, float b)
     {
         const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -139,10 +167,20 @@ struct MsgBF16 {
         asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(q));
         return fmaxf(fminf(r, 3.0e38f), -3.0e38f);
     }
+    // the same where |q| >= FLT_MIN is known (no clamp)
+    static __device__ __forceinline__ float qinv_normal(float q)
+    {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(q));
+        return r;
+    }
     // a lane's pairs of a row: columns 4 lane + {0 .. 3} (16 bytes; each
     // access of the warp is one contiguous 512-byte span)
     static constexpr int G = 4;
     static constexpr int NSTAGE = 4;   // ring stages of 16 rows (20 KB with BF16 Q)
+    // two stages per row-sum reduction (four rows per consumer warp): half the
+    // shuffles of this instruction-bound form per pair
+    static constexpr int SPC = 2;
     // diagonal and edge tiles also move 16 whole rows per copy (the unowned
     // entries are masked by the consumers): sixteen times fewer bulk copies
     // for a few percent more bytes, faster for this instruction-heavy form
@@ -178,6 +216,7 @@ struct TileInfo {
     long long L;        // work-list index (error records)
     int n, Nt, I, J;
     int t, zero_h, frozen, end;
+    int qnormal;        // every off-diagonal |q| >= FLT_MIN (lambda^2 >= 2 FLT_MIN)
 };
 
 // Shared state of the producer and the CW consumer warps.
@@ -273,6 +312,9 @@ __device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, con
             ti.t = t;
             ti.zero_h = *(volatile const int*)&ctrl->zero_h;
             ti.frozen = *(volatile const int*)&ctrl->p_frozen;
+            // q = +-(K + lambda^2) with K >= 0: |q| >= lambda^2, also after the
+            // rounding of a BF16 store
+            ti.qnormal = p.lam2 >= 2.f * FLT_MIN;
             ti.end = 0;
             mbar_arrive_expect_tx(&sm.tfull[slot], 6 * T * sizeof(float));
         }
@@ -391,10 +433,16 @@ __device__ __forceinline__ void st4(float* row, int lane, const float (&o)[4])
 // Sums the eight values {a0, a1, a2, 0, b0, b1, b2, 0} over the warp in a
 // fixed order: afterwards every lane of the group (lane / 4) % 8 = k holds the
 // total of value k (nine shuffles for two rows).
+__device__ __forceinline__ float reduce_scatter8x(const float (&x)[8], int lane);
 __device__ __forceinline__ float reduce_scatter8(float a0, float a1, float a2, float b0, float b1, float b2,
                                                  int lane)
 {
     const float x[8] = {a0, a1, a2, 0.f, b0, b1, b2, 0.f};
+    return reduce_scatter8x(x, lane);
+}
+// The same for eight values {x0 .. x7}.
+__device__ __forceinline__ float reduce_scatter8x(const float (&x)[8], int lane)
+{
     const bool hi = (lane & 16) != 0;
     float y[4];
 #pragma unroll
@@ -454,7 +502,7 @@ __device__ __forceinline__ float2 sub2(float2 c, float2 b) { return __ffma2_rn(m
 // slots outside the pair set are never read, so writing them is harmless.
 // The arithmetic runs on the column pairs {0, 1} and {2, 3} two at a time; a
 // lane's row sums add columns {0, 2} and {1, 3} first, then the two halves.
-template <bool FULL, bool FROZEN, class MSG, class QSrc>
+template <bool FULL, bool FROZEN, bool QN, class MSG, class QSrc>
 __device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char* S, int lr, int lane, int r,
                                            int cols, bool diag, int it, bool zero, bool zero_h, float rP,
                                            float rH, float rM, ColVals& cv, typename MSG::T2* __restrict__ gp,
@@ -473,7 +521,7 @@ __device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char
         v[k] = FULL || (c < cols && (!diag || c > r));
     }
     T2 pw[4], hw[4], nw[4];   // stored words
-    float2 pv[4], hv[4], nh[4];
+    float2 pv[4], hv[4];
     if (zero) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) { pw[k] = MSG::pack(0.f, 0.f); pv[k] = make_float2(0.f, 0.f); }
@@ -486,11 +534,13 @@ __device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char
     if (FROZEN) {
         if (zero_h) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) hv[k] = make_float2(0.f, 0.f);
+            for (int k = 0; k < 4; ++k) { hw[k] = MSG::pack(0.f, 0.f); hv[k] = make_float2(0.f, 0.f); }
         } else {
             MSG::load4(Sh, lane, hw);                           // {H_ij, H_ji}
+            if constexpr (!MSG::MIXED) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) hv[k] = MSG::unpack(hw[k]);
+                for (int k = 0; k < 4; ++k) hv[k] = MSG::unpack(hw[k]);
+            }
         }
         // With P at its fixed point, P_ij = -q^2 / d_i, so the H update
         // -q (htilde_i - H_ji) / d_i equals P_ij (htilde_i - H_ji) / q: one
@@ -501,11 +551,23 @@ __device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char
         // (MSG::qinv keeps the factor finite).
 #pragma unroll
         for (int k = 0; k < 4; k += 2) {
-            const float2 qi = make_float2(MSG::qinv(q[k]), MSG::qinv(q[k + 1]));
-            const float2 dr = sub2(rH2, make_float2(hv[k].y, hv[k + 1].y));              // htilde_i - H_ji
-            const float2 dc = sub2(make_float2(cv.H[k], cv.H[k + 1]), make_float2(hv[k].x, hv[k + 1].x));
-            const float2 hx = mul2(mul2(make_float2(pv[k].x, pv[k + 1].x), dr), qi);   // H_ij
-            const float2 hy = mul2(mul2(make_float2(pv[k].y, pv[k + 1].y), dc), qi);   // H_ji
+            float2 hx, hy;   // new H_ij, H_ji
+            if constexpr (MSG::MIXED) {
+                // P (H_ji - htilde_i) (-1 / q): the same value, read from the BF16 halves
+                const float2 nqi = QN ? make_float2(MSG::qinv_normal(-q[k]), MSG::qinv_normal(-q[k + 1]))
+                                      : make_float2(MSG::qinv(-q[k]), MSG::qinv(-q[k + 1]));
+                const float2 er = make_float2(MSG::hi_minus(hw[k], rH), MSG::hi_minus(hw[k + 1], rH));
+                const float2 ec = make_float2(MSG::lo_minus(hw[k], cv.H[k]), MSG::lo_minus(hw[k + 1], cv.H[k + 1]));
+                hx = mul2(mul2(make_float2(pv[k].x, pv[k + 1].x), er), nqi);
+                hy = mul2(mul2(make_float2(pv[k].y, pv[k + 1].y), ec), nqi);
+            } else {
+                const float2 qi = QN ? make_float2(MSG::qinv_normal(q[k]), MSG::qinv_normal(q[k + 1]))
+                                     : make_float2(MSG::qinv(q[k]), MSG::qinv(q[k + 1]));
+                const float2 dr = sub2(rH2, make_float2(hv[k].y, hv[k + 1].y));              // htilde_i - H_ji
+                const float2 dc = sub2(make_float2(cv.H[k], cv.H[k + 1]), make_float2(hv[k].x, hv[k + 1].x));
+                hx = mul2(mul2(make_float2(pv[k].x, pv[k + 1].x), dr), qi);
+                hy = mul2(mul2(make_float2(pv[k].y, pv[k + 1].y), dc), qi);
+            }
             nw[k] = MSG::pack(hx.x, hy.x);
             nw[k + 1] = MSG::pack(hx.y, hy.y);
         }
@@ -553,27 +615,35 @@ __device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char
     MSG::store4(gh + r * T, lane, nw);
     // sums over the valid pairs: H into the row / column sums, q mu of the
     // other end into the residual sums
-#pragma unroll
-    for (int k = 0; k < 4; ++k) nh[k] = MSG::unpack(nw[k]);
     // (slots outside the pair set add zeros; their column aggregates may lie
     // beyond n and are not read)
     float qv[4], mv[4];
+    T2 nwv[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         qv[k] = q[k];
         mv[k] = cv.M[k];
-        if (!FULL && !v[k]) { nh[k] = make_float2(0.f, 0.f); qv[k] = 0.f; mv[k] = 0.f; }
+        nwv[k] = nw[k];
+        if (!FULL && !v[k]) { nwv[k] = MSG::pack(0.f, 0.f); qv[k] = 0.f; mv[k] = 0.f; }
     }
     const float2 rM2 = make_float2(rM, rM);
     float2 sh = make_float2(0.f, 0.f), sr = make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < 4; k += 2) {
         const float2 q01 = make_float2(qv[k], qv[k + 1]);
-        sh = add2(sh, make_float2(nh[k].y, nh[k + 1].y));
+        if constexpr (MSG::MIXED) {
+            MSG::add_hi(sh.x, nwv[k]);
+            MSG::add_hi(sh.y, nwv[k + 1]);
+            MSG::add_lo(cv.aH[k], nwv[k]);
+            MSG::add_lo(cv.aH[k + 1], nwv[k + 1]);
+        } else {
+            const float2 n0 = MSG::unpack(nwv[k]), n1 = MSG::unpack(nwv[k + 1]);
+            sh = add2(sh, make_float2(n0.y, n1.y));
+            const float2 ah = add2(make_float2(cv.aH[k], cv.aH[k + 1]), make_float2(n0.x, n1.x));
+            cv.aH[k] = ah.x; cv.aH[k + 1] = ah.y;
+        }
         sr = fma2(q01, make_float2(mv[k], mv[k + 1]), sr);
-        const float2 ah = add2(make_float2(cv.aH[k], cv.aH[k + 1]), make_float2(nh[k].x, nh[k + 1].x));
         const float2 ar = fma2(q01, rM2, make_float2(cv.aR[k], cv.aR[k + 1]));
-        cv.aH[k] = ah.x; cv.aH[k + 1] = ah.y;
         cv.aR[k] = ar.x; cv.aR[k + 1] = ar.y;
     }
     rs[1] += sh.x + sh.y;
@@ -581,14 +651,15 @@ __device__ __forceinline__ void update_row(const QSrc& qsrc, const unsigned char
 }
 
 // Per-tile constants of one consumer warp.
+// (The rest of the tile's parameters stay in the tile slot, sm.info[slot],
+// and are read again where needed, so that they take no registers in the
+// pair loop.)
 struct TileCtx {
     int cw, lane, rows, cols;
     bool diag;
     int it;
     bool zero, zero_h;
-    Ctrl* ctrl;
-    long long L;
-    const float (*ag)[T];   // the tile slot's aggregates: rows 0..2, columns 3..5
+    int slot;   // the tile slot: aggregates sm.agg[slot] (rows 0..2, columns 3..5), parameters sm.info[slot]
 };
 
 // One tile's chunk rows for one consumer warp: waits for each ring stage,
@@ -596,7 +667,7 @@ struct TileCtx {
 // sm.rp/rh/rr and its column partials in sm.cp (not when FROZEN), sm.ch and
 // sm.cr.  Specialised per tile kind so that a frozen-P tile keeps neither the
 // column P values nor their sums in registers.
-template <int CW, bool FULL, bool FROZEN, int SB, class MSG, class QSrc>
+template <int CW, bool FULL, bool FROZEN, bool QN, int SB, class MSG, class QSrc>
 __device__ __forceinline__ void consume_tile(const QSrc& qsrc, SweepTail<CW>& sm, const unsigned char* ring,
                                              const TileCtx& tc, typename MSG::T2* __restrict__ gp,
                                              typename MSG::T2* __restrict__ gh, int& stage, uint32_t& phase,
@@ -604,52 +675,74 @@ __device__ __forceinline__ void consume_tile(const QSrc& qsrc, SweepTail<CW>& sm
 {
     const int cw = tc.cw, lane = tc.lane, rows = tc.rows;
     constexpr int G = MSG::G;
+    const float (*ag)[T] = sm.agg[tc.slot];
     ColVals cv;
-    ld4<G>(tc.ag[4], lane, cv.H);
-    ld4<G>(tc.ag[5], lane, cv.M);
-    if (!FROZEN) ld4<G>(tc.ag[3], lane, cv.P);
+    ld4<G>(ag[4], lane, cv.H);
+    ld4<G>(ag[5], lane, cv.M);
+    if (!FROZEN) ld4<G>(ag[3], lane, cv.P);
 #pragma unroll
     for (int k = 0; k < 4; ++k) cv.aP[k] = cv.aH[k] = cv.aR[k] = 0.f;
-    constexpr int RC = rc<MSG>(), RPW = RC / CW;
-    static_assert(RPW * CW == RC && (RPW == 1 || RPW == 2), "one or two rows per consumer warp and stage");
-    const int nch = (rows + RC - 1) / RC;
+    // A group of SPC consecutive ring stages (RPS rows of each per warp) is
+    // reduced together: RPW = SPC * RPS rows of the warp, cw + CW u.
+    constexpr int RC = rc<MSG>(), SPC = MSG::SPC, RPS = RC / CW, RPW = SPC * RPS;
+    static_assert(RPS * CW == RC && (RPW == 1 || RPW == 2 || RPW == 4), "1, 2 or 4 rows per consumer warp and group");
+    const int nst = (rows + RC - 1) / RC;   // ring stages of this tile
 #pragma unroll 1
-    for (int ch = 0; ch < nch; ++ch) {
-        if (!abort && !mbar_wait_warp(&sm.full[stage], phase)) {
-            abort = true;
-            if (lane == 0) record_error(tc.ctrl, ST_ETIMEOUT, tc.L);
-        }
-        // this warp's rows of the stage: cw, cw + CW, ...
+    for (int ch = 0; ch < nst; ch += SPC) {
         float rs[RPW][3];
 #pragma unroll
-        for (int u = 0; u < RPW; ++u) {
-            const int lr = cw + CW * u, r = ch * RC + lr;
-            rs[u][0] = rs[u][1] = rs[u][2] = 0.f;
-            if (!abort && r < rows) {
-                const unsigned char* S = ring + (size_t)stage * SB;
-                update_row<FULL, FROZEN, MSG>(qsrc, S, lr, lane, r, tc.cols, tc.diag, tc.it, tc.zero, tc.zero_h,
-                                              tc.ag[0][r], tc.ag[1][r], tc.ag[2][r], cv, gp, gh, rs[u], bad,
-                                              changed);
+        for (int g = 0; g < SPC; ++g) {
+#pragma unroll
+            for (int u = 0; u < RPS; ++u) rs[g * RPS + u][0] = rs[g * RPS + u][1] = rs[g * RPS + u][2] = 0.f;
+            if (SPC > 1 && ch + g >= nst) continue;   // a tile with an odd number of stages
+            if (!abort && !mbar_wait_warp(&sm.full[stage], phase)) {
+                abort = true;
+                if (lane == 0) record_error(sm.info[tc.slot].ctrl, ST_ETIMEOUT, sm.info[tc.slot].L);
             }
+            if (!abort) {
+                const unsigned char* S = ring + (size_t)stage * SB;
+#pragma unroll
+                for (int u = 0; u < RPS; ++u) {
+                    const int lr = cw + CW * u, r = (ch + g) * RC + lr;
+                    if (FULL || r < rows)
+                        update_row<FULL, FROZEN, QN, MSG>(qsrc, S, lr, lane, r, tc.cols, tc.diag, tc.it, tc.zero,
+                                                      tc.zero_h, ag[0][r], ag[1][r], ag[2][r], cv, gp, gh,
+                                                      rs[g * RPS + u], bad, changed);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.empty[stage]);
+            if (++stage == stages<MSG>()) { stage = 0; phase ^= 1u; }
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&sm.empty[stage]);
-        if (++stage == stages<MSG>()) { stage = 0; phase ^= 1u; }
-        // row sums {P, H, R} of the warp's rows over the warp
-        if constexpr (RPW == 2 && FROZEN) {
+        // row sums {P, H, R} of the warp's rows over the warp; group row u is
+        // tile row ch RC + cw + CW u
+        const int r0 = ch * RC + cw;
+        if constexpr (RPW == 4 && FROZEN) {
             // the P sums of a frozen round are not needed
-            const float v = reduce_scatter4(rs[0][1], rs[0][2], rs[RPW - 1][1], rs[RPW - 1][2], lane);
-            const int qi = (lane >> 3) & 3, r = ch * RC + cw + CW * (qi >> 1);
+            const float x[8] = {rs[0][1], rs[0][2], rs[1][1], rs[1][2], rs[2][1], rs[2][2], rs[3][1], rs[3][2]};
+            const float v = reduce_scatter8x(x, lane);
+            const int qi = (lane >> 2) & 7, r = r0 + CW * (qi >> 1);
+            if ((lane & 3) == 0 && r < rows) ((qi & 1) ? sm.rr : sm.rh)[r] = v;
+        } else if constexpr (RPW == 4) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float v = reduce_scatter8(rs[2 * h][0], rs[2 * h][1], rs[2 * h][2], rs[2 * h + 1][0],
+                                                rs[2 * h + 1][1], rs[2 * h + 1][2], lane);
+                const int qi = (lane >> 2) & 7, qv = qi & 3, r = r0 + CW * (2 * h + (qi >> 2));
+                if ((lane & 3) == 0 && qv < 3 && r < rows) (qv == 0 ? sm.rp : (qv == 1 ? sm.rh : sm.rr))[r] = v;
+            }
+        } else if constexpr (RPW == 2 && FROZEN) {
+            const float v = reduce_scatter4(rs[0][1], rs[0][2], rs[1][1], rs[1][2], lane);
+            const int qi = (lane >> 3) & 3, r = r0 + CW * (qi >> 1);
             if ((lane & 7) == 0 && r < rows) ((qi & 1) ? sm.rr : sm.rh)[r] = v;
         } else if constexpr (RPW == 2) {
-            const float v = reduce_scatter8(rs[0][0], rs[0][1], rs[0][2], rs[RPW - 1][0], rs[RPW - 1][1],
-                                            rs[RPW - 1][2], lane);
-            const int qi = (lane >> 2) & 7, qv = qi & 3, r = ch * RC + cw + CW * (qi >> 2);
+            const float v = reduce_scatter8(rs[0][0], rs[0][1], rs[0][2], rs[1][0], rs[1][1], rs[1][2], lane);
+            const int qi = (lane >> 2) & 7, qv = qi & 3, r = r0 + CW * (qi >> 2);
             if ((lane & 3) == 0 && qv < 3 && r < rows) (qv == 0 ? sm.rp : (qv == 1 ? sm.rh : sm.rr))[r] = v;
         } else {
             const float v = reduce_scatter4(rs[0][0], rs[0][1], rs[0][2], 0.f, lane);
-            const int qv = (lane >> 3) & 3, r = ch * RC + cw;
-            if ((lane & 7) == 0 && qv < 3 && r < rows) (qv == 0 ? sm.rp : (qv == 1 ? sm.rh : sm.rr))[r] = v;
+            const int qv = (lane >> 3) & 3;
+            if ((lane & 7) == 0 && qv < 3 && r0 < rows) (qv == 0 ? sm.rp : (qv == 1 ? sm.rh : sm.rr))[r0] = v;
         }
     }
     if (!FROZEN) st4<G>(sm.cp[cw], lane, cv.aP);
@@ -679,38 +772,53 @@ __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, co
         }
         consumer_bar<CW>();   // also: the previous tile's sums are read out
         if (*(volatile int*)&sm.cabort) break;
+        if (sm.info[slot].end) break;
+        bool changed = false, bad = false;
+        TileCtx tc;
+        typename MSG::T2 *gp, *gh;
+        bool full, frozen, qnormal;
+        {
+            const TileInfo& ti = sm.info[slot];
+            const int n = ti.n, I = ti.I, J = ti.J;
+            tc.cw = cw;
+            tc.lane = lane;
+            tc.rows = min(T, n - I * T);
+            tc.cols = min(T, n - J * T);
+            tc.diag = (I == J);
+            tc.it = it;
+            tc.zero = (ti.t == 0);   // Step 1: all messages 0, nothing to read
+            tc.zero_h = ti.zero_h != 0;
+            tc.slot = slot;
+            full = !tc.diag && tc.cols == T;
+            frozen = ti.frozen != 0;
+            qnormal = ti.qnormal != 0;
+            gp = static_cast<typename MSG::T2*>(ti.Pst);
+            gh = static_cast<typename MSG::T2*>(ti.Hst);
+        }
+        if (!abort && !qsrc.tile_begin(it, lane)) {
+            abort = true;
+            if (lane == 0) record_error(sm.info[slot].ctrl, ST_ETIMEOUT, sm.info[slot].L);
+        }
+        if (full) {
+            if (frozen && qnormal)
+                consume_tile<CW, true, true, true, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
+            else if (frozen)
+                consume_tile<CW, true, true, false, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
+            else consume_tile<CW, true, false, false, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
+        } else {
+            if (frozen) consume_tile<CW, false, true, false, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
+            else consume_tile<CW, false, false, false, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
+        }
+        // the tile's remaining parameters, read before the slot is released
         const TileInfo ti = sm.info[slot];
-        if (ti.end) break;
         Ctrl* ctrl = ti.ctrl;
-        const long long L = ti.L;
-        const int t = ti.t;
-        const bool zero = (t == 0);   // Step 1: all messages 0, nothing to read
-        const bool zero_h = ti.zero_h != 0;
-        const bool frozen = ti.frozen != 0;
-        bool changed = false;
-        const int n = ti.n, Nt = ti.Nt;
+        const int n = ti.n, Nt = ti.Nt, I = ti.I, J = ti.J;
+        const int rows = tc.rows, cols = tc.cols;
+        const bool diag = tc.diag;
+        frozen = ti.frozen != 0;
         float* partP = ti.part;
         float* partH = partP + (size_t)Nt * n;
         float* partR = partH + (size_t)Nt * n;
-        bool bad = false;
-        const int I = ti.I, J = ti.J;
-        const int rows = min(T, n - I * T), cols = min(T, n - J * T);
-        const bool diag = (I == J);
-        const bool full = !diag && cols == T;
-        if (!abort && !qsrc.tile_begin(it, lane)) {
-            abort = true;
-            if (lane == 0) record_error(ctrl, ST_ETIMEOUT, L);
-        }
-        typename MSG::T2* gp = static_cast<typename MSG::T2*>(ti.Pst);
-        typename MSG::T2* gh = static_cast<typename MSG::T2*>(ti.Hst);
-        TileCtx tc{cw, lane, rows, cols, diag, it, zero, zero_h, ctrl, L, sm.agg[slot]};
-        if (full) {
-            if (frozen) consume_tile<CW, true, true, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
-            else consume_tile<CW, true, false, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
-        } else {
-            if (frozen) consume_tile<CW, false, true, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
-            else consume_tile<CW, false, false, SB, MSG>(qsrc, sm, ring, tc, gp, gh, stage, phase, abort, bad, changed);
-        }
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.tempty[slot]);   // tile slot free for the producer
         if (++slot == 2) { slot = 0; tph ^= 1u; }
@@ -815,7 +923,7 @@ struct RcExtra {
     unsigned long long drain;
     uint32_t tmem_base;
     int abort;
-    ColChunk cols[4];   // column constants, one chunk per epilogue warp
+    ColTile cols[4];    // column constants of the current tile, one set per epilogue warp
 };
 
 template <class MSG>
@@ -977,23 +1085,27 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
             }
             tc_fence_after();
             const int I = w.y, J = w.z, i = I * T + r;
-            const float yi = i < n ? p.y[i] : 0.f, si = i < n ? p.sqb[i] : 0.f;
-            const float ai = -p.gamma * kLog2e * si, c2 = 2.f * p.gamma * kLog2e;
-            const uint32_t syi = __float_as_uint(yi) & 0x80000000u;
+            const float* y = p.y;
+            const float* sqb = p.sqb;
+            const float gamma = p.gamma, lam2 = p.lam2;
+            const float yi = i < n ? y[i] : 0.f, si = i < n ? sqb[i] : 0.f;
+            stage_tile_cols(ex.cols[g], y, sqb, n, J, gamma, lane, 0, T / 32);
+            const float ai = -gamma * kLog2e * si, c2 = 2.f * gamma * kLog2e;
+            const uint32_t s1 = __float_as_uint(yi) & 0x80000000u, si2 = s1 | (s1 >> 16);
             __nv_bfloat16* qrow = qtile + (size_t)acc * TT + (size_t)r * T;
 #pragma unroll 1
             for (int cc = 0; cc < T / 32; ++cc) {
-                const int jl = J * T + 32 * cc + lane;
-                const float yl = jl < n ? p.y[jl] : 0.f, sl = jl < n ? p.sqb[jl] : 0.f;
-                stage_cols(ex.cols[g], yl, sl, p.gamma, lane);
                 const uint32_t valid = chunk_valid(n, I, J, r, cc);
                 uint4* dst = reinterpret_cast<uint4*>(qrow + 32 * cc);
+                float v[32];
+                tmem_ld32(tbase + (uint32_t)acc * T + ((uint32_t)(32 * g) << 16) + (uint32_t)(32 * cc), v);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    float v[16];
-                    tmem_ld16(tbase + (uint32_t)acc * T + ((uint32_t)(32 * g) << 16) + (uint32_t)(32 * cc + 16 * h), v);
+                    float vh[16];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) vh[u] = v[16 * h + u];
                     uint4 out[2];
-                    q_half_bf16(v, 16 * h, ai, syi, ex.cols[g], c2, p.lam2, valid, out);
+                    q_half_bf16(vh, 32 * cc + 16 * h, ai, si2, ex.cols[g], c2, lam2, (valid >> (16 * h)) & 0xffffu, out);
                     dst[2 * h] = out[0];
                     dst[2 * h + 1] = out[1];
                 }
