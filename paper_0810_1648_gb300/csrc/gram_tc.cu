@@ -124,8 +124,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     k_form_q_tc(const Inst* __restrict__ tab, const int4* __restrict__ work, long long ntiles)
 {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* base = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    unsigned char* base = align_smem(smem_raw, 1024);
     unsigned char* ops = base;                                   // XSTAGES x (A block, B block)
     TcSmem& sm = *reinterpret_cast<TcSmem*>(base + XSTAGES * 2 * BLK_BYTES);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;

@@ -164,8 +164,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
     k_form_q_tc32(const Inst* __restrict__ tab, const int4* __restrict__ work, long long ntiles, int norms_only)
 {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* ops = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    unsigned char* ops = align_smem(smem_raw, 1024);
     T3Smem& sm = *reinterpret_cast<T3Smem*>(ops + T3_STAGES * T3_STAGE_BYTES);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 

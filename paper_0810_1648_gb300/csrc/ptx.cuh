@@ -18,6 +18,16 @@ __device__ __forceinline__ uint32_t smem_u32(const void* ptr)
     return (uint32_t)__cvta_generic_to_shared(ptr);
 }
 
+// Rounds a dynamic shared-memory pointer up to a multiple of `a` bytes (a
+// power of two) by adding an offset to it: the result keeps the provenance of
+// the __shared__ array, so the compiler emits shared-memory loads and stores
+// through it (a round trip through an integer would leave it a generic
+// pointer, and every access through it a generic one).
+__device__ __forceinline__ unsigned char* align_smem(unsigned char* raw, uint32_t a)
+{
+    return raw + ((a - (smem_u32(raw) & (a - 1))) & (a - 1));
+}
+
 __device__ __forceinline__ unsigned long long global_ns()
 {
     unsigned long long t;

@@ -874,11 +874,6 @@ struct StoredQ {
     }
 };
 
-__device__ __forceinline__ unsigned char* align_smem(unsigned char* raw, uintptr_t a)
-{
-    return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + a - 1) & ~(a - 1));
-}
-
 template <typename QT, class MSG>
 __global__ void __launch_bounds__(SWEEP_THREADS, sweep_ctas<MSG>())
     k_sweep(const Inst* __restrict__ tab, const int4* __restrict__ work, const Sched* __restrict__ sched, int stage_no)
