@@ -75,14 +75,18 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t pari
     return true;
 }
 
-// Warp-uniform bounded wait: lane 0 waits, the result is broadcast, so every
-// lane takes the same branch (needed before .sync.aligned instructions and
-// full-mask shuffles).
+// Warp-uniform bounded wait (every lane takes the same branch afterwards, as
+// .sync.aligned instructions and full-mask shuffles need): all lanes test the
+// phase and the warp proceeds once every lane has seen it complete; the time
+// limit is likewise decided by a vote.  No lane diverges on the fast path.
 __device__ __forceinline__ bool mbar_wait_warp(unsigned long long* bar, uint32_t parity)
 {
-    bool ok = false;
-    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity);
-    return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+        if (__any_sync(0xffffffffu, global_ns() - t0 > kWaitLimitNs)) return false;
+    }
 }
 
 __device__ __forceinline__ uint64_t l2_evict_first_policy()
