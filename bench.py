@@ -142,9 +142,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _traffic_from_profile(kernel_src: str):
+# The sources the pair sweep is compiled from: sweep.cu and the headers it
+# includes.  The profile summaries record the SHA-256 of their concatenation.
+SWEEP_SOURCES = ("sweep.cu", "common.cuh", "ptx.cuh", "qtile_epi.cuh")
+
+
+def sweep_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_0810_1648_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def _traffic_from_profile():
     """DRAM bytes per launch of the pair sweep from the committed ncu summary,
-    or None when the kernel source changed since the counters were taken."""
+    or None when the kernel sources changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "k_sweep_plain_large.txt")
     try:
         txt = open(path).read()
@@ -154,8 +167,7 @@ def _traffic_from_profile(kernel_src: str):
     m_b = re.search(r"^traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt, re.M)
     if not (m_sha and m_b):
         return None
-    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-    return float(m_b.group(1)) if sha == m_sha.group(1) else None
+    return float(m_b.group(1)) if sweep_source_sha() == m_sha.group(1) else None
 
 
 def _peak_gbs() -> float:
@@ -777,7 +789,7 @@ def run_ours(args):
         peak, peak_src = float(peaks["hbm_gbs"]), "measured"
     else:
         peak, peak_src = 6800.0, "fallback"
-    traffic = _traffic_from_profile(os.path.join(ROOT, "paper_0810_1648_gb300", "csrc", "sweep.cu"))
+    traffic = _traffic_from_profile()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None,
             "traffic": traffic if (args.workload == "plain_large" and args.q_mode == "f32") else None,
