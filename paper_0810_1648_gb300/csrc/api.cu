@@ -114,6 +114,10 @@ struct gabp_svm_s {
     size_t spool_bytes = 0;
     float* tilemax = nullptr;       // per-tile maxima (formation's first pass)
     int* slab = nullptr;            // slab of every tile in the compacted storage, -1 = dropped
+    int* srow = nullptr;            // compacted slot space: block row I owns [srow[I], srow[I + 1])
+    int2* tslot = nullptr;          // slots {row role, column role} of each kept tile (by slab)
+    double* rsum = nullptr;         // the whole matrix's sum_{j != i} |Q_ij| (first pass), per node
+    long long nslot = 0;            // slots of the compacted slot space
     Inst inst{};
     Inst* d_tab = nullptr;          // device copy of inst (a one-instance batch)
     int4* work_all = nullptr;       // every tile {0, I, J, L}, row by row (formation)
@@ -166,7 +170,8 @@ gabp_status check_formed(gabp_svm_t h)
 
 // Device memory plan of one handle (bytes, 256-aligned sub-buffers).
 struct Plan {
-    size_t X, vec, agg, part, state, q, qref, work, tilemax, ctrl, rhist, final3, blockbuf, xp, xp3, tab, nbl, total;
+    size_t X, vec, agg, part, state, q, qref, work, tilemax, sparse, ctrl, rhist, final3, blockbuf, xp, xp3, tab, nbl,
+        total;
 };
 
 // Bytes of the per-pair arrays (messages, stored Q, FP32 copy) for `tiles` tiles.
@@ -178,19 +183,26 @@ size_t pair_bytes(long long tiles, int q_mode, int msg_bf16)
            (q_mode == GABP_Q_BF16 ? align_up(tt * 4, 256) : 0);
 }
 
+// Bytes of the four slot-partial arrays for `nslot` slots of T nodes.
+size_t part_bytes(long long nslot) { return align_up((size_t)4 * nslot * T * sizeof(float), 256); }
+
 Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_mode, int msg_bf16, bool sparse)
 {
     Plan p{};
     // the tile-sparse option keeps a second tile list (the swept tiles), the
-    // tile maxima and the slab map; its per-pair arrays are allocated later,
-    // for the kept tiles only (pair_bytes)
+    // tile maxima, the slab map, the compacted slot space (srow, tslot) and
+    // the first pass's row sums; its per-pair arrays and slot partials are
+    // allocated later, for the kept tiles only (pair_bytes, part_bytes)
     p.tilemax = sparse ? 2 * align_up((size_t)ntiles * sizeof(float), 256) : 0;
+    p.sparse = sparse ? align_up((size_t)(Nt + 1) * sizeof(int), 256) + align_up((size_t)ntiles * sizeof(int2), 256) +
+                            align_up((size_t)n * sizeof(double), 256)
+                      : 0;
     p.xp = q_mode != GABP_Q_F32 ? align_up(bf16_pack_bytes(Nt, (int)m), 1024) : 0;
     p.xp3 = align_up(pack3_bytes(Nt, (int)m), 1024);   // the FP32 Gram's three BF16 planes
     p.X = align_up((size_t)n * m * sizeof(float), 256);
     p.vec = align_up((size_t)npad * sizeof(float), 256);
     p.agg = align_up((size_t)8 * npad * sizeof(float), 256);   // 2 x {P, h, mu} + staged {P, h}
-    p.part = align_up((size_t)4 * Nt * n * sizeof(float), 256);
+    p.part = sparse ? 0 : part_bytes((long long)Nt * Nt);
     const long long dense_tiles = sparse ? 0 : ntiles;
     p.state = 2 * align_up((size_t)dense_tiles * TT * (msg_bf16 ? 4 : 8), 256);
     p.q = q_mode == GABP_Q_F32 ? align_up((size_t)dense_tiles * TT * sizeof(float), 256)
@@ -205,7 +217,7 @@ Plan make_plan(int64_t n, int64_t m, int Nt, long long ntiles, int npad, int q_m
     p.rhist = align_up((size_t)kRhistCap * sizeof(double), 256);
     p.final3 = 256;
     p.blockbuf = align_up((size_t)3 * ((n + 31) / 32) * sizeof(double), 256);
-    p.total = p.X + 10 * p.vec + p.agg + p.part + p.state + p.q + p.qref + p.work + p.tilemax + p.ctrl + p.rhist +
+    p.total = p.X + 10 * p.vec + p.agg + p.part + p.state + p.q + p.qref + p.work + p.tilemax + p.sparse + p.ctrl + p.rhist +
               p.final3 + p.blockbuf + p.xp + p.xp3 + p.tab + p.nbl + 2048;
     return p;
 }
@@ -261,36 +273,66 @@ gabp_status build_sweep_list(gabp_svm_t h)
     }
     h->nlive = (long long)wl.size();
     h->stats.tiles_kept = h->nlive;
+    // compacted slot space: block row I's slots are its kept tiles (row or
+    // column block I) in the order of their other block index
+    std::vector<int> cnt((size_t)Nt + 1, 0), srow((size_t)Nt + 1, 0);
+    std::vector<std::vector<int>> other((size_t)Nt);
+    for (const int4& w : wl) {
+        other[(size_t)w.y].push_back(w.z);
+        if (w.z != w.y) other[(size_t)w.z].push_back(w.y);
+    }
+    for (int I = 0; I < Nt; ++I) {
+        std::sort(other[(size_t)I].begin(), other[(size_t)I].end());
+        srow[(size_t)I + 1] = srow[(size_t)I] + (int)other[(size_t)I].size();
+    }
+    auto slot_of = [&](int I, int k) {
+        const auto& o = other[(size_t)I];
+        return srow[(size_t)I] + (int)(std::lower_bound(o.begin(), o.end(), k) - o.begin());
+    };
+    std::vector<int2> tslot(wl.size());
+    for (size_t e = 0; e < wl.size(); ++e) tslot[e] = make_int2(slot_of(wl[e].y, wl[e].z), slot_of(wl[e].z, wl[e].y));
+    h->nslot = srow[(size_t)Nt];
     CK(cudaMemcpyAsync(h->work, wl.data(), wl.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(h->slab, slab.data(), slab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->srow, srow.data(), srow.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->tslot, tslot.data(), tslot.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(h->sched, sc, (size_t)h->nstages * sizeof(Sched), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));   // the host lists go out of scope
     return GABP_OK;
 }
 
-// Tile-sparse option: per-pair arrays for the h->nlive kept tiles, in the
-// second allocation (kept when large enough, else replaced).  GABP_ENOMEM when
-// they do not fit in free device memory.
-gabp_status ensure_pair_storage(gabp_svm_t h)
+// Tile-sparse option: the second allocation holds at least `need` bytes
+// (kept when large enough, else replaced; its contents are not kept).
+// GABP_ENOMEM when that does not fit in free device memory.
+gabp_status ensure_spool(gabp_svm_t h, size_t need, const char* what)
+{
+    need += 1024;
+    if (need <= h->spool_bytes) return GABP_OK;
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->spool) CK(cudaFree(h->spool));
+    h->spool = nullptr;
+    h->spool_bytes = 0;
+    size_t free_b = 0;
+    CK(device_available(&free_b, true));   // cudaMalloc below: the pool's unused memory back first
+    const size_t margin = (size_t)256 << 20;
+    if (need + margin > free_b)
+        return fail(GABP_ENOMEM, "%s need %.2f GB of device memory, %.2f GB free", what, need / 1e9, free_b / 1e9);
+    cudaError_t e = cudaMalloc(&h->spool, need);
+    if (e != cudaSuccess) return fail(GABP_ENOMEM, "cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+    h->spool_bytes = need;
+    return GABP_OK;
+}
+
+// Tile-sparse option: per-pair arrays for the h->nlive kept tiles and the
+// slot partials of the compacted slot space (nslot slots), in the second
+// allocation.
+gabp_status ensure_pair_storage(gabp_svm_t h, long long nslot)
 {
     Inst& p = h->inst;
     const int qm = h->opts.q_mode, mb = h->opts.msg_bf16;
-    const size_t need = pair_bytes(h->nlive, qm, mb) + 1024;
-    if (need > h->spool_bytes) {
-        CK(cudaStreamSynchronize(h->stream));
-        if (h->spool) CK(cudaFree(h->spool));
-        h->spool = nullptr;
-        h->spool_bytes = 0;
-        size_t free_b = 0;
-        CK(device_available(&free_b, true));   // cudaMalloc below: the pool's unused memory back first
-        const size_t margin = (size_t)256 << 20;
-        if (need + margin > free_b)
-            return fail(GABP_ENOMEM, "the %lld kept tiles need %.2f GB of device memory, %.2f GB free",
-                        h->nlive, need / 1e9, free_b / 1e9);
-        cudaError_t e = cudaMalloc(&h->spool, need);
-        if (e != cudaSuccess) return fail(GABP_ENOMEM, "cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
-        h->spool_bytes = need;
-    }
+    char what[64];
+    snprintf(what, sizeof(what), "the %lld kept tiles", h->nlive);
+    if (gabp_status st = ensure_spool(h, pair_bytes(h->nlive, qm, mb) + part_bytes(nslot), what)) return st;
     const size_t tt = (size_t)h->nlive * TT;
     char* b = static_cast<char*>(h->spool);
     const size_t st = align_up(tt * (mb ? 4 : 8), 256);
@@ -302,10 +344,17 @@ gabp_status ensure_pair_storage(gabp_svm_t h)
     if (qm == GABP_Q_F32) {
         p.qstore = b;
         p.qref = (float*)b;
+        b += align_up(tt * 4, 256);
     } else if (qm == GABP_Q_BF16) {
         p.qstore = b;
         p.qref = (float*)(b + align_up(tt * 2, 256));
+        b += align_up(tt * 2, 256) + align_up(tt * 4, 256);
     }
+    p.part = (float*)b;
+    p.nslot = nslot;
+    p.srow = h->srow;
+    p.tslot = h->tslot;
+    p.rsum = h->rsum;
     return GABP_OK;
 }
 
@@ -383,13 +432,25 @@ gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
         // the FP32 copy beside the BF16 store; the row sums it writes again
         // are the same values), the diagonal rule and Step 1, and the BF16
         // tiles.  Recompute needs no second pass.
+        // The first pass writes its |Q| row sums into dense slots (one array,
+        // in the second allocation) and reduces them to rsum, the diagonal
+        // rule's sums; the kept tiles' storage then replaces them.
         if (h->opts.q_mode != GABP_Q_F32)
             CK(launch_pack_bf16(p.X, (int)n, (int)m, p.nkc, h->Nt, (void*)p.Xp, (float*)p.sqb, s));
+        if (gabp_status st = ensure_spool(h, (size_t)h->Nt * h->Nt * T * sizeof(float), "the first pass's row sums"))
+            return st;
+        p.part = static_cast<float*>(h->spool);
+        p.nslot = (long long)h->Nt * h->Nt;
+        p.srow = nullptr;
+        p.tslot = nullptr;
+        p.rsum = nullptr;
+        CK(cudaMemcpyAsync(h->d_tab, &p, sizeof(Inst), cudaMemcpyHostToDevice, s));
         launch_form_q(h->d_tab, h->work_all, h->ntiles, s);
+        launch_row_abs_sums(p, h->rsum, s);
         CK(cudaGetLastError());
-        h->prof.kernel_launches += h->opts.q_mode != GABP_Q_F32 ? 3 : 1;
+        h->prof.kernel_launches += h->opts.q_mode != GABP_Q_F32 ? 4 : 2;
         if (gabp_status st = build_sweep_list(h)) return st;
-        if (gabp_status st = ensure_pair_storage(h)) return st;
+        if (gabp_status st = ensure_pair_storage(h, h->nslot)) return st;
         p.tilemax = nullptr;
         p.slab = h->slab;
         CK(cudaMemcpyAsync(h->d_tab, &p, sizeof(Inst), cudaMemcpyHostToDevice, s));
@@ -674,7 +735,11 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     h->r32 = (float*)take(pl.vec);
     p.agg = (float*)take(pl.agg);
     p.aggmid = p.agg + (size_t)6 * h->npad;
-    p.part = (float*)take(pl.part);
+    p.part = pl.part ? (float*)take(pl.part) : nullptr;   // tile-sparse: with the kept tiles' arrays
+    p.nslot = (long long)h->Nt * h->Nt;
+    p.srow = nullptr;
+    p.tslot = nullptr;
+    p.rsum = nullptr;
     p.Pst = take(pl.state / 2);
     p.Hst = take(pl.state / 2);
     p.msg_bf16 = o.msg_bf16;
@@ -687,6 +752,9 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
         h->work = (int4*)take(wbytes / 2);
         h->tilemax = (float*)take(pl.tilemax / 2);
         h->slab = (int*)take(pl.tilemax / 2);
+        h->srow = (int*)take(align_up((size_t)(h->Nt + 1) * sizeof(int), 256));
+        h->tslot = (int2*)take(align_up((size_t)h->ntiles * sizeof(int2), 256));
+        h->rsum = (double*)take(align_up((size_t)n * sizeof(double), 256));
     } else {
         h->work = h->work_all = (int4*)take(wbytes);   // formation walks the swept list
     }

@@ -59,7 +59,7 @@ MemberPlan member_plan(int64_t n, int64_t m, int q_mode, int msg_bf16, bool alia
     p.X = alias_x ? 0 : aup((size_t)n * m * 4, 256);
     p.vec = aup(npad * 4, 256);
     p.agg = aup(8 * npad * 4, 256);   // 2 x {P, h, mu} + staged {P, h}
-    p.part = aup((size_t)4 * Nt * n * 4, 256);
+    p.part = aup((size_t)4 * Nt * Nt * T * 4, 256);   // slot partials: Nt slots of T nodes per block row
     p.state = 2 * aup((size_t)nt * TT * (msg_bf16 ? 4 : 8), 256);
     p.q = q_mode == 0 ? aup((size_t)nt * TT * 4, 256) : q_mode == 1 ? aup((size_t)nt * TT * 2, 256) : 0;
     p.qref = q_mode == 1 ? aup((size_t)nt * TT * 4, 256) : 0;   // FP32 copy for the refinement residuals
@@ -627,6 +627,10 @@ class Engine {
         p.agg = (float*)take(pl.agg);
         p.aggmid = p.agg + (size_t)6 * p.npad;
         p.part = (float*)take(pl.part);
+        p.nslot = (long long)p.Nt * p.Nt;   // dense slot layout
+        p.srow = nullptr;
+        p.tslot = nullptr;
+        p.rsum = nullptr;
         p.Pst = take(pl.state / 2);
         p.Hst = take(pl.state / 2);
         p.msg_bf16 = msg_bf16;

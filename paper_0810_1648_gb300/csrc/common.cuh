@@ -90,7 +90,12 @@ struct Inst {
                       // when Q is recomputed)
     float* agg;       // [2][3][npad]: double-buffered {Ptilde, htilde, mutilde}
     float* aggmid;    // [2][npad]: {Ptilde, htilde} between the stages of a staged round
-    float* part;      // [4][Nt][n] partial sums
+    float* part;      // [4][nslot][T] slot partial sums (slot_begin / slot_count / tile_slots)
+    long long nslot;  // slots of each partial array: Nt * Nt, or the kept ones (tile-sparse option)
+    const int* srow;  // tile-sparse option: block row I owns slots [srow[I], srow[I + 1]); nullptr = dense
+    const int2* tslot;// tile-sparse option: slots {row role, column role} of swept tile w.w; nullptr = dense
+    const double* rsum;  // tile-sparse option: the whole matrix's sum_{j != i} |Q_ij| per node (formation's
+                         // first pass), for the diagonal rule; nullptr = summed from the slots
     Ctrl* ctrl;
     double* rhist;    // ||r(t)||_inf per round (rhist_cap entries)
     int rhist_cap;
@@ -109,6 +114,30 @@ struct Inst {
     int form_next;    // formation: 1 + the next instance built from the same features (its Q
                       // tiles come from the same Gram tiles), 0 = none
 };
+
+// Slot partials.  Every node has one slot per tile it belongs to (a tile
+// whose row block or column block is the node's block), ordered by the
+// tile's other block index; slot s of an instance covers floats [s T, s T + T)
+// of each partial array, one per node of the block.  Dense instances give
+// block row I the slots I Nt .. I Nt + Nt - 1 (slot I Nt + k for the tile with
+// block k); under the tile-sparse option block row I owns the compacted slots
+// [srow[I], srow[I + 1]) of its kept tiles, in the same order, so that a
+// node's sum over its slots adds the same values in the same order as the
+// dense sum over all slots (those of dropped tiles hold 0).
+__host__ __device__ inline long long slot_begin(const Inst& p, int I)
+{
+    return p.srow ? (long long)p.srow[I] : (long long)I * p.Nt;
+}
+__host__ __device__ inline int slot_count(const Inst& p, int I) { return p.srow ? p.srow[I + 1] - p.srow[I] : p.Nt; }
+// Slots of the tile of work entry w = {instance, I, J, index}: {the row
+// block's (its nodes I T + r), the column block's (nodes J T + c)}.
+__host__ __device__ inline int2 tile_slots(const Inst& p, int4 w)
+{
+    if (p.tslot) return p.tslot[w.w];
+    return make_int2(w.y * p.Nt + w.z, w.z * p.Nt + w.y);
+}
+// Floats of each partial array.
+__host__ __device__ inline size_t part_len(const Inst& p) { return (size_t)p.nslot * T; }
 
 // Work of one round over a set of instances (device resident, so that a
 // captured round stays valid while the set changes).  Tile list entries are
@@ -216,6 +245,9 @@ void launch_reset(const Inst& p, cudaStream_t s);
 
 // Diagonal rule, Step-1 aggregates and control reset.
 void launch_init(const Inst& p, int diag_rule, float delta, cudaStream_t s);
+// rsum[x] = the sum of node x's slots of partial array 0 (the formation's
+// |Q| row sums), in FP64.
+void launch_row_abs_sums(const Inst& p, double* rsum, cudaStream_t s);
 // Solve control: arm the control blocks of tab[0..ninst) for `iters` more rounds with tolerance `tol`.
 void launch_begin(Inst* tab, int ninst, int iters, double tol, cudaStream_t s);
 int num_sms();

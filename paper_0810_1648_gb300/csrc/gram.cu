@@ -119,7 +119,7 @@ __device__ __forceinline__ float sum16(float v)
 // columns) of up to two quantities -> per-node slot partials part_q[k][x].
 template <int NQ>
 __device__ __forceinline__ void reduce_and_write(EpiSmem& es, float (&rs)[NQ][8], float (&cs)[NQ][8],
-                                                 float* const (&part)[NQ], int n, int I, int J)
+                                                 float* const (&part)[NQ], int n, int I, int J, int2 sl)
 {
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15, warp = tid >> 5, lane = tid & 31;
 #pragma unroll
@@ -147,24 +147,26 @@ __device__ __forceinline__ void reduce_and_write(EpiSmem& es, float (&rs)[NQ][8]
         }
     }
     __syncthreads();
+    // slot sl.x of the row block (its nodes I T + r), sl.y of the column block
+    const size_t oR = (size_t)sl.x * T, oC = (size_t)sl.y * T;
     if (I == J) {
         if (tid < T) {
             const int x = I * T + tid;
             if (x < n)
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) part[q][(size_t)I * n + x] = es.rowv[q][tid] + es.colv[q][tid];
+                for (int q = 0; q < NQ; ++q) part[q][oR + tid] = es.rowv[q][tid] + es.colv[q][tid];
         }
     } else {
         if (tid < T) {
             const int x = I * T + tid;
             if (x < n)
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) part[q][(size_t)J * n + x] = es.rowv[q][tid];
+                for (int q = 0; q < NQ; ++q) part[q][oR + tid] = es.rowv[q][tid];
         } else {
             const int c = tid - T, x = J * T + c;
             if (x < n)
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) part[q][(size_t)I * n + x] = es.colv[q][c];
+                for (int q = 0; q < NQ; ++q) part[q][oC + c] = es.colv[q][c];
         }
     }
 }
@@ -232,10 +234,10 @@ __global__ void k_stage_list(const Inst* __restrict__ tab, const int2* __restric
 // FP32 Gram values, from which Q is formed exactly as at formation, so both
 // give the same values.
 template <bool STORED>
-__device__ __forceinline__ void final_tile_sums(const Inst& p, const float* __restrict__ mu, int I, int J,
+__device__ __forceinline__ void final_tile_sums(const Inst& p, const float* __restrict__ mu, int4 w,
                                                 float (&acc)[8][8], EpiSmem& es)
 {
-    const int n = p.n;
+    const int n = p.n, I = w.y, J = w.z;
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
     float yj[8], sj[8], mj[8], aj[8];
 #pragma unroll
@@ -270,8 +272,8 @@ __device__ __forceinline__ void final_tile_sums(const Inst& p, const float* __re
         rs[0][a] = rm;
         rs[1][a] = ra;
     }
-    float* const parts[2] = {p.part, p.part + (size_t)p.Nt * n};
-    reduce_and_write<2>(es, rs, cs, parts, n, I, J);
+    float* const parts[2] = {p.part, p.part + part_len(p)};
+    reduce_and_write<2>(es, rs, cs, parts, n, I, J, tile_slots(p, w));
 }
 
 // Q recomputed by the FP32 Gram (forms without an FP32 store).  One CTA per
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(NTHREADS) k_final_tiles(const Inst* __restrict
     const GramSide S{p.X, p.sq, p.n};
     gram_tile(S, S, p.m, w.y, w.z, sm.g, acc);
     __syncthreads();   // Gram smem is reused by the epilogue
-    final_tile_sums<false>(p, ops[w.x].mu, w.y, w.z, acc, sm.e);
+    final_tile_sums<false>(p, ops[w.x].mu, w, acc, sm.e);
 }
 
 // Q read back from the FP32 tiles (Inst::qref): no Gram, small footprint, so
@@ -309,7 +311,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_final_tiles_q(const Inst* __res
         acc[a][0] = u0.x; acc[a][1] = u0.y; acc[a][2] = u0.z; acc[a][3] = u0.w;
         acc[a][4] = u1.x; acc[a][5] = u1.y; acc[a][6] = u1.z; acc[a][7] = u1.w;
     }
-    final_tile_sums<true>(p, ops[w.x].mu, w.y, w.z, acc, es);
+    final_tile_sums<true>(p, ops[w.x].mu, w, acc, es);
 }
 
 // Per node of a listed node block: r_i = b0_i - Q_ii mu_i - sum part0,
@@ -327,15 +329,18 @@ __global__ void __launch_bounds__(256) k_final_nodes(const Inst* __restrict__ ta
     const StopOp& op = ops[nb.x];
     const float* __restrict__ mu = op.mu;
     const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
-    const int x = nb.y * 32 + lane, n = p.n, Nt = p.Nt;
-    const float* p0 = p.part;
-    const float* p1 = p.part + (size_t)Nt * n;
+    const int x = nb.y * 32 + lane, n = p.n;
     double s0 = 0.0, s1 = 0.0;
-    if (x < n)
-        for (int k = g; k < Nt; k += 8) {
-            s0 += (double)p0[(size_t)k * n + x];
-            s1 += (double)p1[(size_t)k * n + x];
+    if (x < n) {
+        // the node's slots (see slot_begin)
+        const int X = x / T, ns = slot_count(p, X);
+        const float* p0 = p.part + (size_t)slot_begin(p, X) * T + (x - X * T);
+        const float* p1 = p0 + part_len(p);
+        for (int k = g; k < ns; k += 8) {
+            s0 += (double)p0[(size_t)k * T];
+            s1 += (double)p1[(size_t)k * T];
         }
+    }
     __shared__ double red[2][8][32];
     red[0][g][lane] = s0;
     red[1][g][lane] = s1;

@@ -370,23 +370,24 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                 epi_bar();
                 // per-node slot partials (fixed order): row sums of the tile's rows,
                 // column sums of its columns; both roles on a diagonal tile
-                float* part = p.part;
+                // (slot sl.x of the row block, sl.y of the column block)
+                const int2 sl = tile_slots(p, w);
+                float* partR = p.part + (size_t)sl.x * T;
+                float* partC = p.part + (size_t)sl.y * T;
                 if (I == J) {
                     if (etid < T) {
                         const int x = I * T + etid;
                         if (x < n)
-                            part[(size_t)I * n + x] = (sm.rowsum[0][etid] + sm.rowsum[1][etid]) +
-                                                      (((sm.colsum[0][etid] + sm.colsum[1][etid]) + sm.colsum[2][etid]) +
-                                                       sm.colsum[3][etid]);
+                            partR[etid] = (sm.rowsum[0][etid] + sm.rowsum[1][etid]) +
+                                          (((sm.colsum[0][etid] + sm.colsum[1][etid]) + sm.colsum[2][etid]) +
+                                           sm.colsum[3][etid]);
                     }
                 } else if (etid < T) {
                     const int x = I * T + etid;
-                    if (x < n) part[(size_t)J * n + x] = sm.rowsum[0][etid] + sm.rowsum[1][etid];
+                    if (x < n) partR[etid] = sm.rowsum[0][etid] + sm.rowsum[1][etid];
                 } else if (etid < 2 * T) {
                     const int c = etid - T, x = J * T + c;
-                    if (x < n)
-                        part[(size_t)I * n + x] =
-                            ((sm.colsum[0][c] + sm.colsum[1][c]) + sm.colsum[2][c]) + sm.colsum[3][c];
+                    if (x < n) partC[c] = ((sm.colsum[0][c] + sm.colsum[1][c]) + sm.colsum[2][c]) + sm.colsum[3][c];
                 }
                 if (etid == 0 && p.tilemax) {
                     float m2 = 0.f;

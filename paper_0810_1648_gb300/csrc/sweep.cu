@@ -211,10 +211,12 @@ __host__ __device__ constexpr size_t state_chunk() { return 2 * pchunk<MSG>(); }
 struct TileInfo {
     void* Pst;          // the tile's P message block
     void* Hst;          // the tile's H message block
-    float* part;        // the instance's partial sums
+    float* part;        // the instance's slot partial sums
+    long long plen;     // floats of each partial array
     Ctrl* ctrl;
     long long L;        // work-list index (error records)
     int n, Nt, I, J;
+    int sR, sC;         // the tile's slots: row block's, column block's
     int t, zero_h, frozen, end;
     int qnormal;        // every off-diagonal |q| >= FLT_MIN (lambda^2 >= 2 FLT_MIN)
 };
@@ -306,9 +308,12 @@ __device__ __forceinline__ void sweep_producer(const Inst* __restrict__ tab, con
             ti.Pst = const_cast<typename MSG::T2*>(sp);
             ti.Hst = const_cast<typename MSG::T2*>(sh);
             ti.part = p.part;
+            ti.plen = (long long)part_len(p);
             ti.ctrl = ctrl;
             ti.L = L;
             ti.n = n; ti.Nt = p.Nt; ti.I = I; ti.J = J;
+            const int2 sl = tile_slots(p, w);
+            ti.sR = sl.x; ti.sC = sl.y;
             ti.t = t;
             ti.zero_h = *(volatile const int*)&ctrl->zero_h;
             ti.frozen = *(volatile const int*)&ctrl->p_frozen;
@@ -812,13 +817,14 @@ __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, co
         // the tile's remaining parameters, read before the slot is released
         const TileInfo ti = sm.info[slot];
         Ctrl* ctrl = ti.ctrl;
-        const int n = ti.n, Nt = ti.Nt, I = ti.I, J = ti.J;
+        const int I = ti.I;
         const int rows = tc.rows, cols = tc.cols;
         const bool diag = tc.diag;
         frozen = ti.frozen != 0;
         float* partP = ti.part;
-        float* partH = partP + (size_t)Nt * n;
-        float* partR = partH + (size_t)Nt * n;
+        float* partH = partP + ti.plen;
+        float* partR = partH + ti.plen;
+        const size_t oR = (size_t)ti.sR * T, oC = (size_t)ti.sC * T;
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.tempty[slot]);   // tile slot free for the producer
         if (++slot == 2) { slot = 0; tph ^= 1u; }
@@ -832,13 +838,13 @@ __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, co
                 float P = sm.rp[ctid], H = sm.rh[ctid], R = sm.rr[ctid];
 #pragma unroll
                 for (int w = 0; w < CW; ++w) { P += sm.cp[w][ctid]; H += sm.ch[w][ctid]; R += sm.cr[w][ctid]; }
-                const size_t o = (size_t)I * n + I * T + ctid;
+                const size_t o = oR + ctid;
                 if (!frozen) partP[o] = P;
                 partH[o] = H; partR[o] = R;
             }
         } else if (ctid < T) {
             if (ctid < rows) {
-                const size_t o = (size_t)J * n + I * T + ctid;
+                const size_t o = oR + ctid;
                 if (!frozen) partP[o] = sm.rp[ctid];
                 partH[o] = sm.rh[ctid]; partR[o] = sm.rr[ctid];
             }
@@ -848,7 +854,7 @@ __device__ __forceinline__ void sweep_consumers(const Inst* __restrict__ tab, co
                 float P = 0.f, H = 0.f, R = 0.f;
 #pragma unroll
                 for (int w = 0; w < CW; ++w) { P += sm.cp[w][c]; H += sm.ch[w][c]; R += sm.cr[w][c]; }
-                const size_t o = (size_t)I * n + J * T + c;
+                const size_t o = oC + c;
                 if (!frozen) partP[o] = P;
                 partH[o] = H; partR[o] = R;
             }
@@ -1196,25 +1202,26 @@ __device__ __forceinline__ void finalize_decide(const Inst& p, Ctrl* ctrl, int t
     __threadfence();
 }
 
-// Compensated sums of node x's slots k = k0, k0 + step, ... < Nt of NA
-// partial arrays (P, H[, R]), eight loads of each in flight; P reads as 0
-// when frozen (Ptilde is kept then).
+// Compensated sums of node x's slots k = k0, k0 + step, ... (of the
+// slot_count of its block) of NA partial arrays (P, H[, R]), eight loads of
+// each in flight; P reads as 0 when frozen (Ptilde is kept then).
 template <int NA>
 __device__ __forceinline__ void slot_sums(const Inst& p, int x, int k0, int step, bool frozen, float (&s)[NA],
                                           float (&c)[NA])
 {
-    const int n = p.n, Nt = p.Nt;
-    const float* part = p.part;
+    const int X = x / T, ns = slot_count(p, X);
+    const size_t len = part_len(p);
+    const float* part = p.part + (size_t)slot_begin(p, X) * T + (x - X * T);
 #pragma unroll
     for (int a = 0; a < NA; ++a) s[a] = c[a] = 0.f;
     int k = k0;
-    for (; k + 7 * step < Nt; k += 8 * step) {
+    for (; k + 7 * step < ns; k += 8 * step) {
         float v[NA][8];
 #pragma unroll
         for (int u = 0; u < 8; ++u)
 #pragma unroll
             for (int a = 0; a < NA; ++a) {
-                const size_t o = ((size_t)a * Nt + k + u * step) * n + x;
+                const size_t o = a * len + (size_t)(k + u * step) * T;
                 v[a][u] = (a == 0 && frozen) ? 0.f : part[o];
             }
 #pragma unroll
@@ -1222,9 +1229,9 @@ __device__ __forceinline__ void slot_sums(const Inst& p, int x, int k0, int step
 #pragma unroll
             for (int a = 0; a < NA; ++a) acc2(s[a], c[a], v[a][u]);
     }
-    for (; k < Nt; k += step)
+    for (; k < ns; k += step)
 #pragma unroll
-        for (int a = 0; a < NA; ++a) acc2(s[a], c[a], (a == 0 && frozen) ? 0.f : part[((size_t)a * Nt + k) * n + x]);
+        for (int a = 0; a < NA; ++a) acc2(s[a], c[a], (a == 0 && frozen) ? 0.f : part[a * len + (size_t)k * T]);
 }
 
 // Node-block units of a round's finalize.  Blocks [0, nsmall) of the list
@@ -1330,16 +1337,30 @@ __global__ void __launch_bounds__(256, 4)
 // slots of dropped tiles are never written by a sweep.
 __device__ __forceinline__ void zero_slots(const Inst& p, int x, bool with_p)
 {
-    float* partP = p.part;
-    float* partH = partP + (size_t)p.Nt * p.n;
-    float* partR = partH + (size_t)p.Nt * p.n;
-    for (int k = 0; k < p.Nt; ++k) {
+    const int X = x / T, ns = slot_count(p, X);
+    const size_t len = part_len(p);
+    float* partP = p.part + (size_t)slot_begin(p, X) * T + (x - X * T);
+    float* partH = partP + len;
+    float* partR = partH + len;
+    for (int k = 0; k < ns; ++k) {
         if (with_p) {
-            partP[(size_t)k * p.n + x] = 0.f;
-            partR[(size_t)k * p.n + x] = 0.f;
+            partP[(size_t)k * T] = 0.f;
+            partR[(size_t)k * T] = 0.f;
         }
-        partH[(size_t)k * p.n + x] = 0.f;
+        partH[(size_t)k * T] = 0.f;
     }
+}
+
+// The whole matrix's sum_{j != i} |Q_ij| of node x: the formation's slot sums
+// (array 0), or the first pass's sums of the tile-sparse option.
+__device__ __forceinline__ double offdiag_abs_sum(const Inst& p, int x)
+{
+    if (p.rsum) return p.rsum[x];
+    const int X = x / T, ns = slot_count(p, X);
+    const float* s0 = p.part + (size_t)slot_begin(p, X) * T + (x - X * T);
+    double R = 0.0;
+    for (int k = 0; k < ns; ++k) R += (double)s0[(size_t)k * T];
+    return R;
 }
 
 // Between the stages of a staged round: Ptilde and htilde of every node from
@@ -1513,8 +1534,7 @@ __global__ void k_init(Inst p, int diag_rule, float delta)
         c->rinf = -1.0;
     }
     if (x >= p.n) return;
-    double R = 0.0;
-    for (int k = 0; k < p.Nt; ++k) R += (double)p.part[(size_t)k * p.n + x];
+    const double R = offdiag_abs_sum(p, x);
     zero_slots(p, x, true);   // all messages start at 0
     const double lam2 = p.lam2;
     const double base = 1.0 + lam2 + 1.0 / (double)p.C;
@@ -1529,6 +1549,12 @@ __global__ void k_init(Inst p, int diag_rule, float delta)
     p.agg[p.npad + x] = bx;
     p.agg[2 * p.npad + x] = bx / qf;
     note_margin(p.ctrl, qf, R);
+}
+
+__global__ void k_row_abs_sums(Inst p, double* __restrict__ rsum)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < p.n) rsum[x] = offdiag_abs_sum(p, x);
 }
 
 // k_init over listed node blocks (block 0 of an instance resets its control block).
@@ -1550,8 +1576,7 @@ __global__ void k_init_list(const Inst* __restrict__ tab, const int2* __restrict
     }
     const int x = nb.y * 32 + threadIdx.x;
     if (threadIdx.x >= 32 || x >= p.n) return;
-    double R = 0.0;
-    for (int k = 0; k < p.Nt; ++k) R += (double)p.part[(size_t)k * p.n + x];
+    const double R = offdiag_abs_sum(p, x);
     zero_slots(p, x, true);   // all messages start at 0
     const double lam2 = p.lam2;
     const double base = 1.0 + lam2 + 1.0 / (double)p.C;
@@ -1629,6 +1654,11 @@ __global__ void k_get_pairs(Inst p, const long long* __restrict__ ij, long long 
 void launch_init(const Inst& p, int diag_rule, float delta, cudaStream_t s)
 {
     k_init<<<(p.n + 255) / 256, 256, 0, s>>>(p, diag_rule, delta);
+}
+
+void launch_row_abs_sums(const Inst& p, double* rsum, cudaStream_t s)
+{
+    k_row_abs_sums<<<(p.n + 255) / 256, 256, 0, s>>>(p, rsum);
 }
 
 void launch_reset(const Inst& p, cudaStream_t s) { k_reset<<<(p.n + 255) / 256, 256, 0, s>>>(p); }
