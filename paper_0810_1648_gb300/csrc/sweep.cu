@@ -946,10 +946,26 @@ struct RecomputedQ {
     {
         if (lane == 0) mbar_arrive(&ex->qempty[it & 1]);
     }
+    // The tile's rows are stored with their 16-byte chunks permuted: chunk c
+    // of row r sits at chunk c ^ (r % 8), so that the epilogue's stores (one
+    // row per lane, the same chunk) spread over all banks; a consumer warp
+    // still reads one row's 256 contiguous bytes.
     template <int G>
     __device__ __forceinline__ void q4(const unsigned char*, int, int r, int lane, int it, float (&q)[4]) const
     {
-        ld4<G>(qtile + (size_t)(it & 1) * TT + (size_t)r * T, lane, q);
+        const unsigned char* row = reinterpret_cast<const unsigned char*>(qtile + (size_t)(it & 1) * TT + (size_t)r * T);
+        const int sw = r & 7;
+        if constexpr (G == 4) {
+            const uint2 u = *reinterpret_cast<const uint2*>(row + (((lane >> 1) ^ sw) << 4) + ((lane & 1) << 3));
+            const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+            const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+            q[0] = a.x; q[1] = a.y; q[2] = b.x; q[3] = b.y;
+        } else {
+            const int o = ((lane >> 2) ^ sw) << 4 | ((lane & 3) << 2);
+            const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(row + o));
+            const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(row + 128 + o));
+            q[0] = a.x; q[1] = a.y; q[2] = b.x; q[3] = b.y;
+        }
     }
 };
 
@@ -1093,11 +1109,11 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
             stage_tile_cols(ex.cols[g], y, sqb, n, J, gamma, lane, 0, T / 32);
             const float ai = -gamma * kLog2e * si, c2 = 2.f * gamma * kLog2e;
             const uint32_t s1 = __float_as_uint(yi) & 0x80000000u, si2 = s1 | (s1 >> 16);
-            __nv_bfloat16* qrow = qtile + (size_t)acc * TT + (size_t)r * T;
+            uint4* qrow = reinterpret_cast<uint4*>(qtile + (size_t)acc * TT + (size_t)r * T);   // 16 chunks
+            const int sw = r & 7;   // chunk c stored at c ^ sw (see RecomputedQ)
 #pragma unroll 1
             for (int cc = 0; cc < T / 32; ++cc) {
                 const uint32_t valid = chunk_valid(n, I, J, r, cc);
-                uint4* dst = reinterpret_cast<uint4*>(qrow + 32 * cc);
                 float v[32];
                 tmem_ld32(tbase + (uint32_t)acc * T + ((uint32_t)(32 * g) << 16) + (uint32_t)(32 * cc), v);
 #pragma unroll
@@ -1107,8 +1123,8 @@ __global__ void __launch_bounds__(RC_THREADS, 1)
                     for (int u = 0; u < 16; ++u) vh[u] = v[16 * h + u];
                     uint4 out[2];
                     q_half_bf16(vh, 32 * cc + 16 * h, ai, si2, ex.cols[g], c2, lam2, (valid >> (16 * h)) & 0xffffu, out);
-                    dst[2 * h] = out[0];
-                    dst[2 * h + 1] = out[1];
+                    qrow[(4 * cc + 2 * h) ^ sw] = out[0];
+                    qrow[(4 * cc + 2 * h + 1) ^ sw] = out[1];
                 }
             }
             tc_fence_before();
