@@ -1262,10 +1262,11 @@ __device__ __forceinline__ int fin_units(const Sched* sc, int& usmall)
     return usmall + (sc->nblocks - sc->nsmall);
 }
 
-// Per node x: compensated sums of its Nt slots, next aggregates, residual
+// Per node x: compensated sums of its slots, next aggregates, residual
 // r_x(t) in FP64, max |r| -> ctrl; the last node block of an instance to
-// finish decides.
-__global__ void __launch_bounds__(256, 4)
+// finish decides.  Five CTAs per SM (48 registers a thread), so that one
+// CTA per 32-node block of n = 20000 (625) runs in a single wave.
+__global__ void __launch_bounds__(256, 5)
     k_finalize(const Inst* __restrict__ tab, const int2* __restrict__ nbl, const Sched* __restrict__ sched)
 {
     int usmall;
