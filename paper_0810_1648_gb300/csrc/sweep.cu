@@ -22,9 +22,10 @@
 // issued by a producer warp well ahead of use; consumer warp w takes rows w
 // and w + 8 of each 16-row chunk, each lane four of their columns laid out so
 // that every warp access to a row is one contiguous 512-byte span (lane_col).
-// Row sums go through one warp reduction per two rows, column sums stay in registers and
-// meet in shared memory, and each node's per-tile sums go to its own slot
-// (common.cuh), so the reduction order is fixed and the result reproducible.
+// Row sums go through one warp reduction per two rows (four with BF16
+// messages), column sums stay in registers and meet in shared memory, and each
+// node's per-tile sums go to its own slot (common.cuh), so the reduction order
+// is fixed and the result reproducible.
 #include "common.cuh"
 #include "ptx.cuh"
 #include "qtile_epi.cuh"
@@ -63,8 +64,9 @@ __device__ __forceinline__ void consumer_bar() { asm volatile("bar.sync 1, %0;" 
 //                 turn the Gram rows into BF16 Q values in a double-buffered
 //                 shared-memory Q tile, which the consumers read in place of
 //                 a stored tile (bitwise the same values as the BF16 store).
-// Rows per ring stage (16), split over the consumer warps: two per warp
-// with 8 consumer warps (stored Q), one per warp with 16 (recompute).
+// Rows per ring stage (16), two per consumer warp (eight consumer warps in
+// both kernels, so that the recomputed and the stored form sum in the same
+// order).
 constexpr int RC_ROWS = 16;
 template <class MSG>
 __host__ __device__ constexpr int rc() { return RC_ROWS; }
