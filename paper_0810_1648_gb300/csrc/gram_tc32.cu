@@ -137,7 +137,7 @@ struct T3Smem {
     float colsum[4][T];                 // per lane quarter: column sums over its 32 rows
     float rowsum[2][T];                 // per column half: row sums
     float tmx[T3_EPI_WARPS];
-    alignas(16) float cy[T3_EPI_WARPS][64];   // a warp's 64 columns: labels
+    alignas(16) uint32_t cy[T3_EPI_WARPS][64];   // a warp's 64 columns: sign bits of the labels
     alignas(16) float cs[T3_EPI_WARPS][64];   // and FP32 norms
 };
 
@@ -158,6 +158,39 @@ __device__ __forceinline__ float transpose_sum32(float (&v)[32], int lane)
         }
     }
     return v[0];
+}
+
+// FP32 Q entries of 32 columns of one tile row from the Gram values g,
+// the staged column sign bits sy and norms sn: q = y_i y_j (exp(-gamma d2) +
+// lambda^2), d2 = max(0, ||x_i||^2 + ||x_j||^2 - 2 g); the label product is a
+// flip of the sign bit (y = +-1).  Not FULL: entries outside the pair set
+// (i >= n, column j0 + cb + c >= n, or c + cb <= rdiag on a diagonal tile)
+// are 0.  Adds |q| to the row sums rs4[c % 4].
+template <bool FULL>
+__device__ __forceinline__ void q_chunk32(const float* g, const uint32_t* sy, const float* sn, float si, uint32_t syi,
+                                          float ngam, float lam2, int i, int n, int cb, int j0, int rdiag,
+                                          float (&q)[32], float (&rs4)[4])
+{
+#pragma unroll
+    for (int c4 = 0; c4 < 32; c4 += 4) {
+        const uint4 y4 = *reinterpret_cast<const uint4*>(sy + c4);
+        const float4 s4 = *reinterpret_cast<const float4*>(sn + c4);
+        const uint32_t yj[4] = {y4.x, y4.y, y4.z, y4.w};
+        const float sj[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const float d2 = fmaxf(0.f, si + sj[t] - 2.f * g[c4 + t]);
+            const float e = expf(ngam * d2) + lam2;
+            float qv = __uint_as_float(__float_as_uint(e) ^ syi ^ yj[t]);
+            if (!FULL) {
+                const int c = cb + c4 + t;
+                const bool valid = i < n && j0 + c < n && c > rdiag;
+                qv = valid ? qv : 0.f;
+            }
+            q[c4 + t] = qv;
+            rs4[t] += fabsf(qv);
+        }
+    }
 }
 
 __global__ void __launch_bounds__(T3_THREADS, 1)
@@ -292,8 +325,19 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                         tmem_ld16(tbase + (uint32_t)(acc * T3_NACC + a) * T + ((uint32_t)(32 * g) << 16) +
                                       (uint32_t)(c0 + 16 * j),
                                   v);
+                        if (kc == 0 && a == 0) {
 #pragma unroll
-                        for (int c = 0; c < 16; ++c) ga[16 * j + c] = (kc == 0 && a == 0) ? v[c] : ga[16 * j + c] + v[c];
+                            for (int c = 0; c < 16; ++c) ga[16 * j + c] = v[c];
+                        } else {
+                            // two columns per instruction, each rounded as a scalar add
+#pragma unroll
+                            for (int c = 0; c < 16; c += 2) {
+                                const float2 t2 = __fadd2_rn(make_float2(ga[16 * j + c], ga[16 * j + c + 1]),
+                                                             make_float2(v[c], v[c + 1]));
+                                ga[16 * j + c] = t2.x;
+                                ga[16 * j + c + 1] = t2.y;
+                            }
+                        }
                     }
                 }
                 tc_fence_before();
@@ -328,32 +372,28 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
                     const int j = J * T + c0 + 32 * u + lane;
-                    sm.cy[ew][32 * u + lane] = j < n ? p.y[j] : 0.f;
+                    sm.cy[ew][32 * u + lane] = j < n ? (__float_as_uint(p.y[j]) & 0x80000000u) : 0u;
                     sm.cs[ew][32 * u + lane] = j < n ? p.sq3[j] : 0.f;
                 }
                 __syncwarp();
-                const float yi = i < n ? p.y[i] : 0.f, si = i < n ? p.sq3[i] : 0.f;
+                const float si = i < n ? p.sq3[i] : 0.f, ngam = -p.gamma, lam2 = p.lam2;
+                const uint32_t syi = i < n ? (__float_as_uint(p.y[i]) & 0x80000000u) : 0u;
+                // interior tile: every pair valid
+                const bool full = I != J && (I + 1) * T <= n && (J + 1) * T <= n;
                 float* qt = p.qref ? p.qref + (size_t)w.w * TT + (size_t)r * T + c0 : nullptr;
                 float rs4[4] = {0.f, 0.f, 0.f, 0.f}, tmx = 0.f;   // row sum in four interleaved parts
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
                     float q[32];
+                    if (full)
+                        q_chunk32<true>(ga + 32 * u, sm.cy[ew] + 32 * u, sm.cs[ew] + 32 * u, si, syi, ngam, lam2,
+                                        0, 0, 0, 0, 0, q, rs4);
+                    else
+                        q_chunk32<false>(ga + 32 * u, sm.cy[ew] + 32 * u, sm.cs[ew] + 32 * u, si, syi, ngam, lam2,
+                                         i, n, c0 + 32 * u, J * T, I == J ? r : -1, q, rs4);
+                    if (p.tilemax) {
 #pragma unroll
-                    for (int c4 = 0; c4 < 32; c4 += 4) {
-                        const float4 y4 = *reinterpret_cast<const float4*>(&sm.cy[ew][32 * u + c4]);
-                        const float4 s4 = *reinterpret_cast<const float4*>(&sm.cs[ew][32 * u + c4]);
-                        const float yj[4] = {y4.x, y4.y, y4.z, y4.w};
-                        const float sj[4] = {s4.x, s4.y, s4.z, s4.w};
-#pragma unroll
-                        for (int t = 0; t < 4; ++t) {
-                            const int c = c0 + 32 * u + c4 + t, j = J * T + c;
-                            const bool valid = i < n && j < n && (I != J || c > r);
-                            const float d2 = fmaxf(0.f, si + sj[t] - 2.f * ga[32 * u + c4 + t]);
-                            const float qv = yi * yj[t] * (expf(-p.gamma * d2) + p.lam2);
-                            q[c4 + t] = valid ? qv : 0.f;
-                            rs4[t] += fabsf(q[c4 + t]);
-                            tmx = fmaxf(tmx, fabsf(q[c4 + t]));
-                        }
+                        for (int c = 0; c < 32; ++c) tmx = fmaxf(tmx, fabsf(q[c]));
                     }
                     if (qt) {
 #pragma unroll
