@@ -416,9 +416,10 @@ def run_sparse(args):
     big = args.sparse_n > 20000
     if big:
         tau = 5e-5
-        p = workloads.clustered_mixture(args.sparse_n, 64, seed=5, gamma=0.3, C=1.0, sigma=0.5)
+        comps = args.sparse_comps
+        p = workloads.clustered_mixture(args.sparse_n, 64, seed=5, gamma=0.3, C=1.0, comps=comps, sigma=0.5)
         names = (("tile_sparse", tau),)
-        desc = (f"tile-sparse kernel: n={p.n}, m=64 mixture (3 components per class, sigma 0.5, seed 5) with "
+        desc = (f"tile-sparse kernel: n={p.n}, m=64 mixture ({comps} components per class, sigma 0.5, seed 5) with "
                 f"rows grouped by component, RBF gamma=0.3, C=1, tiles with max |Q_ij| <= {tau} dropped; "
                 "100 synchronous sweeps per step; the dense message state (8 n^2 bytes) exceeds the device")
     else:
@@ -927,6 +928,9 @@ def main():
                          "bf16_refined_staged (default all)")
     ap.add_argument("--sparse-n", type=int, default=20000,
                     help="sparse_large: n of the clustered set (20000, or e.g. 200000 beyond dense memory)")
+    ap.add_argument("--sparse-comps", type=int, default=3,
+                    help="sparse_large beyond 20000: mixture components per class (3; more components keep "
+                         "fewer tiles, e.g. 12 at n=500000)")
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--duration", type=float, default=60.0)
     ap.add_argument("--max-members", type=int, default=64)
