@@ -124,9 +124,13 @@ typedef struct {
                               128 x 128 tiles): every off-diagonal tile whose largest |Q_ij| <= sparse_tau
                               is dropped, i.e. solved as 0 (its messages stay 0 and are never swept);
                               the diagonal keeps the row sums of the whole matrix, so the matrix stays
-                              diagonally dominant and only the dropped entries change.  Effective when rows are
-                              ordered so that near points share tiles.  0 = dense (default).  Single-
-                              instance API only (not the batched or served forms) */
+                              diagonally dominant and only the dropped entries change.  Device memory:
+                              the messages, Q and per-node partial sums of the kept tiles only, plus
+                              bookkeeping of 48 B per tile and, during formation, a temporary array of
+                              4 n^2 / 128 B for the first pass's row sums (freed before the kept tiles'
+                              storage is allocated).  Effective when rows are ordered so that near points
+                              share tiles.  0 = dense (default).  Single-instance API only (not the
+                              batched or served forms) */
     int32_t reserved[1];
 } gabp_svm_opts;
 
