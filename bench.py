@@ -491,6 +491,71 @@ def run_sparse(args):
     return 0
 
 
+# Shapes (n x m) of the data sets the paper times in Section 5 (Tables 2 and 3),
+# with the paper's run time in seconds and its hardware: context only (other
+# machines, other data).  The bench fills them with the seeded mixture.
+PAPER_SHAPES = (
+    ("table2_6238x617", 6238, 617, 228.0, "5 x 3.5 GHz Pentium, MPICH2"),
+    ("table2_20000x16", 20000, 16, 468.0, "5 x 3.5 GHz Pentium, MPICH2"),
+    ("table2_8124x117", 8124, 117, 226.0, "5 x 3.5 GHz Pentium, MPICH2"),
+    ("table2_12960x25", 12960, 25, 221.0, "5 x 3.5 GHz Pentium, MPICH2"),
+    ("table2_5473x10", 5473, 10, 26.0, "5 x 3.5 GHz Pentium, MPICH2"),
+    ("table2_7494x16", 7494, 16, 45.0, "5 x 3.5 GHz Pentium, MPICH2"),
+    ("table2_4601x57", 4601, 57, 49.0, "5 x 3.5 GHz Pentium, MPICH2"),
+    ("table3_150000x54", 150000, 54, 468.0, "1024 CPUs of an IBM Blue Gene"),
+    ("table3_60000x784", 60000, 784, 756.0, "1024 CPUs of an IBM Blue Gene"),
+)
+
+
+def run_paper_shapes(args):
+    """Whole solves (formation + rounds to ||r||_inf < 1e-6, at most 200) on
+    seeded mixtures with the shapes of the data sets Section 5 times, gamma =
+    1/m, C = 1, plain FP32 and BF16 refined, inputs resident on the device,
+    CUDA events around each solve (after one warm-up solve).  The paper's run
+    times are quoted beside them as context: they were measured on CPU
+    clusters, on the real data sets, for the whole training."""
+    import torch
+
+    from paper_0810_1648_gb300 import build as gbuild
+    from paper_0810_1648_gb300 import gabp
+    if not os.path.exists(gabp.LIB_PATH):
+        gbuild.build()
+    gabp.load()
+    stream = torch.cuda.Stream()
+    out = {}
+    for k, (name, n, m, paper_s, hw) in enumerate(PAPER_SHAPES):
+        p = workloads.mixture(n, m, seed=300 + k, gamma=1.0 / m, C=1.0)
+        Xd, yd = torch.from_numpy(p.X).cuda(), torch.from_numpy(p.y).cuda()
+        alpha = torch.empty(n, dtype=torch.float32, device="cuda")
+        res = {"n": n, "m": m, "paper_run_time_s": paper_s, "paper_hardware": hw}
+        for form, kw in (("f32", dict(q_mode=0)), ("bf16_refined", dict(q_mode=1, refine=10, msg_bf16=1))):
+            h = gabp.svm_create(Xd, yd, p.gamma, p.C, gabp.opts_default(stream=stream.cuda_stream, chunk=8, **kw))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for rep in range(2):
+                torch.cuda.synchronize()
+                e0.record(stream)
+                gabp.svm_refit(h, Xd, yd, p.gamma, p.C)
+                rinf, it = gabp.svm_solve(h, 200, 1e-6, alpha)
+                e1.record(stream)
+                torch.cuda.synchronize()
+            st = gabp.svm_get_stats(h)
+            res[form] = {"ms": float(e0.elapsed_time(e1)), "rounds": int(it), "residual_inf": float(rinf),
+                         "converged": int(st["converged"]), "err_bound_over_C": st["err_bound"] / p.C,
+                         "support_vectors": int((alpha > 0).sum().item())}
+            gabp.svm_destroy(h)
+        out[name] = res
+        del Xd, yd, alpha
+        torch.cuda.empty_cache()
+    line = {"metric": METRIC, "value": None, "unit": "ms per whole solve", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "higher_is_better": False, "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "seeded mixtures (3 components per class, sigma 0.7) with the shapes of the data "
+                                   "sets of the paper's Tables 2 and 3, gamma = 1/m, C = 1, to ||r||_inf < 1e-6 "
+                                   "(at most 200 rounds), formation included"},
+            "shapes": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _serve_run(gabp, rate, duration, q_mode, msg_bf16, stages, max_members):
     """Replays the seeded Poisson stream (rate/s for `duration` s) in real time
     through the continuous-batching server; returns latency percentiles,
@@ -922,7 +987,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched, precision and serving measurements added to the default line")
     ap.add_argument("--workload", default="plain_large",
-                    choices=["plain_large", "precision_large", "batch_grid", "serve", "sparse_large"])
+                    choices=["plain_large", "precision_large", "batch_grid", "serve", "sparse_large",
+                             "paper_shapes"])
     ap.add_argument("--batch-modes", default="",
                     help="batch_grid: comma-separated subset of f32, bf16q_refined, bf16_refined, f32_staged, "
                          "bf16_refined_staged (default all)")
@@ -953,6 +1019,8 @@ def main():
         return run_batch(args)
     if args.workload == "sparse_large":
         return run_sparse(args)
+    if args.workload == "paper_shapes":
+        return run_paper_shapes(args)
     if args.workload == "serve":
         return run_serve(args)
     if args.impl == "reference":
