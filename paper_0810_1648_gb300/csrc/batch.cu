@@ -155,23 +155,41 @@ __global__ void k_fetch(const W* __restrict__ src, W* __restrict__ dst, size_t c
 // instance in slot order, each instance's tiles (I, J) of the stage's band
 // I-major (the order the sweeps' results do not depend on, kept anyway);
 // node blocks of the instances finalized one warp per block first; and every
-// stage's Sched.  One CTA: the instances go through in chunks of blockDim
-// with a block-wide scan for their offsets, one warp writes one instance's
-// entries.
+// stage's Sched.  Every CTA computes all offsets (the instances go through in
+// chunks of blockDim with a block-wide scan); instance k's entries are written
+// by one warp of CTA k % gridDim.x, so the writing is spread over the GPU.
 constexpr int kListThreads = 1024;
 
+// Exclusive scan over the block (blockDim.x a multiple of 32, at most 1024):
+// warp-shuffle scans, then one scan of the warp totals.  sc[blockDim.x - 1]
+// holds the block's total afterwards, until the next call.
 __device__ __forceinline__ long long block_scan_excl(long long v, long long* sc)
 {
-    const int tid = threadIdx.x;
-    sc[tid] = v;
-    __syncthreads();
-    for (int d = 1; d < (int)blockDim.x; d <<= 1) {
-        const long long a = tid >= d ? sc[tid - d] : 0;
-        __syncthreads();
-        sc[tid] += a;
-        __syncthreads();
+    __shared__ long long wsum[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (int)blockDim.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
     }
-    return sc[tid] - v;   // sc[blockDim - 1] holds the chunk's total until the next call
+    __syncthreads();   // wsum and sc of the previous call are consumed
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        long long w = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += y;
+        }
+        wsum[lane] = w;   // inclusive scan of the warp totals
+    }
+    __syncthreads();
+    const long long incl = x + (warp > 0 ? wsum[warp - 1] : 0);
+    sc[tid] = incl;
+    __syncthreads();
+    return incl - v;
 }
 
 __global__ void __launch_bounds__(kListThreads)
@@ -210,7 +228,7 @@ __global__ void __launch_bounds__(kListThreads)
             const long long total = sc[blockDim.x - 1];
             __syncthreads();
             for (int i = warp; i < (int)blockDim.x; i += nw) {
-                if (m_k[i] < 0) continue;
+                if (m_k[i] < 0 || m_k[i] % (int)gridDim.x != (int)blockIdx.x) continue;
                 const int kk = m_k[i], nt = m_a[i], bs = m_b[i], be = m_c[i];
                 long long o = m_off[i];
                 for (int I = 0; I < be; ++I) {
@@ -245,7 +263,7 @@ __global__ void __launch_bounds__(kListThreads)
             const long long total = sc[blockDim.x - 1];
             __syncthreads();
             for (int i = warp; i < (int)blockDim.x; i += nw) {
-                if (m_k[i] < 0) continue;
+                if (m_k[i] < 0 || m_k[i] % (int)gridDim.x != (int)blockIdx.x) continue;
                 for (int b = lane; b < m_a[i]; b += 32) nbl[m_off[i] + b] = make_int2(m_k[i], b);
             }
             carry += total;
@@ -255,7 +273,7 @@ __global__ void __launch_bounds__(kListThreads)
         bbase += carry;
     }
     __syncthreads();
-    if (tid < S) {
+    if (blockIdx.x == 0 && tid < S) {
         long long off = 0;
         for (int s2 = 0; s2 < tid; ++s2) off += s_tiles[s2];
         Sched q{};
@@ -847,7 +865,8 @@ class Engine {
         }
         if (tiles > cap_tiles || blocks > cap_nblk) return fail(GABP_ENOMEM, "batch lists exceed their capacity");
         EK(cudaMemcpyAsync(d_live, h_live, (size_t)cap_members * sizeof(int), cudaMemcpyHostToDevice, stream));
-        k_build_lists<<<1, kListThreads, 0, stream>>>(d_tab, d_live, cap_members, nstages, d_work, d_nbl, d_sched);
+        k_build_lists<<<std::max(1, std::min(cap_members, num_sms())), kListThreads, 0, stream>>>(
+            d_tab, d_live, cap_members, nstages, d_work, d_nbl, d_sched);
         EK(cudaGetLastError());
         ++launches;
         live_tiles = tiles;
