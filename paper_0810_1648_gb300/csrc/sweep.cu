@@ -437,17 +437,10 @@ __device__ __forceinline__ void st4(float* row, int lane, const float (&o)[4])
     }
 }
 
-// Sums the eight values {a0, a1, a2, 0, b0, b1, b2, 0} over the warp in a
-// fixed order: afterwards every lane of the group (lane / 4) % 8 = k holds the
-// total of value k (nine shuffles for two rows).
-__device__ __forceinline__ float reduce_scatter8x(const float (&x)[8], int lane);
-__device__ __forceinline__ float reduce_scatter8(float a0, float a1, float a2, float b0, float b1, float b2,
-                                                 int lane)
-{
-    const float x[8] = {a0, a1, a2, 0.f, b0, b1, b2, 0.f};
-    return reduce_scatter8x(x, lane);
-}
-// The same for eight values {x0 .. x7}.
+// Sums the eight values {x0 .. x7} over the warp in a fixed order:
+// afterwards every lane of the group (lane / 4) % 8 = k holds the total of
+// value k (nine shuffles: the three sums of two rows, or the H and residual
+// sums of four rows once P is frozen).
 __device__ __forceinline__ float reduce_scatter8x(const float (&x)[8], int lane)
 {
     const bool hi = (lane & 16) != 0;
@@ -465,6 +458,13 @@ __device__ __forceinline__ float reduce_scatter8x(const float (&x)[8], int lane)
     v += __shfl_xor_sync(0xffffffffu, v, 2);
     v += __shfl_xor_sync(0xffffffffu, v, 1);
     return v;
+}
+// The three sums {P, H, R} of two rows: values {a0, a1, a2, 0, b0, b1, b2, 0}.
+__device__ __forceinline__ float reduce_scatter8(float a0, float a1, float a2, float b0, float b1, float b2,
+                                                 int lane)
+{
+    const float x[8] = {a0, a1, a2, 0.f, b0, b1, b2, 0.f};
+    return reduce_scatter8x(x, lane);
 }
 
 // Sums the four values {a0, a1, a2, a3} over the warp in a fixed order:
@@ -911,9 +911,10 @@ __global__ void __launch_bounds__(SWEEP_THREADS, sweep_ctas<MSG>())
 // ---- fused recompute ------------------------------------------------------
 constexpr int RC_XSTAGES = 2;
 // Consumer warps (two rows of each 16-row stage each).  Sixteen consumers
-// (one row each, 88 registers a thread) measured slower: 0.71 / 0.51 of the
-// copy peak against 0.77 / 0.53 with eight.  Eight also keep the summation
-// order of the stored-Q sweep, so recomputed and stored forms agree bitwise.
+// (one row each, 88 registers a thread) measured slower with an earlier
+// consumer (0.71 / 0.51 of the copy peak against 0.77 / 0.53 with eight).
+// Eight also keep the summation order of the stored-Q sweep, so recomputed
+// and stored forms agree bitwise.
 constexpr int RC_CW = 8;
 constexpr int RC_THREADS = (7 + RC_CW) * 32;   // 3 role warps + 4 epilogue + 8 consumers
 constexpr uint32_t RC_TMEM_COLS = 256;
