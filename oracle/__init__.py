@@ -77,6 +77,8 @@ def _load():
         "orc_q_diag_all": (i32, [D, D, L, L, f64, f64, f64, i32, f64, D, D]),
         "orc_q_diag_tilemax": (i32, [D, D, L, L, f64, f64, f64, i32, f64, L, D, D, D]),
         "orc_residual_tile_sparse": (f64, [D, D, L, L, f64, f64, D, L, ctypes.c_void_p, D, D]),
+        "orc_rows_tile_sparse": (i32, [D, D, L, L, f64, f64, f64, i32, f64, L, f64, ctypes.POINTER(ctypes.c_long), L,
+                                       D, D, D, D, D]),
         "orc_cg_rbf": (i32, [D, D, L, L, f64, f64, f64, i32, f64, D, f64, i32, D, I]),
         "orc_dual_objective": (f64, [D, D, L]),
         "orc_decision": (i32, [D, D, D, L, L, D, L, f64, f64, D]),
@@ -201,6 +203,30 @@ def residual_tile_sparse(X, y, gamma, diag, keep, mu, block=128, lam=None):
     rinf = _load().orc_residual_tile_sparse(px, py, n, m, gamma, lam, pd, int(block), kp.ctypes.data, pm,
                                             r.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     return r, float(rinf)
+
+
+def rows_tile_sparse(X, y, gamma, C, tau, rows, mu, block=128, lam=None, diag_rule=DIAG_DOMINANT, delta=0.1):
+    """For the chosen rows only (matrices too large for the whole-matrix
+    passes): (tmax, R, diag, r) with tmax[k, J] the largest |Q| of tile (I, J)
+    of row k's block row I, R[k] = sum_{j != i} |Q_ij| over the whole row,
+    diag[k] the diagonal rule's Q_ii, and r[k] = 1 - (Q mu)_i of the tile-sparse
+    matrix (tiles (I, J) with J == I or tmax > tau), all in FP64."""
+    X, px = _d(X)
+    y, py = _d(y)
+    n, m = X.shape
+    lam = default_lambda(n) if lam is None else lam
+    mu, pm = _d(mu)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    nt = (n + block - 1) // block
+    k = rows.shape[0]
+    tmax, R, diag, r = np.empty((k, nt)), np.empty(k), np.empty(k), np.empty(k)
+    P = ctypes.POINTER(ctypes.c_double)
+    rc = _load().orc_rows_tile_sparse(px, py, n, m, gamma, lam, C, diag_rule, delta, int(block), float(tau),
+                                      rows.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), k, pm,
+                                      tmax.ctypes.data_as(P), R.ctypes.data_as(P), diag.ctypes.data_as(P),
+                                      r.ctypes.data_as(P))
+    _check(rc, "rows_tile_sparse")
+    return tmax, R, diag, r
 
 
 class GabpResult:

@@ -243,6 +243,58 @@ double orc_residual_tile_sparse(const double* X, const double* y, long n, long m
     return rmax;
 }
 
+/* The same quantities for chosen rows only, for matrices too large for the
+ * whole-matrix passes above: for each row i of rows[0 .. nrows), with I = i /
+ * block, the largest |Q_ab| of every tile (I, J), J = 0 .. Nt - 1 (pairs a != b
+ * of block I x block J: the tile of the pair, upper or lower, holds the same
+ * entries), tmax_rows[k * Nt + J] for the k-th row; R[k] = sum_{j != i} |Q_ij|
+ * over the whole row, diag[k] the diagonal rule's Q_ii from it; and the
+ * residual r[k] = 1 - diag[k] mu_i - sum_j Q_ij mu_j over the j of the tiles
+ * (I, J) kept under the threshold tau (J == I, or tmax > tau), as the
+ * tile-sparse matrix defines it.  O(nrows n m). */
+int orc_rows_tile_sparse(const double* X, const double* y, long n, long m, double gamma, double lam, double C,
+                         int diag_rule, double delta, long block, double tau, const long* rows, long nrows,
+                         const double* mu, double* tmax_rows, double* R, double* diag, double* r)
+{
+    if (n < 1 || m < 1 || block < 1 || !(gamma > 0) || !(C > 0)) return ORC_EINVAL;
+    const long Nt = (n + block - 1) / block;
+    for (long k = 0; k < nrows; ++k) {
+        const long i = rows[k];
+        if (i < 0 || i >= n) return ORC_EINVAL;
+        const long I = i / block, a1 = (I + 1) * block < n ? (I + 1) * block : n;
+        double* tm = tmax_rows + k * Nt;
+        /* tile maxima of block row I (those of the previous row when it has the same block) */
+        const int same = k > 0 && rows[k - 1] / block == I;
+#pragma omp parallel for schedule(dynamic, 4)
+        for (long J = 0; J < Nt; ++J) {
+            if (same) { tm[J] = tm[J - Nt]; continue; }
+            const long b1 = (J + 1) * block < n ? (J + 1) * block : n;
+            double v = 0.0;
+            for (long a = I * block; a < a1; ++a)
+                for (long bb = J * block; bb < b1; ++bb) {
+                    if (a == bb) continue;
+                    const double q = fabs(orc_q_offdiag(X + a * m, X + bb * m, y[a], y[bb], m, gamma, lam));
+                    if (q > v) v = q;
+                }
+            tm[J] = v;
+        }
+        /* whole-row sum, diagonal, kept-tile residual */
+        double s_abs = 0.0, s_mu = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : s_abs, s_mu)
+        for (long j = 0; j < n; ++j) {
+            if (j == i) continue;
+            const double q = orc_q_offdiag(X + i * m, X + j * m, y[i], y[j], m, gamma, lam);
+            s_abs += fabs(q);
+            const long J = j / block;
+            if (J == I || tm[J] > tau) s_mu += q * mu[j];
+        }
+        R[k] = s_abs;
+        diag[k] = orc_q_diag(s_abs, lam, C, diag_rule, delta);
+        r[k] = 1.0 - diag[k] * mu[i] - s_mu;
+    }
+    return ORC_OK;
+}
+
 /* r = b - Q mu, returns ||r||_inf.  The paper's Step 3 tests the messages for
  * convergence without naming a norm; the reading used throughout is the
  * infinity norm of the linear-system residual of the current means. */

@@ -528,6 +528,32 @@ def test_q_diag_tilemax_pass():
             assert keep[I, J] == (I == J or tmax[I, J] > 1e-3)
 
 
+def test_rows_tile_sparse_against_whole_matrix():
+    """The chosen-rows pass equals the whole-matrix passes on those rows: tile
+    maxima of the row's block row (both triangles, from q_diag_tilemax's
+    upper triangle), whole-row |Q| sums and diagonal (q_diag_all), and the
+    residual 1 - Q mu of the dense tile-sparse matrix (ragged n, two block
+    edges, rows on first, inner and last blocks)."""
+    p = workloads.clustered_mixture(301, 5, seed=15, gamma=0.4)
+    X, y = p.X.astype(np.float64), p.y.astype(np.float64)
+    mu = np.random.default_rng(17).standard_normal(p.n)
+    d0, R0 = oracle.q_diag_all(X, y, p.gamma, p.C)
+    rows = np.array([0, 5, 127, 128, 200, 300])
+    for block, tau in ((128, 1e-3), (40, 1e-2)):
+        Q, keep = oracle.build_q_tile_sparse(X, y, p.gamma, p.C, tau, block=block)
+        _, _, tmax_up = oracle.q_diag_tilemax(X, y, p.gamma, p.C, block=block)
+        full = np.maximum(tmax_up, tmax_up.T)   # tile (I, J) and (J, I) hold the same entries
+        tmax, R, d, r = oracle.rows_tile_sparse(X, y, p.gamma, p.C, tau, rows, mu, block=block)
+        for k, i in enumerate(rows):
+            I = i // block
+            np.testing.assert_allclose(tmax[k], full[I], rtol=1e-13, atol=1e-300)
+        np.testing.assert_allclose(R, R0[rows], rtol=1e-12)
+        np.testing.assert_allclose(d, d0[rows], rtol=1e-12)
+        want = (1.0 - Q @ mu)[rows]
+        np.testing.assert_allclose(r, want, rtol=1e-11, atol=1e-12 * np.max(np.abs(want)))
+        assert not keep.all()
+
+
 def test_residual_tile_sparse_against_dense_matrix():
     """The kept-tiles-only residual equals 1 - Q mu with the dense tile-sparse
     matrix of build_q_tile_sparse (ragged n, two block edges)."""
