@@ -426,15 +426,15 @@ gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
     h->prof.kernel_launches += 2;
     if (h->opts.sparse_tau > 0) {
         // Tile-sparse option.  Pass 1 over every tile: tile maxima and |Q|
-        // row sums (the whole matrix's, for the diagonal rule), nothing
-        // stored.  Then the kept-tile list and its compacted storage, and
-        // pass 2 over the kept tiles only: their FP32 values (the store, or
-        // the FP32 copy beside the BF16 store; the row sums it writes again
-        // are the same values), the diagonal rule and Step 1, and the BF16
-        // tiles.  Recompute needs no second pass.
-        // The first pass writes its |Q| row sums into dense slots (one array,
-        // in the second allocation) and reduces them to rsum, the diagonal
-        // rule's sums; the kept tiles' storage then replaces them.
+        // row sums (the whole matrix's, for the diagonal rule), Q not
+        // stored; the row sums go to dense slots (one array, in the second
+        // allocation) and are reduced to rsum per node.  Then the kept-tile
+        // list, the compacted slot space and the kept tiles' storage (which
+        // replaces the dense slots), and pass 2 over the kept tiles only:
+        // their FP32 values (the store, or the FP32 copy beside the BF16
+        // store; the row sums it writes into the compacted slots are not
+        // used, the diagonal rule takes rsum), the diagonal rule and Step 1,
+        // and the BF16 tiles.  Recompute needs no second pass.
         if (h->opts.q_mode != GABP_Q_F32)
             CK(launch_pack_bf16(p.X, (int)n, (int)m, p.nkc, h->Nt, (void*)p.Xp, (float*)p.sqb, s));
         if (gabp_status st = ensure_spool(h, (size_t)h->Nt * h->Nt * T * sizeof(float), "the first pass's row sums"))
