@@ -99,7 +99,8 @@ typedef struct {
     void*   stream;        /* cudaStream_t to run on; NULL = the handle creates its own */
     int32_t diag_rule;     /* gabp_diag_rule, default GABP_DIAG_DOMINANT */
     double  diag_delta;    /* delta of the dominant rule; 0 selects the default 0.1 */
-    int32_t bias_mode;     /* 0 = lambda = 1/n (default), 1 = lambda = bias_lambda (may be 0) */
+    int32_t bias_mode;     /* 0 = lambda = 1/n (default), 1 = lambda = bias_lambda (may be 0;
+                              lambda^2 must not exceed FLT_MAX, else GABP_EINVAL) */
     double  bias_lambda;
     int32_t q_mode;        /* gabp_q_mode, default GABP_Q_F32 */
     int32_t refine;        /* precision form only: up to this many defect-correction passes with the
@@ -126,9 +127,8 @@ typedef struct {
                               the diagonal keeps the row sums of the whole matrix, so the matrix stays
                               diagonally dominant and only the dropped entries change.  Device memory:
                               the messages, Q and per-node partial sums of the kept tiles only, plus
-                              bookkeeping of 48 B per tile and, during formation, a temporary array of
-                              4 n^2 / 128 B for the first pass's row sums (freed before the kept tiles'
-                              storage is allocated).  Effective when rows are ordered so that near points
+                              bookkeeping of 48 B per tile and 8 B per node for the whole matrix's row
+                              sums.  Effective when rows are ordered so that near points
                               share tiles.  0 = dense (default).  Single-instance API only (not the
                               batched or served forms) */
     int32_t reserved[1];
@@ -172,6 +172,8 @@ GABP_API void gabp_svm_opts_default(gabp_svm_opts* opts);
  * Forms Q on the device (Gram kernel fused with exp, bias and labels), weights
  * its diagonal (Section 3.1) and sets the GaBP state to Algorithm 2's Step 1
  * (all messages 0).  Requires n >= 2, m >= 1.
+ * gamma and lambda^2 enter the kernels in FP32: gamma > FLT_MAX or a non-finite
+ * C is GABP_EINVAL (so are the same values in the batched and served forms).
  * Device memory: about 8 n^2 bytes of message state plus the stored Q
  * (2 n^2 bytes for FP32, n^2 for BF16, 0 for recompute); GABP_ENOMEM if that
  * does not fit in free device memory, before anything is allocated.

@@ -6,6 +6,7 @@
 #include "gabp_svm.h"
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdarg>
 #include <climits>
@@ -427,8 +428,8 @@ gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
     if (h->opts.sparse_tau > 0) {
         // Tile-sparse option.  Pass 1 over every tile: tile maxima and |Q|
         // row sums (the whole matrix's, for the diagonal rule), Q not
-        // stored; the row sums go to dense slots (one array, in the second
-        // allocation) and are reduced to rsum per node.  Then the kept-tile
+        // stored; the row sums are added into per-node fixed-point sums
+        // (in rsum's memory, converted to rsum in place).  Then the kept-tile
         // list, the compacted slot space and the kept tiles' storage (which
         // replaces the dense slots), and pass 2 over the kept tiles only:
         // their FP32 values (the store, or the FP32 copy beside the BF16
@@ -437,18 +438,19 @@ gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
         // and the BF16 tiles.  Recompute needs no second pass.
         if (h->opts.q_mode != GABP_Q_F32)
             CK(launch_pack_bf16(p.X, (int)n, (int)m, p.nkc, h->Nt, (void*)p.Xp, (float*)p.sqb, s));
-        if (gabp_status st = ensure_spool(h, (size_t)h->Nt * h->Nt * T * sizeof(float), "the first pass's row sums"))
-            return st;
-        p.part = static_cast<float*>(h->spool);
-        p.nslot = (long long)h->Nt * h->Nt;
+        p.part = nullptr;
+        p.nslot = 0;
         p.srow = nullptr;
         p.tslot = nullptr;
         p.rsum = nullptr;
+        p.rfix = reinterpret_cast<unsigned long long*>(h->rsum);
+        CK(cudaMemsetAsync(h->rsum, 0, (size_t)n * sizeof(double), s));
         CK(cudaMemcpyAsync(h->d_tab, &p, sizeof(Inst), cudaMemcpyHostToDevice, s));
         launch_form_q(h->d_tab, h->work_all, h->ntiles, s);
         launch_row_abs_sums(p, h->rsum, s);
         CK(cudaGetLastError());
         h->prof.kernel_launches += h->opts.q_mode != GABP_Q_F32 ? 4 : 2;
+        p.rfix = nullptr;
         if (gabp_status st = build_sweep_list(h)) return st;
         if (gabp_status st = ensure_pair_storage(h, h->nslot)) return st;
         p.tilemax = nullptr;
@@ -636,7 +638,7 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
                                     (long long)n, (long long)m);
     if (n > (int64_t)1 << 30 || m > (int64_t)1 << 20 || n * m > ((int64_t)1 << 40))
         return fail(GABP_EINVAL, "n or m too large");
-    if (!(gamma > 0) || !std::isfinite(gamma)) return fail(GABP_EINVAL, "gamma must be finite and > 0");
+    if (!(gamma > 0) || !(gamma <= FLT_MAX)) return fail(GABP_EINVAL, "gamma must be > 0 and within FP32 range");
     if (!(C > 0) || !std::isfinite(C)) return fail(GABP_EINVAL, "C must be finite and > 0");
     gabp_svm_opts o;
     gabp_svm_opts_default(&o);
@@ -650,8 +652,8 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
     if (o.diag_rule != GABP_DIAG_DOMINANT && o.diag_rule != GABP_DIAG_SOFT2)
         return fail(GABP_EINVAL, "unknown diag_rule");
     if (!(o.diag_delta > 0) || !std::isfinite(o.diag_delta)) return fail(GABP_EINVAL, "diag_delta must be > 0");
-    if (o.bias_mode == 1 && (!(o.bias_lambda >= 0) || !std::isfinite(o.bias_lambda)))
-        return fail(GABP_EINVAL, "bias_lambda must be finite and >= 0");
+    if (o.bias_mode == 1 && (!(o.bias_lambda >= 0) || !(o.bias_lambda * o.bias_lambda <= FLT_MAX)))
+        return fail(GABP_EINVAL, "bias_lambda must be >= 0 with lambda^2 within FP32 range");
     if (o.q_mode != GABP_Q_F32 && o.q_mode != GABP_Q_BF16 && o.q_mode != GABP_Q_RECOMPUTE)
         return fail(GABP_EINVAL, "unknown q_mode %d", o.q_mode);
     if (o.refine < 0 || o.refine > 64) return fail(GABP_EINVAL, "refine must be in [0, 64]");
@@ -824,7 +826,7 @@ gabp_status gabp_svm_refit(gabp_svm_t h, const void* X, const float* y, double g
     g_err.clear();
     if (gabp_status s = check_handle(h)) return s;
     if (!X || !y) return fail(GABP_EINVAL, "X or y is NULL");
-    if (!(gamma > 0) || !std::isfinite(gamma)) return fail(GABP_EINVAL, "gamma must be finite and > 0");
+    if (!(gamma > 0) || !(gamma <= FLT_MAX)) return fail(GABP_EINVAL, "gamma must be > 0 and within FP32 range");
     if (!(C > 0) || !std::isfinite(C)) return fail(GABP_EINVAL, "C must be finite and > 0");
     h->gamma = gamma;
     h->C = C;

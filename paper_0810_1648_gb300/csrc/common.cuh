@@ -96,6 +96,8 @@ struct Inst {
     const int2* tslot;// tile-sparse option: slots {row role, column role} of swept tile w.w; nullptr = dense
     const double* rsum;  // tile-sparse option: the whole matrix's sum_{j != i} |Q_ij| per node (formation's
                          // first pass), for the diagonal rule; nullptr = summed from the slots
+    unsigned long long* rfix;  // formation: where set, the |Q| row-sum partials are added to these
+                               // per-node fixed-point sums (rsum_fix) instead of written to slots
     Ctrl* ctrl;
     double* rhist;    // ||r(t)||_inf per round (rhist_cap entries)
     int rhist_cap;
@@ -138,6 +140,26 @@ __host__ __device__ inline int2 tile_slots(const Inst& p, int4 w)
 }
 // Floats of each partial array.
 __host__ __device__ inline size_t part_len(const Inst& p) { return (size_t)p.nslot * T; }
+
+// The |Q| row sums R_i = sum_{j != i} |Q_ij| of the diagonal rule are added up
+// in fixed point: each FP32 slot partial v becomes the integer nearest to
+// v 2^s, the integers are summed, and R_i = (that sum) 2^-s.  Integer addition
+// does not depend on the order of its terms, so the dense slot sums and the
+// tile-sparse first pass's atomic sums (no slots) give the same R bit for bit.
+// s is the largest shift that keeps every possible sum below 2^62: each entry
+// is at most 1 + lambda^2 (an RBF value plus the bias term; 1% room for the
+// rounding of the entries), a row has fewer than n of them.  The resolution
+// 2^-s is below 1e-15 R_max.
+__host__ __device__ inline int rsum_shift(int n, float lam2)
+{
+    int e = 0;
+    frexp(1.01 * (double)(n > 2 ? n : 2) * (1.0 + (double)lam2), &e);   // bound < 2^e
+    return 62 - e;
+}
+// 2^s for |s| < 1000, built from the exponent field.
+__device__ __forceinline__ double pow2i(int s) { return __longlong_as_double((long long)(1023 + s) << 52); }
+__device__ __forceinline__ long long rsum_fix(float v, double scale) { return __double2ll_rn((double)v * scale); }
+__device__ __forceinline__ double rsum_unfix(long long a, int shift) { return __ll2double_rn(a) * pow2i(-shift); }
 
 // Work of one round over a set of instances (device resident, so that a
 // captured round stays valid while the set changes).  Tile list entries are
@@ -245,8 +267,8 @@ void launch_reset(const Inst& p, cudaStream_t s);
 
 // Diagonal rule, Step-1 aggregates and control reset.
 void launch_init(const Inst& p, int diag_rule, float delta, cudaStream_t s);
-// rsum[x] = the sum of node x's slots of partial array 0 (the formation's
-// |Q| row sums), in FP64.
+// rsum[x] = R_x from the fixed-point sums that the formation's first pass
+// added into rfix (the same memory, converted in place).
 void launch_row_abs_sums(const Inst& p, double* rsum, cudaStream_t s);
 // Solve control: arm the control blocks of tab[0..ninst) for `iters` more rounds with tolerance `tol`.
 void launch_begin(Inst* tab, int ninst, int iters, double tol, cudaStream_t s);

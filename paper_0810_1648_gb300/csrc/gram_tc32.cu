@@ -410,24 +410,34 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                 epi_bar();
                 // per-node slot partials (fixed order): row sums of the tile's rows,
                 // column sums of its columns; both roles on a diagonal tile
-                // (slot sl.x of the row block, sl.y of the column block)
-                const int2 sl = tile_slots(p, w);
-                float* partR = p.part + (size_t)sl.x * T;
-                float* partC = p.part + (size_t)sl.y * T;
+                // (slot sl.x of the row block, sl.y of the column block).  Where
+                // rfix is set they are added to the nodes' fixed-point sums instead.
+                int x = -1, off = 0, role = 0;
+                float v = 0.f;
                 if (I == J) {
                     if (etid < T) {
-                        const int x = I * T + etid;
-                        if (x < n)
-                            partR[etid] = (sm.rowsum[0][etid] + sm.rowsum[1][etid]) +
-                                          (((sm.colsum[0][etid] + sm.colsum[1][etid]) + sm.colsum[2][etid]) +
-                                           sm.colsum[3][etid]);
+                        x = I * T + etid;
+                        off = etid;
+                        v = (sm.rowsum[0][etid] + sm.rowsum[1][etid]) +
+                            (((sm.colsum[0][etid] + sm.colsum[1][etid]) + sm.colsum[2][etid]) + sm.colsum[3][etid]);
                     }
                 } else if (etid < T) {
-                    const int x = I * T + etid;
-                    if (x < n) partR[etid] = sm.rowsum[0][etid] + sm.rowsum[1][etid];
+                    x = I * T + etid;
+                    off = etid;
+                    v = sm.rowsum[0][etid] + sm.rowsum[1][etid];
                 } else if (etid < 2 * T) {
-                    const int c = etid - T, x = J * T + c;
-                    if (x < n) partC[c] = ((sm.colsum[0][c] + sm.colsum[1][c]) + sm.colsum[2][c]) + sm.colsum[3][c];
+                    off = etid - T;
+                    x = J * T + off;
+                    role = 1;
+                    v = ((sm.colsum[0][off] + sm.colsum[1][off]) + sm.colsum[2][off]) + sm.colsum[3][off];
+                }
+                if (x >= 0 && x < n) {
+                    if (p.rfix) {
+                        atomicAdd(p.rfix + x, (unsigned long long)rsum_fix(v, pow2i(rsum_shift(n, lam2))));
+                    } else {
+                        const int2 sl = tile_slots(p, w);
+                        p.part[(size_t)(role ? sl.y : sl.x) * T + off] = v;
+                    }
                 }
                 if (etid == 0 && p.tilemax) {
                     float m2 = 0.f;

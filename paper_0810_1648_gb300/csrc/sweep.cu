@@ -1372,15 +1372,17 @@ __device__ __forceinline__ void zero_slots(const Inst& p, int x, bool with_p)
 }
 
 // The whole matrix's sum_{j != i} |Q_ij| of node x: the formation's slot sums
-// (array 0), or the first pass's sums of the tile-sparse option.
+// (array 0) added in fixed point (rsum_fix), or the first pass's sums of the
+// tile-sparse option (the same value).
 __device__ __forceinline__ double offdiag_abs_sum(const Inst& p, int x)
 {
     if (p.rsum) return p.rsum[x];
-    const int X = x / T, ns = slot_count(p, X);
+    const int X = x / T, ns = slot_count(p, X), sh = rsum_shift(p.n, p.lam2);
+    const double scale = pow2i(sh);
     const float* s0 = p.part + (size_t)slot_begin(p, X) * T + (x - X * T);
-    double R = 0.0;
-    for (int k = 0; k < ns; ++k) R += (double)s0[(size_t)k * T];
-    return R;
+    long long a = 0;
+    for (int k = 0; k < ns; ++k) a += rsum_fix(s0[(size_t)k * T], scale);
+    return rsum_unfix(a, sh);
 }
 
 // Between the stages of a staged round: Ptilde and htilde of every node from
@@ -1574,7 +1576,10 @@ __global__ void k_init(Inst p, int diag_rule, float delta)
 __global__ void k_row_abs_sums(Inst p, double* __restrict__ rsum)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x < p.n) rsum[x] = offdiag_abs_sum(p, x);
+    if (x < p.n) {
+        const long long a = reinterpret_cast<const long long*>(rsum)[x];
+        rsum[x] = rsum_unfix(a, rsum_shift(p.n, p.lam2));
+    }
 }
 
 // k_init over listed node blocks (block 0 of an instance resets its control block).

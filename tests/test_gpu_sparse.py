@@ -148,7 +148,7 @@ def test_tile_sparse_beyond_dense_memory():
         # slot partials (16 B per node and slot: two slots of 128 nodes per kept
         # off-diagonal tile) exist for the kept tiles only; the rest is O(n)
         # and 48 B per tile of bookkeeping (dense slot partials, 16 n^2 / 128 B,
-        # would add 5 GB here)
+        # would add 5 GB here; the first pass's row sums take 8 B a node)
         ntiles = nt * (nt + 1) // 2
         bound = 20 * 128 * 128 * kept + 16 * 128 * 2 * kept + 64 * ntiles + (1 << 29)
         assert st["device_bytes"] <= bound, (st["device_bytes"], bound)
