@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cfloat>
 #include <cmath>
 #include <cstring>
 #include <deque>
@@ -603,7 +604,8 @@ class Engine {
         Member& M = mem[(size_t)slot];
         const int64_t n = pr.n, m = pr.m;
         if (n < 2 || m < 1 || !pr.X || !pr.y) return fail(GABP_EINVAL, "problem needs n >= 2, m >= 1, X and y");
-        if (!(pr.gamma > 0) || !(pr.C > 0)) return fail(GABP_EINVAL, "problem needs gamma > 0 and C > 0");
+        if (!(pr.gamma > 0) || !(pr.gamma <= FLT_MAX) || !(pr.C > 0) || !std::isfinite(pr.C))
+            return fail(GABP_EINVAL, "problem needs gamma in (0, FLT_MAX] and finite C > 0");
         const MemberPlan pl = member_plan(n, m, q_mode, msg_bf16, alias_x());
         M = Member{};
         M.used = true;
@@ -1224,7 +1226,7 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
     if (o.q_mode < 0 || o.q_mode > 2 || o.refine < 0 || o.refine > 64 || o.msg_bf16 < 0 || o.msg_bf16 > 1 ||
         (o.msg_bf16 && o.q_mode == 0) || o.task < 0 || o.task > 1 || o.stages < 0 || o.stages > kMaxStages ||
         o.sparse_tau != 0.f ||
-        (o.bias_mode == 1 && (!(o.bias_lambda >= 0) || !std::isfinite(o.bias_lambda)))) {
+        (o.bias_mode == 1 && (!(o.bias_lambda >= 0) || !(o.bias_lambda * o.bias_lambda <= FLT_MAX)))) {
         set_last_error("gabp_batch_solve: bad q_mode, refine, msg_bf16, task or bias");
         return GABP_EINVAL;
     }
@@ -1232,7 +1234,8 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
     size_t bytes = 0;
     for (int64_t k = 0; k < count; ++k) {
         const gabp_problem& p = probs[k];
-        if (p.n < 2 || p.m < 1 || p.n > (1 << 30) || !p.X || !p.y || !(p.gamma > 0) || !(p.C > 0)) {
+        if (p.n < 2 || p.m < 1 || p.n > (1 << 30) || !p.X || !p.y || !(p.gamma > 0) ||
+            !(p.gamma <= FLT_MAX) || !(p.C > 0) || !std::isfinite(p.C)) {
             set_last_error(("gabp_batch_solve: problem " + std::to_string(k) + " is invalid").c_str());
             return GABP_EINVAL;
         }
@@ -1392,7 +1395,8 @@ gabp_status gabp_server_create(const gabp_server_cfg* cfg, gabp_server_t* out)
     if (c.max_members > 4096 || c.iters < 0 || std::isnan(c.tol) || c.opts.q_mode < 0 || c.opts.q_mode > 2 ||
         (c.opts.msg_bf16 && c.opts.q_mode == 0) || c.opts.task < 0 || c.opts.task > 1 || c.opts.stages < 0 ||
         c.opts.stages > kMaxStages || c.opts.sparse_tau != 0.f ||
-        (c.opts.bias_mode == 1 && (!(c.opts.bias_lambda >= 0) || !std::isfinite(c.opts.bias_lambda)))) {
+        (c.opts.bias_mode == 1 &&
+         (!(c.opts.bias_lambda >= 0) || !(c.opts.bias_lambda * c.opts.bias_lambda <= FLT_MAX)))) {
         set_last_error("gabp_server_create: bad configuration");
         return GABP_EINVAL;
     }
@@ -1425,7 +1429,8 @@ gabp_status gabp_server_submit_ex(gabp_server_t s, const gabp_problem* p, float*
 {
     gabp::set_last_error("");
     if (!s || !p || !ticket) { gabp::set_last_error("gabp_server_submit: null argument"); return GABP_EINVAL; }
-    if (p->n < 2 || p->m < 1 || !p->X || !p->y || !(p->gamma > 0) || !(p->C > 0)) {
+    if (p->n < 2 || p->m < 1 || !p->X || !p->y || !(p->gamma > 0) || !(p->gamma <= FLT_MAX) || !(p->C > 0) ||
+        !std::isfinite(p->C)) {
         gabp::set_last_error("gabp_server_submit: invalid problem");
         return GABP_EINVAL;
     }
