@@ -391,10 +391,10 @@ GABP_API gabp_status gabp_svm_get_profile(gabp_svm_t h, gabp_svm_profile* out, i
  * cudaMalloc, cudaFree or allocating library routine.  Sizes must satisfy
  * n + t + ceil(n/128) * t <= 1048576 floats, else GABP_EINVAL (split the test
  * rows into smaller calls).  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  Every call shares the array and keeps
- * the last call's contents: calls whose work overlaps on the GPU (other
- * streams, other host threads) race and must be serialised by the caller.
+ * device address (cudaGetSymbolAddress) with that device current.  Every
+ * call shares the array and keeps the last call's contents: calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.
  */
 GABP_API gabp_status gabp_decision_noalloc(const float* X, const float* y, const float* alpha,
                                            int64_t n, int64_t m, const float* Xtest, int64_t t,
