@@ -94,7 +94,8 @@ typedef enum {
 /* Options.  gabp_svm_opts_default() fills the defaults; a zero-initialised
  * struct also means the defaults except where noted. */
 typedef struct {
-    int32_t x_dtype;       /* layout of X and Xtest: 0 = float32 (default), 1 = float64 (converted to FP32 on the device) */
+    int32_t x_dtype;       /* layout of X and Xtest: 0 = float32 (default), 1 = float64 (converted to FP32
+                              on the device), 2 = bfloat16 (widened to FP32 on the device, exactly) */
     int32_t ptr_mode;      /* 0 = host pointers (copied in/out, default), 1 = device pointers */
     void*   stream;        /* cudaStream_t to run on; NULL = the handle creates its own */
     int32_t diag_rule;     /* gabp_diag_rule, default GABP_DIAG_DOMINANT */

@@ -365,7 +365,7 @@ gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
     cudaStream_t s = h->stream;
     const int64_t n = h->n, m = h->m;
     const bool dev = h->opts.ptr_mode == 1;
-    const bool f64 = h->opts.x_dtype == 1;
+    const int xd = h->opts.x_dtype;
     Inst& p = h->inst;
     p.gamma = (float)h->gamma;
     p.lam2 = (float)(h->lambda * h->lambda);
@@ -399,16 +399,16 @@ gabp_status stage_and_form(gabp_svm_t h, const void* X, const float* y)
     void* tmp = nullptr;
     const void* src = X;
     if (!dev) {
-        if (f64) {
-            CK(cudaMallocAsync(&tmp, (size_t)n * m * sizeof(double), s));
-            CK(cudaMemcpyAsync(tmp, X, (size_t)n * m * sizeof(double), cudaMemcpyHostToDevice, s));
+        if (xd != 0) {   // FP64 / BF16 rows: widened to FP32 by the staging kernel
+            CK(cudaMallocAsync(&tmp, (size_t)n * m * x_elem_bytes(xd), s));
+            CK(cudaMemcpyAsync(tmp, X, (size_t)n * m * x_elem_bytes(xd), cudaMemcpyHostToDevice, s));
             src = tmp;
         } else {
             CK(cudaMemcpyAsync((void*)p.X, X, (size_t)n * m * sizeof(float), cudaMemcpyHostToDevice, s));
             src = p.X;
         }
     }
-    launch_stage(src, f64 ? 1 : 0, (int)n, (int)m, const_cast<float*>(p.y), (float*)p.X, (float*)p.sq, (float*)p.b,
+    launch_stage(src, xd, (int)n, (int)m, const_cast<float*>(p.y), (float*)p.X, (float*)p.sq, (float*)p.b,
                  const_cast<float*>(p.b0), p.task, p.ctrl, s);
     h->prof.kernel_launches += 1;
     CK(cudaGetLastError());
@@ -647,7 +647,7 @@ gabp_status gabp_svm_create_ex(const void* X, const float* y, int64_t n, int64_t
         if (o.diag_delta == 0) o.diag_delta = 0.1;
         if (o.chunk <= 0) o.chunk = 16;
     }
-    if (o.x_dtype != 0 && o.x_dtype != 1) return fail(GABP_EINVAL, "x_dtype must be 0 (f32) or 1 (f64)");
+    if (o.x_dtype < 0 || o.x_dtype > 2) return fail(GABP_EINVAL, "x_dtype must be 0 (f32), 1 (f64) or 2 (bf16)");
     if (o.ptr_mode != 0 && o.ptr_mode != 1) return fail(GABP_EINVAL, "ptr_mode must be 0 or 1");
     if (o.diag_rule != GABP_DIAG_DOMINANT && o.diag_rule != GABP_DIAG_SOFT2)
         return fail(GABP_EINVAL, "unknown diag_rule");
@@ -1003,12 +1003,13 @@ gabp_status gabp_svm_decision(gabp_svm_t h, const void* Xtest, int64_t t, float*
     if (t > ((int64_t)1 << 30)) return fail(GABP_EINVAL, "t too large");
     NvtxRange nv("gabp.decision");
     cudaStream_t s = h->stream;
-    const bool dev = h->opts.ptr_mode == 1, f64 = h->opts.x_dtype == 1;
+    const bool dev = h->opts.ptr_mode == 1;
+    const int xd = h->opts.x_dtype;
     const int64_t m = h->m;
     const int Ntt = (int)((t + T - 1) / T);
     const long long ntl = (long long)Ntt * h->Nt;
     const size_t bx = align_up((size_t)t * m * sizeof(float), 256), bsq = align_up((size_t)t * 4, 256);
-    const size_t bin = (!dev && f64) ? align_up((size_t)t * m * sizeof(double), 256) : 0;
+    const size_t bin = (!dev && xd != 0) ? align_up((size_t)t * m * x_elem_bytes(xd), 256) : 0;
     const size_t bpart = align_up((size_t)h->Nt * t * sizeof(float), 256);
     const size_t bw = align_up((size_t)ntl * sizeof(int2), 256), bout = align_up((size_t)t * 4, 256);
     char* tmp = nullptr;
@@ -1028,8 +1029,8 @@ gabp_status gabp_svm_decision(gabp_svm_t h, const void* Xtest, int64_t t, float*
         CK(cudaMemcpyAsync(w, wl.data(), wl.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
         const void* src = Xtest;
         if (!dev) {
-            if (f64) {
-                CK(cudaMemcpyAsync(in, Xtest, (size_t)t * m * sizeof(double), cudaMemcpyHostToDevice, s));
+            if (xd != 0) {
+                CK(cudaMemcpyAsync(in, Xtest, (size_t)t * m * x_elem_bytes(xd), cudaMemcpyHostToDevice, s));
                 src = in;
             } else {
                 CK(cudaMemcpyAsync(Xt, Xtest, (size_t)t * m * sizeof(float), cudaMemcpyHostToDevice, s));
@@ -1039,7 +1040,7 @@ gabp_status gabp_svm_decision(gabp_svm_t h, const void* Xtest, int64_t t, float*
         CK(cudaMemcpyAsync(h->hctrl, h->inst.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         const int saved_status = h->hctrl->status;
-        launch_stage(src, f64 ? 1 : 0, (int)t, (int)m, nullptr, Xt, sqt, nullptr, nullptr, 0, h->inst.ctrl, s);
+        launch_stage(src, xd, (int)t, (int)m, nullptr, Xt, sqt, nullptr, nullptr, 0, h->inst.ctrl, s);
         h->prof.kernel_launches += 1;
         CK(cudaMemcpyAsync(h->hctrl, h->inst.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));

@@ -305,7 +305,7 @@ class Engine {
         if (e_ != cudaSuccess) return fail(GABP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-    int q_mode = 0, diag_rule = 0, x_f64 = 0, ptr_mode = 0, msg_bf16 = 0, task = 0, bias_mode = 0;
+    int q_mode = 0, diag_rule = 0, x_dtype = 0, ptr_mode = 0, msg_bf16 = 0, task = 0, bias_mode = 0;
     bool host_direct = false;   // the GPU reads pageable host memory coherently
     int nstages = 1;   // message schedule: 1 synchronous, > 1 staged
     double delta = 0.1, sv_threshold = 0.0, bias_lambda = 0.0;
@@ -388,7 +388,7 @@ class Engine {
         bias_lambda = o.bias_lambda;
         diag_rule = o.diag_rule;
         delta = o.diag_delta > 0 ? o.diag_delta : 0.1;
-        x_f64 = o.x_dtype;
+        x_dtype = o.x_dtype;
         ptr_mode = o.ptr_mode;
         sv_threshold = o.sv_threshold;
         handover = refine_handover(o.refine_handover, o.msg_bf16);
@@ -489,7 +489,7 @@ class Engine {
         m.evg = -1;
     }
 
-    bool alias_x() const { return ptr_mode == 1 && x_f64 == 0; }
+    bool alias_x() const { return ptr_mode == 1 && x_dtype == 0; }
 
     // Host-to-device copy of an input array.  Where the GPU reads pageable
     // host memory coherently (cudaDevAttrPageableMemoryAccess, e.g. a Grace
@@ -546,7 +546,7 @@ class Engine {
                nblk <= cap_nblk && q_mode == o.q_mode && msg_bf16 == o.msg_bf16 && task == o.task &&
                nstages == (o.stages > 1 ? o.stages : 1) && bias_mode == o.bias_mode &&
                bias_lambda == o.bias_lambda && diag_rule == o.diag_rule &&
-               delta == (o.diag_delta > 0 ? o.diag_delta : 0.1) && x_f64 == o.x_dtype && ptr_mode == o.ptr_mode &&
+               delta == (o.diag_delta > 0 ? o.diag_delta : 0.1) && x_dtype == o.x_dtype && ptr_mode == o.ptr_mode &&
                sv_threshold == o.sv_threshold && handover == refine_handover(o.refine_handover, o.msg_bf16) &&
                inner == refine_inner(o.refine_inner, o.msg_bf16);
     }
@@ -689,22 +689,22 @@ class Engine {
             if (ptr_mode) EK(cudaMemcpyAsync((void*)p.y, pr.y, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
             else if (gabp_status st = fetch((void*)p.y, pr.y, (size_t)n * 4, s)) return st;
         }
-        if (!x_f64) {
+        if (x_dtype == 0) {
             // FP32 rows: read in place from device memory, else copied into X;
             // the batched staging of form_pending() checks them
             if (!alias_x())
                 if (gabp_status st = fetch((void*)p.X, pr.X, (size_t)n * m * 4, s)) return st;
         } else {
-            // FP64 input: convert and check now
+            // FP64 / BF16 input: widen to FP32 and check now
             EK(cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), s));
             const void* src = pr.X;
             void* tmp = nullptr;
             if (!ptr_mode) {
-                EK(cudaMallocAsync(&tmp, (size_t)n * m * 8, s));
-                if (gabp_status st = fetch(tmp, pr.X, (size_t)n * m * 8, s)) return st;
+                EK(cudaMallocAsync(&tmp, (size_t)n * m * x_elem_bytes(x_dtype), s));
+                if (gabp_status st = fetch(tmp, pr.X, (size_t)n * m * x_elem_bytes(x_dtype), s)) return st;
                 src = tmp;
             }
-            launch_stage(src, x_f64, (int)n, (int)m, const_cast<float*>(p.y), (float*)p.X, (float*)p.sq,
+            launch_stage(src, x_dtype, (int)n, (int)m, const_cast<float*>(p.y), (float*)p.X, (float*)p.sq,
                          (float*)p.b, const_cast<float*>(p.b0), p.task, p.ctrl, s);
             ++launches;
             if (tmp) EK(cudaFreeAsync(tmp, s));
@@ -1225,9 +1225,9 @@ gabp_status gabp_batch_solve(const gabp_problem* probs, int64_t count, const gab
     if (o.diag_delta == 0) o.diag_delta = 0.1;
     if (o.q_mode < 0 || o.q_mode > 2 || o.refine < 0 || o.refine > 64 || o.msg_bf16 < 0 || o.msg_bf16 > 1 ||
         (o.msg_bf16 && o.q_mode == 0) || o.task < 0 || o.task > 1 || o.stages < 0 || o.stages > kMaxStages ||
-        o.sparse_tau != 0.f ||
+        o.sparse_tau != 0.f || o.x_dtype < 0 || o.x_dtype > 2 || o.ptr_mode < 0 || o.ptr_mode > 1 ||
         (o.bias_mode == 1 && (!(o.bias_lambda >= 0) || !(o.bias_lambda * o.bias_lambda <= FLT_MAX)))) {
-        set_last_error("gabp_batch_solve: bad q_mode, refine, msg_bf16, task or bias");
+        set_last_error("gabp_batch_solve: bad q_mode, refine, msg_bf16, task, x_dtype, ptr_mode or bias");
         return GABP_EINVAL;
     }
     long long tiles = 0, nblk = 0;
@@ -1394,8 +1394,8 @@ gabp_status gabp_server_create(const gabp_server_cfg* cfg, gabp_server_t* out)
     if (c.max_members <= 0) c.max_members = 64;
     if (c.max_members > 4096 || c.iters < 0 || std::isnan(c.tol) || c.opts.q_mode < 0 || c.opts.q_mode > 2 ||
         (c.opts.msg_bf16 && c.opts.q_mode == 0) || c.opts.task < 0 || c.opts.task > 1 || c.opts.stages < 0 ||
-        c.opts.stages > kMaxStages || c.opts.sparse_tau != 0.f ||
-        (c.opts.bias_mode == 1 &&
+        c.opts.stages > kMaxStages || c.opts.sparse_tau != 0.f || c.opts.x_dtype < 0 || c.opts.x_dtype > 2 ||
+        c.opts.ptr_mode < 0 || c.opts.ptr_mode > 1 || (c.opts.bias_mode == 1 &&
          (!(c.opts.bias_lambda >= 0) || !(c.opts.bias_lambda * c.opts.bias_lambda <= FLT_MAX)))) {
         set_last_error("gabp_server_create: bad configuration");
         return GABP_EINVAL;

@@ -228,8 +228,10 @@ struct GramSide {
 // y must be +-1, b = b0 = 1.  KRR (task 1): y holds finite targets, which move
 // to b and b0, and y becomes 1 (no labels in Q).  y, b, b0 may be null (test
 // points).  Returns nothing; errors go to ctrl->status.
-void launch_stage(const void* X, int x_f64, int n, int m, float* y, float* Xf, float* sq,
+void launch_stage(const void* X, int x_dtype, int n, int m, float* y, float* Xf, float* sq,
                   float* b, float* b0, int task, Ctrl* ctrl, cudaStream_t s);
+// Bytes of one feature of the input layout x_dtype (0 FP32, 1 FP64, 2 BF16).
+inline size_t x_elem_bytes(int x_dtype) { return x_dtype == 1 ? 8 : x_dtype == 2 ? 2 : 4; }
 // Refinement schedule of the precision forms (0 selects the default): the
 // first solve hands over to the defect correction at ||r||_inf < handover, each
 // correction pass stops at inner * ||r||_inf of its right-hand side.

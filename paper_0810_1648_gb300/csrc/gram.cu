@@ -172,9 +172,10 @@ __device__ __forceinline__ void reduce_and_write(EpiSmem& es, float (&rs)[NQ][8]
 }
 
 // ---------------------------------------------------------------- staging
-// One row: FP32 copy (from FP32 or FP64 input), squared norm, finiteness and
-// label checks, b_i = 1 (the SVM right-hand side: the linear term 1'h of the dual).
-__device__ __forceinline__ void stage_row(const void* __restrict__ X, int x_f64, int i, int m,
+// One row: FP32 copy (from FP32, FP64 or BF16 input; BF16 widens exactly),
+// squared norm, finiteness and label checks, b_i = 1 (the SVM right-hand
+// side: the linear term 1'h of the dual).
+__device__ __forceinline__ void stage_row(const void* __restrict__ X, int x_dtype, int i, int m,
                                           float* __restrict__ y, float* __restrict__ Xf,
                                           float* __restrict__ sq, float* __restrict__ b,
                                           float* __restrict__ b0, int task, Ctrl* ctrl)
@@ -183,7 +184,9 @@ __device__ __forceinline__ void stage_row(const void* __restrict__ X, int x_f64,
     bool ok = true;
     for (int k = 0; k < m; ++k) {
         const size_t e = (size_t)i * m + k;
-        const float v = x_f64 ? (float)static_cast<const double*>(X)[e] : static_cast<const float*>(X)[e];
+        const float v = x_dtype == 1   ? (float)static_cast<const double*>(X)[e]
+                        : x_dtype == 2 ? __bfloat162float(static_cast<const __nv_bfloat16*>(X)[e])
+                                       : static_cast<const float*>(X)[e];
         ok &= isfinite(v);
         if (Xf != X) Xf[e] = v;
         s = fmaf(v, v, s);
@@ -205,12 +208,12 @@ __device__ __forceinline__ void stage_row(const void* __restrict__ X, int x_f64,
     if (!ok && atomicCAS(&ctrl->status, 0, (int)ST_EINVAL) == 0) ctrl->bad_index = i;
 }
 
-__global__ void k_stage(const void* __restrict__ X, int x_f64, int n, int m, float* __restrict__ y,
+__global__ void k_stage(const void* __restrict__ X, int x_dtype, int n, int m, float* __restrict__ y,
                         float* __restrict__ Xf, float* __restrict__ sq, float* __restrict__ b,
                         float* __restrict__ b0, int task, Ctrl* ctrl)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) stage_row(X, x_f64, i, m, y, Xf, sq, b, b0, task, ctrl);
+    if (i < n) stage_row(X, x_dtype, i, m, y, Xf, sq, b, b0, task, ctrl);
 }
 
 // Listed node blocks of instances whose FP32 rows already sit in their X.
@@ -491,10 +494,10 @@ void launch_stage_list(const Inst* tab, const int2* nbl, int nblocks, cudaStream
     if (nblocks > 0) k_stage_list<<<nblocks, 32, 0, s>>>(tab, nbl);
 }
 
-void launch_stage(const void* X, int x_f64, int n, int m, float* y, float* Xf, float* sq,
+void launch_stage(const void* X, int x_dtype, int n, int m, float* y, float* Xf, float* sq,
                   float* b, float* b0, int task, Ctrl* ctrl, cudaStream_t s)
 {
-    k_stage<<<(n + 255) / 256, 256, 0, s>>>(X, x_f64, n, m, y, Xf, sq, b, b0, task, ctrl);
+    k_stage<<<(n + 255) / 256, 256, 0, s>>>(X, x_dtype, n, m, y, Xf, sq, b, b0, task, ctrl);
 }
 
 void launch_final(const Inst* tab, const StopOp* ops, const int4* tiles, long long ntiles, const int2* nbl,

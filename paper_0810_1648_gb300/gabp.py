@@ -196,12 +196,18 @@ def opts_default(**kw) -> Opts:
     return o
 
 
+def _torch_x_dtype(X) -> int:
+    """opts.x_dtype of a torch feature tensor: 0 float32, 1 float64, 2 bfloat16."""
+    import torch
+    codes = {torch.float32: 0, torch.float64: 1, torch.bfloat16: 2}
+    if X.dtype not in codes:
+        raise TypeError("X must be float32, float64 or bfloat16")
+    return codes[X.dtype]
+
+
 def _prep_x(X, device_mode):
     if device_mode:
-        import torch
-        if X.dtype not in (torch.float32, torch.float64):
-            raise TypeError("X must be float32 or float64")
-        return X.contiguous(), (1 if X.dtype == torch.float64 else 0)
+        return X.contiguous(), _torch_x_dtype(X)
     X = np.asarray(X)
     if X.dtype not in (np.float32, np.float64):
         X = X.astype(np.float32)
@@ -215,12 +221,10 @@ def svm_create(X, y, gamma: float, C: float, opts: Opts | None = None):
     device_mode = _is_cuda(X)
     if _is_torch(X) and not device_mode:
         import torch
-        if X.dtype not in (torch.float32, torch.float64):
-            raise TypeError("X must be float32 or float64")
         o = opts if opts is not None else opts_default()
-        o.x_dtype = 1 if X.dtype == torch.float64 else 0
+        o.x_dtype = _torch_x_dtype(X)
         o.ptr_mode = 0
-        y = y.to(dtype=torch.float32).contiguous()
+        y = torch.as_tensor(y, dtype=torch.float32).contiguous()
         h = ctypes.c_void_p()
         _check(load().gabp_svm_create_ex(_ptr(X.contiguous()), _ptr(y), X.shape[0], X.shape[1],
                                          float(gamma), float(C), ctypes.byref(o), ctypes.byref(h)))
@@ -352,14 +356,15 @@ def selftest_bounded_wait(limit_ns: int) -> int:
 
 def batch_solve(problems, iters: int, tol: float, means: bool = False, **opts):
     """gabp_batch_solve over a list of workloads.Problem-like objects: numpy X
-    (float32/float64) and y, or float32 torch CUDA tensors for all of them
-    (device pointer mode; alphas then come back as CUDA tensors).  Returns
+    (float32/float64) and y, or torch CUDA tensors for all of them (X float32
+    or bfloat16, one dtype for all; y float32; device pointer mode; alphas
+    then come back as CUDA tensors).  Returns
     (list of alpha arrays, list of result dicts, overall status); with
     means=True each result dict also carries the unclipped means under "mu"
     (same array kind as alpha)."""
     probs = (Problem * len(problems))()
     keep, alphas, mus = [], [], []
-    f64 = None
+    xcode = None   # opts.x_dtype shared by every problem
     dev = len(problems) > 0 and _is_cuda(problems[0].X)
     if dev:
         import torch
@@ -367,8 +372,10 @@ def batch_solve(problems, iters: int, tol: float, means: bool = False, **opts):
         if dev:
             X = p.X.contiguous()
             y = p.y.contiguous()
-            assert X.dtype == torch.float32 and y.dtype == torch.float32 and y.is_cuda
-            f64 = False
+            assert y.dtype == torch.float32 and y.is_cuda
+            xd = _torch_x_dtype(X)
+            assert xd != 1 and (xcode is None or xcode == xd), "one X dtype (float32 or bfloat16) for all problems"
+            xcode = xd
             keep += [X, y]
             probs[k] = Problem(X.data_ptr(), y.data_ptr(), X.shape[0], X.shape[1], float(p.gamma), float(p.C))
             alphas.append(torch.empty(X.shape[0], dtype=torch.float32, device=X.device))
@@ -376,9 +383,9 @@ def batch_solve(problems, iters: int, tol: float, means: bool = False, **opts):
                 mus.append(torch.empty(X.shape[0], dtype=torch.float32, device=X.device))
             continue
         X = np.ascontiguousarray(p.X)
-        if f64 is None:
-            f64 = X.dtype == np.float64
-        X = X.astype(np.float64 if f64 else np.float32, copy=False)
+        if xcode is None:
+            xcode = 1 if X.dtype == np.float64 else 0
+        X = X.astype(np.float64 if xcode == 1 else np.float32, copy=False)
         y = np.ascontiguousarray(p.y, dtype=np.float32)
         keep += [X, y]
         probs[k] = Problem(X.ctypes.data, y.ctypes.data, X.shape[0], X.shape[1], float(p.gamma), float(p.C))
@@ -393,7 +400,7 @@ def batch_solve(problems, iters: int, tol: float, means: bool = False, **opts):
         if means:
             res[k].mu = mus[k].data_ptr() if dev else mus[k].ctypes.data
     o = opts_default(**opts)
-    o.x_dtype = 1 if f64 else 0
+    o.x_dtype = xcode or 0
     if dev:
         o.ptr_mode = 1
     rc = load().gabp_batch_solve(probs, len(problems), ctypes.byref(o), int(iters), float(tol), res)
@@ -514,7 +521,20 @@ class GabpSVM:
         self.n, self.m = int(X.shape[0]), int(X.shape[1])
         self.device_mode = _is_cuda(X)
         self.C = float(C)
-        self.h = svm_create(X, y, gamma, C, opts_default(**opts))
+        o = opts_default(**opts)
+        self.h = svm_create(X, y, gamma, C, o)
+        self.x_dtype = int(o.x_dtype)   # the layout every later X / Xtest must have
+
+    def _x(self, X):
+        """X in the handle's layout (torch tensors are passed as they are and
+        must already have it; numpy arrays are converted)."""
+        if _is_torch(X):
+            if _torch_x_dtype(X) != self.x_dtype:
+                raise TypeError(f"X has {X.dtype}; this solver was created with x_dtype {self.x_dtype}")
+            return X.contiguous()
+        if self.x_dtype == 2:
+            raise TypeError("this solver reads bfloat16 rows: pass a torch bfloat16 tensor")
+        return np.ascontiguousarray(X, dtype=np.float64 if self.x_dtype == 1 else np.float32)
 
     def solve(self, iters: int = 200, tol: float = 1e-6):
         if self.device_mode:
@@ -534,11 +554,11 @@ class GabpSVM:
         return out
 
     def decision(self, Xt):
+        Xt = self._x(Xt)
         if self.device_mode:
             import torch
             out = torch.empty(Xt.shape[0], dtype=torch.float32, device="cuda")
         else:
-            Xt = np.ascontiguousarray(Xt)
             out = np.empty(Xt.shape[0], dtype=np.float32)
         svm_decision(self.h, Xt, out)
         return out
@@ -551,6 +571,9 @@ class GabpSVM:
 
     def refit(self, X, y, gamma, C):
         self.C = float(C)
+        X = self._x(X)
+        if not _is_torch(y):
+            y = np.ascontiguousarray(y, dtype=np.float32)
         svm_refit(self.h, X, y, gamma, C)
 
     def close(self):

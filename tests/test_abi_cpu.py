@@ -49,7 +49,8 @@ def test_argument_errors_before_device_work(lib):
     assert lib.gabp_svm_create(V(X.ctypes.data), V(y.ctypes.data), 4, 3, 1.0, float("inf"),
                                ctypes.byref(h)) == gabp.EINVAL
     for bad in (dict(task=2), dict(stages=17), dict(stages=-1), dict(msg_bf16=1), dict(refine=65),
-                dict(bias_mode=1, bias_lambda=2e19), dict(bias_mode=1, bias_lambda=-1.0)):
+                dict(bias_mode=1, bias_lambda=2e19), dict(bias_mode=1, bias_lambda=-1.0),
+                dict(x_dtype=3), dict(x_dtype=-1), dict(ptr_mode=2)):
         o = gabp.opts_default(**bad)
         assert lib.gabp_svm_create_ex(V(X.ctypes.data), V(y.ctypes.data), 4, 3, 1.0, 1.0,
                                       ctypes.byref(o), ctypes.byref(h)) == gabp.EINVAL, bad
