@@ -65,11 +65,15 @@ __device__ __forceinline__ void stage_tile_cols(ColTile& ct, const float* __rest
 }
 
 // 2^t by the hardware approximation (relative error of a few units in the
-// last place of FP32, far below the BF16 rounding of the Q entries).
+// last place of FP32, far below the BF16 rounding of the Q entries), with
+// results below the smallest normal FP32 value flushed to 0: such kernel
+// values (gamma d2 > 87) only matter without the bias term (lambda = 0),
+// where they stand for entries below 1.2e-38 of a matrix whose diagonal is
+// at least 1.
 __device__ __forceinline__ float ex2_approx(float t)
 {
     float r;
-    asm("ex2.approx.f32 %0, %1;" : "=f"(r) : "f"(t));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(t));
     return r;
 }
 

@@ -372,9 +372,11 @@ def batch_solve(problems, iters: int, tol: float, means: bool = False, **opts):
         if dev:
             X = p.X.contiguous()
             y = p.y.contiguous()
-            assert y.dtype == torch.float32 and y.is_cuda
+            if y.dtype != torch.float32 or not y.is_cuda:
+                raise TypeError("device-mode labels must be float32 CUDA tensors")
             xd = _torch_x_dtype(X)
-            assert xd != 1 and (xcode is None or xcode == xd), "one X dtype (float32 or bfloat16) for all problems"
+            if xd == 1 or (xcode is not None and xcode != xd):
+                raise TypeError("device-mode rows: one dtype (float32 or bfloat16) for all problems")
             xcode = xd
             keep += [X, y]
             probs[k] = Problem(X.data_ptr(), y.data_ptr(), X.shape[0], X.shape[1], float(p.gamma), float(p.C))

@@ -72,6 +72,20 @@ def test_q_formation_matches_oracle(n, m):
     assert np.array_equal(Qg, Qg.T)
 
 
+@pytest.mark.parametrize("n,lam", [(2, 0.0), (300, 30.0), (1000, 1e3), (2500, None)])
+def test_diagonal_rule_across_bias_scales(n, lam):
+    """The dominant rule's row sums R_i (Section 3.1's diagonal weighting) are
+    added in fixed point with a shift chosen from n and lambda^2; across bias
+    scales from 0 to lambda^2 = 1e6 the diagonal must match the oracle's FP64
+    sums of the whole row, relative to the diagonal, at the entries' FP32 bar."""
+    p = workloads.mixture(n, 7, seed=61 + n, C=1.0)
+    kw = {} if lam is None else dict(bias_mode=1, bias_lambda=lam)
+    s = gabp.GabpSVM(p.X, p.y, p.gamma, p.C, **kw)
+    Qg = gabp.svm_get_q(s.h, n).astype(np.float64)
+    Qo = oracle.build_q(p.X.astype(np.float64), p.y.astype(np.float64), p.gamma, p.C, lam=lam)
+    np.testing.assert_allclose(np.diag(Qg), np.diag(Qo), rtol=REL_Q)
+
+
 @pytest.mark.parametrize("n,m", SHAPES)
 @pytest.mark.parametrize("iters", [0, 1, 2, 10])
 def test_rounds_match_oracle(n, m, iters):
