@@ -121,3 +121,27 @@ def test_known_fault_tokens_do_not_mask_a_missing_device(lib, monkeypatch):
         with pytest.raises(gabp.GabpError) as ei:
             gabp.svm_create(X, y, 0.5, 1.0)
         assert ei.value.status == gabp.ECUDA, tok
+
+
+def test_binding_input_layouts():
+    """The binding maps torch dtypes onto opts.x_dtype and keeps later rows in
+    the layout the handle was created with (no handle needed: the check is
+    host-side marshalling)."""
+    torch = pytest.importorskip("torch")
+    assert gabp._torch_x_dtype(torch.zeros(2, 2)) == 0
+    assert gabp._torch_x_dtype(torch.zeros(2, 2, dtype=torch.float64)) == 1
+    assert gabp._torch_x_dtype(torch.zeros(2, 2, dtype=torch.bfloat16)) == 2
+    with pytest.raises(TypeError):
+        gabp._torch_x_dtype(torch.zeros(2, 2, dtype=torch.float16))
+    s = object.__new__(gabp.GabpSVM)
+    s.h = None
+    s.x_dtype = 1
+    x = s._x(np.ones((3, 2), np.float32))          # numpy rows are converted to the handle's layout
+    assert x.dtype == np.float64 and x.flags["C_CONTIGUOUS"]
+    with pytest.raises(TypeError):
+        s._x(torch.ones(3, 2))                      # torch rows must already have it
+    s.x_dtype = 2
+    with pytest.raises(TypeError):
+        s._x(np.ones((3, 2), np.float32))           # numpy has no BF16: such handles take torch rows
+    t = torch.ones(3, 2, dtype=torch.bfloat16)
+    assert s._x(t) is t
